@@ -1,0 +1,85 @@
+/*
+ * cvf_oracle.h -- interface of the CPU oracle (test infrastructure only; see
+ * cvf_oracle.c).  This header belongs to the oracle alone: the CUDA library
+ * has its own, independent definitions.
+ */
+#ifndef CVF_ORACLE_H
+#define CVF_ORACLE_H
+#include <stdint.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+
+#define ORC_INIT_RANDOM 0
+#define ORC_INIT_ORDERED 1
+#define ORC_SCHED_CHECKERBOARD 0
+#define ORC_SCHED_LAYERED 1
+
+/* Philox counter word 3 (stream tag) and the reserved counter word 0 values */
+#define ORC_TAG_ACCEPT 0u
+#define ORC_TAG_PROPOSE 1u
+#define ORC_TAG_INIT 2u
+#define ORC_TAG_VOLUME 3u
+#define ORC_TAG_LAYERS 4u
+#define ORC_CELL_VOLUME 0xFFFFFFFFu
+#define ORC_CELL_LAYERS 0xFFFFFFFEu
+
+/* Parameters in reduced units: energies in eps, lengths in r0, volumes in
+   v0 = r0^3 (Table 1). */
+typedef struct {
+  int32_t L, q;
+  double epsilon, cutoff;
+  double J, J_sigma, v_HB;
+  double kT, P;
+  double v_iso_init, dv_max_frac;
+  uint64_t seed;
+  int32_t init, schedule, volume_moves, rng_words;
+} orc_params;
+
+typedef struct {
+  int64_t sweep, n_hb, n_hb_raw, n_coop, acc_sigma, acc_volume;
+  double V_iso, V, U_LJ, H;
+  int32_t g, pad;
+} orc_obs;
+
+typedef struct {
+  orc_params p;
+  int64_t N;
+  uint16_t *w;
+  double V_iso, dV_max;
+  int64_t sweep, n_hb_raw, n_coop, acc_sigma, acc_volume;
+  int32_t g, pad;
+  uint64_t table[2][3][7];
+} orc_state;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4]);
+double orc_lj_cell_energy(double v_iso, double epsilon, double cutoff);
+int orc_shell_table(double cutoff, int64_t *d2s, int64_t *mult, int cap);
+void orc_threshold_table(const orc_params *p, uint64_t out[2][3][7]);
+void orc_recount(const orc_params *p, const uint16_t *w, int64_t *n_hb_raw,
+                 int64_t *n_coop);
+int orc_check_params(const orc_params *p);
+void orc_bond_partner(int32_t L, int64_t c, int arm, int64_t *c_out,
+                      int *arm_out);
+int orc_init(orc_state *st, const orc_params *p, uint16_t *w);
+int orc_set(orc_state *st, const orc_params *p, uint16_t *w, double V_iso,
+            int64_t sweep);
+void orc_volume_move(orc_state *st);
+void orc_step(orc_state *st);
+void orc_observables(const orc_state *st, orc_obs *o);
+int64_t orc_run(orc_state *st, int64_t n, int32_t record_every, orc_obs *ring,
+                int64_t cap);
+void orc_layer_order(const orc_params *p, int64_t step, int order[4]);
+void orc_arm_probe(const orc_params *p, const uint16_t *w, int64_t c, int arm,
+                   uint32_t k, int32_t g, uint32_t *s_new, int32_t *dhb,
+                   int32_t *dc, uint64_t *T);
+void orc_arm_probe_all(const orc_params *p, const uint16_t *cfgs, int64_t n,
+                       int32_t g, uint32_t *s_new, uint64_t *T);
+void orc_window_run(const orc_params *p, uint16_t *w, int32_t x0, int32_t y0,
+                    int32_t W, int32_t H, int64_t step0, int64_t K,
+                    const int32_t *gates);
+int64_t orc_volume_chain(const orc_params *p, double V_iso, int64_t step0,
+                         int64_t K, double *V_out, int32_t *g_out,
+                         int64_t *acc_out);
+#endif
