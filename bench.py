@@ -1,0 +1,329 @@
+"""Benchmark of the CVF Metropolis hot path on GB300.
+
+Workload (one "step"): 1000 MC steps -- each one volume move plus a full
+checkerboard sweep of the four sigma_ij of every cell, with the N_HB /
+N_sigma reductions -- of a 4096 x 4096 lattice (q = 6), cycling through the
+six lattices of the 4096^2 configuration: random (seed 3) and ordered init at
+270, 300 and 330 K, 0.1 MPa.  Inputs (the lattices) are resident in HBM when
+the timed region starts; L2 is flushed between timed steps.
+
+  value  = sigma updates per ns = 4 L^2 x sweeps / device time (CUDA events)
+  e2e    = the same through the C ABI with host buffers: set_state (H2D),
+           sweep, get_state (D2H) and observables inside the timed region
+  --impl reference   times the CPU oracle on the same metric (bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+from dataclasses import asdict
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CVF Metropolis updates/ns at 4096²; batched replica sweeps/s, p50/p99"
+UNIT = "updates/ns"
+L2_FLUSH_BYTES = 512 << 20  # > 126.5 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=4096)
+    ap.add_argument("--sweeps", type=int, default=1000, help="MC steps per benchmark step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-sweeps", type=int, default=10)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_configs(L):
+    from paper_2505_05919_gb300 import workloads
+    cfgs = workloads.c3()
+    for c in cfgs:
+        c["L"] = L
+    return cfgs
+
+
+def oracle_params(cfg, seed_offset=0):
+    import oracle
+    return oracle.physical_params(cfg["T"], cfg["P"], L=cfg["L"], q=cfg["q"],
+                                  seed=cfg["seed"] + seed_offset, init=cfg["init"])
+
+
+def lib_params(cfg, seed_offset=0):
+    """Library parameters from the workload recipe (library-side units)."""
+    from paper_2505_05919_gb300 import params
+    return params(cfg["T"], cfg["P"], L=cfg["L"], q=cfg["q"], seed=cfg["seed"] + seed_offset,
+                  init=cfg["init"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        out.update(sm_mhz=statistics.median(loaded) if loaded else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(cfg, sample_sweeps):
+    """The oracle, single-threaded, on a bounded sample of the workload."""
+    import oracle
+    op = oracle_params(cfg)
+    t0 = time.perf_counter()
+    o = oracle.Oracle(op)
+    t1 = time.perf_counter()
+    o.run(sample_sweeps)
+    t2 = time.perf_counter()
+    upd = 4.0 * cfg["L"] * cfg["L"] * sample_sweeps
+    return {"value": upd / ((t2 - t1) * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "L=%d, %d MC steps from the random init (seed %d, %g K), one thread; "
+                      "init %.1f s not counted" % (cfg["L"], sample_sweeps, cfg["seed"], cfg["T"], t1 - t0)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cfg = workload_configs(args.L)[1]  # random init, 300 K
+    op = oracle_params(cfg)
+    o = oracle.Oracle(op)
+    per_step = max(1, args.cpu_sample_sweeps // 10)
+    for _ in range(args.warmup):
+        o.run(per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.run(per_step)
+    dt = time.perf_counter() - t0
+    upd = 4.0 * args.L * args.L * per_step * args.steps
+    value = upd / (dt * 1e9)
+    sample = ("each step: %d MC step(s) of the L=%d lattice (random init seed %d, %g K, %g MPa) "
+              "by the single-threaded oracle" % (per_step, args.L, cfg["seed"], cfg["T"], cfg["P"]))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16+int64+f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "L=%d q=6 CVF 2D checkerboard Metropolis, oracle sample" % args.L},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2505_05919_gb300 import Lattice, _capi, build as libbuild
+    libbuild.build()
+    _capi.load()
+
+    cfgs = workload_configs(args.L)
+    L, S = args.L, args.sweeps
+    stream = torch.cuda.Stream()
+    lats = []
+    with torch.cuda.stream(stream):
+        for c in cfgs:
+            lats.append(Lattice(lib_params(c, seed_offset=rank * 7919), stream=stream))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up (graphs instantiated here)
+    for i in range(args.warmup):
+        lats[i % len(lats)].sweep(S)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    t_wall0 = time.perf_counter()
+    step_ms = []
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lats[i % len(lats)].sweep(S)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    dev_s = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s = float(t.item())
+    updates = 4.0 * L * L * S * args.steps * world
+    value = updates / (dev_s * 1e9)
+    obs = [l.observables() for l in lats]
+
+    # dominant kernel: the sweep kernels of one MC step, timed alone
+    sw_ms = []
+    lat = lats[1]
+    for _ in range(5):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lat.sweep(200)
+        ev1.record(stream)
+        ev1.synchronize()
+        sw_ms.append(ev0.elapsed_time(ev1) / 200)
+    per_sweep_ms = statistics.median(sw_ms)
+    peaks, peak_kind = measured_peaks()
+    bytes_per_sweep = 4.0 * L * L  # read 2 B + write 2 B per cell (1 B per sigma update)
+    achieved_gbs = bytes_per_sweep / (per_sweep_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "one MC step (volume move + two half-sweep kernels)",
+                "peak_kind": peak_kind}
+
+    # end to end through the C ABI with host buffers
+    e2e_ms = []
+    host_in = np.empty((L, L), np.uint16)
+    host_out = np.empty((L, L), np.uint16)
+    lat = lats[1]
+    host_in[:] = lat.state()
+    V0 = lat.observables()["V_iso"]
+    for i in range(max(2, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.set_state(host_in, V0, 0)
+        lat.sweep(S)
+        _capi.cvf_get_state(lat.h, host_out.ctypes.data, L * L)
+        o = lat.observables()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_s = statistics.median(e2e_ms) / 1e3
+    e2e = {"value": 4.0 * L * L * S / (e2e_s * 1e9), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * L * L, "d2h_bytes_per_step": 2 * L * L + 96}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            try:
+                cpu = cpu_baseline(cfgs[1], args.cpu_sample_sweeps)
+            except Exception as e:  # the baseline never blocks the line
+                cpu = {"value": None, "error": str(e)}
+        launches_per_sweep = 3
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16+int64+f64", "data": "synthetic",
+            "config": {"workload": "CVF 2D L=%d q=6, %d MC steps/step, random(seed 3)+ordered init at "
+                                   "270/300/330 K, 0.1 MPa" % (L, S),
+                       "L": L, "sweeps_per_step": S, "l2": "flushed between timed steps (512 MB write)",
+                       "rng_words": 1, "schedule": "checkerboard"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps * (S * launches_per_sweep + 1),
+            "clocks": clocks,
+            "wall_s": t_wall,
+            "per_sweep_ms": per_sweep_ms,
+            "acceptance": [o["acc_sigma"] / max(1, 4 * L * L * o["sweep"]) for o in obs],
+        }
+        print(json.dumps(line))
+    for l in lats:
+        l.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,179 @@
+/*
+ * cvf.h -- C ABI of the GB300 (sm_103a) CVF Monte Carlo library.
+ *
+ * The library runs the Metropolis hot path of the CVF water model of
+ * arXiv:2505.05919 on one GPU: the parallel update of the hydrogen-bond
+ * indices sigma_ij (Sec. II.C), the counts N_HB and N_sigma of Eq. (H), and
+ * the isobaric update of the global volume V_iso (Sec. II.B, step 1), on a
+ * periodic 2D square lattice with one molecule and four bonding indices per
+ * cell (q states each).  One Monte Carlo step ("sweep") is: one volume move,
+ * then every sigma once (Sec. II.B order V_iso -> eta -> sigma; eta is
+ * identically 1 in 2D because a cell has exactly four neighbours).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an int status: CVF_OK (0) or one of the CVF_E*
+ *     codes below.  cvf_last_error() gives a text for the calling thread's
+ *     last failure.
+ *   - Units are reduced (Table 1): energies in eps (5.5 kJ/mol), lengths in
+ *     r0 (2.9 A), volumes in v0 = r0^3.  cvf_params_physical converts
+ *     (T [K], P [MPa]).
+ *   - Lattice layout: cell c = y*L + x (x fastest), one uint16 word per cell
+ *     holding sigma of arm a in bits [3a, 3a+3) (bits 12..15 zero).  Arms
+ *     0..3 = left, right, front, back; arm 0 points to +x, arm 1 to -x, arm 2
+ *     to +y, arm 3 to -y (the paper's worked example of Sec. II.C: arm 0 of
+ *     cell c pairs with arm 1 of cell c+1).  A bond joins arm a of a cell
+ *     with arm a^1 of its neighbour in direction a.
+ *   - Streams: every handle enqueues its GPU work on the cudaStream_t given
+ *     at creation (passed as void*; NULL = the legacy default stream).  Calls
+ *     that return host data synchronise that stream; the others are
+ *     asynchronous.
+ *   - Ownership: host buffers are always the caller's.  Device memory the
+ *     library allocates is freed by the matching destroy call.  A device
+ *     buffer the caller passes in stays the caller's and must outlive the
+ *     handle.
+ *   - Thread safety: a handle must not be used from two threads at once.
+ */
+#ifndef CVF_H
+#define CVF_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CVF_OK 0
+#define CVF_EINVAL 1    /* invalid argument or parameter */
+#define CVF_ENOMEM 2    /* device or host allocation failed */
+#define CVF_ECUDA 3     /* a CUDA runtime call failed */
+#define CVF_ETIMEOUT 4  /* a bounded device-side wait gave up */
+#define CVF_EBUSY 5     /* the handle has work that conflicts with the call */
+#define CVF_EOVERFLOW 6 /* the observable ring overwrote unread records */
+
+#define CVF_INIT_RANDOM 0
+#define CVF_INIT_ORDERED 1
+#define CVF_SCHED_CHECKERBOARD 0
+#define CVF_SCHED_LAYERED 1
+
+/* Model and run parameters (reduced units).  Sec. II.A names: J and J_sigma
+ * are the covalent and cooperative hydrogen-bond energies of Eq. (H), v_HB
+ * the volume per bond of Eq. (V), epsilon and cutoff the Lennard-Jones
+ * energy and range (Table 1), kT and P the thermodynamic state. */
+typedef struct cvf_params {
+  int32_t L;            /* lattice side, even, 2 <= L <= 65534 */
+  int32_t q;            /* states per bonding index, 2 <= q <= 8 (q = 6, Sec. II.A) */
+  double epsilon;       /* LJ energy scale (1 = eps; 0 switches U_LJ off) */
+  double cutoff;        /* LJ cutoff in r0 (6, Sec. II.A) */
+  double J;             /* covalent HB energy (2.0 = J/(4 eps) 0.5, Table 1) */
+  double J_sigma;       /* cooperative energy (0.32 = J_sigma/(4 eps) 0.08) */
+  double v_HB;          /* volume per HB in v0 (0.6, Sec. II.A) */
+  double kT;            /* temperature, kT/eps > 0 */
+  double P;             /* pressure, P v0/eps */
+  double v_iso_init;    /* initial V_iso / N in v0 (>= 1; default 2^(1/3)) */
+  double dv_max_frac;   /* volume step: |dV| <= dv_max_frac * N v_iso_init */
+  uint64_t seed;        /* Philox4x32-10 key (low word, high word) */
+  int32_t init;         /* CVF_INIT_RANDOM or CVF_INIT_ORDERED (all sigma 0) */
+  int32_t schedule;     /* CVF_SCHED_CHECKERBOARD (default) or CVF_SCHED_LAYERED */
+  int32_t volume_moves; /* 1: isobaric volume move each step; 0: fixed V_iso */
+  int32_t rng_words;    /* 1: one 32-bit word per update (default); 2: two */
+} cvf_params;
+
+/* Observables after a completed step (Eq. V and Eq. H). */
+typedef struct cvf_obs {
+  int64_t sweep;      /* completed MC steps */
+  int64_t n_hb;       /* N_HB = g * N_HB_raw (gas cells form no bonds) */
+  int64_t n_hb_raw;   /* pairs with sigma_ij == sigma_ji */
+  int64_t n_coop;     /* N_sigma: equal pairs inside the cells */
+  int64_t acc_sigma;  /* accepted sigma moves since creation/set_state */
+  int64_t acc_volume; /* accepted volume moves since creation/set_state */
+  double V_iso;       /* isotropic volume, v0 */
+  double V;           /* V = V_iso + v_HB N_HB (Eq. V) */
+  double U_LJ;        /* Lennard-Jones energy, eps */
+  double H;           /* H = U_LJ - J N_HB - J_sigma N_sigma + P V (Eq. H) */
+  int32_t g;          /* gate: 1 liquid-like (V_iso/N < 2 v0), 0 gas-like */
+  int32_t pad;
+} cvf_obs;
+
+typedef struct cvf_handle cvf_handle;
+typedef struct cvf_batch cvf_batch;
+
+/* Text of the calling thread's last error ("" when none).  The pointer is
+ * valid until the next failing call on the same thread. */
+const char *cvf_last_error(void);
+
+/* Fills *out with the Table 1 parameters (L = 64, q = 6, epsilon = 1,
+ * cutoff = 6, J = 2, J_sigma = 0.32, v_HB = 0.6, v_iso_init = 2^(1/3),
+ * dv_max_frac = 0.01, seed 1, random init, checkerboard, volume moves on,
+ * one RNG word per update) at T = 300 K, P = 0.1 MPa. */
+int cvf_params_default(cvf_params *out);
+
+/* Table 1 parameters at the physical state point (T_kelvin, P_MPa):
+ * kT/eps = T R / 5.5 kJ/mol, P v0/eps = P r0^3 N_A / 5.5 kJ/mol.
+ * CVF_EINVAL if T_kelvin <= 0 or out is NULL. */
+int cvf_params_physical(double T_kelvin, double P_MPa, cvf_params *out);
+
+/* The 42 Metropolis thresholds of the parameters (Sec. II.C with Eq. H),
+ * laid out [g][dN_HB + 1][dN_sigma + 3] for g in {0,1}, dN_HB in {-1,0,1},
+ * dN_sigma in {-3..3}: T = 2^32 when dH = -g J_eff dN_HB - J_sigma dN_sigma
+ * <= 0, else floor(exp(-dH/kT) 2^32), J_eff = J - P v_HB.  A move is
+ * accepted when its 32-bit draw u satisfies u < T.  Host only. */
+int cvf_threshold_table(const cvf_params *p, uint64_t out[42]);
+
+/* Creates a lattice handle and initialises it on the device (random init
+ * from Philox((c, 0, 0, 2), seed) or all sigma = 0), with V_iso = N
+ * v_iso_init, N_HB_raw and N_sigma counted, sweep = 0.
+ *   stream     cudaStream_t as void* (NULL: legacy default stream).
+ *   dev_state  NULL: the library allocates the lattice.  Otherwise a device
+ *              buffer of 2*L*L uint16 words (the lattice and its double
+ *              buffer), 16-byte aligned, owned by the caller.
+ *   out        receives the handle.
+ * CVF_EINVAL for invalid parameters, CVF_ENOMEM/CVF_ECUDA on device
+ * failure (nothing is leaked). */
+int cvf_create(const cvf_params *p, void *stream, void *dev_state,
+               cvf_handle **out);
+
+/* Enqueues n_sweeps MC steps (volume move, then the checkerboard -- or
+ * layered -- sigma sweep).  When record_every > 0 the observables after
+ * every step whose count is a multiple of record_every are appended to the
+ * device ring (capacity 65536 records, read with cvf_drain_series).  The
+ * steps run as CUDA graphs; the call returns without waiting.
+ * CVF_EINVAL if n_sweeps < 0 or record_every < 0. */
+int cvf_sweep(cvf_handle *h, int64_t n_sweeps, int32_t record_every);
+
+/* Observables after the last completed step; synchronises the stream. */
+int cvf_observables(cvf_handle *h, cvf_obs *out);
+
+/* Moves the unread ring records (oldest first) into host[0..cap) and sets
+ * *n to their number; synchronises the stream.  Returns CVF_EOVERFLOW (with
+ * the newest records still delivered) when records were overwritten since
+ * the last drain. */
+int cvf_drain_series(cvf_handle *h, cvf_obs *host, int64_t cap, int64_t *n);
+
+/* Copies the lattice (L*L words, layout above) to host; synchronises.
+ * CVF_EINVAL if n != L*L. */
+int cvf_get_state(cvf_handle *h, uint16_t *host, size_t n);
+
+/* Replaces the lattice by host[0..n) (n = L*L), sets V_iso and the step
+ * counter, recounts N_HB_raw and N_sigma, and clears the acceptance
+ * counters and the ring.  Every word is validated on the host first
+ * (arms < q, bits 12..15 zero): CVF_EINVAL otherwise, with nothing changed.
+ * V_iso must be >= N (the hard core).  Synchronises. */
+int cvf_set_state(cvf_handle *h, const uint16_t *host, size_t n, double V_iso,
+                  int64_t sweep);
+
+/* Recounts N_HB_raw and N_sigma from the current lattice with a separate
+ * reduction kernel (independent of the counts the sweep maintains);
+ * synchronises. */
+int cvf_recount(cvf_handle *h, int64_t *n_hb_raw, int64_t *n_sigma);
+
+/* Device address of the current lattice (L*L words), valid until the next
+ * call that enqueues work on the handle. */
+int cvf_state_device_ptr(cvf_handle *h, void **dev_ptr);
+
+/* Waits for the handle's stream, frees what the library allocated. */
+int cvf_destroy(cvf_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CVF_H */

@@ -10,6 +10,7 @@ only builds it with gcc and marshals arguments through ctypes.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass, field, asdict
@@ -132,7 +133,7 @@ class OracleParams:
     v_HB: float = 0.6
     kT: float = 0.4535
     P: float = 2.6704e-4
-    v_iso_init: float = 2.0 ** (1.0 / 3.0)
+    v_iso_init: float = math.cbrt(2.0)
     dv_max_frac: float = 0.01
     seed: int = 1
     init: int = INIT_RANDOM

@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) implementation of the CVF water model's parallel Metropolis
+hot path (arXiv:2505.05919): packed 2D lattice, Philox-driven checkerboard
+sweep, N_HB / N_sigma reductions and the FP64 isobaric volume move, behind
+the C ABI of ``include/cvf.h``."""
+from . import _capi
+from ._capi import CvfError, cvf_params, cvf_obs
+from .lattice import Lattice, params, params_from_dict
+
+__all__ = ["Lattice", "params", "params_from_dict", "CvfError", "cvf_params", "cvf_obs", "_capi"]

@@ -1,0 +1,182 @@
+"""ctypes binding of ``include/cvf.h`` -- argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: the work runs in ``libcvf.so``'s CUDA kernels.  The
+library must have been built (``paper_2505_05919_gb300.build.build()``);
+without it every call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+CVF_OK, CVF_EINVAL, CVF_ENOMEM, CVF_ECUDA, CVF_ETIMEOUT, CVF_EBUSY, CVF_EOVERFLOW = range(7)
+CVF_INIT_RANDOM, CVF_INIT_ORDERED = 0, 1
+CVF_SCHED_CHECKERBOARD, CVF_SCHED_LAYERED = 0, 1
+
+_ERRNAMES = {1: "CVF_EINVAL", 2: "CVF_ENOMEM", 3: "CVF_ECUDA", 4: "CVF_ETIMEOUT",
+             5: "CVF_EBUSY", 6: "CVF_EOVERFLOW"}
+
+
+class CvfError(RuntimeError):
+    def __init__(self, code: int, func: str, text: str):
+        self.code = code
+        super().__init__("%s returned %s: %s" % (func, _ERRNAMES.get(code, str(code)), text))
+
+
+class cvf_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("q", ctypes.c_int32),
+                ("epsilon", ctypes.c_double), ("cutoff", ctypes.c_double),
+                ("J", ctypes.c_double), ("J_sigma", ctypes.c_double),
+                ("v_HB", ctypes.c_double), ("kT", ctypes.c_double),
+                ("P", ctypes.c_double), ("v_iso_init", ctypes.c_double),
+                ("dv_max_frac", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("init", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("volume_moves", ctypes.c_int32), ("rng_words", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class cvf_obs(ctypes.Structure):
+    _fields_ = [("sweep", ctypes.c_int64), ("n_hb", ctypes.c_int64),
+                ("n_hb_raw", ctypes.c_int64), ("n_coop", ctypes.c_int64),
+                ("acc_sigma", ctypes.c_int64), ("acc_volume", ctypes.c_int64),
+                ("V_iso", ctypes.c_double), ("V", ctypes.c_double),
+                ("U_LJ", ctypes.c_double), ("H", ctypes.c_double),
+                ("g", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_SIGS = {
+    "cvf_last_error": (ctypes.c_char_p, []),
+    "cvf_params_default": (ctypes.c_int, [_P(cvf_params)]),
+    "cvf_params_physical": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _P(cvf_params)]),
+    "cvf_threshold_table": (ctypes.c_int, [_P(cvf_params), _P(ctypes.c_uint64)]),
+    "cvf_create": (ctypes.c_int, [_P(cvf_params), _vp, _vp, _P(_vp)]),
+    "cvf_sweep": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int32]),
+    "cvf_observables": (ctypes.c_int, [_vp, _P(cvf_obs)]),
+    "cvf_drain_series": (ctypes.c_int, [_vp, _P(cvf_obs), ctypes.c_int64, _P(ctypes.c_int64)]),
+    "cvf_get_state": (ctypes.c_int, [_vp, _P(ctypes.c_uint16), ctypes.c_size_t]),
+    "cvf_set_state": (ctypes.c_int, [_vp, _P(ctypes.c_uint16), ctypes.c_size_t, ctypes.c_double,
+                                     ctypes.c_int64]),
+    "cvf_recount": (ctypes.c_int, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
+    "cvf_state_device_ptr": (ctypes.c_int, [_vp, _P(_vp)]),
+    "cvf_destroy": (ctypes.c_int, [_vp]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """The loaded libcvf.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError("libcvf.so is not built (run __graft_entry__.build() or "
+                               "paper_2505_05919_gb300.build.build()); there is no fallback")
+    L = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int, func: str) -> int:
+    if rc != CVF_OK:
+        raise CvfError(rc, func, cvf_last_error())
+    return rc
+
+
+def cvf_last_error() -> str:
+    return load().cvf_last_error().decode(errors="replace")
+
+
+def cvf_params_default() -> cvf_params:
+    p = cvf_params()
+    _check(load().cvf_params_default(ctypes.byref(p)), "cvf_params_default")
+    return p
+
+
+def cvf_params_physical(T_kelvin: float, P_MPa: float) -> cvf_params:
+    p = cvf_params()
+    _check(load().cvf_params_physical(T_kelvin, P_MPa, ctypes.byref(p)), "cvf_params_physical")
+    return p
+
+
+def cvf_threshold_table(p: cvf_params):
+    out = (ctypes.c_uint64 * 42)()
+    _check(load().cvf_threshold_table(ctypes.byref(p), out), "cvf_threshold_table")
+    return list(out)
+
+
+def cvf_create(p: cvf_params, stream: int | None = None, dev_state: int | None = None) -> int:
+    h = _vp()
+    _check(load().cvf_create(ctypes.byref(p), stream or None, dev_state or None, ctypes.byref(h)),
+           "cvf_create")
+    return h.value
+
+
+def cvf_sweep(h: int, n_sweeps: int, record_every: int = 0) -> None:
+    _check(load().cvf_sweep(h, n_sweeps, record_every), "cvf_sweep")
+
+
+def cvf_observables(h: int) -> cvf_obs:
+    o = cvf_obs()
+    _check(load().cvf_observables(h, ctypes.byref(o)), "cvf_observables")
+    return o
+
+
+def cvf_drain_series(h: int, cap: int):
+    """Returns (records, overflowed)."""
+    buf = (cvf_obs * max(cap, 1))()
+    n = ctypes.c_int64()
+    rc = load().cvf_drain_series(h, buf, cap, ctypes.byref(n))
+    if rc not in (CVF_OK, CVF_EOVERFLOW):
+        _check(rc, "cvf_drain_series")
+    return [buf[i] for i in range(n.value)], rc == CVF_EOVERFLOW
+
+
+def cvf_get_state(h: int, host_ptr: int, n: int) -> None:
+    _check(load().cvf_get_state(h, ctypes.cast(host_ptr, _P(ctypes.c_uint16)), n), "cvf_get_state")
+
+
+def cvf_set_state(h: int, host_ptr: int, n: int, V_iso: float, sweep: int) -> None:
+    _check(load().cvf_set_state(h, ctypes.cast(host_ptr, _P(ctypes.c_uint16)), n, V_iso, sweep),
+           "cvf_set_state")
+
+
+def cvf_recount(h: int):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().cvf_recount(h, ctypes.byref(a), ctypes.byref(b)), "cvf_recount")
+    return a.value, b.value
+
+
+def cvf_state_device_ptr(h: int) -> int:
+    p = _vp()
+    _check(load().cvf_state_device_ptr(h, ctypes.byref(p)), "cvf_state_device_ptr")
+    return p.value
+
+
+def cvf_destroy(h: int) -> None:
+    _check(load().cvf_destroy(h), "cvf_destroy")

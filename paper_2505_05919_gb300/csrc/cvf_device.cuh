@@ -1,0 +1,322 @@
+// cvf_device.cuh -- device building blocks of the CVF Metropolis path
+// (arXiv:2505.05919): counter-based Philox4x32-10 words, the Metropolis
+// update of the four bonding indices of one cell, bond/pair counting, and the
+// FP64 isobaric volume move.  Included by the kernel translation units only.
+#pragma once
+#include <cstdint>
+
+#include "cvf.h"
+
+namespace cvf {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11).  The counter is (c, step_lo, step_hi,
+// tag); the key is the 64-bit seed.  Ten rounds; the round keys are the seed
+// words advanced by the Weyl constants and are computed once on the host.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxMul0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxMul1 = 0xCD9E8D57u;
+constexpr uint32_t kWeyl0 = 0x9E3779B9u;
+constexpr uint32_t kWeyl1 = 0xBB67AE85u;
+
+constexpr uint32_t kTagAccept = 0u;   // acceptance words (and proposals, 1 word/update)
+constexpr uint32_t kTagPropose = 1u;  // proposal words (2 words/update)
+constexpr uint32_t kTagInit = 2u;     // random initial sigma
+constexpr uint32_t kTagVolume = 3u;   // volume move
+constexpr uint32_t kTagLayers = 4u;   // layered-schedule arm order
+constexpr uint32_t kCellVolume = 0xFFFFFFFFu;
+constexpr uint32_t kCellLayers = 0xFFFFFFFEu;
+
+struct RoundKeys {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+inline RoundKeys make_round_keys(uint64_t seed) {
+  RoundKeys K;
+  uint32_t a = (uint32_t)(seed & 0xFFFFFFFFu), b = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    K.k0[r] = a;
+    K.k1[r] = b;
+    a += kWeyl0;
+    b += kWeyl1;
+  }
+  return K;
+}
+
+struct Words4 {
+  uint32_t x, y, z, w;
+};
+
+// Ten Philox rounds on (x0, x1, x2, x3): counter words 0 and 2 are multiplied
+// by the Philox constants; the high halves are mixed with words 1, 3 and the
+// round key, the low halves become the new words 1 and 3.
+__device__ __forceinline__ Words4 philox(uint32_t x0, uint32_t x1, uint32_t x2,
+                                         uint32_t x3, const RoundKeys& K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t m0 = (uint64_t)x0 * kPhiloxMul0;
+    const uint64_t m1 = (uint64_t)x2 * kPhiloxMul1;
+    const uint32_t y0 = (uint32_t)(m1 >> 32) ^ x1 ^ K.k0[r];
+    const uint32_t y2 = (uint32_t)(m0 >> 32) ^ x3 ^ K.k1[r];
+    x1 = (uint32_t)m1;
+    x3 = (uint32_t)m0;
+    x0 = y0;
+    x2 = y2;
+  }
+  return Words4{x0, x1, x2, x3};
+}
+
+// Same, with the round keys derived from the seed in registers (used where
+// every thread may serve a different replica).
+__device__ __forceinline__ Words4 philox_seed(uint32_t x0, uint32_t x1,
+                                              uint32_t x2, uint32_t x3,
+                                              uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t m0 = (uint64_t)x0 * kPhiloxMul0;
+    const uint64_t m1 = (uint64_t)x2 * kPhiloxMul1;
+    const uint32_t y0 = (uint32_t)(m1 >> 32) ^ x1 ^ k0;
+    const uint32_t y2 = (uint32_t)(m0 >> 32) ^ x3 ^ k1;
+    x1 = (uint32_t)m1;
+    x3 = (uint32_t)m0;
+    x0 = y0;
+    x2 = y2;
+    k0 += kWeyl0;
+    k1 += kWeyl1;
+  }
+  return Words4{x0, x1, x2, x3};
+}
+
+// ---------------------------------------------------------------------------
+// Metropolis update of the four arms of one cell (Sec. II.C).
+//   w        packed cell word (sigma_a in bits [3a, 3a+3))
+//   part[a]  sigma of the arm that arm a bonds with (arm a^1 of the
+//            neighbour in direction a)
+//   acc[a]   32-bit acceptance draw, kk[a] proposal offset in [0, q-1)
+//   T        the 21 thresholds of the current gate, [dN_HB+1][dN_sigma+3]
+// Arms are visited in the order 0..3; each sees the arms already updated.
+// The proposal is sigma' = (sigma + 1 + k) mod q, uniform over the other q-1
+// states; the move is accepted when acc < T(dN_HB, dN_sigma).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t arm_of(uint32_t w, int a) {
+  return (w >> (3 * a)) & 7u;
+}
+
+__device__ __forceinline__ uint32_t update_cell(uint32_t w, const uint32_t part[4],
+                                                const uint32_t acc[4],
+                                                const uint32_t kk[4], uint32_t q,
+                                                const unsigned long long* T,
+                                                uint32_t& naccepted) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const uint32_t s = arm_of(w, a);
+    uint32_t sp = s + 1u + kk[a];
+    sp = (sp >= q) ? sp - q : sp;
+    const uint32_t n = part[a];
+    const int dhb = (int)(sp == n) - (int)(s == n);
+    int dc = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (b == a) continue;
+      const uint32_t sb = arm_of(w, b);
+      dc += (int)(sp == sb) - (int)(s == sb);
+    }
+    const unsigned long long t = T[(dhb + 1) * 7 + (dc + 3)];
+    if ((unsigned long long)acc[a] < t) {
+      w = (w & ~(7u << (3 * a))) | (sp << (3 * a));
+      ++naccepted;
+    }
+  }
+  return w;
+}
+
+// The acceptance draws and proposal offsets of a cell from its Philox words.
+// One word per update: w (q-1) = k 2^32 + u splits into the proposal offset k
+// (high word) and the acceptance draw u (low word).  Two words per update:
+// u from tag 0, k = floor(p (q-1) / 2^32) from tag 1.
+template <int RNG_WORDS>
+__device__ __forceinline__ void cell_draws(uint32_t c, uint32_t step_lo,
+                                           uint32_t step_hi, const RoundKeys& K,
+                                           uint32_t q, uint32_t acc[4],
+                                           uint32_t kk[4]) {
+  const Words4 u = philox(c, step_lo, step_hi, kTagAccept, K);
+  const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+  if (RNG_WORDS == 1) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const uint64_t prod = (uint64_t)uw[a] * (uint64_t)(q - 1u);
+      kk[a] = (uint32_t)(prod >> 32);
+      acc[a] = (uint32_t)prod;
+    }
+  } else {
+    const Words4 p = philox(c, step_lo, step_hi, kTagPropose, K);
+    const uint32_t pw[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      acc[a] = uw[a];
+      kk[a] = __umulhi(pw[a], q - 1u);
+    }
+  }
+}
+
+// Equal pairs among the four arms of a cell (its share of N_sigma).
+__device__ __forceinline__ uint32_t cell_pairs(uint32_t w) {
+  const uint32_t a0 = arm_of(w, 0), a1 = arm_of(w, 1), a2 = arm_of(w, 2),
+                 a3 = arm_of(w, 3);
+  return (uint32_t)(a0 == a1) + (uint32_t)(a0 == a2) + (uint32_t)(a0 == a3) +
+         (uint32_t)(a1 == a2) + (uint32_t)(a1 == a3) + (uint32_t)(a2 == a3);
+}
+
+// Formed bonds of a cell given its four partner arms.
+__device__ __forceinline__ uint32_t cell_bonds(uint32_t w, const uint32_t part[4]) {
+  return (uint32_t)(arm_of(w, 0) == part[0]) + (uint32_t)(arm_of(w, 1) == part[1]) +
+         (uint32_t)(arm_of(w, 2) == part[2]) + (uint32_t)(arm_of(w, 3) == part[3]);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 part: Lennard-Jones energy per cell, volume move, observables.
+// These must evaluate the same IEEE operations in the same order as any other
+// implementation of the same readings; the library is compiled with
+// -fmad=false so no multiply-add is contracted.
+// ---------------------------------------------------------------------------
+constexpr int kMaxShells = 256;
+
+struct VolumeArgs {
+  int64_t N;
+  double epsilon, cutoff2;
+  double J, J_sigma, v_HB, kT, P;
+  double dV_max;
+  int32_t volume_moves;
+  int32_t nshell;
+  double shell_d2[kMaxShells];    // |d|^2 of the square-lattice shells, ascending
+  double shell_mult[kMaxShells];  // number of lattice vectors in each shell
+};
+
+// u(v) = 2 eps sum_shells m [y^6 - y^3], y = 1/(|d|^2 v), over shells with
+// |d|^2 v < cutoff^2 (a pair at lattice vector d of a monolayer of spacing
+// sqrt(v) is at distance sqrt(|d|^2 v); half of each pair per cell).
+__device__ __forceinline__ double lj_cell_energy(const VolumeArgs& V, double v) {
+  double acc = 0.0;
+  for (int s = 0; s < V.nshell; ++s) {
+    const double d2 = V.shell_d2[s];
+    if (!(d2 * v < V.cutoff2)) continue;
+    const double y = 1.0 / (d2 * v);
+    const double y3 = y * y * y;
+    const double y6 = y3 * y3;
+    acc = acc + V.shell_mult[s] * (y6 - y3);
+  }
+  return (2.0 * V.epsilon) * acc;
+}
+
+__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
+  const uint64_t m = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+  return (double)m * (1.0 / 9007199254740992.0);
+}
+
+// Device copy of the handle's scalar state.
+struct Ctrl {
+  // committed state after the last completed step
+  long long sweep;
+  long long n_hb_raw;
+  long long n_coop;
+  long long acc_sigma;
+  long long acc_volume;
+  double V_iso;
+  int g;
+  int record_every;
+  // per-step accumulators (zero between steps)
+  unsigned long long acc_hb;
+  unsigned long long acc_pairs;
+  unsigned long long acc_moves;
+  unsigned int done;
+  unsigned int pad;
+  // observable ring: records written so far (monotone)
+  long long ring_head;
+};
+
+// One volume move (Sec. II.B step 1, with the readings of the oracle):
+// dV = (2 u1 - 1) dV_max, hard core v' >= 1, gate g' = [v' < 2], enthalpy
+// change N du + P dV - (g' - g) J_eff N_HB_raw, acceptance
+// u2 < exp(-dH/kT + N ln(V'/V)).
+__device__ __forceinline__ void volume_move(const VolumeArgs& V, Ctrl* ctl,
+                                            const RoundKeys& K) {
+  const long long step = ctl->sweep;
+  const Words4 r = philox(kCellVolume, (uint32_t)((unsigned long long)step & 0xFFFFFFFFu),
+                          (uint32_t)((unsigned long long)step >> 32), kTagVolume, K);
+  const double u1 = u53(r.x, r.y);
+  const double u2 = u53(r.z, r.w);
+  const double Nd = (double)V.N;
+  const double dV = (2.0 * u1 - 1.0) * V.dV_max;
+  const double V_old = ctl->V_iso;
+  const double V_new = V_old + dV;
+  const double v_old = V_old / Nd;
+  const double v_new = V_new / Nd;
+  if (v_new < 1.0) return;
+  const int g_new = (v_new < 2.0) ? 1 : 0;
+  const double J_eff = V.J - V.P * V.v_HB;
+  const double du = lj_cell_energy(V, v_new) - lj_cell_energy(V, v_old);
+  const double t1 = Nd * du;
+  const double t2 = V.P * dV;
+  const double t3 = ((double)(g_new - ctl->g) * J_eff) * (double)ctl->n_hb_raw;
+  const double dH = (t1 + t2) - t3;
+  const double arg = -dH / V.kT + Nd * log(V_new / V_old);
+  if (u2 < exp(arg)) {
+    ctl->V_iso = V_new;
+    ctl->g = g_new;
+    ctl->acc_volume += 1;
+  }
+}
+
+// Observables of the committed state (Eq. V and Eq. H).
+__device__ __forceinline__ cvf_obs make_obs(const VolumeArgs& V, const Ctrl* ctl) {
+  cvf_obs o;
+  const double Nd = (double)V.N;
+  const long long nhb = ctl->g ? ctl->n_hb_raw : 0;
+  const double U = Nd * lj_cell_energy(V, ctl->V_iso / Nd);
+  const double vol = ctl->V_iso + V.v_HB * (double)nhb;
+  const double H = ((U - V.J * (double)nhb) - V.J_sigma * (double)ctl->n_coop) + V.P * vol;
+  o.sweep = ctl->sweep;
+  o.n_hb = nhb;
+  o.n_hb_raw = ctl->n_hb_raw;
+  o.n_coop = ctl->n_coop;
+  o.acc_sigma = ctl->acc_sigma;
+  o.acc_volume = ctl->acc_volume;
+  o.V_iso = ctl->V_iso;
+  o.V = vol;
+  o.U_LJ = U;
+  o.H = H;
+  o.g = ctl->g;
+  o.pad = 0;
+  return o;
+}
+
+// Block-wide sum of three counters; the result is valid in thread 0.
+template <int NT>
+__device__ __forceinline__ void block_sum3(uint32_t& a, uint32_t& b, uint32_t& c) {
+  __shared__ uint32_t red[3][NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+    c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+    red[2][wid] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = 0; b = 0; c = 0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) {
+      a += red[0][i];
+      b += red[1][i];
+      c += red[2][i];
+    }
+  }
+}
+
+}  // namespace cvf

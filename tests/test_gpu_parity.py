@@ -1,0 +1,223 @@
+"""GPU path vs CPU oracle, through the C ABI.
+
+Bar: the packed lattice is bit-exact, every integer counter is equal, and the
+FP64 observables (V_iso, V, U_LJ, H) agree to a relative 1e-12.  The oracle
+receives its inputs from the seeded workload recipes and its own unit
+conversion, never from the GPU path.
+"""
+from dataclasses import asdict
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_05919_gb300 import Lattice, params_from_dict, _capi, workloads
+
+pytestmark = pytest.mark.gpu
+
+FP_REL = 1e-12
+INT_KEYS = ("sweep", "n_hb", "n_hb_raw", "n_coop", "acc_sigma", "acc_volume", "g")
+FP_KEYS = ("V_iso", "V", "U_LJ", "H")
+
+
+def assert_obs_equal(got, want, ctx=""):
+    for k in INT_KEYS:
+        assert got[k] == want[k], (ctx, k, got[k], want[k])
+    for k in FP_KEYS:
+        assert abs(got[k] - want[k]) <= FP_REL * max(abs(want[k]), 1e-300), (ctx, k, got[k], want[k])
+
+
+def gpu_run(op, K, record_every=0):
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        lat.sweep(K, record_every)
+        state = lat.state()
+        obs = lat.observables()
+        recs, overflow = lat.drain()
+        hb, co = lat.recount()
+    assert not overflow
+    assert (hb, co) == (obs["n_hb_raw"], obs["n_coop"]), "sweep counts differ from the recount kernel"
+    return state, obs, recs
+
+
+def oracle_run(op, K, record_every=0):
+    o = oracle.Oracle(op)
+    recs = o.run(K, record_every)
+    return o.state(), o.observables(), recs
+
+
+CASES = [
+    # L, K, extra parameters
+    (2, 300, {}),
+    (4, 300, dict(q=2)),
+    (6, 200, dict(q=8)),
+    (8, 200, dict(init=oracle.INIT_ORDERED)),
+    (16, 150, dict(rng_words=2)),
+    (64, 1000, {}),                                   # 4096 cells, 1000 steps, ambient
+    (130, 60, dict(T=270.0)),                         # odd number of word pairs per row
+    (130, 40, dict(T=330.0, P=50.0, rng_words=2)),
+    (258, 25, dict(init=oracle.INIT_ORDERED, T=330.0)),
+    (96, 80, dict(volume_moves=0, q=3)),
+]
+
+
+@pytest.mark.parametrize("L,K,extra", CASES, ids=[f"L{c[0]}-K{c[1]}-{i}" for i, c in enumerate(CASES)])
+def test_checkerboard_parity(L, K, extra):
+    extra = dict(extra)
+    T = extra.pop("T", 300.0)
+    P = extra.pop("P", 0.1)
+    op = oracle.physical_params(T, P, L=L, seed=100 + L + K, dv_max_frac=0.02, **extra)
+    s_gpu, o_gpu, _ = gpu_run(op, K)
+    s_ref, o_ref, _ = oracle_run(op, K)
+    assert np.array_equal(s_gpu, s_ref)
+    assert_obs_equal(o_gpu, o_ref)
+    assert 0 <= o_gpu["n_hb_raw"] <= 2 * L * L and 0 <= o_gpu["n_coop"] <= 6 * L * L
+
+
+@pytest.mark.parametrize("L,K,rng_words", [(2, 100, 1), (8, 80, 2), (64, 60, 1), (130, 20, 2)])
+def test_layered_parity(L, K, rng_words):
+    op = oracle.physical_params(300.0, 0.1, L=L, seed=7 + L, schedule=oracle.SCHED_LAYERED,
+                                rng_words=rng_words, dv_max_frac=0.02)
+    s_gpu, o_gpu, _ = gpu_run(op, K)
+    s_ref, o_ref, _ = oracle_run(op, K)
+    assert np.array_equal(s_gpu, s_ref)
+    assert_obs_equal(o_gpu, o_ref)
+
+
+def test_series_parity_record_every():
+    # configuration 2's recording pattern (every 10 steps) on a 64 x 64 lattice
+    op = oracle.physical_params(300.0, 0.1, L=64, seed=2)
+    _, _, r_gpu = gpu_run(op, 200, record_every=10)
+    _, _, r_ref = oracle_run(op, 200, record_every=10)
+    assert len(r_gpu) == len(r_ref) == 20
+    for a, b in zip(r_gpu, r_ref):
+        assert_obs_equal(a, b)
+
+
+@pytest.mark.parametrize("case", ["gas", "gate_flips", "hot", "cold", "no_lj"])
+def test_special_regimes(case):
+    kw = dict(L=16, seed=31)
+    if case == "gas":        # v_iso > 2: gas-like cells form no bonds (g = 0)
+        op = oracle.physical_params(300.0, 0.1, v_iso_init=2.5, **kw)
+    elif case == "gate_flips":  # volume steps large enough to cross v_iso = 2 often
+        op = oracle.OracleParams(kT=3.0, P=0.9, epsilon=0.0, v_iso_init=1.9, dv_max_frac=0.2, **kw)
+    elif case == "hot":
+        op = oracle.OracleParams(kT=1e300, **kw)
+    elif case == "cold":
+        op = oracle.OracleParams(kT=1e-3, init=oracle.INIT_ORDERED, **kw)
+    else:
+        op = oracle.physical_params(300.0, 0.1, epsilon=0.0, **kw)
+    s_gpu, o_gpu, r_gpu = gpu_run(op, 400, record_every=1)
+    s_ref, o_ref, r_ref = oracle_run(op, 400, record_every=1)
+    assert np.array_equal(s_gpu, s_ref)
+    assert_obs_equal(o_gpu, o_ref, case)
+    for a, b in zip(r_gpu, r_ref):
+        assert_obs_equal(a, b, case)
+    if case == "gate_flips":
+        gs = {r["g"] for r in r_ref}
+        assert gs == {0, 1}, "the gate never flipped; the case tests nothing"
+
+
+def test_set_state_resume_bit_exact():
+    op = oracle.physical_params(300.0, 0.1, L=32, seed=9, dv_max_frac=0.05)
+    p = params_from_dict(asdict(op))
+    with Lattice(p) as a:
+        a.sweep(37)
+        mid = a.state()
+        mo = a.observables()
+    with Lattice(p) as b:
+        b.set_state(mid, mo["V_iso"], mo["sweep"])
+        b.sweep(25)
+        s_b, o_b = b.state(), b.observables()
+    ref = oracle.Oracle(op)
+    ref.run(62)
+    assert np.array_equal(s_b, ref.state())
+    want = ref.observables()
+    for k in ("sweep", "n_hb_raw", "n_coop", "g"):
+        assert o_b[k] == want[k]
+    for k in FP_KEYS:
+        assert abs(o_b[k] - want[k]) <= FP_REL * abs(want[k])
+
+
+def test_set_state_arbitrary_configuration():
+    L = 24
+    words = workloads.random_words(L, 5, seed=44)
+    op = oracle.physical_params(300.0, 0.1, L=L, q=5, seed=12)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        lat.set_state(words, V_iso=L * L * 1.3, sweep=1000)
+        assert np.array_equal(lat.state(), words)
+        assert lat.recount() == oracle.recount(op, words)
+        lat.sweep(30)
+        s_gpu, o_gpu = lat.state(), lat.observables()
+    ref = oracle.Oracle(op, state=words, V_iso=L * L * 1.3, sweep=1000)
+    ref.run(30)
+    assert np.array_equal(s_gpu, ref.state())
+    assert_obs_equal(o_gpu, ref.observables())
+
+
+def test_invalid_inputs_rejected():
+    op = oracle.physical_params(300.0, 0.1, L=8, q=6)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        before = lat.state()
+        bad = before.copy()
+        bad[3, 3] = 6  # arm 0 = 6 >= q
+        with pytest.raises(_capi.CvfError) as e:
+            lat.set_state(bad, V_iso=80.0)
+        assert e.value.code == _capi.CVF_EINVAL
+        bad = before.copy()
+        bad[0, 0] |= 1 << 13
+        with pytest.raises(_capi.CvfError):
+            lat.set_state(bad, V_iso=80.0)
+        with pytest.raises(_capi.CvfError):
+            lat.set_state(before, V_iso=63.0)  # below the hard core N v0
+        with pytest.raises(_capi.CvfError):
+            lat.sweep(-1)
+        assert np.array_equal(lat.state(), before)
+        lat.sweep(0)
+        assert lat.observables()["sweep"] == 0
+    with pytest.raises(_capi.CvfError):
+        Lattice(params_from_dict(asdict(oracle.OracleParams(L=7))))
+
+
+def test_ring_overflow_keeps_newest():
+    op = oracle.OracleParams(L=2, volume_moves=0, seed=3)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        lat.sweep(65536 + 100, 1)
+        recs, overflow = lat.drain(1 << 17)
+        assert overflow
+        assert len(recs) == 65536
+        assert recs[0]["sweep"] == 101 and recs[-1]["sweep"] == 65636
+
+
+def test_full_size_sampled_windows():
+    """4096 x 4096, random init seed 3, ambient: the configuration the
+    benchmark times.  The oracle cannot run the whole lattice, so after K
+    steps it recomputes sampled windows: a checkerboard step moves information
+    by at most two cells, so a window run with its border frozen is exact
+    more than 2K cells inside.  V_iso follows from the oracle's own volume
+    chain (no gate flip is proposed at this state point)."""
+    L, K = 4096, 6
+    op = oracle.physical_params(300.0, 0.1, L=L, q=6, seed=3)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        init_gpu = lat.state()
+        lat.sweep(K)
+        s_gpu = lat.state()
+        o_gpu = lat.observables()
+        hb, co = lat.recount()
+    assert (hb, co) == (o_gpu["n_hb_raw"], o_gpu["n_coop"])
+    ref0 = oracle.Oracle(op)
+    assert np.array_equal(init_gpu, ref0.state())
+    done, V, g, acc = oracle.volume_chain(op, ref0.observables()["V_iso"], 0, K)
+    assert done == K
+    assert V[-1] == pytest.approx(o_gpu["V_iso"], rel=FP_REL)
+    assert o_gpu["acc_volume"] == acc
+    rng = np.random.default_rng(2024)
+    margin, inner = 2 * K + 2, 48
+    full = ref0.state()
+    for _ in range(8):
+        x0 = int(rng.integers(0, L - inner - 2 * margin))
+        y0 = int(rng.integers(0, L - inner - 2 * margin))
+        W = inner + 2 * margin
+        out = oracle.window_run(op, full, x0, y0, W, W, 0, g).reshape(L, L)
+        ys, xs = slice(y0 + margin, y0 + margin + inner), slice(x0 + margin, x0 + margin + inner)
+        assert np.array_equal(s_gpu[ys, xs], out[ys, xs])
+    assert 0 < o_gpu["n_hb_raw"] <= 2 * L * L and 0 < o_gpu["n_coop"] <= 6 * L * L
