@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=1000, help="MC steps per benchmark step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-sweeps", type=int, default=10)
+    ap.add_argument("--mode", default="full", choices=["full", "kernel"],
+                    help="kernel: one lattice, warm-up then timed sweeps only (profiling case)")
     return ap.parse_args()
 
 
@@ -188,10 +190,39 @@ def run_reference(args):
     return 0
 
 
+def run_kernel_mode(args):
+    """Small profiling case: one lattice (random init, 300 K), `warmup`
+    sweeps, then `steps` sweeps timed with CUDA events; no flush buffer."""
+    import torch
+    from paper_2505_05919_gb300 import Lattice, _capi, build as libbuild
+    libbuild.build()
+    _capi.load()
+    cfg = workload_configs(args.L)[1]
+    stream = torch.cuda.Stream()
+    lat = Lattice(lib_params(cfg), stream=stream)
+    lat.sweep(args.warmup)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat.sweep(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    o = lat.observables()
+    lat.close()
+    print(json.dumps({"mode": "kernel", "L": args.L, "sweeps": args.steps, "ms": ms,
+                      "updates_per_ns": 4.0 * args.L * args.L * args.steps / (ms * 1e6),
+                      "n_hb_raw": o["n_hb_raw"], "n_coop": o["n_coop"]}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "kernel":
+        return run_kernel_mode(args)
     import numpy as np
     import torch
     rank, world, local = dist_env()
@@ -268,7 +299,7 @@ def main():
     achieved_gbs = bytes_per_sweep / (per_sweep_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "one MC step (volume move + two half-sweep kernels)",
+                "kernel": "one MC step (volume-move kernel + tiled sweep kernel)",
                 "peak_kind": peak_kind}
 
     # end to end through the C ABI with host buffers
@@ -298,7 +329,7 @@ def main():
                 cpu = cpu_baseline(cfgs[1], args.cpu_sample_sweeps)
             except Exception as e:  # the baseline never blocks the line
                 cpu = {"value": None, "error": str(e)}
-        launches_per_sweep = 3
+        launches_per_sweep = 2  # volume move + tiled sweep
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,

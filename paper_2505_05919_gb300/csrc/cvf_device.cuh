@@ -4,6 +4,7 @@
 // FP64 isobaric volume move.  Included by the kernel translation units only.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "cvf.h"
 
@@ -175,6 +176,69 @@ __device__ __forceinline__ uint32_t cell_bonds(uint32_t w, const uint32_t part[4
 }
 
 // ---------------------------------------------------------------------------
+// Same update in the form the sweep kernels use.  Arms are held as 4*sigma
+// (s4[a]); cnt holds, in nibble v, the number of arms of the cell with
+// sigma = v.  For arm a with partner value n the word cnt + 8 << 4n has
+// nibble f(v) = #{b : sigma_b = v} + 8 [n = v], so f(sigma') - f(sigma) =
+// (dN_sigma - 1) + 8 dN_HB, and (dN_HB + 1) * 8 + (dN_sigma + 3) =
+// f(sigma') - f(sigma) + 12 indexes a 24-entry threshold row (entries with
+// dN_sigma + 3 = 7 are never used).  TAB holds T - 1 as uint32 (accept iff
+// u <= T - 1) when no threshold is 0, else T as uint64 (accept iff u < T).
+// ---------------------------------------------------------------------------
+template <bool CMP64>
+struct ThresholdRow {
+  using type = typename std::conditional<CMP64, unsigned long long, uint32_t>::type;
+};
+
+template <bool CMP64>
+__device__ __forceinline__ bool accept_draw(uint32_t u,
+                                            typename ThresholdRow<CMP64>::type t) {
+  if (CMP64)
+    return (unsigned long long)u < (unsigned long long)t;
+  else
+    return u <= (uint32_t)t;
+}
+
+template <bool CMP64>
+__device__ __forceinline__ uint32_t update_cell4(uint32_t w, const uint32_t nb4[4],
+                                                 const uint32_t acc[4], const uint32_t kk[4],
+                                                 uint32_t q4,
+                                                 const typename ThresholdRow<CMP64>::type* T,
+                                                 uint32_t& naccepted, uint32_t& pairs) {
+  uint32_t s4[4];
+  s4[0] = (w << 2) & 0x1Cu;
+  s4[1] = (w >> 1) & 0x1Cu;
+  s4[2] = (w >> 4) & 0x1Cu;
+  s4[3] = (w >> 7) & 0x1Cu;
+  uint32_t oh[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) oh[a] = 1u << s4[a];
+  uint32_t cnt = oh[0] + oh[1] + oh[2] + oh[3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const uint32_t wa = cnt + (8u << nb4[a]);
+    uint32_t sp4 = s4[a] + 4u * kk[a] + 4u;
+    sp4 = (sp4 >= q4) ? sp4 - q4 : sp4;
+    const int fsp = (int)((wa >> sp4) & 0xFu);
+    const int fs = (int)((wa >> s4[a]) & 0xFu);
+    const bool ok = accept_draw<CMP64>(acc[a], T[fsp - fs + 12]);
+    if (ok) {
+      const uint32_t ohp = 1u << sp4;
+      cnt = cnt + ohp - oh[a];
+      oh[a] = ohp;
+      s4[a] = sp4;
+      ++naccepted;
+    }
+  }
+  // equal pairs: sum over arms of (#arms with the same value - 1), halved
+  uint32_t same = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) same += (cnt >> s4[a]) & 0xFu;
+  pairs += (same - 4u) >> 1;
+  return (s4[0] >> 2) | (s4[1] << 1) | (s4[2] << 4) | (s4[3] << 7);
+}
+
+// ---------------------------------------------------------------------------
 // FP64 part: Lennard-Jones energy per cell, volume move, observables.
 // These must evaluate the same IEEE operations in the same order as any other
 // implementation of the same readings; the library is compiled with
@@ -230,7 +294,7 @@ struct Ctrl {
   unsigned long long acc_pairs;
   unsigned long long acc_moves;
   unsigned int done;
-  unsigned int pad;
+  unsigned int tile_next;
   // observable ring: records written so far (monotone)
   long long ring_head;
 };

@@ -42,11 +42,15 @@ __global__ void k_init(uint16_t* __restrict__ state, int32_t L, uint32_t q, int 
 }
 
 // Full recount of N_HB_raw (the +x and +y bond of every cell) and N_sigma
-// (equal pairs inside every cell); adds the totals to out[0], out[1].
-__global__ void __launch_bounds__(kThreads) k_recount(const uint16_t* __restrict__ state,
-                                                      int32_t L,
+// (equal pairs inside every cell); adds the totals to out[0], out[1].  With
+// ctl != nullptr the lattice read is the half of the state pair that the
+// running step writes (buffer (sweep + 1) & 1).
+__global__ void __launch_bounds__(kThreads) k_recount(const uint16_t* __restrict__ base,
+                                                      int32_t L, const Ctrl* ctl,
                                                       unsigned long long* out) {
   const long long N = (long long)L * L;
+  const uint16_t* state = base;
+  if (ctl) state = base + (size_t)((ctl->sweep + 1) & 1) * N;
   uint32_t hb = 0, pairs = 0, unused = 0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
        c += (long long)gridDim.x * blockDim.x) {
@@ -120,6 +124,7 @@ __device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cv
   ctl->acc_pairs = 0;
   ctl->acc_moves = 0;
   ctl->done = 0;
+  ctl->tile_next = 0;
   ctl->sweep += 1;
   const int every = ctl->record_every;
   if (every > 0 && ctl->sweep % every == 0) {
@@ -143,84 +148,188 @@ __device__ __forceinline__ bool last_block(unsigned int* done) {
   return is_last != 0;
 }
 
-// Checkerboard half-sweep (colour k): every cell with (x + y) & 1 == k updates
-// its four arms.  Cells of one colour interact only through cells of the
-// other colour, which stay fixed during the half-sweep, so the update is in
-// place.  One thread handles one 32-bit word = a pair of horizontally
-// adjacent cells, exactly one of which has colour k.  Colour 0 adds the
-// in-cell pair counts of its cells; colour 1 adds those of its cells and the
-// bonds of its cells (every bond has exactly one colour-1 end) and, in the
-// last block, closes the step.
-template <int RNG_WORDS>
-__global__ void __launch_bounds__(kThreads) k_half_sweep(LatticeArgs A, int colour) {
-  __shared__ unsigned long long sT[21];
+// ---------------------------------------------------------------------------
+// Checkerboard sweep, both colours in one launch (Sec. II.C, read for 2D:
+// colour (x + y) & 1, colour 0 first).  The lattice is cut into tiles of
+// kTileRows rows x kTileWords 32-bit words (two cells per word: one of each
+// colour).  A block stages its tile plus a halo of two rows and one word from
+// the step's source buffer, updates the colour-0 cells of the tile and of the
+// one-cell ring around it (the ring's updates are recomputed identically by
+// the neighbouring tile: same inputs, same counter-based draws), then the
+// colour-1 cells of the tile, and writes the tile to the other buffer of the
+// state pair.  Blocks take tiles from a per-step atomic counter.
+// Per tile and per thread the counts of N_sigma (all tile cells), N_HB_raw
+// (the four bonds of every colour-1 cell: each bond has exactly one colour-1
+// end) and accepted moves are summed; the last block closes the step.
+// ---------------------------------------------------------------------------
+constexpr int kTileRows = 64;
+constexpr int kTileWords = 64;
+constexpr int kInRows = kTileRows + 4, kInCols = kTileWords + 2;
+constexpr int kMidRows = kTileRows + 2, kMidCols = kTileWords + 2;
+
+// 4*sigma of arm b of the 16-bit cell in half `hi` of a word.
+__device__ __forceinline__ uint32_t arm4(uint32_t word, int hi, int b) {
+  const int sh = 16 * hi + 3 * b - 2;
+  return (sh >= 0) ? ((word >> sh) & 0x1Cu) : ((word << 2) & 0x1Cu);
+}
+
+// Update the cell in half `hi` of word `own` (row r, word j of a staged
+// grid); xm / xp are the words to the left / right, ym / yp below / above.
+template <int RNG_WORDS, bool CMP64>
+__device__ __forceinline__ uint32_t update_in_word(
+    uint32_t own, uint32_t xm_word, uint32_t xp_word, uint32_t ym_word, uint32_t yp_word, int hi,
+    uint32_t c, uint32_t s_lo, uint32_t s_hi, const RoundKeys& K, uint32_t q,
+    const typename ThresholdRow<CMP64>::type* T, uint32_t& nacc, uint32_t& pairs,
+    uint32_t* bonds) {
+  // partner arms: arm 0 (+x) <-> arm 1 of the +x cell, arm 1 (-x) <-> arm 0 of
+  // the -x cell, arm 2 (+y) <-> arm 3 of the +y cell, arm 3 <-> arm 2 of -y
+  uint32_t nb4[4];
+  if (hi) {
+    nb4[0] = arm4(xp_word, 0, 1);
+    nb4[1] = arm4(own, 0, 0);
+  } else {
+    nb4[0] = arm4(own, 1, 1);
+    nb4[1] = arm4(xm_word, 1, 0);
+  }
+  nb4[2] = arm4(yp_word, hi, 3);
+  nb4[3] = arm4(ym_word, hi, 2);
+  const uint32_t w = hi ? (own >> 16) : (own & 0xFFFFu);
+  uint32_t acc[4], kk[4];
+  cell_draws<RNG_WORDS>(c, s_lo, s_hi, K, q, acc, kk);
+  const uint32_t wn = update_cell4<CMP64>(w, nb4, acc, kk, 4u * q, T, nacc, pairs);
+  if (bonds) {
+    *bonds += (uint32_t)(((wn << 2) & 0x1Cu) == nb4[0]) + (uint32_t)(((wn >> 1) & 0x1Cu) == nb4[1]) +
+              (uint32_t)(((wn >> 4) & 0x1Cu) == nb4[2]) + (uint32_t)(((wn >> 7) & 0x1Cu) == nb4[3]);
+  }
+  return hi ? ((own & 0xFFFFu) | (wn << 16)) : ((own & 0xFFFF0000u) | wn);
+}
+
+template <int RNG_WORDS, bool CMP64>
+__global__ void __launch_bounds__(kThreads) k_sweep_tiled(LatticeArgs A) {
+  using TT = typename ThresholdRow<CMP64>::type;
+  __shared__ uint32_t s_in[kInRows][kInCols];
+  __shared__ uint32_t s_mid[kMidRows][kMidCols];
+  __shared__ TT sT[24];
+  __shared__ int s_tile;
   Ctrl* ctl = A.ctrl;
   const int g = ctl->g;
   const long long step = ctl->sweep;
-  if (threadIdx.x < 21) sT[threadIdx.x] = A.table[g * 21 + threadIdx.x];
-  __syncthreads();
+  if (threadIdx.x < 24) {
+    const unsigned long long t = A.table24[g * 24 + threadIdx.x];
+    sT[threadIdx.x] = CMP64 ? (TT)t : (TT)(uint32_t)(t - 1ull);
+  }
   const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
   const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
   const int L = A.L;
   const int Lh = L >> 1;
-  const long long npairs = (long long)L * Lh;
-  const uint32_t* __restrict__ st32 = reinterpret_cast<const uint32_t*>(A.state);
+  const long long N = (long long)L * L;
+  const uint32_t* __restrict__ src =
+      reinterpret_cast<const uint32_t*>(A.state + (size_t)(step & 1) * N);
+  uint32_t* __restrict__ dst = reinterpret_cast<uint32_t*>(A.state + (size_t)((step + 1) & 1) * N);
+  const int tiles_x = (Lh + kTileWords - 1) / kTileWords;
+  const int ntiles = tiles_x * ((L + kTileRows - 1) / kTileRows);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = kThreads / 32;
   uint32_t pairs = 0, bonds = 0, nacc = 0;
-  for (long long pi = blockIdx.x * (long long)blockDim.x + threadIdx.x; pi < npairs;
-       pi += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(pi / Lh);
-    const int p = (int)(pi - (long long)y * Lh);
-    const int hi = (y + colour) & 1;  // own cell in the high half of the word
-    const int x = 2 * p + hi;
-    const uint32_t own = st32[pi];
-    const uint32_t wyp = st32[(long long)(y + 1 == L ? 0 : y + 1) * Lh + p];
-    const uint32_t wym = st32[(long long)(y == 0 ? L - 1 : y - 1) * Lh + p];
-    uint32_t w, nxp, nxm;
-    if (hi) {
-      w = own >> 16;
-      nxm = own & 0xFFFFu;
-      nxp = st32[(long long)y * Lh + (p + 1 == Lh ? 0 : p + 1)] & 0xFFFFu;
-    } else {
-      w = own & 0xFFFFu;
-      nxp = own >> 16;
-      nxm = st32[(long long)y * Lh + (p == 0 ? Lh - 1 : p - 1)] >> 16;
+  for (;;) {
+    __syncthreads();  // previous tile fully consumed; sT visible
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctl->tile_next, 1u);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const int y0 = (t / tiles_x) * kTileRows;
+    const int p0 = (t % tiles_x) * kTileWords;
+    const int th = min(kTileRows, L - y0);
+    const int tw = min(kTileWords, Lh - p0);
+    // stage rows y0-2 .. y0+th+1, words p0-1 .. p0+tw (periodic)
+    for (int rr = warp; rr < th + 4; rr += kWarps) {
+      int y = y0 + rr - 2;
+      y = (y < 0) ? y + L : (y >= L ? y - L : y);
+      const uint32_t* row = src + (size_t)y * Lh;
+      for (int jj = lane; jj < tw + 2; jj += 32) {
+        int p = p0 + jj - 1;
+        p = (p < 0) ? p + Lh : (p >= Lh ? p - Lh : p);
+        s_in[rr][jj] = row[p];
+      }
     }
-    const uint32_t nyp = hi ? (wyp >> 16) : (wyp & 0xFFFFu);
-    const uint32_t nym = hi ? (wym >> 16) : (wym & 0xFFFFu);
-    // partner arms: arm 0 (+x) <-> arm 1 of the +x cell, arm 1 (-x) <-> arm 0
-    // of the -x cell, arm 2 (+y) <-> arm 3 of the +y cell, arm 3 <-> arm 2
-    const uint32_t part[4] = {arm_of(nxp, 1), arm_of(nxm, 0), arm_of(nyp, 3), arm_of(nym, 2)};
-    uint32_t acc[4], kk[4];
-    cell_draws<RNG_WORDS>((uint32_t)((long long)y * L + x), s_lo, s_hi, A.keys, A.q, acc, kk);
-    w = update_cell(w, part, acc, kk, A.q, sT, nacc);
-    A.state[(long long)y * L + x] = (uint16_t)w;
-    pairs += cell_pairs(w);
-    if (colour) bonds += cell_bonds(w, part);
+    __syncthreads();
+    // colour 0: tile rows -1 .. th, words 0 .. tw-1 (the colour-0 cell of a
+    // word is its low half on even rows, its high half on odd rows)
+    for (int r = warp - 1; r <= th; r += kWarps) {
+      const int y = y0 + r;
+      const int hi = y & 1;
+      const int yg = (y < 0) ? y + L : (y >= L ? y - L : y);
+      const bool inside = (r >= 0) && (r < th);
+      for (int j = lane; j < tw; j += 32) {
+        const int xg = 2 * (p0 + j) + hi;
+        uint32_t dummy = 0;
+        const uint32_t out = update_in_word<RNG_WORDS, CMP64>(
+            s_in[r + 2][j + 1], s_in[r + 2][j], s_in[r + 2][j + 2], s_in[r + 1][j + 1],
+            s_in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), s_lo, s_hi, A.keys,
+            A.q, sT, inside ? nacc : dummy, inside ? pairs : dummy, nullptr);
+        s_mid[r + 1][j + 1] = out;
+      }
+    }
+    // colour 0 on the ring: per row r the one colour-0 cell just outside the
+    // tile, x0 - 1 (high half of word -1) on odd rows, x0 + 2 tw (low half of
+    // word tw) on even rows
+    for (int i = threadIdx.x; i < th + 2; i += kThreads) {
+      const int r = i - 1;
+      const int y = y0 + r;
+      const int hi = y & 1;
+      const int j = hi ? -1 : tw;
+      const int yg = (y < 0) ? y + L : (y >= L ? y - L : y);
+      int xg = 2 * (p0 + j) + hi;
+      xg = (xg < 0) ? xg + L : (xg >= L ? xg - L : xg);
+      uint32_t dummy = 0, dummy2 = 0;
+      // the unused side of the ring word is clamped into the staged columns
+      const int jm = max(j, 0), jp = min(j + 2, tw + 1);
+      const uint32_t out = update_in_word<RNG_WORDS, CMP64>(
+          s_in[r + 2][j + 1], s_in[r + 2][jm], s_in[r + 2][jp], s_in[r + 1][j + 1],
+          s_in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), s_lo, s_hi, A.keys, A.q,
+          sT, dummy, dummy2, nullptr);
+      s_mid[r + 1][j + 1] = out;
+    }
+    __syncthreads();
+    // colour 1: tile rows 0 .. th-1 (low half on odd rows, high on even rows)
+    for (int r = warp; r < th; r += kWarps) {
+      const int y = y0 + r;
+      const int hi = (y & 1) ^ 1;
+      uint32_t* drow = dst + (size_t)y * Lh + p0;
+      for (int j = lane; j < tw; j += 32) {
+        const int xg = 2 * (p0 + j) + hi;
+        const uint32_t out = update_in_word<RNG_WORDS, CMP64>(
+            s_mid[r + 1][j + 1], s_mid[r + 1][j], s_mid[r + 1][j + 2], s_mid[r][j + 1],
+            s_mid[r + 2][j + 1], hi, (uint32_t)((long long)y * L + xg), s_lo, s_hi, A.keys, A.q,
+            sT, nacc, pairs, &bonds);
+        drow[j] = out;
+      }
+    }
   }
   block_sum3<kThreads>(pairs, bonds, nacc);
   if (threadIdx.x == 0) {
     atomicAdd(&ctl->acc_pairs, (unsigned long long)pairs);
-    if (colour) atomicAdd(&ctl->acc_hb, (unsigned long long)bonds);
+    atomicAdd(&ctl->acc_hb, (unsigned long long)bonds);
     atomicAdd(&ctl->acc_moves, (unsigned long long)nacc);
   }
-  if (colour == 1 && last_block(&ctl->done) && threadIdx.x == 0)
-    finalize_step(*A.vol, ctl, A.ring, A.ring_cap);
+  if (last_block(&ctl->done) && threadIdx.x == 0) finalize_step(*A.vol, ctl, A.ring, A.ring_cap);
 }
 
 // Layered schedule: pass `pass` updates arm order[pass] of every cell, where
 // the order is a Fisher-Yates permutation drawn from Philox((2^32-2, step,
 // tag 4)).  The same arm of all cells forms one domain (its members interact
-// only with other domains), so the pass is in place.
+// only with other domains).  Pass 0 reads the step's source buffer and writes
+// every cell to the other buffer; passes 1..3 update that buffer in place.
 template <int RNG_WORDS>
 __global__ void __launch_bounds__(kThreads) k_layer_pass(LatticeArgs A, int pass) {
-  __shared__ unsigned long long sT[21];
+  __shared__ unsigned long long sT[24];
   __shared__ int s_arm;
   Ctrl* ctl = A.ctrl;
   const int g = ctl->g;
   const long long step = ctl->sweep;
   const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
   const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
-  if (threadIdx.x < 21) sT[threadIdx.x] = A.table[g * 21 + threadIdx.x];
+  if (threadIdx.x < 24) sT[threadIdx.x] = A.table24[g * 24 + threadIdx.x];
   if (threadIdx.x == 0) {
     const Words4 r = philox(kCellLayers, s_lo, s_hi, kTagLayers, A.keys);
     const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
@@ -237,6 +346,8 @@ __global__ void __launch_bounds__(kThreads) k_layer_pass(LatticeArgs A, int pass
   const int a = s_arm;
   const int L = A.L;
   const long long N = (long long)L * L;
+  uint16_t* dst = A.state + (size_t)((step + 1) & 1) * N;
+  const uint16_t* src = (pass == 0) ? A.state + (size_t)(step & 1) * N : dst;
   uint32_t nacc = 0, unused0 = 0, unused1 = 0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
        c += (long long)gridDim.x * blockDim.x) {
@@ -246,8 +357,8 @@ __global__ void __launch_bounds__(kThreads) k_layer_pass(LatticeArgs A, int pass
     else if (a == 1) xn = (x == 0) ? L - 1 : x - 1;
     else if (a == 2) yn = (y + 1 == L) ? 0 : y + 1;
     else yn = (y == 0) ? L - 1 : y - 1;
-    const uint32_t w = A.state[c];
-    const uint32_t n = arm_of(A.state[(long long)yn * L + xn], a ^ 1);
+    const uint32_t w = src[c];
+    const uint32_t n = arm_of(src[(long long)yn * L + xn], a ^ 1);
     uint32_t acc[4], kk[4];
     cell_draws<RNG_WORDS>((uint32_t)c, s_lo, s_hi, A.keys, A.q, acc, kk);
     const uint32_t s = arm_of(w, a);
@@ -260,10 +371,12 @@ __global__ void __launch_bounds__(kThreads) k_layer_pass(LatticeArgs A, int pass
       const uint32_t sb = arm_of(w, b);
       dc += (int)(sp == sb) - (int)(s == sb);
     }
-    if ((unsigned long long)acc[a] < sT[(dhb + 1) * 7 + (dc + 3)]) {
-      A.state[c] = (uint16_t)((w & ~(7u << (3 * a))) | (sp << (3 * a)));
+    uint32_t wn = w;
+    if ((unsigned long long)acc[a] < sT[(dhb + 1) * 8 + (dc + 3)]) {
+      wn = (w & ~(7u << (3 * a))) | (sp << (3 * a));
       ++nacc;
     }
+    if (pass == 0 || wn != w) dst[c] = (uint16_t)wn;
   }
   block_sum3<kThreads>(nacc, unused0, unused1);
   if (threadIdx.x == 0) atomicAdd(&ctl->acc_moves, (unsigned long long)nacc);
@@ -291,12 +404,14 @@ struct cvf_handle {
   long long ring_cap;
   long long ring_tail;
   cvf_obs* obs_dev;
-  unsigned long long* table_dev;
+  unsigned long long* table_dev;     // [2][24] (dN_HB+1)*8 + dN_sigma+3
+  bool cmp64;                        // some threshold is 0: compare in 64 bits
+  long long sweep_host;              // steps enqueued so far: buffer sweep & 1 is current
   VolumeArgs* vol_dev;
   unsigned long long* rc_dev;
   void* host_pinned;
   LatticeArgs args;
-  int grid_pairs, grid_cells;
+  int grid_tiles, grid_cells;
   cudaGraphExec_t graph;
   int graph_steps;
 };
@@ -332,12 +447,14 @@ void enqueue_step(cvf_handle* h, cudaStream_t s) {
   if (h->p.volume_moves) k_volume_move<<<1, 32, 0, s>>>(h->vol_dev, h->ctrl, h->args.keys);
   const bool one = h->p.rng_words == 1;
   if (h->p.schedule == CVF_SCHED_CHECKERBOARD) {
-    for (int colour = 0; colour < 2; ++colour) {
-      if (one)
-        k_half_sweep<1><<<h->grid_pairs, kThreads, 0, s>>>(h->args, colour);
-      else
-        k_half_sweep<2><<<h->grid_pairs, kThreads, 0, s>>>(h->args, colour);
-    }
+    if (one && !h->cmp64)
+      k_sweep_tiled<1, false><<<h->grid_tiles, kThreads, 0, s>>>(h->args);
+    else if (one)
+      k_sweep_tiled<1, true><<<h->grid_tiles, kThreads, 0, s>>>(h->args);
+    else if (!h->cmp64)
+      k_sweep_tiled<2, false><<<h->grid_tiles, kThreads, 0, s>>>(h->args);
+    else
+      k_sweep_tiled<2, true><<<h->grid_tiles, kThreads, 0, s>>>(h->args);
   } else {
     for (int pass = 0; pass < 4; ++pass) {
       if (one)
@@ -345,15 +462,34 @@ void enqueue_step(cvf_handle* h, cudaStream_t s) {
       else
         k_layer_pass<2><<<h->grid_cells, kThreads, 0, s>>>(h->args, pass);
     }
-    k_recount<<<h->grid_cells, kThreads, 0, s>>>(h->state, h->p.L, &h->ctrl->acc_hb);
+    k_recount<<<h->grid_cells, kThreads, 0, s>>>(h->state, h->p.L, h->ctrl, &h->ctrl->acc_hb);
     k_finalize<<<1, 32, 0, s>>>(h->args);
   }
+}
+
+// The half of the state pair that holds the lattice after the enqueued steps.
+uint16_t* current(cvf_handle* h) { return h->state + (size_t)(h->sweep_host & 1) * h->N; }
+
+// Persistent grid of the tiled sweep: as many blocks as fit on the GPU at
+// once, but no more than there are tiles.
+int tiled_grid(int L, bool cmp64, int rng_words) {
+  int per_sm = 1;
+  const void* fn = (rng_words == 1)
+                       ? (cmp64 ? (const void*)k_sweep_tiled<1, true> : (const void*)k_sweep_tiled<1, false>)
+                       : (cmp64 ? (const void*)k_sweep_tiled<2, true> : (const void*)k_sweep_tiled<2, false>);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const long long tiles = (long long)((L / 2 + kTileWords - 1) / kTileWords) *
+                          ((L + kTileRows - 1) / kTileRows);
+  return (int)std::max<long long>(1, std::min<long long>(tiles, (long long)sm_count() * per_sm));
 }
 
 int recount_into_ctrl(cvf_handle* h) {
   // acc_hb and acc_pairs are adjacent: the recount adds into both
   static_assert(offsetof(Ctrl, acc_pairs) == offsetof(Ctrl, acc_hb) + 8, "layout");
-  k_recount<<<h->grid_cells, kThreads, 0, h->stream>>>(h->state, h->p.L, &h->ctrl->acc_hb);
+  k_recount<<<h->grid_cells, kThreads, 0, h->stream>>>(current(h), h->p.L, nullptr,
+                                                       &h->ctrl->acc_hb);
   k_commit_counts<<<1, 32, 0, h->stream>>>(h->ctrl);
   CVF_CUDA_CHECK(cudaGetLastError());
   return CVF_OK;
@@ -420,13 +556,24 @@ int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** 
   CREATE_CHECK(cudaMalloc(&h->ctrl, sizeof(Ctrl)));
   CREATE_CHECK(cudaMalloc(&h->ring, sizeof(cvf_obs) * (size_t)h->ring_cap));
   CREATE_CHECK(cudaMalloc(&h->obs_dev, sizeof(cvf_obs)));
-  CREATE_CHECK(cudaMalloc(&h->table_dev, sizeof(unsigned long long) * 42));
+  CREATE_CHECK(cudaMalloc(&h->table_dev, sizeof(unsigned long long) * 48));
   CREATE_CHECK(cudaMalloc(&h->vol_dev, sizeof(VolumeArgs)));
   CREATE_CHECK(cudaMalloc(&h->rc_dev, sizeof(unsigned long long) * 2));
   CREATE_CHECK(cudaMallocHost(&h->host_pinned, 4096));
 
   uint64_t table[42];
   threshold_table(p, table);
+  // device layout [g][(dN_HB+1)*8 + dN_sigma+3]; slot dN_sigma+3 = 7 unused
+  unsigned long long table24[48];
+  std::memset(table24, 0, sizeof(table24));
+  h->cmp64 = false;
+  for (int g = 0; g < 2; ++g)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 7; ++j) {
+        const uint64_t t = table[(g * 3 + i) * 7 + j];
+        table24[g * 24 + i * 8 + j] = t;
+        if (t == 0) h->cmp64 = true;
+      }
   VolumeArgs va;
   std::memset(&va, 0, sizeof(va));
   va.N = h->N;
@@ -444,20 +591,22 @@ int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** 
     va.shell_d2[i] = (double)d2[i];
     va.shell_mult[i] = (double)mult[i];
   }
-  CREATE_CHECK(cudaMemcpyAsync(h->table_dev, table, sizeof(table), cudaMemcpyHostToDevice, h->stream));
+  CREATE_CHECK(cudaMemcpyAsync(h->table_dev, table24, sizeof(table24), cudaMemcpyHostToDevice,
+                               h->stream));
   CREATE_CHECK(cudaMemcpyAsync(h->vol_dev, &va, sizeof(va), cudaMemcpyHostToDevice, h->stream));
   CREATE_CHECK(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
 
   h->args.state = h->state;
   h->args.ctrl = h->ctrl;
-  h->args.table = h->table_dev;
+  h->args.table24 = h->table_dev;
   h->args.vol = h->vol_dev;
   h->args.ring = h->ring;
   h->args.ring_cap = h->ring_cap;
   h->args.keys = make_round_keys(p->seed);
   h->args.L = p->L;
   h->args.q = (uint32_t)p->q;
-  h->grid_pairs = grid_for(h->N / 2, 8);
+  h->grid_tiles = tiled_grid(h->p.L, h->cmp64, h->p.rng_words);
+  h->sweep_host = 0;
   h->grid_cells = grid_for(h->N, 8);
 
   k_init<<<h->grid_cells, kThreads, 0, h->stream>>>(h->state, p->L, (uint32_t)p->q,
@@ -494,6 +643,7 @@ int cvf_sweep(cvf_handle* h, int64_t n_sweeps, int32_t record_every) {
   }
   for (; left > 0; --left) enqueue_step(h, h->stream);
   CVF_CUDA_CHECK(cudaGetLastError());
+  h->sweep_host += n_sweeps;
   return CVF_OK;
 }
 
@@ -540,7 +690,7 @@ int cvf_drain_series(cvf_handle* h, cvf_obs* host, int64_t cap, int64_t* n) {
 int cvf_get_state(cvf_handle* h, uint16_t* host, size_t n) {
   if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");
   if ((long long)n != h->N) return set_error(CVF_EINVAL, "n=%zu, lattice has %lld cells", n, h->N);
-  CVF_CUDA_CHECK(cudaMemcpyAsync(host, h->state, sizeof(uint16_t) * n, cudaMemcpyDeviceToHost,
+  CVF_CUDA_CHECK(cudaMemcpyAsync(host, current(h), sizeof(uint16_t) * n, cudaMemcpyDeviceToHost,
                                  h->stream));
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
   return CVF_OK;
@@ -559,7 +709,8 @@ int cvf_set_state(cvf_handle* h, const uint16_t* host, size_t n, double V_iso, i
         (((w >> 9) & 7u) >= q))
       return set_error(CVF_EINVAL, "word %zu = 0x%04x is not a valid cell for q = %u", i, w, q);
   }
-  CVF_CUDA_CHECK(cudaMemcpyAsync(h->state, host, sizeof(uint16_t) * n, cudaMemcpyHostToDevice,
+  h->sweep_host = sweep;
+  CVF_CUDA_CHECK(cudaMemcpyAsync(current(h), host, sizeof(uint16_t) * n, cudaMemcpyHostToDevice,
                                  h->stream));
   k_set_ctrl<<<1, 32, 0, h->stream>>>(h->ctrl, V_iso, sweep, h->N);
   int rc = recount_into_ctrl(h);
@@ -572,7 +723,7 @@ int cvf_set_state(cvf_handle* h, const uint16_t* host, size_t n, double V_iso, i
 int cvf_recount(cvf_handle* h, int64_t* n_hb_raw, int64_t* n_sigma) {
   if (!h || !n_hb_raw || !n_sigma) return set_error(CVF_EINVAL, "NULL argument");
   CVF_CUDA_CHECK(cudaMemsetAsync(h->rc_dev, 0, sizeof(unsigned long long) * 2, h->stream));
-  k_recount<<<h->grid_cells, kThreads, 0, h->stream>>>(h->state, h->p.L, h->rc_dev);
+  k_recount<<<h->grid_cells, kThreads, 0, h->stream>>>(current(h), h->p.L, nullptr, h->rc_dev);
   CVF_CUDA_CHECK(cudaGetLastError());
   CVF_CUDA_CHECK(cudaMemcpyAsync(h->host_pinned, h->rc_dev, sizeof(unsigned long long) * 2,
                                  cudaMemcpyDeviceToHost, h->stream));
@@ -585,7 +736,7 @@ int cvf_recount(cvf_handle* h, int64_t* n_hb_raw, int64_t* n_sigma) {
 
 int cvf_state_device_ptr(cvf_handle* h, void** dev_ptr) {
   if (!h || !dev_ptr) return set_error(CVF_EINVAL, "NULL argument");
-  *dev_ptr = h->state;
+  *dev_ptr = current(h);
   return CVF_OK;
 }
 
