@@ -122,9 +122,13 @@ static uint32_t orc_arm(uint16_t word, int arm) {
 /* vector d is |d|^2 v_iso.  A pair contributes 4 eps [(1/dist)^12 -         */
 /* (1/dist)^6] when dist < cutoff (strict).  Every cell sees the same        */
 /* infinite-lattice neighbourhood, so U_LJ = N u(v_iso) with                 */
-/*   u(v) = 1/2 sum_{d != 0, |d|^2 v < cutoff^2} 4 eps [y^6 - y^3],          */
-/*   y = 1 / (|d|^2 v),                                                      */
-/* summed shell by shell in increasing |d|^2.  v >= 1 is the hard core.      */
+/*   u(v) = 1/2 sum_{d != 0, |d|^2 v < cutoff^2} 4 eps [(x/|d|^2)^6 -        */
+/*          (x/|d|^2)^3],  x = v0/v_iso = 1/v,                               */
+/* evaluated as 2 eps [x^6 S12(n) - x^3 S6(n)], where the n shells with      */
+/* |d|^2 v < cutoff^2 are the first n in increasing |d|^2 and S12, S6 are    */
+/* the prefix sums of m/|d|^12 and m/|d|^6 over shells (m = number of        */
+/* lattice vectors in the shell), accumulated in increasing |d|^2.           */
+/* v >= 1 is the hard core.                                                  */
 /* ------------------------------------------------------------------------ */
 #define ORC_MAX_SHELLS 4096
 static int orc_shells(double cutoff, int64_t d2s[], int64_t mult[]) {
@@ -148,25 +152,29 @@ static int orc_shells(double cutoff, int64_t d2s[], int64_t mult[]) {
 }
 
 double orc_lj_cell_energy(double v_iso, double epsilon, double cutoff) {
-  /* the shell list depends on the cutoff only; keep the last one */
+  /* the shell list and its prefix sums depend on the cutoff only */
   static int64_t d2s[ORC_MAX_SHELLS], mult[ORC_MAX_SHELLS];
+  static double S12[ORC_MAX_SHELLS + 1], S6[ORC_MAX_SHELLS + 1];
   static double last_cutoff = -1.0;
   static int n = 0;
   if (cutoff != last_cutoff) {
     n = orc_shells(cutoff, d2s, mult);
+    S12[0] = 0.0;
+    S6[0] = 0.0;
+    for (int s = 0; s < n; ++s) {
+      int64_t d6 = d2s[s] * d2s[s] * d2s[s];
+      S12[s + 1] = S12[s] + (double)mult[s] / ((double)d6 * (double)d6);
+      S6[s + 1] = S6[s] + (double)mult[s] / (double)d6;
+    }
     last_cutoff = cutoff;
   }
   double rc2 = cutoff * cutoff;
-  double acc = 0.0;
-  for (int s = 0; s < n; ++s) {
-    double d2 = (double)d2s[s];
-    if (!(d2 * v_iso < rc2)) continue;
-    double y = 1.0 / (d2 * v_iso);
-    double y3 = y * y * y;
-    double y6 = y3 * y3;
-    acc = acc + (double)mult[s] * (y6 - y3);
-  }
-  return (2.0 * epsilon) * acc;
+  int k = 0;
+  while (k < n && (double)d2s[k] * v_iso < rc2) ++k;
+  double x = 1.0 / v_iso;
+  double x3 = x * x * x;
+  double x6 = x3 * x3;
+  return (2.0 * epsilon) * (x6 * S12[k] - x3 * S6[k]);
 }
 
 int orc_shell_table(double cutoff, int64_t *d2s, int64_t *mult, int cap) {

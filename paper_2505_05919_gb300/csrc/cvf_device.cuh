@@ -176,14 +176,19 @@ __device__ __forceinline__ uint32_t cell_bonds(uint32_t w, const uint32_t part[4
 }
 
 // ---------------------------------------------------------------------------
-// Same update in the form the sweep kernels use.  Arms are held as 4*sigma
-// (s4[a]); cnt holds, in nibble v, the number of arms of the cell with
-// sigma = v.  For arm a with partner value n the word cnt + 8 << 4n has
-// nibble f(v) = #{b : sigma_b = v} + 8 [n = v], so f(sigma') - f(sigma) =
-// (dN_sigma - 1) + 8 dN_HB, and (dN_HB + 1) * 8 + (dN_sigma + 3) =
-// f(sigma') - f(sigma) + 12 indexes a 24-entry threshold row (entries with
-// dN_sigma + 3 = 7 are never used).  TAB holds T - 1 as uint32 (accept iff
-// u <= T - 1) when no threshold is 0, else T as uint64 (accept iff u < T).
+// Same update in the form the sweep kernels use, arranged so that most of the
+// integer work runs as multiply-adds (the FMA pipe) rather than as shifts and
+// logic ops (the ALU pipe, which is the busier one).
+//
+// cnt holds, in nibble v, the number of arms of the cell with sigma = v.  For
+// a value v let oh(v) = 2^(4v) and m(v) = 2^(28-4v); the nibble v of a word X
+// is then (X * m(v)) >> 28, a multiply and a high multiply by 16.  For arm a
+// with partner value n the word cnt + 8 oh(n) has nibble f(v) = #{b : sigma_b
+// = v} + 8 [n = v], so f(sigma') - f(sigma) = (dN_sigma - 1) + 8 dN_HB, and
+// (dN_HB + 1) * 8 + (dN_sigma + 3) = f(sigma') - f(sigma) + 12 indexes a
+// 24-entry threshold row (entries with dN_sigma + 3 = 7 are never used).
+// TAB holds T - 1 as uint32 (accept iff u <= T - 1) when no threshold is 0,
+// else T as uint64 (accept iff u < T).
 // ---------------------------------------------------------------------------
 template <bool CMP64>
 struct ThresholdRow {
@@ -199,43 +204,60 @@ __device__ __forceinline__ bool accept_draw(uint32_t u,
     return u <= (uint32_t)t;
 }
 
-template <bool CMP64>
-__device__ __forceinline__ uint32_t update_cell4(uint32_t w, const uint32_t nb4[4],
-                                                 const uint32_t acc[4], const uint32_t kk[4],
-                                                 uint32_t q4,
-                                                 const typename ThresholdRow<CMP64>::type* T,
-                                                 uint32_t& naccepted, uint32_t& pairs) {
-  uint32_t s4[4];
-  s4[0] = (w << 2) & 0x1Cu;
-  s4[1] = (w >> 1) & 0x1Cu;
-  s4[2] = (w >> 4) & 0x1Cu;
-  s4[3] = (w >> 7) & 0x1Cu;
-  uint32_t oh[4];
+// Nibble `v` (given as m(v)) of x.
+__device__ __forceinline__ uint32_t nibble(uint32_t x, uint32_t mv) {
+  return __umulhi(x * mv, 16u);
+}
+
+// Update the four arms of one cell.
+//   t4[a]  4 * sigma_a of the cell (in/out)
+//   nb8[a] 8 oh(partner value of arm a)
+//   acc, kk  acceptance draws and proposal offsets
+//   q4     4 q
+//   T      threshold row (24 entries, see above)
+// Adds the accepted moves to naccepted and the cell's equal-pair count,
+// plus 4, times 2 (sum over arms of the number of arms sharing its value) to
+// pair_sum; returns the bonds formed with the partners when BONDS.
+template <bool CMP64, bool BONDS>
+__device__ __forceinline__ uint32_t update_arms(uint32_t t4[4], const uint32_t nb8[4],
+                                                const uint32_t acc[4], const uint32_t kk[4],
+                                                uint32_t q4,
+                                                const typename ThresholdRow<CMP64>::type* T,
+                                                uint32_t& naccepted, uint32_t& pair_sum) {
+  uint32_t oh[4], m[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) oh[a] = 1u << s4[a];
+  for (int a = 0; a < 4; ++a) {
+    oh[a] = 1u << t4[a];
+    m[a] = 0x10000000u >> t4[a];
+  }
   uint32_t cnt = oh[0] + oh[1] + oh[2] + oh[3];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    const uint32_t wa = cnt + (8u << nb4[a]);
-    uint32_t sp4 = s4[a] + 4u * kk[a] + 4u;
-    sp4 = (sp4 >= q4) ? sp4 - q4 : sp4;
-    const int fsp = (int)((wa >> sp4) & 0xFu);
-    const int fs = (int)((wa >> s4[a]) & 0xFu);
+    const uint32_t wa = cnt + nb8[a];
+    uint32_t tp = t4[a] + 4u * kk[a] + 4u;
+    tp = (tp >= q4) ? tp - q4 : tp;
+    const uint32_t mp = 0x10000000u >> tp;
+    const int fsp = (int)nibble(wa, mp);
+    const int fs = (int)nibble(wa, m[a]);
     const bool ok = accept_draw<CMP64>(acc[a], T[fsp - fs + 12]);
     if (ok) {
-      const uint32_t ohp = 1u << sp4;
+      const uint32_t ohp = 1u << tp;
       cnt = cnt + ohp - oh[a];
       oh[a] = ohp;
-      s4[a] = sp4;
+      m[a] = mp;
+      t4[a] = tp;
       ++naccepted;
     }
   }
-  // equal pairs: sum over arms of (#arms with the same value - 1), halved
-  uint32_t same = 0;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) same += (cnt >> s4[a]) & 0xFu;
-  pairs += (same - 4u) >> 1;
-  return (s4[0] >> 2) | (s4[1] << 1) | (s4[2] << 4) | (s4[3] << 7);
+  for (int a = 0; a < 4; ++a) pair_sum += nibble(cnt, m[a]);
+  uint32_t bonds = 0;
+  if (BONDS) {
+    // nb8 * m = 2^(31 + 4 (n - sigma)) mod 2^32: bit 31 set iff n == sigma
+#pragma unroll
+    for (int a = 0; a < 4; ++a) bonds += __umulhi(nb8[a] * m[a], 2u);
+  }
+  return bonds;
 }
 
 // ---------------------------------------------------------------------------
@@ -253,24 +275,21 @@ struct VolumeArgs {
   double dV_max;
   int32_t volume_moves;
   int32_t nshell;
-  double shell_d2[kMaxShells];    // |d|^2 of the square-lattice shells, ascending
-  double shell_mult[kMaxShells];  // number of lattice vectors in each shell
+  double shell_d2[kMaxShells];   // |d|^2 of the square-lattice shells, ascending
+  double S12[kMaxShells + 1];    // prefix sums of m / |d|^12 over the shells
+  double S6[kMaxShells + 1];     // prefix sums of m / |d|^6
 };
 
-// u(v) = 2 eps sum_shells m [y^6 - y^3], y = 1/(|d|^2 v), over shells with
-// |d|^2 v < cutoff^2 (a pair at lattice vector d of a monolayer of spacing
-// sqrt(v) is at distance sqrt(|d|^2 v); half of each pair per cell).
+// u(v) = 2 eps [x^6 S12(n) - x^3 S6(n)], x = 1/v, n = number of shells with
+// |d|^2 v < cutoff^2: the LJ energy per cell of a monolayer of lattice
+// spacing sqrt(v) (half of each pair per cell), shell by shell.
 __device__ __forceinline__ double lj_cell_energy(const VolumeArgs& V, double v) {
-  double acc = 0.0;
-  for (int s = 0; s < V.nshell; ++s) {
-    const double d2 = V.shell_d2[s];
-    if (!(d2 * v < V.cutoff2)) continue;
-    const double y = 1.0 / (d2 * v);
-    const double y3 = y * y * y;
-    const double y6 = y3 * y3;
-    acc = acc + V.shell_mult[s] * (y6 - y3);
-  }
-  return (2.0 * V.epsilon) * acc;
+  int k = 0;
+  while (k < V.nshell && V.shell_d2[k] * v < V.cutoff2) ++k;
+  const double x = 1.0 / v;
+  const double x3 = x * x * x;
+  const double x6 = x3 * x3;
+  return (2.0 * V.epsilon) * (x6 * V.S12[k] - x3 * V.S6[k]);
 }
 
 __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
@@ -287,8 +306,24 @@ struct Ctrl {
   long long acc_sigma;
   long long acc_volume;
   double V_iso;
+  double u_cell;        // u(V_iso / N)
   int g;
   int record_every;
+  // the volume move of step `sweep` (already decided; its gate drives the
+  // sigma sweep of that step)
+  double next_V;
+  double next_u;
+  int next_g;
+  int next_acc;
+  // the volume move of step `sweep + 1`, decided early by the sweep kernel
+  // when it does not depend on the bonds (ahead_state 1), or left to the end
+  // of the step (ahead_state 0)
+  double ahead_V;
+  double ahead_u;
+  int ahead_g;
+  int ahead_acc;
+  int ahead_state;
+  int pad0;
   // per-step accumulators (zero between steps)
   unsigned long long acc_hb;
   unsigned long long acc_pairs;
@@ -299,37 +334,53 @@ struct Ctrl {
   long long ring_head;
 };
 
-// One volume move (Sec. II.B step 1, with the readings of the oracle):
-// dV = (2 u1 - 1) dV_max, hard core v' >= 1, gate g' = [v' < 2], enthalpy
-// change N du + P dV - (g' - g) J_eff N_HB_raw, acceptance
-// u2 < exp(-dH/kT + N ln(V'/V)).
-__device__ __forceinline__ void volume_move(const VolumeArgs& V, Ctrl* ctl,
-                                            const RoundKeys& K) {
-  const long long step = ctl->sweep;
+struct VolumeResult {
+  double V, u;
+  int g, accepted;
+};
+
+// The volume move of MC step `step` (Sec. II.B step 1, with the oracle's
+// readings): dV = (2 u1 - 1) dV_max from Philox((2^32-1, step, 3)); the hard
+// core rejects v' < 1; the gate is g' = [v' < 2]; the enthalpy change is
+// N (u(v') - u(v)) + P dV - (g' - g) J_eff N_HB_raw and the move is accepted
+// when u2 < exp(-dH/kT + N ln(V'/V)).  When n_hb_raw < 0 (bonds not yet
+// known) and the proposal would change the gate, returns false and decides
+// nothing; otherwise fills *out and returns true.
+__device__ __forceinline__ bool volume_decide(const VolumeArgs& V, long long step, double V_old,
+                                              double u_old, int g, long long n_hb_raw,
+                                              const RoundKeys& K, VolumeResult* out) {
+  out->V = V_old;
+  out->u = u_old;
+  out->g = g;
+  out->accepted = 0;
+  if (!V.volume_moves) return true;
   const Words4 r = philox(kCellVolume, (uint32_t)((unsigned long long)step & 0xFFFFFFFFu),
                           (uint32_t)((unsigned long long)step >> 32), kTagVolume, K);
   const double u1 = u53(r.x, r.y);
   const double u2 = u53(r.z, r.w);
   const double Nd = (double)V.N;
   const double dV = (2.0 * u1 - 1.0) * V.dV_max;
-  const double V_old = ctl->V_iso;
   const double V_new = V_old + dV;
-  const double v_old = V_old / Nd;
   const double v_new = V_new / Nd;
-  if (v_new < 1.0) return;
+  if (v_new < 1.0) return true;
   const int g_new = (v_new < 2.0) ? 1 : 0;
+  if (g_new != g && n_hb_raw < 0) return false;
   const double J_eff = V.J - V.P * V.v_HB;
-  const double du = lj_cell_energy(V, v_new) - lj_cell_energy(V, v_old);
+  const double u_new = lj_cell_energy(V, v_new);
+  const double du = u_new - u_old;
   const double t1 = Nd * du;
   const double t2 = V.P * dV;
-  const double t3 = ((double)(g_new - ctl->g) * J_eff) * (double)ctl->n_hb_raw;
+  // with unknown bonds the gate is unchanged here, so the bond term is zero
+  const double t3 = ((double)(g_new - g) * J_eff) * (double)(n_hb_raw < 0 ? 0 : n_hb_raw);
   const double dH = (t1 + t2) - t3;
   const double arg = -dH / V.kT + Nd * log(V_new / V_old);
   if (u2 < exp(arg)) {
-    ctl->V_iso = V_new;
-    ctl->g = g_new;
-    ctl->acc_volume += 1;
+    out->V = V_new;
+    out->u = u_new;
+    out->g = g_new;
+    out->accepted = 1;
   }
+  return true;
 }
 
 // Observables of the committed state (Eq. V and Eq. H).
@@ -337,7 +388,7 @@ __device__ __forceinline__ cvf_obs make_obs(const VolumeArgs& V, const Ctrl* ctl
   cvf_obs o;
   const double Nd = (double)V.N;
   const long long nhb = ctl->g ? ctl->n_hb_raw : 0;
-  const double U = Nd * lj_cell_energy(V, ctl->V_iso / Nd);
+  const double U = Nd * ctl->u_cell;
   const double vol = ctl->V_iso + V.v_HB * (double)nhb;
   const double H = ((U - V.J * (double)nhb) - V.J_sigma * (double)ctl->n_coop) + V.P * vol;
   o.sweep = ctl->sweep;

@@ -80,11 +80,15 @@ __global__ void k_commit_counts(Ctrl* ctl) {
   }
 }
 
-__global__ void k_set_ctrl(Ctrl* ctl, double V_iso, long long sweep, long long N) {
+__global__ void k_set_ctrl(const VolumeArgs* __restrict__ V, Ctrl* ctl, double V_iso,
+                           long long sweep, long long N) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ctl->sweep = sweep;
     ctl->V_iso = V_iso;
+    ctl->u_cell = lj_cell_energy(*V, V_iso / (double)N);
     ctl->g = (V_iso / (double)N < 2.0) ? 1 : 0;
+    ctl->ahead_state = 0;
+    ctl->tile_next = 0;
     ctl->acc_sigma = 0;
     ctl->acc_volume = 0;
     ctl->acc_hb = 0;
@@ -100,9 +104,19 @@ __global__ void k_set_record(Ctrl* ctl, int record_every) {
   if (threadIdx.x == 0 && blockIdx.x == 0) ctl->record_every = record_every;
 }
 
-// One volume move (single thread).
-__global__ void k_volume_move(const VolumeArgs* __restrict__ V, Ctrl* ctl, RoundKeys K) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) volume_move(*V, ctl, K);
+// The volume move of the next step from the committed state (run once after
+// the lattice or the counters are (re)set; afterwards every step's end
+// prepares the move of the following step).
+__global__ void k_volume_prologue(const VolumeArgs* __restrict__ V, Ctrl* ctl, RoundKeys K) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    VolumeResult r;
+    volume_decide(*V, ctl->sweep, ctl->V_iso, ctl->u_cell, ctl->g, ctl->n_hb_raw, K, &r);
+    ctl->next_V = r.V;
+    ctl->next_u = r.u;
+    ctl->next_g = r.g;
+    ctl->next_acc = r.accepted;
+    ctl->ahead_state = 0;
+  }
 }
 
 __global__ void k_observables(const VolumeArgs* __restrict__ V, const Ctrl* ctl,
@@ -111,15 +125,21 @@ __global__ void k_observables(const VolumeArgs* __restrict__ V, const Ctrl* ctl,
 }
 
 // End of a step, run by one thread once every block's counts are in:
-// commit the counts, advance the step counter, append the observables to the
-// ring when the step count is a multiple of record_every.
+// commit the counts and the step's volume move, advance the step counter,
+// append the observables to the ring when the step count is a multiple of
+// record_every, and settle the volume move of the next step (taken from the
+// early decision when there is one, else decided now with the new bonds).
 __device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cvf_obs* ring,
-                                              long long ring_cap) {
+                                              long long ring_cap, const RoundKeys& K) {
   volatile Ctrl* vc = ctl;
   const unsigned long long hb = vc->acc_hb, pairs = vc->acc_pairs, moves = vc->acc_moves;
   ctl->n_hb_raw = (long long)hb;
   ctl->n_coop = (long long)pairs;
   ctl->acc_sigma += (long long)moves;
+  ctl->V_iso = ctl->next_V;
+  ctl->u_cell = ctl->next_u;
+  ctl->g = ctl->next_g;
+  ctl->acc_volume += ctl->next_acc;
   ctl->acc_hb = 0;
   ctl->acc_pairs = 0;
   ctl->acc_moves = 0;
@@ -131,6 +151,20 @@ __device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cv
     ring[ctl->ring_head % ring_cap] = make_obs(V, ctl);
     ctl->ring_head += 1;
   }
+  VolumeResult r;
+  if (vc->ahead_state == 1) {
+    r.V = vc->ahead_V;
+    r.u = vc->ahead_u;
+    r.g = vc->ahead_g;
+    r.accepted = vc->ahead_acc;
+  } else {
+    volume_decide(V, ctl->sweep, ctl->V_iso, ctl->u_cell, ctl->g, ctl->n_hb_raw, K, &r);
+  }
+  ctl->next_V = r.V;
+  ctl->next_u = r.u;
+  ctl->next_g = r.g;
+  ctl->next_acc = r.accepted;
+  ctl->ahead_state = 0;
 }
 
 // True in every thread of the block that arrives last (after all blocks
@@ -175,32 +209,34 @@ __device__ __forceinline__ uint32_t arm4(uint32_t word, int hi, int b) {
 
 // Update the cell in half `hi` of word `own` (row r, word j of a staged
 // grid); xm / xp are the words to the left / right, ym / yp below / above.
-template <int RNG_WORDS, bool CMP64>
+template <int RNG_WORDS, bool CMP64, bool BONDS>
 __device__ __forceinline__ uint32_t update_in_word(
     uint32_t own, uint32_t xm_word, uint32_t xp_word, uint32_t ym_word, uint32_t yp_word, int hi,
     uint32_t c, uint32_t s_lo, uint32_t s_hi, const RoundKeys& K, uint32_t q,
-    const typename ThresholdRow<CMP64>::type* T, uint32_t& nacc, uint32_t& pairs,
-    uint32_t* bonds) {
+    const typename ThresholdRow<CMP64>::type* T, uint32_t& nacc, uint32_t& pair_sum,
+    uint32_t& bonds) {
   // partner arms: arm 0 (+x) <-> arm 1 of the +x cell, arm 1 (-x) <-> arm 0 of
   // the -x cell, arm 2 (+y) <-> arm 3 of the +y cell, arm 3 <-> arm 2 of -y
-  uint32_t nb4[4];
+  uint32_t n4[4];
   if (hi) {
-    nb4[0] = arm4(xp_word, 0, 1);
-    nb4[1] = arm4(own, 0, 0);
+    n4[0] = arm4(xp_word, 0, 1);
+    n4[1] = arm4(own, 0, 0);
   } else {
-    nb4[0] = arm4(own, 1, 1);
-    nb4[1] = arm4(xm_word, 1, 0);
+    n4[0] = arm4(own, 1, 1);
+    n4[1] = arm4(xm_word, 1, 0);
   }
-  nb4[2] = arm4(yp_word, hi, 3);
-  nb4[3] = arm4(ym_word, hi, 2);
-  const uint32_t w = hi ? (own >> 16) : (own & 0xFFFFu);
+  n4[2] = arm4(yp_word, hi, 3);
+  n4[3] = arm4(ym_word, hi, 2);
+  uint32_t nb8[4], t4[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    nb8[a] = 8u << n4[a];
+    t4[a] = arm4(own, hi, a);
+  }
   uint32_t acc[4], kk[4];
   cell_draws<RNG_WORDS>(c, s_lo, s_hi, K, q, acc, kk);
-  const uint32_t wn = update_cell4<CMP64>(w, nb4, acc, kk, 4u * q, T, nacc, pairs);
-  if (bonds) {
-    *bonds += (uint32_t)(((wn << 2) & 0x1Cu) == nb4[0]) + (uint32_t)(((wn >> 1) & 0x1Cu) == nb4[1]) +
-              (uint32_t)(((wn >> 4) & 0x1Cu) == nb4[2]) + (uint32_t)(((wn >> 7) & 0x1Cu) == nb4[3]);
-  }
+  bonds += update_arms<CMP64, BONDS>(t4, nb8, acc, kk, 4u * q, T, nacc, pair_sum);
+  const uint32_t wn = (t4[0] >> 2) | (t4[1] << 1) | (t4[2] << 4) | (t4[3] << 7);
   return hi ? ((own & 0xFFFFu) | (wn << 16)) : ((own & 0xFFFF0000u) | wn);
 }
 
@@ -212,8 +248,26 @@ __global__ void __launch_bounds__(kThreads) k_sweep_tiled(LatticeArgs A) {
   __shared__ TT sT[24];
   __shared__ int s_tile;
   Ctrl* ctl = A.ctrl;
-  const int g = ctl->g;
+  const int g = ctl->next_g;
   const long long step = ctl->sweep;
+  if (blockIdx.x == 0) {
+    // the volume block: decide the next step's volume move now when it does
+    // not depend on this step's bonds, while the other blocks sweep
+    if (threadIdx.x == 0) {
+      VolumeResult r;
+      if (volume_decide(*A.vol, step + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1, A.keys,
+                        &r)) {
+        ctl->ahead_V = r.V;
+        ctl->ahead_u = r.u;
+        ctl->ahead_g = r.g;
+        ctl->ahead_acc = r.accepted;
+        ctl->ahead_state = 1;
+      }
+    }
+    if (last_block(&ctl->done) && threadIdx.x == 0)
+      finalize_step(*A.vol, ctl, A.ring, A.ring_cap, A.keys);
+    return;
+  }
   if (threadIdx.x < 24) {
     const unsigned long long t = A.table24[g * 24 + threadIdx.x];
     sT[threadIdx.x] = CMP64 ? (TT)t : (TT)(uint32_t)(t - 1ull);
@@ -230,7 +284,8 @@ __global__ void __launch_bounds__(kThreads) k_sweep_tiled(LatticeArgs A) {
   const int ntiles = tiles_x * ((L + kTileRows - 1) / kTileRows);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int kWarps = kThreads / 32;
-  uint32_t pairs = 0, bonds = 0, nacc = 0;
+  // pair_sum adds, per counted cell, 4 + 2 * (its equal pairs)
+  uint32_t pair_sum = 0, ncells = 0, bonds = 0, nacc = 0;
   for (;;) {
     __syncthreads();  // previous tile fully consumed; sT visible
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctl->tile_next, 1u);
@@ -262,11 +317,12 @@ __global__ void __launch_bounds__(kThreads) k_sweep_tiled(LatticeArgs A) {
       const bool inside = (r >= 0) && (r < th);
       for (int j = lane; j < tw; j += 32) {
         const int xg = 2 * (p0 + j) + hi;
-        uint32_t dummy = 0;
-        const uint32_t out = update_in_word<RNG_WORDS, CMP64>(
+        uint32_t dummy = 0, dummy_b = 0;
+        const uint32_t out = update_in_word<RNG_WORDS, CMP64, false>(
             s_in[r + 2][j + 1], s_in[r + 2][j], s_in[r + 2][j + 2], s_in[r + 1][j + 1],
             s_in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), s_lo, s_hi, A.keys,
-            A.q, sT, inside ? nacc : dummy, inside ? pairs : dummy, nullptr);
+            A.q, sT, inside ? nacc : dummy, inside ? pair_sum : dummy, dummy_b);
+        if (inside) ++ncells;
         s_mid[r + 1][j + 1] = out;
       }
     }
@@ -281,13 +337,13 @@ __global__ void __launch_bounds__(kThreads) k_sweep_tiled(LatticeArgs A) {
       const int yg = (y < 0) ? y + L : (y >= L ? y - L : y);
       int xg = 2 * (p0 + j) + hi;
       xg = (xg < 0) ? xg + L : (xg >= L ? xg - L : xg);
-      uint32_t dummy = 0, dummy2 = 0;
+      uint32_t dummy = 0, dummy2 = 0, dummy3 = 0;
       // the unused side of the ring word is clamped into the staged columns
       const int jm = max(j, 0), jp = min(j + 2, tw + 1);
-      const uint32_t out = update_in_word<RNG_WORDS, CMP64>(
+      const uint32_t out = update_in_word<RNG_WORDS, CMP64, false>(
           s_in[r + 2][j + 1], s_in[r + 2][jm], s_in[r + 2][jp], s_in[r + 1][j + 1],
           s_in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), s_lo, s_hi, A.keys, A.q,
-          sT, dummy, dummy2, nullptr);
+          sT, dummy, dummy2, dummy3);
       s_mid[r + 1][j + 1] = out;
     }
     __syncthreads();
@@ -298,21 +354,24 @@ __global__ void __launch_bounds__(kThreads) k_sweep_tiled(LatticeArgs A) {
       uint32_t* drow = dst + (size_t)y * Lh + p0;
       for (int j = lane; j < tw; j += 32) {
         const int xg = 2 * (p0 + j) + hi;
-        const uint32_t out = update_in_word<RNG_WORDS, CMP64>(
+        const uint32_t out = update_in_word<RNG_WORDS, CMP64, true>(
             s_mid[r + 1][j + 1], s_mid[r + 1][j], s_mid[r + 1][j + 2], s_mid[r][j + 1],
             s_mid[r + 2][j + 1], hi, (uint32_t)((long long)y * L + xg), s_lo, s_hi, A.keys, A.q,
-            sT, nacc, pairs, &bonds);
+            sT, nacc, pair_sum, bonds);
+        ++ncells;
         drow[j] = out;
       }
     }
   }
+  uint32_t pairs = (pair_sum - 4u * ncells) >> 1;
   block_sum3<kThreads>(pairs, bonds, nacc);
   if (threadIdx.x == 0) {
     atomicAdd(&ctl->acc_pairs, (unsigned long long)pairs);
     atomicAdd(&ctl->acc_hb, (unsigned long long)bonds);
     atomicAdd(&ctl->acc_moves, (unsigned long long)nacc);
   }
-  if (last_block(&ctl->done) && threadIdx.x == 0) finalize_step(*A.vol, ctl, A.ring, A.ring_cap);
+  if (last_block(&ctl->done) && threadIdx.x == 0)
+    finalize_step(*A.vol, ctl, A.ring, A.ring_cap, A.keys);
 }
 
 // Layered schedule: pass `pass` updates arm order[pass] of every cell, where
@@ -325,7 +384,7 @@ __global__ void __launch_bounds__(kThreads) k_layer_pass(LatticeArgs A, int pass
   __shared__ unsigned long long sT[24];
   __shared__ int s_arm;
   Ctrl* ctl = A.ctrl;
-  const int g = ctl->g;
+  const int g = ctl->next_g;
   const long long step = ctl->sweep;
   const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
   const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
@@ -384,7 +443,8 @@ __global__ void __launch_bounds__(kThreads) k_layer_pass(LatticeArgs A, int pass
 
 // Close a layered step after the recount of its final configuration.
 __global__ void k_finalize(LatticeArgs A) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) finalize_step(*A.vol, A.ctrl, A.ring, A.ring_cap);
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    finalize_step(*A.vol, A.ctrl, A.ring, A.ring_cap, A.keys);
 }
 
 }  // namespace cvf
@@ -444,7 +504,6 @@ void release(cvf_handle* h) {
 
 // Enqueue one MC step on stream s.
 void enqueue_step(cvf_handle* h, cudaStream_t s) {
-  if (h->p.volume_moves) k_volume_move<<<1, 32, 0, s>>>(h->vol_dev, h->ctrl, h->args.keys);
   const bool one = h->p.rng_words == 1;
   if (h->p.schedule == CVF_SCHED_CHECKERBOARD) {
     if (one && !h->cmp64)
@@ -482,7 +541,8 @@ int tiled_grid(int L, bool cmp64, int rng_words) {
     per_sm = 1;
   const long long tiles = (long long)((L / 2 + kTileWords - 1) / kTileWords) *
                           ((L + kTileRows - 1) / kTileRows);
-  return (int)std::max<long long>(1, std::min<long long>(tiles, (long long)sm_count() * per_sm));
+  // + 1: block 0 decides the next volume move instead of taking tiles
+  return 1 + (int)std::max<long long>(1, std::min<long long>(tiles, (long long)sm_count() * per_sm));
 }
 
 int recount_into_ctrl(cvf_handle* h) {
@@ -491,6 +551,7 @@ int recount_into_ctrl(cvf_handle* h) {
   k_recount<<<h->grid_cells, kThreads, 0, h->stream>>>(current(h), h->p.L, nullptr,
                                                        &h->ctrl->acc_hb);
   k_commit_counts<<<1, 32, 0, h->stream>>>(h->ctrl);
+  k_volume_prologue<<<1, 32, 0, h->stream>>>(h->vol_dev, h->ctrl, h->args.keys);
   CVF_CUDA_CHECK(cudaGetLastError());
   return CVF_OK;
 }
@@ -587,9 +648,13 @@ int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** 
   va.dV_max = p->dv_max_frac * ((double)h->N * p->v_iso_init);
   va.volume_moves = p->volume_moves;
   va.nshell = (int)d2.size();
+  va.S12[0] = 0.0;
+  va.S6[0] = 0.0;
   for (size_t i = 0; i < d2.size(); ++i) {
     va.shell_d2[i] = (double)d2[i];
-    va.shell_mult[i] = (double)mult[i];
+    const int64_t d6 = d2[i] * d2[i] * d2[i];
+    va.S12[i + 1] = va.S12[i] + (double)mult[i] / ((double)d6 * (double)d6);
+    va.S6[i + 1] = va.S6[i] + (double)mult[i] / (double)d6;
   }
   CREATE_CHECK(cudaMemcpyAsync(h->table_dev, table24, sizeof(table24), cudaMemcpyHostToDevice,
                                h->stream));
@@ -612,7 +677,8 @@ int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** 
   k_init<<<h->grid_cells, kThreads, 0, h->stream>>>(h->state, p->L, (uint32_t)p->q,
                                                      p->init == CVF_INIT_RANDOM ? 1 : 0,
                                                      h->args.keys);
-  k_set_ctrl<<<1, 32, 0, h->stream>>>(h->ctrl, (double)h->N * p->v_iso_init, 0, h->N);
+  k_set_ctrl<<<1, 32, 0, h->stream>>>(h->vol_dev, h->ctrl, (double)h->N * p->v_iso_init, 0,
+                                      h->N);
   rc = recount_into_ctrl(h);
   if (rc) {
     release(h);
@@ -712,7 +778,7 @@ int cvf_set_state(cvf_handle* h, const uint16_t* host, size_t n, double V_iso, i
   h->sweep_host = sweep;
   CVF_CUDA_CHECK(cudaMemcpyAsync(current(h), host, sizeof(uint16_t) * n, cudaMemcpyHostToDevice,
                                  h->stream));
-  k_set_ctrl<<<1, 32, 0, h->stream>>>(h->ctrl, V_iso, sweep, h->N);
+  k_set_ctrl<<<1, 32, 0, h->stream>>>(h->vol_dev, h->ctrl, V_iso, sweep, h->N);
   int rc = recount_into_ctrl(h);
   if (rc) return rc;
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
