@@ -173,6 +173,58 @@ int cvf_state_device_ptr(cvf_handle *h, void **dev_ptr);
 /* Waits for the handle's stream, frees what the library allocated. */
 int cvf_destroy(cvf_handle *h);
 
+/* ------------------------------------------------------------------------
+ * Batched replicas: many independent lattices (their own L, q, T, P, seed,
+ * init) advanced by one persistent, cooperative, graph-captured launch.
+ * Every replica computes exactly what cvf_create + cvf_sweep compute for it
+ * alone (same steps, same counter-based draws).  Replicas use the
+ * checkerboard schedule and share rng_words.  Replica ids are slot numbers
+ * 0 .. n_slots-1; a removed slot is reused by a later add.
+ * ------------------------------------------------------------------------ */
+
+/* Creates a batch holding n replicas with parameters params[0..n) (n may be
+ * 0), each initialised as by cvf_create; ids are 0..n-1.  Work is enqueued on
+ * stream (cudaStream_t as void*).  CVF_EINVAL for invalid parameters, a
+ * layered schedule or differing rng_words; CVF_ENOMEM when device memory
+ * runs out (nothing leaked). */
+int cvf_batch_create(const cvf_params *params, int32_t n, void *stream,
+                     cvf_batch **out);
+
+/* Adds one replica (allocates its state pair, control block, tables and a
+ * 1024-record observable ring, initialises it; synchronises the stream) and
+ * returns its id.  CVF_ENOMEM when the device has no room for it. */
+int cvf_batch_add(cvf_batch *b, const cvf_params *p, int32_t *replica);
+
+/* Frees a replica (waits for the stream first); its id becomes free. */
+int cvf_batch_remove(cvf_batch *b, int32_t replica);
+
+/* Number of slots (live or free) and of live replicas. */
+int cvf_batch_size(cvf_batch *b, int32_t *n_slots, int32_t *n_live);
+
+/* Advances replica i by sweeps[i] MC steps, i = 0..n-1 with n the slot count
+ * (0 for free slots and for replicas to leave alone), in one persistent
+ * launch; returns without waiting.  At most 64 distinct nonzero step counts
+ * and 2^31-1 steps per replica per call.  A bounded device-side wait that
+ * gives up is reported by the next call that reads results (CVF_ETIMEOUT). */
+int cvf_batch_sweep(cvf_batch *b, const int64_t *sweeps, int32_t n);
+
+/* Waits for the batch's stream; CVF_ETIMEOUT if the last launch gave up. */
+int cvf_batch_sync(cvf_batch *b);
+
+/* Observables / lattice (L*L words, layout above) of one replica; both
+ * synchronise the stream. */
+int cvf_batch_observables(cvf_batch *b, int32_t replica, cvf_obs *out);
+int cvf_batch_get_state(cvf_batch *b, int32_t replica, uint16_t *host,
+                        size_t n);
+
+/* Tile shape of the batched kernel: config c selects rows x words from a
+ * fixed list (cvf_batch_tile_config); chosen by the autotuner. */
+int cvf_batch_set_tiles(cvf_batch *b, int32_t config);
+int cvf_batch_tile_config(int32_t config, int32_t *rows, int32_t *words);
+
+/* Waits for the stream and frees every replica and the batch. */
+int cvf_batch_destroy(cvf_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

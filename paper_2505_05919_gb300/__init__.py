@@ -5,5 +5,7 @@ the C ABI of ``include/cvf.h``."""
 from . import _capi
 from ._capi import CvfError, cvf_params, cvf_obs
 from .lattice import Lattice, params, params_from_dict
+from .batch import Batch, tile_configs
 
-__all__ = ["Lattice", "params", "params_from_dict", "CvfError", "cvf_params", "cvf_obs", "_capi"]
+__all__ = ["Lattice", "Batch", "tile_configs", "params", "params_from_dict", "CvfError",
+           "cvf_params", "cvf_obs", "_capi"]

@@ -69,6 +69,17 @@ _SIGS = {
     "cvf_recount": (ctypes.c_int, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
     "cvf_state_device_ptr": (ctypes.c_int, [_vp, _P(_vp)]),
     "cvf_destroy": (ctypes.c_int, [_vp]),
+    "cvf_batch_create": (ctypes.c_int, [_P(cvf_params), ctypes.c_int32, _vp, _P(_vp)]),
+    "cvf_batch_add": (ctypes.c_int, [_vp, _P(cvf_params), _P(ctypes.c_int32)]),
+    "cvf_batch_remove": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "cvf_batch_size": (ctypes.c_int, [_vp, _P(ctypes.c_int32), _P(ctypes.c_int32)]),
+    "cvf_batch_sweep": (ctypes.c_int, [_vp, _P(ctypes.c_int64), ctypes.c_int32]),
+    "cvf_batch_sync": (ctypes.c_int, [_vp]),
+    "cvf_batch_observables": (ctypes.c_int, [_vp, ctypes.c_int32, _P(cvf_obs)]),
+    "cvf_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int32, _P(ctypes.c_uint16), ctypes.c_size_t]),
+    "cvf_batch_set_tiles": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "cvf_batch_tile_config": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_int32)]),
+    "cvf_batch_destroy": (ctypes.c_int, [_vp]),
 }
 
 _lib = None
@@ -180,3 +191,64 @@ def cvf_state_device_ptr(h: int) -> int:
 
 def cvf_destroy(h: int) -> None:
     _check(load().cvf_destroy(h), "cvf_destroy")
+
+
+# ---------------------------------------------------------------- batches --
+def cvf_batch_create(params_list, stream: int | None = None) -> int:
+    n = len(params_list)
+    arr = (cvf_params * max(n, 1))(*params_list)
+    b = _vp()
+    _check(load().cvf_batch_create(arr, n, stream or None, ctypes.byref(b)), "cvf_batch_create")
+    return b.value
+
+
+def cvf_batch_add(b: int, p: cvf_params) -> int:
+    rid = ctypes.c_int32()
+    _check(load().cvf_batch_add(b, ctypes.byref(p), ctypes.byref(rid)), "cvf_batch_add")
+    return rid.value
+
+
+def cvf_batch_remove(b: int, replica: int) -> None:
+    _check(load().cvf_batch_remove(b, replica), "cvf_batch_remove")
+
+
+def cvf_batch_size(b: int):
+    a, c = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().cvf_batch_size(b, ctypes.byref(a), ctypes.byref(c)), "cvf_batch_size")
+    return a.value, c.value
+
+
+def cvf_batch_sweep(b: int, sweeps) -> None:
+    n = len(sweeps)
+    arr = (ctypes.c_int64 * max(n, 1))(*[int(x) for x in sweeps])
+    _check(load().cvf_batch_sweep(b, arr, n), "cvf_batch_sweep")
+
+
+def cvf_batch_sync(b: int) -> None:
+    _check(load().cvf_batch_sync(b), "cvf_batch_sync")
+
+
+def cvf_batch_observables(b: int, replica: int) -> cvf_obs:
+    o = cvf_obs()
+    _check(load().cvf_batch_observables(b, replica, ctypes.byref(o)), "cvf_batch_observables")
+    return o
+
+
+def cvf_batch_get_state(b: int, replica: int, host_ptr: int, n: int) -> None:
+    _check(load().cvf_batch_get_state(b, replica, ctypes.cast(host_ptr, _P(ctypes.c_uint16)), n),
+           "cvf_batch_get_state")
+
+
+def cvf_batch_set_tiles(b: int, config: int) -> None:
+    _check(load().cvf_batch_set_tiles(b, config), "cvf_batch_set_tiles")
+
+
+def cvf_batch_tile_config(config: int):
+    r, w = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().cvf_batch_tile_config(config, ctypes.byref(r), ctypes.byref(w)),
+           "cvf_batch_tile_config")
+    return r.value, w.value
+
+
+def cvf_batch_destroy(b: int) -> None:
+    _check(load().cvf_batch_destroy(b), "cvf_batch_destroy")

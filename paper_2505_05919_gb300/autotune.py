@@ -1,0 +1,51 @@
+"""Autotuner of the batched kernel's tile shape.
+
+For a list of replica parameters it builds a scratch batch with the same
+lattice sizes (other seeds, so the caller's replicas are untouched), times a
+short probe on every tile configuration with CUDA events, and returns the
+fastest.  Results are cached per size signature for the process.
+"""
+from __future__ import annotations
+
+import copy
+
+from . import _capi
+from .batch import Batch, tile_configs
+
+_cache: dict = {}
+
+
+def signature(params_list) -> tuple:
+    return tuple(sorted((p.L, p.q, p.rng_words) for p in params_list))
+
+
+def autotune(params_list, probe_sweeps: int = 20, warmup: int = 3, stream=None):
+    """Returns (best_config, {config: ms_per_step})."""
+    import torch
+    key = (signature(params_list), probe_sweeps)
+    if key in _cache:
+        return _cache[key]
+    scratch = []
+    for p in params_list:
+        q = copy.copy(p)
+        q.seed = (p.seed * 2654435761 + 97) & 0xFFFFFFFFFFFFFFFF
+        scratch.append(q)
+    stream = stream if stream is not None else torch.cuda.Stream()
+    timings = {}
+    with Batch(scratch, stream=stream) as b:
+        n = b.slots()
+        for cfg in range(len(tile_configs())):
+            b.set_tiles(cfg)
+            b.sweep([warmup] * n)
+            b.sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.sweep([probe_sweeps] * n)
+            e1.record(stream)
+            e1.synchronize()
+            b.sync()
+            timings[cfg] = e0.elapsed_time(e1) / probe_sweeps
+    best = min(timings, key=timings.get)
+    _cache[key] = (best, timings)
+    return best, timings

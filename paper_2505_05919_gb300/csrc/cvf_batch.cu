@@ -1,0 +1,715 @@
+// cvf_batch.cu -- many independent lattices ("replicas": differing L, q, T,
+// P, seeds) advanced by one persistent, cooperative, graph-captured launch.
+//
+// Work items are (relative step s, replica r, tile t), dequeued from one
+// atomic counter in step-major order.  An item waits until replica r has
+// completed s steps in this launch (a bounded spin on a per-replica progress
+// counter, acquire/release); the last tile of a replica-step commits the step
+// (counts, volume move, observables: finalize_step) and releases the
+// replica's next step.  Items are processed one at a time in dequeue order by
+// co-resident blocks, so the oldest unfinished item can always run: there is
+// no deadlock, and a wait that still exceeds its limit sets an error word and
+// ends the launch (reported as CVF_ETIMEOUT).  Every replica computes exactly
+// what it computes alone (same tile code, same counter-based draws).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "cvf.h"
+#include "cvf_device.cuh"
+#include "cvf_host.h"
+#include "cvf_lattice.cuh"
+#include "cvf_tile.cuh"
+
+using namespace cvf;
+
+namespace cvf {
+
+struct ReplicaDesc {
+  uint16_t* state;  // state pair, 2 * L * L words
+  Ctrl* ctrl;
+  const unsigned long long* table24;
+  const VolumeArgs* vol;
+  cvf_obs* ring;
+  long long ring_cap;
+  RoundKeys keys;
+  uint32_t seed_lo, seed_hi;
+  int32_t L;
+  uint32_t q;
+};
+
+// Launch description written by the host before every launch.
+constexpr int kBatchMaxSegments = 64;
+struct BatchWork {
+  unsigned long long next;   // item counter
+  unsigned int error;        // 1: a wait gave up
+  unsigned int pad;
+  long long total_items;
+  int32_t n_active;          // replicas advanced by this launch
+  int32_t nseg;
+  int32_t tile_rows, tile_words;
+  long long seg_s0[kBatchMaxSegments + 1];    // first relative step of each segment
+  long long seg_base[kBatchMaxSegments + 1];  // first item of each segment
+  int32_t seg_active[kBatchMaxSegments];      // active replicas (prefix of `order`)
+  // followed in device memory by: int32 order[n_active], int64 tile_prefix[n_active + 1],
+  // uint32 progress[n_replicas]
+};
+
+constexpr unsigned int kSpinLimit = 1u << 22;  // bounded wait (about a second)
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__global__ void k_batch_reset(BatchWork* W, unsigned int* progress, int n_replicas) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_replicas; i += gridDim.x * blockDim.x)
+    progress[i] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    W->next = 0;
+    W->error = 0;
+  }
+}
+
+template <int RNG_WORDS, bool CMP64, int TR, int TW>
+__global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_batch_sweep(const ReplicaDesc* __restrict__ reps,
+                                                             BatchWork* W,
+                                                             const int32_t* __restrict__ order,
+                                                             const long long* __restrict__ tile_prefix,
+                                                             unsigned int* progress) {
+  using TT = typename ThresholdRow<CMP64>::type;
+  __shared__ TileSmem<TR, TW> S;
+  __shared__ ProposalTable P;
+  __shared__ TT sT[24];
+  __shared__ int s_rep, s_tile, s_abort, s_last;
+  __shared__ long long s_rel;
+  __shared__ uint32_t s_q;
+  if (threadIdx.x == 0) s_q = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int abort = 0;
+      const unsigned long long i = atomicAdd(&W->next, 1ull);
+      if ((long long)i >= W->total_items || *(volatile unsigned int*)&W->error) {
+        abort = 1;
+      } else {
+        // decode the item: segment, relative step, replica, tile
+        int k = 0;
+        while (k + 1 < W->nseg && (long long)i >= W->seg_base[k + 1]) ++k;
+        const int A = W->seg_active[k];
+        const long long T = tile_prefix[A];
+        const long long rel = (long long)i - W->seg_base[k];
+        const long long s = W->seg_s0[k] + rel / T;
+        const long long j = rel % T;
+        int lo = 0, hi = A;  // largest ri with tile_prefix[ri] <= j
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (tile_prefix[mid] <= j) lo = mid;
+          else hi = mid;
+        }
+        const int rep = order[lo];
+        s_rep = rep;
+        s_tile = (int)(j - tile_prefix[lo]);
+        s_rel = s;
+        // wait until the replica has completed s steps of this launch
+        unsigned int spins = 0;
+        while (ld_acquire(&progress[rep]) < (unsigned int)s) {
+          if (*(volatile unsigned int*)&W->error) { abort = 1; break; }
+          if (++spins > kSpinLimit) {
+            atomicExch(&W->error, 1u);
+            abort = 1;
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+      s_abort = abort;
+    }
+    __syncthreads();
+    if (s_abort) break;
+    const ReplicaDesc& R = reps[s_rep];
+    Ctrl* ctl = R.ctrl;
+    volatile Ctrl* vc = ctl;
+    const long long step = vc->sweep;
+    const int g = vc->next_g;
+    if (threadIdx.x < 24) {
+      const unsigned long long t = R.table24[g * 24 + threadIdx.x];
+      sT[threadIdx.x] = CMP64 ? (TT)t : (TT)(uint32_t)(t - 1ull);
+    }
+    if (s_q != R.q) {  // block-uniform
+      fill_proposal_table(P, R.q);
+      __syncthreads();
+      if (threadIdx.x == 0) s_q = R.q;
+    }
+    __syncthreads();
+    const int L = R.L, Lh = L >> 1;
+    const long long N = (long long)L * L;
+    StepView<KeysSeed> v;
+    v.src = reinterpret_cast<const uint32_t*>(R.state + (size_t)(step & 1) * N);
+    v.dst = reinterpret_cast<uint32_t*>(R.state + (size_t)((step + 1) & 1) * N);
+    v.L = L;
+    v.Lh = Lh;
+    v.q = R.q;
+    v.s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
+    v.s_hi = (uint32_t)((unsigned long long)step >> 32);
+    v.keys.k0 = R.seed_lo;
+    v.keys.k1 = R.seed_hi;
+    const int tiles_x = (Lh + TW - 1) / TW;
+    const int ntiles = tiles_x * ((L + TR - 1) / TR);
+    const int t = s_tile;
+    TileCounts cnt{0, 0, 0, 0};
+    sweep_tile<RNG_WORDS, CMP64, TR, TW, kThreads, KeysSeed, true>(
+        v, (t / tiles_x) * TR, (t % tiles_x) * TW, S, P, sT, cnt);
+    uint32_t pairs = cnt.pairs(), bonds = cnt.bonds, nacc = cnt.nacc;
+    block_sum3<kThreads>(pairs, bonds, nacc);
+    if (threadIdx.x == 0) {
+      atomicAdd(&ctl->acc_pairs, (unsigned long long)pairs);
+      atomicAdd(&ctl->acc_hb, (unsigned long long)bonds);
+      atomicAdd(&ctl->acc_moves, (unsigned long long)nacc);
+      __threadfence();
+      const unsigned int prev = atomicAdd(&ctl->done, 1u);
+      s_last = (prev == (unsigned int)ntiles - 1u) ? 1 : 0;
+      if (s_last) {
+        __threadfence();
+        finalize_step(*R.vol, ctl, R.ring, R.ring_cap, R.keys);
+        __threadfence();
+        st_release(&progress[s_rep], (unsigned int)(s_rel + 1));
+      }
+    }
+  }
+}
+
+}  // namespace cvf
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TileConfig {
+  int rows, words;
+};
+constexpr TileConfig kTileConfigs[] = {{64, 64}, {32, 32}, {32, 16}, {16, 16}};
+constexpr int kNumTileConfigs = 4;
+constexpr long long kReplicaRingCap = 1024;
+
+struct Replica {
+  bool live;
+  cvf_params p;
+  long long N;
+  void* mem;  // one allocation: state pair, Ctrl, table, VolumeArgs, ring
+  uint16_t* state;
+  Ctrl* ctrl;
+  unsigned long long* table;
+  VolumeArgs* vol;
+  cvf_obs* ring;
+  long long ring_tail;
+  long long sweep_host;
+  bool cmp64;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct cvf_batch {
+  cudaStream_t stream;
+  cudaStream_t cap_stream;
+  std::vector<Replica> reps;
+  int rng_words;       // shared by all replicas (-1 while empty)
+  int tile_cfg;
+  ReplicaDesc* d_reps;
+  int d_reps_cap;
+  bool reps_dirty;
+  void* d_work;
+  size_t d_work_bytes;
+  void* h_work;  // pinned staging of the launch description
+  size_t h_work_bytes;
+  cvf_obs* d_obs;
+  void* h_pinned;
+  cudaGraphExec_t graph[kNumTileConfigs][2];  // [config][cmp64]
+  int graph_n_reps[kNumTileConfigs][2];
+  void* graph_work[kNumTileConfigs][2];
+  int grid[kNumTileConfigs][2];
+};
+
+namespace {
+
+using KernelFn = void (*)(const ReplicaDesc*, BatchWork*, const int32_t*, const long long*,
+                          unsigned int*);
+
+template <int RW, bool C64>
+KernelFn pick_cfg(int cfg) {
+  switch (cfg) {
+    case 0: return k_batch_sweep<RW, C64, 64, 64>;
+    case 1: return k_batch_sweep<RW, C64, 32, 32>;
+    case 2: return k_batch_sweep<RW, C64, 32, 16>;
+    default: return k_batch_sweep<RW, C64, 16, 16>;
+  }
+}
+
+KernelFn pick_kernel(int rng_words, bool cmp64, int cfg) {
+  if (rng_words == 1) return cmp64 ? pick_cfg<1, true>(cfg) : pick_cfg<1, false>(cfg);
+  return cmp64 ? pick_cfg<2, true>(cfg) : pick_cfg<2, false>(cfg);
+}
+
+long long tiles_of(int L, int cfg) {
+  const TileConfig& c = kTileConfigs[cfg];
+  return (long long)((L / 2 + c.words - 1) / c.words) * ((L + c.rows - 1) / c.rows);
+}
+
+bool any_cmp64(const cvf_batch* b) {
+  for (const Replica& r : b->reps)
+    if (r.live && r.cmp64) return true;
+  return false;
+}
+
+void free_replica(Replica& r) {
+  if (r.mem) cudaFree(r.mem);
+  r = Replica();
+}
+
+// Captured graphs hold device addresses; drop them when a buffer moves.
+void drop_graphs(cvf_batch* b) {
+  for (int c = 0; c < kNumTileConfigs; ++c)
+    for (int k = 0; k < 2; ++k) {
+      if (b->graph[c][k]) cudaGraphExecDestroy(b->graph[c][k]);
+      b->graph[c][k] = nullptr;
+    }
+}
+
+int upload_descs(cvf_batch* b) {
+  if (!b->reps_dirty) return CVF_OK;
+  const int n = (int)b->reps.size();
+  if (n > b->d_reps_cap) {
+    int cap = std::max(16, b->d_reps_cap * 2);
+    while (cap < n) cap *= 2;
+    ReplicaDesc* d = nullptr;
+    CVF_CUDA_CHECK(cudaMalloc(&d, sizeof(ReplicaDesc) * cap));
+    if (b->d_reps) {
+      cudaStreamSynchronize(b->stream);
+      cudaFree(b->d_reps);
+    }
+    drop_graphs(b);
+    b->d_reps = d;
+    b->d_reps_cap = cap;
+  }
+  std::vector<ReplicaDesc> h(std::max(n, 1));
+  for (int i = 0; i < n; ++i) {
+    const Replica& r = b->reps[i];
+    ReplicaDesc& d = h[i];
+    std::memset(&d, 0, sizeof(d));
+    if (!r.live) continue;
+    d.state = r.state;
+    d.ctrl = r.ctrl;
+    d.table24 = r.table;
+    d.vol = r.vol;
+    d.ring = r.ring;
+    d.ring_cap = kReplicaRingCap;
+    d.keys = make_round_keys(r.p.seed);
+    d.seed_lo = (uint32_t)(r.p.seed & 0xFFFFFFFFu);
+    d.seed_hi = (uint32_t)(r.p.seed >> 32);
+    d.L = r.p.L;
+    d.q = (uint32_t)r.p.q;
+  }
+  if (n > 0)
+    CVF_CUDA_CHECK(cudaMemcpyAsync(b->d_reps, h.data(), sizeof(ReplicaDesc) * n,
+                                   cudaMemcpyHostToDevice, b->stream));
+  // the copy reads a host vector: wait for it before the vector goes away
+  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
+  b->reps_dirty = false;
+  return CVF_OK;
+}
+
+int ensure_work_buffer(cvf_batch* b, size_t bytes) {
+  if (bytes <= b->d_work_bytes) return CVF_OK;
+  size_t cap = std::max<size_t>(bytes, 2 * b->d_work_bytes);
+  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
+  if (b->d_work) cudaFree(b->d_work);
+  if (b->h_work) cudaFreeHost(b->h_work);
+  b->d_work = nullptr;
+  b->h_work = nullptr;
+  b->d_work_bytes = b->h_work_bytes = 0;
+  drop_graphs(b);
+  CVF_CUDA_CHECK(cudaMalloc(&b->d_work, cap));
+  CVF_CUDA_CHECK(cudaMallocHost(&b->h_work, cap));
+  b->d_work_bytes = b->h_work_bytes = cap;
+  return CVF_OK;
+}
+
+// Addresses of the arrays that follow the BatchWork header.
+struct WorkLayout {
+  size_t order_off, prefix_off, progress_off, total;
+};
+WorkLayout work_layout(int n_active, int n_reps) {
+  WorkLayout w;
+  w.order_off = align256(sizeof(BatchWork));
+  w.prefix_off = align256(w.order_off + sizeof(int32_t) * std::max(n_active, 1));
+  w.progress_off = align256(w.prefix_off + sizeof(long long) * (n_active + 1));
+  w.total = align256(w.progress_off + sizeof(unsigned int) * std::max(n_reps, 1));
+  return w;
+}
+
+// One launch over the work in b->d_work: reset + persistent kernel, captured
+// as a graph the first time for a given configuration and replica count.
+int launch(cvf_batch* b, int cfg, bool cmp64, int n_reps, int n_active) {
+  const int c64 = cmp64 ? 1 : 0;
+  KernelFn fn = pick_kernel(b->rng_words, cmp64, cfg);
+  if (b->grid[cfg][c64] == 0) {
+    int per_sm = 0;
+    CVF_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, kThreads, 0));
+    if (per_sm < 1) return set_error(CVF_ECUDA, "batch kernel cannot be resident");
+    b->grid[cfg][c64] = per_sm * sm_count();
+  }
+  (void)n_active;
+  const WorkLayout wl = work_layout(n_reps, n_reps);
+  char* base = reinterpret_cast<char*>(b->d_work);
+  BatchWork* W = reinterpret_cast<BatchWork*>(base);
+  const int32_t* order = reinterpret_cast<const int32_t*>(base + wl.order_off);
+  const long long* prefix = reinterpret_cast<const long long*>(base + wl.prefix_off);
+  unsigned int* progress = reinterpret_cast<unsigned int*>(base + wl.progress_off);
+  auto enqueue = [&](cudaStream_t s) -> cudaError_t {
+    k_batch_reset<<<std::max(1, (n_reps + 255) / 256), 256, 0, s>>>(W, progress, n_reps);
+    cudaLaunchConfig_t lc;
+    std::memset(&lc, 0, sizeof(lc));
+    lc.gridDim = dim3(b->grid[cfg][c64]);
+    lc.blockDim = dim3(kThreads);
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, fn, (const ReplicaDesc*)b->d_reps, W, order, prefix, progress);
+  };
+  // the graph bakes in the array offsets, which depend on the counts
+  const bool reuse = b->graph[cfg][c64] && b->graph_n_reps[cfg][c64] == n_reps &&
+                     b->graph_work[cfg][c64] == b->d_work;
+  if (!reuse) {
+    if (b->graph[cfg][c64]) {
+      cudaGraphExecDestroy(b->graph[cfg][c64]);
+      b->graph[cfg][c64] = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t le = enqueue(b->cap_stream);
+      e = cudaStreamEndCapture(b->cap_stream, &g);
+      if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) {
+      e = cudaGraphInstantiate(&b->graph[cfg][c64], g, 0);
+      cudaGraphDestroy(g);
+    }
+    if (e != cudaSuccess) {
+      b->graph[cfg][c64] = nullptr;
+      cudaGetLastError();
+      // capture unsupported here: launch directly (still one persistent launch)
+      CVF_CUDA_CHECK(enqueue(b->stream));
+      return CVF_OK;
+    }
+    b->graph_n_reps[cfg][c64] = n_reps;
+    b->graph_work[cfg][c64] = b->d_work;
+  }
+  CVF_CUDA_CHECK(cudaGraphLaunch(b->graph[cfg][c64], b->stream));
+  return CVF_OK;
+}
+
+int check_replica(cvf_batch* b, int32_t id) {
+  if (!b) return set_error(CVF_EINVAL, "batch is NULL");
+  if (id < 0 || id >= (int)b->reps.size() || !b->reps[id].live)
+    return set_error(CVF_EINVAL, "replica %d does not exist", id);
+  return CVF_OK;
+}
+
+// Reads the error word of the last launch (synchronises the stream).
+int batch_status(cvf_batch* b) {
+  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
+  if (!b->d_work) return CVF_OK;
+  CVF_CUDA_CHECK(cudaMemcpyAsync(b->h_pinned,
+                                 reinterpret_cast<char*>(b->d_work) + offsetof(BatchWork, error),
+                                 sizeof(unsigned int), cudaMemcpyDeviceToHost, b->stream));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
+  unsigned int err = 0;
+  std::memcpy(&err, b->h_pinned, sizeof(err));
+  if (err) return set_error(CVF_ETIMEOUT, "a replica wait in the batched sweep gave up");
+  return CVF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cvf_batch_create(const cvf_params* params, int32_t n, void* stream, cvf_batch** out) {
+  if (!out) return set_error(CVF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 0 || (n > 0 && !params)) return set_error(CVF_EINVAL, "bad replica list");
+  cvf_batch* b = new (std::nothrow) cvf_batch();
+  if (!b) return set_error(CVF_ENOMEM, "host allocation failed");
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
+  b->rng_words = -1;
+  b->tile_cfg = 1;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_obs, sizeof(cvf_obs));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_pinned, 4096);
+  if (e != cudaSuccess) {
+    cvf_batch_destroy(b);
+    return set_error(CVF_ECUDA, "batch setup: %s", cudaGetErrorString(e));
+  }
+  for (int i = 0; i < n; ++i) {
+    int32_t id;
+    const int rc = cvf_batch_add(b, &params[i], &id);
+    if (rc) {
+      cvf_batch_destroy(b);
+      return rc;
+    }
+  }
+  *out = b;
+  return CVF_OK;
+}
+
+int cvf_batch_add(cvf_batch* b, const cvf_params* p, int32_t* replica) {
+  if (!b || !replica) return set_error(CVF_EINVAL, "NULL argument");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->schedule != CVF_SCHED_CHECKERBOARD)
+    return set_error(CVF_EINVAL, "batched replicas use the checkerboard schedule");
+  if (b->rng_words >= 0 && p->rng_words != b->rng_words)
+    return set_error(CVF_EINVAL, "all replicas of a batch share rng_words (%d)", b->rng_words);
+  std::vector<int64_t> d2, mult;
+  lattice_shells(p->cutoff, &d2, &mult);
+  if ((int)d2.size() > kMaxShells) return set_error(CVF_EINVAL, "cutoff too large");
+  Replica r = Replica();
+  r.p = *p;
+  r.N = (long long)p->L * p->L;
+  const size_t o_state = 0;
+  const size_t o_ctrl = align256(o_state + sizeof(uint16_t) * 2 * (size_t)r.N);
+  const size_t o_table = align256(o_ctrl + sizeof(Ctrl));
+  const size_t o_vol = align256(o_table + sizeof(unsigned long long) * 48);
+  const size_t o_ring = align256(o_vol + sizeof(VolumeArgs));
+  const size_t total = align256(o_ring + sizeof(cvf_obs) * kReplicaRingCap);
+  cudaError_t e = cudaMalloc(&r.mem, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(e == cudaErrorMemoryAllocation ? CVF_ENOMEM : CVF_ECUDA,
+                     "replica allocation (%zu bytes): %s", total, cudaGetErrorString(e));
+  }
+  char* m = reinterpret_cast<char*>(r.mem);
+  r.state = reinterpret_cast<uint16_t*>(m + o_state);
+  r.ctrl = reinterpret_cast<Ctrl*>(m + o_ctrl);
+  r.table = reinterpret_cast<unsigned long long*>(m + o_table);
+  r.vol = reinterpret_cast<VolumeArgs*>(m + o_vol);
+  r.ring = reinterpret_cast<cvf_obs*>(m + o_ring);
+  unsigned long long t24[48];
+  r.cmp64 = fill_table24(p, t24);
+  VolumeArgs va;
+  fill_volume_args(p, r.N, d2, mult, &va);
+  const RoundKeys K = make_round_keys(p->seed);
+  cudaStream_t s = b->stream;
+#define ADD_CHECK(expr)                                                             \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      free_replica(r);                                                              \
+      return set_error(CVF_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_)); \
+    }                                                                               \
+  } while (0)
+  ADD_CHECK(cudaMemcpyAsync(r.table, t24, sizeof(t24), cudaMemcpyHostToDevice, s));
+  ADD_CHECK(cudaMemcpyAsync(r.vol, &va, sizeof(va), cudaMemcpyHostToDevice, s));
+  ADD_CHECK(cudaMemsetAsync(r.ctrl, 0, sizeof(Ctrl), s));
+  const int grid = (int)std::max<long long>(1, std::min<long long>((r.N + 255) / 256, 4096));
+  k_init<<<grid, 256, 0, s>>>(r.state, p->L, (uint32_t)p->q, p->init == CVF_INIT_RANDOM ? 1 : 0, K);
+  k_set_ctrl<<<1, 32, 0, s>>>(r.vol, r.ctrl, (double)r.N * p->v_iso_init, 0, r.N);
+  k_recount<<<grid, kThreads, 0, s>>>(r.state, p->L, nullptr, &r.ctrl->acc_hb);
+  k_commit_counts<<<1, 32, 0, s>>>(r.ctrl);
+  k_volume_prologue<<<1, 32, 0, s>>>(r.vol, r.ctrl, K);
+  ADD_CHECK(cudaGetLastError());
+  // the host copies above read stack memory: complete them before returning
+  ADD_CHECK(cudaStreamSynchronize(s));
+#undef ADD_CHECK
+  r.live = true;
+  r.sweep_host = 0;
+  r.ring_tail = 0;
+  int id = -1;
+  for (int i = 0; i < (int)b->reps.size(); ++i)
+    if (!b->reps[i].live) {
+      id = i;
+      break;
+    }
+  if (id < 0) {
+    id = (int)b->reps.size();
+    b->reps.push_back(r);
+  } else {
+    b->reps[id] = r;
+  }
+  if (b->rng_words < 0) b->rng_words = p->rng_words;
+  b->reps_dirty = true;
+  *replica = id;
+  return CVF_OK;
+}
+
+int cvf_batch_remove(cvf_batch* b, int32_t replica) {
+  int rc = check_replica(b, replica);
+  if (rc) return rc;
+  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
+  free_replica(b->reps[replica]);
+  b->reps_dirty = true;
+  bool any = false;
+  for (const Replica& r : b->reps) any = any || r.live;
+  if (!any) b->rng_words = -1;
+  return CVF_OK;
+}
+
+int cvf_batch_size(cvf_batch* b, int32_t* n_slots, int32_t* n_live) {
+  if (!b || !n_slots || !n_live) return set_error(CVF_EINVAL, "NULL argument");
+  *n_slots = (int32_t)b->reps.size();
+  int live = 0;
+  for (const Replica& r : b->reps) live += r.live ? 1 : 0;
+  *n_live = live;
+  return CVF_OK;
+}
+
+int cvf_batch_set_tiles(cvf_batch* b, int32_t config) {
+  if (!b) return set_error(CVF_EINVAL, "batch is NULL");
+  if (config < 0 || config >= kNumTileConfigs)
+    return set_error(CVF_EINVAL, "tile config %d (0..%d)", config, kNumTileConfigs - 1);
+  b->tile_cfg = config;
+  return CVF_OK;
+}
+
+int cvf_batch_tile_config(int32_t config, int32_t* rows, int32_t* words) {
+  if (config < 0 || config >= kNumTileConfigs || !rows || !words)
+    return set_error(CVF_EINVAL, "tile config %d (0..%d)", config, kNumTileConfigs - 1);
+  *rows = kTileConfigs[config].rows;
+  *words = kTileConfigs[config].words;
+  return CVF_OK;
+}
+
+int cvf_batch_sweep(cvf_batch* b, const int64_t* sweeps, int32_t n) {
+  if (!b) return set_error(CVF_EINVAL, "batch is NULL");
+  if (n != (int)b->reps.size() || (n > 0 && !sweeps))
+    return set_error(CVF_EINVAL, "need one step count per replica slot (%zu)", b->reps.size());
+  std::vector<int32_t> act;
+  for (int i = 0; i < n; ++i) {
+    if (sweeps[i] < 0) return set_error(CVF_EINVAL, "negative step count for replica %d", i);
+    if (sweeps[i] > 0 && !b->reps[i].live)
+      return set_error(CVF_EINVAL, "steps requested for removed replica %d", i);
+    if (sweeps[i] > 0) act.push_back(i);
+  }
+  if (act.empty()) return CVF_OK;
+  for (int i : act)
+    if (sweeps[i] > 0x7FFFFFFF) return set_error(CVF_EINVAL, "at most 2^31-1 steps per call");
+  int rc = upload_descs(b);
+  if (rc) return rc;
+  std::stable_sort(act.begin(), act.end(), [&](int a, int c) { return sweeps[a] > sweeps[c]; });
+  const int cfg = b->tile_cfg;
+  const int na = (int)act.size();
+  // array capacities follow the slot count, so a captured graph stays valid
+  // whatever subset of replicas a call advances
+  const WorkLayout wl = work_layout(n, n);
+  rc = ensure_work_buffer(b, wl.total);
+  if (rc) return rc;
+  // segments of constant active prefix, in increasing relative step
+  std::vector<long long> prefix(na + 1, 0);
+  for (int k = 0; k < na; ++k) prefix[k + 1] = prefix[k] + tiles_of(b->reps[act[k]].p.L, cfg);
+  std::vector<long long> bounds;  // distinct step counts, ascending
+  for (int k = na - 1; k >= 0; --k)
+    if (bounds.empty() || bounds.back() != sweeps[act[k]]) bounds.push_back(sweeps[act[k]]);
+  if ((int)bounds.size() > kBatchMaxSegments)
+    return set_error(CVF_EINVAL, "at most %d distinct step counts per call", kBatchMaxSegments);
+  // wait for the previous launch before rewriting its description
+  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
+  char* h = reinterpret_cast<char*>(b->h_work);
+  std::memset(h, 0, sizeof(BatchWork));
+  BatchWork* W = reinterpret_cast<BatchWork*>(h);
+  W->n_active = na;
+  W->tile_rows = kTileConfigs[cfg].rows;
+  W->tile_words = kTileConfigs[cfg].words;
+  long long s0 = 0, base = 0;
+  int nseg = 0;
+  for (long long ub : bounds) {
+    int active = 0;
+    while (active < na && sweeps[act[active]] > s0) ++active;
+    W->seg_s0[nseg] = s0;
+    W->seg_base[nseg] = base;
+    W->seg_active[nseg] = active;
+    base += (ub - s0) * prefix[active];
+    s0 = ub;
+    ++nseg;
+  }
+  W->seg_s0[nseg] = s0;
+  W->seg_base[nseg] = base;
+  W->nseg = nseg;
+  W->total_items = base;
+  std::memcpy(h + wl.order_off, act.data(), sizeof(int32_t) * na);
+  std::memcpy(h + wl.prefix_off, prefix.data(), sizeof(long long) * (na + 1));
+  CVF_CUDA_CHECK(cudaMemcpyAsync(b->d_work, h, wl.progress_off, cudaMemcpyHostToDevice, b->stream));
+  rc = launch(b, cfg, any_cmp64(b), n, na);
+  if (rc) return rc;
+  for (int i : act) b->reps[i].sweep_host += sweeps[i];
+  return CVF_OK;
+}
+
+int cvf_batch_sync(cvf_batch* b) {
+  if (!b) return set_error(CVF_EINVAL, "batch is NULL");
+  return batch_status(b);
+}
+
+int cvf_batch_observables(cvf_batch* b, int32_t replica, cvf_obs* out) {
+  int rc = check_replica(b, replica);
+  if (rc) return rc;
+  if (!out) return set_error(CVF_EINVAL, "out is NULL");
+  rc = batch_status(b);
+  if (rc) return rc;
+  const Replica& r = b->reps[replica];
+  k_observables<<<1, 32, 0, b->stream>>>(r.vol, r.ctrl, b->d_obs);
+  CVF_CUDA_CHECK(cudaGetLastError());
+  CVF_CUDA_CHECK(cudaMemcpyAsync(b->h_pinned, b->d_obs, sizeof(cvf_obs), cudaMemcpyDeviceToHost,
+                                 b->stream));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
+  std::memcpy(out, b->h_pinned, sizeof(cvf_obs));
+  return CVF_OK;
+}
+
+int cvf_batch_get_state(cvf_batch* b, int32_t replica, uint16_t* host, size_t n) {
+  int rc = check_replica(b, replica);
+  if (rc) return rc;
+  const Replica& r = b->reps[replica];
+  if (!host || (long long)n != r.N)
+    return set_error(CVF_EINVAL, "n=%zu, replica %d has %lld cells", n, replica, r.N);
+  rc = batch_status(b);
+  if (rc) return rc;
+  CVF_CUDA_CHECK(cudaMemcpyAsync(host, r.state + (size_t)(r.sweep_host & 1) * r.N,
+                                 sizeof(uint16_t) * n, cudaMemcpyDeviceToHost, b->stream));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
+  return CVF_OK;
+}
+
+int cvf_batch_destroy(cvf_batch* b) {
+  if (!b) return CVF_OK;
+  cudaStreamSynchronize(b->stream);
+  for (Replica& r : b->reps) free_replica(r);
+  for (int c = 0; c < kNumTileConfigs; ++c)
+    for (int k = 0; k < 2; ++k)
+      if (b->graph[c][k]) cudaGraphExecDestroy(b->graph[c][k]);
+  if (b->d_reps) cudaFree(b->d_reps);
+  if (b->d_work) cudaFree(b->d_work);
+  if (b->h_work) cudaFreeHost(b->h_work);
+  if (b->d_obs) cudaFree(b->d_obs);
+  if (b->h_pinned) cudaFreeHost(b->h_pinned);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+  return CVF_OK;
+}
+
+}  // extern "C"

@@ -406,6 +406,76 @@ __device__ __forceinline__ cvf_obs make_obs(const VolumeArgs& V, const Ctrl* ctl
   return o;
 }
 
+// End of a step, run by one thread once every block's counts are in:
+// commit the counts and the step's volume move, advance the step counter,
+// append the observables to the ring when the step count is a multiple of
+// record_every, and settle the volume move of the next step (taken from the
+// early decision when there is one, else decided now with the new bonds).
+// All accesses go through a volatile view: in the batched kernel the
+// previous step of the same lattice was closed by another SM without a
+// kernel boundary in between.
+__device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cvf_obs* ring,
+                                              long long ring_cap, const RoundKeys& K) {
+  volatile Ctrl* c = ctl;
+  Ctrl s;  // committed state after this step
+  s.n_hb_raw = (long long)c->acc_hb;
+  s.n_coop = (long long)c->acc_pairs;
+  s.acc_sigma = c->acc_sigma + (long long)c->acc_moves;
+  s.V_iso = c->next_V;
+  s.u_cell = c->next_u;
+  s.g = c->next_g;
+  s.acc_volume = c->acc_volume + c->next_acc;
+  s.sweep = c->sweep + 1;
+  c->n_hb_raw = s.n_hb_raw;
+  c->n_coop = s.n_coop;
+  c->acc_sigma = s.acc_sigma;
+  c->V_iso = s.V_iso;
+  c->u_cell = s.u_cell;
+  c->g = s.g;
+  c->acc_volume = s.acc_volume;
+  c->acc_hb = 0;
+  c->acc_pairs = 0;
+  c->acc_moves = 0;
+  c->done = 0;
+  c->tile_next = 0;
+  c->sweep = s.sweep;
+  const int every = c->record_every;
+  if (every > 0 && s.sweep % every == 0) {
+    const long long head = c->ring_head;
+    ring[head % ring_cap] = make_obs(V, &s);
+    c->ring_head = head + 1;
+  }
+  VolumeResult r;
+  if (c->ahead_state == 1) {
+    r.V = c->ahead_V;
+    r.u = c->ahead_u;
+    r.g = c->ahead_g;
+    r.accepted = c->ahead_acc;
+  } else {
+    volume_decide(V, s.sweep, s.V_iso, s.u_cell, s.g, s.n_hb_raw, K, &r);
+  }
+  c->next_V = r.V;
+  c->next_u = r.u;
+  c->next_g = r.g;
+  c->next_acc = r.accepted;
+  c->ahead_state = 0;
+}
+
+// True in every thread of the block that arrives last (after all blocks
+// have published their atomics).
+__device__ __forceinline__ bool last_block(unsigned int* done) {
+  __shared__ int is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(done, 1u);
+    is_last = (prev == gridDim.x - 1) ? 1 : 0;
+    if (is_last) __threadfence();
+  }
+  __syncthreads();
+  return is_last != 0;
+}
+
 // Block-wide sum of three counters; the result is valid in thread 0.
 template <int NT>
 __device__ __forceinline__ void block_sum3(uint32_t& a, uint32_t& b, uint32_t& c) {

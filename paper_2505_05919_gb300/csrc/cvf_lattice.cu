@@ -15,6 +15,7 @@
 #include "cvf_device.cuh"
 #include "cvf_host.h"
 #include "cvf_lattice.cuh"
+#include "cvf_tile.cuh"
 
 using namespace cvf;
 
@@ -124,127 +125,20 @@ __global__ void k_observables(const VolumeArgs* __restrict__ V, const Ctrl* ctl,
   if (threadIdx.x == 0 && blockIdx.x == 0) *out = make_obs(*V, ctl);
 }
 
-// End of a step, run by one thread once every block's counts are in:
-// commit the counts and the step's volume move, advance the step counter,
-// append the observables to the ring when the step count is a multiple of
-// record_every, and settle the volume move of the next step (taken from the
-// early decision when there is one, else decided now with the new bonds).
-__device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cvf_obs* ring,
-                                              long long ring_cap, const RoundKeys& K) {
-  volatile Ctrl* vc = ctl;
-  const unsigned long long hb = vc->acc_hb, pairs = vc->acc_pairs, moves = vc->acc_moves;
-  ctl->n_hb_raw = (long long)hb;
-  ctl->n_coop = (long long)pairs;
-  ctl->acc_sigma += (long long)moves;
-  ctl->V_iso = ctl->next_V;
-  ctl->u_cell = ctl->next_u;
-  ctl->g = ctl->next_g;
-  ctl->acc_volume += ctl->next_acc;
-  ctl->acc_hb = 0;
-  ctl->acc_pairs = 0;
-  ctl->acc_moves = 0;
-  ctl->done = 0;
-  ctl->tile_next = 0;
-  ctl->sweep += 1;
-  const int every = ctl->record_every;
-  if (every > 0 && ctl->sweep % every == 0) {
-    ring[ctl->ring_head % ring_cap] = make_obs(V, ctl);
-    ctl->ring_head += 1;
-  }
-  VolumeResult r;
-  if (vc->ahead_state == 1) {
-    r.V = vc->ahead_V;
-    r.u = vc->ahead_u;
-    r.g = vc->ahead_g;
-    r.accepted = vc->ahead_acc;
-  } else {
-    volume_decide(V, ctl->sweep, ctl->V_iso, ctl->u_cell, ctl->g, ctl->n_hb_raw, K, &r);
-  }
-  ctl->next_V = r.V;
-  ctl->next_u = r.u;
-  ctl->next_g = r.g;
-  ctl->next_acc = r.accepted;
-  ctl->ahead_state = 0;
-}
-
-// True in every thread of the block that arrives last (after all blocks
-// have published their atomics).
-__device__ __forceinline__ bool last_block(unsigned int* done) {
-  __shared__ int is_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned int prev = atomicAdd(done, 1u);
-    is_last = (prev == gridDim.x - 1) ? 1 : 0;
-    if (is_last) __threadfence();
-  }
-  __syncthreads();
-  return is_last != 0;
-}
-
 // ---------------------------------------------------------------------------
-// Checkerboard sweep, both colours in one launch (Sec. II.C, read for 2D:
-// colour (x + y) & 1, colour 0 first).  The lattice is cut into tiles of
-// kTileRows rows x kTileWords 32-bit words (two cells per word: one of each
-// colour).  A block stages its tile plus a halo of two rows and one word from
-// the step's source buffer, updates the colour-0 cells of the tile and of the
-// one-cell ring around it (the ring's updates are recomputed identically by
-// the neighbouring tile: same inputs, same counter-based draws), then the
-// colour-1 cells of the tile, and writes the tile to the other buffer of the
-// state pair.  Blocks take tiles from a per-step atomic counter.
-// Per tile and per thread the counts of N_sigma (all tile cells), N_HB_raw
-// (the four bonds of every colour-1 cell: each bond has exactly one colour-1
-// end) and accepted moves are summed; the last block closes the step.
+// Checkerboard sweep, both colours in one launch (the tile algorithm is in
+// cvf_tile.cuh).  Blocks take tiles from a per-step atomic counter; block 0
+// instead decides the next step's volume move early (it depends on the bonds
+// only when the gate would change).  Per thread the counts of N_sigma (all
+// tile cells), N_HB_raw (the four bonds of every colour-1 cell: each bond has
+// exactly one colour-1 end) and accepted moves are summed, block-reduced and
+// added with one atomic each; the last block closes the step.
 // ---------------------------------------------------------------------------
-constexpr int kTileRows = 64;
-constexpr int kTileWords = 64;
-constexpr int kInRows = kTileRows + 4, kInCols = kTileWords + 2;
-constexpr int kMidRows = kTileRows + 2, kMidCols = kTileWords + 2;
-
-// 4*sigma of arm b of the 16-bit cell in half `hi` of a word.
-__device__ __forceinline__ uint32_t arm4(uint32_t word, int hi, int b) {
-  const int sh = 16 * hi + 3 * b - 2;
-  return (sh >= 0) ? ((word >> sh) & 0x1Cu) : ((word << 2) & 0x1Cu);
-}
-
-// Update the cell in half `hi` of word `own` (row r, word j of a staged
-// grid); xm / xp are the words to the left / right, ym / yp below / above.
-template <int RNG_WORDS, bool CMP64, bool BONDS>
-__device__ __forceinline__ uint32_t update_in_word(
-    uint32_t own, uint32_t xm_word, uint32_t xp_word, uint32_t ym_word, uint32_t yp_word, int hi,
-    uint32_t c, uint32_t s_lo, uint32_t s_hi, const RoundKeys& K, uint32_t q,
-    const typename ThresholdRow<CMP64>::type* T, uint32_t& nacc, uint32_t& pair_sum,
-    uint32_t& bonds) {
-  // partner arms: arm 0 (+x) <-> arm 1 of the +x cell, arm 1 (-x) <-> arm 0 of
-  // the -x cell, arm 2 (+y) <-> arm 3 of the +y cell, arm 3 <-> arm 2 of -y
-  uint32_t n4[4];
-  if (hi) {
-    n4[0] = arm4(xp_word, 0, 1);
-    n4[1] = arm4(own, 0, 0);
-  } else {
-    n4[0] = arm4(own, 1, 1);
-    n4[1] = arm4(xm_word, 1, 0);
-  }
-  n4[2] = arm4(yp_word, hi, 3);
-  n4[3] = arm4(ym_word, hi, 2);
-  uint32_t nb8[4], t4[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    nb8[a] = 8u << n4[a];
-    t4[a] = arm4(own, hi, a);
-  }
-  uint32_t acc[4], kk[4];
-  cell_draws<RNG_WORDS>(c, s_lo, s_hi, K, q, acc, kk);
-  bonds += update_arms<CMP64, BONDS>(t4, nb8, acc, kk, 4u * q, T, nacc, pair_sum);
-  const uint32_t wn = (t4[0] >> 2) | (t4[1] << 1) | (t4[2] << 4) | (t4[3] << 7);
-  return hi ? ((own & 0xFFFFu) | (wn << 16)) : ((own & 0xFFFF0000u) | wn);
-}
-
 template <int RNG_WORDS, bool CMP64>
-__global__ void __launch_bounds__(kThreads) k_sweep_tiled(LatticeArgs A) {
+__global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_sweep_tiled(LatticeArgs A) {
   using TT = typename ThresholdRow<CMP64>::type;
-  __shared__ uint32_t s_in[kInRows][kInCols];
-  __shared__ uint32_t s_mid[kMidRows][kMidCols];
+  __shared__ TileSmem<kTileRows, kTileWords> S;
+  __shared__ ProposalTable P;
   __shared__ TT sT[24];
   __shared__ int s_tile;
   Ctrl* ctl = A.ctrl;
@@ -272,98 +166,30 @@ __global__ void __launch_bounds__(kThreads) k_sweep_tiled(LatticeArgs A) {
     const unsigned long long t = A.table24[g * 24 + threadIdx.x];
     sT[threadIdx.x] = CMP64 ? (TT)t : (TT)(uint32_t)(t - 1ull);
   }
-  const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
-  const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
-  const int L = A.L;
-  const int Lh = L >> 1;
-  const long long N = (long long)L * L;
-  const uint32_t* __restrict__ src =
-      reinterpret_cast<const uint32_t*>(A.state + (size_t)(step & 1) * N);
-  uint32_t* __restrict__ dst = reinterpret_cast<uint32_t*>(A.state + (size_t)((step + 1) & 1) * N);
-  const int tiles_x = (Lh + kTileWords - 1) / kTileWords;
-  const int ntiles = tiles_x * ((L + kTileRows - 1) / kTileRows);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kWarps = kThreads / 32;
-  // pair_sum adds, per counted cell, 4 + 2 * (its equal pairs)
-  uint32_t pair_sum = 0, ncells = 0, bonds = 0, nacc = 0;
+  fill_proposal_table(P, A.q);
+  const long long N = (long long)A.L * A.L;
+  StepView<KeysRound> v;
+  v.src = reinterpret_cast<const uint32_t*>(A.state + (size_t)(step & 1) * N);
+  v.dst = reinterpret_cast<uint32_t*>(A.state + (size_t)((step + 1) & 1) * N);
+  v.L = A.L;
+  v.Lh = A.L >> 1;
+  v.q = A.q;
+  v.s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
+  v.s_hi = (uint32_t)((unsigned long long)step >> 32);
+  v.keys.K = &A.keys;
+  const int tiles_x = (v.Lh + kTileWords - 1) / kTileWords;
+  const int ntiles = tiles_x * ((v.L + kTileRows - 1) / kTileRows);
+  TileCounts cnt{0, 0, 0, 0};
   for (;;) {
-    __syncthreads();  // previous tile fully consumed; sT visible
+    __syncthreads();  // previous tile fully consumed; tables visible
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctl->tile_next, 1u);
     __syncthreads();
     const int t = s_tile;
     if (t >= ntiles) break;
-    const int y0 = (t / tiles_x) * kTileRows;
-    const int p0 = (t % tiles_x) * kTileWords;
-    const int th = min(kTileRows, L - y0);
-    const int tw = min(kTileWords, Lh - p0);
-    // stage rows y0-2 .. y0+th+1, words p0-1 .. p0+tw (periodic)
-    for (int rr = warp; rr < th + 4; rr += kWarps) {
-      int y = y0 + rr - 2;
-      y = (y < 0) ? y + L : (y >= L ? y - L : y);
-      const uint32_t* row = src + (size_t)y * Lh;
-      for (int jj = lane; jj < tw + 2; jj += 32) {
-        int p = p0 + jj - 1;
-        p = (p < 0) ? p + Lh : (p >= Lh ? p - Lh : p);
-        s_in[rr][jj] = row[p];
-      }
-    }
-    __syncthreads();
-    // colour 0: tile rows -1 .. th, words 0 .. tw-1 (the colour-0 cell of a
-    // word is its low half on even rows, its high half on odd rows)
-    for (int r = warp - 1; r <= th; r += kWarps) {
-      const int y = y0 + r;
-      const int hi = y & 1;
-      const int yg = (y < 0) ? y + L : (y >= L ? y - L : y);
-      const bool inside = (r >= 0) && (r < th);
-      for (int j = lane; j < tw; j += 32) {
-        const int xg = 2 * (p0 + j) + hi;
-        uint32_t dummy = 0, dummy_b = 0;
-        const uint32_t out = update_in_word<RNG_WORDS, CMP64, false>(
-            s_in[r + 2][j + 1], s_in[r + 2][j], s_in[r + 2][j + 2], s_in[r + 1][j + 1],
-            s_in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), s_lo, s_hi, A.keys,
-            A.q, sT, inside ? nacc : dummy, inside ? pair_sum : dummy, dummy_b);
-        if (inside) ++ncells;
-        s_mid[r + 1][j + 1] = out;
-      }
-    }
-    // colour 0 on the ring: per row r the one colour-0 cell just outside the
-    // tile, x0 - 1 (high half of word -1) on odd rows, x0 + 2 tw (low half of
-    // word tw) on even rows
-    for (int i = threadIdx.x; i < th + 2; i += kThreads) {
-      const int r = i - 1;
-      const int y = y0 + r;
-      const int hi = y & 1;
-      const int j = hi ? -1 : tw;
-      const int yg = (y < 0) ? y + L : (y >= L ? y - L : y);
-      int xg = 2 * (p0 + j) + hi;
-      xg = (xg < 0) ? xg + L : (xg >= L ? xg - L : xg);
-      uint32_t dummy = 0, dummy2 = 0, dummy3 = 0;
-      // the unused side of the ring word is clamped into the staged columns
-      const int jm = max(j, 0), jp = min(j + 2, tw + 1);
-      const uint32_t out = update_in_word<RNG_WORDS, CMP64, false>(
-          s_in[r + 2][j + 1], s_in[r + 2][jm], s_in[r + 2][jp], s_in[r + 1][j + 1],
-          s_in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), s_lo, s_hi, A.keys, A.q,
-          sT, dummy, dummy2, dummy3);
-      s_mid[r + 1][j + 1] = out;
-    }
-    __syncthreads();
-    // colour 1: tile rows 0 .. th-1 (low half on odd rows, high on even rows)
-    for (int r = warp; r < th; r += kWarps) {
-      const int y = y0 + r;
-      const int hi = (y & 1) ^ 1;
-      uint32_t* drow = dst + (size_t)y * Lh + p0;
-      for (int j = lane; j < tw; j += 32) {
-        const int xg = 2 * (p0 + j) + hi;
-        const uint32_t out = update_in_word<RNG_WORDS, CMP64, true>(
-            s_mid[r + 1][j + 1], s_mid[r + 1][j], s_mid[r + 1][j + 2], s_mid[r][j + 1],
-            s_mid[r + 2][j + 1], hi, (uint32_t)((long long)y * L + xg), s_lo, s_hi, A.keys, A.q,
-            sT, nacc, pair_sum, bonds);
-        ++ncells;
-        drow[j] = out;
-      }
-    }
+    sweep_tile<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads>(
+        v, (t / tiles_x) * kTileRows, (t % tiles_x) * kTileWords, S, P, sT, cnt);
   }
-  uint32_t pairs = (pair_sum - 4u * ncells) >> 1;
+  uint32_t pairs = cnt.pairs(), bonds = cnt.bonds, nacc = cnt.nacc;
   block_sum3<kThreads>(pairs, bonds, nacc);
   if (threadIdx.x == 0) {
     atomicAdd(&ctl->acc_pairs, (unsigned long long)pairs);
@@ -445,6 +271,53 @@ __global__ void __launch_bounds__(kThreads) k_layer_pass(LatticeArgs A, int pass
 __global__ void k_finalize(LatticeArgs A) {
   if (threadIdx.x == 0 && blockIdx.x == 0)
     finalize_step(*A.vol, A.ctrl, A.ring, A.ring_cap, A.keys);
+}
+
+}  // namespace cvf
+
+namespace cvf {
+
+// Device threshold rows [g][(dN_HB+1)*8 + dN_sigma+3] (slot dN_sigma+3 = 7
+// unused); returns true when some threshold is 0 (64-bit compares needed).
+bool fill_table24(const cvf_params* p, unsigned long long table24[48]) {
+  uint64_t table[42];
+  threshold_table(p, table);
+  std::memset(table24, 0, sizeof(unsigned long long) * 48);
+  bool cmp64 = false;
+  for (int g = 0; g < 2; ++g)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 7; ++j) {
+        const uint64_t t = table[(g * 3 + i) * 7 + j];
+        table24[g * 24 + i * 8 + j] = t;
+        if (t == 0) cmp64 = true;
+      }
+  return cmp64;
+}
+
+// FP64 parameters and the LJ shell prefix sums (accumulated in increasing
+// |d|^2: S12 of m/|d|^12, S6 of m/|d|^6).
+void fill_volume_args(const cvf_params* p, long long N, const std::vector<int64_t>& d2,
+                      const std::vector<int64_t>& mult, VolumeArgs* va) {
+  std::memset(va, 0, sizeof(*va));
+  va->N = N;
+  va->epsilon = p->epsilon;
+  va->cutoff2 = p->cutoff * p->cutoff;
+  va->J = p->J;
+  va->J_sigma = p->J_sigma;
+  va->v_HB = p->v_HB;
+  va->kT = p->kT;
+  va->P = p->P;
+  va->dV_max = p->dv_max_frac * ((double)N * p->v_iso_init);
+  va->volume_moves = p->volume_moves;
+  va->nshell = (int)d2.size();
+  va->S12[0] = 0.0;
+  va->S6[0] = 0.0;
+  for (size_t i = 0; i < d2.size(); ++i) {
+    va->shell_d2[i] = (double)d2[i];
+    const int64_t d6 = d2[i] * d2[i] * d2[i];
+    va->S12[i + 1] = va->S12[i] + (double)mult[i] / ((double)d6 * (double)d6);
+    va->S6[i + 1] = va->S6[i] + (double)mult[i] / (double)d6;
+  }
 }
 
 }  // namespace cvf
@@ -622,40 +495,10 @@ int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** 
   CREATE_CHECK(cudaMalloc(&h->rc_dev, sizeof(unsigned long long) * 2));
   CREATE_CHECK(cudaMallocHost(&h->host_pinned, 4096));
 
-  uint64_t table[42];
-  threshold_table(p, table);
-  // device layout [g][(dN_HB+1)*8 + dN_sigma+3]; slot dN_sigma+3 = 7 unused
   unsigned long long table24[48];
-  std::memset(table24, 0, sizeof(table24));
-  h->cmp64 = false;
-  for (int g = 0; g < 2; ++g)
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 7; ++j) {
-        const uint64_t t = table[(g * 3 + i) * 7 + j];
-        table24[g * 24 + i * 8 + j] = t;
-        if (t == 0) h->cmp64 = true;
-      }
+  h->cmp64 = fill_table24(p, table24);
   VolumeArgs va;
-  std::memset(&va, 0, sizeof(va));
-  va.N = h->N;
-  va.epsilon = p->epsilon;
-  va.cutoff2 = p->cutoff * p->cutoff;
-  va.J = p->J;
-  va.J_sigma = p->J_sigma;
-  va.v_HB = p->v_HB;
-  va.kT = p->kT;
-  va.P = p->P;
-  va.dV_max = p->dv_max_frac * ((double)h->N * p->v_iso_init);
-  va.volume_moves = p->volume_moves;
-  va.nshell = (int)d2.size();
-  va.S12[0] = 0.0;
-  va.S6[0] = 0.0;
-  for (size_t i = 0; i < d2.size(); ++i) {
-    va.shell_d2[i] = (double)d2[i];
-    const int64_t d6 = d2[i] * d2[i] * d2[i];
-    va.S12[i + 1] = va.S12[i] + (double)mult[i] / ((double)d6 * (double)d6);
-    va.S6[i + 1] = va.S6[i] + (double)mult[i] / (double)d6;
-  }
+  fill_volume_args(p, h->N, d2, mult, &va);
   CREATE_CHECK(cudaMemcpyAsync(h->table_dev, table24, sizeof(table24), cudaMemcpyHostToDevice,
                                h->stream));
   CREATE_CHECK(cudaMemcpyAsync(h->vol_dev, &va, sizeof(va), cudaMemcpyHostToDevice, h->stream));

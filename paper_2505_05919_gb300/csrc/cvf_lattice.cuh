@@ -1,12 +1,18 @@
 // cvf_lattice.cuh -- launch arguments of the single-lattice kernels.
 #pragma once
 #include <cstdint>
+#include <vector>
 
 #include "cvf_device.cuh"
 
 namespace cvf {
 
 constexpr int kThreads = 256;
+// tiles of the single-lattice sweep: 64 rows x 64 words (128 cells)
+constexpr int kTileRows = 64;
+constexpr int kTileWords = 64;
+// register budget of the sweep kernel: four 256-thread blocks per SM
+constexpr int kSweepBlocksPerSM = 4;
 
 struct LatticeArgs {
   uint16_t* state;                   // state pair: 2 * L*L packed cell words
@@ -19,5 +25,23 @@ struct LatticeArgs {
   int32_t L;
   uint32_t q;
 };
+
+// Kernels of cvf_lattice.cu that the batch reuses for initialisation and
+// observables.
+__global__ void k_init(uint16_t* __restrict__ state, int32_t L, uint32_t q, int random,
+                       RoundKeys K);
+__global__ void k_recount(const uint16_t* __restrict__ base, int32_t L, const Ctrl* ctl,
+                          unsigned long long* out);
+__global__ void k_commit_counts(Ctrl* ctl);
+__global__ void k_set_ctrl(const VolumeArgs* __restrict__ V, Ctrl* ctl, double V_iso,
+                           long long sweep, long long N);
+__global__ void k_set_record(Ctrl* ctl, int record_every);
+__global__ void k_volume_prologue(const VolumeArgs* __restrict__ V, Ctrl* ctl, RoundKeys K);
+__global__ void k_observables(const VolumeArgs* __restrict__ V, const Ctrl* ctl, cvf_obs* out);
+
+// Host helpers shared by both paths.
+void fill_volume_args(const cvf_params* p, long long N, const std::vector<int64_t>& d2,
+                      const std::vector<int64_t>& mult, VolumeArgs* va);
+bool fill_table24(const cvf_params* p, unsigned long long table24[48]);
 
 }  // namespace cvf

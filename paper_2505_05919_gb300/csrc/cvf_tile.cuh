@@ -1,0 +1,277 @@
+// cvf_tile.cuh -- one tile of the checkerboard sweep (Sec. II.C read for the
+// 2D lattice: colour (x + y) & 1, colour 0 first), shared by the
+// single-lattice kernel and the batched persistent kernel.
+//
+// A tile is TR rows x TW 32-bit words (two cells per word, one of each
+// colour).  The block stages the tile plus a halo of two rows and one word
+// from the step's source buffer, updates the colour-0 cells of the tile and
+// of the one-cell ring around it (the ring's updates are recomputed
+// identically by the neighbouring tile: same inputs, same counter-based
+// draws), then the colour-1 cells of the tile, and writes the tile to the
+// step's destination buffer.
+#pragma once
+#include <cstdint>
+
+#include "cvf_device.cuh"
+
+namespace cvf {
+
+// Proposal lookup for the current q: entry 8 sigma + k holds, for the
+// proposed value sigma' = (sigma + 1 + k) mod q, the word 4 sigma', 2^(28 -
+// 4 sigma') and 2^(4 sigma') (see update_arms).  Filled by the block.
+struct ProposalTable {
+  uint32_t t4[64];
+  uint32_t m[64];
+  uint32_t oh[64];
+};
+
+__device__ __forceinline__ void fill_proposal_table(ProposalTable& P, uint32_t q) {
+  for (int e = threadIdx.x; e < 64; e += blockDim.x) {
+    const uint32_t s = (uint32_t)e >> 3, k = (uint32_t)e & 7u;
+    const uint32_t sp = (s + 1u + k) % q;
+    P.t4[e] = 4u * sp;
+    P.m[e] = 0x10000000u >> (4u * sp);
+    P.oh[e] = 1u << (4u * sp);
+  }
+}
+
+__device__ __forceinline__ uint32_t lds_at(const uint32_t* base, uint32_t byte_off) {
+  return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(base) + byte_off);
+}
+
+// Metropolis update of the four arms of one cell, with the count-nibble
+// bookkeeping of update_arms (cvf_device.cuh) and the proposal taken from
+// the block's ProposalTable.  t4[a] = 4 sigma_a (in/out), nb8[a] = 8 oh(n_a).
+template <bool CMP64, bool BONDS>
+__device__ __forceinline__ uint32_t update_arms_tab(uint32_t t4[4], const uint32_t nb8[4],
+                                                    const uint32_t acc[4], const uint32_t kk[4],
+                                                    const ProposalTable& P,
+                                                    const typename ThresholdRow<CMP64>::type* T,
+                                                    uint32_t& naccepted, uint32_t& pair_sum) {
+  uint32_t oh[4], m[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    oh[a] = 1u << t4[a];
+    m[a] = 0x10000000u >> t4[a];
+  }
+  uint32_t cnt = oh[0] + oh[1] + oh[2] + oh[3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const uint32_t wa = cnt + nb8[a];
+    const uint32_t off = 8u * t4[a] + 4u * kk[a];  // byte offset of entry 8 sigma + k
+    const uint32_t tp = lds_at(P.t4, off);
+    const uint32_t mp = lds_at(P.m, off);
+    const uint32_t ohp = lds_at(P.oh, off);
+    const int fsp = (int)nibble(wa, mp);
+    const int fs = (int)nibble(wa, m[a]);
+    if (accept_draw<CMP64>(acc[a], T[fsp - fs + 12])) {
+      cnt = cnt + ohp - oh[a];
+      oh[a] = ohp;
+      m[a] = mp;
+      t4[a] = tp;
+      ++naccepted;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) pair_sum += nibble(cnt, m[a]);
+  uint32_t bonds = 0;
+  if (BONDS) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) bonds += __umulhi(nb8[a] * m[a], 2u);
+  }
+  return bonds;
+}
+
+// 4*sigma of arm b of the 16-bit cell in half `hi` of a word.
+__device__ __forceinline__ uint32_t arm4(uint32_t word, int hi, int b) {
+  const int sh = 16 * hi + 3 * b - 2;
+  return (sh >= 0) ? ((word >> sh) & 0x1Cu) : ((word << 2) & 0x1Cu);
+}
+
+// Philox key material of the lattice being swept: the precomputed round keys
+// (single lattice) or the seed words, advanced in registers (batch, where
+// consecutive tiles may belong to different replicas).
+struct KeysRound {
+  const RoundKeys* K;
+};
+struct KeysSeed {
+  uint32_t k0, k1;
+};
+
+template <int RNG_WORDS>
+__device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi, const KeysRound& k,
+                                      uint32_t q, uint32_t acc[4], uint32_t kk[4]) {
+  cell_draws<RNG_WORDS>(c, s_lo, s_hi, *k.K, q, acc, kk);
+}
+
+template <int RNG_WORDS>
+__device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi, const KeysSeed& k,
+                                      uint32_t q, uint32_t acc[4], uint32_t kk[4]) {
+  const Words4 u = philox_seed(c, s_lo, s_hi, kTagAccept, k.k0, k.k1);
+  const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+  if (RNG_WORDS == 1) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const uint64_t prod = (uint64_t)uw[a] * (uint64_t)(q - 1u);
+      kk[a] = (uint32_t)(prod >> 32);
+      acc[a] = (uint32_t)prod;
+    }
+  } else {
+    const Words4 p = philox_seed(c, s_lo, s_hi, kTagPropose, k.k0, k.k1);
+    const uint32_t pw[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      acc[a] = uw[a];
+      kk[a] = __umulhi(pw[a], q - 1u);
+    }
+  }
+}
+
+// Update the cell in half `hi` of word `own`; xm / xp are the words to the
+// left / right, ym / yp the words of the rows y-1 / y+1.
+template <int RNG_WORDS, bool CMP64, bool BONDS, typename KEYS>
+__device__ __forceinline__ uint32_t update_in_word(
+    uint32_t own, uint32_t xm_word, uint32_t xp_word, uint32_t ym_word, uint32_t yp_word, int hi,
+    uint32_t c, uint32_t s_lo, uint32_t s_hi, const KEYS& keys, uint32_t q,
+    const ProposalTable& P, const typename ThresholdRow<CMP64>::type* T, uint32_t& nacc,
+    uint32_t& pair_sum, uint32_t& bonds) {
+  // partner arms: arm 0 (+x) <-> arm 1 of the +x cell, arm 1 (-x) <-> arm 0 of
+  // the -x cell, arm 2 (+y) <-> arm 3 of the +y cell, arm 3 <-> arm 2 of -y
+  uint32_t n4[4];
+  if (hi) {
+    n4[0] = arm4(xp_word, 0, 1);
+    n4[1] = arm4(own, 0, 0);
+  } else {
+    n4[0] = arm4(own, 1, 1);
+    n4[1] = arm4(xm_word, 1, 0);
+  }
+  n4[2] = arm4(yp_word, hi, 3);
+  n4[3] = arm4(ym_word, hi, 2);
+  uint32_t nb8[4], t4[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    nb8[a] = 8u << n4[a];
+    t4[a] = arm4(own, hi, a);
+  }
+  uint32_t acc[4], kk[4];
+  draws<RNG_WORDS>(c, s_lo, s_hi, keys, q, acc, kk);
+  bonds += update_arms_tab<CMP64, BONDS>(t4, nb8, acc, kk, P, T, nacc, pair_sum);
+  const uint32_t wn = (t4[0] >> 2) | (t4[1] << 1) | (t4[2] << 4) | (t4[3] << 7);
+  return hi ? ((own & 0xFFFFu) | (wn << 16)) : ((own & 0xFFFF0000u) | wn);
+}
+
+template <int TR, int TW>
+struct TileSmem {
+  uint32_t in[TR + 4][TW + 2];   // rows y0-2 .. y0+TR+1, words p0-1 .. p0+TW
+  uint32_t mid[TR + 2][TW + 2];  // after colour 0: rows y0-1 .. y0+TR
+};
+
+// Per-thread counts of the cells a thread finished inside its tiles:
+// pair_sum adds 4 + 2 (equal pairs) per counted cell.
+struct TileCounts {
+  uint32_t pair_sum, ncells, bonds, nacc;
+  __device__ __forceinline__ uint32_t pairs() const { return (pair_sum - 4u * ncells) >> 1; }
+};
+
+// One lattice for one step, as a tile sees it.
+template <typename KEYS>
+struct StepView {
+  const uint32_t* src;  // state words of the step's source buffer
+  uint32_t* dst;        // destination buffer
+  int L, Lh;
+  uint32_t q;
+  uint32_t s_lo, s_hi;  // step index
+  KEYS keys;
+};
+
+// Sweep the tile at rows y0.., words p0.. of one lattice.  Called by all
+// threads of the block; ends with the tile written to dst (no trailing
+// barrier: the caller synchronises before reusing the shared buffers).
+// CG: stage through L2 only (the source may have been written by other SMs
+// since this SM last cached it, without a kernel boundary in between).
+// A warp covers max(1, 32/TW) rows per pass, one lane per word.
+template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS, bool CG = false>
+__device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int p0,
+                                           TileSmem<TR, TW>& S, const ProposalTable& P,
+                                           const typename ThresholdRow<CMP64>::type* T,
+                                           TileCounts& cnt) {
+  static_assert(TW >= 32 ? (TW % 32 == 0) : (32 % TW == 0), "tile width");
+  constexpr int kRows = (TW >= 32) ? 1 : 32 / TW;  // rows per warp pass
+  constexpr int kLanes = (TW >= 32) ? 32 : TW;     // lanes per row
+  const int L = v.L, Lh = v.Lh;
+  const int th = min(TR, L - y0);
+  const int tw = min(TW, Lh - p0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lrow = lane / kLanes, lcol = lane % kLanes;
+  constexpr int kWarps = NT / 32;
+  // stage rows y0-2 .. y0+th+1, words p0-1 .. p0+tw (periodic)
+  for (int rr = warp; rr < th + 4; rr += kWarps) {
+    int y = y0 + rr - 2;
+    y = (y < 0) ? y + L : (y >= L ? y - L : y);
+    const uint32_t* row = v.src + (size_t)y * Lh;
+    for (int jj = lane; jj < tw + 2; jj += 32) {
+      int p = p0 + jj - 1;
+      p = (p < 0) ? p + Lh : (p >= Lh ? p - Lh : p);
+      S.in[rr][jj] = CG ? __ldcg(row + p) : row[p];
+    }
+  }
+  __syncthreads();
+  // colour 0: tile rows -1 .. th, words 0 .. tw-1 (the colour-0 cell of a
+  // word is its low half on even rows, its high half on odd rows)
+  for (int r0 = warp * kRows - 1; r0 <= th; r0 += kWarps * kRows) {
+    const int r = r0 + lrow;
+    if (r > th) continue;
+    const int y = y0 + r;
+    const int hi = y & 1;
+    const int yg = (y < 0) ? y + L : (y >= L ? y - L : y);
+    const bool inside = (r >= 0) && (r < th);
+    for (int j = lcol; j < tw; j += kLanes) {
+      const int xg = 2 * (p0 + j) + hi;
+      uint32_t dummy = 0, dummy_b = 0;
+      const uint32_t out = update_in_word<RNG_WORDS, CMP64, false>(
+          S.in[r + 2][j + 1], S.in[r + 2][j], S.in[r + 2][j + 2], S.in[r + 1][j + 1],
+          S.in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), v.s_lo, v.s_hi, v.keys,
+          v.q, P, T, inside ? cnt.nacc : dummy, inside ? cnt.pair_sum : dummy, dummy_b);
+      if (inside) ++cnt.ncells;
+      S.mid[r + 1][j + 1] = out;
+    }
+  }
+  // colour 0 on the ring: per row r the one colour-0 cell just outside the
+  // tile, x0 - 1 (high half of word -1) on odd rows, x0 + 2 tw (low half of
+  // word tw) on even rows
+  for (int i = threadIdx.x; i < th + 2; i += NT) {
+    const int r = i - 1;
+    const int y = y0 + r;
+    const int hi = y & 1;
+    const int j = hi ? -1 : tw;
+    const int yg = (y < 0) ? y + L : (y >= L ? y - L : y);
+    int xg = 2 * (p0 + j) + hi;
+    xg = (xg < 0) ? xg + L : (xg >= L ? xg - L : xg);
+    uint32_t d0 = 0, d1 = 0, d2 = 0;
+    // the unused side of the ring word is clamped into the staged columns
+    const int jm = max(j, 0), jp = min(j + 2, tw + 1);
+    S.mid[r + 1][j + 1] = update_in_word<RNG_WORDS, CMP64, false>(
+        S.in[r + 2][j + 1], S.in[r + 2][jm], S.in[r + 2][jp], S.in[r + 1][j + 1],
+        S.in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), v.s_lo, v.s_hi, v.keys, v.q,
+        P, T, d0, d1, d2);
+  }
+  __syncthreads();
+  // colour 1: tile rows 0 .. th-1 (low half on odd rows, high on even rows)
+  for (int r0 = warp * kRows; r0 < th; r0 += kWarps * kRows) {
+    const int r = r0 + lrow;
+    if (r >= th) continue;
+    const int y = y0 + r;
+    const int hi = (y & 1) ^ 1;
+    uint32_t* drow = v.dst + (size_t)y * Lh + p0;
+    for (int j = lcol; j < tw; j += kLanes) {
+      const int xg = 2 * (p0 + j) + hi;
+      drow[j] = update_in_word<RNG_WORDS, CMP64, true>(
+          S.mid[r + 1][j + 1], S.mid[r + 1][j], S.mid[r + 1][j + 2], S.mid[r][j + 1],
+          S.mid[r + 2][j + 1], hi, (uint32_t)((long long)y * L + xg), v.s_lo, v.s_hi, v.keys,
+          v.q, P, T, cnt.nacc, cnt.pair_sum, cnt.bonds);
+      ++cnt.ncells;
+    }
+  }
+}
+
+}  // namespace cvf
