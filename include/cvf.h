@@ -173,6 +173,35 @@ int cvf_state_device_ptr(cvf_handle *h, void **dev_ptr);
 /* Waits for the handle's stream, frees what the library allocated. */
 int cvf_destroy(cvf_handle *h);
 
+/* Allocation-free sweep.  The paper has no counterpart: this entry point is
+ * for callers that cannot let a library call cudaMalloc -- applications that
+ * own all device memory through their own pool, or that must not allocate
+ * once running because an allocation can synchronise the device or fail
+ * under memory pressure in the middle of a run.  It advances a caller-owned
+ * lattice by n_sweeps MC steps (checkerboard schedule) and allocates nothing:
+ * the control block, counters, thresholds, FP64 parameters and up to 256
+ * recorded observable sets live in a fixed 64 KB device array that the
+ * library defines at file scope (every GPU that loads the library holds it
+ * until the process exits).
+ *   dev_state    device buffer of 2*L*L uint16 words (16-byte aligned): the
+ *                lattice is read from half (sweep & 1) and left in half
+ *                ((sweep + n_sweeps) & 1); the other half is overwritten.
+ *   V_iso, sweep the volume and the step count the run continues from
+ *                (acceptance counters start at 0 for the call).
+ *   record_every observables after every step whose count is a multiple of
+ *                it are copied to host_series[0..series_cap) (at most 256 per
+ *                call, else CVF_EINVAL); *n_series receives their number.
+ *   host_obs     receives the observables after the last step.
+ * The call synchronises `stream`.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call on a device uses the same array and clears
+ * what must start at zero, so calls whose GPU work overlaps (other threads,
+ * other streams) race with each other: serialise them. */
+int cvf_sweep_noalloc(const cvf_params *p, void *dev_state, double V_iso,
+                      int64_t sweep, int64_t n_sweeps, int32_t record_every,
+                      cvf_obs *host_series, int64_t series_cap,
+                      int64_t *n_series, cvf_obs *host_obs, void *stream);
+
 /* ------------------------------------------------------------------------
  * Batched replicas: many independent lattices (their own L, q, T, P, seed,
  * init) advanced by one persistent, cooperative, graph-captured launch.

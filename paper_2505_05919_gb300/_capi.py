@@ -69,6 +69,9 @@ _SIGS = {
     "cvf_recount": (ctypes.c_int, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
     "cvf_state_device_ptr": (ctypes.c_int, [_vp, _P(_vp)]),
     "cvf_destroy": (ctypes.c_int, [_vp]),
+    "cvf_sweep_noalloc": (ctypes.c_int, [_P(cvf_params), _vp, ctypes.c_double, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.c_int32, _P(cvf_obs), ctypes.c_int64,
+                                         _P(ctypes.c_int64), _P(cvf_obs), _vp]),
     "cvf_batch_create": (ctypes.c_int, [_P(cvf_params), ctypes.c_int32, _vp, _P(_vp)]),
     "cvf_batch_add": (ctypes.c_int, [_vp, _P(cvf_params), _P(ctypes.c_int32)]),
     "cvf_batch_remove": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -191,6 +194,18 @@ def cvf_state_device_ptr(h: int) -> int:
 
 def cvf_destroy(h: int) -> None:
     _check(load().cvf_destroy(h), "cvf_destroy")
+
+
+def cvf_sweep_noalloc(p: cvf_params, dev_state: int, V_iso: float, sweep: int, n_sweeps: int,
+                      record_every: int = 0, series_cap: int = 0, stream: int | None = None):
+    """Returns (observables, records).  Allocates nothing on the device."""
+    series = (cvf_obs * max(series_cap, 1))()
+    n = ctypes.c_int64()
+    out = cvf_obs()
+    _check(load().cvf_sweep_noalloc(ctypes.byref(p), dev_state, V_iso, sweep, n_sweeps, record_every,
+                                    series, series_cap, ctypes.byref(n), ctypes.byref(out),
+                                    stream or None), "cvf_sweep_noalloc")
+    return out, [series[i] for i in range(n.value)]
 
 
 # ---------------------------------------------------------------- batches --

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -658,3 +659,188 @@ int cvf_destroy(cvf_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free sweep (cvf_sweep_noalloc).  Everything the sweep needs
+// besides the caller's lattice -- the control block with its counters, the
+// threshold rows, the FP64 parameters and a short observable ring -- lives in
+// one file-scope device array of fixed size instead of memory from
+// cudaMalloc.  Every GPU that loads the library holds this array until the
+// process exits.  All calls on a device share it: the call clears what must
+// start at zero, and calls whose GPU work overlaps race on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocRing = 256;                 // recorded steps per call
+constexpr size_t kNoAllocScratchBytes = 64 * 1024;
+
+struct NoAllocScratch {
+  Ctrl ctrl;
+  unsigned long long table24[48];
+  VolumeArgs vol;
+  cvf_obs obs;
+  cvf_obs ring[kNoAllocRing];
+};
+static_assert(sizeof(NoAllocScratch) <= kNoAllocScratchBytes, "scratch layout");
+
+struct Table48 {
+  unsigned long long t[48];
+};
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices];
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace cvf {
+
+// Copies the call's parameters (passed by value) into the scratch and clears
+// the control block.
+__global__ void k_noalloc_setup(NoAllocScratch* s, VolumeArgs va, Table48 t) {
+  if (blockIdx.x != 0) return;
+  for (int i = threadIdx.x; i < 48; i += blockDim.x) s->table24[i] = t.t[i];
+  unsigned char* c = reinterpret_cast<unsigned char*>(&s->ctrl);
+  for (int i = threadIdx.x; i < (int)sizeof(Ctrl); i += blockDim.x) c[i] = 0;
+  if (threadIdx.x == 0) s->vol = va;
+}
+
+}  // namespace cvf
+
+namespace {
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code may not use the array's name as a device address).
+int noalloc_scratch(NoAllocScratch** out) {
+  int dev = 0;
+  CVF_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(CVF_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return set_error(CVF_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
+                       cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = reinterpret_cast<NoAllocScratch*>(g_noalloc_ptr[dev]);
+  return CVF_OK;
+}
+
+// The FP64 parameters and LJ shell prefix sums, built in fixed-size storage
+// (this path allocates nothing, not even host memory).  Same shells, same
+// order, same sums as fill_volume_args.
+int noalloc_volume_args(const cvf_params* p, long long N, VolumeArgs* va) {
+  std::memset(va, 0, sizeof(*va));
+  const int R = (int)std::ceil(p->cutoff);
+  int n = 0;
+  va->S12[0] = 0.0;
+  va->S6[0] = 0.0;
+  for (int64_t d2 = 1; d2 <= 2LL * R * R; ++d2) {
+    int64_t m = 0;
+    for (int i = -R; i <= R; ++i)
+      for (int j = -R; j <= R; ++j)
+        if ((int64_t)i * i + (int64_t)j * j == d2) ++m;
+    if (m == 0 || !((double)d2 < p->cutoff * p->cutoff)) continue;
+    if (n >= kMaxShells) return set_error(CVF_EINVAL, "cutoff too large");
+    va->shell_d2[n] = (double)d2;
+    const int64_t d6 = d2 * d2 * d2;
+    va->S12[n + 1] = va->S12[n] + (double)m / ((double)d6 * (double)d6);
+    va->S6[n + 1] = va->S6[n] + (double)m / (double)d6;
+    ++n;
+  }
+  va->nshell = n;
+  va->N = N;
+  va->epsilon = p->epsilon;
+  va->cutoff2 = p->cutoff * p->cutoff;
+  va->J = p->J;
+  va->J_sigma = p->J_sigma;
+  va->v_HB = p->v_HB;
+  va->kT = p->kT;
+  va->P = p->P;
+  va->dV_max = p->dv_max_frac * ((double)N * p->v_iso_init);
+  va->volume_moves = p->volume_moves;
+  return CVF_OK;
+}
+
+}  // namespace
+
+extern "C" int cvf_sweep_noalloc(const cvf_params* p, void* dev_state, double V_iso,
+                                 int64_t sweep, int64_t n_sweeps, int32_t record_every,
+                                 cvf_obs* host_series, int64_t series_cap, int64_t* n_series,
+                                 cvf_obs* host_obs, void* stream) {
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!dev_state || !host_obs || !n_series)
+    return set_error(CVF_EINVAL, "dev_state, host_obs and n_series are required");
+  if (reinterpret_cast<uintptr_t>(dev_state) & 15u)
+    return set_error(CVF_EINVAL, "dev_state must be 16-byte aligned");
+  if (p->schedule != CVF_SCHED_CHECKERBOARD)
+    return set_error(CVF_EINVAL, "cvf_sweep_noalloc runs the checkerboard schedule only");
+  const long long N = (long long)p->L * p->L;
+  if (!(V_iso >= (double)N) || !std::isfinite(V_iso))
+    return set_error(CVF_EINVAL, "V_iso=%g below the hard core N v0 = %lld", V_iso, N);
+  if (sweep < 0 || n_sweeps < 0 || record_every < 0 || series_cap < 0)
+    return set_error(CVF_EINVAL, "sweep, n_sweeps, record_every and series_cap must be >= 0");
+  long long records = 0;
+  if (record_every > 0)
+    records = (sweep + n_sweeps) / record_every - sweep / record_every;
+  if (records > kNoAllocRing)
+    return set_error(CVF_EINVAL,
+                     "%lld recorded steps requested; this entry point keeps at most %d per call",
+                     records, kNoAllocRing);
+  if (records > series_cap || (records > 0 && !host_series))
+    return set_error(CVF_EINVAL, "host_series holds %lld records, %lld needed",
+                     (long long)series_cap, records);
+  NoAllocScratch* s = nullptr;
+  rc = noalloc_scratch(&s);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Table48 t48;
+  const bool cmp64 = fill_table24(p, t48.t);
+  VolumeArgs va;
+  rc = noalloc_volume_args(p, N, &va);
+  if (rc) return rc;
+  LatticeArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.state = reinterpret_cast<uint16_t*>(dev_state);
+  A.ctrl = &s->ctrl;
+  A.table24 = s->table24;
+  A.vol = &s->vol;
+  A.ring = s->ring;
+  A.ring_cap = kNoAllocRing;
+  A.keys = make_round_keys(p->seed);
+  A.L = p->L;
+  A.q = (uint32_t)p->q;
+  uint16_t* cur = A.state + (size_t)(sweep & 1) * N;
+  const int grid_cells = grid_for(N, 8);
+  k_noalloc_setup<<<1, 256, 0, st>>>(s, va, t48);
+  k_set_ctrl<<<1, 32, 0, st>>>(&s->vol, &s->ctrl, V_iso, sweep, N);
+  k_recount<<<grid_cells, kThreads, 0, st>>>(cur, p->L, nullptr, &s->ctrl.acc_hb);
+  k_commit_counts<<<1, 32, 0, st>>>(&s->ctrl);
+  k_volume_prologue<<<1, 32, 0, st>>>(&s->vol, &s->ctrl, A.keys);
+  k_set_record<<<1, 32, 0, st>>>(&s->ctrl, record_every);
+  const int grid = tiled_grid(p->L, cmp64, p->rng_words);
+  for (int64_t i = 0; i < n_sweeps; ++i) {
+    if (p->rng_words == 1 && !cmp64)
+      k_sweep_tiled<1, false><<<grid, kThreads, 0, st>>>(A);
+    else if (p->rng_words == 1)
+      k_sweep_tiled<1, true><<<grid, kThreads, 0, st>>>(A);
+    else if (!cmp64)
+      k_sweep_tiled<2, false><<<grid, kThreads, 0, st>>>(A);
+    else
+      k_sweep_tiled<2, true><<<grid, kThreads, 0, st>>>(A);
+  }
+  k_observables<<<1, 32, 0, st>>>(&s->vol, &s->ctrl, &s->obs);
+  CVF_CUDA_CHECK(cudaGetLastError());
+  CVF_CUDA_CHECK(cudaMemcpyAsync(host_obs, &s->obs, sizeof(cvf_obs), cudaMemcpyDeviceToHost, st));
+  if (records > 0)
+    CVF_CUDA_CHECK(cudaMemcpyAsync(host_series, s->ring, sizeof(cvf_obs) * records,
+                                   cudaMemcpyDeviceToHost, st));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(st));
+  *n_series = records;
+  return CVF_OK;
+}
