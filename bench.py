@@ -45,7 +45,19 @@ def parse():
     ap.add_argument("--cpu-sample-sweeps", type=int, default=10)
     ap.add_argument("--mode", default="full", choices=["full", "kernel"],
                     help="kernel: one lattice, warm-up then timed sweeps only (profiling case)")
+    ap.add_argument("--batch-sweeps", type=int, default=5000,
+                    help="steps per replica in the batched measurement (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="time budget of the serving measurement (0: skip)")
     return ap.parse_args()
+
+
+# Integer work of one sigma update (SURVEY 8(d) figure with one Philox call
+# per cell): a quarter of a Philox4x32-10 call (10 rounds of two 32x32->64
+# multiplies and two 3-input XORs = 40 ops per cell) plus about 20 ops of the
+# update rule.  Peak: 152 SMs x 128 integer lanes x the 2070 MHz maximum clock.
+ALU_OPS_PER_UPDATE = 30.0
+ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 
 
 def dist_env():
@@ -217,6 +229,79 @@ def run_kernel_mode(args):
     return 0
 
 
+def measure_batched(args, rank):
+    """Configuration 4: 256 replicas (L from {32..512}, T x P grid), the same
+    number of steps each, in one persistent launch per call; tile shape from
+    the autotuner.  Baseline: the same replicas one per launch sequence (a
+    Lattice each, 200 steps), as replica-steps per second."""
+    import torch
+    from paper_2505_05919_gb300 import Batch, Lattice, params, workloads
+    from paper_2505_05919_gb300.autotune import autotune
+    reps = workloads.c4(sweeps=args.batch_sweeps)
+    ps = [params(r["T"], r["P"], L=r["L"], q=r["q"], seed=r["seed"] + rank * 100003) for r in reps]
+    stream = torch.cuda.Stream()
+    best, timings = autotune(ps, probe_sweeps=20, stream=stream)
+    with Batch(ps, stream=stream) as b:
+        b.set_tiles(best)
+        b.sweep([3] * len(ps))
+        b.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.sweep([args.batch_sweeps] * len(ps))
+        e1.record(stream)
+        e1.synchronize()
+        b.sync()
+        ms = e0.elapsed_time(e1)
+    cells = sum(r["L"] * r["L"] for r in reps)
+    batched_rate = len(ps) * args.batch_sweeps / (ms / 1e3)
+    solo_steps = 200
+    solo_ms = 0.0
+    with torch.cuda.stream(stream):
+        for p in ps:
+            with Lattice(p, stream=stream) as lat:
+                lat.sweep(3)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lat.sweep(solo_steps)
+                e1.record(stream)
+                e1.synchronize()
+                solo_ms += e0.elapsed_time(e1)
+    solo_rate = len(ps) * solo_steps / (solo_ms / 1e3)
+    return {"value": batched_rate, "unit": "replica-sweeps/s", "replicas": len(ps),
+            "sweeps_each": args.batch_sweeps, "ms": ms,
+            "updates_per_ns": 4.0 * cells * args.batch_sweeps / (ms * 1e6),
+            "one_replica_per_launch": {"value": solo_rate, "unit": "replica-sweeps/s",
+                                       "sweeps_each": solo_steps},
+            "speedup_vs_one_replica_per_launch": batched_rate / solo_rate,
+            "tile_config": best, "autotune_ms_per_step": timings,
+            "workload": "256 replicas, L from {32,64,128,256,512} (seed 4), T_i = 270 + 4i K, "
+                        "P_j = 0.1 + j 49.9/15 MPa, seeds 1000 + r"}
+
+
+def measure_serving(args, rank):
+    """Configuration 5: Poisson arrivals (200 jobs/s) of EOS jobs, L uniform in
+    {64..2048}, steps log-uniform in 10^3..10^5, served by continuous batching
+    for a fixed wall-clock budget (the offered load exceeds one GPU's
+    throughput about twentyfold, so the queue grows; finished jobs give the
+    latency percentiles)."""
+    from paper_2505_05919_gb300 import workloads
+    from paper_2505_05919_gb300.serve import Job, Server
+    jobs = [Job(T=j["T"], P=j["P"], L=j["L"], sweeps=j["sweeps"], seed=j["seed"] + rank * 100003,
+                arrival=j["arrival"]) for j in workloads.c5()]
+    srv = Server(epoch_steps=500)
+    try:
+        stats = srv.run_trace(jobs, time_limit=args.serve_seconds)
+    finally:
+        srv.close()
+    stats["offered_jobs_per_s"] = 200.0
+    stats["workload"] = ("Poisson 200 jobs/s (seed 5), L uniform {64,...,2048}, steps log-uniform "
+                         "1e3..1e5, (T, P) uniform 270-330 K x 0.1-50 MPa, %.0f s budget" % args.serve_seconds)
+    return stats
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -282,7 +367,8 @@ def main():
     value = updates / (dev_s * 1e9)
     obs = [l.observables() for l in lats]
 
-    # dominant kernel: the sweep kernels of one MC step, timed alone
+    # dominant kernel: k_sweep_tiled, one launch per MC step; its average
+    # duration from CUDA events around 200 steps on the lattice's stream
     sw_ms = []
     lat = lats[1]
     for _ in range(5):
@@ -295,12 +381,18 @@ def main():
         sw_ms.append(ev0.elapsed_time(ev1) / 200)
     per_sweep_ms = statistics.median(sw_ms)
     peaks, peak_kind = measured_peaks()
+    upd_per_s = 4.0 * L * L / (per_sweep_ms * 1e-3)
+    roofline = {"bound": "alu", "achieved": ALU_OPS_PER_UPDATE * upd_per_s / 1e12,
+                "peak": ALU_PEAK_TOPS, "unit": "Tintop/s",
+                "frac": ALU_OPS_PER_UPDATE * upd_per_s / 1e12 / ALU_PEAK_TOPS,
+                "traffic": None, "kernel": "k_sweep_tiled (one launch per MC step)",
+                "ops_per_update": ALU_OPS_PER_UPDATE,
+                "peak_kind": "derived: 152 SM x 128 lanes x 2070 MHz"}
     bytes_per_sweep = 4.0 * L * L  # read 2 B + write 2 B per cell (1 B per sigma update)
     achieved_gbs = bytes_per_sweep / (per_sweep_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "one MC step (volume-move kernel + tiled sweep kernel)",
-                "peak_kind": peak_kind}
+    roofline_hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
+                    "bytes_per_update": 1.0, "peak_kind": peak_kind}
 
     # end to end through the C ABI with host buffers
     e2e_ms = []
@@ -321,6 +413,9 @@ def main():
     e2e = {"value": 4.0 * L * L * S / (e2e_s * 1e9), "unit": UNIT,
            "h2d_bytes_per_step": 2 * L * L, "d2h_bytes_per_step": 2 * L * L + 96}
 
+    batched = measure_batched(args, rank) if args.batch_sweeps > 0 else None
+    serving = measure_serving(args, rank) if args.serve_seconds > 0 else None
+
     line = None
     if rank == 0:
         cpu = None
@@ -329,7 +424,7 @@ def main():
                 cpu = cpu_baseline(cfgs[1], args.cpu_sample_sweeps)
             except Exception as e:  # the baseline never blocks the line
                 cpu = {"value": None, "error": str(e)}
-        launches_per_sweep = 2  # volume move + tiled sweep
+        launches_per_sweep = 1  # k_sweep_tiled (the volume move runs inside it)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,
@@ -339,9 +434,12 @@ def main():
                        "L": L, "sweeps_per_step": S, "l2": "flushed between timed steps (512 MB write)",
                        "rng_words": 1, "schedule": "checkerboard"},
             "roofline": roofline,
+            "roofline_hbm": roofline_hbm,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps * (S * launches_per_sweep + 1),
+            "batched": batched,
+            "serving": serving,
             "clocks": clocks,
             "wall_s": t_wall,
             "per_sweep_ms": per_sweep_ms,
