@@ -58,13 +58,16 @@ def parse():
 # update rule.  Peak: 152 SMs x 128 integer lanes x the 2070 MHz maximum clock.
 ALU_OPS_PER_UPDATE = 30.0
 ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
+# DRAM bytes (read + write) of one k_sweep_tiled launch at L = 4096, from one
+# ncu capture of the current kernel; scaled by L^2 for other sizes (the state
+# is read once per step, the writes stay in L2).  Reset to None whenever the
+# kernel changes until a new capture is taken.
+SWEEP_DRAM_BYTES_4096 = 34.18e6
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2505_05919_gb300 import dist
+    return dist.env()
 
 
 def workload_configs(L):
@@ -235,10 +238,10 @@ def measure_batched(args, rank):
     the autotuner.  Baseline: the same replicas one per launch sequence (a
     Lattice each, 200 steps), as replica-steps per second."""
     import torch
-    from paper_2505_05919_gb300 import Batch, Lattice, params, workloads
+    from paper_2505_05919_gb300 import Batch, Lattice, dist, params, workloads
     from paper_2505_05919_gb300.autotune import autotune
     reps = workloads.c4(sweeps=args.batch_sweeps)
-    ps = [params(r["T"], r["P"], L=r["L"], q=r["q"], seed=r["seed"] + rank * 100003) for r in reps]
+    ps = [params(r["T"], r["P"], L=r["L"], q=r["q"], seed=r["seed"] + dist.seed_offset(rank)) for r in reps]
     stream = torch.cuda.Stream()
     best, timings = autotune(ps, probe_sweeps=20, stream=stream)
     with Batch(ps, stream=stream) as b:
@@ -287,9 +290,9 @@ def measure_serving(args, rank):
     for a fixed wall-clock budget (the offered load exceeds one GPU's
     throughput about twentyfold, so the queue grows; finished jobs give the
     latency percentiles)."""
-    from paper_2505_05919_gb300 import workloads
+    from paper_2505_05919_gb300 import dist, workloads
     from paper_2505_05919_gb300.serve import Job, Server
-    jobs = [Job(T=j["T"], P=j["P"], L=j["L"], sweeps=j["sweeps"], seed=j["seed"] + rank * 100003,
+    jobs = [Job(T=j["T"], P=j["P"], L=j["L"], sweeps=j["sweeps"], seed=j["seed"] + dist.seed_offset(rank),
                 arrival=j["arrival"]) for j in workloads.c5()]
     srv = Server(epoch_steps=500)
     try:
@@ -310,11 +313,10 @@ def main():
         return run_kernel_mode(args)
     import numpy as np
     import torch
+    from paper_2505_05919_gb300 import dist
     rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
+    dist.init()
     from paper_2505_05919_gb300 import Lattice, _capi, build as libbuild
     libbuild.build()
     _capi.load()
@@ -325,14 +327,12 @@ def main():
     lats = []
     with torch.cuda.stream(stream):
         for c in cfgs:
-            lats.append(Lattice(lib_params(c, seed_offset=rank * 7919), stream=stream))
+            lats.append(Lattice(lib_params(c, seed_offset=dist.seed_offset(rank)), stream=stream))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def barrier():
         torch.cuda.synchronize()
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        dist.barrier()
 
     # warm-up (graphs instantiated here)
     for i in range(args.warmup):
@@ -357,12 +357,7 @@ def main():
     barrier()
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
-    dev_s = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = float(t.item())
+    dev_s = dist.max_over_ranks(sum(step_ms) / 1e3)
     updates = 4.0 * L * L * S * args.steps * world
     value = updates / (dev_s * 1e9)
     obs = [l.observables() for l in lats]
@@ -385,7 +380,10 @@ def main():
     roofline = {"bound": "alu", "achieved": ALU_OPS_PER_UPDATE * upd_per_s / 1e12,
                 "peak": ALU_PEAK_TOPS, "unit": "Tintop/s",
                 "frac": ALU_OPS_PER_UPDATE * upd_per_s / 1e12 / ALU_PEAK_TOPS,
-                "traffic": None, "kernel": "k_sweep_tiled (one launch per MC step)",
+                "traffic": (SWEEP_DRAM_BYTES_4096 * (L / 4096.0) ** 2
+                            if SWEEP_DRAM_BYTES_4096 else None),
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "kernel": "k_sweep_tiled (one launch per MC step)",
                 "ops_per_update": ALU_OPS_PER_UPDATE,
                 "peak_kind": "derived: 152 SM x 128 lanes x 2070 MHz"}
     bytes_per_sweep = 4.0 * L * L  # read 2 B + write 2 B per cell (1 B per sigma update)
@@ -448,9 +446,7 @@ def main():
         print(json.dumps(line))
     for l in lats:
         l.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    dist.finalize()
     return 0
 
 
