@@ -92,6 +92,9 @@ typedef struct cvf_obs {
   double H;           /* H = U_LJ - J N_HB - J_sigma N_sigma + P V (Eq. H) */
   int32_t g;          /* gate: 1 liquid-like (V_iso/N < 2 v0), 0 gas-like */
   int32_t pad;
+  int64_t n_state[8]; /* N_q': sigma variables in state q' (q' >= q: 0);
+                         the order parameter is M = max N_q' / (4N),
+                         Eq. (correlation) */
 } cvf_obs;
 
 typedef struct cvf_handle cvf_handle;

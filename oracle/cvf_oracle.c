@@ -478,7 +478,9 @@ void orc_step(orc_state *st) {
 }
 
 /* Observables (Eq. V and Eq. H): N_HB = g N_HB_raw, V = V_iso + v_HB N_HB,
-   U_LJ = N u(v_iso), H = U_LJ - J N_HB - J_sigma N_sigma + P V. */
+   U_LJ = N u(v_iso), H = U_LJ - J N_HB - J_sigma N_sigma + P V; and N_q', the
+   number of sigma variables in each state q' (Eq. correlation, the counts
+   the order parameter M is the maximum of). */
 void orc_observables(const orc_state *st, orc_obs *o) {
   const orc_params *p = &st->p;
   double Nd = (double)st->N;
@@ -499,6 +501,8 @@ void orc_observables(const orc_state *st, orc_obs *o) {
   o->U_LJ = U;
   o->H = H;
   o->g = st->g;
+  for (int64_t c = 0; c < st->N; ++c)
+    for (int a = 0; a < 4; ++a) o->n_state[orc_arm(st->w[c], a)] += 1;
 }
 
 /* n steps; after every step whose new count is a multiple of record_every

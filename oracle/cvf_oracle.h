@@ -40,6 +40,7 @@ typedef struct {
   int64_t sweep, n_hb, n_hb_raw, n_coop, acc_sigma, acc_volume;
   double V_iso, V, U_LJ, H;
   int32_t g, pad;
+  int64_t n_state[8]; /* number of sigma variables in each state q' */
 } orc_obs;
 
 typedef struct {

@@ -94,7 +94,9 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_batch_sweep(con
   __shared__ int s_rep, s_tile, s_abort, s_last;
   __shared__ long long s_rel;
   __shared__ uint32_t s_q;
+  __shared__ uint32_t s_hist4[4];
   if (threadIdx.x == 0) s_q = 0;
+  if (threadIdx.x < 4) s_hist4[threadIdx.x] = 0;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -168,8 +170,10 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_batch_sweep(con
     const int ntiles = tiles_x * ((L + TR - 1) / TR);
     const int t = s_tile;
     TileCounts cnt{0, 0, 0, 0};
+    const bool rec = step_recorded(vc->record_every, step);
     sweep_tile<RNG_WORDS, CMP64, TR, TW, kThreads, KeysSeed, true>(
-        v, (t / tiles_x) * TR, (t % tiles_x) * TW, S, P, sT, cnt);
+        v, (t / tiles_x) * TR, (t % tiles_x) * TW, S, P, sT, cnt, rec ? s_hist4 : nullptr,
+        ctl->acc_hist);
     uint32_t pairs = cnt.pairs(), bonds = cnt.bonds, nacc = cnt.nacc;
     block_sum3<kThreads>(pairs, bonds, nacc);
     if (threadIdx.x == 0) {
@@ -236,6 +240,7 @@ struct cvf_batch {
   void* h_work;  // pinned staging of the launch description
   size_t h_work_bytes;
   cvf_obs* d_obs;
+  unsigned long long* d_hist;
   void* h_pinned;
   cudaGraphExec_t graph[kNumTileConfigs][2];  // [config][cmp64]
   int graph_n_reps[kNumTileConfigs][2];
@@ -461,6 +466,7 @@ int cvf_batch_create(const cvf_params* params, int32_t n, void* stream, cvf_batc
   b->tile_cfg = 1;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_obs, sizeof(cvf_obs));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_hist, sizeof(unsigned long long) * 9);
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_pinned, 4096);
   if (e != cudaSuccess) {
     cvf_batch_destroy(b);
@@ -672,7 +678,10 @@ int cvf_batch_observables(cvf_batch* b, int32_t replica, cvf_obs* out) {
   rc = batch_status(b);
   if (rc) return rc;
   const Replica& r = b->reps[replica];
-  k_observables<<<1, 32, 0, b->stream>>>(r.vol, r.ctrl, b->d_obs);
+  CVF_CUDA_CHECK(cudaMemsetAsync(b->d_hist, 0, sizeof(unsigned long long) * 9, b->stream));
+  k_histogram<<<(int)std::max<long long>(1, std::min<long long>((r.N + kThreads - 1) / kThreads, 2048)),
+                kThreads, 0, b->stream>>>(r.state + (size_t)(r.sweep_host & 1) * r.N, r.N, b->d_hist);
+  k_observables<<<1, 32, 0, b->stream>>>(r.vol, r.ctrl, b->d_hist, b->d_obs);
   CVF_CUDA_CHECK(cudaGetLastError());
   CVF_CUDA_CHECK(cudaMemcpyAsync(b->h_pinned, b->d_obs, sizeof(cvf_obs), cudaMemcpyDeviceToHost,
                                  b->stream));
@@ -706,6 +715,7 @@ int cvf_batch_destroy(cvf_batch* b) {
   if (b->d_work) cudaFree(b->d_work);
   if (b->h_work) cudaFreeHost(b->h_work);
   if (b->d_obs) cudaFree(b->d_obs);
+  if (b->d_hist) cudaFree(b->d_hist);
   if (b->h_pinned) cudaFreeHost(b->h_pinned);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;

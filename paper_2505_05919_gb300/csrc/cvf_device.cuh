@@ -332,6 +332,10 @@ struct Ctrl {
   unsigned int tile_next;
   // observable ring: records written so far (monotone)
   long long ring_head;
+  // N_q' of the step being recorded (accumulated by the sweep only when its
+  // observables go to the ring) and of the last recorded step
+  unsigned long long acc_hist[8];
+  long long hist[8];
 };
 
 struct VolumeResult {
@@ -403,6 +407,7 @@ __device__ __forceinline__ cvf_obs make_obs(const VolumeArgs& V, const Ctrl* ctl
   o.H = H;
   o.g = ctl->g;
   o.pad = 0;
+  for (int v = 0; v < 8; ++v) o.n_state[v] = ctl->hist[v];
   return o;
 }
 
@@ -418,8 +423,12 @@ __device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cv
                                               long long ring_cap, const RoundKeys& K) {
   volatile Ctrl* c = ctl;
   Ctrl s;  // committed state after this step
+  const int every = c->record_every;
+  const bool recorded = (every > 0) && ((c->sweep + 1) % every == 0);
   s.n_hb_raw = (long long)c->acc_hb;
-  s.n_coop = (long long)c->acc_pairs;
+  // N_sigma is counted by the sweep only on recorded steps; otherwise it is
+  // unknown (-1) until a recount (cvf_observables counts it on demand)
+  s.n_coop = recorded ? (long long)c->acc_pairs : -1;
   s.acc_sigma = c->acc_sigma + (long long)c->acc_moves;
   s.V_iso = c->next_V;
   s.u_cell = c->next_u;
@@ -439,8 +448,12 @@ __device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cv
   c->done = 0;
   c->tile_next = 0;
   c->sweep = s.sweep;
-  const int every = c->record_every;
-  if (every > 0 && s.sweep % every == 0) {
+  if (recorded) {
+    for (int v = 0; v < 8; ++v) {
+      s.hist[v] = (long long)c->acc_hist[v];
+      c->hist[v] = s.hist[v];
+      c->acc_hist[v] = 0;
+    }
     const long long head = c->ring_head;
     ring[head % ring_cap] = make_obs(V, &s);
     c->ring_head = head + 1;
@@ -474,6 +487,36 @@ __device__ __forceinline__ bool last_block(unsigned int* done) {
   }
   __syncthreads();
   return is_last != 0;
+}
+
+// True when the observables after step `step` (0-based, so the count after
+// it is step + 1) go to the ring: the sweep then also accumulates N_q'.
+__device__ __forceinline__ bool step_recorded(int every, long long step) {
+  return every > 0 && (step + 1) % every == 0;
+}
+
+// N_q' of the cells a block finishes, accumulated only on recorded steps in
+// four shared words: lane v & 3 (16 bits) of word v & 3, v < 4 in the low
+// half, v >= 4 in the high half, from each cell's count word (nibble v =
+// number of the cell's arms with sigma = v).  A tile adds at most 4 x 8192
+// to a lane; the words are moved to the 64-bit totals after every tile.
+__device__ __forceinline__ void hist_add_cell(uint32_t* s_hist4, uint32_t cnt) {
+  atomicAdd(&s_hist4[0], cnt & 0x000F000Fu);
+  atomicAdd(&s_hist4[1], (cnt >> 4) & 0x000F000Fu);
+  atomicAdd(&s_hist4[2], (cnt >> 8) & 0x000F000Fu);
+  atomicAdd(&s_hist4[3], (cnt >> 12) & 0x000F000Fu);
+}
+
+// Called by the whole block after its shared adds are complete (after a
+// barrier): moves the four words to out[0..8) and clears them.
+__device__ __forceinline__ void hist_flush(uint32_t* s_hist4, unsigned long long* out) {
+  if (threadIdx.x < 4) {
+    const uint32_t w = s_hist4[threadIdx.x];
+    if (w & 0xFFFFu) atomicAdd(&out[threadIdx.x], (unsigned long long)(w & 0xFFFFu));
+    if (w >> 16) atomicAdd(&out[threadIdx.x + 4], (unsigned long long)(w >> 16));
+    s_hist4[threadIdx.x] = 0;
+    __threadfence();  // visible before the block reports itself done
+  }
 }
 
 // Block-wide sum of three counters; the result is valid in thread 0.

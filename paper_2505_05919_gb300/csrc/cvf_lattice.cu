@@ -122,8 +122,43 @@ __global__ void k_volume_prologue(const VolumeArgs* __restrict__ V, Ctrl* ctl, R
 }
 
 __global__ void k_observables(const VolumeArgs* __restrict__ V, const Ctrl* ctl,
-                              cvf_obs* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *out = make_obs(*V, ctl);
+                              const unsigned long long* hist, cvf_obs* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    Ctrl c = *ctl;
+    if (hist) c.n_coop = (long long)hist[8];  // counted now from the lattice
+    cvf_obs o = make_obs(*V, &c);
+    if (hist)
+      for (int v = 0; v < 8; ++v) o.n_state[v] = (long long)hist[v];
+    *out = o;
+  }
+}
+
+// N_q' of a lattice (the number of sigma variables in each state) added to
+// out[0..8), and its equal in-cell pairs (N_sigma) added to out[8].
+__global__ void __launch_bounds__(kThreads) k_histogram(const uint16_t* __restrict__ state,
+                                                        long long N, unsigned long long* out) {
+  __shared__ unsigned long long s_cnt[9];
+  if (threadIdx.x < 9) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  uint32_t pairs = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint32_t w = state[i];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const uint32_t v = (w >> (3 * a)) & 7u;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) c[k] += (v == (uint32_t)k) ? 1u : 0u;
+    }
+    pairs += cell_pairs(w);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (c[k]) atomicAdd(&s_cnt[k], (unsigned long long)c[k]);
+  if (pairs) atomicAdd(&s_cnt[8], (unsigned long long)pairs);
+  __syncthreads();
+  if (threadIdx.x < 9 && s_cnt[threadIdx.x]) atomicAdd(&out[threadIdx.x], s_cnt[threadIdx.x]);
 }
 
 // ---------------------------------------------------------------------------
@@ -181,6 +216,9 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_sweep_tiled(Lat
   const int tiles_x = (v.Lh + kTileWords - 1) / kTileWords;
   const int ntiles = tiles_x * ((v.L + kTileRows - 1) / kTileRows);
   TileCounts cnt{0, 0, 0, 0};
+  __shared__ uint32_t s_hist4[4];
+  const bool rec = step_recorded(ctl->record_every, step);
+  if (threadIdx.x < 4) s_hist4[threadIdx.x] = 0;
   for (;;) {
     __syncthreads();  // previous tile fully consumed; tables visible
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctl->tile_next, 1u);
@@ -188,7 +226,8 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_sweep_tiled(Lat
     const int t = s_tile;
     if (t >= ntiles) break;
     sweep_tile<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads>(
-        v, (t / tiles_x) * kTileRows, (t % tiles_x) * kTileWords, S, P, sT, cnt);
+        v, (t / tiles_x) * kTileRows, (t % tiles_x) * kTileWords, S, P, sT, cnt,
+        rec ? s_hist4 : nullptr, ctl->acc_hist);
   }
   uint32_t pairs = cnt.pairs(), bonds = cnt.bonds, nacc = cnt.nacc;
   block_sum3<kThreads>(pairs, bonds, nacc);
@@ -493,7 +532,7 @@ int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** 
   CREATE_CHECK(cudaMalloc(&h->obs_dev, sizeof(cvf_obs)));
   CREATE_CHECK(cudaMalloc(&h->table_dev, sizeof(unsigned long long) * 48));
   CREATE_CHECK(cudaMalloc(&h->vol_dev, sizeof(VolumeArgs)));
-  CREATE_CHECK(cudaMalloc(&h->rc_dev, sizeof(unsigned long long) * 2));
+  CREATE_CHECK(cudaMalloc(&h->rc_dev, sizeof(unsigned long long) * 9));
   CREATE_CHECK(cudaMallocHost(&h->host_pinned, 4096));
 
   unsigned long long table24[48];
@@ -559,7 +598,9 @@ int cvf_sweep(cvf_handle* h, int64_t n_sweeps, int32_t record_every) {
 
 int cvf_observables(cvf_handle* h, cvf_obs* out) {
   if (!h || !out) return set_error(CVF_EINVAL, "NULL argument");
-  k_observables<<<1, 32, 0, h->stream>>>(h->vol_dev, h->ctrl, h->obs_dev);
+  CVF_CUDA_CHECK(cudaMemsetAsync(h->rc_dev, 0, sizeof(unsigned long long) * 9, h->stream));
+  k_histogram<<<h->grid_cells, kThreads, 0, h->stream>>>(current(h), h->N, h->rc_dev);
+  k_observables<<<1, 32, 0, h->stream>>>(h->vol_dev, h->ctrl, h->rc_dev, h->obs_dev);
   CVF_CUDA_CHECK(cudaGetLastError());
   CVF_CUDA_CHECK(cudaMemcpyAsync(h->host_pinned, h->obs_dev, sizeof(cvf_obs),
                                  cudaMemcpyDeviceToHost, h->stream));
@@ -676,6 +717,7 @@ constexpr size_t kNoAllocScratchBytes = 64 * 1024;
 
 struct NoAllocScratch {
   Ctrl ctrl;
+  unsigned long long hist[9];
   unsigned long long table24[48];
   VolumeArgs vol;
   cvf_obs obs;
@@ -834,7 +876,10 @@ extern "C" int cvf_sweep_noalloc(const cvf_params* p, void* dev_state, double V_
     else
       k_sweep_tiled<2, true><<<grid, kThreads, 0, st>>>(A);
   }
-  k_observables<<<1, 32, 0, st>>>(&s->vol, &s->ctrl, &s->obs);
+  CVF_CUDA_CHECK(cudaMemsetAsync(s->hist, 0, sizeof(s->hist), st));
+  k_histogram<<<grid_cells, kThreads, 0, st>>>(A.state + (size_t)((sweep + n_sweeps) & 1) * N, N,
+                                               s->hist);
+  k_observables<<<1, 32, 0, st>>>(&s->vol, &s->ctrl, s->hist, &s->obs);
   CVF_CUDA_CHECK(cudaGetLastError());
   CVF_CUDA_CHECK(cudaMemcpyAsync(host_obs, &s->obs, sizeof(cvf_obs), cudaMemcpyDeviceToHost, st));
   if (records > 0)

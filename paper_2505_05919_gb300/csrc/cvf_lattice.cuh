@@ -37,7 +37,10 @@ __global__ void k_set_ctrl(const VolumeArgs* __restrict__ V, Ctrl* ctl, double V
                            long long sweep, long long N);
 __global__ void k_set_record(Ctrl* ctl, int record_every);
 __global__ void k_volume_prologue(const VolumeArgs* __restrict__ V, Ctrl* ctl, RoundKeys K);
-__global__ void k_observables(const VolumeArgs* __restrict__ V, const Ctrl* ctl, cvf_obs* out);
+__global__ void k_observables(const VolumeArgs* __restrict__ V, const Ctrl* ctl,
+                              const unsigned long long* hist, cvf_obs* out);
+__global__ void k_histogram(const uint16_t* __restrict__ state, long long N,
+                            unsigned long long* out);
 
 // Host helpers shared by both paths.
 void fill_volume_args(const cvf_params* p, long long N, const std::vector<int64_t>& d2,

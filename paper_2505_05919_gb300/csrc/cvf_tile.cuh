@@ -47,7 +47,8 @@ __device__ __forceinline__ uint32_t update_arms_tab(uint32_t t4[4], const uint32
                                                     const uint32_t acc[4], const uint32_t kk[4],
                                                     const ProposalTable& P,
                                                     const typename ThresholdRow<CMP64>::type* T,
-                                                    uint32_t& naccepted, uint32_t& pair_sum) {
+                                                    uint32_t& naccepted, uint32_t& pair_sum,
+                                                    uint32_t& cnt_out, bool count_pairs) {
   uint32_t oh[4], m[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -72,8 +73,11 @@ __device__ __forceinline__ uint32_t update_arms_tab(uint32_t t4[4], const uint32
       ++naccepted;
     }
   }
+  if (count_pairs) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a) pair_sum += nibble(cnt, m[a]);
+    for (int a = 0; a < 4; ++a) pair_sum += nibble(cnt, m[a]);
+  }
+  cnt_out = cnt;
   uint32_t bonds = 0;
   if (BONDS) {
 #pragma unroll
@@ -134,7 +138,7 @@ __device__ __forceinline__ uint32_t update_in_word(
     uint32_t own, uint32_t xm_word, uint32_t xp_word, uint32_t ym_word, uint32_t yp_word, int hi,
     uint32_t c, uint32_t s_lo, uint32_t s_hi, const KEYS& keys, uint32_t q,
     const ProposalTable& P, const typename ThresholdRow<CMP64>::type* T, uint32_t& nacc,
-    uint32_t& pair_sum, uint32_t& bonds) {
+    uint32_t& pair_sum, uint32_t& bonds, uint32_t* s_hist4) {
   // partner arms: arm 0 (+x) <-> arm 1 of the +x cell, arm 1 (-x) <-> arm 0 of
   // the -x cell, arm 2 (+y) <-> arm 3 of the +y cell, arm 3 <-> arm 2 of -y
   uint32_t n4[4];
@@ -155,7 +159,11 @@ __device__ __forceinline__ uint32_t update_in_word(
   }
   uint32_t acc[4], kk[4];
   draws<RNG_WORDS>(c, s_lo, s_hi, keys, q, acc, kk);
-  bonds += update_arms_tab<CMP64, BONDS>(t4, nb8, acc, kk, P, T, nacc, pair_sum);
+  uint32_t cnt;
+  // equal pairs (N_sigma) and N_q' only on recorded steps (s_hist4 set)
+  bonds += update_arms_tab<CMP64, BONDS>(t4, nb8, acc, kk, P, T, nacc, pair_sum, cnt,
+                                         s_hist4 != nullptr);
+  if (s_hist4) hist_add_cell(s_hist4, cnt);
   const uint32_t wn = (t4[0] >> 2) | (t4[1] << 1) | (t4[2] << 4) | (t4[3] << 7);
   return hi ? ((own & 0xFFFFu) | (wn << 16)) : ((own & 0xFFFF0000u) | wn);
 }
@@ -187,6 +195,10 @@ struct StepView {
 // Sweep the tile at rows y0.., words p0.. of one lattice.  Called by all
 // threads of the block; ends with the tile written to dst (no trailing
 // barrier: the caller synchronises before reusing the shared buffers).
+// s_hist4 != nullptr (recorded steps): N_q' of the tile's cells is added to
+// hist_out[0..8) through the block's four zeroed shared words, and the equal
+// pairs (N_sigma) are counted; on other steps neither is (N_HB_raw, which the
+// volume move needs, and the accepted moves are counted on every step).
 // CG: stage through L2 only (the source may have been written by other SMs
 // since this SM last cached it, without a kernel boundary in between).
 // A warp covers max(1, 32/TW) rows per pass, one lane per word.
@@ -194,7 +206,8 @@ template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS, bool
 __device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int p0,
                                            TileSmem<TR, TW>& S, const ProposalTable& P,
                                            const typename ThresholdRow<CMP64>::type* T,
-                                           TileCounts& cnt) {
+                                           TileCounts& cnt, uint32_t* s_hist4,
+                                           unsigned long long* hist_out) {
   static_assert(TW >= 32 ? (TW % 32 == 0) : (32 % TW == 0), "tile width");
   constexpr int kRows = (TW >= 32) ? 1 : 32 / TW;  // rows per warp pass
   constexpr int kLanes = (TW >= 32) ? 32 : TW;     // lanes per row
@@ -231,7 +244,8 @@ __device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int 
       const uint32_t out = update_in_word<RNG_WORDS, CMP64, false>(
           S.in[r + 2][j + 1], S.in[r + 2][j], S.in[r + 2][j + 2], S.in[r + 1][j + 1],
           S.in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), v.s_lo, v.s_hi, v.keys,
-          v.q, P, T, inside ? cnt.nacc : dummy, inside ? cnt.pair_sum : dummy, dummy_b);
+          v.q, P, T, inside ? cnt.nacc : dummy, inside ? cnt.pair_sum : dummy, dummy_b,
+          inside ? s_hist4 : nullptr);
       if (inside) ++cnt.ncells;
       S.mid[r + 1][j + 1] = out;
     }
@@ -253,7 +267,7 @@ __device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int 
     S.mid[r + 1][j + 1] = update_in_word<RNG_WORDS, CMP64, false>(
         S.in[r + 2][j + 1], S.in[r + 2][jm], S.in[r + 2][jp], S.in[r + 1][j + 1],
         S.in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), v.s_lo, v.s_hi, v.keys, v.q,
-        P, T, d0, d1, d2);
+        P, T, d0, d1, d2, nullptr);
   }
   __syncthreads();
   // colour 1: tile rows 0 .. th-1 (low half on odd rows, high on even rows)
@@ -268,9 +282,13 @@ __device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int 
       drow[j] = update_in_word<RNG_WORDS, CMP64, true>(
           S.mid[r + 1][j + 1], S.mid[r + 1][j], S.mid[r + 1][j + 2], S.mid[r][j + 1],
           S.mid[r + 2][j + 1], hi, (uint32_t)((long long)y * L + xg), v.s_lo, v.s_hi, v.keys,
-          v.q, P, T, cnt.nacc, cnt.pair_sum, cnt.bonds);
+          v.q, P, T, cnt.nacc, cnt.pair_sum, cnt.bonds, s_hist4);
       ++cnt.ncells;
     }
+  }
+  if (s_hist4) {  // block-uniform: only on recorded steps
+    __syncthreads();
+    hist_flush(s_hist4, hist_out);
   }
 }
 

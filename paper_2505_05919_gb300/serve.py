@@ -8,7 +8,8 @@ the device as one replica of a Batch.  Each epoch it
      covers the new replica and a slot is free,
   2. advances every resident job by min(remaining, epoch_steps) steps in one
      persistent launch (jobs admitted at this boundary run alongside jobs
-     that are half done),
+     that are half done); with epoch_cell_steps set, epoch_steps follows the
+     resident work so that an epoch stays about that many cell-steps long,
   3. retires finished jobs: their observables (and optionally the lattice)
      are read back and their replica is freed.
 
@@ -64,10 +65,14 @@ class Server:
 
     def __init__(self, epoch_steps: int = 200, max_resident: int = 512,
                  hbm_reserve_bytes: int = 1 << 30, mem_budget_bytes: int | None = None,
-                 tile_config: int | None = None, stream=None):
+                 tile_config: int | None = None, stream=None,
+                 epoch_cell_steps: float | None = None, max_resident_cells: int | None = None):
         import torch
         self.torch = torch
         self.epoch_steps = int(epoch_steps)
+        self.epoch_cell_steps = epoch_cell_steps
+        self.max_resident_cells = max_resident_cells
+        self.resident_cells = 0
         self.max_resident = int(max_resident)
         self.reserve = int(hbm_reserve_bytes)
         self.budget = mem_budget_bytes          # optional cap on what jobs may hold
@@ -105,12 +110,16 @@ class Server:
             if j.id == job_id:
                 self.batch.remove(rid)
                 self.held_bytes -= j.device_bytes
+                self.resident_cells -= j.L * j.L
                 del self.resident[rid]
                 return True
         return False
 
     def _fits(self, job: Job) -> bool:
         if len(self.resident) >= self.max_resident:
+            return False
+        if (self.max_resident_cells is not None and self.resident
+                and self.resident_cells + job.L * job.L > self.max_resident_cells):
             return False
         if self.budget is not None:
             return self.held_bytes + job.device_bytes <= self.budget
@@ -124,6 +133,7 @@ class Server:
             job.admitted = self.now()
             self.resident[rid] = job
             self.held_bytes += job.device_bytes
+            self.resident_cells += job.L * job.L
 
     # ----------------------------------------------------------------- epoch --
     def step(self) -> int:
@@ -133,9 +143,12 @@ class Server:
         if not self.resident:
             return 0
         n = self.batch.slots()
+        steps = self.epoch_steps
+        if self.epoch_cell_steps:
+            steps = max(1, min(self.epoch_steps, int(self.epoch_cell_steps // max(1, self.resident_cells))))
         plan = [0] * n
         for rid, job in self.resident.items():
-            plan[rid] = min(self.epoch_steps, job.sweeps - job.done)
+            plan[rid] = min(steps, job.sweeps - job.done)
         self.batch.sweep(plan)
         self.batch.sync()
         self.epochs += 1
@@ -151,6 +164,7 @@ class Server:
                 job.finished = self.now()
                 self.batch.remove(rid)
                 self.held_bytes -= job.device_bytes
+                self.resident_cells -= job.L * job.L
                 del self.resident[rid]
                 self.finished.append(job)
                 finished += 1

@@ -35,6 +35,7 @@ def _solo(p, steps_list):
 def _same(o1, o2):
     for k in INT_KEYS:
         assert o1[k] == o2[k], k
+    assert list(o1["n_state"]) == list(o2["n_state"])
     for k in FP_KEYS:
         assert abs(o1[k] - o2[k]) <= 1e-12 * abs(o2[k]), k
 

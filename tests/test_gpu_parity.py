@@ -23,6 +23,7 @@ FP_KEYS = ("V_iso", "V", "U_LJ", "H")
 def assert_obs_equal(got, want, ctx=""):
     for k in INT_KEYS:
         assert got[k] == want[k], (ctx, k, got[k], want[k])
+    assert list(got["n_state"]) == list(want["n_state"]), (ctx, "n_state")
     for k in FP_KEYS:
         assert abs(got[k] - want[k]) <= FP_REL * max(abs(want[k]), 1e-300), (ctx, k, got[k], want[k])
 
@@ -91,6 +92,22 @@ def test_series_parity_record_every():
     assert len(r_gpu) == len(r_ref) == 20
     for a, b in zip(r_gpu, r_ref):
         assert_obs_equal(a, b)
+
+
+def test_order_parameter_series_matches_oracle():
+    """N_q' recorded every step by the sweep kernel, hence M(t) and C_M(dt)
+    (Eq. correlation), equal the oracle's."""
+    from paper_2505_05919_gb300 import analysis
+    op = oracle.physical_params(250.0, 0.1, L=32, seed=8)
+    _, o_gpu, r_gpu = gpu_run(op, 600, record_every=1)
+    _, o_ref, r_ref = oracle_run(op, 600, record_every=1)
+    assert [r["n_state"] for r in r_gpu] == [r["n_state"] for r in r_ref]
+    m_gpu = analysis.order_series(r_gpu, 32 * 32)
+    m_ref = analysis.order_series(r_ref, 32 * 32)
+    assert np.array_equal(m_gpu, m_ref)
+    c = analysis.autocorrelation(m_gpu[100:], 50)
+    assert c[0] == pytest.approx(1.0)
+    assert np.array_equal(c, analysis.autocorrelation(m_ref[100:], 50))
 
 
 @pytest.mark.parametrize("case", ["gas", "gate_flips", "hot", "cold", "no_lj"])

@@ -18,7 +18,7 @@ def _alone(job):
 def _check_same(job):
     s, o = _alone(job)
     assert np.array_equal(job.state, s), job.id
-    for k in ("sweep", "n_hb_raw", "n_coop", "acc_sigma", "acc_volume", "g"):
+    for k in ("sweep", "n_hb_raw", "n_coop", "acc_sigma", "acc_volume", "g", "n_state"):
         assert job.observables[k] == o[k], (job.id, k)
     for k in ("V_iso", "V", "U_LJ", "H"):
         assert abs(job.observables[k] - o[k]) <= 1e-12 * abs(o[k]), (job.id, k)

@@ -30,6 +30,7 @@ def _compare(got, want, counts_too=True):
         keys += ["acc_sigma", "acc_volume"]
     for k in keys:
         assert got[k] == want[k], (k, got[k], want[k])
+    assert list(got["n_state"]) == list(want["n_state"])
     for k in ("V_iso", "V", "U_LJ", "H"):
         assert abs(got[k] - want[k]) <= FP_REL * abs(want[k]), (k, got[k], want[k])
 
