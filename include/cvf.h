@@ -91,7 +91,8 @@ typedef struct cvf_obs {
   double U_LJ;        /* Lennard-Jones energy, eps */
   double H;           /* H = U_LJ - J N_HB - J_sigma N_sigma + P V (Eq. H) */
   int32_t g;          /* gate: 1 liquid-like (V_iso/N < 2 v0), 0 gas-like */
-  int32_t pad;
+  int32_t status;     /* 0; nonzero if a bounded device-side wait gave up
+                         (the call then returns CVF_ETIMEOUT) */
   int64_t n_state[8]; /* N_q': sigma variables in state q' (q' >= q: 0);
                          the order parameter is M = max N_q' / (4N),
                          Eq. (correlation) */
@@ -143,7 +144,9 @@ int cvf_create(const cvf_params *p, void *stream, void *dev_state,
  * CVF_EINVAL if n_sweeps < 0 or record_every < 0. */
 int cvf_sweep(cvf_handle *h, int64_t n_sweeps, int32_t record_every);
 
-/* Observables after the last completed step; synchronises the stream. */
+/* Observables after the last completed step; synchronises the stream.
+ * N_sigma and N_q' are counted from the lattice by this call.  Returns
+ * CVF_ETIMEOUT (with *out filled) if a bounded wait in a sweep gave up. */
 int cvf_observables(cvf_handle *h, cvf_obs *out);
 
 /* Moves the unread ring records (oldest first) into host[0..cap) and sets

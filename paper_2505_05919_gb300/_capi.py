@@ -46,11 +46,11 @@ class cvf_obs(ctypes.Structure):
                 ("acc_sigma", ctypes.c_int64), ("acc_volume", ctypes.c_int64),
                 ("V_iso", ctypes.c_double), ("V", ctypes.c_double),
                 ("U_LJ", ctypes.c_double), ("H", ctypes.c_double),
-                ("g", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("g", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("n_state", ctypes.c_int64 * 8)]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad", "n_state")}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "n_state"}
         d["n_state"] = list(self.n_state)
         return d
 

@@ -336,6 +336,8 @@ struct Ctrl {
   // observables go to the ring) and of the last recorded step
   unsigned long long acc_hist[8];
   long long hist[8];
+  unsigned int error;  // nonzero: a bounded device-side wait gave up
+  unsigned int pad1;
 };
 
 struct VolumeResult {
@@ -406,7 +408,7 @@ __device__ __forceinline__ cvf_obs make_obs(const VolumeArgs& V, const Ctrl* ctl
   o.U_LJ = U;
   o.H = H;
   o.g = ctl->g;
-  o.pad = 0;
+  o.status = (int32_t)ctl->error;
   for (int v = 0; v < 8; ++v) o.n_state[v] = ctl->hist[v];
   return o;
 }

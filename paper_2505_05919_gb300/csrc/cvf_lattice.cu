@@ -17,6 +17,8 @@
 #include "cvf_host.h"
 #include "cvf_lattice.cuh"
 #include "cvf_tile.cuh"
+#include "cvf_tma.cuh"
+#include <cudaTypedefs.h>
 
 using namespace cvf;
 
@@ -170,13 +172,21 @@ __global__ void __launch_bounds__(kThreads) k_histogram(const uint16_t* __restri
 // exactly one colour-1 end) and accepted moves are summed, block-reduced and
 // added with one atomic each; the last block closes the step.
 // ---------------------------------------------------------------------------
+// Bounded wait for a TMA stage (the copies complete in microseconds; the
+// limit only guards against a copy that never lands).
+constexpr uint32_t kTmaWaitLimit = 1u << 26;
+
 template <int RNG_WORDS, bool CMP64>
-__global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_sweep_tiled(LatticeArgs A) {
+__global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
+    k_sweep_tiled(LatticeArgs A, const __grid_constant__ CUtensorMap tm0,
+                  const __grid_constant__ CUtensorMap tm1) {
   using TT = typename ThresholdRow<CMP64>::type;
   __shared__ TileSmem<kTileRows, kTileWords> S;
   __shared__ ProposalTable P;
   __shared__ TT sT[24];
-  __shared__ int s_tile;
+  __shared__ int s_tile, s_next;
+  __shared__ uint32_t s_hist4[4];
+  __shared__ alignas(8) uint64_t s_bar;
   Ctrl* ctl = A.ctrl;
   const int g = ctl->next_g;
   const long long step = ctl->sweep;
@@ -213,21 +223,85 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_sweep_tiled(Lat
   v.s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
   v.s_hi = (uint32_t)((unsigned long long)step >> 32);
   v.keys.K = &A.keys;
+  const CUtensorMap* tmap = (step & 1) ? &tm1 : &tm0;  // map of the source buffer
   const int tiles_x = (v.Lh + kTileWords - 1) / kTileWords;
   const int ntiles = tiles_x * ((v.L + kTileRows - 1) / kTileRows);
-  TileCounts cnt{0, 0, 0, 0};
-  __shared__ uint32_t s_hist4[4];
   const bool rec = step_recorded(ctl->record_every, step);
+  TileCounts cnt{0, 0, 0, 0};
   if (threadIdx.x < 4) s_hist4[threadIdx.x] = 0;
-  for (;;) {
-    __syncthreads();  // previous tile fully consumed; tables visible
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&ctl->tile_next, 1u);
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    s_tile = (int)atomicAdd(&ctl->tile_next, 1u);
+  }
+  __syncthreads();
+
+  // Start the copy of tile t into S.in: one TMA box for tiles whose halo lies
+  // inside the lattice, 4-byte cp.async copies otherwise (periodic wrap).
+  // Returns whether the copy goes through the barrier.
+  auto stage = [&](int t) -> bool {
+    const TileGeom gm = tile_geom<kTileRows, kTileWords>(v.L, v.Lh, (t / tiles_x) * kTileRows,
+                                                         (t % tiles_x) * kTileWords);
+    const bool tma = A.use_tma && gm.th == kTileRows && gm.tw == kTileWords && gm.p0 >= 4 &&
+                     gm.p0 + kTileWords + 4 <= v.Lh && gm.y0 >= 2 &&
+                     gm.y0 + kTileRows + 2 <= v.L;
+    if (tma) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async_shared();
+        mbar_arrive_expect_tx(&s_bar, (uint32_t)sizeof(S.in));
+        tma_load_2d(&S.in[0][0], tmap, gm.p0 - 4, gm.y0 - 2, &s_bar);
+      }
+    } else {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int rr = warp; rr < gm.th + 4; rr += kThreads / 32) {
+        int y = gm.y0 + rr - 2;
+        y = (y < 0) ? y + v.L : (y >= v.L ? y - v.L : y);
+        const uint32_t* row = v.src + (size_t)y * v.Lh;
+        for (int jj = lane; jj < gm.tw + 2; jj += 32) {
+          int p = gm.p0 + jj - 1;
+          p = (p < 0) ? p + v.Lh : (p >= v.Lh ? p - v.Lh : p);
+          cp_async4(&S.in[rr][jj + kInColOff], row + p);
+        }
+      }
+      cp_async_commit();
+    }
+    return tma;
+  };
+
+  uint32_t parity = 0;
+  int t = s_tile;
+  bool t_tma = (t < ntiles) ? stage(t) : false;
+  while (t < ntiles) {
+    // wait for tile t's input
+    if (t_tma) {
+      uint32_t spins = 0;
+      while (!mbar_try_wait(&s_bar, parity)) {
+        if (++spins > kTmaWaitLimit) {
+          atomicOr(&ctl->error, 1u);
+          break;
+        }
+      }
+      parity ^= 1u;
+    } else {
+      cp_async_wait_all();
+    }
     __syncthreads();
-    const int t = s_tile;
-    if (t >= ntiles) break;
-    sweep_tile<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads>(
-        v, (t / tiles_x) * kTileRows, (t % tiles_x) * kTileWords, S, P, sT, cnt,
-        rec ? s_hist4 : nullptr, ctl->acc_hist);
+    const TileGeom gm = tile_geom<kTileRows, kTileWords>(v.L, v.Lh, (t / tiles_x) * kTileRows,
+                                                         (t % tiles_x) * kTileWords);
+    colour0<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads>(v, gm, S, P, sT, cnt,
+                                                               rec ? s_hist4 : nullptr);
+    if (threadIdx.x == 0) s_next = (int)atomicAdd(&ctl->tile_next, 1u);
+    __syncthreads();  // S.in is free: fetch the next tile while colour 1 runs
+    const int t2 = s_next;
+    const bool t2_tma = (t2 < ntiles) ? stage(t2) : false;
+    colour1<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads>(v, gm, S, P, sT, cnt,
+                                                               rec ? s_hist4 : nullptr);
+    if (rec) {
+      __syncthreads();
+      hist_flush(s_hist4, ctl->acc_hist);
+    }
+    __syncthreads();  // S.mid is free for the next tile
+    t = t2;
+    t_tma = t2_tma;
   }
   uint32_t pairs = cnt.pairs(), bonds = cnt.bonds, nacc = cnt.nacc;
   block_sum3<kThreads>(pairs, bonds, nacc);
@@ -384,6 +458,7 @@ struct cvf_handle {
   unsigned long long* rc_dev;
   void* host_pinned;
   LatticeArgs args;
+  CUtensorMap tm[2];  // TMA descriptors of the two halves of the state pair
   int grid_tiles, grid_cells;
   cudaGraphExec_t graph;
   int graph_steps;
@@ -420,13 +495,13 @@ void enqueue_step(cvf_handle* h, cudaStream_t s) {
   const bool one = h->p.rng_words == 1;
   if (h->p.schedule == CVF_SCHED_CHECKERBOARD) {
     if (one && !h->cmp64)
-      k_sweep_tiled<1, false><<<h->grid_tiles, kThreads, 0, s>>>(h->args);
+      k_sweep_tiled<1, false><<<h->grid_tiles, kThreads, 0, s>>>(h->args, h->tm[0], h->tm[1]);
     else if (one)
-      k_sweep_tiled<1, true><<<h->grid_tiles, kThreads, 0, s>>>(h->args);
+      k_sweep_tiled<1, true><<<h->grid_tiles, kThreads, 0, s>>>(h->args, h->tm[0], h->tm[1]);
     else if (!h->cmp64)
-      k_sweep_tiled<2, false><<<h->grid_tiles, kThreads, 0, s>>>(h->args);
+      k_sweep_tiled<2, false><<<h->grid_tiles, kThreads, 0, s>>>(h->args, h->tm[0], h->tm[1]);
     else
-      k_sweep_tiled<2, true><<<h->grid_tiles, kThreads, 0, s>>>(h->args);
+      k_sweep_tiled<2, true><<<h->grid_tiles, kThreads, 0, s>>>(h->args, h->tm[0], h->tm[1]);
   } else {
     for (int pass = 0; pass < 4; ++pass) {
       if (one)
@@ -441,6 +516,42 @@ void enqueue_step(cvf_handle* h, cudaStream_t s) {
 
 // The half of the state pair that holds the lattice after the enqueued steps.
 uint16_t* current(cvf_handle* h) { return h->state + (size_t)(h->sweep_host & 1) * h->N; }
+
+// TMA descriptors of the two lattice buffers (uint32 words, Lh x L, box of
+// kTileWords + 8 words x kTileRows + 4 rows).  Needs 16-byte aligned rows and
+// buffers (L a multiple of 8); returns false (cp.async staging only) when
+// that or the driver entry point is unavailable.
+bool encode_state_maps(uint16_t* state, int L, CUtensorMap tm[2]) {
+  std::memset(tm, 0, sizeof(CUtensorMap) * 2);
+  if (L % 8 != 0) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const long long N = (long long)L * L;
+  const cuuint64_t dims[2] = {(cuuint64_t)(L / 2), (cuuint64_t)L};
+  const cuuint64_t strides[1] = {(cuuint64_t)(L / 2) * 4};
+  const cuuint32_t box[2] = {kTileWords + 8, kTileRows + 4};
+  const cuuint32_t elem[2] = {1, 1};
+  for (int b = 0; b < 2; ++b) {
+    void* base = state + (size_t)b * N;
+    if (reinterpret_cast<uintptr_t>(base) & 15u) return false;
+    if (encode(&tm[b], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, base, dims, strides, box, elem,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
 
 // Persistent grid of the tiled sweep: as many blocks as fit on the GPU at
 // once, but no more than there are tiles.
@@ -554,6 +665,7 @@ int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** 
   h->args.L = p->L;
   h->args.q = (uint32_t)p->q;
   h->grid_tiles = tiled_grid(h->p.L, h->cmp64, h->p.rng_words);
+  h->args.use_tma = encode_state_maps(h->state, p->L, h->tm) ? 1 : 0;
   h->sweep_host = 0;
   h->grid_cells = grid_for(h->N, 8);
 
@@ -606,6 +718,9 @@ int cvf_observables(cvf_handle* h, cvf_obs* out) {
                                  cudaMemcpyDeviceToHost, h->stream));
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
   std::memcpy(out, h->host_pinned, sizeof(cvf_obs));
+  if (out->status)
+    return set_error(CVF_ETIMEOUT, "a bounded wait in the sweep kernel gave up (status %d)",
+                     out->status);
   return CVF_OK;
 }
 
@@ -866,15 +981,17 @@ extern "C" int cvf_sweep_noalloc(const cvf_params* p, void* dev_state, double V_
   k_volume_prologue<<<1, 32, 0, st>>>(&s->vol, &s->ctrl, A.keys);
   k_set_record<<<1, 32, 0, st>>>(&s->ctrl, record_every);
   const int grid = tiled_grid(p->L, cmp64, p->rng_words);
+  CUtensorMap no_map;  // this path stages every tile with cp.async
+  std::memset(&no_map, 0, sizeof(no_map));
   for (int64_t i = 0; i < n_sweeps; ++i) {
     if (p->rng_words == 1 && !cmp64)
-      k_sweep_tiled<1, false><<<grid, kThreads, 0, st>>>(A);
+      k_sweep_tiled<1, false><<<grid, kThreads, 0, st>>>(A, no_map, no_map);
     else if (p->rng_words == 1)
-      k_sweep_tiled<1, true><<<grid, kThreads, 0, st>>>(A);
+      k_sweep_tiled<1, true><<<grid, kThreads, 0, st>>>(A, no_map, no_map);
     else if (!cmp64)
-      k_sweep_tiled<2, false><<<grid, kThreads, 0, st>>>(A);
+      k_sweep_tiled<2, false><<<grid, kThreads, 0, st>>>(A, no_map, no_map);
     else
-      k_sweep_tiled<2, true><<<grid, kThreads, 0, st>>>(A);
+      k_sweep_tiled<2, true><<<grid, kThreads, 0, st>>>(A, no_map, no_map);
   }
   CVF_CUDA_CHECK(cudaMemsetAsync(s->hist, 0, sizeof(s->hist), st));
   k_histogram<<<grid_cells, kThreads, 0, st>>>(A.state + (size_t)((sweep + n_sweeps) & 1) * N, N,

@@ -24,6 +24,7 @@ struct LatticeArgs {
   RoundKeys keys;                    // Philox round keys of the seed
   int32_t L;
   uint32_t q;
+  int32_t use_tma;                   // 1: interior tiles are staged by TMA
 };
 
 // Kernels of cvf_lattice.cu that the batch reuses for initialisation and

@@ -168,10 +168,14 @@ __device__ __forceinline__ uint32_t update_in_word(
   return hi ? ((own & 0xFFFFu) | (wn << 16)) : ((own & 0xFFFF0000u) | wn);
 }
 
+// Staged input: rows y0-2 .. y0+TR+1 and words p0-4 .. p0+TW+3 (a 16-byte
+// aligned box, so one TMA copy can fill it); word p0-1+jj sits in column
+// jj+3.  After colour 0: rows y0-1 .. y0+TR, words p0-1 .. p0+TW.
+constexpr int kInColOff = 3;
 template <int TR, int TW>
 struct TileSmem {
-  uint32_t in[TR + 4][TW + 2];   // rows y0-2 .. y0+TR+1, words p0-1 .. p0+TW
-  uint32_t mid[TR + 2][TW + 2];  // after colour 0: rows y0-1 .. y0+TR
+  alignas(128) uint32_t in[TR + 4][TW + 8];
+  uint32_t mid[TR + 2][TW + 2];
 };
 
 // Per-thread counts of the cells a thread finished inside its tiles:
@@ -192,46 +196,55 @@ struct StepView {
   KEYS keys;
 };
 
-// Sweep the tile at rows y0.., words p0.. of one lattice.  Called by all
-// threads of the block; ends with the tile written to dst (no trailing
-// barrier: the caller synchronises before reusing the shared buffers).
-// s_hist4 != nullptr (recorded steps): N_q' of the tile's cells is added to
-// hist_out[0..8) through the block's four zeroed shared words, and the equal
-// pairs (N_sigma) are counted; on other steps neither is (N_HB_raw, which the
-// volume move needs, and the accepted moves are counted on every step).
-// CG: stage through L2 only (the source may have been written by other SMs
-// since this SM last cached it, without a kernel boundary in between).
-// A warp covers max(1, 32/TW) rows per pass, one lane per word.
-template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS, bool CG = false>
-__device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int p0,
-                                           TileSmem<TR, TW>& S, const ProposalTable& P,
-                                           const typename ThresholdRow<CMP64>::type* T,
-                                           TileCounts& cnt, uint32_t* s_hist4,
-                                           unsigned long long* hist_out) {
-  static_assert(TW >= 32 ? (TW % 32 == 0) : (32 % TW == 0), "tile width");
-  constexpr int kRows = (TW >= 32) ? 1 : 32 / TW;  // rows per warp pass
-  constexpr int kLanes = (TW >= 32) ? 32 : TW;     // lanes per row
+// Tile geometry shared by the pieces below.
+struct TileGeom {
+  int y0, p0, th, tw;
+};
+
+template <int TR, int TW>
+__device__ __forceinline__ TileGeom tile_geom(int L, int Lh, int y0, int p0) {
+  return TileGeom{y0, p0, min(TR, L - y0), min(TW, Lh - p0)};
+}
+
+// Stage rows y0-2 .. y0+th+1, words p0-1 .. p0+tw (periodic) with ordinary
+// loads (CG: through L2 only -- the source may have been written by other
+// SMs since this SM last cached it, without a kernel boundary in between).
+template <int TR, int TW, int NT, bool CG, typename KEYS>
+__device__ __forceinline__ void stage_plain(const StepView<KEYS>& v, const TileGeom& g,
+                                            TileSmem<TR, TW>& S) {
   const int L = v.L, Lh = v.Lh;
-  const int th = min(TR, L - y0);
-  const int tw = min(TW, Lh - p0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int lrow = lane / kLanes, lcol = lane % kLanes;
-  constexpr int kWarps = NT / 32;
-  // stage rows y0-2 .. y0+th+1, words p0-1 .. p0+tw (periodic)
-  for (int rr = warp; rr < th + 4; rr += kWarps) {
-    int y = y0 + rr - 2;
+  for (int rr = warp; rr < g.th + 4; rr += NT / 32) {
+    int y = g.y0 + rr - 2;
     y = (y < 0) ? y + L : (y >= L ? y - L : y);
     const uint32_t* row = v.src + (size_t)y * Lh;
-    for (int jj = lane; jj < tw + 2; jj += 32) {
-      int p = p0 + jj - 1;
+    for (int jj = lane; jj < g.tw + 2; jj += 32) {
+      int p = g.p0 + jj - 1;
       p = (p < 0) ? p + Lh : (p >= Lh ? p - Lh : p);
-      S.in[rr][jj] = CG ? __ldcg(row + p) : row[p];
+      S.in[rr][jj + kInColOff] = CG ? __ldcg(row + p) : row[p];
     }
   }
-  __syncthreads();
-  // colour 0: tile rows -1 .. th, words 0 .. tw-1 (the colour-0 cell of a
-  // word is its low half on even rows, its high half on odd rows)
-  for (int r0 = warp * kRows - 1; r0 <= th; r0 += kWarps * kRows) {
+}
+
+// Colour 0: tile rows -1 .. th, words 0 .. tw-1 (the colour-0 cell of a word
+// is its low half on even rows, its high half on odd rows), then the one
+// colour-0 cell per row just outside the tile (x0 - 1, high half of word -1,
+// on odd rows; x0 + 2 tw, low half of word tw, on even rows).  Reads S.in,
+// writes S.mid.  s_hist4 != nullptr (recorded steps): N_q' and the equal
+// pairs of the tile's cells are counted.
+template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS>
+__device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom& g,
+                                        TileSmem<TR, TW>& S, const ProposalTable& P,
+                                        const typename ThresholdRow<CMP64>::type* T,
+                                        TileCounts& cnt, uint32_t* s_hist4) {
+  constexpr int kRows = (TW >= 32) ? 1 : 32 / TW;  // rows per warp pass
+  constexpr int kLanes = (TW >= 32) ? 32 : TW;     // lanes per row
+  constexpr int C = kInColOff + 1;                 // column of word 0
+  const int L = v.L;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lrow = lane / kLanes, lcol = lane % kLanes;
+  const int th = g.th, tw = g.tw, y0 = g.y0, p0 = g.p0;
+  for (int r0 = warp * kRows - 1; r0 <= th; r0 += (NT / 32) * kRows) {
     const int r = r0 + lrow;
     if (r > th) continue;
     const int y = y0 + r;
@@ -242,17 +255,14 @@ __device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int 
       const int xg = 2 * (p0 + j) + hi;
       uint32_t dummy = 0, dummy_b = 0;
       const uint32_t out = update_in_word<RNG_WORDS, CMP64, false>(
-          S.in[r + 2][j + 1], S.in[r + 2][j], S.in[r + 2][j + 2], S.in[r + 1][j + 1],
-          S.in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), v.s_lo, v.s_hi, v.keys,
-          v.q, P, T, inside ? cnt.nacc : dummy, inside ? cnt.pair_sum : dummy, dummy_b,
-          inside ? s_hist4 : nullptr);
+          S.in[r + 2][j + C], S.in[r + 2][j + C - 1], S.in[r + 2][j + C + 1],
+          S.in[r + 1][j + C], S.in[r + 3][j + C], hi, (uint32_t)((long long)yg * L + xg),
+          v.s_lo, v.s_hi, v.keys, v.q, P, T, inside ? cnt.nacc : dummy,
+          inside ? cnt.pair_sum : dummy, dummy_b, inside ? s_hist4 : nullptr);
       if (inside) ++cnt.ncells;
       S.mid[r + 1][j + 1] = out;
     }
   }
-  // colour 0 on the ring: per row r the one colour-0 cell just outside the
-  // tile, x0 - 1 (high half of word -1) on odd rows, x0 + 2 tw (low half of
-  // word tw) on even rows
   for (int i = threadIdx.x; i < th + 2; i += NT) {
     const int r = i - 1;
     const int y = y0 + r;
@@ -265,13 +275,26 @@ __device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int 
     // the unused side of the ring word is clamped into the staged columns
     const int jm = max(j, 0), jp = min(j + 2, tw + 1);
     S.mid[r + 1][j + 1] = update_in_word<RNG_WORDS, CMP64, false>(
-        S.in[r + 2][j + 1], S.in[r + 2][jm], S.in[r + 2][jp], S.in[r + 1][j + 1],
-        S.in[r + 3][j + 1], hi, (uint32_t)((long long)yg * L + xg), v.s_lo, v.s_hi, v.keys, v.q,
-        P, T, d0, d1, d2, nullptr);
+        S.in[r + 2][j + C], S.in[r + 2][jm + kInColOff], S.in[r + 2][jp + kInColOff],
+        S.in[r + 1][j + C], S.in[r + 3][j + C], hi, (uint32_t)((long long)yg * L + xg), v.s_lo,
+        v.s_hi, v.keys, v.q, P, T, d0, d1, d2, nullptr);
   }
-  __syncthreads();
-  // colour 1: tile rows 0 .. th-1 (low half on odd rows, high on even rows)
-  for (int r0 = warp * kRows; r0 < th; r0 += kWarps * kRows) {
+}
+
+// Colour 1: tile rows 0 .. th-1 (low half on odd rows, high on even rows),
+// from S.mid to the destination buffer.
+template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS>
+__device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom& g,
+                                        TileSmem<TR, TW>& S, const ProposalTable& P,
+                                        const typename ThresholdRow<CMP64>::type* T,
+                                        TileCounts& cnt, uint32_t* s_hist4) {
+  constexpr int kRows = (TW >= 32) ? 1 : 32 / TW;
+  constexpr int kLanes = (TW >= 32) ? 32 : TW;
+  const int L = v.L, Lh = v.Lh;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lrow = lane / kLanes, lcol = lane % kLanes;
+  const int th = g.th, tw = g.tw, y0 = g.y0, p0 = g.p0;
+  for (int r0 = warp * kRows; r0 < th; r0 += (NT / 32) * kRows) {
     const int r = r0 + lrow;
     if (r >= th) continue;
     const int y = y0 + r;
@@ -286,6 +309,29 @@ __device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int 
       ++cnt.ncells;
     }
   }
+}
+
+// Sweep the tile at rows y0.., words p0.. of one lattice with synchronous
+// staging.  Called by all threads of the block; ends with the tile written
+// to dst (no trailing barrier: the caller synchronises before reusing the
+// shared buffers).  s_hist4 != nullptr (recorded steps): N_q' of the tile's
+// cells is added to hist_out[0..8) through the block's four zeroed shared
+// words, and the equal pairs (N_sigma) are counted; on other steps neither
+// is (N_HB_raw, which the volume move needs, and the accepted moves are
+// counted on every step).  A warp covers max(1, 32/TW) rows per pass.
+template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS, bool CG = false>
+__device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int p0,
+                                           TileSmem<TR, TW>& S, const ProposalTable& P,
+                                           const typename ThresholdRow<CMP64>::type* T,
+                                           TileCounts& cnt, uint32_t* s_hist4,
+                                           unsigned long long* hist_out) {
+  static_assert(TW >= 32 ? (TW % 32 == 0) : (32 % TW == 0), "tile width");
+  const TileGeom g = tile_geom<TR, TW>(v.L, v.Lh, y0, p0);
+  stage_plain<TR, TW, NT, CG>(v, g, S);
+  __syncthreads();
+  colour0<RNG_WORDS, CMP64, TR, TW, NT>(v, g, S, P, T, cnt, s_hist4);
+  __syncthreads();
+  colour1<RNG_WORDS, CMP64, TR, TW, NT>(v, g, S, P, T, cnt, s_hist4);
   if (s_hist4) {  // block-uniform: only on recorded steps
     __syncthreads();
     hist_flush(s_hist4, hist_out);
