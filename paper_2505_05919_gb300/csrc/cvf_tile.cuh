@@ -263,7 +263,11 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
       S.mid[r + 1][j + 1] = out;
     }
   }
-  for (int i = threadIdx.x; i < th + 2; i += NT) {
+  // the ring goes to the warps after the first two, which take one row of
+  // the th + 2 fewer than warps 0 and 1 when 8 warps share 66 rows
+  const int ring0 = (NT >= 128 && TW >= 32) ? 64 : 0;
+  for (int i = (int)threadIdx.x - ring0; i < th + 2; i += NT) {
+    if (i < 0) continue;
     const int r = i - 1;
     const int y = y0 + r;
     const int hi = y & 1;
