@@ -1,11 +1,12 @@
-"""CPU oracle of the CVF 2D Metropolis hot path -- TEST INFRASTRUCTURE.
+"""CPU oracle of the CVF Metropolis hot path (2D and 3D) -- TEST INFRASTRUCTURE.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
 (``cpu_baseline`` and ``--impl reference``) may import this package.  The
 product library (``paper_2505_05919_gb300``) never does; the two share no code.
 
-The arithmetic lives in ``cvf_oracle.c`` (plain single-threaded C); this module
-only builds it with gcc and marshals arguments through ctypes.
+The arithmetic lives in ``cvf_oracle.c`` (2D) and ``cvf_oracle3.c`` (the 3D
+cubic-lattice variant), plain single-threaded C; this module only builds them
+with gcc and marshals arguments through ctypes.
 """
 from __future__ import annotations
 
@@ -19,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cvf_oracle.c")
+_SRC3 = os.path.join(_HERE, "cvf_oracle3.c")
 _LIB = os.path.join(_HERE, "libcvf_oracle.so")
 
 INIT_RANDOM, INIT_ORDERED = 0, 1
@@ -28,12 +30,12 @@ SCHED_CHECKERBOARD, SCHED_LAYERED = 0, 1
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC3),
                                               os.path.getmtime(os.path.join(_HERE, "cvf_oracle.h")))):
         return _LIB
     tmp = _LIB + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+           "-fPIC", "-shared", "-o", tmp, _SRC, _SRC3, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -75,6 +77,16 @@ class State(ctypes.Structure):
                 ("pad", ctypes.c_int32), ("table", ctypes.c_uint64 * 42)]
 
 
+class State3(ctypes.Structure):
+    _fields_ = [("p", Params), ("N", ctypes.c_int64),
+                ("w", ctypes.POINTER(ctypes.c_uint32)),
+                ("V_iso", ctypes.c_double), ("dV_max", ctypes.c_double),
+                ("sweep", ctypes.c_int64), ("n_hb_raw", ctypes.c_int64),
+                ("n_coop", ctypes.c_int64), ("acc_sigma", ctypes.c_int64),
+                ("acc_volume", ctypes.c_int64), ("g", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("table", ctypes.c_uint64 * 66)]
+
+
 _lib = None
 
 
@@ -109,6 +121,25 @@ def lib():
                                       ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, i32p]),
             "orc_volume_chain": (ctypes.c_int64, [P(Params), ctypes.c_double, ctypes.c_int64,
                                                   ctypes.c_int64, dp, i32p, i64p]),
+            # 3D variant
+            "orc3_neighbour": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int]),
+            "orc3_shell_table": (ctypes.c_int, [ctypes.c_double, i64p, i64p, ctypes.c_int]),
+            "orc3_lj_cell_energy": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+            "orc3_threshold_table": (None, [P(Params), u64p]),
+            "orc3_recount": (None, [P(Params), u32p, i64p, i64p]),
+            "orc3_check_params": (ctypes.c_int, [P(Params)]),
+            "orc3_init": (ctypes.c_int, [P(State3), P(Params), u32p]),
+            "orc3_set": (ctypes.c_int, [P(State3), P(Params), u32p, ctypes.c_double, ctypes.c_int64]),
+            "orc3_volume_move": (None, [P(State3)]),
+            "orc3_permutation": (None, [ctypes.c_int, P(ctypes.c_int)]),
+            "orc3_layer_order": (None, [P(Params), ctypes.c_int64, P(ctypes.c_int)]),
+            "orc3_step": (None, [P(State3)]),
+            "orc3_observables": (None, [P(State3), P(Obs)]),
+            "orc3_run": (ctypes.c_int64, [P(State3), ctypes.c_int64, ctypes.c_int32, P(Obs), ctypes.c_int64]),
+            "orc3_arm_probe": (None, [P(Params), u32p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
+                                      ctypes.c_int32, u32p, u64p]),
+            "orc3_volume_chain": (ctypes.c_int64, [P(Params), ctypes.c_double, ctypes.c_int64,
+                                                   ctypes.c_int64, ctypes.c_int64, dp]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -286,3 +317,126 @@ class Oracle:
 
     def recount(self):
         return recount(self.p, self.w)
+
+
+# --------------------------------------------------------------------------
+# 3D variant: cubic lattice, six arms per cell, layered schedule
+# --------------------------------------------------------------------------
+def params3(**kw) -> OracleParams:
+    """3D defaults: v_iso0 = sqrt(2) (the pair minimum r = 2^(1/6) r0 with
+    v = r^3), the layered schedule and one random word per update."""
+    base = dict(L=16, v_iso_init=math.sqrt(2.0), schedule=SCHED_LAYERED, rng_words=1)
+    base.update(kw)
+    return OracleParams(**base)
+
+
+def physical_params3(T_kelvin: float, P_MPa: float, **kw) -> OracleParams:
+    p = physical_params(T_kelvin, P_MPa)
+    return params3(kT=p.kT, P=p.P, **kw)
+
+
+def neighbour3(L: int, cell: int, arm: int) -> int:
+    return lib().orc3_neighbour(L, cell, arm)
+
+
+def shell_table3(cutoff: float = 6.0):
+    d2 = np.zeros(4096, np.int64)
+    m = np.zeros(4096, np.int64)
+    n = lib().orc3_shell_table(cutoff, _ptr(d2, ctypes.c_int64), _ptr(m, ctypes.c_int64), 4096)
+    return d2[:n].copy(), m[:n].copy()
+
+
+def lj_cell_energy3(v_iso: float, epsilon: float = 1.0, cutoff: float = 6.0) -> float:
+    return lib().orc3_lj_cell_energy(v_iso, epsilon, cutoff)
+
+
+def threshold_table3(p: OracleParams) -> np.ndarray:
+    out = np.zeros(66, np.uint64)
+    cp = p.c()
+    lib().orc3_threshold_table(ctypes.byref(cp), _ptr(out, ctypes.c_uint64))
+    return out.reshape(2, 3, 11)
+
+
+def recount3(p: OracleParams, w: np.ndarray):
+    a = np.ascontiguousarray(w, dtype=np.uint32).reshape(-1)
+    hb, co = ctypes.c_int64(), ctypes.c_int64()
+    cp = p.c()
+    lib().orc3_recount(ctypes.byref(cp), _ptr(a, ctypes.c_uint32), ctypes.byref(hb), ctypes.byref(co))
+    return hb.value, co.value
+
+
+def permutation3(idx: int):
+    out = (ctypes.c_int * 6)()
+    lib().orc3_permutation(idx, out)
+    return list(out)
+
+
+def layer_order3(p: OracleParams, step: int):
+    out = (ctypes.c_int * 6)()
+    cp = p.c()
+    lib().orc3_layer_order(ctypes.byref(cp), step, out)
+    return list(out)
+
+
+def arm_probe3(p: OracleParams, w: np.ndarray, cell: int, arm: int, k: int, g: int):
+    a = np.ascontiguousarray(w, dtype=np.uint32).reshape(-1)
+    s_new, T = ctypes.c_uint32(), ctypes.c_uint64()
+    cp = p.c()
+    lib().orc3_arm_probe(ctypes.byref(cp), _ptr(a, ctypes.c_uint32), cell, arm, k, g,
+                         ctypes.byref(s_new), ctypes.byref(T))
+    return s_new.value, T.value
+
+
+def volume_chain3(p: OracleParams, V_iso: float, n_hb_raw: int, step0: int, K: int):
+    V = np.zeros(K, np.float64)
+    cp = p.c()
+    acc = lib().orc3_volume_chain(ctypes.byref(cp), V_iso, n_hb_raw, step0, K,
+                                  _ptr(V, ctypes.c_double))
+    return V, acc
+
+
+class Oracle3:
+    """One cubic lattice advanced by the 3D oracle, step by step."""
+
+    def __init__(self, p: OracleParams, state: np.ndarray | None = None,
+                 V_iso: float | None = None, sweep: int = 0):
+        self.p = p
+        self._cp = p.c()
+        self.N = p.L ** 3
+        self.w = np.zeros(self.N, np.uint32)
+        self.st = State3()
+        if state is None:
+            rc = lib().orc3_init(ctypes.byref(self.st), ctypes.byref(self._cp),
+                                 _ptr(self.w, ctypes.c_uint32))
+        else:
+            self.w[:] = np.asarray(state, dtype=np.uint32).reshape(-1)
+            if V_iso is None:
+                V_iso = self.N * p.v_iso_init
+            rc = lib().orc3_set(ctypes.byref(self.st), ctypes.byref(self._cp),
+                                _ptr(self.w, ctypes.c_uint32), V_iso, sweep)
+        if rc != 0:
+            raise ValueError("oracle rejected the parameters (code %d)" % rc)
+
+    def step(self) -> None:
+        lib().orc3_step(ctypes.byref(self.st))
+
+    def run(self, n: int, record_every: int = 0) -> list:
+        cap = (n // record_every + 1) if record_every > 0 else 0
+        ring = (Obs * max(cap, 1))()
+        k = lib().orc3_run(ctypes.byref(self.st), n, record_every, ring, cap)
+        return [ring[i].as_dict() for i in range(k)]
+
+    def volume_move(self) -> None:
+        lib().orc3_volume_move(ctypes.byref(self.st))
+
+    def observables(self) -> dict:
+        o = Obs()
+        lib().orc3_observables(ctypes.byref(self.st), ctypes.byref(o))
+        return o.as_dict()
+
+    def state(self) -> np.ndarray:
+        L = self.p.L
+        return self.w.reshape(L, L, L).copy()
+
+    def recount(self):
+        return recount3(self.p, self.w)

@@ -83,4 +83,37 @@ void orc_window_run(const orc_params *p, uint16_t *w, int32_t x0, int32_t y0,
 int64_t orc_volume_chain(const orc_params *p, double V_iso, int64_t step0,
                          int64_t K, double *V_out, int32_t *g_out,
                          int64_t *acc_out);
+/* ---- 3D variant (cvf_oracle3.c): cubic lattice, six arms per cell packed
+   3 bits each in one uint32 word, layered schedule. ---- */
+typedef struct {
+  orc_params p;
+  int64_t N;
+  uint32_t *w;
+  double V_iso, dV_max;
+  int64_t sweep, n_hb_raw, n_coop, acc_sigma, acc_volume;
+  int32_t g, pad;
+  uint64_t table[2][3][11];
+} orc3_state;
+
+int64_t orc3_neighbour(int32_t L, int64_t c, int arm);
+int orc3_shell_table(double cutoff, int64_t *d2s, int64_t *mult, int cap);
+double orc3_lj_cell_energy(double v_iso, double epsilon, double cutoff);
+void orc3_threshold_table(const orc_params *p, uint64_t out[2][3][11]);
+void orc3_recount(const orc_params *p, const uint32_t *w, int64_t *n_hb_raw,
+                  int64_t *n_coop);
+int orc3_check_params(const orc_params *p);
+int orc3_init(orc3_state *st, const orc_params *p, uint32_t *w);
+int orc3_set(orc3_state *st, const orc_params *p, uint32_t *w, double V_iso,
+             int64_t sweep);
+void orc3_volume_move(orc3_state *st);
+void orc3_permutation(int idx, int order[6]);
+void orc3_layer_order(const orc_params *p, int64_t step, int order[6]);
+void orc3_step(orc3_state *st);
+void orc3_observables(const orc3_state *st, orc_obs *o);
+int64_t orc3_run(orc3_state *st, int64_t n, int32_t record_every, orc_obs *ring,
+                 int64_t cap);
+void orc3_arm_probe(const orc_params *p, const uint32_t *w, int64_t c, int a,
+                    uint32_t k, int32_t g, uint32_t *s_new, uint64_t *T);
+int64_t orc3_volume_chain(const orc_params *p, double V_iso, int64_t n_hb_raw,
+                          int64_t step0, int64_t K, double *V_out);
 #endif

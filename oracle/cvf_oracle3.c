@@ -1,0 +1,386 @@
+/*
+ * cvf_oracle3.c -- plain CPU oracle of the paper's own 3D CVF Metropolis
+ * (arXiv:2505.05919, Sec. II): a periodic cubic lattice of N = L^3 cells,
+ * six bonding indices per cell, the layered partition of Sec. II.C (the six
+ * arm domains updated one after the other, in an order drawn every MC step),
+ * Eq. (H) with up to C(6,2) = 15 cooperative pairs per cell, and the isobaric
+ * volume move of Sec. II.B with the Lennard-Jones sum of the cubic lattice.
+ *
+ * TEST INFRASTRUCTURE, like cvf_oracle.c: only tests/, smoke() and the CPU
+ * legs of bench.py use it; it shares no code with the CUDA library.  Every
+ * step is written in the order of the paper, one variable at a time.
+ *
+ * Readings (besides the 2D oracle's, which carry over):
+ *   - cell c = x + L (y + L z) and arms 0..5 = left, right, front, back,
+ *     top, bottom (Sec. II.C; the cell coordinates of Table S1).  The
+ *     coalescing example of Sec. II.C (left arms of cells 0..15 meet the
+ *     right arms of cells 1..16) puts arm 0 at +x, and Table S1's covalent
+ *     pair (257, 337) joins the top arm of cell (1,0,0) with the bottom arm
+ *     of cell (1,0,1), so arm 4 points to +z; arm 2 points to +y by the same
+ *     pattern (the paper prints no y example), and arm a ^ 1 is the
+ *     opposite of arm a;
+ *   - eta_ij = 1 for every pair: the checkerboard-cube eta update of App. A
+ *     is not built (its allowed cube configurations are given only in a
+ *     figure), so up to six bonds per molecule are possible here;
+ *   - one MC step: volume move, then six passes, pass i updating arm
+ *     order[i] of every cell; order is permutation number
+ *     floor(w 720 / 2^32) of the six arms in lexicographic order, w word 0
+ *     of Philox((2^32-2, step, 4));
+ *   - random numbers: the draw of arm a of cell c in step s is word c mod 4
+ *     of Philox((floor(c / 4), s, 8 + a)); w (q-1) = k 2^32 + u gives the
+ *     proposal offset k and the acceptance draw u; the random initial state
+ *     is sigma_a(c) = floor(w q / 2^32), w word c mod 4 of
+ *     Philox((floor(c / 4), 0, 16 + a));
+ *   - Lennard-Jones: r = v_iso^(1/3) (Sec. II.A); a lattice vector d lies
+ *     inside the 6 r0 cutoff iff |d|^6 v^2 < 6^6; per cell
+ *     u(v) = 2 eps [v^-4 S12(n) - v^-2 S6(n)] with S12, S6 the sums of
+ *     m / |d|^12 and m / |d|^6 over the first n shells;
+ *   - the gate is liquid iff v_iso < 2 (Sec. II.A, gas-like when
+ *     v_iso >= 2 v0).
+ * Compile: gcc -O2 -std=c11 -ffp-contract=off (with cvf_oracle.c).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "cvf_oracle.h"
+
+static uint32_t o3_arm(uint32_t w, int a) { return (w >> (3 * a)) & 7u; }
+
+static void o3_philox(const orc_params *p, uint32_t word0, int64_t step, uint32_t tag,
+                      uint32_t out[4]) {
+  uint32_t ctr[4] = {word0, (uint32_t)((uint64_t)step & 0xFFFFFFFFu),
+                     (uint32_t)((uint64_t)step >> 32), tag};
+  uint32_t key[2] = {(uint32_t)(p->seed & 0xFFFFFFFFu), (uint32_t)(p->seed >> 32)};
+  orc_philox4x32_10(ctr, key, out);
+}
+
+static uint32_t o3_scale(uint32_t w, uint32_t n) {
+  return (uint32_t)(((uint64_t)w * (uint64_t)n) >> 32);
+}
+
+/* The random word of (cell c, tag) in step `step`: word c mod 4 of the
+   Philox block of counter (c / 4, step, tag). */
+static uint32_t o3_word(const orc_params *p, int64_t c, int64_t step, uint32_t tag) {
+  uint32_t r[4];
+  o3_philox(p, (uint32_t)(c / 4), step, tag, r);
+  return r[c % 4];
+}
+
+int64_t orc3_neighbour(int32_t L, int64_t c, int arm) {
+  int64_t x = c % L, y = (c / L) % L, z = c / ((int64_t)L * L);
+  switch (arm) {
+    case 0: x = (x + 1) % L; break;
+    case 1: x = (x + L - 1) % L; break;
+    case 2: y = (y + 1) % L; break;
+    case 3: y = (y + L - 1) % L; break;
+    case 4: z = (z + 1) % L; break;
+    default: z = (z + L - 1) % L; break;
+  }
+  return (z * L + y) * L + x;
+}
+
+/* ---------------------------------------------------------------- LJ 3D --- */
+/* Shells of the cubic lattice inside the cutoff at the hard-core density:
+   squared lengths |d|^2 < cutoff^2 (ascending) and their multiplicities,
+   counted by brute force over a cube of lattice vectors. */
+int orc3_shell_table(double cutoff, int64_t *d2s, int64_t *mult, int cap) {
+  int R = (int)ceil(cutoff) + 1;
+  int64_t maxd2 = (int64_t)(cutoff * cutoff) + 1;
+  int n = 0;
+  for (int64_t d2 = 1; d2 <= maxd2; ++d2) {
+    if (!((double)d2 < cutoff * cutoff)) continue;
+    int64_t m = 0;
+    for (int i = -R; i <= R; ++i)
+      for (int j = -R; j <= R; ++j)
+        for (int k = -R; k <= R; ++k)
+          if ((int64_t)i * i + (int64_t)j * j + (int64_t)k * k == d2) ++m;
+    if (m > 0) {
+      if (n >= cap) return -1;
+      d2s[n] = d2;
+      mult[n] = m;
+      ++n;
+    }
+  }
+  return n;
+}
+
+#define O3_MAX_SHELLS 1024
+double orc3_lj_cell_energy(double v_iso, double epsilon, double cutoff) {
+  static int64_t d2s[O3_MAX_SHELLS], mult[O3_MAX_SHELLS];
+  static double S12[O3_MAX_SHELLS + 1], S6[O3_MAX_SHELLS + 1];
+  static double last_cutoff = -1.0;
+  static int n = 0;
+  if (cutoff != last_cutoff) {
+    n = orc3_shell_table(cutoff, d2s, mult, O3_MAX_SHELLS);
+    if (n < 0) n = 0;
+    S12[0] = 0.0;
+    S6[0] = 0.0;
+    for (int s = 0; s < n; ++s) {
+      int64_t d6 = d2s[s] * d2s[s] * d2s[s];
+      S12[s + 1] = S12[s] + (double)mult[s] / ((double)d6 * (double)d6);
+      S6[s + 1] = S6[s] + (double)mult[s] / (double)d6;
+    }
+    last_cutoff = cutoff;
+  }
+  double rc6 = cutoff * cutoff * cutoff * cutoff * cutoff * cutoff;
+  int k = 0;
+  while (k < n && (double)(d2s[k] * d2s[k] * d2s[k]) * v_iso * v_iso < rc6) ++k;
+  double x = 1.0 / v_iso;
+  double x2 = x * x;
+  double x4 = x2 * x2;
+  return (2.0 * epsilon) * (x4 * S12[k] - x2 * S6[k]);
+}
+
+/* ------------------------------------------------------------ thresholds -- */
+/* [g][dN_HB + 1][dN_sigma + 5]: dN_sigma in -5..5 (five other arms). */
+void orc3_threshold_table(const orc_params *p, uint64_t out[2][3][11]) {
+  double J_eff = p->J - p->P * p->v_HB;
+  for (int g = 0; g < 2; ++g)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 11; ++j) {
+        int dhb = i - 1, dc = j - 5;
+        double dH = -((double)g * J_eff) * (double)dhb - p->J_sigma * (double)dc;
+        out[g][i][j] = (dH <= 0.0) ? ((uint64_t)1 << 32)
+                                   : (uint64_t)(exp(-dH / p->kT) * 4294967296.0);
+      }
+}
+
+/* ----------------------------------------------------------------- state -- */
+/* Full count: bonds between arm a of c and arm a^1 of its neighbour (each
+   bond once, from its +axis end) and the equal pairs among a cell's six
+   arms. */
+void orc3_recount(const orc_params *p, const uint32_t *w, int64_t *n_hb_raw,
+                  int64_t *n_coop) {
+  int64_t N = (int64_t)p->L * p->L * p->L, hb = 0, co = 0;
+  for (int64_t c = 0; c < N; ++c) {
+    uint32_t wc = w[c];
+    for (int a = 0; a < 6; a += 2)
+      if (o3_arm(wc, a) == o3_arm(w[orc3_neighbour(p->L, c, a)], a + 1)) ++hb;
+    for (int a = 0; a < 6; ++a)
+      for (int b = a + 1; b < 6; ++b)
+        if (o3_arm(wc, a) == o3_arm(wc, b)) ++co;
+  }
+  *n_hb_raw = hb;
+  *n_coop = co;
+}
+
+int orc3_check_params(const orc_params *p) {
+  if (p->L < 2 || p->L > 1024) return ORC_EINVAL;
+  if (p->q < 2 || p->q > 8) return ORC_EINVAL;
+  if (!(p->kT > 0.0) || !(p->v_iso_init >= 1.0) || !(p->dv_max_frac >= 0.0))
+    return ORC_EINVAL;
+  if (p->init != ORC_INIT_RANDOM && p->init != ORC_INIT_ORDERED) return ORC_EINVAL;
+  if (p->schedule != ORC_SCHED_LAYERED || p->rng_words != 1) return ORC_EINVAL;
+  return ORC_OK;
+}
+
+static void o3_start(orc3_state *st, const orc_params *p, uint32_t *w, double V_iso,
+                     int64_t sweep) {
+  memset(st, 0, sizeof(*st));
+  st->p = *p;
+  st->N = (int64_t)p->L * p->L * p->L;
+  st->w = w;
+  st->V_iso = V_iso;
+  st->g = (V_iso / (double)st->N < 2.0) ? 1 : 0;
+  st->dV_max = p->dv_max_frac * ((double)st->N * p->v_iso_init);
+  st->sweep = sweep;
+  orc3_threshold_table(p, st->table);
+  orc3_recount(p, w, &st->n_hb_raw, &st->n_coop);
+}
+
+int orc3_init(orc3_state *st, const orc_params *p, uint32_t *w) {
+  int rc = orc3_check_params(p);
+  if (rc) return rc;
+  int64_t N = (int64_t)p->L * p->L * p->L;
+  for (int64_t c = 0; c < N; ++c) {
+    uint32_t word = 0;
+    if (p->init == ORC_INIT_RANDOM)
+      for (int a = 0; a < 6; ++a)
+        word |= o3_scale(o3_word(p, c, 0, 16u + (uint32_t)a), (uint32_t)p->q) << (3 * a);
+    w[c] = word;
+  }
+  o3_start(st, p, w, (double)N * p->v_iso_init, 0);
+  return ORC_OK;
+}
+
+int orc3_set(orc3_state *st, const orc_params *p, uint32_t *w, double V_iso, int64_t sweep) {
+  int rc = orc3_check_params(p);
+  if (rc) return rc;
+  o3_start(st, p, w, V_iso, sweep);
+  return ORC_OK;
+}
+
+/* Volume move (Sec. II.B step 1) with the 2D oracle's readings and the 3D
+   cell energy: dV = (2 u1 - 1) dV_max; hard core v' < 1 rejected; gate
+   g' = [v' < 2]; dH = N (u(v') - u(v)) + P dV - (g' - g) J_eff N_HB_raw;
+   accepted iff u2 < exp(-dH / kT + N ln(V'/V)). */
+static double o3_u53(uint32_t hi, uint32_t lo) {
+  uint64_t m = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+  return (double)m * (1.0 / 9007199254740992.0);
+}
+
+void orc3_volume_move(orc3_state *st) {
+  const orc_params *p = &st->p;
+  uint32_t r[4];
+  o3_philox(p, ORC_CELL_VOLUME, st->sweep, ORC_TAG_VOLUME, r);
+  double u1 = o3_u53(r[0], r[1]);
+  double u2 = o3_u53(r[2], r[3]);
+  double Nd = (double)st->N;
+  double dV = (2.0 * u1 - 1.0) * st->dV_max;
+  double V_old = st->V_iso;
+  double V_new = V_old + dV;
+  double v_old = V_old / Nd;
+  double v_new = V_new / Nd;
+  if (v_new < 1.0) return;
+  int32_t g_new = (v_new < 2.0) ? 1 : 0;
+  double J_eff = p->J - p->P * p->v_HB;
+  double du = orc3_lj_cell_energy(v_new, p->epsilon, p->cutoff) -
+              orc3_lj_cell_energy(v_old, p->epsilon, p->cutoff);
+  double t1 = Nd * du;
+  double t2 = p->P * dV;
+  double t3 = ((double)(g_new - st->g) * J_eff) * (double)st->n_hb_raw;
+  double dH = (t1 + t2) - t3;
+  double arg = -dH / p->kT + Nd * log(V_new / V_old);
+  if (u2 < exp(arg)) {
+    st->V_iso = V_new;
+    st->g = g_new;
+    st->acc_volume += 1;
+  }
+}
+
+/* Permutation number idx (0..719) of the six arms in lexicographic order,
+   decoded digit by digit in the factorial number system. */
+void orc3_permutation(int idx, int order[6]) {
+  int avail[6] = {0, 1, 2, 3, 4, 5};
+  int n = 6;
+  int fact = 120;
+  for (int i = 0; i < 6; ++i) {
+    int j = idx / fact;
+    idx = idx % fact;
+    order[i] = avail[j];
+    for (int t = j; t < n - 1; ++t) avail[t] = avail[t + 1];
+    --n;
+    if (n > 0) fact /= n;
+  }
+}
+
+void orc3_layer_order(const orc_params *p, int64_t step, int order[6]) {
+  uint32_t r[4];
+  o3_philox(p, ORC_CELL_LAYERS, step, ORC_TAG_LAYERS, r);
+  orc3_permutation((int)o3_scale(r[0], 720u), order);
+}
+
+/* Metropolis update of arm a of cell c (Sec. II.C): the proposal is one of
+   the q-1 other states; dN_HB compares with arm a^1 of the neighbour in
+   direction a, dN_sigma with the five other arms of the cell (Eq. H). */
+static void o3_update_arm(orc3_state *st, int64_t c, int a) {
+  const orc_params *p = &st->p;
+  uint32_t w = o3_word(p, c, st->sweep, 8u + (uint32_t)a);
+  uint64_t prod = (uint64_t)w * (uint64_t)(p->q - 1);
+  uint32_t k = (uint32_t)(prod >> 32), u = (uint32_t)prod;
+  uint32_t wc = st->w[c];
+  uint32_t s = o3_arm(wc, a);
+  uint32_t sp = (s + 1u + k) % (uint32_t)p->q;
+  uint32_t nb = o3_arm(st->w[orc3_neighbour(p->L, c, a)], a ^ 1);
+  int dhb = (sp == nb) - (s == nb);
+  int dc = 0;
+  for (int b = 0; b < 6; ++b) {
+    if (b == a) continue;
+    uint32_t sb = o3_arm(wc, b);
+    dc += (sp == sb) - (s == sb);
+  }
+  if ((uint64_t)u < st->table[st->g][dhb + 1][dc + 5]) {
+    st->w[c] = (wc & ~(7u << (3 * a))) | (sp << (3 * a));
+    st->n_hb_raw += dhb;
+    st->n_coop += dc;
+    st->acc_sigma += 1;
+  }
+}
+
+/* One MC step (Sec. II.B): V_iso, then eta (fixed at 1 here), then sigma by
+   six passes over the arm domains in the drawn order. */
+void orc3_step(orc3_state *st) {
+  if (st->p.volume_moves) orc3_volume_move(st);
+  int order[6];
+  orc3_layer_order(&st->p, st->sweep, order);
+  for (int pass = 0; pass < 6; ++pass)
+    for (int64_t c = 0; c < st->N; ++c) o3_update_arm(st, c, order[pass]);
+  st->sweep += 1;
+}
+
+/* Observables (Eq. V, Eq. H) and N_q' over all 6N variables. */
+void orc3_observables(const orc3_state *st, orc_obs *o) {
+  const orc_params *p = &st->p;
+  double Nd = (double)st->N;
+  int64_t nhb = st->g ? st->n_hb_raw : 0;
+  double U = Nd * orc3_lj_cell_energy(st->V_iso / Nd, p->epsilon, p->cutoff);
+  double V = st->V_iso + p->v_HB * (double)nhb;
+  double H = ((U - p->J * (double)nhb) - p->J_sigma * (double)st->n_coop) + p->P * V;
+  memset(o, 0, sizeof(*o));
+  o->sweep = st->sweep;
+  o->n_hb = nhb;
+  o->n_hb_raw = st->n_hb_raw;
+  o->n_coop = st->n_coop;
+  o->acc_sigma = st->acc_sigma;
+  o->acc_volume = st->acc_volume;
+  o->V_iso = st->V_iso;
+  o->V = V;
+  o->U_LJ = U;
+  o->H = H;
+  o->g = st->g;
+  for (int64_t c = 0; c < st->N; ++c)
+    for (int a = 0; a < 6; ++a) o->n_state[o3_arm(st->w[c], a)] += 1;
+}
+
+int64_t orc3_run(orc3_state *st, int64_t n, int32_t record_every, orc_obs *ring, int64_t cap) {
+  int64_t nrec = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    orc3_step(st);
+    if (record_every > 0 && st->sweep % record_every == 0 && ring && nrec < cap)
+      orc3_observables(st, &ring[nrec++]);
+  }
+  return nrec;
+}
+
+/* The decision data of arm a of cell c for proposal offset k on an explicit
+   configuration: new state and threshold (for the detailed-balance pin). */
+void orc3_arm_probe(const orc_params *p, const uint32_t *w, int64_t c, int a, uint32_t k,
+                    int32_t g, uint32_t *s_new, uint64_t *T) {
+  uint64_t table[2][3][11];
+  orc3_threshold_table(p, table);
+  uint32_t wc = w[c];
+  uint32_t s = o3_arm(wc, a);
+  uint32_t sp = (s + 1u + k) % (uint32_t)p->q;
+  uint32_t nb = o3_arm(w[orc3_neighbour(p->L, c, a)], a ^ 1);
+  int dhb = (sp == nb) - (s == nb);
+  int dc = 0;
+  for (int b = 0; b < 6; ++b) {
+    if (b == a) continue;
+    uint32_t sb = o3_arm(wc, b);
+    dc += (sp == sb) - (s == sb);
+  }
+  *s_new = sp;
+  *T = table[g][dhb + 1][dc + 5];
+}
+
+/* The volume chain alone (no sigma updates) from V_iso with the bonds held
+   at n_hb_raw, for the truncated-Gamma pin. */
+int64_t orc3_volume_chain(const orc_params *p, double V_iso, int64_t n_hb_raw, int64_t step0,
+                          int64_t K, double *V_out) {
+  orc3_state st;
+  memset(&st, 0, sizeof(st));
+  st.p = *p;
+  st.N = (int64_t)p->L * p->L * p->L;
+  st.V_iso = V_iso;
+  st.g = (V_iso / (double)st.N < 2.0) ? 1 : 0;
+  st.dV_max = p->dv_max_frac * ((double)st.N * p->v_iso_init);
+  st.n_hb_raw = n_hb_raw;
+  for (int64_t i = 0; i < K; ++i) {
+    st.sweep = step0 + i;
+    orc3_volume_move(&st);
+    V_out[i] = st.V_iso;
+  }
+  return st.acc_volume;
+}
