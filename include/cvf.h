@@ -260,6 +260,84 @@ int cvf_batch_tile_config(int32_t config, int32_t *rows, int32_t *words);
 /* Waits for the stream and frees every replica and the batch. */
 int cvf_batch_destroy(cvf_batch *b);
 
+/* ------------------------------------------------------------------------
+ * The paper's own 3D model: a periodic cubic lattice of N = L^3 cells with
+ * six bonding indices per cell (Sec. II.A: six nearest neighbours), updated
+ * by the layered partition of Sec. II.C -- the six arm domains one after the
+ * other, in an order drawn every MC step -- with up to C(6,2) = 15
+ * cooperative pairs per cell in Eq. (H).  eta_ij is identically 1 (the
+ * checkerboard-cube eta update of App. A is not built).
+ *   - Layout: cell c = x + L (y + L z), one uint32 word per cell holding
+ *     sigma of arm a in bits [3a, 3a+3) (bits 18..31 zero).  Arms 0..5 =
+ *     left, right, front, back, top, bottom point to +x, -x, +y, -y, +z, -z
+ *     (Sec. II.C's coalescing example and Table S1: arm 0 of cell c pairs
+ *     with arm 1 of cell c+1, arm 4 of cell (1,0,0) with arm 5 of (1,0,1)).
+ *   - One MC step: the volume move (Sec. II.B, with the cubic-lattice LJ
+ *     energy u(v) = 2 eps [v^-4 S12 - v^-2 S6], r = v^(1/3)), then six
+ *     passes, pass i updating arm order[i] of every cell; order is the
+ *     permutation number floor(w 720 / 2^32) (lexicographic) of the six arms,
+ *     w word 0 of Philox((2^32-2, step, 4)).
+ *   - Draws: the update of arm a of cell c in step s uses word c mod 4 of
+ *     Philox((c / 4, s, 8 + a), seed): w (q-1) = k 2^32 + u gives the
+ *     proposal sigma' = (sigma + 1 + k) mod q and the acceptance draw u;
+ *     random init sigma_a(c) = floor(w q / 2^32), w word c mod 4 of
+ *     Philox((c / 4, 0, 16 + a)).
+ *   - Parameters: cvf_params with L the cube side (2 <= L <= 1024), schedule
+ *     CVF_SCHED_LAYERED and rng_words 1 (other values: CVF_EINVAL);
+ *     v_iso_init defaults to 2^(1/2) (the pair minimum r = 2^(1/6) r0).
+ *   - Observables: cvf_obs as above with N_HB <= 3N, N_sigma <= 15N and the
+ *     order parameter M = max N_q' / (6N).
+ * Streams, ownership, errors and thread safety as for cvf_handle.
+ * ------------------------------------------------------------------------ */
+typedef struct cvf3_handle cvf3_handle;
+
+/* Table 1 parameters at (T_kelvin, P_MPa) for the cubic lattice: as
+ * cvf_params_physical with L = 16, v_iso_init = 2^(1/2), the layered
+ * schedule and one RNG word per update. */
+int cvf3_params_physical(double T_kelvin, double P_MPa, cvf_params *out);
+
+/* The 66 thresholds [g][dN_HB + 1][dN_sigma + 5] (dN_sigma in -5..5, the
+ * five other arms of the cell): T = 2^32 when dH = -g J_eff dN_HB -
+ * J_sigma dN_sigma <= 0, else floor(exp(-dH/kT) 2^32).  Host only. */
+int cvf3_threshold_table(const cvf_params *p, uint64_t out[66]);
+
+/* Creates a cubic lattice on the device (random or ordered init), V_iso =
+ * N v_iso_init, counts N_HB_raw and N_sigma, sweep = 0.
+ *   dev_state  NULL: the library allocates the lattice; otherwise a device
+ *              buffer of L^3 uint32 words, 16-byte aligned, owned by the
+ *              caller (the passes update it in place). */
+int cvf3_create(const cvf_params *p, void *stream, void *dev_state,
+                cvf3_handle **out);
+
+/* Enqueues n_sweeps MC steps (graph-captured; returns without waiting);
+ * record_every as for cvf_sweep (ring of 65536 records). */
+int cvf3_sweep(cvf3_handle *h, int64_t n_sweeps, int32_t record_every);
+
+/* Observables after the last completed step (N_q' counted from the lattice
+ * by this call); synchronises.  N_HB_raw and N_sigma are the counts the
+ * passes maintain incrementally. */
+int cvf3_observables(cvf3_handle *h, cvf_obs *out);
+
+/* As cvf_drain_series. */
+int cvf3_drain_series(cvf3_handle *h, cvf_obs *host, int64_t cap, int64_t *n);
+
+/* Copies / replaces the lattice (n = L^3 words, layout above).  set_state
+ * validates every word on the host (arms < q, bits 18..31 zero), sets V_iso
+ * (>= N) and the step counter, recounts, clears the acceptance counters and
+ * the ring.  Both synchronise. */
+int cvf3_get_state(cvf3_handle *h, uint32_t *host, size_t n);
+int cvf3_set_state(cvf3_handle *h, const uint32_t *host, size_t n,
+                   double V_iso, int64_t sweep);
+
+/* Recounts N_HB_raw and N_sigma with a separate reduction; synchronises. */
+int cvf3_recount(cvf3_handle *h, int64_t *n_hb_raw, int64_t *n_sigma);
+
+/* Device address of the lattice (L^3 words). */
+int cvf3_state_device_ptr(cvf3_handle *h, void **dev_ptr);
+
+/* Waits for the handle's stream, frees what the library allocated. */
+int cvf3_destroy(cvf3_handle *h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,19 @@ _SIGS = {
     "cvf_batch_set_tiles": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "cvf_batch_tile_config": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_int32)]),
     "cvf_batch_destroy": (ctypes.c_int, [_vp]),
+    # cubic lattice (the paper's 3D model)
+    "cvf3_params_physical": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _P(cvf_params)]),
+    "cvf3_threshold_table": (ctypes.c_int, [_P(cvf_params), _P(ctypes.c_uint64)]),
+    "cvf3_create": (ctypes.c_int, [_P(cvf_params), _vp, _vp, _P(_vp)]),
+    "cvf3_sweep": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int32]),
+    "cvf3_observables": (ctypes.c_int, [_vp, _P(cvf_obs)]),
+    "cvf3_drain_series": (ctypes.c_int, [_vp, _P(cvf_obs), ctypes.c_int64, _P(ctypes.c_int64)]),
+    "cvf3_get_state": (ctypes.c_int, [_vp, _P(ctypes.c_uint32), ctypes.c_size_t]),
+    "cvf3_set_state": (ctypes.c_int, [_vp, _P(ctypes.c_uint32), ctypes.c_size_t, ctypes.c_double,
+                                      ctypes.c_int64]),
+    "cvf3_recount": (ctypes.c_int, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
+    "cvf3_state_device_ptr": (ctypes.c_int, [_vp, _P(_vp)]),
+    "cvf3_destroy": (ctypes.c_int, [_vp]),
 }
 
 _lib = None
@@ -270,3 +283,68 @@ def cvf_batch_tile_config(config: int):
 
 def cvf_batch_destroy(b: int) -> None:
     _check(load().cvf_batch_destroy(b), "cvf_batch_destroy")
+
+
+# ----------------------------------------------------------- cubic lattice --
+def cvf3_params_physical(T_kelvin: float, P_MPa: float) -> cvf_params:
+    p = cvf_params()
+    _check(load().cvf3_params_physical(T_kelvin, P_MPa, ctypes.byref(p)), "cvf3_params_physical")
+    return p
+
+
+def cvf3_threshold_table(p: cvf_params):
+    out = (ctypes.c_uint64 * 66)()
+    _check(load().cvf3_threshold_table(ctypes.byref(p), out), "cvf3_threshold_table")
+    return list(out)
+
+
+def cvf3_create(p: cvf_params, stream: int | None = None, dev_state: int | None = None) -> int:
+    h = _vp()
+    _check(load().cvf3_create(ctypes.byref(p), stream or None, dev_state or None, ctypes.byref(h)),
+           "cvf3_create")
+    return h.value
+
+
+def cvf3_sweep(h: int, n_sweeps: int, record_every: int = 0) -> None:
+    _check(load().cvf3_sweep(h, n_sweeps, record_every), "cvf3_sweep")
+
+
+def cvf3_observables(h: int) -> cvf_obs:
+    o = cvf_obs()
+    _check(load().cvf3_observables(h, ctypes.byref(o)), "cvf3_observables")
+    return o
+
+
+def cvf3_drain_series(h: int, cap: int):
+    """Returns (records, overflowed)."""
+    buf = (cvf_obs * max(cap, 1))()
+    n = ctypes.c_int64()
+    rc = load().cvf3_drain_series(h, buf, cap, ctypes.byref(n))
+    if rc not in (CVF_OK, CVF_EOVERFLOW):
+        _check(rc, "cvf3_drain_series")
+    return [buf[i] for i in range(n.value)], rc == CVF_EOVERFLOW
+
+
+def cvf3_get_state(h: int, host_ptr: int, n: int) -> None:
+    _check(load().cvf3_get_state(h, ctypes.cast(host_ptr, _P(ctypes.c_uint32)), n), "cvf3_get_state")
+
+
+def cvf3_set_state(h: int, host_ptr: int, n: int, V_iso: float, sweep: int) -> None:
+    _check(load().cvf3_set_state(h, ctypes.cast(host_ptr, _P(ctypes.c_uint32)), n, V_iso, sweep),
+           "cvf3_set_state")
+
+
+def cvf3_recount(h: int):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().cvf3_recount(h, ctypes.byref(a), ctypes.byref(b)), "cvf3_recount")
+    return a.value, b.value
+
+
+def cvf3_state_device_ptr(h: int) -> int:
+    p = _vp()
+    _check(load().cvf3_state_device_ptr(h, ctypes.byref(p)), "cvf3_state_device_ptr")
+    return p.value
+
+
+def cvf3_destroy(h: int) -> None:
+    _check(load().cvf3_destroy(h), "cvf3_destroy")

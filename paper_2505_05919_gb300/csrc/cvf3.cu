@@ -1,0 +1,895 @@
+// cvf3.cu -- the paper's own 3D CVF Metropolis (arXiv:2505.05919, Sec. II):
+// a periodic cubic lattice, six bonding indices per cell packed 3 bits each
+// in one uint32 word, the layered partition of Sec. II.C (the six arm
+// domains updated one after the other in an order drawn every MC step), the
+// counts of Eq. (H) kept incrementally, and the isobaric volume move of
+// Sec. II.B with the cubic-lattice Lennard-Jones energy.
+//
+// Launch structure.  A pass over arm a reads, besides the cell's own word,
+// only arm a^1 of the neighbour in direction a.  That arm changes only in
+// the pass over a^1.  So consecutive passes whose arms contain no opposite
+// pair can run in one launch, each thread taking its cells through all of
+// them in registers: every neighbour arm it reads is constant during the
+// launch, whichever version of the neighbour's word it sees, and the result
+// is the one of the passes run one after the other.  The six passes of a
+// step are cut greedily before the first arm whose opposite is already in
+// the current launch, which gives 2 to 4 launches (2.67 on average over the
+// 720 orders); every step enqueues four launches, the unused ones return at
+// once, and the fourth commits the step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cvf_device.cuh"
+#include "cvf_host.h"
+#include "cvf_lattice.cuh"
+
+namespace cvf {
+namespace {
+
+constexpr int kThreads3 = 256;
+constexpr int kLaunches3 = 4;           // launches per MC step (most segments)
+constexpr int kGraphSteps3 = 32;
+constexpr long long kRingCap3 = 65536;
+constexpr uint32_t kTagArm0 = 8u;       // draws of arm a: Philox tag 8 + a
+constexpr uint32_t kTagInit0 = 16u;     // random init of arm a: tag 16 + a
+constexpr uint32_t kRep6 = 0x9249u;     // bit 3b set for b = 0..5
+constexpr int kMaxSide3 = 1024;
+
+// Unsigned division by an invariant d (1 <= d < 2^31) for any 32-bit n,
+// after Granlund and Montgomery, "Division by invariant integers using
+// multiplication" (PLDI 1994, Fig. 4.1): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n),
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+struct FastDiv {
+  uint32_t m, sh1, sh2;
+};
+
+FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < (unsigned long long)d) ++l;
+  FastDiv f;
+  f.m = (uint32_t)(((((1ull << l) - d) << 32) / d) + 1);
+  f.sh1 = l < 1 ? l : 1;
+  f.sh2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  const uint32_t t = __umulhi(f.m, n);
+  return (t + ((n - t) >> f.sh1)) >> f.sh2;
+}
+
+struct Args3 {
+  uint32_t* state;                  // L^3 words, updated in place
+  Ctrl* ctrl;
+  const unsigned long long* table;  // [g][(dN_HB+1)*11 + dN_sigma+5]
+  const VolumeArgs* vol;
+  cvf_obs* ring;
+  long long ring_cap;
+  RoundKeys keys;
+  uint32_t L, L2, N;
+  uint32_t groups;                  // ceil(N / 4): four consecutive cells each
+  uint32_t G;                       // L / 4 (groups per row when L % 4 == 0)
+  uint32_t q;
+  FastDiv div_G, div_L, div_L2;
+};
+
+// ---------------------------------------------------------------------------
+// Arm order and launch plan of a step.  The order is permutation number
+// floor(w 720 / 2^32) of the six arms (lexicographic), w word 0 of
+// Philox((2^32-2, step, 4)).  Plan word: bits 3i..3i+2 the arm of pass i,
+// bit 17 + i set when pass i opens a new launch (i = 1..5).
+// ---------------------------------------------------------------------------
+__device__ uint32_t make_plan(long long step, const RoundKeys& K) {
+  const Words4 r = philox(kCellLayers, (uint32_t)((unsigned long long)step & 0xFFFFFFFFu),
+                          (uint32_t)((unsigned long long)step >> 32), kTagLayers, K);
+  uint32_t idx = __umulhi(r.x, 720u);
+  int avail[6] = {0, 1, 2, 3, 4, 5};
+  const uint32_t fact[6] = {120u, 24u, 6u, 2u, 1u, 1u};
+  uint32_t plan = 0, in_launch = 0;
+  int left = 6;
+  for (int i = 0; i < 6; ++i) {
+    const uint32_t j = idx / fact[i];
+    idx -= j * fact[i];
+    const int a = avail[j];
+    for (int t = (int)j; t < left - 1; ++t) avail[t] = avail[t + 1];
+    --left;
+    if (in_launch & (1u << (a ^ 1))) {
+      plan |= 1u << (17 + i);
+      in_launch = 0;
+    }
+    in_launch |= 1u << a;
+    plan |= (uint32_t)a << (3 * i);
+  }
+  return plan;
+}
+
+__device__ __forceinline__ int plan_launches(uint32_t plan) { return 1 + __popc(plan >> 18); }
+
+// Arms of launch j of the plan (at most three: no opposite pair).
+__device__ int plan_arms(uint32_t plan, int j, int* arms) {
+  int launch = 0, n = 0;
+  for (int i = 0; i < 6; ++i) {
+    if (i > 0 && ((plan >> (17 + i)) & 1u)) ++launch;
+    if (launch == j && n < 3) arms[n++] = (int)((plan >> (3 * i)) & 7u);
+  }
+  return n;
+}
+
+// ---------------------------------------------------------------------------
+// Metropolis update of arm `a` (shift sh = 3a) of one cell (Sec. II.C with
+// Eq. H): w the cell word, n the partner arm's value (arm a^1 of the
+// neighbour in direction a), r the cell's 32-bit draw.  Proposal
+// sigma' = (sigma + 1 + k) mod q with w (q-1) = k 2^32 + u; dN_sigma from
+// the equal arms of the word: bit 3b of (x | x>>1 | x>>2) & 0x9249, x = w ^
+// (v * 0x9249), is set when arm b differs from v, so
+// dN_sigma = popc(differ from sigma) - popc(differ from sigma') + 1.
+// ---------------------------------------------------------------------------
+template <bool CMP64>
+__device__ __forceinline__ uint32_t update_arm3(uint32_t w, uint32_t n, uint32_t r, uint32_t sh,
+                                                uint32_t q, const uint32_t* T32,
+                                                const unsigned long long* T64, int& dhb_sum,
+                                                int& dc_sum, uint32_t& nacc) {
+  const uint32_t s = (w >> sh) & 7u;
+  const uint32_t k = __umulhi(r, q - 1u);
+  const uint32_t u = r * (q - 1u);
+  uint32_t sp = s + 1u + k;
+  sp = (sp >= q) ? sp - q : sp;
+  const int dhb = (int)(sp == n) - (int)(s == n);
+  const uint32_t xs = w ^ (s * kRep6);
+  const uint32_t xp = w ^ (sp * kRep6);
+  const uint32_t ds = (xs | (xs >> 1) | (xs >> 2)) & kRep6;
+  const uint32_t dp = (xp | (xp >> 1) | (xp >> 2)) & kRep6;
+  const int dc = __popc(ds) - __popc(dp) + 1;
+  const int idx = dhb * 11 + dc + 16;  // (dN_HB + 1) * 11 + dN_sigma + 5
+  const bool accept = CMP64 ? ((unsigned long long)u < T64[idx]) : (u <= T32[idx]);
+  if (accept) {
+    w ^= (s ^ sp) << sh;
+    dhb_sum += dhb;
+    dc_sum += dc;
+    ++nacc;
+  }
+  return w;
+}
+
+// N_q' of the four final cell words of a group, added to the block's eight
+// shared counters: per word a count word (nibble v = arms in state v), two
+// words summed (nibbles <= 12), nibbles v and v+4 moved to the 16-bit lanes
+// of word v (<= 24 per lane), reduced over the converged lanes of the warp
+// (<= 768 per lane) and added by the lowest of them.
+__device__ __forceinline__ uint32_t count_word(uint32_t w) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int b = 0; b < 6; ++b) c += 1u << (4u * ((w >> (3 * b)) & 7u));
+  return c;
+}
+
+__device__ __forceinline__ void hist_group(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
+                                           uint32_t* s_hist) {
+  const uint32_t h01 = count_word(w0) + count_word(w1);
+  const uint32_t h23 = count_word(w2) + count_word(w3);
+  const unsigned mask = __activemask();
+  const int leader = __ffs(mask) - 1;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    uint32_t lanes = ((h01 >> (4 * v)) & 0x000F000Fu) + ((h23 >> (4 * v)) & 0x000F000Fu);
+    lanes = __reduce_add_sync(mask, lanes);
+    if ((int)(threadIdx.x & 31) == leader) {
+      if (lanes & 0xFFFFu) atomicAdd(&s_hist[v], lanes & 0xFFFFu);
+      if (lanes >> 16) atomicAdd(&s_hist[v + 4], lanes >> 16);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One launch of a step.  ALIGNED: L % 4 == 0, a group (four consecutive
+// cells) lies in one row, its words and its y/z neighbours' words are
+// 16-byte vectors.  Otherwise every cell computes its own coordinates.
+// Launch 0 has one extra block (block 0) that decides the next step's volume
+// move early when it cannot depend on the bonds (no gate change); launch
+// kLaunches3 - 1 commits the step.
+// ---------------------------------------------------------------------------
+template <bool ALIGNED, bool CMP64>
+__global__ void __launch_bounds__(kThreads3) k_pass3(Args3 A, int launch) {
+  __shared__ uint32_t sT32[33];
+  __shared__ unsigned long long sT64[CMP64 ? 33 : 1];
+  __shared__ int s_arm[3];
+  __shared__ int s_n, s_rec;
+  __shared__ uint32_t s_hist[8];
+  Ctrl* ctl = A.ctrl;
+  const bool fin = (launch == kLaunches3 - 1);
+  if (threadIdx.x == 0) {
+    uint32_t plan;
+    if (launch == 0) {
+      plan = make_plan(ctl->sweep, A.keys);
+      if (blockIdx.x == 0) ctl->plan = (int)plan;
+    } else {
+      plan = (uint32_t)ctl->plan;
+    }
+    int arms[3] = {0, 0, 0};
+    const int n = plan_arms(plan, launch, arms);
+    s_n = n;
+    for (int i = 0; i < 3; ++i) s_arm[i] = arms[i];
+    // N_q' is accumulated by the launch that finishes a recorded step
+    s_rec = (n > 0 && launch == plan_launches(plan) - 1 &&
+             step_recorded(ctl->record_every, ctl->sweep)) ? 1 : 0;
+  }
+  __syncthreads();
+  const int n_arms = s_n;
+  if (launch == 0 && blockIdx.x == 0) {
+    if (threadIdx.x == 0) {
+      VolumeResult r;
+      if (volume_decide(*A.vol, ctl->sweep + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1,
+                        A.keys, &r)) {
+        ctl->ahead_V = r.V;
+        ctl->ahead_u = r.u;
+        ctl->ahead_g = r.g;
+        ctl->ahead_acc = r.accepted;
+        ctl->ahead_state = 1;
+      }
+    }
+    return;
+  }
+  if (n_arms == 0) {
+    // nothing to update in this launch; the last one still commits the step
+    if (fin && blockIdx.x == 0 && threadIdx.x == 0)
+      finalize_step<true>(*A.vol, ctl, A.ring, A.ring_cap, A.keys);
+    return;
+  }
+  const long long step = ctl->sweep;
+  const int g = ctl->next_g;
+  const bool rec = s_rec != 0;
+  if (threadIdx.x < 33) {
+    const unsigned long long t = A.table[g * 33 + threadIdx.x];
+    if (CMP64)
+      sT64[threadIdx.x] = t;
+    else
+      sT32[threadIdx.x] = (uint32_t)(t - 1ull);  // every t >= 1 here
+  }
+  if (threadIdx.x < 8) s_hist[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
+  const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
+  const uint32_t q = A.q;
+  const uint32_t first_block = (launch == 0) ? 1u : 0u;
+  const uint32_t nblk = gridDim.x - first_block;
+  int dhb_sum = 0, dc_sum = 0;
+  uint32_t nacc = 0;
+  uint32_t* __restrict__ st = A.state;
+  for (uint32_t gi = (blockIdx.x - first_block) * kThreads3 + threadIdx.x; gi < A.groups;
+       gi += nblk * kThreads3) {
+    const uint32_t c0 = gi * 4u;
+    if (ALIGNED) {
+      const uint32_t row = fdiv(gi, A.div_G);      // y + L z
+      const uint32_t xg = gi - row * A.G;
+      const uint32_t z = fdiv(row, A.div_L);
+      const uint32_t y = row - z * A.L;
+      const uint4 own = *reinterpret_cast<const uint4*>(st + c0);
+      uint32_t w0 = own.x, w1 = own.y, w2 = own.z, w3 = own.w;
+      for (int p = 0; p < n_arms; ++p) {
+        const int a = s_arm[p];
+        const uint32_t sh = 3u * (uint32_t)a, shn = 3u * (uint32_t)(a ^ 1);
+        uint32_t n0, n1, n2, n3;
+        if (a == 0) {
+          n0 = w1;
+          n1 = w2;
+          n2 = w3;
+          n3 = st[(4u * xg + 4u == A.L) ? c0 + 4u - A.L : c0 + 4u];
+        } else if (a == 1) {
+          n0 = st[(xg == 0u) ? c0 + A.L - 1u : c0 - 1u];
+          n1 = w0;
+          n2 = w1;
+          n3 = w2;
+        } else {
+          uint32_t off;
+          if (a == 2)
+            off = (y == A.L - 1u) ? c0 + A.L - A.L2 : c0 + A.L;
+          else if (a == 3)
+            off = (y == 0u) ? c0 + A.L2 - A.L : c0 - A.L;
+          else if (a == 4)
+            off = (z == A.L - 1u) ? c0 + A.L2 - A.N : c0 + A.L2;
+          else
+            off = (z == 0u) ? c0 + A.N - A.L2 : c0 - A.L2;
+          const uint4 nb = *reinterpret_cast<const uint4*>(st + off);
+          n0 = nb.x;
+          n1 = nb.y;
+          n2 = nb.z;
+          n3 = nb.w;
+        }
+        const Words4 r = philox(gi, s_lo, s_hi, kTagArm0 + (uint32_t)a, A.keys);
+        w0 = update_arm3<CMP64>(w0, (n0 >> shn) & 7u, r.x, sh, q, sT32, sT64, dhb_sum, dc_sum, nacc);
+        w1 = update_arm3<CMP64>(w1, (n1 >> shn) & 7u, r.y, sh, q, sT32, sT64, dhb_sum, dc_sum, nacc);
+        w2 = update_arm3<CMP64>(w2, (n2 >> shn) & 7u, r.z, sh, q, sT32, sT64, dhb_sum, dc_sum, nacc);
+        w3 = update_arm3<CMP64>(w3, (n3 >> shn) & 7u, r.w, sh, q, sT32, sT64, dhb_sum, dc_sum, nacc);
+      }
+      *reinterpret_cast<uint4*>(st + c0) = make_uint4(w0, w1, w2, w3);
+      if (rec) hist_group(w0, w1, w2, w3, s_hist);
+    } else {
+      uint32_t w[4], x[4], y[4], z[4];
+      bool valid[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t c = c0 + (uint32_t)i;
+        valid[i] = c < A.N;
+        const uint32_t cc = valid[i] ? c : 0u;
+        z[i] = fdiv(cc, A.div_L2);
+        const uint32_t rem = cc - z[i] * A.L2;
+        y[i] = fdiv(rem, A.div_L);
+        x[i] = rem - y[i] * A.L;
+        w[i] = valid[i] ? st[c] : 0u;
+      }
+      for (int p = 0; p < n_arms; ++p) {
+        const int a = s_arm[p];
+        const uint32_t sh = 3u * (uint32_t)a, shn = 3u * (uint32_t)(a ^ 1);
+        const Words4 r = philox(gi, s_lo, s_hi, kTagArm0 + (uint32_t)a, A.keys);
+        const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (!valid[i]) continue;
+          const uint32_t c = c0 + (uint32_t)i;
+          uint32_t nb;
+          if (a == 0)
+            nb = (x[i] + 1u == A.L) ? c + 1u - A.L : c + 1u;
+          else if (a == 1)
+            nb = (x[i] == 0u) ? c + A.L - 1u : c - 1u;
+          else if (a == 2)
+            nb = (y[i] + 1u == A.L) ? c + A.L - A.L2 : c + A.L;
+          else if (a == 3)
+            nb = (y[i] == 0u) ? c + A.L2 - A.L : c - A.L;
+          else if (a == 4)
+            nb = (z[i] + 1u == A.L) ? c + A.L2 - A.N : c + A.L2;
+          else
+            nb = (z[i] == 0u) ? c + A.N - A.L2 : c - A.L2;
+          w[i] = update_arm3<CMP64>(w[i], (st[nb] >> shn) & 7u, rw[i], sh, q, sT32, sT64,
+                                    dhb_sum, dc_sum, nacc);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (valid[i]) st[c0 + (uint32_t)i] = w[i];
+      if (rec) {
+        // cells past the end hold word 0, counted as six arms in state 0
+        hist_group(w[0], w[1], w[2], w[3], s_hist);
+        if (!valid[1] || !valid[2] || !valid[3]) {
+          // a zero word counts six arms in state 0: take them back
+          const uint32_t missing = (uint32_t)(!valid[1]) + (uint32_t)(!valid[2]) + (uint32_t)(!valid[3]);
+          atomicSub(&s_hist[0], 6u * missing);
+        }
+      }
+    }
+  }
+  uint32_t a1 = (uint32_t)dhb_sum, a2 = (uint32_t)dc_sum, a3 = nacc;
+  block_sum3<kThreads3>(a1, a2, a3);
+  if (threadIdx.x == 0) {
+    atomicAdd(&ctl->acc_hb, (unsigned long long)(long long)(int)a1);
+    atomicAdd(&ctl->acc_pairs, (unsigned long long)(long long)(int)a2);
+    atomicAdd(&ctl->acc_moves, (unsigned long long)a3);
+  }
+  if (rec) {
+    __syncthreads();
+    if (threadIdx.x < 8 && s_hist[threadIdx.x])
+      atomicAdd(&ctl->acc_hist[threadIdx.x], (unsigned long long)s_hist[threadIdx.x]);
+  }
+  if (fin && last_block(&ctl->done) && threadIdx.x == 0)
+    finalize_step<true>(*A.vol, ctl, A.ring, A.ring_cap, A.keys);
+}
+
+// Random init: sigma_a(c) = floor(w q / 2^32), w word c mod 4 of
+// Philox((c / 4, 0, 0, 16 + a)); ordered init: every sigma 0.
+__global__ void __launch_bounds__(kThreads3) k_init3(uint32_t* __restrict__ state, uint32_t N,
+                                                      uint32_t groups, uint32_t q, int random,
+                                                      RoundKeys K) {
+  for (uint32_t gi = blockIdx.x * kThreads3 + threadIdx.x; gi < groups;
+       gi += gridDim.x * kThreads3) {
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    if (random) {
+      for (int a = 0; a < 6; ++a) {
+        const Words4 r = philox(gi, 0u, 0u, kTagInit0 + (uint32_t)a, K);
+        const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] |= __umulhi(rw[i], q) << (3 * a);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (gi * 4u + (uint32_t)i < N) state[gi * 4u + (uint32_t)i] = w[i];
+  }
+}
+
+// Full count of a lattice: N_HB_raw (arms 0, 2, 4 against arms 1, 3, 5 of
+// the +x, +y, +z neighbours) and N_sigma (equal pairs among the six arms)
+// added to acc2[0], acc2[1]; N_q' added to hist[0..8).  Either may be NULL.
+__global__ void __launch_bounds__(kThreads3) k_count3(const uint32_t* __restrict__ state,
+                                                       uint32_t L, uint32_t L2, uint32_t N,
+                                                       FastDiv div_L, FastDiv div_L2,
+                                                       unsigned long long* acc2,
+                                                       unsigned long long* hist) {
+  __shared__ unsigned long long s_cnt[8];
+  if (threadIdx.x < 8) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t hb = 0, pairs = 0, unused = 0;
+  uint32_t h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (uint32_t c = blockIdx.x * kThreads3 + threadIdx.x; c < N; c += gridDim.x * kThreads3) {
+    const uint32_t z = fdiv(c, div_L2);
+    const uint32_t rem = c - z * L2;
+    const uint32_t y = fdiv(rem, div_L);
+    const uint32_t x = rem - y * L;
+    const uint32_t w = state[c];
+    const uint32_t wx = state[(x + 1u == L) ? c + 1u - L : c + 1u];
+    const uint32_t wy = state[(y + 1u == L) ? c + L - L2 : c + L];
+    const uint32_t wz = state[(z + 1u == L) ? c + L2 - N : c + L2];
+    hb += (uint32_t)(((w >> 0) & 7u) == ((wx >> 3) & 7u));
+    hb += (uint32_t)(((w >> 6) & 7u) == ((wy >> 9) & 7u));
+    hb += (uint32_t)(((w >> 12) & 7u) == ((wz >> 15) & 7u));
+    const uint32_t cnt = count_word(w);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const uint32_t m = (cnt >> (4 * v)) & 15u;
+      pairs += m * (m - 1u) / 2u;
+      h[v] += m;
+    }
+  }
+  if (hist)
+    for (int v = 0; v < 8; ++v)
+      if (h[v]) atomicAdd(&s_cnt[v], (unsigned long long)h[v]);
+  block_sum3<kThreads3>(hb, pairs, unused);
+  if (threadIdx.x == 0 && acc2) {
+    atomicAdd(&acc2[0], (unsigned long long)hb);
+    atomicAdd(&acc2[1], (unsigned long long)pairs);
+  }
+  __syncthreads();
+  if (hist && threadIdx.x < 8 && s_cnt[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+// Observables of the committed state with N_q' from a count of the lattice.
+__global__ void k_observables3(const VolumeArgs* __restrict__ V, const Ctrl* ctl,
+                               const unsigned long long* hist, cvf_obs* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    cvf_obs o = make_obs(*V, ctl);
+    for (int v = 0; v < 8; ++v) o.n_state[v] = (long long)hist[v];
+    *out = o;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+
+int check_params3(const cvf_params* p) {
+  if (!p) return set_error(CVF_EINVAL, "params is NULL");
+  if (p->L < 2 || p->L > kMaxSide3)
+    return set_error(CVF_EINVAL, "L=%d: need 2 <= L <= %d for the cubic lattice", p->L,
+                     kMaxSide3);
+  if (p->schedule != CVF_SCHED_LAYERED)
+    return set_error(CVF_EINVAL, "the cubic lattice runs the layered schedule only");
+  if (p->rng_words != 1)
+    return set_error(CVF_EINVAL, "the cubic lattice draws one word per update (rng_words 1)");
+  cvf_params t = *p;
+  t.L = 2;  // the side rules of the square lattice do not apply here
+  return check_params(&t);
+}
+
+void threshold_table3(const cvf_params* p, uint64_t out[66]) {
+  const double J_eff = p->J - p->P * p->v_HB;
+  for (int g = 0; g < 2; ++g)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 11; ++j) {
+        const int dhb = i - 1, dc = j - 5;
+        const double dH = -((double)g * J_eff) * (double)dhb - p->J_sigma * (double)dc;
+        out[(g * 3 + i) * 11 + j] = (dH <= 0.0)
+                                        ? ((uint64_t)1 << 32)
+                                        : (uint64_t)(std::exp(-dH / p->kT) * 4294967296.0);
+      }
+}
+
+// Shells of the cubic lattice inside the cutoff: |d|^2 (ascending) and the
+// number of lattice vectors of each length.
+void cubic_shells(double cutoff, std::vector<int64_t>* d2, std::vector<int64_t>* mult) {
+  d2->clear();
+  mult->clear();
+  const int R = (int)std::ceil(cutoff);
+  std::vector<int64_t> count((size_t)3 * R * R + 1, 0);
+  for (int i = -R; i <= R; ++i)
+    for (int j = -R; j <= R; ++j)
+      for (int k = -R; k <= R; ++k) {
+        const int64_t s = (int64_t)i * i + (int64_t)j * j + (int64_t)k * k;
+        if (s > 0) count[(size_t)s] += 1;
+      }
+  for (size_t s = 1; s < count.size(); ++s)
+    if (count[s] > 0 && (double)s < cutoff * cutoff) {
+      d2->push_back((int64_t)s);
+      mult->push_back(count[s]);
+    }
+}
+
+// FP64 parameters of the volume move for the cubic lattice: shell keys
+// |d|^6 against cutoff^6, prefix sums of m/|d|^12 and m/|d|^6 in increasing
+// |d|.
+void fill_volume_args3(const cvf_params* p, long long N, const std::vector<int64_t>& d2,
+                       const std::vector<int64_t>& mult, VolumeArgs* va) {
+  std::memset(va, 0, sizeof(*va));
+  va->N = N;
+  va->epsilon = p->epsilon;
+  const double c = p->cutoff;
+  va->cutoff2 = c * c * c * c * c * c;
+  va->J = p->J;
+  va->J_sigma = p->J_sigma;
+  va->v_HB = p->v_HB;
+  va->kT = p->kT;
+  va->P = p->P;
+  va->dV_max = p->dv_max_frac * ((double)N * p->v_iso_init);
+  va->volume_moves = p->volume_moves;
+  va->dim = 3;
+  va->nshell = (int32_t)d2.size();
+  va->S12[0] = 0.0;
+  va->S6[0] = 0.0;
+  for (size_t s = 0; s < d2.size(); ++s) {
+    const int64_t d6 = d2[s] * d2[s] * d2[s];
+    va->shell_d2[s] = (double)d6;
+    va->S12[s + 1] = va->S12[s] + (double)mult[s] / ((double)d6 * (double)d6);
+    va->S6[s + 1] = va->S6[s] + (double)mult[s] / (double)d6;
+  }
+}
+
+}  // namespace
+}  // namespace cvf
+
+using namespace cvf;
+
+struct cvf3_handle {
+  cvf_params p;
+  long long N;
+  cudaStream_t stream;
+  cudaStream_t cap_stream;
+  uint32_t* state;
+  bool own_state;
+  Ctrl* ctrl;
+  cvf_obs* ring;
+  long long ring_cap;
+  long long ring_tail;
+  cvf_obs* obs_dev;
+  unsigned long long* table_dev;
+  VolumeArgs* vol_dev;
+  unsigned long long* rc_dev;  // 10 counters: N_q'[8], N_HB_raw, N_sigma
+  void* host_pinned;
+  Args3 args;
+  bool cmp64;
+  bool aligned;
+  int grid;
+  int grid_count;
+  cudaGraphExec_t graph;
+};
+
+namespace {
+
+void release3(cvf3_handle* h) {
+  if (!h) return;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->own_state && h->state) cudaFree(h->state);
+  if (h->ctrl) cudaFree(h->ctrl);
+  if (h->ring) cudaFree(h->ring);
+  if (h->obs_dev) cudaFree(h->obs_dev);
+  if (h->table_dev) cudaFree(h->table_dev);
+  if (h->vol_dev) cudaFree(h->vol_dev);
+  if (h->rc_dev) cudaFree(h->rc_dev);
+  if (h->host_pinned) cudaFreeHost(h->host_pinned);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+const void* pass_kernel(bool aligned, bool cmp64) {
+  if (aligned) return cmp64 ? (const void*)k_pass3<true, true> : (const void*)k_pass3<true, false>;
+  return cmp64 ? (const void*)k_pass3<false, true> : (const void*)k_pass3<false, false>;
+}
+
+void enqueue_step3(cvf3_handle* h, cudaStream_t s) {
+  for (int j = 0; j < kLaunches3; ++j) {
+    const int grid = h->grid + (j == 0 ? 1 : 0);
+    if (h->aligned) {
+      if (h->cmp64)
+        k_pass3<true, true><<<grid, kThreads3, 0, s>>>(h->args, j);
+      else
+        k_pass3<true, false><<<grid, kThreads3, 0, s>>>(h->args, j);
+    } else {
+      if (h->cmp64)
+        k_pass3<false, true><<<grid, kThreads3, 0, s>>>(h->args, j);
+      else
+        k_pass3<false, false><<<grid, kThreads3, 0, s>>>(h->args, j);
+    }
+  }
+}
+
+int build_graph3(cvf3_handle* h) {
+  if (h->graph) return CVF_OK;
+  cudaGraph_t g = nullptr;
+  CVF_CUDA_CHECK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < kGraphSteps3; ++i) enqueue_step3(h, h->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (e != cudaSuccess) return set_error(CVF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    return set_error(CVF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  return CVF_OK;
+}
+
+// Count the lattice into the control block (committed N_HB_raw, N_sigma) and
+// prepare the next volume move.
+int recount_into_ctrl3(cvf3_handle* h) {
+  static_assert(offsetof(Ctrl, acc_pairs) == offsetof(Ctrl, acc_hb) + 8, "layout");
+  k_count3<<<h->grid_count, kThreads3, 0, h->stream>>>(h->state, h->args.L, h->args.L2,
+                                                        h->args.N, h->args.div_L, h->args.div_L2,
+                                                        &h->ctrl->acc_hb, nullptr);
+  k_commit_counts<<<1, 32, 0, h->stream>>>(h->ctrl);
+  k_volume_prologue<<<1, 32, 0, h->stream>>>(h->vol_dev, h->ctrl, h->args.keys);
+  CVF_CUDA_CHECK(cudaGetLastError());
+  return CVF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cvf3_params_physical(double T_kelvin, double P_MPa, cvf_params* out) {
+  const int rc = cvf_params_physical(T_kelvin, P_MPa, out);
+  if (rc) return rc;
+  out->L = 16;
+  out->v_iso_init = std::sqrt(2.0);
+  out->schedule = CVF_SCHED_LAYERED;
+  out->rng_words = 1;
+  return CVF_OK;
+}
+
+int cvf3_threshold_table(const cvf_params* p, uint64_t out[66]) {
+  if (!out) return set_error(CVF_EINVAL, "out is NULL");
+  const int rc = check_params3(p);
+  if (rc) return rc;
+  threshold_table3(p, out);
+  return CVF_OK;
+}
+
+int cvf3_create(const cvf_params* p, void* stream, void* dev_state, cvf3_handle** out) {
+  if (!out) return set_error(CVF_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = check_params3(p);
+  if (rc) return rc;
+  if (dev_state && (reinterpret_cast<uintptr_t>(dev_state) & 15u))
+    return set_error(CVF_EINVAL, "dev_state must be 16-byte aligned");
+  std::vector<int64_t> d2, mult;
+  cubic_shells(p->cutoff, &d2, &mult);
+  if ((int)d2.size() > kMaxShells)
+    return set_error(CVF_EINVAL, "cutoff %g needs %zu shells (max %d)", p->cutoff, d2.size(),
+                     kMaxShells);
+  cvf3_handle* h = new (std::nothrow) cvf3_handle();
+  if (!h) return set_error(CVF_ENOMEM, "host allocation failed");
+  std::memset(h, 0, sizeof(*h));
+  h->p = *p;
+  const uint32_t L = (uint32_t)p->L;
+  h->N = (long long)L * L * L;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->ring_cap = kRingCap3;
+#define CREATE_CHECK(expr)                                                        \
+  do {                                                                            \
+    cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      int code_ = (e_ == cudaErrorMemoryAllocation) ? CVF_ENOMEM : CVF_ECUDA;     \
+      set_error(code_, "%s failed: %s", #expr, cudaGetErrorString(e_));           \
+      release3(h);                                                                \
+      return code_;                                                               \
+    }                                                                             \
+  } while (0)
+  CREATE_CHECK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (dev_state) {
+    h->state = reinterpret_cast<uint32_t*>(dev_state);
+    h->own_state = false;
+  } else {
+    CREATE_CHECK(cudaMalloc(&h->state, sizeof(uint32_t) * (size_t)h->N));
+    h->own_state = true;
+  }
+  CREATE_CHECK(cudaMalloc(&h->ctrl, sizeof(Ctrl)));
+  CREATE_CHECK(cudaMalloc(&h->ring, sizeof(cvf_obs) * (size_t)h->ring_cap));
+  CREATE_CHECK(cudaMalloc(&h->obs_dev, sizeof(cvf_obs)));
+  CREATE_CHECK(cudaMalloc(&h->table_dev, sizeof(unsigned long long) * 66));
+  CREATE_CHECK(cudaMalloc(&h->vol_dev, sizeof(VolumeArgs)));
+  CREATE_CHECK(cudaMalloc(&h->rc_dev, sizeof(unsigned long long) * 10));
+  CREATE_CHECK(cudaMallocHost(&h->host_pinned, 4096));
+
+  uint64_t table[66];
+  threshold_table3(p, table);
+  h->cmp64 = false;
+  for (int i = 0; i < 66; ++i)
+    if (table[i] == 0) h->cmp64 = true;
+  VolumeArgs va;
+  fill_volume_args3(p, h->N, d2, mult, &va);
+  CREATE_CHECK(cudaMemcpyAsync(h->table_dev, table, sizeof(table), cudaMemcpyHostToDevice,
+                               h->stream));
+  CREATE_CHECK(cudaMemcpyAsync(h->vol_dev, &va, sizeof(va), cudaMemcpyHostToDevice, h->stream));
+  CREATE_CHECK(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+
+  Args3& A = h->args;
+  A.state = h->state;
+  A.ctrl = h->ctrl;
+  A.table = h->table_dev;
+  A.vol = h->vol_dev;
+  A.ring = h->ring;
+  A.ring_cap = h->ring_cap;
+  A.keys = make_round_keys(p->seed);
+  A.L = L;
+  A.L2 = L * L;
+  A.N = (uint32_t)h->N;
+  A.groups = (uint32_t)((h->N + 3) / 4);
+  A.G = L / 4u;
+  A.q = (uint32_t)p->q;
+  h->aligned = (L % 4u) == 0u;
+  A.div_G = make_fastdiv(h->aligned ? A.G : 1u);
+  A.div_L = make_fastdiv(L);
+  A.div_L2 = make_fastdiv(L * L);
+
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel(h->aligned, h->cmp64),
+                                                    kThreads3, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const long long blocks = ((long long)A.groups + kThreads3 - 1) / kThreads3;
+  h->grid = (int)std::max<long long>(1, std::min<long long>(blocks, (long long)sm_count() * per_sm));
+  h->grid_count = (int)std::max<long long>(
+      1, std::min<long long>((h->N + kThreads3 - 1) / kThreads3, (long long)sm_count() * 8));
+
+  const int gi = (int)std::max<long long>(
+      1, std::min<long long>(((long long)A.groups + kThreads3 - 1) / kThreads3,
+                             (long long)sm_count() * 8));
+  k_init3<<<gi, kThreads3, 0, h->stream>>>(h->state, A.N, A.groups, A.q,
+                                            p->init == CVF_INIT_RANDOM ? 1 : 0, A.keys);
+  k_set_ctrl<<<1, 32, 0, h->stream>>>(h->vol_dev, h->ctrl, (double)h->N * p->v_iso_init, 0,
+                                      h->N);
+  rc = recount_into_ctrl3(h);
+  if (rc) {
+    release3(h);
+    return rc;
+  }
+  CREATE_CHECK(cudaGetLastError());
+  CREATE_CHECK(cudaStreamSynchronize(h->stream));
+#undef CREATE_CHECK
+  *out = h;
+  return CVF_OK;
+}
+
+int cvf3_sweep(cvf3_handle* h, int64_t n_sweeps, int32_t record_every) {
+  if (!h) return set_error(CVF_EINVAL, "handle is NULL");
+  if (n_sweeps < 0 || record_every < 0)
+    return set_error(CVF_EINVAL, "n_sweeps=%lld, record_every=%d must be >= 0",
+                     (long long)n_sweeps, record_every);
+  if (n_sweeps == 0) return CVF_OK;
+  k_set_record<<<1, 32, 0, h->stream>>>(h->ctrl, record_every);
+  long long left = n_sweeps;
+  if (left >= kGraphSteps3) {
+    const int rc = build_graph3(h);
+    if (rc) return rc;
+    while (left >= kGraphSteps3) {
+      CVF_CUDA_CHECK(cudaGraphLaunch(h->graph, h->stream));
+      left -= kGraphSteps3;
+    }
+  }
+  for (; left > 0; --left) enqueue_step3(h, h->stream);
+  CVF_CUDA_CHECK(cudaGetLastError());
+  return CVF_OK;
+}
+
+int cvf3_observables(cvf3_handle* h, cvf_obs* out) {
+  if (!h || !out) return set_error(CVF_EINVAL, "NULL argument");
+  CVF_CUDA_CHECK(cudaMemsetAsync(h->rc_dev, 0, sizeof(unsigned long long) * 10, h->stream));
+  k_count3<<<h->grid_count, kThreads3, 0, h->stream>>>(h->state, h->args.L, h->args.L2,
+                                                        h->args.N, h->args.div_L, h->args.div_L2,
+                                                        nullptr, h->rc_dev);
+  k_observables3<<<1, 32, 0, h->stream>>>(h->vol_dev, h->ctrl, h->rc_dev, h->obs_dev);
+  CVF_CUDA_CHECK(cudaGetLastError());
+  CVF_CUDA_CHECK(cudaMemcpyAsync(h->host_pinned, h->obs_dev, sizeof(cvf_obs),
+                                 cudaMemcpyDeviceToHost, h->stream));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  std::memcpy(out, h->host_pinned, sizeof(cvf_obs));
+  return CVF_OK;
+}
+
+int cvf3_drain_series(cvf3_handle* h, cvf_obs* host, int64_t cap, int64_t* n) {
+  if (!h || !n || cap < 0 || (cap > 0 && !host)) return set_error(CVF_EINVAL, "bad argument");
+  *n = 0;
+  Ctrl c;
+  CVF_CUDA_CHECK(cudaMemcpyAsync(h->host_pinned, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
+                                 h->stream));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  std::memcpy(&c, h->host_pinned, sizeof(Ctrl));
+  int status = CVF_OK;
+  if (c.ring_head - h->ring_tail > h->ring_cap) {
+    h->ring_tail = c.ring_head - h->ring_cap;
+    status = set_error(CVF_EOVERFLOW, "observable ring overwrote unread records");
+  }
+  const long long take = std::min<long long>(c.ring_head - h->ring_tail, cap);
+  long long done = 0;
+  while (done < take) {
+    const long long slot = (h->ring_tail + done) % h->ring_cap;
+    const long long chunk = std::min<long long>(take - done, h->ring_cap - slot);
+    CVF_CUDA_CHECK(cudaMemcpyAsync(host + done, h->ring + slot, sizeof(cvf_obs) * chunk,
+                                   cudaMemcpyDeviceToHost, h->stream));
+    done += chunk;
+  }
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  h->ring_tail += take;
+  *n = take;
+  return status;
+}
+
+int cvf3_get_state(cvf3_handle* h, uint32_t* host, size_t n) {
+  if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");
+  if ((long long)n != h->N) return set_error(CVF_EINVAL, "n=%zu, lattice has %lld cells", n, h->N);
+  CVF_CUDA_CHECK(cudaMemcpyAsync(host, h->state, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost,
+                                 h->stream));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  return CVF_OK;
+}
+
+int cvf3_set_state(cvf3_handle* h, const uint32_t* host, size_t n, double V_iso, int64_t sweep) {
+  if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");
+  if ((long long)n != h->N) return set_error(CVF_EINVAL, "n=%zu, lattice has %lld cells", n, h->N);
+  if (!(V_iso >= (double)h->N) || !std::isfinite(V_iso))
+    return set_error(CVF_EINVAL, "V_iso=%g must be >= N=%lld (hard core)", V_iso, h->N);
+  if (sweep < 0) return set_error(CVF_EINVAL, "sweep=%lld must be >= 0", (long long)sweep);
+  const uint32_t q = (uint32_t)h->p.q;
+  for (size_t i = 0; i < n; ++i) {
+    const uint32_t w = host[i];
+    bool ok = (w >> 18) == 0u;
+    for (int a = 0; a < 6 && ok; ++a) ok = ((w >> (3 * a)) & 7u) < q;
+    if (!ok) return set_error(CVF_EINVAL, "word %zu = 0x%x: arms must be < q=%u, bits 18..31 zero",
+                              i, w, q);
+  }
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  CVF_CUDA_CHECK(cudaMemcpyAsync(h->state, host, sizeof(uint32_t) * n, cudaMemcpyHostToDevice,
+                                 h->stream));
+  k_set_ctrl<<<1, 32, 0, h->stream>>>(h->vol_dev, h->ctrl, V_iso, sweep, h->N);
+  int rc = recount_into_ctrl3(h);
+  if (rc) return rc;
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  h->ring_tail = 0;
+  return CVF_OK;
+}
+
+int cvf3_recount(cvf3_handle* h, int64_t* n_hb_raw, int64_t* n_sigma) {
+  if (!h || !n_hb_raw || !n_sigma) return set_error(CVF_EINVAL, "NULL argument");
+  CVF_CUDA_CHECK(cudaMemsetAsync(h->rc_dev, 0, sizeof(unsigned long long) * 10, h->stream));
+  k_count3<<<h->grid_count, kThreads3, 0, h->stream>>>(h->state, h->args.L, h->args.L2,
+                                                        h->args.N, h->args.div_L, h->args.div_L2,
+                                                        h->rc_dev + 8, nullptr);
+  CVF_CUDA_CHECK(cudaGetLastError());
+  unsigned long long r[2];
+  CVF_CUDA_CHECK(cudaMemcpyAsync(h->host_pinned, h->rc_dev + 8, sizeof(r), cudaMemcpyDeviceToHost,
+                                 h->stream));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  std::memcpy(r, h->host_pinned, sizeof(r));
+  *n_hb_raw = (int64_t)r[0];
+  *n_sigma = (int64_t)r[1];
+  return CVF_OK;
+}
+
+int cvf3_state_device_ptr(cvf3_handle* h, void** dev_ptr) {
+  if (!h || !dev_ptr) return set_error(CVF_EINVAL, "NULL argument");
+  *dev_ptr = h->state;
+  return CVF_OK;
+}
+
+int cvf3_destroy(cvf3_handle* h) {
+  if (!h) return CVF_OK;
+  cudaStreamSynchronize(h->stream);
+  release3(h);
+  return CVF_OK;
+}
+
+}  // extern "C"

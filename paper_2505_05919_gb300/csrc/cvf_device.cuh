@@ -270,21 +270,33 @@ constexpr int kMaxShells = 256;
 
 struct VolumeArgs {
   int64_t N;
-  double epsilon, cutoff2;
+  double epsilon, cutoff2;       // cutoff2: cutoff^2 (2D) or cutoff^6 (3D)
   double J, J_sigma, v_HB, kT, P;
   double dV_max;
   int32_t volume_moves;
   int32_t nshell;
-  double shell_d2[kMaxShells];   // |d|^2 of the square-lattice shells, ascending
+  int32_t dim;                   // 3: cubic lattice; anything else: square lattice
+  int32_t pad_dim;
+  double shell_d2[kMaxShells];   // 2D: |d|^2 of the shells, ascending; 3D: |d|^6
   double S12[kMaxShells + 1];    // prefix sums of m / |d|^12 over the shells
   double S6[kMaxShells + 1];     // prefix sums of m / |d|^6
 };
 
-// u(v) = 2 eps [x^6 S12(n) - x^3 S6(n)], x = 1/v, n = number of shells with
-// |d|^2 v < cutoff^2: the LJ energy per cell of a monolayer of lattice
+// 2D: u(v) = 2 eps [x^6 S12(n) - x^3 S6(n)], x = 1/v, n = number of shells
+// with |d|^2 v < cutoff^2: the LJ energy per cell of a monolayer of lattice
 // spacing sqrt(v) (half of each pair per cell), shell by shell.
+// 3D: u(v) = 2 eps [x^4 S12(n) - x^2 S6(n)], n = number of shells with
+// |d|^6 v^2 < cutoff^6: the cubic lattice of spacing r = v^(1/3) (Sec. II.A),
+// tested without cube roots.
 __device__ __forceinline__ double lj_cell_energy(const VolumeArgs& V, double v) {
   int k = 0;
+  if (V.dim == 3) {
+    while (k < V.nshell && V.shell_d2[k] * v * v < V.cutoff2) ++k;
+    const double x = 1.0 / v;
+    const double x2 = x * x;
+    const double x4 = x2 * x2;
+    return (2.0 * V.epsilon) * (x4 * V.S12[k] - x2 * V.S6[k]);
+  }
   while (k < V.nshell && V.shell_d2[k] * v < V.cutoff2) ++k;
   const double x = 1.0 / v;
   const double x3 = x * x * x;
@@ -323,7 +335,7 @@ struct Ctrl {
   int ahead_g;
   int ahead_acc;
   int ahead_state;
-  int pad0;
+  int plan;             // cubic lattice: launch plan of the current step's six passes
   // per-step accumulators (zero between steps)
   unsigned long long acc_hb;
   unsigned long long acc_pairs;
@@ -421,16 +433,26 @@ __device__ __forceinline__ cvf_obs make_obs(const VolumeArgs& V, const Ctrl* ctl
 // All accesses go through a volatile view: in the batched kernel the
 // previous step of the same lattice was closed by another SM without a
 // kernel boundary in between.
+// DELTA = false: acc_hb / acc_pairs hold the step's totals (the square
+// lattice recounts its bonds in every sweep).  DELTA = true: they hold the
+// changes made by the accepted moves (two's complement), added to the
+// committed counts (the cubic lattice's layered passes).
+template <bool DELTA = false>
 __device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cvf_obs* ring,
                                               long long ring_cap, const RoundKeys& K) {
   volatile Ctrl* c = ctl;
   Ctrl s;  // committed state after this step
   const int every = c->record_every;
   const bool recorded = (every > 0) && ((c->sweep + 1) % every == 0);
-  s.n_hb_raw = (long long)c->acc_hb;
-  // N_sigma is counted by the sweep only on recorded steps; otherwise it is
-  // unknown (-1) until a recount (cvf_observables counts it on demand)
-  s.n_coop = recorded ? (long long)c->acc_pairs : -1;
+  if (DELTA) {
+    s.n_hb_raw = c->n_hb_raw + (long long)c->acc_hb;
+    s.n_coop = c->n_coop + (long long)c->acc_pairs;
+  } else {
+    s.n_hb_raw = (long long)c->acc_hb;
+    // N_sigma is counted by the sweep only on recorded steps; otherwise it is
+    // unknown (-1) until a recount (cvf_observables counts it on demand)
+    s.n_coop = recorded ? (long long)c->acc_pairs : -1;
+  }
   s.acc_sigma = c->acc_sigma + (long long)c->acc_moves;
   s.V_iso = c->next_V;
   s.u_cell = c->next_u;

@@ -26,13 +26,14 @@ def _declared():
         if fn.endswith(".h"):
             text = open(os.path.join(ROOT, "include", fn)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names |= set(re.findall(r"\b(cvf_[a-z0-9_]+)\s*\(", text))
+            names |= set(re.findall(r"\b(cvf3?_[a-z0-9_]+)\s*\(", text))
     return names
 
 
 def test_exports_every_declared_symbol(lib):
     names = _declared()
     assert "cvf_create" in names and "cvf_sweep" in names and "cvf_destroy" in names
+    assert "cvf3_create" in names and "cvf3_sweep" in names and "cvf3_destroy" in names
     for n in sorted(names):
         assert hasattr(lib, n), n
     # and the binding wraps each of them under the same name
@@ -85,3 +86,32 @@ def test_workloads_are_deterministic():
     assert int(((w >> 0) & 7).max()) < 6
     jobs = workloads.c5(n_jobs=50)
     assert all(jobs[i]["arrival"] <= jobs[i + 1]["arrival"] for i in range(49))
+
+
+# ------------------------------------------------------------ cubic lattice --
+def test_cvf3_params_physical(lib):
+    for T, P in ((270.0, 0.1), (330.0, 50.0)):
+        got = _capi.cvf3_params_physical(T, P)
+        want = oracle.physical_params3(T, P)
+        assert got.kT == pytest.approx(want.kT, rel=1e-15)
+        assert got.P == pytest.approx(want.P, rel=1e-15)
+        assert got.v_iso_init == want.v_iso_init == 2 ** 0.5
+        assert (got.schedule, got.rng_words, got.L) == (_capi.CVF_SCHED_LAYERED, 1, 16)
+
+
+@pytest.mark.parametrize("T,P", [(270, 0.1), (300, 0.1), (330, 50.0)])
+@pytest.mark.parametrize("q", [2, 6, 8])
+def test_cvf3_threshold_table_equals_oracle(lib, T, P, q):
+    op = oracle.physical_params3(T, P, q=q)
+    got = np.array(_capi.cvf3_threshold_table(_capi.cvf_params(**asdict(op))), dtype=np.uint64)
+    assert np.array_equal(got, oracle.threshold_table3(op).reshape(-1))
+
+
+@pytest.mark.parametrize("field,value", [("schedule", 0), ("rng_words", 2), ("L", 1025), ("L", 1),
+                                         ("q", 9), ("kT", 0.0), ("v_iso_init", 0.9)])
+def test_cvf3_rejects_bad_params(lib, field, value):
+    p = _capi.cvf3_params_physical(300.0, 0.1)
+    setattr(p, field, value)
+    with pytest.raises(_capi.CvfError) as e:
+        _capi.cvf3_threshold_table(p)
+    assert e.value.code == _capi.CVF_EINVAL

@@ -1,0 +1,150 @@
+"""GPU parity of the cubic-lattice path (``cvf3_*``) against the 3D oracle.
+
+Same seeded inputs on both sides; the packed lattice, every integer counter
+and N_q' must be bit-identical, FP64 observables within rel 1e-12 (both sides
+evaluate the same IEEE operations in the same order, so they are in practice
+equal).  Sizes cover the 16-byte-vector path (L % 4 == 0) and the per-cell
+path (odd L, L = 2 with a neighbour on both sides, N % 4 != 0 tails), the
+graph-captured steps and the steps launched one by one, both inits, three
+(T, P) points, gate flips of the volume move, the 64-bit threshold compare,
+checkpoint/resume, and the paper's largest cube (260^3 = 17 576 000 cells).
+"""
+from dataclasses import asdict
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_05919_gb300 import Lattice3, _capi, params_from_dict
+
+pytestmark = pytest.mark.gpu
+
+INT_KEYS = ("sweep", "n_hb", "n_hb_raw", "n_coop", "acc_sigma", "acc_volume", "g")
+FP_KEYS = ("V_iso", "V", "U_LJ", "H")
+REL = 1e-12
+
+
+def _same(got, want, ctx=""):
+    for k in INT_KEYS:
+        assert got[k] == want[k], (ctx, k, got[k], want[k])
+    assert list(got["n_state"]) == list(want["n_state"]), ctx
+    for k in FP_KEYS:
+        assert abs(got[k] - want[k]) <= REL * abs(want[k]), (ctx, k, got[k], want[k])
+
+
+def _run_both(op, steps, record_every=0):
+    ref = oracle.Oracle3(op)
+    want_series = ref.run(steps, record_every)
+    with Lattice3(params_from_dict(asdict(op))) as lat:
+        lat.sweep(steps, record_every)
+        got_series, overflow = lat.drain()
+        assert not overflow
+        return (lat.state(), lat.observables(), lat.recount(), got_series), \
+               (ref.state(), ref.observables(), ref.recount(), want_series)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4, 5, 6, 8, 12, 16])
+@pytest.mark.parametrize("init", [oracle.INIT_RANDOM, oracle.INIT_ORDERED])
+def test_lattice3_matches_oracle(L, init):
+    op = oracle.physical_params3(300.0, 0.1, L=L, init=init, seed=100 + L)
+    got, want = _run_both(op, 45)
+    assert np.array_equal(got[0], want[0])
+    _same(got[1], want[1], (L, init))
+    assert got[2] == want[2] == (want[1]["n_hb_raw"], want[1]["n_coop"])
+
+
+@pytest.mark.parametrize("T,P", [(270.0, 0.1), (300.0, 25.0), (330.0, 50.0)])
+@pytest.mark.parametrize("q", [3, 6, 8])
+def test_lattice3_state_points(T, P, q):
+    op = oracle.physical_params3(T, P, L=8, q=q, seed=int(T) + q, dv_max_frac=0.05)
+    got, want = _run_both(op, 40)
+    assert np.array_equal(got[0], want[0])
+    _same(got[1], want[1], (T, P, q))
+
+
+@pytest.mark.parametrize("L,every", [(5, 3), (8, 1), (12, 7)])
+def test_lattice3_series_matches_oracle(L, every):
+    op = oracle.physical_params3(285.0, 10.0, L=L, seed=7 + L, dv_max_frac=0.05)
+    got, want = _run_both(op, 70, record_every=every)
+    assert len(got[3]) == len(want[3]) == 70 // every
+    for i, (g, w) in enumerate(zip(got[3], want[3])):
+        _same(g, w, ("record", i))
+
+
+@pytest.mark.parametrize("L,P,kT", [(2, 1.2, 3.0), (3, 2.0, 5.0), (4, 3.0, 5.0)])
+def test_lattice3_gate_flips(L, P, kT):
+    # small hot cubes near v = 2 whose volume moves cross the liquid/gas gate,
+    # so the move of the next step is sometimes decided only after the bonds
+    op = oracle.params3(L=L, kT=kT, P=P, epsilon=0.0, v_iso_init=1.9, dv_max_frac=0.2, seed=31)
+    got, want = _run_both(op, 300, record_every=1)
+    gates = [r["g"] for r in want[3]]
+    assert sum(a != b for a, b in zip(gates, gates[1:])) >= 3
+    assert np.array_equal(got[0], want[0])
+    for i, (g, w) in enumerate(zip(got[3], want[3])):
+        _same(g, w, ("record", i))
+
+
+def test_lattice3_cmp64_ground_state():
+    # kT -> 0: thresholds of 0 (the 64-bit compare) and a frozen ordered cube
+    op = oracle.params3(L=8, kT=1e-3, init=oracle.INIT_ORDERED, dv_max_frac=0.001, seed=3)
+    assert (oracle.threshold_table3(op) == 0).any()
+    got, want = _run_both(op, 40)
+    assert not got[0].any() and np.array_equal(got[0], want[0])
+    _same(got[1], want[1])
+    assert got[1]["n_hb_raw"] == 3 * 512 and got[1]["n_coop"] == 15 * 512
+
+
+def test_lattice3_checkpoint_resume():
+    op = oracle.physical_params3(300.0, 0.1, L=12, seed=41, dv_max_frac=0.05)
+    mid = oracle.Oracle3(op)
+    mid.run(17)
+    ob = mid.observables()
+    ref = oracle.Oracle3(op)
+    ref.run(50)
+    with Lattice3(params_from_dict(asdict(op))) as lat:
+        lat.sweep(3)                     # overwritten by set_state
+        lat.set_state(mid.state(), ob["V_iso"], ob["sweep"])
+        assert lat.observables()["n_hb_raw"] == ob["n_hb_raw"]
+        lat.sweep(33)
+        s, o = lat.state(), lat.observables()
+    assert np.array_equal(s, ref.state())
+    want = ref.observables()
+    for k in ("sweep", "n_hb_raw", "n_coop", "g", "n_state"):
+        assert o[k] == want[k], k
+    for k in FP_KEYS:
+        assert abs(o[k] - want[k]) <= REL * abs(want[k]), k
+
+
+def test_lattice3_calls_split_like_one_run():
+    op = oracle.physical_params3(300.0, 0.1, L=6, seed=5)
+    ref = oracle.Oracle3(op)
+    ref.run(80)
+    with Lattice3(params_from_dict(asdict(op))) as lat:
+        for n in (0, 1, 31, 32, 5, 11):
+            lat.sweep(n)
+        assert np.array_equal(lat.state(), ref.state())
+        _same(lat.observables(), ref.observables())
+
+
+def test_lattice3_rejects_bad_state():
+    op = oracle.physical_params3(300.0, 0.1, L=4, q=6)
+    with Lattice3(params_from_dict(asdict(op))) as lat:
+        good = lat.state()
+        for bad_word in (6, 6 << 15, 1 << 18):
+            w = good.copy().reshape(-1)
+            w[5] = bad_word
+            with pytest.raises(_capi.CvfError):
+                lat.set_state(w, 64 * 1.5)
+        with pytest.raises(_capi.CvfError):
+            lat.set_state(good, 63.0)     # V_iso below the hard core N v0
+        assert np.array_equal(lat.state(), good)
+
+
+@pytest.mark.parametrize("L,steps", [(130, 3), (128, 4), (260, 2)])
+def test_lattice3_large_cubes(L, steps):
+    # full-size parity: the largest cube of the paper's scaling runs (260^3)
+    # and a large cube on the per-cell path (130^3), whole lattice compared
+    op = oracle.physical_params3(300.0, 0.1, L=L, seed=3)
+    got, want = _run_both(op, steps)
+    assert np.array_equal(got[0], want[0])
+    _same(got[1], want[1], L)
