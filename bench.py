@@ -11,6 +11,10 @@ the timed region starts; L2 is flushed between timed steps.
   e2e    = the same through the C ABI with host buffers: set_state (H2D),
            sweep, get_state (D2H) and observables inside the timed region
   --impl reference   times the CPU oracle on the same metric (bounded sample)
+
+The line also carries the batched (256 replicas, one persistent launch),
+serving (continuous batching of arriving jobs) and cubic (the paper's own 3D
+model at 260^3) measurements.
 """
 from __future__ import annotations
 
@@ -43,8 +47,13 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=1000, help="MC steps per benchmark step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-sweeps", type=int, default=10)
-    ap.add_argument("--mode", default="full", choices=["full", "kernel"],
-                    help="kernel: one lattice, warm-up then timed sweeps only (profiling case)")
+    ap.add_argument("--mode", default="full", choices=["full", "kernel", "kernel3"],
+                    help="kernel / kernel3: one square / cubic lattice, warm-up then timed "
+                         "sweeps only (profiling cases)")
+    ap.add_argument("--L3", type=int, default=260,
+                    help="cube side of the 3D measurement (260: the paper's largest lattice)")
+    ap.add_argument("--cubic-sweeps", type=int, default=320,
+                    help="timed MC steps of the 3D measurement (0: skip)")
     ap.add_argument("--batch-sweeps", type=int, default=5000,
                     help="steps per replica in the batched measurement (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
@@ -232,6 +241,97 @@ def run_kernel_mode(args):
     return 0
 
 
+# The paper's own 3D figure (context, other hardware): 280 ms per Metropolis
+# MC step at N = 260^3 on an RTX 3060, cuRAND generation and copies included.
+PAPER_3D_MS_PER_STEP_260 = 280.0
+# DRAM bytes (read + write) of the k_pass3 launches of one MC step at
+# L = 260 from an ncu capture of the current kernel; None until taken.
+PASS3_DRAM_BYTES_260 = None
+
+
+def run_kernel3_mode(args):
+    """Profiling case of the cubic lattice: one cube (random init seed 3,
+    300 K, 0.1 MPa), `warmup` MC steps, then `steps` timed with CUDA events."""
+    import torch
+    from paper_2505_05919_gb300 import Lattice3, params3, _capi, build as libbuild
+    libbuild.build()
+    _capi.load()
+    stream = torch.cuda.Stream()
+    lat = Lattice3(params3(300.0, 0.1, L=args.L3, seed=3), stream=stream)
+    lat.sweep(args.warmup)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat.sweep(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    o = lat.observables()
+    lat.close()
+    print(json.dumps({"mode": "kernel3", "L": args.L3, "sweeps": args.steps, "ms": ms,
+                      "updates_per_ns": 6.0 * args.L3 ** 3 * args.steps / (ms * 1e6),
+                      "n_hb_raw": o["n_hb_raw"], "n_coop": o["n_coop"]}))
+    return 0
+
+
+def measure_cubic(args, rank, world):
+    """The paper's own 3D model at its largest size (260^3, q = 6, 300 K,
+    0.1 MPa, random init seed 3): MC steps of the six-arm layered schedule
+    timed with CUDA events on the lattice's stream (the 70 MB lattice stays
+    in HBM/L2), next to the paper's 280 ms per step on an RTX 3060 and the 3D
+    oracle on a bounded sample."""
+    import torch
+    from paper_2505_05919_gb300 import Lattice3, dist, params3
+    L, S = args.L3, args.cubic_sweeps
+    stream = torch.cuda.Stream()
+    lat = Lattice3(params3(300.0, 0.1, L=L, seed=3 + dist.seed_offset(rank)), stream=stream)
+    lat.sweep(64)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.sweep(S)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1) / S)
+    per_step = statistics.median(ms)
+    dev_s = dist.max_over_ranks(per_step / 1e3)
+    o = lat.observables()
+    lat.close()
+    upd = 6.0 * L ** 3
+    out = {"value": upd * world / (dev_s * 1e9), "unit": UNIT, "L": L, "N": L ** 3,
+           "ms_per_mc_step": dev_s * 1e3, "sweeps_timed": S,
+           "paper_ms_per_mc_step": PAPER_3D_MS_PER_STEP_260 if L == 260 else None,
+           "paper_hardware": "RTX 3060 (sm_86), cuRAND and copies included",
+           "launches_per_mc_step": 4,
+           "roofline": {"bound": "alu", "achieved": ALU_OPS_PER_UPDATE * upd / (per_step * 1e-3) / 1e12,
+                        "peak": ALU_PEAK_TOPS, "unit": "Tintop/s",
+                        "frac": ALU_OPS_PER_UPDATE * upd / (per_step * 1e-3) / 1e12 / ALU_PEAK_TOPS,
+                        "traffic": PASS3_DRAM_BYTES_260 if L == 260 else None,
+                        "kernel": "k_pass3 (four launches per MC step)"},
+           "acceptance": o["acc_sigma"] / max(1.0, upd * o["sweep"]),
+           "workload": "CVF 3D cubic lattice L=%d q=6, layered six-arm schedule, random init "
+                       "(seed 3), 300 K, 0.1 MPa" % L}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            import oracle
+            Lc = min(L, 128)
+            ref = oracle.Oracle3(oracle.physical_params3(300.0, 0.1, L=Lc, seed=3))
+            t0 = time.perf_counter()
+            ref.run(3)
+            dt = time.perf_counter() - t0
+            out["cpu_baseline"] = {"value": 6.0 * Lc ** 3 * 3 / (dt * 1e9), "unit": UNIT, "cores": 1,
+                                   "kind": "oracle",
+                                   "sample": "3D oracle, L=%d, 3 MC steps from the random init, "
+                                             "one thread" % Lc}
+        except Exception as e:
+            out["cpu_baseline"] = {"value": None, "error": str(e)}
+    return out
+
+
 def measure_batched(args, rank):
     """Configuration 4: 256 replicas (L from {32..512}, T x P grid), the same
     number of steps each, in one persistent launch per call; tile shape from
@@ -323,6 +423,8 @@ def main():
         return run_reference(args)
     if args.mode == "kernel":
         return run_kernel_mode(args)
+    if args.mode == "kernel3":
+        return run_kernel3_mode(args)
     import numpy as np
     import torch
     from paper_2505_05919_gb300 import dist
@@ -423,6 +525,7 @@ def main():
     e2e = {"value": 4.0 * L * L * S / (e2e_s * 1e9), "unit": UNIT,
            "h2d_bytes_per_step": 2 * L * L, "d2h_bytes_per_step": 2 * L * L + 96}
 
+    cubic = measure_cubic(args, rank, world) if args.cubic_sweeps > 0 else None
     batched = measure_batched(args, rank) if args.batch_sweeps > 0 else None
     serving = measure_serving(args, rank) if args.serve_seconds > 0 else None
 
@@ -450,6 +553,7 @@ def main():
             "gpu_launches": args.steps * (S * launches_per_sweep + 1),
             "batched": batched,
             "serving": serving,
+            "cubic": cubic,
             "clocks": clocks,
             "wall_s": t_wall,
             "per_sweep_ms": per_sweep_ms,

@@ -268,7 +268,8 @@ int cvf_batch_destroy(cvf_batch *b);
  * cooperative pairs per cell in Eq. (H).  eta_ij is identically 1 (the
  * checkerboard-cube eta update of App. A is not built).
  *   - Layout: cell c = x + L (y + L z), one uint32 word per cell holding
- *     sigma of arm a in bits [3a, 3a+3) (bits 18..31 zero).  Arms 0..5 =
+ *     sigma of arm a in bits [4a, 4a+3) -- one nibble per arm, bits 4a+3 and
+ *     24..31 zero.  Arms 0..5 =
  *     left, right, front, back, top, bottom point to +x, -x, +y, -y, +z, -z
  *     (Sec. II.C's coalescing example and Table S1: arm 0 of cell c pairs
  *     with arm 1 of cell c+1, arm 4 of cell (1,0,0) with arm 5 of (1,0,1)).
@@ -322,7 +323,7 @@ int cvf3_observables(cvf3_handle *h, cvf_obs *out);
 int cvf3_drain_series(cvf3_handle *h, cvf_obs *host, int64_t cap, int64_t *n);
 
 /* Copies / replaces the lattice (n = L^3 words, layout above).  set_state
- * validates every word on the host (arms < q, bits 18..31 zero), sets V_iso
+ * validates every word on the host (arms < q, other bits zero), sets V_iso
  * (>= N) and the step counter, recounts, clears the acceptance counters and
  * the ring.  Both synchronise. */
 int cvf3_get_state(cvf3_handle *h, uint32_t *host, size_t n);

@@ -83,8 +83,9 @@ void orc_window_run(const orc_params *p, uint16_t *w, int32_t x0, int32_t y0,
 int64_t orc_volume_chain(const orc_params *p, double V_iso, int64_t step0,
                          int64_t K, double *V_out, int32_t *g_out,
                          int64_t *acc_out);
-/* ---- 3D variant (cvf_oracle3.c): cubic lattice, six arms per cell packed
-   3 bits each in one uint32 word, layered schedule. ---- */
+/* ---- 3D variant (cvf_oracle3.c): cubic lattice, six arms per cell, one
+   nibble each (sigma in its low 3 bits) in one uint32 word, layered
+   schedule. ---- */
 typedef struct {
   orc_params p;
   int64_t N;

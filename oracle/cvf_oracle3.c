@@ -11,6 +11,8 @@
  * step is written in the order of the paper, one variable at a time.
  *
  * Readings (besides the 2D oracle's, which carry over):
+ *   - state: one uint32 word per cell, sigma of arm a in bits [4a, 4a+3)
+ *     (one nibble per arm, bit 4a+3 and bits 24..31 zero);
  *   - cell c = x + L (y + L z) and arms 0..5 = left, right, front, back,
  *     top, bottom (Sec. II.C; the cell coordinates of Table S1).  The
  *     coalescing example of Sec. II.C (left arms of cells 0..15 meet the
@@ -46,7 +48,7 @@
 
 #include "cvf_oracle.h"
 
-static uint32_t o3_arm(uint32_t w, int a) { return (w >> (3 * a)) & 7u; }
+static uint32_t o3_arm(uint32_t w, int a) { return (w >> (4 * a)) & 7u; }
 
 static void o3_philox(const orc_params *p, uint32_t word0, int64_t step, uint32_t tag,
                       uint32_t out[4]) {
@@ -198,7 +200,7 @@ int orc3_init(orc3_state *st, const orc_params *p, uint32_t *w) {
     uint32_t word = 0;
     if (p->init == ORC_INIT_RANDOM)
       for (int a = 0; a < 6; ++a)
-        word |= o3_scale(o3_word(p, c, 0, 16u + (uint32_t)a), (uint32_t)p->q) << (3 * a);
+        word |= o3_scale(o3_word(p, c, 0, 16u + (uint32_t)a), (uint32_t)p->q) << (4 * a);
     w[c] = word;
   }
   o3_start(st, p, w, (double)N * p->v_iso_init, 0);
@@ -292,7 +294,7 @@ static void o3_update_arm(orc3_state *st, int64_t c, int a) {
     dc += (sp == sb) - (s == sb);
   }
   if ((uint64_t)u < st->table[st->g][dhb + 1][dc + 5]) {
-    st->w[c] = (wc & ~(7u << (3 * a))) | (sp << (3 * a));
+    st->w[c] = (wc & ~(7u << (4 * a))) | (sp << (4 * a));
     st->n_hb_raw += dhb;
     st->n_coop += dc;
     st->acc_sigma += 1;

@@ -1,6 +1,6 @@
 // cvf3.cu -- the paper's own 3D CVF Metropolis (arXiv:2505.05919, Sec. II):
-// a periodic cubic lattice, six bonding indices per cell packed 3 bits each
-// in one uint32 word, the layered partition of Sec. II.C (the six arm
+// a periodic cubic lattice, six bonding indices per cell, one nibble each in
+// one uint32 word, the layered partition of Sec. II.C (the six arm
 // domains updated one after the other in an order drawn every MC step), the
 // counts of Eq. (H) kept incrementally, and the isobaric volume move of
 // Sec. II.B with the cubic-lattice Lennard-Jones energy.
@@ -37,7 +37,9 @@ constexpr int kGraphSteps3 = 32;
 constexpr long long kRingCap3 = 65536;
 constexpr uint32_t kTagArm0 = 8u;       // draws of arm a: Philox tag 8 + a
 constexpr uint32_t kTagInit0 = 16u;     // random init of arm a: tag 16 + a
-constexpr uint32_t kRep6 = 0x9249u;     // bit 3b set for b = 0..5
+constexpr uint32_t kR7 = 0x1111111u;    // 1 in nibbles 0..6
+constexpr uint32_t kM7 = 0x8888888u;    // bit 3 of nibbles 0..6
+constexpr uint32_t kArmBits = 0x777777u;  // the sigma bits of the six arm nibbles
 constexpr int kMaxSide3 = 1024;
 
 // Unsigned division by an invariant d (1 <= d < 2^31) for any 32-bit n,
@@ -122,39 +124,58 @@ __device__ int plan_arms(uint32_t plan, int j, int* arms) {
 }
 
 // ---------------------------------------------------------------------------
-// Metropolis update of arm `a` (shift sh = 3a) of one cell (Sec. II.C with
-// Eq. H): w the cell word, n the partner arm's value (arm a^1 of the
-// neighbour in direction a), r the cell's 32-bit draw.  Proposal
-// sigma' = (sigma + 1 + k) mod q with w (q-1) = k 2^32 + u; dN_sigma from
-// the equal arms of the word: bit 3b of (x | x>>1 | x>>2) & 0x9249, x = w ^
-// (v * 0x9249), is set when arm b differs from v, so
-// dN_sigma = popc(differ from sigma) - popc(differ from sigma') + 1.
+// Metropolis update of arm a of one cell (Sec. II.C with Eq. H).
+//   w     the cell word (sigma_b in nibble b), nw the neighbour's word in
+//         direction a (its nibble a^1 is the partner arm), r the cell's draw
+//   sh    4a; nsh = 24 - 4 (a^1) moves the partner nibble to nibble 6;
+//   amask 0xF << 4a
+// Proposal: w (q-1) = k 2^32 + u, sigma' from the shared table
+// prop[8 sigma + k] = ((sigma + 1 + k) mod q) * 0x1111111 (sigma' in nibbles
+// 0..6).  With the partner in nibble 6 of wn, f(v) = (((wn ^ v R) | M) - R)
+// & M has bit 3 of nibble b set iff nibble b differs from v (no borrow
+// crosses a nibble since every nibble is >= 8 before the subtraction).  So
+// popc f(sigma) = A_s + b_s and popc f(sigma') = A_p + b_p, with A_v the arms
+// differing from v and b_v = [partner != v] (bit 27); dN_HB = b_s - b_p and
+// dN_sigma = A_s - A_p + 1, and the threshold row index
+// 11 dN_HB + dN_sigma + 16 = (popc f_s + 10 b_s) - (popc f_p + 10 b_p) + 17.
+// The row holds {T - 1, packed count change}; an accepted move adds the
+// latter ((1 << 24) + ((dN_HB + 1) << 16) + dN_sigma + 5) to pk.
 // ---------------------------------------------------------------------------
+struct Row3 {
+  uint32_t t;      // T - 1 (every T >= 1 on this path) or unused (64-bit path)
+  uint32_t delta;  // packed count change of an accepted move
+};
+
 template <bool CMP64>
-__device__ __forceinline__ uint32_t update_arm3(uint32_t w, uint32_t n, uint32_t r, uint32_t sh,
-                                                uint32_t q, const uint32_t* T32,
-                                                const unsigned long long* T64, int& dhb_sum,
-                                                int& dc_sum, uint32_t& nacc) {
+__device__ __forceinline__ uint32_t update_arm3(uint32_t w, uint32_t nw, uint32_t r, uint32_t sh,
+                                                uint32_t nsh, uint32_t amask, uint32_t qm1,
+                                                const uint32_t* prop, const Row3* rows,
+                                                const unsigned long long* T64, uint32_t& pk) {
   const uint32_t s = (w >> sh) & 7u;
-  const uint32_t k = __umulhi(r, q - 1u);
-  const uint32_t u = r * (q - 1u);
-  uint32_t sp = s + 1u + k;
-  sp = (sp >= q) ? sp - q : sp;
-  const int dhb = (int)(sp == n) - (int)(s == n);
-  const uint32_t xs = w ^ (s * kRep6);
-  const uint32_t xp = w ^ (sp * kRep6);
-  const uint32_t ds = (xs | (xs >> 1) | (xs >> 2)) & kRep6;
-  const uint32_t dp = (xp | (xp >> 1) | (xp >> 2)) & kRep6;
-  const int dc = __popc(ds) - __popc(dp) + 1;
-  const int idx = dhb * 11 + dc + 16;  // (dN_HB + 1) * 11 + dN_sigma + 5
-  const bool accept = CMP64 ? ((unsigned long long)u < T64[idx]) : (u <= T32[idx]);
+  const uint32_t k = __umulhi(r, qm1);
+  const uint32_t u = r * qm1;
+  const uint32_t sR = s * kR7;
+  const uint32_t spR = prop[s * 8u + k];
+  const uint32_t wn = w | ((nw << nsh) & 0x7000000u);
+  const uint32_t fs = (((wn ^ sR) | kM7) - kR7) & kM7;
+  const uint32_t fp = (((wn ^ spR) | kM7) - kR7) & kM7;
+  const int idx = (int)(__popc(fs) + 10u * (fs >> 27)) - (int)(__popc(fp) + 10u * (fp >> 27)) + 17;
+  const Row3 row = rows[idx];
+  const bool accept = CMP64 ? ((unsigned long long)u < T64[idx]) : (u <= row.t);
   if (accept) {
-    w ^= (s ^ sp) << sh;
-    dhb_sum += dhb;
-    dc_sum += dc;
-    ++nacc;
+    w ^= (sR ^ spR) & amask;
+    pk += row.delta;
   }
   return w;
+}
+
+// Adds a group's packed count changes to the thread's totals.
+__device__ __forceinline__ void unpack_counts(uint32_t& pk, uint32_t& nacc, uint32_t& hb_b,
+                                              uint32_t& dc_b) {
+  nacc += pk >> 24;
+  hb_b += (pk >> 16) & 0xFFu;
+  dc_b += pk & 0xFFFFu;
+  pk = 0;
 }
 
 // N_q' of the four final cell words of a group, added to the block's eight
@@ -165,7 +186,7 @@ __device__ __forceinline__ uint32_t update_arm3(uint32_t w, uint32_t n, uint32_t
 __device__ __forceinline__ uint32_t count_word(uint32_t w) {
   uint32_t c = 0;
 #pragma unroll
-  for (int b = 0; b < 6; ++b) c += 1u << (4u * ((w >> (3 * b)) & 7u));
+  for (int b = 0; b < 6; ++b) c += 1u << (4u * ((w >> (4 * b)) & 7u));
   return c;
 }
 
@@ -196,7 +217,8 @@ __device__ __forceinline__ void hist_group(uint32_t w0, uint32_t w1, uint32_t w2
 // ---------------------------------------------------------------------------
 template <bool ALIGNED, bool CMP64>
 __global__ void __launch_bounds__(kThreads3) k_pass3(Args3 A, int launch) {
-  __shared__ uint32_t sT32[33];
+  __shared__ Row3 sRows[33];
+  __shared__ uint32_t sProp[64];
   __shared__ unsigned long long sT64[CMP64 ? 33 : 1];
   __shared__ int s_arm[3];
   __shared__ int s_n, s_rec;
@@ -244,22 +266,28 @@ __global__ void __launch_bounds__(kThreads3) k_pass3(Args3 A, int launch) {
   const long long step = ctl->sweep;
   const int g = ctl->next_g;
   const bool rec = s_rec != 0;
+  const uint32_t q = A.q;
   if (threadIdx.x < 33) {
     const unsigned long long t = A.table[g * 33 + threadIdx.x];
-    if (CMP64)
-      sT64[threadIdx.x] = t;
-    else
-      sT32[threadIdx.x] = (uint32_t)(t - 1ull);  // every t >= 1 here
+    if (CMP64) sT64[threadIdx.x] = t;
+    const int dhb = (int)threadIdx.x / 11 - 1, dc = (int)threadIdx.x % 11 - 5;
+    sRows[threadIdx.x].t = (uint32_t)(t - 1ull);  // every t >= 1 unless CMP64
+    sRows[threadIdx.x].delta = (1u << 24) + ((uint32_t)(dhb + 1) << 16) + (uint32_t)(dc + 5);
+  } else if (threadIdx.x >= 64 && threadIdx.x < 128) {
+    const uint32_t s = (threadIdx.x - 64) >> 3, k = (threadIdx.x - 64) & 7u;
+    uint32_t sp = s + 1u + k;
+    while (sp >= q) sp -= q;
+    sProp[threadIdx.x - 64] = (s < q && k + 1u < q) ? sp * kR7 : 0u;
   }
   if (threadIdx.x < 8) s_hist[threadIdx.x] = 0;
   __syncthreads();
   const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
   const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
-  const uint32_t q = A.q;
+  const uint32_t qm1 = q - 1u;
   const uint32_t first_block = (launch == 0) ? 1u : 0u;
   const uint32_t nblk = gridDim.x - first_block;
-  int dhb_sum = 0, dc_sum = 0;
-  uint32_t nacc = 0;
+  // accepted moves and the biased sums of their dN_HB + 1 and dN_sigma + 5
+  uint32_t nacc = 0, hb_b = 0, dc_b = 0, pk = 0;
   uint32_t* __restrict__ st = A.state;
   for (uint32_t gi = (blockIdx.x - first_block) * kThreads3 + threadIdx.x; gi < A.groups;
        gi += nblk * kThreads3) {
@@ -273,7 +301,8 @@ __global__ void __launch_bounds__(kThreads3) k_pass3(Args3 A, int launch) {
       uint32_t w0 = own.x, w1 = own.y, w2 = own.z, w3 = own.w;
       for (int p = 0; p < n_arms; ++p) {
         const int a = s_arm[p];
-        const uint32_t sh = 3u * (uint32_t)a, shn = 3u * (uint32_t)(a ^ 1);
+        const uint32_t sh = 4u * (uint32_t)a, nsh = 24u - 4u * (uint32_t)(a ^ 1);
+        const uint32_t amask = 0xFu << sh;
         uint32_t n0, n1, n2, n3;
         if (a == 0) {
           n0 = w1;
@@ -302,11 +331,12 @@ __global__ void __launch_bounds__(kThreads3) k_pass3(Args3 A, int launch) {
           n3 = nb.w;
         }
         const Words4 r = philox(gi, s_lo, s_hi, kTagArm0 + (uint32_t)a, A.keys);
-        w0 = update_arm3<CMP64>(w0, (n0 >> shn) & 7u, r.x, sh, q, sT32, sT64, dhb_sum, dc_sum, nacc);
-        w1 = update_arm3<CMP64>(w1, (n1 >> shn) & 7u, r.y, sh, q, sT32, sT64, dhb_sum, dc_sum, nacc);
-        w2 = update_arm3<CMP64>(w2, (n2 >> shn) & 7u, r.z, sh, q, sT32, sT64, dhb_sum, dc_sum, nacc);
-        w3 = update_arm3<CMP64>(w3, (n3 >> shn) & 7u, r.w, sh, q, sT32, sT64, dhb_sum, dc_sum, nacc);
+        w0 = update_arm3<CMP64>(w0, n0, r.x, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+        w1 = update_arm3<CMP64>(w1, n1, r.y, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+        w2 = update_arm3<CMP64>(w2, n2, r.z, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+        w3 = update_arm3<CMP64>(w3, n3, r.w, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
       }
+      unpack_counts(pk, nacc, hb_b, dc_b);
       *reinterpret_cast<uint4*>(st + c0) = make_uint4(w0, w1, w2, w3);
       if (rec) hist_group(w0, w1, w2, w3, s_hist);
     } else {
@@ -325,7 +355,8 @@ __global__ void __launch_bounds__(kThreads3) k_pass3(Args3 A, int launch) {
       }
       for (int p = 0; p < n_arms; ++p) {
         const int a = s_arm[p];
-        const uint32_t sh = 3u * (uint32_t)a, shn = 3u * (uint32_t)(a ^ 1);
+        const uint32_t sh = 4u * (uint32_t)a, nsh = 24u - 4u * (uint32_t)(a ^ 1);
+        const uint32_t amask = 0xFu << sh;
         const Words4 r = philox(gi, s_lo, s_hi, kTagArm0 + (uint32_t)a, A.keys);
         const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
@@ -345,10 +376,11 @@ __global__ void __launch_bounds__(kThreads3) k_pass3(Args3 A, int launch) {
             nb = (z[i] + 1u == A.L) ? c + A.L2 - A.N : c + A.L2;
           else
             nb = (z[i] == 0u) ? c + A.N - A.L2 : c - A.L2;
-          w[i] = update_arm3<CMP64>(w[i], (st[nb] >> shn) & 7u, rw[i], sh, q, sT32, sT64,
-                                    dhb_sum, dc_sum, nacc);
+          w[i] = update_arm3<CMP64>(w[i], st[nb], rw[i], sh, nsh, amask, qm1, sProp, sRows,
+                                    sT64, pk);
         }
       }
+      unpack_counts(pk, nacc, hb_b, dc_b);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
         if (valid[i]) st[c0 + (uint32_t)i] = w[i];
@@ -363,7 +395,7 @@ __global__ void __launch_bounds__(kThreads3) k_pass3(Args3 A, int launch) {
       }
     }
   }
-  uint32_t a1 = (uint32_t)dhb_sum, a2 = (uint32_t)dc_sum, a3 = nacc;
+  uint32_t a1 = hb_b - nacc, a2 = dc_b - 5u * nacc, a3 = nacc;  // two's complement sums
   block_sum3<kThreads3>(a1, a2, a3);
   if (threadIdx.x == 0) {
     atomicAdd(&ctl->acc_hb, (unsigned long long)(long long)(int)a1);
@@ -392,7 +424,7 @@ __global__ void __launch_bounds__(kThreads3) k_init3(uint32_t* __restrict__ stat
         const Words4 r = philox(gi, 0u, 0u, kTagInit0 + (uint32_t)a, K);
         const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) w[i] |= __umulhi(rw[i], q) << (3 * a);
+        for (int i = 0; i < 4; ++i) w[i] |= __umulhi(rw[i], q) << (4 * a);
       }
     }
 #pragma unroll
@@ -423,9 +455,9 @@ __global__ void __launch_bounds__(kThreads3) k_count3(const uint32_t* __restrict
     const uint32_t wx = state[(x + 1u == L) ? c + 1u - L : c + 1u];
     const uint32_t wy = state[(y + 1u == L) ? c + L - L2 : c + L];
     const uint32_t wz = state[(z + 1u == L) ? c + L2 - N : c + L2];
-    hb += (uint32_t)(((w >> 0) & 7u) == ((wx >> 3) & 7u));
-    hb += (uint32_t)(((w >> 6) & 7u) == ((wy >> 9) & 7u));
-    hb += (uint32_t)(((w >> 12) & 7u) == ((wz >> 15) & 7u));
+    hb += (uint32_t)(((w >> 0) & 7u) == ((wx >> 4) & 7u));
+    hb += (uint32_t)(((w >> 8) & 7u) == ((wy >> 12) & 7u));
+    hb += (uint32_t)(((w >> 16) & 7u) == ((wz >> 20) & 7u));
     const uint32_t cnt = count_word(w);
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
@@ -846,10 +878,11 @@ int cvf3_set_state(cvf3_handle* h, const uint32_t* host, size_t n, double V_iso,
   const uint32_t q = (uint32_t)h->p.q;
   for (size_t i = 0; i < n; ++i) {
     const uint32_t w = host[i];
-    bool ok = (w >> 18) == 0u;
-    for (int a = 0; a < 6 && ok; ++a) ok = ((w >> (3 * a)) & 7u) < q;
-    if (!ok) return set_error(CVF_EINVAL, "word %zu = 0x%x: arms must be < q=%u, bits 18..31 zero",
-                              i, w, q);
+    bool ok = (w & ~kArmBits) == 0u;
+    for (int a = 0; a < 6 && ok; ++a) ok = ((w >> (4 * a)) & 7u) < q;
+    if (!ok)
+      return set_error(CVF_EINVAL, "word %zu = 0x%x: arms must be < q=%u, bits 4a+3 and 24..31 zero",
+                       i, w, q);
   }
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
   CVF_CUDA_CHECK(cudaMemcpyAsync(h->state, host, sizeof(uint32_t) * n, cudaMemcpyHostToDevice,

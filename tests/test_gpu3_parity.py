@@ -130,7 +130,7 @@ def test_lattice3_rejects_bad_state():
     op = oracle.physical_params3(300.0, 0.1, L=4, q=6)
     with Lattice3(params_from_dict(asdict(op))) as lat:
         good = lat.state()
-        for bad_word in (6, 6 << 15, 1 << 18):
+        for bad_word in (6, 6 << 20, 1 << 24, 1 << 3, 1 << 23):
             w = good.copy().reshape(-1)
             w[5] = bad_word
             with pytest.raises(_capi.CvfError):

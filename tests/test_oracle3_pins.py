@@ -33,9 +33,10 @@ def _batch_mean(x, nbatch=50):
 
 
 def _arms(words):
-    """[6, L, L, L] arm values of packed words indexed [z, y, x]."""
+    """[6, L, L, L] arm values of the words (sigma_a in bits [4a, 4a+3))
+    indexed [z, y, x]."""
     w = np.asarray(words).astype(np.int64)
-    return [(w >> (3 * a)) & 7 for a in range(6)]
+    return [(w >> (4 * a)) & 7 for a in range(6)]
 
 
 def _counts_bruteforce(words, L):
@@ -74,7 +75,7 @@ def _lj_bruteforce(v, epsilon=1.0, cutoff=6.0, box=7):
 def _random_words(rng, n, q):
     w = np.zeros(n, np.uint32)
     for a in range(6):
-        w |= (rng.integers(0, q, n).astype(np.uint32) << np.uint32(3 * a))
+        w |= (rng.integers(0, q, n).astype(np.uint32) << np.uint32(4 * a))
     return w
 
 
@@ -173,14 +174,14 @@ def test_detailed_balance_against_recount(L, q, g, kT):
         hb0, co0 = _counts_bruteforce(w, L)
         c = int(rng.integers(N))
         for a in range(6):
-            s = (int(w[c]) >> (3 * a)) & 7
+            s = (int(w[c]) >> (4 * a)) & 7
             seen = set()
             for k in range(q - 1):
                 sp, T = oracle.arm_probe3(p, w, c, a, k, g)
                 assert sp != s and sp < q
                 seen.add(sp)
                 w2 = w.copy()
-                w2[c] = (int(w[c]) & ~(7 << (3 * a))) | (sp << (3 * a))
+                w2[c] = (int(w[c]) & ~(7 << (4 * a))) | (sp << (4 * a))
                 hb1, co1 = _counts_bruteforce(w2, L)
                 dH = -g * J_eff * (hb1 - hb0) - p.J_sigma * (co1 - co0)
                 k_rev = (s - sp - 1) % q
