@@ -216,7 +216,7 @@ __device__ __forceinline__ void hist_group(uint32_t w0, uint32_t w1, uint32_t w2
 // kLaunches3 - 1 commits the step.
 // ---------------------------------------------------------------------------
 template <bool ALIGNED, bool CMP64>
-__global__ void __launch_bounds__(kThreads3) k_pass3(Args3 A, int launch) {
+__global__ void __launch_bounds__(kThreads3, 4) k_pass3(Args3 A, int launch) {
   __shared__ Row3 sRows[33];
   __shared__ uint32_t sProp[64];
   __shared__ unsigned long long sT64[CMP64 ? 33 : 1];
@@ -289,57 +289,71 @@ __global__ void __launch_bounds__(kThreads3) k_pass3(Args3 A, int launch) {
   // accepted moves and the biased sums of their dN_HB + 1 and dN_sigma + 5
   uint32_t nacc = 0, hb_b = 0, dc_b = 0, pk = 0;
   uint32_t* __restrict__ st = A.state;
-  for (uint32_t gi = (blockIdx.x - first_block) * kThreads3 + threadIdx.x; gi < A.groups;
-       gi += nblk * kThreads3) {
-    const uint32_t c0 = gi * 4u;
-    if (ALIGNED) {
+  const uint32_t stride = nblk * kThreads3;
+  const uint32_t g_first = (blockIdx.x - first_block) * kThreads3 + threadIdx.x;
+  if (ALIGNED) {
+    // the words of the next group are requested before this group's
+    // arithmetic, and every neighbour word of this group before its first
+    // pass, so that the loads overlap the Philox and update chains
+    const int arm0 = s_arm[0], arm1 = s_arm[1], arm2 = s_arm[2];
+    uint4 next = make_uint4(0u, 0u, 0u, 0u);
+    if (g_first < A.groups) next = *reinterpret_cast<const uint4*>(st + 4u * g_first);
+    for (uint32_t gi = g_first; gi < A.groups; gi += stride) {
+      const uint32_t c0 = gi * 4u;
+      const uint4 own = next;
+      if (gi + stride < A.groups) next = *reinterpret_cast<const uint4*>(st + 4u * (gi + stride));
       const uint32_t row = fdiv(gi, A.div_G);      // y + L z
       const uint32_t xg = gi - row * A.G;
       const uint32_t z = fdiv(row, A.div_L);
       const uint32_t y = row - z * A.L;
-      const uint4 own = *reinterpret_cast<const uint4*>(st + c0);
-      uint32_t w0 = own.x, w1 = own.y, w2 = own.z, w3 = own.w;
-      for (int p = 0; p < n_arms; ++p) {
-        const int a = s_arm[p];
-        const uint32_t sh = 4u * (uint32_t)a, nsh = 24u - 4u * (uint32_t)(a ^ 1);
-        const uint32_t amask = 0xFu << sh;
-        uint32_t n0, n1, n2, n3;
-        if (a == 0) {
-          n0 = w1;
-          n1 = w2;
-          n2 = w3;
-          n3 = st[(4u * xg + 4u == A.L) ? c0 + 4u - A.L : c0 + 4u];
-        } else if (a == 1) {
-          n0 = st[(xg == 0u) ? c0 + A.L - 1u : c0 - 1u];
-          n1 = w0;
-          n2 = w1;
-          n3 = w2;
-        } else {
-          uint32_t off;
-          if (a == 2)
-            off = (y == A.L - 1u) ? c0 + A.L - A.L2 : c0 + A.L;
-          else if (a == 3)
-            off = (y == 0u) ? c0 + A.L2 - A.L : c0 - A.L;
-          else if (a == 4)
-            off = (z == A.L - 1u) ? c0 + A.L2 - A.N : c0 + A.L2;
-          else
-            off = (z == 0u) ? c0 + A.N - A.L2 : c0 - A.L2;
-          const uint4 nb = *reinterpret_cast<const uint4*>(st + off);
-          n0 = nb.x;
-          n1 = nb.y;
-          n2 = nb.z;
-          n3 = nb.w;
+      uint4 nbv[3];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const int a = (p == 0) ? arm0 : (p == 1) ? arm1 : arm2;
+        nbv[p] = make_uint4(0u, 0u, 0u, 0u);
+        if (p < n_arms) {
+          // arm a^1 of a neighbour is constant during the launch, so the
+          // cell's own words as loaded serve for the x neighbours
+          if (a == 0) {
+            nbv[p] = make_uint4(own.y, own.z, own.w,
+                                st[(4u * xg + 4u == A.L) ? c0 + 4u - A.L : c0 + 4u]);
+          } else if (a == 1) {
+            nbv[p] = make_uint4(st[(xg == 0u) ? c0 + A.L - 1u : c0 - 1u], own.x, own.y, own.z);
+          } else {
+            uint32_t off;
+            if (a == 2)
+              off = (y == A.L - 1u) ? c0 + A.L - A.L2 : c0 + A.L;
+            else if (a == 3)
+              off = (y == 0u) ? c0 + A.L2 - A.L : c0 - A.L;
+            else if (a == 4)
+              off = (z == A.L - 1u) ? c0 + A.L2 - A.N : c0 + A.L2;
+            else
+              off = (z == 0u) ? c0 + A.N - A.L2 : c0 - A.L2;
+            nbv[p] = *reinterpret_cast<const uint4*>(st + off);
+          }
         }
-        const Words4 r = philox(gi, s_lo, s_hi, kTagArm0 + (uint32_t)a, A.keys);
-        w0 = update_arm3<CMP64>(w0, n0, r.x, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
-        w1 = update_arm3<CMP64>(w1, n1, r.y, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
-        w2 = update_arm3<CMP64>(w2, n2, r.z, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
-        w3 = update_arm3<CMP64>(w3, n3, r.w, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+      }
+      uint32_t w0 = own.x, w1 = own.y, w2 = own.z, w3 = own.w;
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        if (p < n_arms) {
+          const int a = (p == 0) ? arm0 : (p == 1) ? arm1 : arm2;
+          const uint32_t sh = 4u * (uint32_t)a, nsh = 24u - 4u * (uint32_t)(a ^ 1);
+          const uint32_t amask = 0xFu << sh;
+          const Words4 r = philox(gi, s_lo, s_hi, kTagArm0 + (uint32_t)a, A.keys);
+          w0 = update_arm3<CMP64>(w0, nbv[p].x, r.x, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+          w1 = update_arm3<CMP64>(w1, nbv[p].y, r.y, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+          w2 = update_arm3<CMP64>(w2, nbv[p].z, r.z, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+          w3 = update_arm3<CMP64>(w3, nbv[p].w, r.w, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+        }
       }
       unpack_counts(pk, nacc, hb_b, dc_b);
       *reinterpret_cast<uint4*>(st + c0) = make_uint4(w0, w1, w2, w3);
       if (rec) hist_group(w0, w1, w2, w3, s_hist);
-    } else {
+    }
+  } else {
+    for (uint32_t gi = g_first; gi < A.groups; gi += stride) {
+      const uint32_t c0 = gi * 4u;
       uint32_t w[4], x[4], y[4], z[4];
       bool valid[4];
 #pragma unroll
