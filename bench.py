@@ -244,9 +244,10 @@ def run_kernel_mode(args):
 # The paper's own 3D figure (context, other hardware): 280 ms per Metropolis
 # MC step at N = 260^3 on an RTX 3060, cuRAND generation and copies included.
 PAPER_3D_MS_PER_STEP_260 = 280.0
-# DRAM bytes (read + write) of the k_pass3 launches of one MC step at
-# L = 260 from an ncu capture of the current kernel; None until taken.
-PASS3_DRAM_BYTES_260 = None
+# DRAM bytes (read + write) of one two-arm k_pass3 launch at L = 260 (the
+# commonest kind), from an ncu capture of the current kernel; reset to None
+# whenever the kernel changes until a new capture is taken.
+PASS3_DRAM_BYTES_260 = 81.0e6
 
 
 def run_kernel3_mode(args):
@@ -311,6 +312,7 @@ def measure_cubic(args, rank, world):
                         "peak": ALU_PEAK_TOPS, "unit": "Tintop/s",
                         "frac": ALU_OPS_PER_UPDATE * upd / (per_step * 1e-3) / 1e12 / ALU_PEAK_TOPS,
                         "traffic": PASS3_DRAM_BYTES_260 if L == 260 else None,
+                        "traffic_unit": "bytes per two-arm launch (ncu dram read + write)",
                         "kernel": "k_pass3 (four launches per MC step)"},
            "acceptance": o["acc_sigma"] / max(1.0, upd * o["sweep"]),
            "workload": "CVF 3D cubic lattice L=%d q=6, layered six-arm schedule, random init "
