@@ -18,7 +18,8 @@
  *     r0 (2.9 A), volumes in v0 = r0^3.  cvf_params_physical converts
  *     (T [K], P [MPa]).
  *   - Lattice layout: cell c = y*L + x (x fastest), one uint16 word per cell
- *     holding sigma of arm a in bits [3a, 3a+3) (bits 12..15 zero).  Arms
+ *     holding sigma of arm a in bits [4a, 4a+3) -- one nibble per arm, bits
+ *     3, 7, 11 and 15 zero.  Arms
  *     0..3 = left, right, front, back; arm 0 points to +x, arm 1 to -x, arm 2
  *     to +y, arm 3 to -y (the paper's worked example of Sec. II.C: arm 0 of
  *     cell c pairs with arm 1 of cell c+1).  A bond joins arm a of a cell
@@ -162,7 +163,8 @@ int cvf_get_state(cvf_handle *h, uint16_t *host, size_t n);
 /* Replaces the lattice by host[0..n) (n = L*L), sets V_iso and the step
  * counter, recounts N_HB_raw and N_sigma, and clears the acceptance
  * counters and the ring.  Every word is validated on the host first
- * (arms < q, bits 12..15 zero): CVF_EINVAL otherwise, with nothing changed.
+ * (arms < q, bits 3, 7, 11, 15 zero): CVF_EINVAL otherwise, with nothing
+ * changed.
  * V_iso must be >= N (the hard core).  Synchronises. */
 int cvf_set_state(cvf_handle *h, const uint16_t *host, size_t n, double V_iso,
                   int64_t sweep);

@@ -90,7 +90,7 @@ static uint32_t orc_scale(uint32_t w, uint32_t n) {
 /* of cells 1..16) puts the "left" partner of cell c at c+1, i.e. arm 0     */
 /* points to +x and arm 1 to -x; by the same rule arm 2 points to +y and    */
 /* arm 3 to -y.  A bond of arm a pairs with arm a^1 of the neighbour in     */
-/* direction a.  Packed word: sigma of arm a in bits [3a, 3a+3).            */
+/* direction a.  Packed word: sigma of arm a in bits [4a, 4a+3).            */
 /* ------------------------------------------------------------------------ */
 static int64_t orc_neighbour(int32_t L, int64_t c, int arm) {
   int64_t x = c % L, y = c / L;
@@ -111,8 +111,10 @@ void orc_bond_partner(int32_t L, int64_t c, int arm, int64_t *c_out,
   *arm_out = arm ^ 1;
 }
 
+/* Cell word: sigma of arm a in bits [4a, 4a+3), one nibble per arm; bits
+   4a+3 are zero. */
 static uint32_t orc_arm(uint16_t word, int arm) {
-  return ((uint32_t)word >> (3 * arm)) & 7u;
+  return ((uint32_t)word >> (4 * arm)) & 7u;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -274,7 +276,7 @@ int orc_init(orc_state *st, const orc_params *p, uint16_t *w) {
       uint32_t r[4];
       orc_draw(p, (uint32_t)c, 0, ORC_TAG_INIT, r);
       for (int a = 0; a < 4; ++a)
-        word |= (uint16_t)(orc_scale(r[a], (uint32_t)p->q) << (3 * a));
+        word |= (uint16_t)(orc_scale(r[a], (uint32_t)p->q) << (4 * a));
     }
     w[c] = word;
   }
@@ -296,7 +298,7 @@ int orc_set(orc_state *st, const orc_params *p, uint16_t *w, double V_iso,
   st->w = w;
   for (int64_t c = 0; c < st->N; ++c)
     for (int a = 0; a < 4; ++a)
-      if (orc_arm(w[c], a) >= (uint32_t)p->q || (w[c] >> 12)) return ORC_EINVAL;
+      if (orc_arm(w[c], a) >= (uint32_t)p->q || (w[c] & 0x8888u)) return ORC_EINVAL;
   orc_set_volume(st, V_iso);
   st->dV_max = p->dv_max_frac * ((double)st->N * p->v_iso_init);
   st->sweep = sweep;
@@ -412,7 +414,7 @@ static void orc_update_arm(orc_state *st, int64_t c, int arm, uint32_t acc,
                    &T);
   if ((uint64_t)acc < T) {
     uint16_t wc = st->w[c];
-    wc = (uint16_t)((wc & ~(7u << (3 * arm))) | (sp << (3 * arm)));
+    wc = (uint16_t)((wc & ~(7u << (4 * arm))) | (sp << (4 * arm)));
     st->w[c] = wc;
     st->n_hb_raw += dhb;
     st->n_coop += dc;

@@ -87,10 +87,8 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_batch_sweep(con
                                                              const int32_t* __restrict__ order,
                                                              const long long* __restrict__ tile_prefix,
                                                              unsigned int* progress) {
-  using TT = typename ThresholdRow<CMP64>::type;
   __shared__ TileSmem<TR, TW> S;
-  __shared__ ProposalTable P;
-  __shared__ TT sT[24];
+  __shared__ Tables2 Tb;
   __shared__ int s_rep, s_tile, s_abort, s_last;
   __shared__ long long s_rel;
   __shared__ uint32_t s_q;
@@ -144,12 +142,9 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_batch_sweep(con
     volatile Ctrl* vc = ctl;
     const long long step = vc->sweep;
     const int g = vc->next_g;
-    if (threadIdx.x < 24) {
-      const unsigned long long t = R.table24[g * 24 + threadIdx.x];
-      sT[threadIdx.x] = CMP64 ? (TT)t : (TT)(uint32_t)(t - 1ull);
-    }
+    fill_rows2(Tb, R.table24, g);
     if (s_q != R.q) {  // block-uniform
-      fill_proposal_table(P, R.q);
+      fill_prop2(Tb, R.q);
       __syncthreads();
       if (threadIdx.x == 0) s_q = R.q;
     }
@@ -169,23 +164,23 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_batch_sweep(con
     const int tiles_x = (Lh + TW - 1) / TW;
     const int ntiles = tiles_x * ((L + TR - 1) / TR);
     const int t = s_tile;
-    TileCounts cnt{0, 0, 0, 0};
+    TileCounts cnt{0, 0, 0};
     const bool rec = step_recorded(vc->record_every, step);
     sweep_tile<RNG_WORDS, CMP64, TR, TW, kThreads, KeysSeed, true>(
-        v, (t / tiles_x) * TR, (t % tiles_x) * TW, S, P, sT, cnt, rec ? s_hist4 : nullptr,
+        v, (t / tiles_x) * TR, (t % tiles_x) * TW, S, Tb, cnt, rec ? s_hist4 : nullptr,
         ctl->acc_hist);
-    uint32_t pairs = cnt.pairs(), bonds = cnt.bonds, nacc = cnt.nacc;
-    block_sum3<kThreads>(pairs, bonds, nacc);
+    uint32_t dhb = (uint32_t)cnt.dhb(), dc = (uint32_t)cnt.dc(), nacc = cnt.nacc;
+    block_sum3<kThreads>(dhb, dc, nacc);  // two's complement sums
     if (threadIdx.x == 0) {
-      atomicAdd(&ctl->acc_pairs, (unsigned long long)pairs);
-      atomicAdd(&ctl->acc_hb, (unsigned long long)bonds);
+      atomicAdd(&ctl->acc_hb, (unsigned long long)(long long)(int)dhb);
+      atomicAdd(&ctl->acc_pairs, (unsigned long long)(long long)(int)dc);
       atomicAdd(&ctl->acc_moves, (unsigned long long)nacc);
       __threadfence();
       const unsigned int prev = atomicAdd(&ctl->done, 1u);
       s_last = (prev == (unsigned int)ntiles - 1u) ? 1 : 0;
       if (s_last) {
         __threadfence();
-        finalize_step(*R.vol, ctl, R.ring, R.ring_cap, R.keys);
+        finalize_step<true>(*R.vol, ctl, R.ring, R.ring_cap, R.keys);
         __threadfence();
         st_release(&progress[s_rep], (unsigned int)(s_rel + 1));
       }

@@ -1,7 +1,7 @@
 // cvf_device.cuh -- device building blocks of the CVF Metropolis path
-// (arXiv:2505.05919): counter-based Philox4x32-10 words, the Metropolis
-// update of the four bonding indices of one cell, bond/pair counting, and the
-// FP64 isobaric volume move.  Included by the kernel translation units only.
+// (arXiv:2505.05919): counter-based Philox4x32-10 words and the draws of a
+// cell, cell-word helpers, the FP64 isobaric volume move, the end of a step
+// and block reductions.  Included by the kernel translation units only.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -89,47 +89,10 @@ __device__ __forceinline__ Words4 philox_seed(uint32_t x0, uint32_t x1,
   return Words4{x0, x1, x2, x3};
 }
 
-// ---------------------------------------------------------------------------
-// Metropolis update of the four arms of one cell (Sec. II.C).
-//   w        packed cell word (sigma_a in bits [3a, 3a+3))
-//   part[a]  sigma of the arm that arm a bonds with (arm a^1 of the
-//            neighbour in direction a)
-//   acc[a]   32-bit acceptance draw, kk[a] proposal offset in [0, q-1)
-//   T        the 21 thresholds of the current gate, [dN_HB+1][dN_sigma+3]
-// Arms are visited in the order 0..3; each sees the arms already updated.
-// The proposal is sigma' = (sigma + 1 + k) mod q, uniform over the other q-1
-// states; the move is accepted when acc < T(dN_HB, dN_sigma).
-// ---------------------------------------------------------------------------
+// Cell word of the square lattice: sigma of arm a in bits [4a, 4a+3) (one
+// nibble per arm, bits 4a+3 zero).
 __device__ __forceinline__ uint32_t arm_of(uint32_t w, int a) {
-  return (w >> (3 * a)) & 7u;
-}
-
-__device__ __forceinline__ uint32_t update_cell(uint32_t w, const uint32_t part[4],
-                                                const uint32_t acc[4],
-                                                const uint32_t kk[4], uint32_t q,
-                                                const unsigned long long* T,
-                                                uint32_t& naccepted) {
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const uint32_t s = arm_of(w, a);
-    uint32_t sp = s + 1u + kk[a];
-    sp = (sp >= q) ? sp - q : sp;
-    const uint32_t n = part[a];
-    const int dhb = (int)(sp == n) - (int)(s == n);
-    int dc = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      if (b == a) continue;
-      const uint32_t sb = arm_of(w, b);
-      dc += (int)(sp == sb) - (int)(s == sb);
-    }
-    const unsigned long long t = T[(dhb + 1) * 7 + (dc + 3)];
-    if ((unsigned long long)acc[a] < t) {
-      w = (w & ~(7u << (3 * a))) | (sp << (3 * a));
-      ++naccepted;
-    }
-  }
-  return w;
+  return (w >> (4 * a)) & 7u;
 }
 
 // The acceptance draws and proposal offsets of a cell from its Philox words.
@@ -167,97 +130,6 @@ __device__ __forceinline__ uint32_t cell_pairs(uint32_t w) {
                  a3 = arm_of(w, 3);
   return (uint32_t)(a0 == a1) + (uint32_t)(a0 == a2) + (uint32_t)(a0 == a3) +
          (uint32_t)(a1 == a2) + (uint32_t)(a1 == a3) + (uint32_t)(a2 == a3);
-}
-
-// Formed bonds of a cell given its four partner arms.
-__device__ __forceinline__ uint32_t cell_bonds(uint32_t w, const uint32_t part[4]) {
-  return (uint32_t)(arm_of(w, 0) == part[0]) + (uint32_t)(arm_of(w, 1) == part[1]) +
-         (uint32_t)(arm_of(w, 2) == part[2]) + (uint32_t)(arm_of(w, 3) == part[3]);
-}
-
-// ---------------------------------------------------------------------------
-// Same update in the form the sweep kernels use, arranged so that most of the
-// integer work runs as multiply-adds (the FMA pipe) rather than as shifts and
-// logic ops (the ALU pipe, which is the busier one).
-//
-// cnt holds, in nibble v, the number of arms of the cell with sigma = v.  For
-// a value v let oh(v) = 2^(4v) and m(v) = 2^(28-4v); the nibble v of a word X
-// is then (X * m(v)) >> 28, a multiply and a high multiply by 16.  For arm a
-// with partner value n the word cnt + 8 oh(n) has nibble f(v) = #{b : sigma_b
-// = v} + 8 [n = v], so f(sigma') - f(sigma) = (dN_sigma - 1) + 8 dN_HB, and
-// (dN_HB + 1) * 8 + (dN_sigma + 3) = f(sigma') - f(sigma) + 12 indexes a
-// 24-entry threshold row (entries with dN_sigma + 3 = 7 are never used).
-// TAB holds T - 1 as uint32 (accept iff u <= T - 1) when no threshold is 0,
-// else T as uint64 (accept iff u < T).
-// ---------------------------------------------------------------------------
-template <bool CMP64>
-struct ThresholdRow {
-  using type = typename std::conditional<CMP64, unsigned long long, uint32_t>::type;
-};
-
-template <bool CMP64>
-__device__ __forceinline__ bool accept_draw(uint32_t u,
-                                            typename ThresholdRow<CMP64>::type t) {
-  if (CMP64)
-    return (unsigned long long)u < (unsigned long long)t;
-  else
-    return u <= (uint32_t)t;
-}
-
-// Nibble `v` (given as m(v)) of x.
-__device__ __forceinline__ uint32_t nibble(uint32_t x, uint32_t mv) {
-  return __umulhi(x * mv, 16u);
-}
-
-// Update the four arms of one cell.
-//   t4[a]  4 * sigma_a of the cell (in/out)
-//   nb8[a] 8 oh(partner value of arm a)
-//   acc, kk  acceptance draws and proposal offsets
-//   q4     4 q
-//   T      threshold row (24 entries, see above)
-// Adds the accepted moves to naccepted and the cell's equal-pair count,
-// plus 4, times 2 (sum over arms of the number of arms sharing its value) to
-// pair_sum; returns the bonds formed with the partners when BONDS.
-template <bool CMP64, bool BONDS>
-__device__ __forceinline__ uint32_t update_arms(uint32_t t4[4], const uint32_t nb8[4],
-                                                const uint32_t acc[4], const uint32_t kk[4],
-                                                uint32_t q4,
-                                                const typename ThresholdRow<CMP64>::type* T,
-                                                uint32_t& naccepted, uint32_t& pair_sum) {
-  uint32_t oh[4], m[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    oh[a] = 1u << t4[a];
-    m[a] = 0x10000000u >> t4[a];
-  }
-  uint32_t cnt = oh[0] + oh[1] + oh[2] + oh[3];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const uint32_t wa = cnt + nb8[a];
-    uint32_t tp = t4[a] + 4u * kk[a] + 4u;
-    tp = (tp >= q4) ? tp - q4 : tp;
-    const uint32_t mp = 0x10000000u >> tp;
-    const int fsp = (int)nibble(wa, mp);
-    const int fs = (int)nibble(wa, m[a]);
-    const bool ok = accept_draw<CMP64>(acc[a], T[fsp - fs + 12]);
-    if (ok) {
-      const uint32_t ohp = 1u << tp;
-      cnt = cnt + ohp - oh[a];
-      oh[a] = ohp;
-      m[a] = mp;
-      t4[a] = tp;
-      ++naccepted;
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) pair_sum += nibble(cnt, m[a]);
-  uint32_t bonds = 0;
-  if (BONDS) {
-    // nb8 * m = 2^(31 + 4 (n - sigma)) mod 2^32: bit 31 set iff n == sigma
-#pragma unroll
-    for (int a = 0; a < 4; ++a) bonds += __umulhi(nb8[a] * m[a], 2u);
-  }
-  return bonds;
 }
 
 // ---------------------------------------------------------------------------

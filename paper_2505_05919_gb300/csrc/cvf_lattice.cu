@@ -38,8 +38,8 @@ __global__ void k_init(uint16_t* __restrict__ state, int32_t L, uint32_t q, int 
     uint32_t w = 0;
     if (random) {
       const Words4 r = philox((uint32_t)c, 0u, 0u, kTagInit, K);
-      w = __umulhi(r.x, q) | (__umulhi(r.y, q) << 3) | (__umulhi(r.z, q) << 6) |
-          (__umulhi(r.w, q) << 9);
+      w = __umulhi(r.x, q) | (__umulhi(r.y, q) << 4) | (__umulhi(r.z, q) << 8) |
+          (__umulhi(r.w, q) << 12);
     }
     state[c] = (uint16_t)w;
   }
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_histogram(const uint16_t* __restri
     const uint32_t w = state[i];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const uint32_t v = (w >> (3 * a)) & 7u;
+      const uint32_t v = (w >> (4 * a)) & 7u;
 #pragma unroll
       for (int k = 0; k < 8; ++k) c[k] += (v == (uint32_t)k) ? 1u : 0u;
     }
@@ -167,10 +167,10 @@ __global__ void __launch_bounds__(kThreads) k_histogram(const uint16_t* __restri
 // Checkerboard sweep, both colours in one launch (the tile algorithm is in
 // cvf_tile.cuh).  Blocks take tiles from a per-step atomic counter; block 0
 // instead decides the next step's volume move early (it depends on the bonds
-// only when the gate would change).  Per thread the counts of N_sigma (all
-// tile cells), N_HB_raw (the four bonds of every colour-1 cell: each bond has
-// exactly one colour-1 end) and accepted moves are summed, block-reduced and
-// added with one atomic each; the last block closes the step.
+// only when the gate would change).  Per thread the accepted moves of the
+// tile cells and their changes of N_HB_raw and N_sigma are summed,
+// block-reduced and added with one atomic each; the last block adds the
+// changes to the committed counts and closes the step.
 // ---------------------------------------------------------------------------
 // Bounded wait for a TMA stage (the copies complete in microseconds; the
 // limit only guards against a copy that never lands).
@@ -180,10 +180,8 @@ template <int RNG_WORDS, bool CMP64>
 __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     k_sweep_tiled(LatticeArgs A, const __grid_constant__ CUtensorMap tm0,
                   const __grid_constant__ CUtensorMap tm1) {
-  using TT = typename ThresholdRow<CMP64>::type;
   __shared__ TileSmem<kTileRows, kTileWords> S;
-  __shared__ ProposalTable P;
-  __shared__ TT sT[24];
+  __shared__ Tables2 Tb;
   __shared__ int s_tile, s_next;
   __shared__ uint32_t s_hist4[4];
   __shared__ alignas(8) uint64_t s_bar;
@@ -205,14 +203,11 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       }
     }
     if (last_block(&ctl->done) && threadIdx.x == 0)
-      finalize_step(*A.vol, ctl, A.ring, A.ring_cap, A.keys);
+      finalize_step<true>(*A.vol, ctl, A.ring, A.ring_cap, A.keys);
     return;
   }
-  if (threadIdx.x < 24) {
-    const unsigned long long t = A.table24[g * 24 + threadIdx.x];
-    sT[threadIdx.x] = CMP64 ? (TT)t : (TT)(uint32_t)(t - 1ull);
-  }
-  fill_proposal_table(P, A.q);
+  fill_rows2(Tb, A.table24, g);
+  fill_prop2(Tb, A.q);
   const long long N = (long long)A.L * A.L;
   StepView<KeysRound> v;
   v.src = reinterpret_cast<const uint32_t*>(A.state + (size_t)(step & 1) * N);
@@ -227,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
   const int tiles_x = (v.Lh + kTileWords - 1) / kTileWords;
   const int ntiles = tiles_x * ((v.L + kTileRows - 1) / kTileRows);
   const bool rec = step_recorded(ctl->record_every, step);
-  TileCounts cnt{0, 0, 0, 0};
+  TileCounts cnt{0, 0, 0};
   if (threadIdx.x < 4) s_hist4[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
@@ -287,13 +282,13 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     __syncthreads();
     const TileGeom gm = tile_geom<kTileRows, kTileWords>(v.L, v.Lh, (t / tiles_x) * kTileRows,
                                                          (t % tiles_x) * kTileWords);
-    colour0<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads>(v, gm, S, P, sT, cnt,
+    colour0<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads>(v, gm, S, Tb, cnt,
                                                                rec ? s_hist4 : nullptr);
     if (threadIdx.x == 0) s_next = (int)atomicAdd(&ctl->tile_next, 1u);
     __syncthreads();  // S.in is free: fetch the next tile while colour 1 runs
     const int t2 = s_next;
     const bool t2_tma = (t2 < ntiles) ? stage(t2) : false;
-    colour1<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads>(v, gm, S, P, sT, cnt,
+    colour1<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads>(v, gm, S, Tb, cnt,
                                                                rec ? s_hist4 : nullptr);
     if (rec) {
       __syncthreads();
@@ -303,15 +298,15 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     t = t2;
     t_tma = t2_tma;
   }
-  uint32_t pairs = cnt.pairs(), bonds = cnt.bonds, nacc = cnt.nacc;
-  block_sum3<kThreads>(pairs, bonds, nacc);
+  uint32_t dhb = (uint32_t)cnt.dhb(), dc = (uint32_t)cnt.dc(), nacc = cnt.nacc;
+  block_sum3<kThreads>(dhb, dc, nacc);  // two's complement sums
   if (threadIdx.x == 0) {
-    atomicAdd(&ctl->acc_pairs, (unsigned long long)pairs);
-    atomicAdd(&ctl->acc_hb, (unsigned long long)bonds);
+    atomicAdd(&ctl->acc_hb, (unsigned long long)(long long)(int)dhb);
+    atomicAdd(&ctl->acc_pairs, (unsigned long long)(long long)(int)dc);
     atomicAdd(&ctl->acc_moves, (unsigned long long)nacc);
   }
   if (last_block(&ctl->done) && threadIdx.x == 0)
-    finalize_step(*A.vol, ctl, A.ring, A.ring_cap, A.keys);
+    finalize_step<true>(*A.vol, ctl, A.ring, A.ring_cap, A.keys);
 }
 
 // Layered schedule: pass `pass` updates arm order[pass] of every cell, where
@@ -372,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) k_layer_pass(LatticeArgs A, int pass
     }
     uint32_t wn = w;
     if ((unsigned long long)acc[a] < sT[(dhb + 1) * 8 + (dc + 3)]) {
-      wn = (w & ~(7u << (3 * a))) | (sp << (3 * a));
+      wn = (w & ~(7u << (4 * a))) | (sp << (4 * a));
       ++nacc;
     }
     if (pass == 0 || wn != w) dst[c] = (uint16_t)wn;
@@ -771,8 +766,8 @@ int cvf_set_state(cvf_handle* h, const uint16_t* host, size_t n, double V_iso, i
   const uint32_t q = (uint32_t)h->p.q;
   for (size_t i = 0; i < n; ++i) {
     const uint32_t w = host[i];
-    if ((w >> 12) || ((w & 7u) >= q) || (((w >> 3) & 7u) >= q) || (((w >> 6) & 7u) >= q) ||
-        (((w >> 9) & 7u) >= q))
+    if ((w & 0x8888u) || ((w & 7u) >= q) || (((w >> 4) & 7u) >= q) || (((w >> 8) & 7u) >= q) ||
+        (((w >> 12) & 7u) >= q))
       return set_error(CVF_EINVAL, "word %zu = 0x%04x is not a valid cell for q = %u", i, w, q);
   }
   h->sweep_host = sweep;

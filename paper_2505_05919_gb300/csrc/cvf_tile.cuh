@@ -16,80 +16,76 @@
 
 namespace cvf {
 
-// Proposal lookup for the current q: entry 8 sigma + k holds, for the
-// proposed value sigma' = (sigma + 1 + k) mod q, the word 4 sigma', 2^(28 -
-// 4 sigma') and 2^(4 sigma') (see update_arms).  Filled by the block.
-struct ProposalTable {
-  uint32_t t4[64];
-  uint32_t m[64];
-  uint32_t oh[64];
+// Shared tables of one (lattice, step): the proposal for the current q and
+// the threshold row of the current gate.
+//   prop[8 sigma + k] = ((sigma + 1 + k) mod q) * 0x11111 (sigma' in nibbles
+//                       0..4)
+//   rows[i]           = {T - 1, packed count change}, i = (dN_HB + 1) * 7 +
+//                       dN_sigma + 3; an accepted move adds the change
+//                       (1 << 20) + ((dN_HB + 1) << 10) + dN_sigma + 3
+//   T64[i]            = T (the 64-bit compare, when some T is 0)
+struct Tables2 {
+  uint2 rows[21];
+  uint32_t prop[64];
+  unsigned long long T64[21];
 };
 
-__device__ __forceinline__ void fill_proposal_table(ProposalTable& P, uint32_t q) {
+// Proposal part of the tables (depends on q only).
+__device__ __forceinline__ void fill_prop2(Tables2& Tb, uint32_t q) {
   for (int e = threadIdx.x; e < 64; e += blockDim.x) {
     const uint32_t s = (uint32_t)e >> 3, k = (uint32_t)e & 7u;
-    const uint32_t sp = (s + 1u + k) % q;
-    P.t4[e] = 4u * sp;
-    P.m[e] = 0x10000000u >> (4u * sp);
-    P.oh[e] = 1u << (4u * sp);
+    uint32_t sp = s + 1u + k;
+    while (sp >= q) sp -= q;
+    Tb.prop[e] = (s < q && k + 1u < q) ? sp * 0x11111u : 0u;
   }
 }
 
-__device__ __forceinline__ uint32_t lds_at(const uint32_t* base, uint32_t byte_off) {
-  return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(base) + byte_off);
+// Threshold part from a [g][(dN_HB+1)*8 + dN_sigma+3] table of 24 per gate.
+__device__ __forceinline__ void fill_rows2(Tables2& Tb, const unsigned long long* table24, int g) {
+  for (int i = threadIdx.x; i < 21; i += blockDim.x) {
+    const int d1 = i / 7, d2 = i % 7;  // dN_HB + 1, dN_sigma + 3
+    const unsigned long long t = table24[g * 24 + d1 * 8 + d2];
+    Tb.rows[i] = make_uint2((uint32_t)(t - 1ull),  // every t >= 1 unless 64-bit compares
+                            (1u << 20) + ((uint32_t)d1 << 10) + (uint32_t)d2);
+    Tb.T64[i] = t;
+  }
 }
 
-// Metropolis update of the four arms of one cell, with the count-nibble
-// bookkeeping of update_arms (cvf_device.cuh) and the proposal taken from
-// the block's ProposalTable.  t4[a] = 4 sigma_a (in/out), nb8[a] = 8 oh(n_a).
-template <bool CMP64, bool BONDS>
-__device__ __forceinline__ uint32_t update_arms_tab(uint32_t t4[4], const uint32_t nb8[4],
-                                                    const uint32_t acc[4], const uint32_t kk[4],
-                                                    const ProposalTable& P,
-                                                    const typename ThresholdRow<CMP64>::type* T,
-                                                    uint32_t& naccepted, uint32_t& pair_sum,
-                                                    uint32_t& cnt_out, bool count_pairs) {
-  uint32_t oh[4], m[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    oh[a] = 1u << t4[a];
-    m[a] = 0x10000000u >> t4[a];
+// Metropolis update of arm a (sh = 4a) of a cell word w (sigma_b in nibble
+// b, b = 0..3) against the partner value pa placed in nibble 4 (bits 16..18),
+// with draw u and proposal offset k (Sec. II.C, Eq. H).  With wn = w | pa,
+// f(v) = (((wn ^ v 0x11111) | 0x88888) - 0x11111) & 0x88888 has bit 3 of
+// nibble b set iff nibble b differs from v (every nibble is >= 8 before the
+// subtraction, so no borrow crosses a nibble).  popc f(sigma) = A_s + b_s and
+// popc f(sigma') = A_p + b_p, with A_v the arms differing from v and b_v =
+// [partner != v] (bit 19); dN_HB = b_s - b_p, dN_sigma = A_s - A_p + 1, and
+// the row index 7 dN_HB + dN_sigma + 10 = (popc f_s + 6 b_s) - (popc f_p +
+// 6 b_p) + 11.
+template <bool CMP64>
+__device__ __forceinline__ uint32_t update_arm2(uint32_t w, uint32_t pa, uint32_t u, uint32_t k,
+                                                uint32_t sh, const Tables2& Tb, uint32_t& pk) {
+  const uint32_t s = (w >> sh) & 7u;
+  const uint32_t sR = s * 0x11111u;
+  const uint32_t spR = Tb.prop[s * 8u + k];
+  const uint32_t wn = w | pa;
+  const uint32_t fs = (((wn ^ sR) | 0x88888u) - 0x11111u) & 0x88888u;
+  const uint32_t fp = (((wn ^ spR) | 0x88888u) - 0x11111u) & 0x88888u;
+  const int idx = (int)(__popc(fs) + 6u * (fs >> 19)) - (int)(__popc(fp) + 6u * (fp >> 19)) + 11;
+  const uint2 row = Tb.rows[idx];
+  const bool accept = CMP64 ? ((unsigned long long)u < Tb.T64[idx]) : (u <= row.x);
+  if (accept) {
+    w ^= (sR ^ spR) & (0xFu << sh);
+    pk += row.y;
   }
-  uint32_t cnt = oh[0] + oh[1] + oh[2] + oh[3];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const uint32_t wa = cnt + nb8[a];
-    const uint32_t off = 8u * t4[a] + 4u * kk[a];  // byte offset of entry 8 sigma + k
-    const uint32_t tp = lds_at(P.t4, off);
-    const uint32_t mp = lds_at(P.m, off);
-    const uint32_t ohp = lds_at(P.oh, off);
-    const int fsp = (int)nibble(wa, mp);
-    const int fs = (int)nibble(wa, m[a]);
-    if (accept_draw<CMP64>(acc[a], T[fsp - fs + 12])) {
-      cnt = cnt + ohp - oh[a];
-      oh[a] = ohp;
-      m[a] = mp;
-      t4[a] = tp;
-      ++naccepted;
-    }
-  }
-  if (count_pairs) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a) pair_sum += nibble(cnt, m[a]);
-  }
-  cnt_out = cnt;
-  uint32_t bonds = 0;
-  if (BONDS) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a) bonds += __umulhi(nb8[a] * m[a], 2u);
-  }
-  return bonds;
+  return w;
 }
 
-// 4*sigma of arm b of the 16-bit cell in half `hi` of a word.
-__device__ __forceinline__ uint32_t arm4(uint32_t word, int hi, int b) {
-  const int sh = 16 * hi + 3 * b - 2;
-  return (sh >= 0) ? ((word >> sh) & 0x1Cu) : ((word << 2) & 0x1Cu);
+// Count word of a cell: nibble v = number of its arms in state v.
+__device__ __forceinline__ uint32_t count_word4(uint32_t w) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) c += 1u << (4u * ((w >> (4 * b)) & 7u));
+  return c;
 }
 
 // Philox key material of the lattice being swept: the precomputed round keys
@@ -131,41 +127,43 @@ __device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi, 
   }
 }
 
-// Update the cell in half `hi` of word `own`; xm / xp are the words to the
-// left / right, ym / yp the words of the rows y-1 / y+1.
-template <int RNG_WORDS, bool CMP64, bool BONDS, typename KEYS>
-__device__ __forceinline__ uint32_t update_in_word(
-    uint32_t own, uint32_t xm_word, uint32_t xp_word, uint32_t ym_word, uint32_t yp_word, int hi,
-    uint32_t c, uint32_t s_lo, uint32_t s_hi, const KEYS& keys, uint32_t q,
-    const ProposalTable& P, const typename ThresholdRow<CMP64>::type* T, uint32_t& nacc,
-    uint32_t& pair_sum, uint32_t& bonds, uint32_t* s_hist4) {
-  // partner arms: arm 0 (+x) <-> arm 1 of the +x cell, arm 1 (-x) <-> arm 0 of
-  // the -x cell, arm 2 (+y) <-> arm 3 of the +y cell, arm 3 <-> arm 2 of -y
-  uint32_t n4[4];
+// Update the cell in half `hi` of word `own` (its four arms in order, each
+// seeing the earlier ones); xm / xp are the words to the left / right, ym /
+// yp the words of the rows y-1 / y+1.  Accepted moves add their packed count
+// changes to pk; with s_hist4 (recorded steps) the cell's N_q' is counted.
+template <int RNG_WORDS, bool CMP64, typename KEYS>
+__device__ __forceinline__ uint32_t update_in_word(uint32_t own, uint32_t xm_word,
+                                                   uint32_t xp_word, uint32_t ym_word,
+                                                   uint32_t yp_word, int hi, uint32_t c,
+                                                   uint32_t s_lo, uint32_t s_hi,
+                                                   const KEYS& keys, uint32_t q,
+                                                   const Tables2& Tb, uint32_t& pk,
+                                                   uint32_t* s_hist4) {
+  // partners, moved to bits 16..18: arm 0 (+x) <-> arm 1 of the +x cell,
+  // arm 1 (-x) <-> arm 0 of the -x cell, arm 2 (+y) <-> arm 3 of the +y cell,
+  // arm 3 (-y) <-> arm 2 of the -y cell
+  uint32_t w, p0, p1, p2, p3;
   if (hi) {
-    n4[0] = arm4(xp_word, 0, 1);
-    n4[1] = arm4(own, 0, 0);
+    w = own >> 16;
+    p0 = (xp_word << 12) & 0x70000u;
+    p1 = (own << 16) & 0x70000u;
+    p2 = (yp_word >> 12) & 0x70000u;
+    p3 = (ym_word >> 8) & 0x70000u;
   } else {
-    n4[0] = arm4(own, 1, 1);
-    n4[1] = arm4(xm_word, 1, 0);
-  }
-  n4[2] = arm4(yp_word, hi, 3);
-  n4[3] = arm4(ym_word, hi, 2);
-  uint32_t nb8[4], t4[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    nb8[a] = 8u << n4[a];
-    t4[a] = arm4(own, hi, a);
+    w = own & 0xFFFFu;
+    p0 = (own >> 4) & 0x70000u;
+    p1 = xm_word & 0x70000u;
+    p2 = (yp_word << 4) & 0x70000u;
+    p3 = (ym_word << 8) & 0x70000u;
   }
   uint32_t acc[4], kk[4];
   draws<RNG_WORDS>(c, s_lo, s_hi, keys, q, acc, kk);
-  uint32_t cnt;
-  // equal pairs (N_sigma) and N_q' only on recorded steps (s_hist4 set)
-  bonds += update_arms_tab<CMP64, BONDS>(t4, nb8, acc, kk, P, T, nacc, pair_sum, cnt,
-                                         s_hist4 != nullptr);
-  if (s_hist4) hist_add_cell(s_hist4, cnt);
-  const uint32_t wn = (t4[0] >> 2) | (t4[1] << 1) | (t4[2] << 4) | (t4[3] << 7);
-  return hi ? ((own & 0xFFFFu) | (wn << 16)) : ((own & 0xFFFF0000u) | wn);
+  w = update_arm2<CMP64>(w, p0, acc[0], kk[0], 0u, Tb, pk);
+  w = update_arm2<CMP64>(w, p1, acc[1], kk[1], 4u, Tb, pk);
+  w = update_arm2<CMP64>(w, p2, acc[2], kk[2], 8u, Tb, pk);
+  w = update_arm2<CMP64>(w, p3, acc[3], kk[3], 12u, Tb, pk);
+  if (s_hist4) hist_add_cell(s_hist4, count_word4(w));
+  return hi ? ((own & 0xFFFFu) | (w << 16)) : ((own & 0xFFFF0000u) | w);
 }
 
 // Staged input: rows y0-2 .. y0+TR+1 and words p0-4 .. p0+TW+3 (a 16-byte
@@ -178,11 +176,20 @@ struct TileSmem {
   uint32_t mid[TR + 2][TW + 2];
 };
 
-// Per-thread counts of the cells a thread finished inside its tiles:
-// pair_sum adds 4 + 2 (equal pairs) per counted cell.
+// Per-thread totals of the accepted moves of the cells a thread finished
+// inside its tiles (ring cells, recomputed by a neighbouring tile that owns
+// them, are not counted): their number and the biased sums of dN_HB + 1 and
+// dN_sigma + 3, moved out of a phase's packed word after each colour phase
+// (a phase adds fewer than 2^10 / 6 moves per thread).
 struct TileCounts {
-  uint32_t pair_sum, ncells, bonds, nacc;
-  __device__ __forceinline__ uint32_t pairs() const { return (pair_sum - 4u * ncells) >> 1; }
+  uint32_t nacc, hb_b, dc_b;
+  __device__ __forceinline__ void add(uint32_t pk) {
+    nacc += pk >> 20;
+    hb_b += (pk >> 10) & 0x3FFu;
+    dc_b += pk & 0x3FFu;
+  }
+  __device__ __forceinline__ int dhb() const { return (int)(hb_b - nacc); }
+  __device__ __forceinline__ int dc() const { return (int)(dc_b - 3u * nacc); }
 };
 
 // One lattice for one step, as a tile sees it.
@@ -230,12 +237,11 @@ __device__ __forceinline__ void stage_plain(const StepView<KEYS>& v, const TileG
 // is its low half on even rows, its high half on odd rows), then the one
 // colour-0 cell per row just outside the tile (x0 - 1, high half of word -1,
 // on odd rows; x0 + 2 tw, low half of word tw, on even rows).  Reads S.in,
-// writes S.mid.  s_hist4 != nullptr (recorded steps): N_q' and the equal
-// pairs of the tile's cells are counted.
+// writes S.mid.  s_hist4 != nullptr (recorded steps): N_q' of the tile's
+// cells is counted.
 template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS>
 __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom& g,
-                                        TileSmem<TR, TW>& S, const ProposalTable& P,
-                                        const typename ThresholdRow<CMP64>::type* T,
+                                        TileSmem<TR, TW>& S, const Tables2& Tb,
                                         TileCounts& cnt, uint32_t* s_hist4) {
   constexpr int kRows = (TW >= 32) ? 1 : 32 / TW;  // rows per warp pass
   constexpr int kLanes = (TW >= 32) ? 32 : TW;     // lanes per row
@@ -244,6 +250,7 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lrow = lane / kLanes, lcol = lane % kLanes;
   const int th = g.th, tw = g.tw, y0 = g.y0, p0 = g.p0;
+  uint32_t pk = 0;
   for (int r0 = warp * kRows - 1; r0 <= th; r0 += (NT / 32) * kRows) {
     const int r = r0 + lrow;
     if (r > th) continue;
@@ -253,16 +260,16 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
     const bool inside = (r >= 0) && (r < th);
     for (int j = lcol; j < tw; j += kLanes) {
       const int xg = 2 * (p0 + j) + hi;
-      uint32_t dummy = 0, dummy_b = 0;
-      const uint32_t out = update_in_word<RNG_WORDS, CMP64, false>(
+      uint32_t pk_row = 0;
+      const uint32_t out = update_in_word<RNG_WORDS, CMP64>(
           S.in[r + 2][j + C], S.in[r + 2][j + C - 1], S.in[r + 2][j + C + 1],
           S.in[r + 1][j + C], S.in[r + 3][j + C], hi, (uint32_t)((long long)yg * L + xg),
-          v.s_lo, v.s_hi, v.keys, v.q, P, T, inside ? cnt.nacc : dummy,
-          inside ? cnt.pair_sum : dummy, dummy_b, inside ? s_hist4 : nullptr);
-      if (inside) ++cnt.ncells;
+          v.s_lo, v.s_hi, v.keys, v.q, Tb, pk_row, inside ? s_hist4 : nullptr);
+      if (inside) pk += pk_row;  // the halo rows belong to other tiles
       S.mid[r + 1][j + 1] = out;
     }
   }
+  cnt.add(pk);
   // the ring goes to the warps after the first two, which take one row of
   // the th + 2 fewer than warps 0 and 1 when 8 warps share 66 rows
   const int ring0 = (NT >= 128 && TW >= 32) ? 64 : 0;
@@ -275,13 +282,13 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
     const int yg = (y < 0) ? y + L : (y >= L ? y - L : y);
     int xg = 2 * (p0 + j) + hi;
     xg = (xg < 0) ? xg + L : (xg >= L ? xg - L : xg);
-    uint32_t d0 = 0, d1 = 0, d2 = 0;
+    uint32_t not_counted = 0;  // the ring cells belong to the neighbouring tiles
     // the unused side of the ring word is clamped into the staged columns
     const int jm = max(j, 0), jp = min(j + 2, tw + 1);
-    S.mid[r + 1][j + 1] = update_in_word<RNG_WORDS, CMP64, false>(
+    S.mid[r + 1][j + 1] = update_in_word<RNG_WORDS, CMP64>(
         S.in[r + 2][j + C], S.in[r + 2][jm + kInColOff], S.in[r + 2][jp + kInColOff],
         S.in[r + 1][j + C], S.in[r + 3][j + C], hi, (uint32_t)((long long)yg * L + xg), v.s_lo,
-        v.s_hi, v.keys, v.q, P, T, d0, d1, d2, nullptr);
+        v.s_hi, v.keys, v.q, Tb, not_counted, nullptr);
   }
 }
 
@@ -289,8 +296,7 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
 // from S.mid to the destination buffer.
 template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS>
 __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom& g,
-                                        TileSmem<TR, TW>& S, const ProposalTable& P,
-                                        const typename ThresholdRow<CMP64>::type* T,
+                                        TileSmem<TR, TW>& S, const Tables2& Tb,
                                         TileCounts& cnt, uint32_t* s_hist4) {
   constexpr int kRows = (TW >= 32) ? 1 : 32 / TW;
   constexpr int kLanes = (TW >= 32) ? 32 : TW;
@@ -298,6 +304,7 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lrow = lane / kLanes, lcol = lane % kLanes;
   const int th = g.th, tw = g.tw, y0 = g.y0, p0 = g.p0;
+  uint32_t pk = 0;
   for (int r0 = warp * kRows; r0 < th; r0 += (NT / 32) * kRows) {
     const int r = r0 + lrow;
     if (r >= th) continue;
@@ -306,13 +313,13 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
     uint32_t* drow = v.dst + (size_t)y * Lh + p0;
     for (int j = lcol; j < tw; j += kLanes) {
       const int xg = 2 * (p0 + j) + hi;
-      drow[j] = update_in_word<RNG_WORDS, CMP64, true>(
+      drow[j] = update_in_word<RNG_WORDS, CMP64>(
           S.mid[r + 1][j + 1], S.mid[r + 1][j], S.mid[r + 1][j + 2], S.mid[r][j + 1],
           S.mid[r + 2][j + 1], hi, (uint32_t)((long long)y * L + xg), v.s_lo, v.s_hi, v.keys,
-          v.q, P, T, cnt.nacc, cnt.pair_sum, cnt.bonds, s_hist4);
-      ++cnt.ncells;
+          v.q, Tb, pk, s_hist4);
     }
   }
+  cnt.add(pk);
 }
 
 // Sweep the tile at rows y0.., words p0.. of one lattice with synchronous
@@ -320,22 +327,20 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
 // to dst (no trailing barrier: the caller synchronises before reusing the
 // shared buffers).  s_hist4 != nullptr (recorded steps): N_q' of the tile's
 // cells is added to hist_out[0..8) through the block's four zeroed shared
-// words, and the equal pairs (N_sigma) are counted; on other steps neither
-// is (N_HB_raw, which the volume move needs, and the accepted moves are
-// counted on every step).  A warp covers max(1, 32/TW) rows per pass.
+// words.  The accepted moves and their dN_HB, dN_sigma are counted on every
+// step.  A warp covers max(1, 32/TW) rows per pass.
 template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS, bool CG = false>
 __device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int p0,
-                                           TileSmem<TR, TW>& S, const ProposalTable& P,
-                                           const typename ThresholdRow<CMP64>::type* T,
+                                           TileSmem<TR, TW>& S, const Tables2& Tb,
                                            TileCounts& cnt, uint32_t* s_hist4,
                                            unsigned long long* hist_out) {
   static_assert(TW >= 32 ? (TW % 32 == 0) : (32 % TW == 0), "tile width");
   const TileGeom g = tile_geom<TR, TW>(v.L, v.Lh, y0, p0);
   stage_plain<TR, TW, NT, CG>(v, g, S);
   __syncthreads();
-  colour0<RNG_WORDS, CMP64, TR, TW, NT>(v, g, S, P, T, cnt, s_hist4);
+  colour0<RNG_WORDS, CMP64, TR, TW, NT>(v, g, S, Tb, cnt, s_hist4);
   __syncthreads();
-  colour1<RNG_WORDS, CMP64, TR, TW, NT>(v, g, S, P, T, cnt, s_hist4);
+  colour1<RNG_WORDS, CMP64, TR, TW, NT>(v, g, S, Tb, cnt, s_hist4);
   if (s_hist4) {  // block-uniform: only on recorded steps
     __syncthreads();
     hist_flush(s_hist4, hist_out);

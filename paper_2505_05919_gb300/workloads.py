@@ -20,7 +20,7 @@ def random_words(L: int, q: int, seed: int) -> np.ndarray:
     arms = rng.integers(0, q, size=(L * L, 4), dtype=np.uint16)
     w = np.zeros(L * L, np.uint16)
     for a in range(4):
-        w |= (arms[:, a] << (3 * a)).astype(np.uint16)
+        w |= (arms[:, a] << (4 * a)).astype(np.uint16)
     return w.reshape(L, L)
 
 

@@ -19,7 +19,7 @@ def test_oracle_state_counts_direct():
     w = o.state().ravel().astype(np.int64)
     direct = np.zeros(8, np.int64)
     for a in range(4):
-        direct += np.bincount((w >> (3 * a)) & 7, minlength=8)
+        direct += np.bincount((w >> (4 * a)) & 7, minlength=8)
     assert list(ob["n_state"]) == list(direct)
     assert sum(ob["n_state"]) == 4 * 144 and all(x == 0 for x in ob["n_state"][5:])
 

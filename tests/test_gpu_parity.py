@@ -183,7 +183,7 @@ def test_invalid_inputs_rejected():
             lat.set_state(bad, V_iso=80.0)
         assert e.value.code == _capi.CVF_EINVAL
         bad = before.copy()
-        bad[0, 0] |= 1 << 13
+        bad[0, 0] |= 1 << 15
         with pytest.raises(_capi.CvfError):
             lat.set_state(bad, V_iso=80.0)
         with pytest.raises(_capi.CvfError):

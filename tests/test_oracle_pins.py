@@ -35,7 +35,7 @@ def _arms_2x2_q2(i):
     w = np.zeros((i.size, 4), np.uint16)
     for c in range(4):
         for a in range(4):
-            w[:, c] |= (((i >> (4 * c + a)) & 1) << (3 * a)).astype(np.uint16)
+            w[:, c] |= (((i >> (4 * c + a)) & 1) << (4 * a)).astype(np.uint16)
     return w
 
 
@@ -46,7 +46,7 @@ def _counts_bruteforce(words, L):
     convention of the paper's worked layout example); N_sigma counts equal
     pairs of arms inside each cell."""
     words = np.asarray(words).reshape(-1, L, L).astype(np.int64)
-    arm = [(words >> (3 * a)) & 7 for a in range(4)]
+    arm = [(words >> (4 * a)) & 7 for a in range(4)]
     hb = (arm[0] == np.roll(arm[1], -1, axis=2)).sum(axis=(1, 2))
     hb += (arm[2] == np.roll(arm[3], -1, axis=1)).sum(axis=(1, 2))
     co = np.zeros(words.shape[0], np.int64)
@@ -152,10 +152,10 @@ def _detailed_balance_check(p, cfgs, g, rev_cfgs=None):
             for k in range(q - 1):
                 new = cfgs.copy()
                 sp = s_new[:, c, a, k].astype(np.uint16)
-                s_old = (cfgs[:, c] >> (3 * a)) & 7
+                s_old = (cfgs[:, c] >> (4 * a)) & 7
                 assert np.all(sp != s_old) and np.all(sp < q)
                 assert np.all(sp == (s_old + 1 + k) % q)
-                new[:, c] = (new[:, c] & ~np.uint16(7 << (3 * a))) | (sp << (3 * a))
+                new[:, c] = (new[:, c] & ~np.uint16(7 << (4 * a))) | (sp << (4 * a))
                 hb2, co2 = _counts_bruteforce(new, L)
                 E2 = -(g * J_eff) * hb2 - p.J_sigma * co2
                 dE = E2 - E
@@ -189,7 +189,7 @@ def test_detailed_balance_4x4_q3_sampled():
     arms = rng.integers(0, 3, size=(60, 16, 4))
     cfgs = np.zeros((60, 16), np.uint16)
     for a in range(4):
-        cfgs |= (arms[:, :, a] << (3 * a)).astype(np.uint16)
+        cfgs |= (arms[:, :, a] << (4 * a)).astype(np.uint16)
     _detailed_balance_check(p, cfgs, 1)
 
 
