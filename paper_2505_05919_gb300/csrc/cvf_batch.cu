@@ -82,7 +82,7 @@ __global__ void k_batch_reset(BatchWork* W, unsigned int* progress, int n_replic
 }
 
 template <int RNG_WORDS, bool CMP64, int TR, int TW>
-__global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM) k_batch_sweep(const ReplicaDesc* __restrict__ reps,
+__global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(const ReplicaDesc* __restrict__ reps,
                                                              BatchWork* W,
                                                              const int32_t* __restrict__ order,
                                                              const long long* __restrict__ tile_prefix,

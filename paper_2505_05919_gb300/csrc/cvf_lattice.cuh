@@ -11,8 +11,11 @@ constexpr int kThreads = 256;
 // tiles of the single-lattice sweep: 64 rows x 64 words (128 cells)
 constexpr int kTileRows = 64;
 constexpr int kTileWords = 64;
-// register budget of the sweep kernel: four 256-thread blocks per SM
-constexpr int kSweepBlocksPerSM = 4;
+// register budgets: five 256-thread blocks per SM for the single-lattice
+// sweep (the most its 38 KB of shared memory allows), four for the batched
+// kernel
+constexpr int kSweepBlocksPerSM = 5;
+constexpr int kBatchBlocksPerSM = 4;
 
 struct LatticeArgs {
   uint16_t* state;                   // state pair: 2 * L*L packed cell words

@@ -258,6 +258,8 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
     const int hi = y & 1;
     const int yg = (y < 0) ? y + L : (y >= L ? y - L : y);
     const bool inside = (r >= 0) && (r < th);
+    // two cells per iteration give the scheduler two independent arm chains
+#pragma unroll 2
     for (int j = lcol; j < tw; j += kLanes) {
       const int xg = 2 * (p0 + j) + hi;
       uint32_t pk_row = 0;
@@ -311,6 +313,7 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
     const int y = y0 + r;
     const int hi = (y & 1) ^ 1;
     uint32_t* drow = v.dst + (size_t)y * Lh + p0;
+#pragma unroll 2
     for (int j = lcol; j < tw; j += kLanes) {
       const int xg = 2 * (p0 + j) + hi;
       drow[j] = update_in_word<RNG_WORDS, CMP64>(
