@@ -183,6 +183,34 @@ def cpu_baseline(cfg, sample_sweeps):
                       "init %.1f s not counted" % (cfg["L"], sample_sweeps, cfg["seed"], cfg["T"], t1 - t0)}
 
 
+def _oracle_replica(args):
+    """One oracle replica for the all-cores baseline (runs in a spawned
+    process): L x L lattice from the random init, `steps` MC steps."""
+    cfg, seed_offset, steps = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    o = oracle.Oracle(oracle_params(cfg, seed_offset=seed_offset))
+    t0 = time.perf_counter()
+    o.run(steps)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(cfg, L=1024, steps=20):
+    """nproc independent oracle replicas run concurrently, one per host core
+    (independent seeds): aggregate sigma updates per ns over the slowest."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    c = dict(cfg)
+    c["L"] = L
+    ctx = mp.get_context("spawn")  # never fork a process that holds a CUDA context
+    with ctx.Pool(n) as pool:
+        times = pool.map(_oracle_replica, [(c, i, steps) for i in range(n)])
+    upd = 4.0 * L * L * steps * n
+    return {"value": upd / (max(times) * 1e9), "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": "%d concurrent replicas (one per core), each L=%d, %d MC steps from the random "
+                      "init (seeds %d..%d), %g K" % (n, L, steps, cfg["seed"], cfg["seed"] + n - 1, cfg["T"])}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -533,12 +561,16 @@ def main():
 
     line = None
     if rank == 0:
-        cpu = None
+        cpu = cpu_all = None
         if not args.no_cpu_baseline and world == 1:
             try:
                 cpu = cpu_baseline(cfgs[1], args.cpu_sample_sweeps)
             except Exception as e:  # the baseline never blocks the line
                 cpu = {"value": None, "error": str(e)}
+            try:
+                cpu_all = cpu_baseline_all_cores(cfgs[1])
+            except Exception as e:
+                cpu_all = {"value": None, "error": str(e)}
         launches_per_sweep = 1  # k_sweep_tiled (the volume move runs inside it)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -551,6 +583,7 @@ def main():
             "roofline": roofline,
             "roofline_hbm": roofline_hbm,
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
             "e2e": e2e,
             "gpu_launches": args.steps * (S * launches_per_sweep + 1),
             "batched": batched,
