@@ -538,8 +538,9 @@ def main():
 
     # end to end through the C ABI with host buffers
     e2e_ms = []
-    host_in = np.empty((L, L), np.uint16)
-    host_out = np.empty((L, L), np.uint16)
+    # pinned host buffers (the contract's end-to-end copies)
+    host_in = torch.empty((L, L), dtype=torch.int16, pin_memory=True).numpy().view(np.uint16)
+    host_out = torch.empty((L, L), dtype=torch.int16, pin_memory=True).numpy().view(np.uint16)
     lat = lats[1]
     host_in[:] = lat.state()
     V0 = lat.observables()["V_iso"]

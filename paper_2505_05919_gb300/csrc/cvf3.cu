@@ -890,7 +890,18 @@ int cvf3_set_state(cvf3_handle* h, const uint32_t* host, size_t n, double V_iso,
     return set_error(CVF_EINVAL, "V_iso=%g must be >= N=%lld (hard core)", V_iso, h->N);
   if (sweep < 0) return set_error(CVF_EINVAL, "sweep=%lld must be >= 0", (long long)sweep);
   const uint32_t q = (uint32_t)h->p.q;
-  for (size_t i = 0; i < n; ++i) {
+  // two cells per 64-bit load: bits outside the arms' sigma bits must be
+  // clear, and then a nibble v is >= q exactly when v + 8 - q sets its bit 3
+  const uint64_t keep = ((uint64_t)kArmBits << 32) | kArmBits;
+  const uint64_t G = ((uint64_t)0x888888u << 32) | 0x888888u;
+  const uint64_t add = (uint64_t)(8u - q) * (((uint64_t)0x111111u << 32) | 0x111111u);
+  size_t i = 0;
+  for (; i + 2 <= n; i += 2) {
+    uint64_t x;
+    std::memcpy(&x, host + i, sizeof(x));
+    if ((x & ~keep) | ((x + add) & G)) break;
+  }
+  for (; i < n; ++i) {
     const uint32_t w = host[i];
     bool ok = (w & ~kArmBits) == 0u;
     for (int a = 0; a < 6 && ok; ++a) ok = ((w >> (4 * a)) & 7u) < q;

@@ -575,6 +575,28 @@ int recount_into_ctrl(cvf_handle* h) {
   return CVF_OK;
 }
 
+// Index of the first word that is not a valid cell (a nibble >= q, or a
+// nibble's bit 3 set), n if none.  Four cells per 64-bit load: with the
+// guard bits clear every nibble v is <= 7, and v + 8 - q sets the nibble's
+// bit 3 exactly when v >= q (no carry leaves a nibble: v + 8 - q <= 13).
+size_t first_invalid_cell(const uint16_t* host, size_t n, uint32_t q) {
+  const uint64_t G = 0x8888888888888888ull;
+  const uint64_t add = (uint64_t)(8u - q) * 0x1111111111111111ull;
+  size_t i = 0;
+  for (; i + 4 <= n; i += 4) {
+    uint64_t x;
+    std::memcpy(&x, host + i, sizeof(x));
+    if ((x & G) | ((x + add) & G)) break;
+  }
+  for (; i < n; ++i) {
+    const uint32_t w = host[i];
+    if ((w & 0x8888u) || ((w & 7u) >= q) || (((w >> 4) & 7u) >= q) || (((w >> 8) & 7u) >= q) ||
+        (((w >> 12) & 7u) >= q))
+      return i;
+  }
+  return n;
+}
+
 int build_graph(cvf_handle* h) {
   if (h->graph) return CVF_OK;
   cudaGraph_t g = nullptr;
@@ -763,13 +785,10 @@ int cvf_set_state(cvf_handle* h, const uint16_t* host, size_t n, double V_iso, i
   if (!(V_iso >= (double)h->N) || !std::isfinite(V_iso))
     return set_error(CVF_EINVAL, "V_iso=%g below the hard core N v0 = %lld", V_iso, h->N);
   if (sweep < 0) return set_error(CVF_EINVAL, "sweep must be >= 0");
-  const uint32_t q = (uint32_t)h->p.q;
-  for (size_t i = 0; i < n; ++i) {
-    const uint32_t w = host[i];
-    if ((w & 0x8888u) || ((w & 7u) >= q) || (((w >> 4) & 7u) >= q) || (((w >> 8) & 7u) >= q) ||
-        (((w >> 12) & 7u) >= q))
-      return set_error(CVF_EINVAL, "word %zu = 0x%04x is not a valid cell for q = %u", i, w, q);
-  }
+  const size_t bad = first_invalid_cell(host, n, (uint32_t)h->p.q);
+  if (bad < n)
+    return set_error(CVF_EINVAL, "word %zu = 0x%04x is not a valid cell for q = %d", bad,
+                     (unsigned)host[bad], h->p.q);
   h->sweep_host = sweep;
   CVF_CUDA_CHECK(cudaMemcpyAsync(current(h), host, sizeof(uint16_t) * n, cudaMemcpyHostToDevice,
                                  h->stream));
