@@ -309,77 +309,201 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     finalize_step<true>(*A.vol, ctl, A.ring, A.ring_cap, A.keys);
 }
 
-// Layered schedule: pass `pass` updates arm order[pass] of every cell, where
-// the order is a Fisher-Yates permutation drawn from Philox((2^32-2, step,
-// tag 4)).  The same arm of all cells forms one domain (its members interact
-// only with other domains).  Pass 0 reads the step's source buffer and writes
-// every cell to the other buffer; passes 1..3 update that buffer in place.
-template <int RNG_WORDS>
-__global__ void __launch_bounds__(kThreads) k_layer_pass(LatticeArgs A, int pass) {
-  __shared__ unsigned long long sT[24];
-  __shared__ int s_arm;
-  Ctrl* ctl = A.ctrl;
-  const int g = ctl->next_g;
-  const long long step = ctl->sweep;
-  const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
-  const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
-  if (threadIdx.x < 24) sT[threadIdx.x] = A.table24[g * 24 + threadIdx.x];
-  if (threadIdx.x == 0) {
-    const Words4 r = philox(kCellLayers, s_lo, s_hi, kTagLayers, A.keys);
-    const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
-    int order[4] = {0, 1, 2, 3};
-    for (int i = 3; i >= 1; --i) {
-      const int j = (int)__umulhi(rw[3 - i], (uint32_t)(i + 1));
-      const int t = order[i];
-      order[i] = order[j];
-      order[j] = t;
-    }
-    s_arm = order[pass];
+// ---------------------------------------------------------------------------
+// Layered schedule (the paper's own scheme, Sec. II.C): the four arm domains
+// one after the other, in a Fisher-Yates order drawn from Philox((2^32-2,
+// step, tag 4)).  A pass over arm a reads, besides the cell, only arm a^1 of
+// its neighbour in direction a, which only the pass over a^1 changes; so
+// consecutive passes without an opposite pair share a launch, each thread
+// taking its two cells (one word) through them in registers (every partner
+// arm it reads is constant during the launch).  The order is cut before the
+// first arm whose opposite is already in the launch: 2 or 3 launches; every
+// step enqueues kLayerLaunches, the unused ones return at once, the last one
+// commits the step.  Launch 0 reads the step's source buffer and writes every
+// word of the other buffer; the later launches update that buffer in place.
+// A cell's draws are its Philox((c, step, 0)) words (and tag 1 with two
+// words per update), recomputed in every launch that updates the cell.
+// ---------------------------------------------------------------------------
+constexpr int kLayerLaunches = 3;
+
+// Plan word: bits 2i..2i+1 the arm of pass i, bit 8 + i set when pass i
+// opens a new launch (i = 1..3).
+__device__ uint32_t layer_plan(long long step, const RoundKeys& K) {
+  const Words4 r = philox(kCellLayers, (uint32_t)((unsigned long long)step & 0xFFFFFFFFu),
+                          (uint32_t)((unsigned long long)step >> 32), kTagLayers, K);
+  const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
+  int order[4] = {0, 1, 2, 3};
+  for (int i = 3; i >= 1; --i) {
+    const int j = (int)__umulhi(rw[3 - i], (uint32_t)(i + 1));
+    const int t = order[i];
+    order[i] = order[j];
+    order[j] = t;
   }
-  __syncthreads();
-  const int a = s_arm;
-  const int L = A.L;
-  const long long N = (long long)L * L;
-  uint16_t* dst = A.state + (size_t)((step + 1) & 1) * N;
-  const uint16_t* src = (pass == 0) ? A.state + (size_t)(step & 1) * N : dst;
-  uint32_t nacc = 0, unused0 = 0, unused1 = 0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(c / L), x = (int)(c - (long long)y * L);
-    int xn = x, yn = y;
-    if (a == 0) xn = (x + 1 == L) ? 0 : x + 1;
-    else if (a == 1) xn = (x == 0) ? L - 1 : x - 1;
-    else if (a == 2) yn = (y + 1 == L) ? 0 : y + 1;
-    else yn = (y == 0) ? L - 1 : y - 1;
-    const uint32_t w = src[c];
-    const uint32_t n = arm_of(src[(long long)yn * L + xn], a ^ 1);
-    uint32_t acc[4], kk[4];
-    cell_draws<RNG_WORDS>((uint32_t)c, s_lo, s_hi, A.keys, A.q, acc, kk);
-    const uint32_t s = arm_of(w, a);
-    uint32_t sp = s + 1u + kk[a];
-    sp = (sp >= A.q) ? sp - A.q : sp;
-    const int dhb = (int)(sp == n) - (int)(s == n);
-    int dc = 0;
-    for (int b = 0; b < 4; ++b) {
-      if (b == a) continue;
-      const uint32_t sb = arm_of(w, b);
-      dc += (int)(sp == sb) - (int)(s == sb);
+  uint32_t plan = 0, in_launch = 0;
+  for (int i = 0; i < 4; ++i) {
+    const int a = order[i];
+    if (in_launch & (1u << (a ^ 1))) {
+      plan |= 1u << (8 + i);
+      in_launch = 0;
     }
-    uint32_t wn = w;
-    if ((unsigned long long)acc[a] < sT[(dhb + 1) * 8 + (dc + 3)]) {
-      wn = (w & ~(7u << (4 * a))) | (sp << (4 * a));
-      ++nacc;
-    }
-    if (pass == 0 || wn != w) dst[c] = (uint16_t)wn;
+    in_launch |= 1u << a;
+    plan |= (uint32_t)a << (2 * i);
   }
-  block_sum3<kThreads>(nacc, unused0, unused1);
-  if (threadIdx.x == 0) atomicAdd(&ctl->acc_moves, (unsigned long long)nacc);
+  return plan;
 }
 
-// Close a layered step after the recount of its final configuration.
-__global__ void k_finalize(LatticeArgs A) {
-  if (threadIdx.x == 0 && blockIdx.x == 0)
-    finalize_step(*A.vol, A.ctrl, A.ring, A.ring_cap, A.keys);
+__device__ int layer_plan_arms(uint32_t plan, int j, int* arms) {
+  int launch = 0, n = 0;
+  for (int i = 0; i < 4; ++i) {
+    if (i > 0 && ((plan >> (8 + i)) & 1u)) ++launch;
+    if (launch == j && n < 2) arms[n++] = (int)((plan >> (2 * i)) & 3u);
+  }
+  return n;
+}
+
+// The partner of arm a of the cell in half `hi` of word `own` (at column p
+// of row y), moved to bits 16..18: arm a^1 of the neighbour in direction a.
+__device__ __forceinline__ uint32_t layer_partner(int a, int hi, uint32_t own, const uint32_t* buf,
+                                                  uint32_t y, uint32_t p, uint32_t L,
+                                                  uint32_t Lh) {
+  if (a == 0) {  // +x: arm 1 of the cell to the right
+    if (!hi) return (own >> 4) & 0x70000u;
+    const uint32_t pn = (p + 1u == Lh) ? 0u : p + 1u;
+    return (buf[y * Lh + pn] << 12) & 0x70000u;
+  }
+  if (a == 1) {  // -x: arm 0 of the cell to the left
+    if (hi) return (own << 16) & 0x70000u;
+    const uint32_t pm = (p == 0u) ? Lh - 1u : p - 1u;
+    return buf[y * Lh + pm] & 0x70000u;
+  }
+  if (a == 2) {  // +y: arm 3 of the cell below, same half
+    const uint32_t yn = (y + 1u == L) ? 0u : y + 1u;
+    const uint32_t wv = buf[yn * Lh + p];
+    return hi ? (wv >> 12) & 0x70000u : (wv << 4) & 0x70000u;
+  }
+  const uint32_t ym = (y == 0u) ? L - 1u : y - 1u;  // -y: arm 2 of the cell above
+  const uint32_t wv = buf[ym * Lh + p];
+  return hi ? (wv >> 8) & 0x70000u : (wv << 8) & 0x70000u;
+}
+
+template <int RNG_WORDS, bool CMP64>
+__global__ void __launch_bounds__(kThreads) k_layer(LatticeArgs A, int launch) {
+  __shared__ Tables2 Tb;
+  __shared__ int s_arm[2];
+  __shared__ int s_n, s_rec;
+  __shared__ uint32_t s_hist[8];
+  Ctrl* ctl = A.ctrl;
+  const bool fin = (launch == kLayerLaunches - 1);
+  if (threadIdx.x == 0) {
+    uint32_t plan;
+    if (launch == 0) {
+      plan = layer_plan(ctl->sweep, A.keys);
+      if (blockIdx.x == 0) ctl->plan = (int)plan;
+    } else {
+      plan = (uint32_t)ctl->plan;
+    }
+    int arms[2] = {0, 0};
+    const int n = layer_plan_arms(plan, launch, arms);
+    s_n = n;
+    s_arm[0] = arms[0];
+    s_arm[1] = arms[1];
+    const int nlaunch = 1 + __popc(plan >> 9);
+    s_rec = (n > 0 && launch == nlaunch - 1 && step_recorded(ctl->record_every, ctl->sweep)) ? 1 : 0;
+  }
+  __syncthreads();
+  const int n_arms = s_n;
+  if (launch == 0 && blockIdx.x == 0) {
+    // the volume block: the next step's move, decided now unless it depends on the bonds
+    if (threadIdx.x == 0) {
+      VolumeResult r;
+      if (volume_decide(*A.vol, ctl->sweep + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1,
+                        A.keys, &r)) {
+        ctl->ahead_V = r.V;
+        ctl->ahead_u = r.u;
+        ctl->ahead_g = r.g;
+        ctl->ahead_acc = r.accepted;
+        ctl->ahead_state = 1;
+      }
+    }
+    return;
+  }
+  if (n_arms == 0) {
+    if (fin && blockIdx.x == 0 && threadIdx.x == 0)
+      finalize_step<true>(*A.vol, ctl, A.ring, A.ring_cap, A.keys);
+    return;
+  }
+  const long long step = ctl->sweep;
+  const int g = ctl->next_g;
+  const bool rec = s_rec != 0;
+  fill_rows2(Tb, A.table24, g);
+  fill_prop2(Tb, A.q);
+  if (threadIdx.x < 8) s_hist[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t L = (uint32_t)A.L, Lh = L >> 1;
+  const long long N = (long long)L * L;
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(A.state + (size_t)(step & 1) * N);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(A.state + (size_t)((step + 1) & 1) * N);
+  const uint32_t* in = (launch == 0) ? src : dst;  // the launch's input words
+  const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
+  const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
+  const int a0 = s_arm[0], a1 = s_arm[1];
+  const uint32_t first_block = (launch == 0) ? 1u : 0u;
+  const uint32_t nwords = (uint32_t)(N >> 1);
+  TileCounts cnt{0, 0, 0};
+  for (uint32_t wi = (blockIdx.x - first_block) * kThreads + threadIdx.x; wi < nwords;
+       wi += (gridDim.x - first_block) * kThreads) {
+    const uint32_t y = wi / Lh, p = wi - y * Lh;
+    const uint32_t own = in[wi];
+    uint32_t out = own;
+    uint32_t pk = 0;
+#pragma unroll
+    for (int hi = 0; hi < 2; ++hi) {
+      uint32_t w = hi ? (own >> 16) : (own & 0xFFFFu);
+      const uint32_t c = y * L + 2u * p + (uint32_t)hi;
+      uint32_t acc[4], kk[4];
+      cell_draws<RNG_WORDS>(c, s_lo, s_hi, A.keys, A.q, acc, kk);
+      for (int k = 0; k < n_arms; ++k) {
+        const int a = k ? a1 : a0;
+        const uint32_t pa = layer_partner(a, hi, own, in, y, p, L, Lh);
+        // the draws of arm a, selected without indexing the arrays at run time
+        const uint32_t ua = (a == 0) ? acc[0] : (a == 1) ? acc[1] : (a == 2) ? acc[2] : acc[3];
+        const uint32_t ka = (a == 0) ? kk[0] : (a == 1) ? kk[1] : (a == 2) ? kk[2] : kk[3];
+        w = update_arm2<CMP64>(w, pa, ua, ka, 4u * (uint32_t)a, Tb, pk);
+      }
+      out = hi ? ((out & 0xFFFFu) | (w << 16)) : ((out & 0xFFFF0000u) | w);
+    }
+    cnt.add(pk);
+    dst[wi] = out;
+    if (rec) {
+      // N_q' of the step's final cells: 16-bit lanes (state v, state v + 4)
+      // summed over the converged lanes of the warp, added by the lowest
+      const uint32_t h = count_word4(out & 0xFFFFu) + count_word4(out >> 16);
+      const unsigned mask = __activemask();
+      const int leader = __ffs(mask) - 1;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const uint32_t lanes = __reduce_add_sync(mask, (h >> (4 * v)) & 0x000F000Fu);
+        if ((int)(threadIdx.x & 31) == leader) {
+          if (lanes & 0xFFFFu) atomicAdd(&s_hist[v], lanes & 0xFFFFu);
+          if (lanes >> 16) atomicAdd(&s_hist[v + 4], lanes >> 16);
+        }
+      }
+    }
+  }
+  uint32_t dhb = (uint32_t)cnt.dhb(), dc = (uint32_t)cnt.dc(), nacc = cnt.nacc;
+  block_sum3<kThreads>(dhb, dc, nacc);  // two's complement sums
+  if (threadIdx.x == 0) {
+    atomicAdd(&ctl->acc_hb, (unsigned long long)(long long)(int)dhb);
+    atomicAdd(&ctl->acc_pairs, (unsigned long long)(long long)(int)dc);
+    atomicAdd(&ctl->acc_moves, (unsigned long long)nacc);
+  }
+  if (rec) {
+    __syncthreads();
+    if (threadIdx.x < 8 && s_hist[threadIdx.x])
+      atomicAdd(&ctl->acc_hist[threadIdx.x], (unsigned long long)s_hist[threadIdx.x]);
+  }
+  if (fin && last_block(&ctl->done) && threadIdx.x == 0)
+    finalize_step<true>(*A.vol, ctl, A.ring, A.ring_cap, A.keys);
 }
 
 }  // namespace cvf
@@ -454,7 +578,7 @@ struct cvf_handle {
   void* host_pinned;
   LatticeArgs args;
   CUtensorMap tm[2];  // TMA descriptors of the two halves of the state pair
-  int grid_tiles, grid_cells;
+  int grid_tiles, grid_cells, grid_layer;
   cudaGraphExec_t graph;
   int graph_steps;
 };
@@ -498,14 +622,17 @@ void enqueue_step(cvf_handle* h, cudaStream_t s) {
     else
       k_sweep_tiled<2, true><<<h->grid_tiles, kThreads, 0, s>>>(h->args, h->tm[0], h->tm[1]);
   } else {
-    for (int pass = 0; pass < 4; ++pass) {
-      if (one)
-        k_layer_pass<1><<<h->grid_cells, kThreads, 0, s>>>(h->args, pass);
+    for (int j = 0; j < kLayerLaunches; ++j) {
+      const int grid = h->grid_layer + (j == 0 ? 1 : 0);  // + the volume block
+      if (one && !h->cmp64)
+        k_layer<1, false><<<grid, kThreads, 0, s>>>(h->args, j);
+      else if (one)
+        k_layer<1, true><<<grid, kThreads, 0, s>>>(h->args, j);
+      else if (!h->cmp64)
+        k_layer<2, false><<<grid, kThreads, 0, s>>>(h->args, j);
       else
-        k_layer_pass<2><<<h->grid_cells, kThreads, 0, s>>>(h->args, pass);
+        k_layer<2, true><<<grid, kThreads, 0, s>>>(h->args, j);
     }
-    k_recount<<<h->grid_cells, kThreads, 0, s>>>(h->state, h->p.L, h->ctrl, &h->ctrl->acc_hb);
-    k_finalize<<<1, 32, 0, s>>>(h->args);
   }
 }
 
@@ -685,6 +812,7 @@ int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** 
   h->args.use_tma = encode_state_maps(h->state, p->L, h->tm) ? 1 : 0;
   h->sweep_host = 0;
   h->grid_cells = grid_for(h->N, 8);
+  h->grid_layer = grid_for(h->N / 2, 8);  // one word (two cells) per thread and iteration
 
   k_init<<<h->grid_cells, kThreads, 0, h->stream>>>(h->state, p->L, (uint32_t)p->q,
                                                      p->init == CVF_INIT_RANDOM ? 1 : 0,

@@ -74,7 +74,8 @@ def test_checkerboard_parity(L, K, extra):
     assert 0 <= o_gpu["n_hb_raw"] <= 2 * L * L and 0 <= o_gpu["n_coop"] <= 6 * L * L
 
 
-@pytest.mark.parametrize("L,K,rng_words", [(2, 100, 1), (8, 80, 2), (64, 60, 1), (130, 20, 2)])
+@pytest.mark.parametrize("L,K,rng_words", [(2, 100, 1), (8, 80, 2), (64, 60, 1), (130, 20, 2),
+                                           (258, 12, 1)])
 def test_layered_parity(L, K, rng_words):
     op = oracle.physical_params(300.0, 0.1, L=L, seed=7 + L, schedule=oracle.SCHED_LAYERED,
                                 rng_words=rng_words, dv_max_frac=0.02)
@@ -82,6 +83,31 @@ def test_layered_parity(L, K, rng_words):
     s_ref, o_ref, _ = oracle_run(op, K)
     assert np.array_equal(s_gpu, s_ref)
     assert_obs_equal(o_gpu, o_ref)
+
+
+@pytest.mark.parametrize("extra", [dict(L=6, T=270.0, init=oracle.INIT_ORDERED, q=3),
+                                   dict(L=16, T=330.0, P=50.0, q=8),
+                                   dict(L=4, kT=3.0, P=1.2, epsilon=0.0, v_iso_init=1.9,
+                                        dv_max_frac=0.2),                       # gate flips
+                                   dict(L=8, kT=1e-3, init=oracle.INIT_ORDERED)])  # 64-bit compare
+def test_layered_series_parity(extra):
+    """The layered schedule's recorded series (counts, N_q', volume, H every
+    3 steps) equal the oracle's, across both inits, state points, gate flips
+    and the 64-bit threshold compare."""
+    extra = dict(extra)
+    if "kT" in extra:  # reduced units given directly
+        op = oracle.OracleParams(schedule=oracle.SCHED_LAYERED, seed=23, **extra)
+    else:
+        T, P = extra.pop("T", 300.0), extra.pop("P", 0.1)
+        op = oracle.physical_params(T, P, schedule=oracle.SCHED_LAYERED, seed=23,
+                                    dv_max_frac=0.02, **extra)
+    s_gpu, o_gpu, r_gpu = gpu_run(op, 90, record_every=3)
+    s_ref, o_ref, r_ref = oracle_run(op, 90, record_every=3)
+    assert np.array_equal(s_gpu, s_ref)
+    assert_obs_equal(o_gpu, o_ref)
+    assert len(r_gpu) == len(r_ref) == 30
+    for i, (a, b) in enumerate(zip(r_gpu, r_ref)):
+        assert_obs_equal(a, b, ("record", i))
 
 
 def test_series_parity_record_every():
