@@ -272,6 +272,10 @@ def run_kernel_mode(args):
 # The paper's own 3D figure (context, other hardware): 280 ms per Metropolis
 # MC step at N = 260^3 on an RTX 3060, cuRAND generation and copies included.
 PAPER_3D_MS_PER_STEP_260 = 280.0
+# The paper's linear fit of its time per Metropolis step against N (Fig. 4
+# caption), for context beside the per-size timings.
+PAPER_3D_FIT_A_MS = 4.11e-6
+PAPER_3D_FIT_B_MS = 1.2e-2
 # DRAM bytes (read + write) of one two-arm k_pass3 launch at L = 260 (the
 # commonest kind), from an ncu capture of the current kernel; reset to None
 # whenever the kernel changes until a new capture is taken.
@@ -345,6 +349,28 @@ def measure_cubic(args, rank, world):
            "acceptance": o["acc_sigma"] / max(1.0, upd * o["sweep"]),
            "workload": "CVF 3D cubic lattice L=%d q=6, layered six-arm schedule, random init "
                        "(seed 3), 300 K, 0.1 MPa" % L}
+    # time per MC step against N over the sizes of the paper's Fig. 4, next
+    # to its linear fit t = a N + b (RTX 3060, 32768 <= N <= 2097152)
+    sizes = []
+    for Ls in (16, 32, 52, 64, 100, 128, 160, 200):
+        lat = Lattice3(params3(300.0, 0.1, L=Ls, seed=3), stream=stream)
+        lat.sweep(64)
+        torch.cuda.synchronize()
+        n_steps = 640 if Ls <= 64 else 320
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.sweep(n_steps)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / n_steps
+        lat.close()
+        Ns = Ls ** 3
+        sizes.append({"L": Ls, "N": Ns, "ms_per_mc_step": t,
+                      "paper_fit_ms_per_mc_step": PAPER_3D_FIT_A_MS * Ns + PAPER_3D_FIT_B_MS,
+                      "updates_per_ns": 6.0 * Ns / (t * 1e6)})
+    out["by_size"] = sizes
+    out["paper_fit"] = "t = 4.11e-6 ms x N + 1.2e-2 ms (RTX 3060, fitted on 32768 <= N <= 2097152)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             import oracle
@@ -359,6 +385,37 @@ def measure_cubic(args, rank, world):
                                              "one thread" % Lc}
         except Exception as e:
             out["cpu_baseline"] = {"value": None, "error": str(e)}
+    return out
+
+
+def measure_small_configs(rank):
+    """Configurations 1 and 2 as single lattices through the public API:
+    C1 = L 64, 1000 MC steps (latency of one small lattice); C2 = L 1024,
+    10^4 steps with the observables recorded every 10 steps (1000 ring
+    records, drained at the end).  Wall-clock around sweep + drain +
+    observables, after a warm-up call that instantiates the step graphs."""
+    import torch
+    from paper_2505_05919_gb300 import Lattice, dist, params, workloads
+    out = {}
+    for name, c in (("c1", workloads.c1()), ("c2", workloads.c2())):
+        stream = torch.cuda.Stream()
+        lat = Lattice(params(c["T"], c["P"], L=c["L"], q=c["q"], seed=c["seed"] + dist.seed_offset(rank)),
+                      stream=stream)
+        every = c.get("record_every", 0)
+        lat.sweep(64, every)
+        lat.drain()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.sweep(c["sweeps"], every)
+        recs, overflow = lat.drain()
+        o = lat.observables()
+        dt = time.perf_counter() - t0
+        lat.close()
+        out[name] = {"L": c["L"], "sweeps": c["sweeps"], "record_every": every,
+                     "records": len(recs), "wall_ms": dt * 1e3,
+                     "ms_per_mc_step": dt * 1e3 / c["sweeps"],
+                     "updates_per_ns": 4.0 * c["L"] ** 2 * c["sweeps"] / (dt * 1e9),
+                     "acceptance": o["acc_sigma"] / max(1.0, 4.0 * c["L"] ** 2 * o["sweep"])}
     return out
 
 
@@ -557,6 +614,7 @@ def main():
            "h2d_bytes_per_step": 2 * L * L, "d2h_bytes_per_step": 2 * L * L + 96}
 
     cubic = measure_cubic(args, rank, world) if args.cubic_sweeps > 0 else None
+    small = measure_small_configs(rank)
     batched = measure_batched(args, rank) if args.batch_sweeps > 0 else None
     serving = measure_serving(args, rank) if args.serve_seconds > 0 else None
 
@@ -590,6 +648,7 @@ def main():
             "batched": batched,
             "serving": serving,
             "cubic": cubic,
+            "small_configs": small,
             "clocks": clocks,
             "wall_s": t_wall,
             "per_sweep_ms": per_sweep_ms,

@@ -178,6 +178,15 @@ int cvf_recount(cvf_handle *h, int64_t *n_hb_raw, int64_t *n_sigma);
  * call that enqueues work on the handle. */
 int cvf_state_device_ptr(cvf_handle *h, void **dev_ptr);
 
+/* Tile shape of the checkerboard sweep: config 0 = 64 rows x 64 words (128
+ * cells), 1 = 32 x 32, 2 = 16 x 32; -1 = automatic (the largest shape whose
+ * tiles fill every resident block, chosen at creation).  The result does
+ * not depend on the shape; set_tiles waits for the stream.  CVF_EINVAL for
+ * other values. */
+int cvf_set_tiles(cvf_handle *h, int32_t config);
+int cvf_get_tiles(cvf_handle *h, int32_t *config, int32_t *rows,
+                  int32_t *words);
+
 /* Waits for the handle's stream, frees what the library allocated. */
 int cvf_destroy(cvf_handle *h);
 

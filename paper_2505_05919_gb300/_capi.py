@@ -72,6 +72,8 @@ _SIGS = {
     "cvf_recount": (ctypes.c_int, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
     "cvf_state_device_ptr": (ctypes.c_int, [_vp, _P(_vp)]),
     "cvf_destroy": (ctypes.c_int, [_vp]),
+    "cvf_set_tiles": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "cvf_get_tiles": (ctypes.c_int, [_vp, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_int32)]),
     "cvf_sweep_noalloc": (ctypes.c_int, [_P(cvf_params), _vp, ctypes.c_double, ctypes.c_int64,
                                          ctypes.c_int64, ctypes.c_int32, _P(cvf_obs), ctypes.c_int64,
                                          _P(ctypes.c_int64), _P(cvf_obs), _vp]),
@@ -210,6 +212,17 @@ def cvf_state_device_ptr(h: int) -> int:
 
 def cvf_destroy(h: int) -> None:
     _check(load().cvf_destroy(h), "cvf_destroy")
+
+
+def cvf_set_tiles(h: int, config: int) -> None:
+    _check(load().cvf_set_tiles(h, config), "cvf_set_tiles")
+
+
+def cvf_get_tiles(h: int):
+    c, r, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().cvf_get_tiles(h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(w)),
+           "cvf_get_tiles")
+    return c.value, r.value, w.value
 
 
 def cvf_sweep_noalloc(p: cvf_params, dev_state: int, V_iso: float, sweep: int, n_sweeps: int,

@@ -176,10 +176,21 @@ __global__ void __launch_bounds__(kThreads) k_histogram(const uint16_t* __restri
 // limit only guards against a copy that never lands).
 constexpr uint32_t kTmaWaitLimit = 1u << 26;
 
-template <int RNG_WORDS, bool CMP64>
+// Tile shapes of the single-lattice sweep (rows x 32-bit words): the large
+// tile for large lattices, smaller ones so that mid-size lattices still
+// give every resident block tiles to take.
+template <int TILE>
+struct TileShape {
+  static constexpr int R = (TILE == 0) ? 64 : (TILE == 1) ? 32 : 16;
+  static constexpr int W = (TILE == 0) ? 64 : 32;
+};
+constexpr int kNumSweepTiles = 3;
+
+template <int RNG_WORDS, bool CMP64, int TILE>
 __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     k_sweep_tiled(LatticeArgs A, const __grid_constant__ CUtensorMap tm0,
                   const __grid_constant__ CUtensorMap tm1) {
+  constexpr int kTileRows = TileShape<TILE>::R, kTileWords = TileShape<TILE>::W;
   __shared__ TileSmem<kTileRows, kTileWords> S;
   __shared__ Tables2 Tb;
   __shared__ int s_tile, s_next;
@@ -579,6 +590,7 @@ struct cvf_handle {
   LatticeArgs args;
   CUtensorMap tm[2];  // TMA descriptors of the two halves of the state pair
   int grid_tiles, grid_cells, grid_layer;
+  int tile;  // tile shape of the sweep (see TileShape)
   cudaGraphExec_t graph;
   int graph_steps;
 };
@@ -609,18 +621,33 @@ void release(cvf_handle* h) {
   delete h;
 }
 
+// The sweep kernel for (rng_words, cmp64, tile shape).
+template <int TILE>
+const void* sweep_kernel_t(int rng_words, bool cmp64) {
+  if (rng_words == 1)
+    return cmp64 ? (const void*)k_sweep_tiled<1, true, TILE> : (const void*)k_sweep_tiled<1, false, TILE>;
+  return cmp64 ? (const void*)k_sweep_tiled<2, true, TILE> : (const void*)k_sweep_tiled<2, false, TILE>;
+}
+
+const void* sweep_kernel(int rng_words, bool cmp64, int tile) {
+  if (tile == 0) return sweep_kernel_t<0>(rng_words, cmp64);
+  if (tile == 1) return sweep_kernel_t<1>(rng_words, cmp64);
+  return sweep_kernel_t<2>(rng_words, cmp64);
+}
+
+void launch_sweep(const void* fn, int grid, cudaStream_t s, const LatticeArgs& A,
+                  const CUtensorMap& tm0, const CUtensorMap& tm1) {
+  void* args[3] = {const_cast<LatticeArgs*>(&A), const_cast<CUtensorMap*>(&tm0),
+                   const_cast<CUtensorMap*>(&tm1)};
+  cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, 0, s);
+}
+
 // Enqueue one MC step on stream s.
 void enqueue_step(cvf_handle* h, cudaStream_t s) {
   const bool one = h->p.rng_words == 1;
   if (h->p.schedule == CVF_SCHED_CHECKERBOARD) {
-    if (one && !h->cmp64)
-      k_sweep_tiled<1, false><<<h->grid_tiles, kThreads, 0, s>>>(h->args, h->tm[0], h->tm[1]);
-    else if (one)
-      k_sweep_tiled<1, true><<<h->grid_tiles, kThreads, 0, s>>>(h->args, h->tm[0], h->tm[1]);
-    else if (!h->cmp64)
-      k_sweep_tiled<2, false><<<h->grid_tiles, kThreads, 0, s>>>(h->args, h->tm[0], h->tm[1]);
-    else
-      k_sweep_tiled<2, true><<<h->grid_tiles, kThreads, 0, s>>>(h->args, h->tm[0], h->tm[1]);
+    launch_sweep(sweep_kernel(h->p.rng_words, h->cmp64, h->tile), h->grid_tiles, s, h->args,
+                 h->tm[0], h->tm[1]);
   } else {
     for (int j = 0; j < kLayerLaunches; ++j) {
       const int grid = h->grid_layer + (j == 0 ? 1 : 0);  // + the volume block
@@ -640,10 +667,10 @@ void enqueue_step(cvf_handle* h, cudaStream_t s) {
 uint16_t* current(cvf_handle* h) { return h->state + (size_t)(h->sweep_host & 1) * h->N; }
 
 // TMA descriptors of the two lattice buffers (uint32 words, Lh x L, box of
-// kTileWords + 8 words x kTileRows + 4 rows).  Needs 16-byte aligned rows and
-// buffers (L a multiple of 8); returns false (cp.async staging only) when
-// that or the driver entry point is unavailable.
-bool encode_state_maps(uint16_t* state, int L, CUtensorMap tm[2]) {
+// tile words + 8 x tile rows + 4).  Needs 16-byte aligned rows and buffers
+// (L a multiple of 8); returns false (cp.async staging only) when that or
+// the driver entry point is unavailable.
+bool encode_state_maps(uint16_t* state, int L, int tile_rows, int tile_words, CUtensorMap tm[2]) {
   std::memset(tm, 0, sizeof(CUtensorMap) * 2);
   if (L % 8 != 0) return false;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -661,7 +688,7 @@ bool encode_state_maps(uint16_t* state, int L, CUtensorMap tm[2]) {
   const long long N = (long long)L * L;
   const cuuint64_t dims[2] = {(cuuint64_t)(L / 2), (cuuint64_t)L};
   const cuuint64_t strides[1] = {(cuuint64_t)(L / 2) * 4};
-  const cuuint32_t box[2] = {kTileWords + 8, kTileRows + 4};
+  const cuuint32_t box[2] = {(cuuint32_t)tile_words + 8, (cuuint32_t)tile_rows + 4};
   const cuuint32_t elem[2] = {1, 1};
   for (int b = 0; b < 2; ++b) {
     void* base = state + (size_t)b * N;
@@ -675,20 +702,54 @@ bool encode_state_maps(uint16_t* state, int L, CUtensorMap tm[2]) {
   return true;
 }
 
-// Persistent grid of the tiled sweep: as many blocks as fit on the GPU at
-// once, but no more than there are tiles.
-int tiled_grid(int L, bool cmp64, int rng_words) {
+void tile_shape(int tile, int* rows, int* words) {
+  *rows = (tile == 0) ? TileShape<0>::R : (tile == 1) ? TileShape<1>::R : TileShape<2>::R;
+  *words = (tile == 0) ? TileShape<0>::W : (tile == 1) ? TileShape<1>::W : TileShape<2>::W;
+}
+
+long long tile_count(int L, int tile) {
+  int r, w;
+  tile_shape(tile, &r, &w);
+  return (long long)((L / 2 + w - 1) / w) * ((L + r - 1) / r);
+}
+
+int resident_sweep_blocks(bool cmp64, int rng_words, int tile) {
   int per_sm = 1;
-  const void* fn = (rng_words == 1)
-                       ? (cmp64 ? (const void*)k_sweep_tiled<1, true> : (const void*)k_sweep_tiled<1, false>)
-                       : (cmp64 ? (const void*)k_sweep_tiled<2, true> : (const void*)k_sweep_tiled<2, false>);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(rng_words, cmp64, tile),
+                                                    kThreads, 0) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  const long long tiles = (long long)((L / 2 + kTileWords - 1) / kTileWords) *
-                          ((L + kTileRows - 1) / kTileRows);
+  return sm_count() * per_sm;
+}
+
+// Tile shape for a lattice: the largest whose tiles fill every resident
+// block, else the smallest.
+int choose_tile(int L, bool cmp64, int rng_words) {
+  for (int t = 0; t < kNumSweepTiles; ++t)
+    if (tile_count(L, t) >= resident_sweep_blocks(cmp64, rng_words, t)) return t;
+  return kNumSweepTiles - 1;
+}
+
+// Persistent grid of the tiled sweep: as many blocks as fit on the GPU at
+// once, but no more than there are tiles.
+int tiled_grid(int L, bool cmp64, int rng_words, int tile) {
+  const long long tiles = tile_count(L, tile);
+  const long long resident = resident_sweep_blocks(cmp64, rng_words, tile);
   // + 1: block 0 decides the next volume move instead of taking tiles
-  return 1 + (int)std::max<long long>(1, std::min<long long>(tiles, (long long)sm_count() * per_sm));
+  return 1 + (int)std::max<long long>(1, std::min<long long>(tiles, resident));
+}
+
+// Adopt tile shape `tile` for the handle: grid, TMA boxes, and a new graph.
+void set_tile(cvf_handle* h, int tile) {
+  h->tile = tile;
+  int r, w;
+  tile_shape(tile, &r, &w);
+  h->grid_tiles = tiled_grid(h->p.L, h->cmp64, h->p.rng_words, tile);
+  h->args.use_tma = encode_state_maps(h->state, h->p.L, r, w, h->tm) ? 1 : 0;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
 }
 
 int recount_into_ctrl(cvf_handle* h) {
@@ -808,8 +869,7 @@ int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** 
   h->args.keys = make_round_keys(p->seed);
   h->args.L = p->L;
   h->args.q = (uint32_t)p->q;
-  h->grid_tiles = tiled_grid(h->p.L, h->cmp64, h->p.rng_words);
-  h->args.use_tma = encode_state_maps(h->state, p->L, h->tm) ? 1 : 0;
+  set_tile(h, choose_tile(p->L, h->cmp64, p->rng_words));
   h->sweep_host = 0;
   h->grid_cells = grid_for(h->N, 8);
   h->grid_layer = grid_for(h->N / 2, 8);  // one word (two cells) per thread and iteration
@@ -945,6 +1005,26 @@ int cvf_recount(cvf_handle* h, int64_t* n_hb_raw, int64_t* n_sigma) {
 int cvf_state_device_ptr(cvf_handle* h, void** dev_ptr) {
   if (!h || !dev_ptr) return set_error(CVF_EINVAL, "NULL argument");
   *dev_ptr = current(h);
+  return CVF_OK;
+}
+
+int cvf_set_tiles(cvf_handle* h, int32_t config) {
+  if (!h) return set_error(CVF_EINVAL, "handle is NULL");
+  if (config < -1 || config >= kNumSweepTiles)
+    return set_error(CVF_EINVAL, "tile config %d: need -1 (automatic) or 0..%d", config,
+                     kNumSweepTiles - 1);
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  set_tile(h, config < 0 ? choose_tile(h->p.L, h->cmp64, h->p.rng_words) : config);
+  return CVF_OK;
+}
+
+int cvf_get_tiles(cvf_handle* h, int32_t* config, int32_t* rows, int32_t* words) {
+  if (!h || !config || !rows || !words) return set_error(CVF_EINVAL, "NULL argument");
+  int r, w;
+  tile_shape(h->tile, &r, &w);
+  *config = h->tile;
+  *rows = r;
+  *words = w;
   return CVF_OK;
 }
 
@@ -1122,19 +1202,12 @@ extern "C" int cvf_sweep_noalloc(const cvf_params* p, void* dev_state, double V_
   k_commit_counts<<<1, 32, 0, st>>>(&s->ctrl);
   k_volume_prologue<<<1, 32, 0, st>>>(&s->vol, &s->ctrl, A.keys);
   k_set_record<<<1, 32, 0, st>>>(&s->ctrl, record_every);
-  const int grid = tiled_grid(p->L, cmp64, p->rng_words);
+  const int tile = choose_tile(p->L, cmp64, p->rng_words);
+  const int grid = tiled_grid(p->L, cmp64, p->rng_words, tile);
+  const void* fn = sweep_kernel(p->rng_words, cmp64, tile);
   CUtensorMap no_map;  // this path stages every tile with cp.async
   std::memset(&no_map, 0, sizeof(no_map));
-  for (int64_t i = 0; i < n_sweeps; ++i) {
-    if (p->rng_words == 1 && !cmp64)
-      k_sweep_tiled<1, false><<<grid, kThreads, 0, st>>>(A, no_map, no_map);
-    else if (p->rng_words == 1)
-      k_sweep_tiled<1, true><<<grid, kThreads, 0, st>>>(A, no_map, no_map);
-    else if (!cmp64)
-      k_sweep_tiled<2, false><<<grid, kThreads, 0, st>>>(A, no_map, no_map);
-    else
-      k_sweep_tiled<2, true><<<grid, kThreads, 0, st>>>(A, no_map, no_map);
-  }
+  for (int64_t i = 0; i < n_sweeps; ++i) launch_sweep(fn, grid, st, A, no_map, no_map);
   CVF_CUDA_CHECK(cudaMemsetAsync(s->hist, 0, sizeof(s->hist), st));
   k_histogram<<<grid_cells, kThreads, 0, st>>>(A.state + (size_t)((sweep + n_sweeps) & 1) * N, N,
                                                s->hist);

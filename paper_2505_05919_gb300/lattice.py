@@ -70,6 +70,14 @@ class Lattice:
     def recount(self):
         return _capi.cvf_recount(self.h)
 
+    def set_tiles(self, config: int) -> None:
+        """Tile shape of the sweep (0: 64x64, 1: 32x32, 2: 16x32 words; -1: automatic)."""
+        _capi.cvf_set_tiles(self.h, config)
+
+    def tiles(self):
+        """(config, rows, words) of the sweep's tile shape."""
+        return _capi.cvf_get_tiles(self.h)
+
     def close(self) -> None:
         if getattr(self, "h", None):
             _capi.cvf_destroy(self.h)

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2505_05919_gb300 import Lattice, params_from_dict, _capi, workloads
+from paper_2505_05919_gb300 import Lattice, params, params_from_dict, _capi, workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -72,6 +72,43 @@ def test_checkerboard_parity(L, K, extra):
     assert np.array_equal(s_gpu, s_ref)
     assert_obs_equal(o_gpu, o_ref)
     assert 0 <= o_gpu["n_hb_raw"] <= 2 * L * L and 0 <= o_gpu["n_coop"] <= 6 * L * L
+
+
+@pytest.mark.parametrize("config", [0, 1, 2])
+@pytest.mark.parametrize("L,K,extra", [(64, 40, {}), (130, 25, dict(rng_words=2)),
+                                       (258, 12, dict(T=270.0, init=oracle.INIT_ORDERED)),
+                                       (34, 60, dict(kT=1e-3))])
+def test_checkerboard_every_tile_shape(config, L, K, extra):
+    """Every tile shape of the sweep (64x64, 32x32, 16x32 words), including
+    ragged edge tiles and odd numbers of words per row, gives the oracle's
+    lattice and counts."""
+    extra = dict(extra)
+    if "kT" in extra:  # the 64-bit threshold compare
+        op = oracle.OracleParams(L=L, seed=300 + L, init=oracle.INIT_ORDERED, **extra)
+    else:
+        T = extra.pop("T", 300.0)
+        op = oracle.physical_params(T, 0.1, L=L, seed=300 + L, dv_max_frac=0.02, **extra)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        lat.set_tiles(config)
+        assert lat.tiles()[0] == config
+        lat.sweep(K, 5)
+        s_gpu, o_gpu = lat.state(), lat.observables()
+        r_gpu, _ = lat.drain()
+    s_ref, o_ref, r_ref = oracle_run(op, K, record_every=5)
+    assert np.array_equal(s_gpu, s_ref)
+    assert_obs_equal(o_gpu, o_ref)
+    for a, b in zip(r_gpu, r_ref):
+        assert_obs_equal(a, b)
+
+
+def test_tile_choice():
+    with Lattice(params(300.0, 0.1, L=4096)) as lat:
+        assert lat.tiles() == (0, 64, 64)  # the large tile at the benchmark size
+    with Lattice(params(300.0, 0.1, L=256)) as lat:
+        c, r, w = lat.tiles()
+        assert c in (0, 1, 2) and (r, w) in ((64, 64), (32, 32), (16, 32))
+        with pytest.raises(_capi.CvfError):
+            lat.set_tiles(3)
 
 
 @pytest.mark.parametrize("L,K,rng_words", [(2, 100, 1), (8, 80, 2), (64, 60, 1), (130, 20, 2),
