@@ -179,10 +179,13 @@ int cvf_recount(cvf_handle *h, int64_t *n_hb_raw, int64_t *n_sigma);
 int cvf_state_device_ptr(cvf_handle *h, void **dev_ptr);
 
 /* Tile shape of the checkerboard sweep: config 0 = 64 rows x 64 words (128
- * cells), 1 = 32 x 32, 2 = 16 x 32; -1 = automatic (the largest shape whose
- * tiles fill every resident block, chosen at creation).  The result does
- * not depend on the shape; set_tiles waits for the stream.  CVF_EINVAL for
- * other values. */
+ * cells), 1 = 32 x 32, 2 = 16 x 32, 3 = the whole lattice resident in the
+ * shared memory of one 8-CTA thread-block cluster for many steps per launch
+ * (16 <= L <= 256, L a multiple of 8; rows = L/8 per CTA); -1 = automatic
+ * (chosen at creation: the resident form for small lattices, else the
+ * largest tile shape whose tiles fill every resident block).  The result
+ * does not depend on the shape; set_tiles waits for the stream.  CVF_EINVAL
+ * for other values, or config 3 where it does not apply. */
 int cvf_set_tiles(cvf_handle *h, int32_t config);
 int cvf_get_tiles(cvf_handle *h, int32_t *config, int32_t *rows,
                   int32_t *words);

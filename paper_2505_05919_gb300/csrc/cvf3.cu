@@ -244,9 +244,12 @@ __global__ void __launch_bounds__(kThreads3, 4) k_pass3(Args3 A, int launch) {
   __syncthreads();
   const int n_arms = s_n;
   if (launch == 0 && blockIdx.x == 0) {
+    __shared__ VolumeArgs sV;  // the parameters at shared-memory latency
+    stage_volume_args(&sV, A.vol);
+    __syncthreads();
     if (threadIdx.x == 0) {
       VolumeResult r;
-      if (volume_decide(*A.vol, ctl->sweep + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1,
+      if (volume_decide(sV, ctl->sweep + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1,
                         A.keys, &r)) {
         ctl->ahead_V = r.V;
         ctl->ahead_u = r.u;

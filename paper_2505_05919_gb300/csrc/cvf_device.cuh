@@ -193,6 +193,16 @@ __device__ __forceinline__ double lj_cell_energy(const VolumeArgs& V, double v) 
   return (2.0 * V.epsilon) * (x6 * V.S12[k] - x3 * V.S6[k]);
 }
 
+// Block-wide copy of the FP64 parameters and shell tables into shared
+// memory (the single thread that decides a volume move then reads them at
+// shared-memory latency); the caller synchronises before using dst.
+__device__ __forceinline__ void stage_volume_args(VolumeArgs* dst, const VolumeArgs* src) {
+  static_assert(sizeof(VolumeArgs) % 8 == 0, "VolumeArgs copies as 64-bit words");
+  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(VolumeArgs) / 8); i += blockDim.x) d[i] = s[i];
+}
+
 __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
   const uint64_t m = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
   return (double)m * (1.0 / 9007199254740992.0);

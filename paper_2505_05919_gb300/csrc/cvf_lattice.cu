@@ -191,7 +191,12 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     k_sweep_tiled(LatticeArgs A, const __grid_constant__ CUtensorMap tm0,
                   const __grid_constant__ CUtensorMap tm1) {
   constexpr int kTileRows = TileShape<TILE>::R, kTileWords = TileShape<TILE>::W;
-  __shared__ TileSmem<kTileRows, kTileWords> S;
+  // the volume block uses the tile buffers for its copy of the parameters
+  __shared__ union {
+    TileSmem<kTileRows, kTileWords> tile;
+    VolumeArgs vol;
+  } U;
+  TileSmem<kTileRows, kTileWords>& S = U.tile;
   __shared__ Tables2 Tb;
   __shared__ int s_tile, s_next;
   __shared__ uint32_t s_hist4[4];
@@ -201,10 +206,14 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
   const long long step = ctl->sweep;
   if (blockIdx.x == 0) {
     // the volume block: decide the next step's volume move now when it does
-    // not depend on this step's bonds, while the other blocks sweep
+    // not depend on this step's bonds, while the other blocks sweep (the
+    // parameters staged into the unused tile buffers first)
+    VolumeArgs* sV = &U.vol;
+    stage_volume_args(sV, A.vol);
+    __syncthreads();
     if (threadIdx.x == 0) {
       VolumeResult r;
-      if (volume_decide(*A.vol, step + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1, A.keys,
+      if (volume_decide(*sV, step + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1, A.keys,
                         &r)) {
         ctl->ahead_V = r.V;
         ctl->ahead_u = r.u;
@@ -425,9 +434,12 @@ __global__ void __launch_bounds__(kThreads) k_layer(LatticeArgs A, int launch) {
   const int n_arms = s_n;
   if (launch == 0 && blockIdx.x == 0) {
     // the volume block: the next step's move, decided now unless it depends on the bonds
+    __shared__ VolumeArgs sV;
+    stage_volume_args(&sV, A.vol);
+    __syncthreads();
     if (threadIdx.x == 0) {
       VolumeResult r;
-      if (volume_decide(*A.vol, ctl->sweep + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1,
+      if (volume_decide(sV, ctl->sweep + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1,
                         A.keys, &r)) {
         ctl->ahead_V = r.V;
         ctl->ahead_u = r.u;
@@ -702,14 +714,26 @@ bool encode_state_maps(uint16_t* state, int L, int tile_rows, int tile_words, CU
   return true;
 }
 
-void tile_shape(int tile, int* rows, int* words) {
+// Tile config kResident: the whole lattice resident in one cluster's shared
+// memory (cvf_resident2.cu), one slab of L / kResCtas rows per CTA.
+constexpr int kResident = kNumSweepTiles;
+// the automatic choice takes the resident sweep up to this side (measured:
+// it beats the tiled sweep there)
+constexpr int kResAutoSide = 128;
+
+void tile_shape(int tile, int L, int* rows, int* words) {
+  if (tile == kResident) {
+    *rows = L / kResCtas;
+    *words = L / 2;
+    return;
+  }
   *rows = (tile == 0) ? TileShape<0>::R : (tile == 1) ? TileShape<1>::R : TileShape<2>::R;
   *words = (tile == 0) ? TileShape<0>::W : (tile == 1) ? TileShape<1>::W : TileShape<2>::W;
 }
 
 long long tile_count(int L, int tile) {
   int r, w;
-  tile_shape(tile, &r, &w);
+  tile_shape(tile, L, &r, &w);
   return (long long)((L / 2 + w - 1) / w) * ((L + r - 1) / r);
 }
 
@@ -742,8 +766,13 @@ int tiled_grid(int L, bool cmp64, int rng_words, int tile) {
 // Adopt tile shape `tile` for the handle: grid, TMA boxes, and a new graph.
 void set_tile(cvf_handle* h, int tile) {
   h->tile = tile;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  if (tile == kResident) return;
   int r, w;
-  tile_shape(tile, &r, &w);
+  tile_shape(tile, h->p.L, &r, &w);
   h->grid_tiles = tiled_grid(h->p.L, h->cmp64, h->p.rng_words, tile);
   h->args.use_tma = encode_state_maps(h->state, h->p.L, r, w, h->tm) ? 1 : 0;
   if (h->graph) {
@@ -869,7 +898,10 @@ int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** 
   h->args.keys = make_round_keys(p->seed);
   h->args.L = p->L;
   h->args.q = (uint32_t)p->q;
-  set_tile(h, choose_tile(p->L, h->cmp64, p->rng_words));
+  set_tile(h, (p->schedule == CVF_SCHED_CHECKERBOARD && p->L <= kResAutoSide &&
+               resident_fits(h->args, p->rng_words, h->cmp64))
+                  ? kResident
+                  : choose_tile(p->L, h->cmp64, p->rng_words));
   h->sweep_host = 0;
   h->grid_cells = grid_for(h->N, 8);
   h->grid_layer = grid_for(h->N / 2, 8);  // one word (two cells) per thread and iteration
@@ -898,6 +930,15 @@ int cvf_sweep(cvf_handle* h, int64_t n_sweeps, int32_t record_every) {
                      (long long)n_sweeps, record_every);
   if (n_sweeps == 0) return CVF_OK;
   k_set_record<<<1, 32, 0, h->stream>>>(h->ctrl, record_every);
+  if (h->tile == kResident && h->p.schedule == CVF_SCHED_CHECKERBOARD) {
+    // many steps per launch; the lattice stays in the cluster's shared memory
+    constexpr long long kChunk = 1 << 16;
+    for (long long done = 0; done < n_sweeps; done += kChunk)
+      CVF_CUDA_CHECK(launch_resident(h->args, h->p.rng_words, h->cmp64,
+                                     std::min(kChunk, n_sweeps - done), h->stream));
+    h->sweep_host += n_sweeps;
+    return CVF_OK;
+  }
   long long left = n_sweeps;
   if (left >= kGraphSteps) {
     int rc = build_graph(h);
@@ -1010,18 +1051,26 @@ int cvf_state_device_ptr(cvf_handle* h, void** dev_ptr) {
 
 int cvf_set_tiles(cvf_handle* h, int32_t config) {
   if (!h) return set_error(CVF_EINVAL, "handle is NULL");
-  if (config < -1 || config >= kNumSweepTiles)
+  if (config < -1 || config > kResident)
     return set_error(CVF_EINVAL, "tile config %d: need -1 (automatic) or 0..%d", config,
-                     kNumSweepTiles - 1);
+                     kResident);
+  const bool res_ok = h->p.schedule == CVF_SCHED_CHECKERBOARD &&
+                      resident_fits(h->args, h->p.rng_words, h->cmp64);
+  if (config == kResident && !res_ok)
+    return set_error(CVF_EINVAL, "the resident sweep needs the checkerboard schedule and "
+                     "%d <= L <= %d, L a multiple of %d", 2 * kResCtas, kResMaxSide, kResCtas);
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
-  set_tile(h, config < 0 ? choose_tile(h->p.L, h->cmp64, h->p.rng_words) : config);
+  if (config < 0)
+    config = (res_ok && h->p.L <= kResAutoSide) ? kResident
+                                                : choose_tile(h->p.L, h->cmp64, h->p.rng_words);
+  set_tile(h, config);
   return CVF_OK;
 }
 
 int cvf_get_tiles(cvf_handle* h, int32_t* config, int32_t* rows, int32_t* words) {
   if (!h || !config || !rows || !words) return set_error(CVF_EINVAL, "NULL argument");
   int r, w;
-  tile_shape(h->tile, &r, &w);
+  tile_shape(h->tile, h->p.L, &r, &w);
   *config = h->tile;
   *rows = r;
   *words = w;

@@ -1,5 +1,7 @@
 // cvf_lattice.cuh -- launch arguments of the single-lattice kernels.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <vector>
 
@@ -45,6 +47,15 @@ __global__ void k_observables(const VolumeArgs* __restrict__ V, const Ctrl* ctl,
                               const unsigned long long* hist, cvf_obs* out);
 __global__ void k_histogram(const uint16_t* __restrict__ state, long long N,
                             unsigned long long* out);
+
+// The resident sweep (cvf_resident2.cu): a square lattice of side L (a
+// multiple of kResCtas, 2 kResCtas <= L <= kResMaxSide) held in the shared
+// memory of one cluster of kResCtas CTAs for many steps per launch.
+constexpr int kResCtas = 8;
+constexpr int kResMaxSide = 256;
+bool resident_fits(const LatticeArgs& A, int rng_words, bool cmp64);
+cudaError_t launch_resident(const LatticeArgs& A, int rng_words, bool cmp64, long long n_steps,
+                            cudaStream_t s);
 
 // Host helpers shared by both paths.
 void fill_volume_args(const cvf_params* p, long long N, const std::vector<int64_t>& d2,

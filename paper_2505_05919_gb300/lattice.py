@@ -71,7 +71,8 @@ class Lattice:
         return _capi.cvf_recount(self.h)
 
     def set_tiles(self, config: int) -> None:
-        """Tile shape of the sweep (0: 64x64, 1: 32x32, 2: 16x32 words; -1: automatic)."""
+        """Tile shape of the sweep (0: 64x64, 1: 32x32, 2: 16x32 words; 3: the
+        whole lattice resident in one thread-block cluster; -1: automatic)."""
         _capi.cvf_set_tiles(self.h, config)
 
     def tiles(self):

@@ -101,14 +101,50 @@ def test_checkerboard_every_tile_shape(config, L, K, extra):
         assert_obs_equal(a, b)
 
 
+@pytest.mark.parametrize("L,K,extra", [(16, 300, {}), (64, 200, dict(rng_words=2)),
+                                       (128, 60, dict(T=270.0, init=oracle.INIT_ORDERED)),
+                                       (256, 20, dict(q=8)), (24, 150, dict(kT=1e-3)),
+                                       (32, 400, dict(kT=3.0, P=1.2, epsilon=0.0, v_iso_init=1.9,
+                                                      dv_max_frac=0.2))])
+def test_resident_cluster_sweep(L, K, extra):
+    """The resident form (the lattice in one cluster's shared memory for the
+    whole call) gives the oracle's lattice, counts and recorded series --
+    both RNG modes, both inits, q = 8, the 64-bit compare, gate flips."""
+    extra = dict(extra)
+    if "kT" in extra:
+        op = oracle.OracleParams(L=L, seed=400 + L, **extra)
+    else:
+        T = extra.pop("T", 300.0)
+        op = oracle.physical_params(T, 0.1, L=L, seed=400 + L, dv_max_frac=0.02, **extra)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        lat.set_tiles(3)
+        assert lat.tiles() == (3, L // 8, L // 2)
+        lat.sweep(K // 2, 1)
+        lat.sweep(K - K // 2, 1)   # two calls: the lattice leaves and re-enters the cluster
+        s_gpu, o_gpu = lat.state(), lat.observables()
+        r_gpu, _ = lat.drain()
+        assert lat.recount() == (o_gpu["n_hb_raw"], o_gpu["n_coop"])
+    s_ref, o_ref, r_ref = oracle_run(op, K, record_every=1)
+    assert np.array_equal(s_gpu, s_ref)
+    assert_obs_equal(o_gpu, o_ref)
+    assert len(r_gpu) == len(r_ref) == K
+    for i, (a, b) in enumerate(zip(r_gpu, r_ref)):
+        assert_obs_equal(a, b, ("record", i))
+
+
 def test_tile_choice():
     with Lattice(params(300.0, 0.1, L=4096)) as lat:
         assert lat.tiles() == (0, 64, 64)  # the large tile at the benchmark size
     with Lattice(params(300.0, 0.1, L=256)) as lat:
         c, r, w = lat.tiles()
-        assert c in (0, 1, 2) and (r, w) in ((64, 64), (32, 32), (16, 32))
+        assert c in (0, 1, 2, 3)
         with pytest.raises(_capi.CvfError):
-            lat.set_tiles(3)
+            lat.set_tiles(4)
+    with Lattice(params(300.0, 0.1, L=64)) as lat:
+        assert lat.tiles()[0] == 3  # small lattices run resident in one cluster
+    with Lattice(params(300.0, 0.1, L=130)) as lat:
+        with pytest.raises(_capi.CvfError):
+            lat.set_tiles(3)      # 130 is not a multiple of 8
 
 
 @pytest.mark.parametrize("L,K,rng_words", [(2, 100, 1), (8, 80, 2), (64, 60, 1), (130, 20, 2),
