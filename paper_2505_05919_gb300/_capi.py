@@ -101,6 +101,8 @@ _SIGS = {
     "cvf3_recount": (ctypes.c_int, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
     "cvf3_state_device_ptr": (ctypes.c_int, [_vp, _P(_vp)]),
     "cvf3_destroy": (ctypes.c_int, [_vp]),
+    "cvf3_set_resident": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "cvf3_get_resident": (ctypes.c_int, [_vp, _P(ctypes.c_int32)]),
 }
 
 _lib = None
@@ -361,3 +363,13 @@ def cvf3_state_device_ptr(h: int) -> int:
 
 def cvf3_destroy(h: int) -> None:
     _check(load().cvf3_destroy(h), "cvf3_destroy")
+
+
+def cvf3_set_resident(h: int, mode: int) -> None:
+    _check(load().cvf3_set_resident(h, mode), "cvf3_set_resident")
+
+
+def cvf3_get_resident(h: int) -> int:
+    r = ctypes.c_int32()
+    _check(load().cvf3_get_resident(h, ctypes.byref(r)), "cvf3_get_resident")
+    return r.value

@@ -16,6 +16,7 @@
 // the current launch, which gives 2 to 4 launches (2.67 on average over the
 // 720 orders); every step enqueues four launches, the unused ones return at
 // once, and the fourth commits the step.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +28,8 @@
 #include "cvf_device.cuh"
 #include "cvf_host.h"
 #include "cvf_lattice.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace cvf {
 namespace {
@@ -495,6 +498,206 @@ __global__ void __launch_bounds__(kThreads3) k_count3(const uint32_t* __restrict
   if (hist && threadIdx.x < 8 && s_cnt[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_cnt[threadIdx.x]);
 }
 
+// ---------------------------------------------------------------------------
+// Small cubes resident in one thread-block cluster (L a multiple of
+// kRes3Ctas, 16 <= L <= 64): CTA r holds the z-planes [r R, (r+1) R),
+// R = L / kRes3Ctas, in shared memory for every step of a call.  The step's
+// launches of k_pass3 become segments separated by cluster barriers; the
+// z-partners across a slab boundary are read from the neighbouring CTA's
+// shared memory.  Every cell is updated with the same draws and rule as in
+// k_pass3, so the results are identical.  A 33rd warp in CTA 0 decides the
+// next step's volume move, overlapping the first segment; CTA 0 commits the
+// step after the last segment.  All CTAs follow the same plan (computed from
+// the step by each), so they meet the same barriers.
+// ---------------------------------------------------------------------------
+constexpr int kRes3Ctas = 8;
+constexpr int kRes3Threads = 256;
+constexpr int kRes3Block = kRes3Threads + 32;
+constexpr int kRes3MaxSide = 64;
+// the automatic choice takes the resident form up to this side (measured:
+// 7.6 / 9.3 us per step at 16^3 / 24^3 against 14.6 / 15.3 with four
+// launches; even at 32^3; slower beyond, where 8 SMs do all the work)
+constexpr int kRes3AutoSide = 24;
+
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait;" ::: "memory"); }
+__device__ __forceinline__ void cl_barrier() {
+  cl_arrive();
+  cl_wait();
+}
+__device__ __forceinline__ void sweepers3_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kRes3Threads) : "memory");
+}
+
+template <bool CMP64>
+__global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_steps) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ uint32_t cube[];  // planes z0 .. z0 + R - 1, L^2 words each
+  __shared__ Row3 sRows[33];
+  __shared__ uint32_t sProp[64];
+  __shared__ unsigned long long sT64[CMP64 ? 33 : 1];
+  __shared__ unsigned long long s_acc[3];   // CTA 0: the step's dN_HB, dN_sigma, moves
+  __shared__ unsigned long long s_hist[8];  // CTA 0: N_q' of a recorded step
+  __shared__ uint32_t s_h[8];               // this CTA's N_q' of a recorded step
+  __shared__ uint32_t red[3][kRes3Threads / 32];
+  __shared__ int s_next_g, s_plan;
+  __shared__ VolumeArgs sV;
+  Ctrl* ctl = A.ctrl;
+  const uint32_t L = A.L, L2 = A.L2, G = A.G, R = L / kRes3Ctas, z0 = rank * R;
+  const uint32_t q = A.q, qm1 = q - 1u;
+  const bool sweeper = threadIdx.x < kRes3Threads;
+  const long long step0 = ctl->sweep;
+  const int every = ctl->record_every;
+  uint32_t* const st = A.state;
+
+  for (uint32_t i = threadIdx.x; i < R * L2; i += blockDim.x) cube[i] = st[z0 * L2 + i];
+  if (threadIdx.x >= 64 && threadIdx.x < 128) {
+    const uint32_t sgm = (threadIdx.x - 64) >> 3, k = (threadIdx.x - 64) & 7u;
+    uint32_t sp = sgm + 1u + k;
+    while (sp >= q) sp -= q;
+    sProp[threadIdx.x - 64] = (sgm < q && k + 1u < q) ? sp * kR7 : 0u;
+  }
+  stage_volume_args(&sV, A.vol);
+  if (rank == 0 && threadIdx.x == 0) s_next_g = ctl->next_g;
+  // the planes just below and above this slab, in the neighbours' shared memory
+  const uint32_t* below = cluster.map_shared_rank(cube, (rank + kRes3Ctas - 1) % kRes3Ctas) + (R - 1) * L2;
+  const uint32_t* above = cluster.map_shared_rank(cube, (rank + 1) % kRes3Ctas);
+  unsigned long long* acc0 = cluster.map_shared_rank(&s_acc[0], 0);
+  unsigned long long* hist0 = cluster.map_shared_rank(&s_hist[0], 0);
+  const int* next_g0 = cluster.map_shared_rank(&s_next_g, 0);
+  int g_cur = -1;
+  __syncthreads();
+  cl_barrier();
+
+  for (long long it = 0; it < n_steps; ++it) {
+    const long long step = step0 + it;
+    if (threadIdx.x == 0) s_plan = (int)make_plan(step, A.keys);
+    __syncthreads();
+    const uint32_t plan = (uint32_t)s_plan;
+    const int nseg = plan_launches(plan);
+    const bool rec = step_recorded(every, step);
+    if (!sweeper) {
+      cl_arrive();  // the end of segment 0
+      if (rank == 0 && threadIdx.x == kRes3Threads) {
+        VolumeResult r;
+        if (volume_decide(sV, step + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1, A.keys, &r)) {
+          ctl->ahead_V = r.V;
+          ctl->ahead_u = r.u;
+          ctl->ahead_g = r.g;
+          ctl->ahead_acc = r.accepted;
+          ctl->ahead_state = 1;
+        }
+      }
+      __syncwarp();
+      cl_wait();
+      for (int j = 1; j < nseg; ++j) cl_barrier();  // the later segments
+      cl_barrier();                                 // the step committed
+      continue;
+    }
+    const int g = *next_g0;
+    if (g != g_cur) {  // uniform over the CTA's sweepers
+      if (threadIdx.x < 33) {
+        const unsigned long long t = A.table[g * 33 + threadIdx.x];
+        if (CMP64) sT64[threadIdx.x] = t;
+        const int dhb = (int)threadIdx.x / 11 - 1, dc = (int)threadIdx.x % 11 - 5;
+        sRows[threadIdx.x].t = (uint32_t)(t - 1ull);
+        sRows[threadIdx.x].delta = (1u << 24) + ((uint32_t)(dhb + 1) << 16) + (uint32_t)(dc + 5);
+      }
+      g_cur = g;
+    }
+    if (rank == 0 && threadIdx.x < 3) s_acc[threadIdx.x] = 0;
+    if (rank == 0 && threadIdx.x < 8) s_hist[threadIdx.x] = 0;
+    if (threadIdx.x < 8) s_h[threadIdx.x] = 0;
+    sweepers3_sync();
+    const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
+    const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
+    uint32_t nacc = 0, hb_b = 0, dc_b = 0, pk = 0;
+    for (int j = 0; j < nseg; ++j) {
+      int arms[3] = {0, 0, 0};
+      const int n_arms = plan_arms(plan, j, arms);
+      for (uint32_t i = threadIdx.x; i < R * L2 / 4u; i += kRes3Threads) {
+        const uint32_t c0 = 4u * i;  // local cell of the group
+        const uint32_t zl = c0 / L2, rem = c0 - zl * L2, y = rem / L, xg = (rem - y * L) >> 2;
+        const uint32_t gi = (z0 * L2 + c0) >> 2;  // global group index (Philox counter)
+        const uint4 own = *reinterpret_cast<const uint4*>(cube + c0);
+        uint32_t w0 = own.x, w1 = own.y, w2 = own.z, w3 = own.w;
+        for (int p = 0; p < n_arms; ++p) {
+          const int a = arms[p];
+          uint4 nb;
+          if (a == 0) {
+            nb = make_uint4(own.y, own.z, own.w, cube[(xg + 1u == G) ? c0 + 4u - L : c0 + 4u]);
+          } else if (a == 1) {
+            nb = make_uint4(cube[(xg == 0u) ? c0 + L - 1u : c0 - 1u], own.x, own.y, own.z);
+          } else if (a == 2) {
+            nb = *reinterpret_cast<const uint4*>(cube + ((y == L - 1u) ? c0 + L - L2 : c0 + L));
+          } else if (a == 3) {
+            nb = *reinterpret_cast<const uint4*>(cube + ((y == 0u) ? c0 + L2 - L : c0 - L));
+          } else if (a == 4) {
+            nb = (zl == R - 1u) ? *reinterpret_cast<const uint4*>(above + rem)
+                                : *reinterpret_cast<const uint4*>(cube + c0 + L2);
+          } else {
+            nb = (zl == 0u) ? *reinterpret_cast<const uint4*>(below + rem)
+                            : *reinterpret_cast<const uint4*>(cube + c0 - L2);
+          }
+          const uint32_t sh = 4u * (uint32_t)a, nsh = 24u - 4u * (uint32_t)(a ^ 1);
+          const uint32_t amask = 0xFu << sh;
+          const Words4 r = philox(gi, s_lo, s_hi, kTagArm0 + (uint32_t)a, A.keys);
+          w0 = update_arm3<CMP64>(w0, nb.x, r.x, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+          w1 = update_arm3<CMP64>(w1, nb.y, r.y, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+          w2 = update_arm3<CMP64>(w2, nb.z, r.z, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+          w3 = update_arm3<CMP64>(w3, nb.w, r.w, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
+        }
+        unpack_counts(pk, nacc, hb_b, dc_b);
+        *reinterpret_cast<uint4*>(cube + c0) = make_uint4(w0, w1, w2, w3);
+        if (rec && j == nseg - 1) hist_group(w0, w1, w2, w3, s_h);
+      }
+      if (j == nseg - 1) {
+        // the step's counts (and N_q') into CTA 0 before the last barrier
+        uint32_t a1 = hb_b - nacc, a2 = dc_b - 5u * nacc, a3 = nacc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a1 += __shfl_xor_sync(0xFFFFFFFFu, a1, o);
+          a2 += __shfl_xor_sync(0xFFFFFFFFu, a2, o);
+          a3 += __shfl_xor_sync(0xFFFFFFFFu, a3, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+          red[0][threadIdx.x >> 5] = a1;
+          red[1][threadIdx.x >> 5] = a2;
+          red[2][threadIdx.x >> 5] = a3;
+        }
+        sweepers3_sync();
+        if (threadIdx.x == 0) {
+          a1 = a2 = a3 = 0;
+          for (int w = 0; w < kRes3Threads / 32; ++w) {
+            a1 += red[0][w];
+            a2 += red[1][w];
+            a3 += red[2][w];
+          }
+          atomicAdd(&acc0[0], (unsigned long long)(long long)(int)a1);
+          atomicAdd(&acc0[1], (unsigned long long)(long long)(int)a2);
+          atomicAdd(&acc0[2], (unsigned long long)a3);
+        }
+        if (rec && threadIdx.x < 8 && s_h[threadIdx.x])
+          atomicAdd(&hist0[threadIdx.x], (unsigned long long)s_h[threadIdx.x]);
+      }
+      cl_barrier();  // segment j done in every CTA
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+      ctl->acc_hb = s_acc[0];
+      ctl->acc_pairs = s_acc[1];
+      ctl->acc_moves = s_acc[2];
+      if (rec)
+        for (int v = 0; v < 8; ++v) ctl->acc_hist[v] = s_hist[v];
+      finalize_step<true>(sV, ctl, A.ring, A.ring_cap, A.keys);
+      s_next_g = ctl->next_g;
+    }
+    cl_barrier();  // the step committed
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < R * L2; i += blockDim.x) st[z0 * L2 + i] = cube[i];
+}
+
 // Observables of the committed state with N_q' from a count of the lattice.
 __global__ void k_observables3(const VolumeArgs* __restrict__ V, const Ctrl* ctl,
                                const unsigned long long* hist, cvf_obs* out) {
@@ -511,6 +714,48 @@ __global__ void k_observables3(const VolumeArgs* __restrict__ V, const Ctrl* ctl
 // Host side
 // ---------------------------------------------------------------------------
 namespace {
+
+template <bool CMP64>
+cudaError_t launch_resident3_t(const Args3& A, long long n_steps, cudaStream_t s, bool query,
+                               int* clusters) {
+  const void* fn = (const void*)k_resident3<CMP64>;
+  const size_t smem = (size_t)(A.L / kRes3Ctas) * A.L2 * sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(kRes3Ctas);
+  cfg.blockDim = dim3(kRes3Block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kRes3Ctas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (query) return cudaOccupancyMaxActiveClusters(clusters, fn, &cfg);
+  return cudaLaunchKernelEx(&cfg, k_resident3<CMP64>, A, n_steps);
+}
+
+cudaError_t launch_resident3(const Args3& A, bool cmp64, long long n_steps, cudaStream_t s) {
+  return cmp64 ? launch_resident3_t<true>(A, n_steps, s, false, nullptr)
+               : launch_resident3_t<false>(A, n_steps, s, false, nullptr);
+}
+
+// Whether the cube can run resident in one cluster on this GPU.
+bool resident3_fits(const Args3& A, bool cmp64) {
+  if (A.L % kRes3Ctas != 0 || A.L < 2 * kRes3Ctas || (int)A.L > kRes3MaxSide) return false;
+  int clusters = 0;
+  const cudaError_t e = cmp64 ? launch_resident3_t<true>(A, 0, nullptr, true, &clusters)
+                              : launch_resident3_t<false>(A, 0, nullptr, true, &clusters);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return clusters >= 1;
+}
 
 int check_params3(const cvf_params* p) {
   if (!p) return set_error(CVF_EINVAL, "params is NULL");
@@ -612,6 +857,7 @@ struct cvf3_handle {
   Args3 args;
   bool cmp64;
   bool aligned;
+  bool resident;  // the cube stays in one cluster's shared memory during a call
   int grid;
   int grid_count;
   cudaGraphExec_t graph;
@@ -791,6 +1037,7 @@ int cvf3_create(const cvf_params* p, void* stream, void* dev_state, cvf3_handle*
     per_sm = 1;
   const long long blocks = ((long long)A.groups + kThreads3 - 1) / kThreads3;
   h->grid = (int)std::max<long long>(1, std::min<long long>(blocks, (long long)sm_count() * per_sm));
+  h->resident = (int)L <= kRes3AutoSide && resident3_fits(A, h->cmp64);
   h->grid_count = (int)std::max<long long>(
       1, std::min<long long>((h->N + kThreads3 - 1) / kThreads3, (long long)sm_count() * 8));
 
@@ -820,6 +1067,13 @@ int cvf3_sweep(cvf3_handle* h, int64_t n_sweeps, int32_t record_every) {
                      (long long)n_sweeps, record_every);
   if (n_sweeps == 0) return CVF_OK;
   k_set_record<<<1, 32, 0, h->stream>>>(h->ctrl, record_every);
+  if (h->resident) {
+    constexpr long long kChunk = 1 << 16;
+    for (long long done = 0; done < n_sweeps; done += kChunk)
+      CVF_CUDA_CHECK(launch_resident3(h->args, h->cmp64, std::min(kChunk, n_sweeps - done),
+                                      h->stream));
+    return CVF_OK;
+  }
   long long left = n_sweeps;
   if (left >= kGraphSteps3) {
     const int rc = build_graph3(h);
@@ -937,6 +1191,24 @@ int cvf3_recount(cvf3_handle* h, int64_t* n_hb_raw, int64_t* n_sigma) {
   std::memcpy(r, h->host_pinned, sizeof(r));
   *n_hb_raw = (int64_t)r[0];
   *n_sigma = (int64_t)r[1];
+  return CVF_OK;
+}
+
+int cvf3_set_resident(cvf3_handle* h, int32_t mode) {
+  if (!h) return set_error(CVF_EINVAL, "handle is NULL");
+  if (mode < -1 || mode > 1) return set_error(CVF_EINVAL, "mode %d: need -1, 0 or 1", mode);
+  const bool fits = resident3_fits(h->args, h->cmp64);
+  if (mode == 1 && !fits)
+    return set_error(CVF_EINVAL, "the resident form needs L a multiple of %d, %d <= L <= %d",
+                     kRes3Ctas, 2 * kRes3Ctas, kRes3MaxSide);
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  h->resident = (mode == 1) || (mode == -1 && fits && h->p.L <= kRes3AutoSide);
+  return CVF_OK;
+}
+
+int cvf3_get_resident(cvf3_handle* h, int32_t* resident) {
+  if (!h || !resident) return set_error(CVF_EINVAL, "NULL argument");
+  *resident = h->resident ? 1 : 0;
   return CVF_OK;
 }
 

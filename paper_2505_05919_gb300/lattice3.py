@@ -64,6 +64,14 @@ class Lattice3:
     def recount(self):
         return _capi.cvf3_recount(self.h)
 
+    def set_resident(self, mode: int) -> None:
+        """1: the cube resident in one thread-block cluster during each call
+        (L a multiple of 8, 16 <= L <= 64); 0: four launches per step; -1: choose."""
+        _capi.cvf3_set_resident(self.h, mode)
+
+    def resident(self) -> bool:
+        return bool(_capi.cvf3_get_resident(self.h))
+
     def close(self) -> None:
         if getattr(self, "h", None):
             _capi.cvf3_destroy(self.h)

@@ -148,3 +148,53 @@ def test_lattice3_large_cubes(L, steps):
     got, want = _run_both(op, steps)
     assert np.array_equal(got[0], want[0])
     _same(got[1], want[1], L)
+
+
+@pytest.mark.parametrize("L,steps,extra", [
+    (16, 120, {}),
+    (24, 60, dict(q=8, init=oracle.INIT_ORDERED)),
+    (32, 40, dict(T=330.0, P=50.0)),
+    (64, 12, {}),
+    (16, 100, dict(kT=1e-3, init=oracle.INIT_ORDERED)),                 # 64-bit compare
+    # gate flips: no bond or LJ bias, v fluctuating about the gate at v = 2
+    (16, 200, dict(kT=1.0, P=0.5, J=0.0, v_HB=0.0, epsilon=0.0, v_iso_init=1.98, dv_max_frac=0.02)),
+])
+def test_lattice3_resident_cluster(L, steps, extra):
+    """The cube resident in one thread-block cluster for each call gives the
+    oracle's lattice, counts, N_q' and recorded series (and the same as the
+    four-launch form)."""
+    extra = dict(extra)
+    if "kT" in extra:
+        op = oracle.params3(L=L, seed=500 + L, **extra)
+    else:
+        T, P = extra.pop("T", 300.0), extra.pop("P", 0.1)
+        op = oracle.physical_params3(T, P, L=L, seed=500 + L, dv_max_frac=0.05, **extra)
+    ref = oracle.Oracle3(op)
+    want = ref.run(steps, 1)
+    if extra.get("dv_max_frac") == 0.02:
+        gates = [r["g"] for r in want]
+        assert sum(a != b for a, b in zip(gates, gates[1:])) >= 10
+    with Lattice3(params_from_dict(asdict(op))) as lat:
+        lat.set_resident(1)
+        assert lat.resident()
+        lat.sweep(steps // 3, 1)
+        lat.sweep(steps - steps // 3, 1)   # two calls: the cube leaves and re-enters the cluster
+        s, o = lat.state(), lat.observables()
+        got, overflow = lat.drain()
+        assert lat.recount() == (o["n_hb_raw"], o["n_coop"])
+    assert not overflow and len(got) == len(want) == steps
+    assert np.array_equal(s, ref.state())
+    _same(o, ref.observables(), L)
+    for i, (g, w) in enumerate(zip(got, want)):
+        _same(g, w, ("record", i))
+
+
+def test_lattice3_resident_choice():
+    with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=16)))) as lat:
+        assert lat.resident()              # small cubes run resident by default
+        lat.set_resident(0)
+        assert not lat.resident()
+    with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=12)))) as lat:
+        assert not lat.resident()          # 12 is not a multiple of 8
+        with pytest.raises(_capi.CvfError):
+            lat.set_resident(1)
