@@ -17,17 +17,19 @@
 namespace cvf {
 
 // Shared tables of one (lattice, step): the proposal for the current q and
-// the threshold row of the current gate.
-//   prop[8 sigma + k] = ((sigma + 1 + k) mod q) * 0x11111 (sigma' in nibbles
-//                       0..4)
-//   rows[i]           = {T - 1, packed count change}, i = (dN_HB + 1) * 7 +
-//                       dN_sigma + 3; an accepted move adds the change
-//                       (1 << 20) + ((dN_HB + 1) << 10) + dN_sigma + 3
-//   T64[i]            = T (the 64-bit compare, when some T is 0)
+// the threshold rows of the current gate.
+//   prop[8 sigma + k] = ((sigma + 1 + k) mod q) * 0x11111111 (sigma' in every
+//                       nibble)
+//   rows[9 ps + pp]   = {T - 1, packed count change} for the nibble counts ps,
+//                       pp of update_arm2 (entries no move can reach are 0);
+//                       an accepted move adds the change (1 << 20) +
+//                       ((dN_HB + 1) << 10) + dN_sigma + 3
+//   T64[9 ps + pp]    = T (the 64-bit compare, when some T is 0)
+constexpr int kRows2 = 72;
 struct Tables2 {
-  uint2 rows[21];
+  uint2 rows[kRows2];
   uint32_t prop[64];
-  unsigned long long T64[21];
+  unsigned long long T64[kRows2];
 };
 
 // Proposal part of the tables (depends on q only).
@@ -36,41 +38,50 @@ __device__ __forceinline__ void fill_prop2(Tables2& Tb, uint32_t q) {
     const uint32_t s = (uint32_t)e >> 3, k = (uint32_t)e & 7u;
     uint32_t sp = s + 1u + k;
     while (sp >= q) sp -= q;
-    Tb.prop[e] = (s < q && k + 1u < q) ? sp * 0x11111u : 0u;
+    Tb.prop[e] = (s < q && k + 1u < q) ? sp * 0x11111111u : 0u;
   }
 }
 
 // Threshold part from a [g][(dN_HB+1)*8 + dN_sigma+3] table of 24 per gate.
+// Entry 9 ps + pp: ps = A_s + 4 b_s with A_s <= 3 the arms differing from
+// sigma and b_s = [partner != sigma]; pp = A_p + 4 b_p with 1 <= A_p <= 4
+// for sigma' -- so b_s = ps >> 2, A_s = ps & 3, b_p = [pp >= 5], A_p = pp -
+// 4 b_p, dN_HB = b_s - b_p and dN_sigma = A_s - A_p + 1.
 __device__ __forceinline__ void fill_rows2(Tables2& Tb, const unsigned long long* table24, int g) {
-  for (int i = threadIdx.x; i < 21; i += blockDim.x) {
-    const int d1 = i / 7, d2 = i % 7;  // dN_HB + 1, dN_sigma + 3
-    const unsigned long long t = table24[g * 24 + d1 * 8 + d2];
+  for (int i = threadIdx.x; i < kRows2; i += blockDim.x) {
+    const int ps = i / 9, pp = i % 9;
+    const int bs = ps >> 2, as = ps & 3, bp = (pp >= 5) ? 1 : 0, ap = pp - 4 * bp;
+    if (ap < 1) {  // unreachable: arm a itself always differs from sigma'
+      Tb.rows[i] = make_uint2(0u, 0u);
+      Tb.T64[i] = 0ull;
+      continue;
+    }
+    const int dhb = bs - bp, dc = as - ap + 1;
+    const unsigned long long t = table24[g * 24 + (dhb + 1) * 8 + (dc + 3)];
     Tb.rows[i] = make_uint2((uint32_t)(t - 1ull),  // every t >= 1 unless 64-bit compares
-                            (1u << 20) + ((uint32_t)d1 << 10) + (uint32_t)d2);
+                            (1u << 20) + ((uint32_t)(dhb + 1) << 10) + (uint32_t)(dc + 3));
     Tb.T64[i] = t;
   }
 }
 
 // Metropolis update of arm a (sh = 4a) of a cell word w (sigma_b in nibble
 // b, b = 0..3) against the partner value pa placed in nibble 4 (bits 16..18),
-// with draw u and proposal offset k (Sec. II.C, Eq. H).  With wn = w | pa,
-// f(v) = (((wn ^ v 0x11111) | 0x88888) - 0x11111) & 0x88888 has bit 3 of
-// nibble b set iff nibble b differs from v (every nibble is >= 8 before the
-// subtraction, so no borrow crosses a nibble).  popc f(sigma) = A_s + b_s and
-// popc f(sigma') = A_p + b_p, with A_v the arms differing from v and b_v =
-// [partner != v] (bit 19); dN_HB = b_s - b_p, dN_sigma = A_s - A_p + 1, and
-// the row index 7 dN_HB + dN_sigma + 10 = (popc f_s + 6 b_s) - (popc f_p +
-// 6 b_p) + 11.
+// with draw u and proposal offset k (Sec. II.C, Eq. H).  The partner is
+// copied into nibbles 4..7 (wn = w | pa * 0x1111); f(v) = (((wn ^ v
+// 0x11111111) | 0x88888888) - 0x11111111) & 0x88888888 has bit 3 of nibble b
+// set iff nibble b differs from v (every nibble is >= 8 before the
+// subtraction, so no borrow crosses a nibble).  So popc f(sigma) = A_s +
+// 4 b_s and popc f(sigma') = A_p + 4 b_p, which index the rows directly.
 template <bool CMP64>
 __device__ __forceinline__ uint32_t update_arm2(uint32_t w, uint32_t pa, uint32_t u, uint32_t k,
                                                 uint32_t sh, const Tables2& Tb, uint32_t& pk) {
   const uint32_t s = (w >> sh) & 7u;
-  const uint32_t sR = s * 0x11111u;
+  const uint32_t sR = s * 0x11111111u;
   const uint32_t spR = Tb.prop[s * 8u + k];
-  const uint32_t wn = w | pa;
-  const uint32_t fs = (((wn ^ sR) | 0x88888u) - 0x11111u) & 0x88888u;
-  const uint32_t fp = (((wn ^ spR) | 0x88888u) - 0x11111u) & 0x88888u;
-  const int idx = (int)(__popc(fs) + 6u * (fs >> 19)) - (int)(__popc(fp) + 6u * (fp >> 19)) + 11;
+  const uint32_t wn = w | (pa * 0x1111u);
+  const uint32_t fs = (((wn ^ sR) | 0x88888888u) - 0x11111111u) & 0x88888888u;
+  const uint32_t fp = (((wn ^ spR) | 0x88888888u) - 0x11111111u) & 0x88888888u;
+  const uint32_t idx = (uint32_t)__popc(fs) * 9u + (uint32_t)__popc(fp);
   const uint2 row = Tb.rows[idx];
   const bool accept = CMP64 ? ((unsigned long long)u < Tb.T64[idx]) : (u <= row.x);
   if (accept) {
