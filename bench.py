@@ -388,6 +388,52 @@ def measure_cubic(args, rank, world):
     return out
 
 
+def copy_bandwidth_gbs(stream, nbytes, reps):
+    """Event-timed bandwidth (read + write bytes / s) of this library's
+    16-byte copy kernel between two device buffers of `nbytes`, copied back
+    and forth `reps` times after three warm-up copies."""
+    import torch
+    from paper_2505_05919_gb300 import _capi
+    a = torch.ones(nbytes, dtype=torch.uint8, device="cuda")
+    b = torch.zeros_like(a)
+    sp = stream.cuda_stream
+    for _ in range(3):
+        _capi.cvf_copy_probe(b.data_ptr(), a.data_ptr(), nbytes, sp)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for r in range(reps):
+        src, dst = (a, b) if r % 2 == 0 else (b, a)
+        _capi.cvf_copy_probe(dst.data_ptr(), src.data_ptr(), nbytes, sp)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    del a, b
+    return 2.0 * nbytes * reps / (ms * 1e-3) / 1e9
+
+
+def cpu_small_configs():
+    """The oracle, one thread, on configurations 1 (in full: L 64, 1000 MC
+    steps) and 2 (L 1024, the first 50 of its 10^4 MC steps, recording every
+    10 as the configuration does); the init is not timed."""
+    import oracle
+    from paper_2505_05919_gb300 import workloads
+    out = {}
+    for name, c, n in (("c1", workloads.c1(), 1000), ("c2", workloads.c2(), 50)):
+        op = oracle.physical_params(c["T"], c["P"], L=c["L"], q=c["q"], seed=c["seed"],
+                                    init=oracle.INIT_RANDOM)
+        o = oracle.Oracle(op)
+        t0 = time.perf_counter()
+        o.run(n, c.get("record_every", 0))
+        dt = time.perf_counter() - t0
+        out[name] = {"value": 4.0 * c["L"] ** 2 * n / (dt * 1e9), "unit": UNIT, "cores": 1,
+                     "kind": "oracle", "ms_per_mc_step": dt * 1e3 / n,
+                     "sample": "L=%d, %d of the configuration's %d MC steps, random init seed %d, "
+                               "one thread" % (c["L"], n, c["sweeps"], c["seed"])}
+    return out
+
+
 def measure_small_configs(rank):
     """Configurations 1 and 2 as single lattices through the public API:
     C1 = L 64, 1000 MC steps (latency of one small lattice); C2 = L 1024,
@@ -609,6 +655,19 @@ def main():
     roofline_hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
                     "bytes_per_update": 1.0, "peak_kind": peak_kind}
+    # the 32 MB state stays in L2 across steps: the byte roofline that
+    # bounds it is the L2 copy bandwidth, measured here with the library's
+    # own copy kernel on the same working-set size (and, for reference, on
+    # buffers 16x the L2, against the driver's STREAM figure)
+    state_bytes = 2 * L * L
+    l2_gbs = copy_bandwidth_gbs(stream, state_bytes, 400)
+    dram_gbs = copy_bandwidth_gbs(stream, 1 << 31, 6)
+    roofline_l2 = {"bound": "l2", "achieved": achieved_gbs, "peak": l2_gbs, "unit": "GB/s",
+                   "frac": achieved_gbs / l2_gbs, "bytes_per_update": 1.0,
+                   "peak_kind": "measured: cvf_copy_probe (16-byte copy kernel) between two "
+                                "L2-resident %d MiB buffers, 400 copies" % (state_bytes >> 20),
+                   "dram_copy_gbs": dram_gbs,
+                   "dram_copy_kind": "same kernel between two 2 GiB buffers, 6 copies"}
 
     # end to end through the C ABI with host buffers
     e2e_ms = []
@@ -647,6 +706,11 @@ def main():
                 cpu_all = cpu_baseline_all_cores(cfgs[1])
             except Exception as e:
                 cpu_all = {"value": None, "error": str(e)}
+            try:
+                for k, v in cpu_small_configs().items():
+                    small[k]["oracle"] = v
+            except Exception as e:
+                small["oracle_error"] = str(e)
         launches_per_sweep = 1  # k_sweep_tiled (the volume move runs inside it)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -658,6 +722,7 @@ def main():
                        "rng_words": 1, "schedule": "checkerboard"},
             "roofline": roofline,
             "roofline_hbm": roofline_hbm,
+            "roofline_l2": roofline_l2,
             "cpu_baseline": cpu,
             "cpu_baseline_all_cores": cpu_all,
             "e2e": e2e,

@@ -363,6 +363,25 @@ int cvf3_get_resident(cvf3_handle *h, int32_t *resident);
 /* Waits for the handle's stream, frees what the library allocated. */
 int cvf3_destroy(cvf3_handle *h);
 
+/* ------------------------------------------------------------------------
+ * Measurement aid: the byte roofline of the sweep's working set.
+ *
+ * The sweep's algorithmic traffic is 2 B read + 2 B written per cell and MC
+ * step (1 B per sigma update).  A 4096^2 lattice (32 MB) stays in the L2
+ * cache across steps, so the byte roofline that bounds it is the L2 copy
+ * bandwidth, which no vendor figure states; timing this copy on two buffers
+ * that together fit in L2 measures it (and on buffers far larger than L2,
+ * the DRAM copy bandwidth).
+ *
+ * cvf_copy_probe: enqueue one copy of `bytes` from device buffer `src` to
+ * device buffer `dst` on `stream` (a cudaStream_t; NULL = legacy default
+ * stream) with 16-byte loads and stores.  Both pointers and `bytes` must be
+ * multiples of 16 and the buffers must not overlap; the caller owns both.
+ * Asynchronous: returns after the launch.  CVF_EINVAL for a NULL or
+ * misaligned argument, CVF_ECUDA if the launch fails.
+ * ------------------------------------------------------------------------ */
+int cvf_copy_probe(void *dst, const void *src, size_t bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

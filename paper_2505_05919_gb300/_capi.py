@@ -103,6 +103,7 @@ _SIGS = {
     "cvf3_destroy": (ctypes.c_int, [_vp]),
     "cvf3_set_resident": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "cvf3_get_resident": (ctypes.c_int, [_vp, _P(ctypes.c_int32)]),
+    "cvf_copy_probe": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
 }
 
 _lib = None
@@ -373,3 +374,8 @@ def cvf3_get_resident(h: int) -> int:
     r = ctypes.c_int32()
     _check(load().cvf3_get_resident(h, ctypes.byref(r)), "cvf3_get_resident")
     return r.value
+
+
+def cvf_copy_probe(dst_ptr: int, src_ptr: int, nbytes: int, stream_ptr: int = 0) -> None:
+    """Enqueue one 16-byte-vector copy of nbytes between device buffers."""
+    _check(load().cvf_copy_probe(dst_ptr, src_ptr, nbytes, stream_ptr or None), "cvf_copy_probe")

@@ -1,0 +1,56 @@
+// cvf_probe.cu -- the byte-roofline probe: a plain 16-byte vector copy whose
+// event-timed bandwidth on a given working set (two buffers that fit in L2,
+// or two much larger than L2) is the denominator for the sweep's algorithmic
+// bytes (read 2 B + write 2 B per cell and step).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cvf_host.h"
+
+namespace cvf {
+namespace {
+
+constexpr int kCopyThreads = 256;
+constexpr int kCopyUnroll = 4;
+
+// Every thread moves kCopyUnroll vectors per iteration: all loads are issued
+// before the first store, so each thread keeps 64 bytes in flight.
+__global__ void __launch_bounds__(kCopyThreads) k_copy16(const uint4* __restrict__ src,
+                                                          uint4* __restrict__ dst, size_t n) {
+  const size_t stride = (size_t)gridDim.x * kCopyThreads;
+  size_t i = (size_t)blockIdx.x * kCopyThreads + threadIdx.x;
+  for (; i + (kCopyUnroll - 1) * stride < n; i += kCopyUnroll * stride) {
+    uint4 v[kCopyUnroll];
+#pragma unroll
+    for (int u = 0; u < kCopyUnroll; ++u) v[u] = src[i + u * stride];
+#pragma unroll
+    for (int u = 0; u < kCopyUnroll; ++u) dst[i + u * stride] = v[u];
+  }
+  for (; i < n; i += stride) dst[i] = src[i];
+}
+
+}  // namespace
+}  // namespace cvf
+
+using namespace cvf;
+
+extern "C" int cvf_copy_probe(void* dst, const void* src, size_t bytes, void* stream) {
+  clear_error();
+  if (!dst || !src) return set_error(CVF_EINVAL, "cvf_copy_probe: NULL buffer");
+  if ((bytes & 15u) || (reinterpret_cast<uintptr_t>(dst) & 15u) ||
+      (reinterpret_cast<uintptr_t>(src) & 15u))
+    return set_error(CVF_EINVAL, "cvf_copy_probe: buffers and size must be 16-byte aligned");
+  if (bytes == 0) return CVF_OK;
+  const size_t n = bytes / 16u;
+  // eight resident blocks of 256 threads per SM fill every SM
+  const size_t want = (n + kCopyThreads - 1) / kCopyThreads;
+  const size_t cap = (size_t)sm_count() * 8u;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  k_copy16<<<grid, kCopyThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const uint4*>(src), reinterpret_cast<uint4*>(dst), n);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return set_error(CVF_ECUDA, "cvf_copy_probe: launch failed: %s", cudaGetErrorString(e));
+  return CVF_OK;
+}

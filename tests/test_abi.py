@@ -115,3 +115,11 @@ def test_cvf3_rejects_bad_params(lib, field, value):
     with pytest.raises(_capi.CvfError) as e:
         _capi.cvf3_threshold_table(p)
     assert e.value.code == _capi.CVF_EINVAL
+
+
+@pytest.mark.parametrize("dst,src,n", [(0, 4096, 16), (4096, 0, 16), (4096, 8192, 24),
+                                       (4100, 8192, 16), (4096, 8200, 16)])
+def test_copy_probe_rejects_bad_arguments_on_host(lib, dst, src, n):
+    # NULL or misaligned arguments are refused before any launch (no GPU here)
+    with pytest.raises(_capi.CvfError):
+        _capi.cvf_copy_probe(dst, src, n, 0)
