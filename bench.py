@@ -396,6 +396,7 @@ def copy_bandwidth_gbs(stream, nbytes, reps):
     from paper_2505_05919_gb300 import _capi
     a = torch.ones(nbytes, dtype=torch.uint8, device="cuda")
     b = torch.zeros_like(a)
+    torch.cuda.synchronize()  # the fills run on torch's stream
     sp = stream.cuda_stream
     for _ in range(3):
         _capi.cvf_copy_probe(b.data_ptr(), a.data_ptr(), nbytes, sp)

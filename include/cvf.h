@@ -382,6 +382,25 @@ int cvf3_destroy(cvf3_handle *h);
  * ------------------------------------------------------------------------ */
 int cvf_copy_probe(void *dst, const void *src, size_t bytes, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Failure detection without a fault.
+ *
+ * Every device-side wait of the library is bounded: a tile of the persistent
+ * batched sweep (cvf_batch_sweep) that waits for its replica's previous step
+ * polls a progress word with acquire loads and gives up after about a second
+ * of polls, after which the launch ends and the next call that reads results
+ * returns CVF_ETIMEOUT with the context intact.
+ *
+ * cvf_wait_probe: run that same wait alone: one device thread polls the
+ * 4-byte-aligned device word `flag` until it is >= `target`, at most `polls`
+ * times (1 <= polls <= 2^22).  Synchronises `stream` (a cudaStream_t; NULL =
+ * legacy default stream).  Returns CVF_OK when the value was seen,
+ * CVF_ETIMEOUT when the wait gave up (a flag that nothing sets), CVF_EINVAL
+ * for a NULL or misaligned flag or `polls` out of range, CVF_ECUDA if a CUDA
+ * call failed.  The caller owns `flag`; the library writes nothing to it.
+ * ------------------------------------------------------------------------ */
+int cvf_wait_probe(const uint32_t *flag, uint32_t target, uint32_t polls, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,6 +104,7 @@ _SIGS = {
     "cvf3_set_resident": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "cvf3_get_resident": (ctypes.c_int, [_vp, _P(ctypes.c_int32)]),
     "cvf_copy_probe": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "cvf_wait_probe": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp]),
 }
 
 _lib = None
@@ -379,3 +380,9 @@ def cvf3_get_resident(h: int) -> int:
 def cvf_copy_probe(dst_ptr: int, src_ptr: int, nbytes: int, stream_ptr: int = 0) -> None:
     """Enqueue one 16-byte-vector copy of nbytes between device buffers."""
     _check(load().cvf_copy_probe(dst_ptr, src_ptr, nbytes, stream_ptr or None), "cvf_copy_probe")
+
+
+def cvf_wait_probe(flag_ptr: int, target: int, polls: int, stream_ptr: int = 0) -> None:
+    """Run the library's bounded device wait on a device word (CvfError with
+    code CVF_ETIMEOUT when it gives up)."""
+    _check(load().cvf_wait_probe(flag_ptr, target, polls, stream_ptr or None), "cvf_wait_probe")

@@ -954,6 +954,7 @@ int cvf3_threshold_table(const cvf_params* p, uint64_t out[66]) {
 }
 
 int cvf3_create(const cvf_params* p, void* stream, void* dev_state, cvf3_handle** out) {
+  NvtxRange nvtx_range("cvf3_create");
   if (!out) return set_error(CVF_EINVAL, "out is NULL");
   *out = nullptr;
   int rc = check_params3(p);
@@ -1061,6 +1062,7 @@ int cvf3_create(const cvf_params* p, void* stream, void* dev_state, cvf3_handle*
 }
 
 int cvf3_sweep(cvf3_handle* h, int64_t n_sweeps, int32_t record_every) {
+  NvtxRange nvtx_range("cvf3_sweep");
   if (!h) return set_error(CVF_EINVAL, "handle is NULL");
   if (n_sweeps < 0 || record_every < 0)
     return set_error(CVF_EINVAL, "n_sweeps=%lld, record_every=%d must be >= 0",
@@ -1089,6 +1091,7 @@ int cvf3_sweep(cvf3_handle* h, int64_t n_sweeps, int32_t record_every) {
 }
 
 int cvf3_observables(cvf3_handle* h, cvf_obs* out) {
+  NvtxRange nvtx_range("cvf3_observables");
   if (!h || !out) return set_error(CVF_EINVAL, "NULL argument");
   CVF_CUDA_CHECK(cudaMemsetAsync(h->rc_dev, 0, sizeof(unsigned long long) * 10, h->stream));
   k_count3<<<h->grid_count, kThreads3, 0, h->stream>>>(h->state, h->args.L, h->args.L2,
@@ -1104,6 +1107,7 @@ int cvf3_observables(cvf3_handle* h, cvf_obs* out) {
 }
 
 int cvf3_drain_series(cvf3_handle* h, cvf_obs* host, int64_t cap, int64_t* n) {
+  NvtxRange nvtx_range("cvf3_drain_series");
   if (!h || !n || cap < 0 || (cap > 0 && !host)) return set_error(CVF_EINVAL, "bad argument");
   *n = 0;
   Ctrl c;
@@ -1132,6 +1136,7 @@ int cvf3_drain_series(cvf3_handle* h, cvf_obs* host, int64_t cap, int64_t* n) {
 }
 
 int cvf3_get_state(cvf3_handle* h, uint32_t* host, size_t n) {
+  NvtxRange nvtx_range("cvf3_get_state");
   if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");
   if ((long long)n != h->N) return set_error(CVF_EINVAL, "n=%zu, lattice has %lld cells", n, h->N);
   CVF_CUDA_CHECK(cudaMemcpyAsync(host, h->state, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost,
@@ -1141,6 +1146,7 @@ int cvf3_get_state(cvf3_handle* h, uint32_t* host, size_t n) {
 }
 
 int cvf3_set_state(cvf3_handle* h, const uint32_t* host, size_t n, double V_iso, int64_t sweep) {
+  NvtxRange nvtx_range("cvf3_set_state");
   if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");
   if ((long long)n != h->N) return set_error(CVF_EINVAL, "n=%zu, lattice has %lld cells", n, h->N);
   if (!(V_iso >= (double)h->N) || !std::isfinite(V_iso))
@@ -1178,6 +1184,7 @@ int cvf3_set_state(cvf3_handle* h, const uint32_t* host, size_t n, double V_iso,
 }
 
 int cvf3_recount(cvf3_handle* h, int64_t* n_hb_raw, int64_t* n_sigma) {
+  NvtxRange nvtx_range("cvf3_recount");
   if (!h || !n_hb_raw || !n_sigma) return set_error(CVF_EINVAL, "NULL argument");
   CVF_CUDA_CHECK(cudaMemsetAsync(h->rc_dev, 0, sizeof(unsigned long long) * 10, h->stream));
   k_count3<<<h->grid_count, kThreads3, 0, h->stream>>>(h->state, h->args.L, h->args.L2,

@@ -60,13 +60,6 @@ struct BatchWork {
   // uint32 progress[n_replicas]
 };
 
-constexpr unsigned int kSpinLimit = 1u << 22;  // bounded wait (about a second)
-
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -122,15 +115,11 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
         s_tile = (int)(j - tile_prefix[lo]);
         s_rel = s;
         // wait until the replica has completed s steps of this launch
-        unsigned int spins = 0;
-        while (ld_acquire(&progress[rep]) < (unsigned int)s) {
-          if (*(volatile unsigned int*)&W->error) { abort = 1; break; }
-          if (++spins > kSpinLimit) {
-            atomicExch(&W->error, 1u);
-            abort = 1;
-            break;
-          }
-          __nanosleep(128);
+        const WaitResult wr =
+            wait_flag_geq(&progress[rep], (unsigned int)s, &W->error, kWaitPollLimit);
+        if (wr != kWaitDone) {
+          if (wr == kWaitGaveUp) atomicExch(&W->error, 1u);
+          abort = 1;
         }
       }
       s_abort = abort;
@@ -451,6 +440,7 @@ int batch_status(cvf_batch* b) {
 extern "C" {
 
 int cvf_batch_create(const cvf_params* params, int32_t n, void* stream, cvf_batch** out) {
+  NvtxRange nvtx_range("cvf_batch_create");
   if (!out) return set_error(CVF_EINVAL, "out is NULL");
   *out = nullptr;
   if (n < 0 || (n > 0 && !params)) return set_error(CVF_EINVAL, "bad replica list");
@@ -480,6 +470,7 @@ int cvf_batch_create(const cvf_params* params, int32_t n, void* stream, cvf_batc
 }
 
 int cvf_batch_add(cvf_batch* b, const cvf_params* p, int32_t* replica) {
+  NvtxRange nvtx_range("cvf_batch_add");
   if (!b || !replica) return set_error(CVF_EINVAL, "NULL argument");
   int rc = check_params(p);
   if (rc) return rc;
@@ -597,6 +588,7 @@ int cvf_batch_tile_config(int32_t config, int32_t* rows, int32_t* words) {
 }
 
 int cvf_batch_sweep(cvf_batch* b, const int64_t* sweeps, int32_t n) {
+  NvtxRange nvtx_range("cvf_batch_sweep");
   if (!b) return set_error(CVF_EINVAL, "batch is NULL");
   if (n != (int)b->reps.size() || (n > 0 && !sweeps))
     return set_error(CVF_EINVAL, "need one step count per replica slot (%zu)", b->reps.size());
@@ -662,11 +654,13 @@ int cvf_batch_sweep(cvf_batch* b, const int64_t* sweeps, int32_t n) {
 }
 
 int cvf_batch_sync(cvf_batch* b) {
+  NvtxRange nvtx_range("cvf_batch_sync");
   if (!b) return set_error(CVF_EINVAL, "batch is NULL");
   return batch_status(b);
 }
 
 int cvf_batch_observables(cvf_batch* b, int32_t replica, cvf_obs* out) {
+  NvtxRange nvtx_range("cvf_batch_observables");
   int rc = check_replica(b, replica);
   if (rc) return rc;
   if (!out) return set_error(CVF_EINVAL, "out is NULL");
@@ -686,6 +680,7 @@ int cvf_batch_observables(cvf_batch* b, int32_t replica, cvf_obs* out) {
 }
 
 int cvf_batch_get_state(cvf_batch* b, int32_t replica, uint16_t* host, size_t n) {
+  NvtxRange nvtx_range("cvf_batch_get_state");
   int rc = check_replica(b, replica);
   if (rc) return rc;
   const Replica& r = b->reps[replica];

@@ -470,4 +470,35 @@ __device__ __forceinline__ void block_sum3(uint32_t& a, uint32_t& b, uint32_t& c
   }
 }
 
+// ---------------------------------------------------------------------------
+// Bounded waits.  A thread that waits for another block (the persistent
+// batched sweep: a tile of step s waits until its replica finished step
+// s - 1) polls with acquire loads and a short sleep, and gives up after a
+// fixed number of polls, so that a wait that can never end returns an error
+// status instead of hanging the GPU.
+// ---------------------------------------------------------------------------
+constexpr unsigned int kWaitPollLimit = 1u << 22;  // about a second of polls
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+enum WaitResult { kWaitDone = 0, kWaitGaveUp = 1, kWaitAborted = 2 };
+
+// Poll until *flag >= target; stop early when *abort_word becomes nonzero
+// (another block gave up), give up after `limit` polls.
+__device__ __forceinline__ WaitResult wait_flag_geq(const unsigned int* flag, unsigned int target,
+                                                    const unsigned int* abort_word,
+                                                    unsigned int limit) {
+  unsigned int polls = 0;
+  while (ld_acquire(flag) < target) {
+    if (abort_word && *(volatile const unsigned int*)abort_word) return kWaitAborted;
+    if (++polls > limit) return kWaitGaveUp;
+    __nanosleep(128);
+  }
+  return kWaitDone;
+}
+
 }  // namespace cvf

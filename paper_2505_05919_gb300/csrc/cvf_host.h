@@ -2,6 +2,7 @@
 // text, CUDA status checks, parameter validation, threshold and shell tables.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdarg>
 #include <cstdint>
@@ -36,5 +37,16 @@ void lattice_shells(double cutoff, std::vector<int64_t>* d2,
                     std::vector<int64_t>* mult);
 
 int sm_count();
+
+// An NVTX range over one host entry point, named after it, so that a
+// profiler that records NVTX (ncu --nvtx, a timeline tracer) can attribute the
+// launches to the API call that made them; without one attached the push and
+// pop return at once.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace cvf

@@ -836,6 +836,7 @@ int build_graph(cvf_handle* h) {
 extern "C" {
 
 int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** out) {
+  NvtxRange nvtx_range("cvf_create");
   if (!out) return set_error(CVF_EINVAL, "out is NULL");
   *out = nullptr;
   int rc = check_params(p);
@@ -924,6 +925,7 @@ int cvf_create(const cvf_params* p, void* stream, void* dev_state, cvf_handle** 
 }
 
 int cvf_sweep(cvf_handle* h, int64_t n_sweeps, int32_t record_every) {
+  NvtxRange nvtx_range("cvf_sweep");
   if (!h) return set_error(CVF_EINVAL, "handle is NULL");
   if (n_sweeps < 0 || record_every < 0)
     return set_error(CVF_EINVAL, "n_sweeps=%lld, record_every=%d must be >= 0",
@@ -955,6 +957,7 @@ int cvf_sweep(cvf_handle* h, int64_t n_sweeps, int32_t record_every) {
 }
 
 int cvf_observables(cvf_handle* h, cvf_obs* out) {
+  NvtxRange nvtx_range("cvf_observables");
   if (!h || !out) return set_error(CVF_EINVAL, "NULL argument");
   CVF_CUDA_CHECK(cudaMemsetAsync(h->rc_dev, 0, sizeof(unsigned long long) * 9, h->stream));
   k_histogram<<<h->grid_cells, kThreads, 0, h->stream>>>(current(h), h->N, h->rc_dev);
@@ -971,6 +974,7 @@ int cvf_observables(cvf_handle* h, cvf_obs* out) {
 }
 
 int cvf_drain_series(cvf_handle* h, cvf_obs* host, int64_t cap, int64_t* n) {
+  NvtxRange nvtx_range("cvf_drain_series");
   if (!h || !n || cap < 0 || (cap > 0 && !host)) return set_error(CVF_EINVAL, "bad argument");
   *n = 0;
   Ctrl c;
@@ -1000,6 +1004,7 @@ int cvf_drain_series(cvf_handle* h, cvf_obs* host, int64_t cap, int64_t* n) {
 }
 
 int cvf_get_state(cvf_handle* h, uint16_t* host, size_t n) {
+  NvtxRange nvtx_range("cvf_get_state");
   if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");
   if ((long long)n != h->N) return set_error(CVF_EINVAL, "n=%zu, lattice has %lld cells", n, h->N);
   CVF_CUDA_CHECK(cudaMemcpyAsync(host, current(h), sizeof(uint16_t) * n, cudaMemcpyDeviceToHost,
@@ -1009,6 +1014,7 @@ int cvf_get_state(cvf_handle* h, uint16_t* host, size_t n) {
 }
 
 int cvf_set_state(cvf_handle* h, const uint16_t* host, size_t n, double V_iso, int64_t sweep) {
+  NvtxRange nvtx_range("cvf_set_state");
   if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");
   if ((long long)n != h->N) return set_error(CVF_EINVAL, "n=%zu, lattice has %lld cells", n, h->N);
   if (!(V_iso >= (double)h->N) || !std::isfinite(V_iso))
@@ -1030,6 +1036,7 @@ int cvf_set_state(cvf_handle* h, const uint16_t* host, size_t n, double V_iso, i
 }
 
 int cvf_recount(cvf_handle* h, int64_t* n_hb_raw, int64_t* n_sigma) {
+  NvtxRange nvtx_range("cvf_recount");
   if (!h || !n_hb_raw || !n_sigma) return set_error(CVF_EINVAL, "NULL argument");
   CVF_CUDA_CHECK(cudaMemsetAsync(h->rc_dev, 0, sizeof(unsigned long long) * 2, h->stream));
   k_recount<<<h->grid_cells, kThreads, 0, h->stream>>>(current(h), h->p.L, nullptr, h->rc_dev);

@@ -1,11 +1,15 @@
-// cvf_probe.cu -- the byte-roofline probe: a plain 16-byte vector copy whose
-// event-timed bandwidth on a given working set (two buffers that fit in L2,
-// or two much larger than L2) is the denominator for the sweep's algorithmic
-// bytes (read 2 B + write 2 B per cell and step).
+// cvf_probe.cu -- measurement and failure-detection aids beside the sweep:
+// the byte-roofline probe (a plain 16-byte vector copy whose event-timed
+// bandwidth on a given working set -- two buffers that fit in L2, or two much
+// larger than L2 -- is the denominator for the sweep's algorithmic bytes,
+// read 2 B + write 2 B per cell and step), and the bounded device wait of the
+// persistent batched sweep run alone on a flag, so that its give-up path is
+// exercised without a fault.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
+#include "cvf_device.cuh"
 #include "cvf_host.h"
 
 namespace cvf {
@@ -30,10 +34,49 @@ __global__ void __launch_bounds__(kCopyThreads) k_copy16(const uint4* __restrict
   for (; i < n; i += stride) dst[i] = src[i];
 }
 
+// One thread waits for *flag >= target exactly as a batched tile waits for
+// its replica; the outcome (WaitResult) goes to *result.
+__global__ void k_wait_probe(const unsigned int* flag, unsigned int target, unsigned int limit,
+                             unsigned int* result) {
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    *result = (unsigned int)wait_flag_geq(flag, target, nullptr, limit);
+}
+
 }  // namespace
 }  // namespace cvf
 
 using namespace cvf;
+
+extern "C" int cvf_wait_probe(const uint32_t* flag, uint32_t target, uint32_t polls, void* stream) {
+  clear_error();
+  if (!flag) return set_error(CVF_EINVAL, "cvf_wait_probe: NULL flag");
+  if (reinterpret_cast<uintptr_t>(flag) & 3u)
+    return set_error(CVF_EINVAL, "cvf_wait_probe: flag must be 4-byte aligned");
+  if (polls < 1 || polls > kWaitPollLimit)
+    return set_error(CVF_EINVAL, "cvf_wait_probe: polls=%u outside 1..%u", polls, kWaitPollLimit);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned int* d_result = nullptr;
+  CVF_CUDA_CHECK(cudaMalloc(&d_result, sizeof(unsigned int)));
+  unsigned int h_result = 0xFFFFFFFFu;
+  cudaError_t e = cudaMemsetAsync(d_result, 0xFF, sizeof(unsigned int), s);
+  if (e == cudaSuccess) {
+    k_wait_probe<<<1, 32, 0, s>>>(reinterpret_cast<const unsigned int*>(flag), target, polls,
+                                  d_result);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h_result, d_result, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_result);
+  if (e != cudaSuccess)
+    return set_error(CVF_ECUDA, "cvf_wait_probe: %s", cudaGetErrorString(e));
+  if (h_result == (unsigned int)kWaitGaveUp)
+    return set_error(CVF_ETIMEOUT, "cvf_wait_probe: the flag did not reach %u within %u polls",
+                     target, polls);
+  if (h_result != (unsigned int)kWaitDone)
+    return set_error(CVF_ECUDA, "cvf_wait_probe: unexpected wait result %u", h_result);
+  return CVF_OK;
+}
 
 extern "C" int cvf_copy_probe(void* dst, const void* src, size_t bytes, void* stream) {
   clear_error();

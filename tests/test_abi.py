@@ -123,3 +123,10 @@ def test_copy_probe_rejects_bad_arguments_on_host(lib, dst, src, n):
     # NULL or misaligned arguments are refused before any launch (no GPU here)
     with pytest.raises(_capi.CvfError):
         _capi.cvf_copy_probe(dst, src, n, 0)
+
+
+@pytest.mark.parametrize("flag,polls", [(0, 16), (4098, 16), (4096, 0), (4096, (1 << 22) + 1)])
+def test_wait_probe_rejects_bad_arguments_on_host(lib, flag, polls):
+    with pytest.raises(_capi.CvfError) as e:
+        _capi.cvf_wait_probe(flag, 1, polls, 0)
+    assert e.value.code == 1  # CVF_EINVAL, before any device work

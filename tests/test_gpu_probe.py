@@ -15,6 +15,7 @@ def test_copy_probe_copies(nbytes):
     a = torch.randint(0, 256, (nbytes,), dtype=torch.uint8, device="cuda", generator=g)
     b = torch.zeros(nbytes + 64, dtype=torch.uint8, device="cuda")
     s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())   # the fills above run on torch's stream
     _capi.cvf_copy_probe(b.data_ptr(), a.data_ptr(), nbytes, s.cuda_stream)
     s.synchronize()
     assert torch.equal(b[:nbytes], a)
@@ -27,3 +28,32 @@ def test_copy_probe_zero_bytes_is_a_no_op():
     _capi.cvf_copy_probe(b.data_ptr(), a.data_ptr(), 0, 0)
     torch.cuda.synchronize()
     assert not b.any()
+
+
+def test_wait_probe_gives_up_with_a_status_and_the_context_survives():
+    """The bounded wait of the persistent batched sweep, on a flag that
+    nothing sets, ends with CVF_ETIMEOUT; afterwards the device still runs a
+    sweep that matches the oracle."""
+    from dataclasses import asdict
+
+    import numpy as np
+
+    import oracle
+    from paper_2505_05919_gb300 import Lattice, params_from_dict
+
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(_capi.CvfError) as e:
+        _capi.cvf_wait_probe(flag.data_ptr(), 1, 1 << 14)
+    assert e.value.code == 4  # CVF_ETIMEOUT
+    op = oracle.physical_params(300.0, 0.1, L=16, seed=9)
+    ref = oracle.Oracle(op)
+    ref.run(12)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        lat.sweep(12)
+        assert np.array_equal(lat.state(), ref.state())
+
+
+def test_wait_probe_returns_when_the_flag_is_set():
+    flag = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    _capi.cvf_wait_probe(flag.data_ptr(), 5, 1 << 14)   # already >= target
+    _capi.cvf_wait_probe(flag.data_ptr(), 7, 1)
