@@ -61,8 +61,8 @@ def parse():
     return ap.parse_args()
 
 
-# Integer work of one sigma update (SURVEY 8(d) figure with one Philox call
-# per cell): a quarter of a Philox4x32-10 call (10 rounds of two 32x32->64
+# Algorithmic integer work of one sigma update with one Philox call per
+# cell: a quarter of a Philox4x32-10 call (10 rounds of two 32x32->64
 # multiplies and two 3-input XORs = 40 ops per cell) plus about 20 ops of the
 # update rule.  Peak: 152 SMs x 128 integer lanes x the 2070 MHz maximum clock.
 ALU_OPS_PER_UPDATE = 30.0
@@ -72,6 +72,11 @@ ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # is read once per step, the writes stay in L2).  Reset to None whenever the
 # kernel changes until a new capture is taken.
 SWEEP_DRAM_BYTES_4096 = 34.69e6
+# Thread instructions executed per sigma update by k_sweep_tiled at L = 4096
+# (smsp__inst_executed.sum x 32 / (4 L^2) from the same capture): the issue
+# rate the kernel sustains is this times the measured update rate, against
+# the 128 thread-instructions per clock an SM can issue.  None when stale.
+SWEEP_INSTR_PER_UPDATE = 113.313481e6 * 32 / (4 * 4096 * 4096)
 
 
 def dist_env():
@@ -656,10 +661,17 @@ def main():
     roofline_hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
                     "bytes_per_update": 1.0, "peak_kind": peak_kind}
+    roofline_issue = None
+    if SWEEP_INSTR_PER_UPDATE:
+        issued = SWEEP_INSTR_PER_UPDATE * upd_per_s / 1e12
+        roofline_issue = {"bound": "issue", "achieved": issued, "peak": ALU_PEAK_TOPS,
+                          "unit": "T thread-instructions/s", "frac": issued / ALU_PEAK_TOPS,
+                          "instructions_per_update": SWEEP_INSTR_PER_UPDATE,
+                          "instructions_source": "ncu smsp__inst_executed.sum of one launch"}
     # the 32 MB state stays in L2 across steps: the byte roofline that
     # bounds it is the L2 copy bandwidth, measured here with the library's
     # own copy kernel on the same working-set size (and, for reference, on
-    # buffers 16x the L2, against the driver's STREAM figure)
+    # buffers 16x the L2, beside the measured HBM copy peak)
     state_bytes = 2 * L * L
     l2_gbs = copy_bandwidth_gbs(stream, state_bytes, 400)
     dram_gbs = copy_bandwidth_gbs(stream, 1 << 31, 6)
@@ -724,6 +736,7 @@ def main():
             "roofline": roofline,
             "roofline_hbm": roofline_hbm,
             "roofline_l2": roofline_l2,
+            "roofline_issue": roofline_issue,
             "cpu_baseline": cpu,
             "cpu_baseline_all_cores": cpu_all,
             "e2e": e2e,
