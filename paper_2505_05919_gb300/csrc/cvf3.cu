@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "cvf_device.cuh"
@@ -298,52 +299,65 @@ __global__ void __launch_bounds__(kThreads3, 4) k_pass3(Args3 A, int launch) {
   const uint32_t stride = nblk * kThreads3;
   const uint32_t g_first = (blockIdx.x - first_block) * kThreads3 + threadIdx.x;
   if (ALIGNED) {
-    // the words of the next group are requested before this group's
-    // arithmetic, and every neighbour word of this group before its first
-    // pass, so that the loads overlap the Philox and update chains
-    const int arm0 = s_arm[0], arm1 = s_arm[1], arm2 = s_arm[2];
-    uint4 next = make_uint4(0u, 0u, 0u, 0u);
-    if (g_first < A.groups) next = *reinterpret_cast<const uint4*>(st + 4u * g_first);
-    for (uint32_t gi = g_first; gi < A.groups; gi += stride) {
-      const uint32_t c0 = gi * 4u;
-      const uint4 own = next;
-      if (gi + stride < A.groups) next = *reinterpret_cast<const uint4*>(st + 4u * (gi + stride));
-      const uint32_t row = fdiv(gi, A.div_G);      // y + L z
-      const uint32_t xg = gi - row * A.G;
-      const uint32_t z = fdiv(row, A.div_L);
-      const uint32_t y = row - z * A.L;
-      uint4 nbv[3];
+    // The group loop is compiled once per number of passes in the launch.
+    // Pass p's neighbour word is at c0 + dlt - (coordinate == edge ? wrp : 0)
+    // with the coordinate (x group, y or z), the edge value, the offset and
+    // the periodic wrap fixed for the launch.
+    auto body = [&](auto na_c) {
+      constexpr int NA = decltype(na_c)::value;
+      int arm[NA];
+      uint32_t ax[NA], edge[NA], dlt[NA], wrp[NA];
 #pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        const int a = (p == 0) ? arm0 : (p == 1) ? arm1 : arm2;
-        nbv[p] = make_uint4(0u, 0u, 0u, 0u);
-        if (p < n_arms) {
-          // arm a^1 of a neighbour is constant during the launch, so the
-          // cell's own words as loaded serve for the x neighbours
-          if (a == 0) {
-            nbv[p] = make_uint4(own.y, own.z, own.w,
-                                st[(4u * xg + 4u == A.L) ? c0 + 4u - A.L : c0 + 4u]);
-          } else if (a == 1) {
-            nbv[p] = make_uint4(st[(xg == 0u) ? c0 + A.L - 1u : c0 - 1u], own.x, own.y, own.z);
-          } else {
-            uint32_t off;
-            if (a == 2)
-              off = (y == A.L - 1u) ? c0 + A.L - A.L2 : c0 + A.L;
-            else if (a == 3)
-              off = (y == 0u) ? c0 + A.L2 - A.L : c0 - A.L;
-            else if (a == 4)
-              off = (z == A.L - 1u) ? c0 + A.L2 - A.N : c0 + A.L2;
-            else
-              off = (z == 0u) ? c0 + A.N - A.L2 : c0 - A.L2;
-            nbv[p] = *reinterpret_cast<const uint4*>(st + off);
-          }
+      for (int p = 0; p < NA; ++p) {
+        const int a = s_arm[p];
+        arm[p] = a;
+        const bool plus = (a & 1) == 0;
+        if (a < 2) {
+          ax[p] = 0u;
+          edge[p] = plus ? A.G - 1u : 0u;
+          dlt[p] = plus ? 4u : 0u - 1u;
+          wrp[p] = plus ? A.L : 0u - A.L;
+        } else if (a < 4) {
+          ax[p] = 1u;
+          edge[p] = plus ? A.L - 1u : 0u;
+          dlt[p] = plus ? A.L : 0u - A.L;
+          wrp[p] = plus ? A.L2 : 0u - A.L2;
+        } else {
+          ax[p] = 2u;
+          edge[p] = plus ? A.L - 1u : 0u;
+          dlt[p] = plus ? A.L2 : 0u - A.L2;
+          wrp[p] = plus ? A.N : 0u - A.N;
         }
       }
-      uint32_t w0 = own.x, w1 = own.y, w2 = own.z, w3 = own.w;
+      uint4 next = make_uint4(0u, 0u, 0u, 0u);
+      if (g_first < A.groups) next = *reinterpret_cast<const uint4*>(st + 4u * g_first);
+      for (uint32_t gi = g_first; gi < A.groups; gi += stride) {
+        const uint32_t c0 = gi * 4u;
+        const uint4 own = next;
+        if (gi + stride < A.groups) next = *reinterpret_cast<const uint4*>(st + 4u * (gi + stride));
+        const uint32_t row = fdiv(gi, A.div_G);      // y + L z
+        const uint32_t xg = gi - row * A.G;
+        const uint32_t z = fdiv(row, A.div_L);
+        const uint32_t y = row - z * A.L;
+        uint4 nbv[NA];
 #pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        if (p < n_arms) {
-          const int a = (p == 0) ? arm0 : (p == 1) ? arm1 : arm2;
+        for (int p = 0; p < NA; ++p) {
+          const uint32_t coord = (ax[p] == 0u) ? xg : ((ax[p] == 1u) ? y : z);
+          const uint32_t off = c0 + dlt[p] - ((coord == edge[p]) ? wrp[p] : 0u);
+          if (arm[p] >= 2) {
+            nbv[p] = *reinterpret_cast<const uint4*>(st + off);
+          } else {
+            // arm a^1 of a neighbour is constant during the launch, so the
+            // cell's own words as loaded serve for the x neighbours
+            const uint32_t xw = st[off];
+            nbv[p] = (arm[p] == 0) ? make_uint4(own.y, own.z, own.w, xw)
+                                   : make_uint4(xw, own.x, own.y, own.z);
+          }
+        }
+        uint32_t w0 = own.x, w1 = own.y, w2 = own.z, w3 = own.w;
+#pragma unroll
+        for (int p = 0; p < NA; ++p) {
+          const int a = arm[p];
           const uint32_t sh = 4u * (uint32_t)a, nsh = 24u - 4u * (uint32_t)(a ^ 1);
           const uint32_t amask = 0xFu << sh;
           const Words4 r = philox(gi, s_lo, s_hi, kTagArm0 + (uint32_t)a, A.keys);
@@ -352,11 +366,17 @@ __global__ void __launch_bounds__(kThreads3, 4) k_pass3(Args3 A, int launch) {
           w2 = update_arm3<CMP64>(w2, nbv[p].z, r.z, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
           w3 = update_arm3<CMP64>(w3, nbv[p].w, r.w, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
         }
+        unpack_counts(pk, nacc, hb_b, dc_b);
+        *reinterpret_cast<uint4*>(st + c0) = make_uint4(w0, w1, w2, w3);
+        if (rec) hist_group(w0, w1, w2, w3, s_hist);
       }
-      unpack_counts(pk, nacc, hb_b, dc_b);
-      *reinterpret_cast<uint4*>(st + c0) = make_uint4(w0, w1, w2, w3);
-      if (rec) hist_group(w0, w1, w2, w3, s_hist);
-    }
+    };
+    if (n_arms == 1)
+      body(std::integral_constant<int, 1>{});
+    else if (n_arms == 2)
+      body(std::integral_constant<int, 2>{});
+    else
+      body(std::integral_constant<int, 3>{});
   } else {
     for (uint32_t gi = g_first; gi < A.groups; gi += stride) {
       const uint32_t c0 = gi * 4u;
