@@ -160,6 +160,14 @@ int cvf_drain_series(cvf_handle *h, cvf_obs *host, int64_t cap, int64_t *n);
  * CVF_EINVAL if n != L*L. */
 int cvf_get_state(cvf_handle *h, uint16_t *host, size_t n);
 
+/* Copies the rectangle of cells x0 <= x < x0 + W, y0 <= y < y0 + H (inside
+ * the lattice, no wrap) to host[0 .. W*H), row by row (host[(y - y0) W +
+ * (x - x0)] = word of cell x + L y); synchronises.  For reading parts of
+ * lattices too large to copy whole.  CVF_EINVAL if the rectangle is empty
+ * or leaves the lattice. */
+int cvf_get_window(cvf_handle *h, int32_t x0, int32_t y0, int32_t W, int32_t H,
+                   uint16_t *host);
+
 /* Replaces the lattice by host[0..n) (n = L*L), sets V_iso and the step
  * counter, recounts N_HB_raw and N_sigma, and clears the acceptance
  * counters and the ring.  Every word is validated on the host first

@@ -117,6 +117,8 @@ def lib():
             "orc_arm_probe": (None, [P(Params), u16p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
                                      ctypes.c_int32, u32p, i32p, i32p, u64p]),
             "orc_arm_probe_all": (None, [P(Params), u16p, ctypes.c_int64, ctypes.c_int32, u32p, u64p]),
+            "orc_init_window": (None, [P(Params), u16p, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32]),
             "orc_window_run": (None, [P(Params), u16p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, i32p]),
             "orc_volume_chain": (ctypes.c_int64, [P(Params), ctypes.c_double, ctypes.c_int64,
@@ -263,6 +265,24 @@ def window_run(p: OracleParams, w_full: np.ndarray, x0: int, y0: int, W: int, H:
     lib().orc_window_run(ctypes.byref(cp), _ptr(a, ctypes.c_uint16), x0, y0, W, H, step0,
                          len(g), _ptr(g, ctypes.c_int32))
     return a
+
+
+def window_init_run(p: OracleParams, w_full: np.ndarray, x0: int, y0: int, W: int, H: int,
+                    step0: int, gates) -> None:
+    """In place on the L x L array w_full (which may be a lazily zeroed
+    array far larger than memory could hold written out): initialise the
+    window's cells by the init rule, then run len(gates) checkerboard steps
+    over the window alone.  Cells more than 2 len(gates) inside the window
+    are then exact; the window must lie inside the lattice."""
+    assert w_full.dtype == np.uint16 and w_full.flags.c_contiguous
+    assert w_full.size == p.L * p.L
+    assert 0 <= x0 and x0 + W <= p.L and 0 <= y0 and y0 + H <= p.L
+    g = np.ascontiguousarray(gates, dtype=np.int32)
+    cp = p.c()
+    ptr = w_full.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16))
+    lib().orc_init_window(ctypes.byref(cp), ptr, x0, y0, W, H)
+    lib().orc_window_run(ctypes.byref(cp), ptr, x0, y0, W, H, step0, len(g),
+                         _ptr(g, ctypes.c_int32))
 
 
 def volume_chain(p: OracleParams, V_iso: float, step0: int, K: int):

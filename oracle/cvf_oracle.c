@@ -263,6 +263,19 @@ static void orc_set_volume(orc_state *st, double V_iso) {
    Ordered init: every sigma = 0, so every bond is formed and every in-cell
    pair is equal.  V_iso starts at N v_iso_init (the paper gives no initial
    volume; the default per-cell value is the pair-LJ minimum 2^(1/3) v0). */
+/* The initial word of cell c: every sigma 0 (ordered), or sigma_a =
+   floor(r_a q / 2^32) with r = Philox((c, 0, 0, 2)) (random). */
+static uint16_t orc_init_word(const orc_params *p, int64_t c) {
+  uint16_t word = 0;
+  if (p->init == ORC_INIT_RANDOM) {
+    uint32_t r[4];
+    orc_draw(p, (uint32_t)c, 0, ORC_TAG_INIT, r);
+    for (int a = 0; a < 4; ++a)
+      word |= (uint16_t)(orc_scale(r[a], (uint32_t)p->q) << (4 * a));
+  }
+  return word;
+}
+
 int orc_init(orc_state *st, const orc_params *p, uint16_t *w) {
   int rc = orc_check_params(p);
   if (rc) return rc;
@@ -270,16 +283,7 @@ int orc_init(orc_state *st, const orc_params *p, uint16_t *w) {
   st->p = *p;
   st->N = (int64_t)p->L * p->L;
   st->w = w;
-  for (int64_t c = 0; c < st->N; ++c) {
-    uint16_t word = 0;
-    if (p->init == ORC_INIT_RANDOM) {
-      uint32_t r[4];
-      orc_draw(p, (uint32_t)c, 0, ORC_TAG_INIT, r);
-      for (int a = 0; a < 4; ++a)
-        word |= (uint16_t)(orc_scale(r[a], (uint32_t)p->q) << (4 * a));
-    }
-    w[c] = word;
-  }
+  for (int64_t c = 0; c < st->N; ++c) w[c] = orc_init_word(p, c);
   orc_set_volume(st, (double)st->N * p->v_iso_init);
   st->dV_max = p->dv_max_frac * ((double)st->N * p->v_iso_init);
   orc_threshold_table(p, st->table);
@@ -585,6 +589,17 @@ void orc_window_run(const orc_params *p, uint16_t *w, int32_t x0, int32_t y0,
           for (int a = 0; a < 4; ++a) orc_update_arm(&st, c, a, acc[a], kk[a]);
         }
   }
+}
+
+/* The initial words of the cells x0 <= x < x0 + W, y0 <= y < y0 + H of the
+   L x L lattice w (the rectangle must lie inside it; nothing else is
+   written), so that a window of a lattice too large to initialise whole can
+   be started and run by orc_window_run. */
+void orc_init_window(const orc_params *p, uint16_t *w, int32_t x0, int32_t y0,
+                     int32_t W, int32_t H) {
+  for (int64_t y = y0; y < (int64_t)y0 + H; ++y)
+    for (int64_t x = x0; x < (int64_t)x0 + W; ++x)
+      w[y * p->L + x] = orc_init_word(p, y * p->L + x);
 }
 
 /* The V_iso chain alone for K steps from (V_iso, step0), valid while no

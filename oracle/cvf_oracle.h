@@ -77,6 +77,8 @@ void orc_arm_probe(const orc_params *p, const uint16_t *w, int64_t c, int arm,
                    int32_t *dc, uint64_t *T);
 void orc_arm_probe_all(const orc_params *p, const uint16_t *cfgs, int64_t n,
                        int32_t g, uint32_t *s_new, uint64_t *T);
+void orc_init_window(const orc_params *p, uint16_t *w, int32_t x0, int32_t y0,
+                     int32_t W, int32_t H);
 void orc_window_run(const orc_params *p, uint16_t *w, int32_t x0, int32_t y0,
                     int32_t W, int32_t H, int64_t step0, int64_t K,
                     const int32_t *gates);

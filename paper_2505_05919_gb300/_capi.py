@@ -103,6 +103,8 @@ _SIGS = {
     "cvf3_destroy": (ctypes.c_int, [_vp]),
     "cvf3_set_resident": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "cvf3_get_resident": (ctypes.c_int, [_vp, _P(ctypes.c_int32)]),
+    "cvf_get_window": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, _P(ctypes.c_uint16)]),
     "cvf_copy_probe": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
     "cvf_wait_probe": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp]),
 }
@@ -386,3 +388,9 @@ def cvf_wait_probe(flag_ptr: int, target: int, polls: int, stream_ptr: int = 0) 
     """Run the library's bounded device wait on a device word (CvfError with
     code CVF_ETIMEOUT when it gives up)."""
     _check(load().cvf_wait_probe(flag_ptr, target, polls, stream_ptr or None), "cvf_wait_probe")
+
+
+def cvf_get_window(h: int, x0: int, y0: int, W: int, H: int, host_ptr: int) -> None:
+    """Copy the H x W rectangle of cell words at (x0, y0) to host_ptr."""
+    _check(load().cvf_get_window(h, x0, y0, W, H, ctypes.cast(host_ptr, _P(ctypes.c_uint16))),
+           "cvf_get_window")

@@ -1013,6 +1013,22 @@ int cvf_get_state(cvf_handle* h, uint16_t* host, size_t n) {
   return CVF_OK;
 }
 
+int cvf_get_window(cvf_handle* h, int32_t x0, int32_t y0, int32_t W, int32_t H,
+                   uint16_t* host) {
+  NvtxRange nvtx_range("cvf_get_window");
+  if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");
+  const long long L = h->p.L;
+  if (W < 1 || H < 1 || x0 < 0 || y0 < 0 || (long long)x0 + W > L || (long long)y0 + H > L)
+    return set_error(CVF_EINVAL, "window x0=%d y0=%d W=%d H=%d outside the %lld x %lld lattice",
+                     x0, y0, W, H, L, L);
+  const uint16_t* src = current(h) + (size_t)y0 * (size_t)L + (size_t)x0;
+  CVF_CUDA_CHECK(cudaMemcpy2DAsync(host, sizeof(uint16_t) * (size_t)W, src,
+                                   sizeof(uint16_t) * (size_t)L, sizeof(uint16_t) * (size_t)W,
+                                   (size_t)H, cudaMemcpyDeviceToHost, h->stream));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  return CVF_OK;
+}
+
 int cvf_set_state(cvf_handle* h, const uint16_t* host, size_t n, double V_iso, int64_t sweep) {
   NvtxRange nvtx_range("cvf_set_state");
   if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");

@@ -63,6 +63,13 @@ class Lattice:
         _capi.cvf_get_state(self.h, out.ctypes.data, self.N)
         return out.reshape(self.L, self.L)
 
+    def window(self, x0: int, y0: int, W: int, H: int) -> np.ndarray:
+        """The H x W rectangle of cell words at (x0, y0), without copying the
+        rest of the lattice."""
+        out = np.empty((H, W), np.uint16)
+        _capi.cvf_get_window(self.h, x0, y0, W, H, out.ctypes.data)
+        return out
+
     def set_state(self, words, V_iso: float, sweep: int = 0) -> None:
         a = np.ascontiguousarray(np.asarray(words, dtype=np.uint16).reshape(-1))
         _capi.cvf_set_state(self.h, a.ctypes.data, a.size, float(V_iso), int(sweep))

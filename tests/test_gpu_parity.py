@@ -339,3 +339,52 @@ def test_full_size_sampled_windows():
         ys, xs = slice(y0 + margin, y0 + margin + inner), slice(x0 + margin, x0 + margin + inner)
         assert np.array_equal(s_gpu[ys, xs], out[ys, xs])
     assert 0 < o_gpu["n_hb_raw"] <= 2 * L * L and 0 < o_gpu["n_coop"] <= 6 * L * L
+
+
+def test_window_reads_match_the_whole_state():
+    op = oracle.physical_params(300.0, 0.1, L=96, seed=12)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        lat.sweep(5)
+        full = lat.state()
+        for x0, y0, W, H in ((0, 0, 96, 96), (0, 0, 1, 1), (95, 95, 1, 1), (7, 60, 33, 36),
+                             (50, 0, 46, 3)):
+            assert np.array_equal(lat.window(x0, y0, W, H), full[y0:y0 + H, x0:x0 + W])
+        for bad in ((-1, 0, 4, 4), (0, 0, 0, 4), (93, 0, 4, 4), (0, 95, 4, 2)):
+            with pytest.raises(_capi.CvfError):
+                lat.window(*bad)
+
+
+@pytest.mark.parametrize("L", [65528, 65534])
+def test_maximum_size_sampled_windows(L):
+    """The largest lattices the library accepts (L = 65534, and 65528, the
+    largest multiple of 8, which stages its tiles by TMA): cell indices up to
+    4.29e9, just under 2^32.  After K steps, windows anywhere in the lattice
+    (both ends of the index range included) equal the oracle's run of the
+    same windows started from the init rule; V_iso follows the oracle's
+    volume chain; the kept counts equal a recount."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 2 * 2 * L * L + (4 << 30):
+        pytest.skip("needs %.1f GB of free device memory" % (4 * L * L / 1e9 + 4))
+    K = 3
+    op = oracle.physical_params(300.0, 0.1, L=L, q=6, seed=21)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        lat.sweep(K)
+        o = lat.observables()
+        assert lat.recount() == (o["n_hb_raw"], o["n_coop"])
+        done, V, g, acc = oracle.volume_chain(op, float(L * L) * op.v_iso_init, 0, K)
+        assert done == K
+        assert abs(o["V_iso"] - V[-1]) <= FP_REL * V[-1] and o["acc_volume"] == acc
+        assert 0 < o["n_hb_raw"] <= 2 * L * L and 0 < o["n_coop"] <= 6 * L * L
+        margin, inner = 2 * K + 2, 32
+        W = inner + 2 * margin
+        lazy = np.zeros((L, L), np.uint16)  # only the windows' pages are ever touched
+        rng = np.random.default_rng(L)
+        corners = [(0, 0), (L - W, 0), (0, L - W), (L - W, L - W)]
+        spots = corners + [(int(rng.integers(0, L - W)), int(rng.integers(0, L - W)))
+                           for _ in range(4)]
+        for x0, y0 in spots:
+            oracle.window_init_run(op, lazy, x0, y0, W, W, 0, g)
+            want = lazy[y0 + margin:y0 + margin + inner, x0 + margin:x0 + margin + inner]
+            got = lat.window(x0 + margin, y0 + margin, inner, inner)
+            assert np.array_equal(got, want), (x0, y0)

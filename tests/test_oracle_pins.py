@@ -380,3 +380,28 @@ def test_volume_move_lj_marginal():
     v = np.array([r["V_iso"] for r in rec]) / N
     m, se = _batch_mean(v, 100)
     assert abs(m - mean_v) < 5 * se + 2e-4, (m, se, mean_v)
+
+
+@pytest.mark.parametrize("init", [oracle.INIT_RANDOM, oracle.INIT_ORDERED])
+def test_window_init_run_matches_whole_lattice(init):
+    """A window started by the init rule alone (the rest of the lattice left
+    zero) and run K steps agrees with the whole lattice more than 2K + 2
+    cells inside its border: the tool behind the sampled checks of lattices
+    too large for the oracle to hold."""
+    L, K = 40, 3
+    op = oracle.physical_params(300.0, 0.1, L=L, seed=17, init=init)
+    ref = oracle.Oracle(op)
+    start = ref.state().copy()
+    done, V, g, _ = oracle.volume_chain(op, ref.observables()["V_iso"], 0, K)
+    assert done == K
+    ref.run(K)
+    whole = np.zeros((L, L), np.uint16)
+    oracle.window_init_run(op, whole, 0, 0, L, L, 0, [])
+    assert np.array_equal(whole, start)          # the init rule, cell by cell
+    w = np.zeros((L, L), np.uint16)
+    x0, y0, W, H = 3, 5, 30, 32
+    oracle.window_init_run(op, w, x0, y0, W, H, 0, g)
+    m = 2 * K + 2
+    inner = (slice(y0 + m, y0 + H - m), slice(x0 + m, x0 + W - m))
+    assert np.array_equal(w[inner], ref.state()[inner])
+    assert not w[:y0].any() and not w[:, :x0].any()  # nothing written outside
