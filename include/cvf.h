@@ -349,6 +349,13 @@ int cvf3_drain_series(cvf3_handle *h, cvf_obs *host, int64_t cap, int64_t *n);
  * (>= N) and the step counter, recounts, clears the acceptance counters and
  * the ring.  Both synchronise. */
 int cvf3_get_state(cvf3_handle *h, uint32_t *host, size_t n);
+
+/* Copies the box x0 <= x < x0 + W, y0 <= y < y0 + H, z0 <= z < z0 + D
+ * (inside the cube, no wrap) to host[0 .. W*H*D), x fastest
+ * (host[((z - z0) H + (y - y0)) W + (x - x0)] = word of cell x + L (y + L z));
+ * synchronises.  CVF_EINVAL if the box is empty or leaves the cube. */
+int cvf3_get_window(cvf3_handle *h, int32_t x0, int32_t y0, int32_t z0, int32_t W,
+                    int32_t H, int32_t D, uint32_t *host);
 int cvf3_set_state(cvf3_handle *h, const uint32_t *host, size_t n,
                    double V_iso, int64_t sweep);
 

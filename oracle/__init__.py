@@ -142,6 +142,9 @@ def lib():
                                       ctypes.c_int32, u32p, u64p]),
             "orc3_volume_chain": (ctypes.c_int64, [P(Params), ctypes.c_double, ctypes.c_int64,
                                                    ctypes.c_int64, ctypes.c_int64, dp]),
+            "orc3_init_window": (None, [P(Params), u32p] + [ctypes.c_int32] * 6),
+            "orc3_window_run": (None, [P(Params), u32p] + [ctypes.c_int32] * 6 +
+                                [ctypes.c_int64, ctypes.c_int64, i32p]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -413,6 +416,23 @@ def volume_chain3(p: OracleParams, V_iso: float, n_hb_raw: int, step0: int, K: i
     acc = lib().orc3_volume_chain(ctypes.byref(cp), V_iso, n_hb_raw, step0, K,
                                   _ptr(V, ctypes.c_double))
     return V, acc
+
+
+def window_init_run3(p: OracleParams, w_full: np.ndarray, x0: int, y0: int, z0: int, W: int,
+                     H: int, D: int, step0: int, gates) -> None:
+    """In place on the L^3 array w_full (possibly lazily zeroed): initialise
+    the box's cells by the init rule, then run len(gates) layered steps over
+    the box alone.  Cells more than 2 len(gates) inside the box are then
+    exact; the box must lie inside the cube."""
+    L = p.L
+    assert w_full.dtype == np.uint32 and w_full.flags.c_contiguous and w_full.size == L ** 3
+    assert 0 <= x0 and x0 + W <= L and 0 <= y0 and y0 + H <= L and 0 <= z0 and z0 + D <= L
+    g = np.ascontiguousarray(gates, dtype=np.int32)
+    cp = p.c()
+    ptr = w_full.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    lib().orc3_init_window(ctypes.byref(cp), ptr, x0, y0, z0, W, H, D)
+    lib().orc3_window_run(ctypes.byref(cp), ptr, x0, y0, z0, W, H, D, step0, len(g),
+                          _ptr(g, ctypes.c_int32))
 
 
 class Oracle3:

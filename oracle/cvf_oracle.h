@@ -117,6 +117,11 @@ int64_t orc3_run(orc3_state *st, int64_t n, int32_t record_every, orc_obs *ring,
                  int64_t cap);
 void orc3_arm_probe(const orc_params *p, const uint32_t *w, int64_t c, int a,
                     uint32_t k, int32_t g, uint32_t *s_new, uint64_t *T);
+void orc3_init_window(const orc_params *p, uint32_t *w, int32_t x0, int32_t y0, int32_t z0,
+                      int32_t W, int32_t H, int32_t D);
+void orc3_window_run(const orc_params *p, uint32_t *w, int32_t x0, int32_t y0, int32_t z0,
+                     int32_t W, int32_t H, int32_t D, int64_t step0, int64_t K,
+                     const int32_t *gates);
 int64_t orc3_volume_chain(const orc_params *p, double V_iso, int64_t n_hb_raw,
                           int64_t step0, int64_t K, double *V_out);
 #endif

@@ -192,17 +192,21 @@ static void o3_start(orc3_state *st, const orc_params *p, uint32_t *w, double V_
   orc3_recount(p, w, &st->n_hb_raw, &st->n_coop);
 }
 
+/* The initial word of cell c: every sigma 0 (ordered), or sigma_a =
+   floor(r q / 2^32) with r word c mod 4 of Philox((c / 4, 0, 0, 16 + a)). */
+static uint32_t o3_init_word(const orc_params *p, int64_t c) {
+  uint32_t word = 0;
+  if (p->init == ORC_INIT_RANDOM)
+    for (int a = 0; a < 6; ++a)
+      word |= o3_scale(o3_word(p, c, 0, 16u + (uint32_t)a), (uint32_t)p->q) << (4 * a);
+  return word;
+}
+
 int orc3_init(orc3_state *st, const orc_params *p, uint32_t *w) {
   int rc = orc3_check_params(p);
   if (rc) return rc;
   int64_t N = (int64_t)p->L * p->L * p->L;
-  for (int64_t c = 0; c < N; ++c) {
-    uint32_t word = 0;
-    if (p->init == ORC_INIT_RANDOM)
-      for (int a = 0; a < 6; ++a)
-        word |= o3_scale(o3_word(p, c, 0, 16u + (uint32_t)a), (uint32_t)p->q) << (4 * a);
-    w[c] = word;
-  }
+  for (int64_t c = 0; c < N; ++c) w[c] = o3_init_word(p, c);
   o3_start(st, p, w, (double)N * p->v_iso_init, 0);
   return ORC_OK;
 }
@@ -310,6 +314,47 @@ void orc3_step(orc3_state *st) {
   for (int pass = 0; pass < 6; ++pass)
     for (int64_t c = 0; c < st->N; ++c) o3_update_arm(st, c, order[pass]);
   st->sweep += 1;
+}
+
+/* The initial words of the box x0 <= x < x0 + W, y0 <= y < y0 + H,
+   z0 <= z < z0 + D of the L^3 cube w (inside it; nothing else written). */
+void orc3_init_window(const orc_params *p, uint32_t *w, int32_t x0, int32_t y0, int32_t z0,
+                      int32_t W, int32_t H, int32_t D) {
+  const int64_t L = p->L;
+  for (int64_t z = z0; z < (int64_t)z0 + D; ++z)
+    for (int64_t y = y0; y < (int64_t)y0 + H; ++y)
+      for (int64_t x = x0; x < (int64_t)x0 + W; ++x) {
+        const int64_t c = (z * L + y) * L + x;
+        w[c] = o3_init_word(p, c);
+      }
+}
+
+/* K steps over the box alone: step s takes the gate gates[s] (the gate its
+   passes use, after its volume move, which the caller's chain provides) and
+   runs the six passes in the step's drawn order over the box's cells.  A
+   pass moves information by at most one cell along its axis, so a step by at
+   most two along each axis: cells more than 2K inside the box are exact. */
+void orc3_window_run(const orc_params *p, uint32_t *w, int32_t x0, int32_t y0, int32_t z0,
+                     int32_t W, int32_t H, int32_t D, int64_t step0, int64_t K,
+                     const int32_t *gates) {
+  orc3_state st;
+  memset(&st, 0, sizeof(st));
+  st.p = *p;
+  st.N = (int64_t)p->L * p->L * p->L;
+  st.w = w;
+  orc3_threshold_table(p, st.table);
+  const int64_t L = p->L;
+  for (int64_t s = 0; s < K; ++s) {
+    st.sweep = step0 + s;
+    st.g = gates[s];
+    int order[6];
+    orc3_layer_order(p, st.sweep, order);
+    for (int pass = 0; pass < 6; ++pass)
+      for (int64_t z = z0; z < (int64_t)z0 + D; ++z)
+        for (int64_t y = y0; y < (int64_t)y0 + H; ++y)
+          for (int64_t x = x0; x < (int64_t)x0 + W; ++x)
+            o3_update_arm(&st, (z * L + y) * L + x, order[pass]);
+  }
 }
 
 /* Observables (Eq. V, Eq. H) and N_q' over all 6N variables. */

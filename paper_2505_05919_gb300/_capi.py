@@ -105,6 +105,7 @@ _SIGS = {
     "cvf3_get_resident": (ctypes.c_int, [_vp, _P(ctypes.c_int32)]),
     "cvf_get_window": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_int32, _P(ctypes.c_uint16)]),
+    "cvf3_get_window": (ctypes.c_int, [_vp] + [ctypes.c_int32] * 6 + [_P(ctypes.c_uint32)]),
     "cvf_copy_probe": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
     "cvf_wait_probe": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp]),
 }
@@ -394,3 +395,10 @@ def cvf_get_window(h: int, x0: int, y0: int, W: int, H: int, host_ptr: int) -> N
     """Copy the H x W rectangle of cell words at (x0, y0) to host_ptr."""
     _check(load().cvf_get_window(h, x0, y0, W, H, ctypes.cast(host_ptr, _P(ctypes.c_uint16))),
            "cvf_get_window")
+
+
+def cvf3_get_window(h: int, x0: int, y0: int, z0: int, W: int, H: int, D: int,
+                    host_ptr: int) -> None:
+    """Copy the D x H x W box of cell words at (x0, y0, z0) to host_ptr."""
+    _check(load().cvf3_get_window(h, x0, y0, z0, W, H, D,
+                                  ctypes.cast(host_ptr, _P(ctypes.c_uint32))), "cvf3_get_window")

@@ -1165,6 +1165,27 @@ int cvf3_get_state(cvf3_handle* h, uint32_t* host, size_t n) {
   return CVF_OK;
 }
 
+int cvf3_get_window(cvf3_handle* h, int32_t x0, int32_t y0, int32_t z0, int32_t W, int32_t H,
+                    int32_t D, uint32_t* host) {
+  NvtxRange nvtx_range("cvf3_get_window");
+  if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");
+  const long long L = h->p.L;
+  if (W < 1 || H < 1 || D < 1 || x0 < 0 || y0 < 0 || z0 < 0 || (long long)x0 + W > L ||
+      (long long)y0 + H > L || (long long)z0 + D > L)
+    return set_error(CVF_EINVAL, "box (%d, %d, %d) + (%d, %d, %d) outside the %lld^3 cube", x0,
+                     y0, z0, W, H, D, L);
+  const size_t row = sizeof(uint32_t) * (size_t)L;
+  for (int32_t z = 0; z < D; ++z) {
+    const uint32_t* src = h->state + ((size_t)(z0 + z) * (size_t)L + (size_t)y0) * (size_t)L +
+                          (size_t)x0;
+    CVF_CUDA_CHECK(cudaMemcpy2DAsync(host + (size_t)z * H * W, sizeof(uint32_t) * (size_t)W, src,
+                                     row, sizeof(uint32_t) * (size_t)W, (size_t)H,
+                                     cudaMemcpyDeviceToHost, h->stream));
+  }
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  return CVF_OK;
+}
+
 int cvf3_set_state(cvf3_handle* h, const uint32_t* host, size_t n, double V_iso, int64_t sweep) {
   NvtxRange nvtx_range("cvf3_set_state");
   if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");

@@ -57,6 +57,13 @@ class Lattice3:
         _capi.cvf3_get_state(self.h, out.ctypes.data, self.N)
         return out.reshape(self.L, self.L, self.L)
 
+    def window(self, x0: int, y0: int, z0: int, W: int, H: int, D: int) -> np.ndarray:
+        """The D x H x W box of cell words at (x0, y0, z0), without copying
+        the rest of the cube."""
+        out = np.empty((D, H, W), np.uint32)
+        _capi.cvf3_get_window(self.h, x0, y0, z0, W, H, D, out.ctypes.data)
+        return out
+
     def set_state(self, words, V_iso: float, sweep: int = 0) -> None:
         a = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).reshape(-1))
         _capi.cvf3_set_state(self.h, a.ctypes.data, a.size, float(V_iso), int(sweep))

@@ -198,3 +198,58 @@ def test_lattice3_resident_choice():
         assert not lat.resident()          # 12 is not a multiple of 8
         with pytest.raises(_capi.CvfError):
             lat.set_resident(1)
+
+
+def test_lattice3_window_reads_match_the_whole_state():
+    op = oracle.physical_params3(300.0, 0.1, L=20, seed=8)
+    with Lattice3(params_from_dict(asdict(op))) as lat:
+        lat.sweep(3)
+        full = lat.state()
+        for x0, y0, z0, W, H, D in ((0, 0, 0, 20, 20, 20), (19, 19, 19, 1, 1, 1),
+                                    (3, 5, 7, 11, 9, 13), (0, 17, 2, 20, 3, 1)):
+            assert np.array_equal(lat.window(x0, y0, z0, W, H, D),
+                                  full[z0:z0 + D, y0:y0 + H, x0:x0 + W])
+        for bad in ((-1, 0, 0, 2, 2, 2), (0, 0, 0, 2, 0, 2), (0, 0, 19, 2, 2, 2)):
+            with pytest.raises(_capi.CvfError):
+                lat.window(*bad)
+
+
+@pytest.mark.parametrize("L", [1024, 1021])
+def test_lattice3_maximum_size_sampled_boxes(L):
+    """The largest cubes the library accepts (1024^3 = 1.07e9 cells on the
+    16-byte group path; 1021^3 on the per-cell path): after K steps, boxes
+    at opposite corners and random places equal the oracle's run of the same
+    boxes started from the init rule; V_iso follows the volume chain; the
+    kept counts equal a recount."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 4 * L ** 3 + (4 << 30):
+        pytest.skip("needs %.1f GB of free device memory" % (4 * L ** 3 / 1e9 + 4))
+    K = 2
+    op = oracle.physical_params3(300.0, 0.1, L=L, seed=23)
+    N = L ** 3
+    with Lattice3(params_from_dict(asdict(op))) as lat:
+        ob0 = lat.observables()
+        lat.sweep(K)
+        o = lat.observables()
+        assert lat.recount() == (o["n_hb_raw"], o["n_coop"])
+    V, acc = oracle.volume_chain3(op, float(N) * op.v_iso_init, ob0["n_hb_raw"], 0, K)
+    gates = [int(v / N < 2.0) for v in V]
+    assert all(gg == ob0["g"] for gg in gates)   # no gate change: the chain needs no bonds
+    assert abs(o["V_iso"] - V[-1]) <= REL * V[-1] and o["acc_volume"] == acc
+    assert 0 < o["n_hb_raw"] <= 3 * N and 0 < o["n_coop"] <= 15 * N
+    margin, inner = 2 * K + 2, 16
+    W = inner + 2 * margin
+    rng = np.random.default_rng(L)
+    spots = [(0, 0, 0), (L - W, L - W, L - W), (L - W, 0, L - W), (0, L - W, 0)]
+    spots += [tuple(int(v) for v in rng.integers(0, L - W, 3)) for _ in range(4)]
+    lazy = np.zeros(N, np.uint32)  # only the boxes' pages are ever touched
+    cube = lazy.reshape(L, L, L)
+    with Lattice3(params_from_dict(asdict(op))) as lat:
+        lat.sweep(K)
+        for x0, y0, z0 in spots:
+            oracle.window_init_run3(op, lazy, x0, y0, z0, W, W, W, 0, gates)
+            want = cube[z0 + margin:z0 + margin + inner, y0 + margin:y0 + margin + inner,
+                        x0 + margin:x0 + margin + inner]
+            got = lat.window(x0 + margin, y0 + margin, z0 + margin, inner, inner, inner)
+            assert np.array_equal(got, want), (x0, y0, z0)

@@ -376,3 +376,31 @@ def test_volume_move_gate_term():
         if abs(u2 - math.exp(min(arg, 700))) < 1e-9:
             continue   # too close to call in a different summation order
         assert acc == (1 if u2 < math.exp(min(arg, 700)) else 0), step
+
+
+@pytest.mark.parametrize("init", [oracle.INIT_RANDOM, oracle.INIT_ORDERED])
+def test_window_init_run3_matches_whole_cube(init):
+    """A box started by the init rule alone and run K layered steps agrees
+    with the whole cube more than 2K + 2 cells inside (a pass moves
+    information one cell along its axis, a step two)."""
+    L, K = 24, 2
+    op = oracle.physical_params3(300.0, 0.1, L=L, seed=19, init=init, dv_max_frac=0.05)
+    ref = oracle.Oracle3(op)
+    start = ref.state().copy()
+    ob = ref.observables()
+    V, _ = oracle.volume_chain3(op, ob["V_iso"], ob["n_hb_raw"], 0, K)
+    gates = [int(v / L ** 3 < 2.0) for v in V]
+    assert all(gg == ob["g"] for gg in gates)    # no gate change: the chain needs no bonds
+    ref.run(K)
+    whole = np.zeros(L ** 3, np.uint32)
+    oracle.window_init_run3(op, whole, 0, 0, 0, L, L, L, 0, [])
+    assert np.array_equal(whole.reshape(start.shape), start)
+    w = np.zeros(L ** 3, np.uint32)
+    x0, y0, z0, W, H, D = 2, 1, 3, 20, 21, 19
+    oracle.window_init_run3(op, w, x0, y0, z0, W, H, D, 0, gates)
+    m = 2 * K + 2
+    cube = w.reshape(L, L, L)
+    want = ref.state().reshape(L, L, L)
+    inner = (slice(z0 + m, z0 + D - m), slice(y0 + m, y0 + H - m), slice(x0 + m, x0 + W - m))
+    assert np.array_equal(cube[inner], want[inner])
+    assert not cube[:z0].any()
