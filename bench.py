@@ -479,7 +479,8 @@ def measure_batched(args, rank):
     single-lattice form, as replica-steps per second."""
     import torch
     from paper_2505_05919_gb300 import Batch, Lattice, dist, params, workloads
-    from paper_2505_05919_gb300.autotune import autotune
+    from paper_2505_05919_gb300.autotune import autotune, cells_per_thread
+    from paper_2505_05919_gb300.batch import tile_configs
     reps = workloads.c4(sweeps=args.batch_sweeps)
     ps = [params(r["T"], r["P"], L=r["L"], q=r["q"], seed=r["seed"] + dist.seed_offset(rank)) for r in reps]
     stream = torch.cuda.Stream()
@@ -535,7 +536,8 @@ def measure_batched(args, rank):
                                       "form": "each replica alone in its fastest single-lattice "
                                               "form (small lattices resident in one cluster)"},
             "speedup_vs_one_lattice_at_a_time": batched_rate / alone_rate,
-            "tile_config": best, "autotune_ms_per_step": timings,
+            "tile_config": best, "tile": list(tile_configs()[best]),
+            "cells_per_thread": cells_per_thread(best), "autotune_ms_per_step": timings,
             "workload": "256 replicas, L from {32,64,128,256,512} (seed 4), T_i = 270 + 4i K, "
                         "P_j = 0.1 + j 49.9/15 MPa, seeds 1000 + r"}
 

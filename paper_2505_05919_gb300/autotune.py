@@ -1,9 +1,16 @@
-"""Autotuner of the batched kernel's tile shape.
+"""Autotuner of the batched kernel's tile shape and cells per thread.
 
-For a list of replica parameters it builds a scratch batch with the same
-lattice sizes (other seeds, so the caller's replicas are untouched), times a
-short probe on every tile configuration with CUDA events, and returns the
-fastest.  Results are cached per size signature for the process.
+A tile configuration is a tile of rows x 32-bit words (two cells per word)
+swept by one block of 256 threads, so it fixes the cells each thread
+updates per colour phase: 64 x 64 words -> 32 cells per thread (16 per
+phase), 32 x 32 -> 8, 32 x 16 -> 4, 16 x 16 -> 2.  Large tiles amortise the
+recomputed one-cell ring and the staging; small ones give small lattices
+enough tiles to fill the GPU.
+
+For a list of replica parameters the tuner builds a scratch batch with the
+same lattice sizes (other seeds, so the caller's replicas are untouched),
+times a short probe on every configuration with CUDA events, and returns
+the fastest.  Results are cached per size signature for the process.
 """
 from __future__ import annotations
 
@@ -17,6 +24,12 @@ _cache: dict = {}
 
 def signature(params_list) -> tuple:
     return tuple(sorted((p.L, p.q, p.rng_words) for p in params_list))
+
+
+def cells_per_thread(config: int) -> int:
+    """Cells one of the block's 256 threads updates per MC step."""
+    rows, words = tile_configs()[config]
+    return 2 * rows * words // 256
 
 
 def autotune(params_list, probe_sweeps: int = 20, warmup: int = 3, stream=None):

@@ -130,3 +130,12 @@ def test_wait_probe_rejects_bad_arguments_on_host(lib, flag, polls):
     with pytest.raises(_capi.CvfError) as e:
         _capi.cvf_wait_probe(flag, 1, polls, 0)
     assert e.value.code == 1  # CVF_EINVAL, before any device work
+
+
+def test_batch_tile_configs_and_cells_per_thread(lib):
+    from paper_2505_05919_gb300.autotune import cells_per_thread
+    from paper_2505_05919_gb300.batch import tile_configs
+    cfgs = tile_configs()
+    assert cfgs[0] == (64, 64)
+    assert [cells_per_thread(c) for c in range(len(cfgs))] == [2 * r * w // 256 for r, w in cfgs]
+    assert cells_per_thread(0) == 32 and min(cells_per_thread(c) for c in range(len(cfgs))) >= 1
