@@ -50,6 +50,7 @@ extern "C" {
 #define CVF_ETIMEOUT 4  /* a bounded device-side wait gave up */
 #define CVF_EBUSY 5     /* the handle has work that conflicts with the call */
 #define CVF_EOVERFLOW 6 /* the observable ring overwrote unread records */
+#define CVF_EBOUNDS 7   /* a debug build's device-side index check failed */
 
 #define CVF_INIT_RANDOM 0
 #define CVF_INIT_ORDERED 1
@@ -92,8 +93,10 @@ typedef struct cvf_obs {
   double U_LJ;        /* Lennard-Jones energy, eps */
   double H;           /* H = U_LJ - J N_HB - J_sigma N_sigma + P V (Eq. H) */
   int32_t g;          /* gate: 1 liquid-like (V_iso/N < 2 v0), 0 gas-like */
-  int32_t status;     /* 0; nonzero if a bounded device-side wait gave up
-                         (the call then returns CVF_ETIMEOUT) */
+  int32_t status;     /* 0; 1 if a bounded device-side wait gave up (the
+                         call then returns CVF_ETIMEOUT); 0x100 + site if a
+                         debug build's index check at `site` failed
+                         (CVF_EBOUNDS) */
   int64_t n_state[8]; /* N_q': sigma variables in state q' (q' >= q: 0);
                          the order parameter is M = max N_q' / (4N),
                          Eq. (correlation) */
@@ -396,6 +399,13 @@ int cvf3_destroy(cvf3_handle *h);
  * misaligned argument, CVF_ECUDA if the launch fails.
  * ------------------------------------------------------------------------ */
 int cvf_copy_probe(void *dst, const void *src, size_t bytes, void *stream);
+
+/* 1 if this library was built with device-side index checks (CVF_DEBUG:
+ * every kernel checks its shared- and global-memory indices and the TMA
+ * alignment rule, records the first failing site in the lattice's status
+ * word, skips the access, and the calls that read results return
+ * CVF_EBOUNDS), 0 for the release build.  Host only. */
+int cvf_debug_checks(void);
 
 /* ------------------------------------------------------------------------
  * Failure detection without a fault.

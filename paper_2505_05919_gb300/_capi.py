@@ -17,7 +17,7 @@ CVF_INIT_RANDOM, CVF_INIT_ORDERED = 0, 1
 CVF_SCHED_CHECKERBOARD, CVF_SCHED_LAYERED = 0, 1
 
 _ERRNAMES = {1: "CVF_EINVAL", 2: "CVF_ENOMEM", 3: "CVF_ECUDA", 4: "CVF_ETIMEOUT",
-             5: "CVF_EBUSY", 6: "CVF_EOVERFLOW"}
+             5: "CVF_EBUSY", 6: "CVF_EOVERFLOW", 7: "CVF_EBOUNDS"}
 
 
 class CvfError(RuntimeError):
@@ -106,6 +106,7 @@ _SIGS = {
     "cvf_get_window": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_int32, _P(ctypes.c_uint16)]),
     "cvf3_get_window": (ctypes.c_int, [_vp] + [ctypes.c_int32] * 6 + [_P(ctypes.c_uint32)]),
+    "cvf_debug_checks": (ctypes.c_int, []),
     "cvf_copy_probe": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
     "cvf_wait_probe": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp]),
 }
@@ -402,3 +403,8 @@ def cvf3_get_window(h: int, x0: int, y0: int, z0: int, W: int, H: int, D: int,
     """Copy the D x H x W box of cell words at (x0, y0, z0) to host_ptr."""
     _check(load().cvf3_get_window(h, x0, y0, z0, W, H, D,
                                   ctypes.cast(host_ptr, _P(ctypes.c_uint32))), "cvf3_get_window")
+
+
+def cvf_debug_checks() -> bool:
+    """Whether the loaded library is the debug build with device index checks."""
+    return load().cvf_debug_checks() == 1

@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(kThreads3, 4) k_pass3(Args3 A, int launch) {
       if (g_first < A.groups) next = *reinterpret_cast<const uint4*>(st + 4u * g_first);
       for (uint32_t gi = g_first; gi < A.groups; gi += stride) {
         const uint32_t c0 = gi * 4u;
+        if (!dcheck(c0 + 3u < A.N, &ctl->error, kSitePass3)) break;
         const uint4 own = next;
         if (gi + stride < A.groups) next = *reinterpret_cast<const uint4*>(st + 4u * (gi + stride));
         const uint32_t row = fdiv(gi, A.div_G);      // y + L z
@@ -345,11 +346,13 @@ __global__ void __launch_bounds__(kThreads3, 4) k_pass3(Args3 A, int launch) {
           const uint32_t coord = (ax[p] == 0u) ? xg : ((ax[p] == 1u) ? y : z);
           const uint32_t off = c0 + dlt[p] - ((coord == edge[p]) ? wrp[p] : 0u);
           if (arm[p] >= 2) {
-            nbv[p] = *reinterpret_cast<const uint4*>(st + off);
+            nbv[p] = dcheck((off & 3u) == 0u && off + 3u < A.N, &ctl->error, kSitePass3)
+                         ? *reinterpret_cast<const uint4*>(st + off)
+                         : make_uint4(0u, 0u, 0u, 0u);
           } else {
             // arm a^1 of a neighbour is constant during the launch, so the
             // cell's own words as loaded serve for the x neighbours
-            const uint32_t xw = st[off];
+            const uint32_t xw = dcheck(off < A.N, &ctl->error, kSitePass3) ? st[off] : 0u;
             nbv[p] = (arm[p] == 0) ? make_uint4(own.y, own.z, own.w, xw)
                                    : make_uint4(xw, own.x, own.y, own.z);
           }
@@ -416,6 +419,7 @@ __global__ void __launch_bounds__(kThreads3, 4) k_pass3(Args3 A, int launch) {
             nb = (z[i] + 1u == A.L) ? c + A.L2 - A.N : c + A.L2;
           else
             nb = (z[i] == 0u) ? c + A.N - A.L2 : c - A.L2;
+          if (!dcheck(nb < A.N, &ctl->error, kSitePass3)) continue;
           w[i] = update_arm3<CMP64>(w[i], st[nb], rw[i], sh, nsh, amask, qm1, sProp, sRows,
                                     sT64, pk);
         }
@@ -636,29 +640,38 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
     for (int j = 0; j < nseg; ++j) {
       int arms[3] = {0, 0, 0};
       const int n_arms = plan_arms(plan, j, arms);
+      // loads of the slab's words (and the neighbouring slabs' planes),
+      // index-checked in debug builds
+      const uint32_t slab = R * L2;
+      auto vec = [&](const uint32_t* base, uint32_t idx, uint32_t n) -> uint4 {
+        return dcheck((idx & 3u) == 0u && idx + 3u < n, &ctl->error, kSiteResident3)
+                   ? *reinterpret_cast<const uint4*>(base + idx)
+                   : make_uint4(0u, 0u, 0u, 0u);
+      };
+      auto word = [&](uint32_t idx) -> uint32_t {
+        return dcheck(idx < slab, &ctl->error, kSiteResident3) ? cube[idx] : 0u;
+      };
       for (uint32_t i = threadIdx.x; i < R * L2 / 4u; i += kRes3Threads) {
         const uint32_t c0 = 4u * i;  // local cell of the group
         const uint32_t zl = c0 / L2, rem = c0 - zl * L2, y = rem / L, xg = (rem - y * L) >> 2;
         const uint32_t gi = (z0 * L2 + c0) >> 2;  // global group index (Philox counter)
-        const uint4 own = *reinterpret_cast<const uint4*>(cube + c0);
+        const uint4 own = vec(cube, c0, slab);
         uint32_t w0 = own.x, w1 = own.y, w2 = own.z, w3 = own.w;
         for (int p = 0; p < n_arms; ++p) {
           const int a = arms[p];
           uint4 nb;
           if (a == 0) {
-            nb = make_uint4(own.y, own.z, own.w, cube[(xg + 1u == G) ? c0 + 4u - L : c0 + 4u]);
+            nb = make_uint4(own.y, own.z, own.w, word((xg + 1u == G) ? c0 + 4u - L : c0 + 4u));
           } else if (a == 1) {
-            nb = make_uint4(cube[(xg == 0u) ? c0 + L - 1u : c0 - 1u], own.x, own.y, own.z);
+            nb = make_uint4(word((xg == 0u) ? c0 + L - 1u : c0 - 1u), own.x, own.y, own.z);
           } else if (a == 2) {
-            nb = *reinterpret_cast<const uint4*>(cube + ((y == L - 1u) ? c0 + L - L2 : c0 + L));
+            nb = vec(cube, (y == L - 1u) ? c0 + L - L2 : c0 + L, slab);
           } else if (a == 3) {
-            nb = *reinterpret_cast<const uint4*>(cube + ((y == 0u) ? c0 + L2 - L : c0 - L));
+            nb = vec(cube, (y == 0u) ? c0 + L2 - L : c0 - L, slab);
           } else if (a == 4) {
-            nb = (zl == R - 1u) ? *reinterpret_cast<const uint4*>(above + rem)
-                                : *reinterpret_cast<const uint4*>(cube + c0 + L2);
+            nb = (zl == R - 1u) ? vec(above, rem, L2) : vec(cube, c0 + L2, slab);
           } else {
-            nb = (zl == 0u) ? *reinterpret_cast<const uint4*>(below + rem)
-                            : *reinterpret_cast<const uint4*>(cube + c0 - L2);
+            nb = (zl == 0u) ? vec(below, rem, L2) : vec(cube, c0 - L2, slab);
           }
           const uint32_t sh = 4u * (uint32_t)a, nsh = 24u - 4u * (uint32_t)(a ^ 1);
           const uint32_t amask = 0xFu << sh;
@@ -669,7 +682,8 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
           w3 = update_arm3<CMP64>(w3, nb.w, r.w, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
         }
         unpack_counts(pk, nacc, hb_b, dc_b);
-        *reinterpret_cast<uint4*>(cube + c0) = make_uint4(w0, w1, w2, w3);
+        if (dcheck(c0 + 3u < slab, &ctl->error, kSiteResident3))
+          *reinterpret_cast<uint4*>(cube + c0) = make_uint4(w0, w1, w2, w3);
         if (rec && j == nseg - 1) hist_group(w0, w1, w2, w3, s_h);
       }
       if (j == nseg - 1) {
@@ -1123,7 +1137,7 @@ int cvf3_observables(cvf3_handle* h, cvf_obs* out) {
                                  cudaMemcpyDeviceToHost, h->stream));
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
   std::memcpy(out, h->host_pinned, sizeof(cvf_obs));
-  return CVF_OK;
+  return status_error(out->status);
 }
 
 int cvf3_drain_series(cvf3_handle* h, cvf_obs* host, int64_t cap, int64_t* n) {

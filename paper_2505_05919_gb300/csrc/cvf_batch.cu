@@ -47,7 +47,7 @@ struct ReplicaDesc {
 constexpr int kBatchMaxSegments = 64;
 struct BatchWork {
   unsigned long long next;   // item counter
-  unsigned int error;        // 1: a wait gave up
+  unsigned int error;        // 1: a wait gave up; 0x100 + site: a debug index check failed
   unsigned int pad;
   long long total_items;
   int32_t n_active;          // replicas advanced by this launch
@@ -114,12 +114,18 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
         s_rep = rep;
         s_tile = (int)(j - tile_prefix[lo]);
         s_rel = s;
-        // wait until the replica has completed s steps of this launch
-        const WaitResult wr =
-            wait_flag_geq(&progress[rep], (unsigned int)s, &W->error, kWaitPollLimit);
-        if (wr != kWaitDone) {
-          if (wr == kWaitGaveUp) atomicExch(&W->error, 1u);
+        if (!dcheck(k < W->nseg && A <= W->n_active && lo >= 0 && lo < A && j >= 0 && j < T &&
+                        j < tile_prefix[lo + 1] && s >= 0,
+                    &W->error, kSiteBatchItem)) {
           abort = 1;
+        } else {
+          // wait until the replica has completed s steps of this launch
+          const WaitResult wr =
+              wait_flag_geq(&progress[rep], (unsigned int)s, &W->error, kWaitPollLimit);
+          if (wr != kWaitDone) {
+            if (wr == kWaitGaveUp) atomicExch(&W->error, 1u);
+            abort = 1;
+          }
         }
       }
       s_abort = abort;
@@ -150,6 +156,7 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     v.s_hi = (uint32_t)((unsigned long long)step >> 32);
     v.keys.k0 = R.seed_lo;
     v.keys.k1 = R.seed_hi;
+    v.err = &W->error;
     const int tiles_x = (Lh + TW - 1) / TW;
     const int ntiles = tiles_x * ((L + TR - 1) / TR);
     const int t = s_tile;
@@ -431,6 +438,9 @@ int batch_status(cvf_batch* b) {
   CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
   unsigned int err = 0;
   std::memcpy(&err, b->h_pinned, sizeof(err));
+  if (err >= 0x100u)
+    return set_error(CVF_EBOUNDS, "a device index check of the batched sweep failed (site %u)",
+                     err - 0x100u);
   if (err) return set_error(CVF_ETIMEOUT, "a replica wait in the batched sweep gave up");
   return CVF_OK;
 }

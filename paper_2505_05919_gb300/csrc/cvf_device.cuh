@@ -471,6 +471,36 @@ __device__ __forceinline__ void block_sum3(uint32_t& a, uint32_t& b, uint32_t& c
 }
 
 // ---------------------------------------------------------------------------
+// Debug builds (compiled with CVF_DEBUG): device-side index checks in place
+// of a memory checker.  dcheck(ok, err, site) records the first failing
+// check of a launch in the lattice's error word as 0x100 + site and returns
+// false, and the caller skips the access instead of faulting; in release
+// builds it is the constant true and the checks compile away.
+// ---------------------------------------------------------------------------
+enum DebugSite : unsigned int {
+  kSiteStage = 1,       // staged tile: source row / word and shared-memory slot
+  kSiteTma = 2,         // TMA box: 16-byte aligned x and the box inside the lattice
+  kSiteTileRead = 3,    // colour phases: shared-memory reads of the staged tile
+  kSiteTileWrite = 4,   // colour phases: shared-memory and global writes
+  kSitePass3 = 5,       // cubic passes: the cell group and its neighbour words
+  kSiteResident2 = 6,   // square lattice resident in one cluster
+  kSiteResident3 = 7,   // cubic lattice resident in one cluster
+  kSiteBatchItem = 8,   // batched sweep: decoded replica and tile of a work item
+  kSiteLayer = 9,       // layered square-lattice passes
+};
+
+#ifdef CVF_DEBUG
+__device__ __forceinline__ bool dcheck(bool ok, unsigned int* err, unsigned int site) {
+  if (!ok && err) atomicCAS(err, 0u, 0x100u + site);
+  return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool dcheck(bool, unsigned int*, unsigned int) {
+  return true;
+}
+#endif
+
+// ---------------------------------------------------------------------------
 // Bounded waits.  A thread that waits for another block (the persistent
 // batched sweep: a tile of step s waits until its replica finished step
 // s - 1) polls with acquire loads and a short sleep, and gives up after a

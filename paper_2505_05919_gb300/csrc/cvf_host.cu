@@ -22,6 +22,15 @@ int set_error(int code, const char* fmt, ...) {
 
 void clear_error() { g_last_error.clear(); }
 
+int status_error(int status) {
+  if (status == 0) return CVF_OK;
+  if (status >= 0x100)
+    return set_error(CVF_EBOUNDS, "a device index check of a debug build failed (site %d)",
+                     status - 0x100);
+  return set_error(CVF_ETIMEOUT, "a bounded wait in the sweep kernel gave up (status %d)",
+                   status);
+}
+
 int check_params(const cvf_params* p) {
   if (!p) return set_error(CVF_EINVAL, "params is NULL");
   if (p->L < 2 || (p->L & 1) || p->L > 65534)
@@ -135,6 +144,14 @@ int cvf_threshold_table(const cvf_params* p, uint64_t out[42]) {
   if (rc) return rc;
   cvf::threshold_table(p, out);
   return CVF_OK;
+}
+
+int cvf_debug_checks(void) {
+#ifdef CVF_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 }  // extern "C"

@@ -38,6 +38,11 @@ void lattice_shells(double cutoff, std::vector<int64_t>* d2,
 
 int sm_count();
 
+// The status word of a lattice's observables as a call result: 0 CVF_OK,
+// 1 CVF_ETIMEOUT (a bounded device wait gave up), 0x100 + site CVF_EBOUNDS
+// (a debug build's index check failed at `site`).
+int status_error(int status);
+
 // An NVTX range over one host entry point, named after it, so that a
 // profiler that records NVTX (ncu --nvtx, a timeline tracer) can attribute the
 // launches to the API call that made them; without one attached the push and

@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
   v.s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
   v.s_hi = (uint32_t)((unsigned long long)step >> 32);
   v.keys.K = &A.keys;
+  v.err = &ctl->error;
   const CUtensorMap* tmap = (step & 1) ? &tm1 : &tm0;  // map of the source buffer
   const int tiles_x = (v.Lh + kTileWords - 1) / kTileWords;
   const int ntiles = tiles_x * ((v.L + kTileRows - 1) / kTileRows);
@@ -262,8 +263,17 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     if (tma) {
       if (threadIdx.x == 0) {
         fence_proxy_async_shared();
-        mbar_arrive_expect_tx(&s_bar, (uint32_t)sizeof(S.in));
-        tma_load_2d(&S.in[0][0], tmap, gm.p0 - 4, gm.y0 - 2, &s_bar);
+        // the box's x (words) must be a multiple of 4 (16 bytes) and the box
+        // inside the lattice; a debug build that finds otherwise arrives
+        // without a copy, so the wait still ends
+        if (dcheck(((gm.p0 - 4) & 3) == 0 && gm.p0 - 4 >= 0 && gm.y0 - 2 >= 0 &&
+                       gm.p0 - 4 + kTileWords + 8 <= v.Lh && gm.y0 - 2 + kTileRows + 4 <= v.L,
+                   v.err, kSiteTma)) {
+          mbar_arrive_expect_tx(&s_bar, (uint32_t)sizeof(S.in));
+          tma_load_2d(&S.in[0][0], tmap, gm.p0 - 4, gm.y0 - 2, &s_bar);
+        } else {
+          mbar_arrive_expect_tx(&s_bar, 0u);
+        }
       }
     } else {
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -274,7 +284,10 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
         for (int jj = lane; jj < gm.tw + 2; jj += 32) {
           int p = gm.p0 + jj - 1;
           p = (p < 0) ? p + v.Lh : (p >= v.Lh ? p - v.Lh : p);
-          cp_async4(&S.in[rr][jj + kInColOff], row + p);
+          if (dcheck(y >= 0 && y < v.L && p >= 0 && p < v.Lh && rr < kTileRows + 4 &&
+                         jj + kInColOff < kTileWords + 8,
+                     v.err, kSiteStage))
+            cp_async4(&S.in[rr][jj + kInColOff], row + p);
         }
       }
       cp_async_commit();
@@ -476,6 +489,7 @@ __global__ void __launch_bounds__(kThreads) k_layer(LatticeArgs A, int launch) {
   for (uint32_t wi = (blockIdx.x - first_block) * kThreads + threadIdx.x; wi < nwords;
        wi += (gridDim.x - first_block) * kThreads) {
     const uint32_t y = wi / Lh, p = wi - y * Lh;
+    if (!dcheck(y < L && p < Lh, &ctl->error, kSiteLayer)) continue;
     const uint32_t own = in[wi];
     uint32_t out = own;
     uint32_t pk = 0;
@@ -967,10 +981,7 @@ int cvf_observables(cvf_handle* h, cvf_obs* out) {
                                  cudaMemcpyDeviceToHost, h->stream));
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
   std::memcpy(out, h->host_pinned, sizeof(cvf_obs));
-  if (out->status)
-    return set_error(CVF_ETIMEOUT, "a bounded wait in the sweep kernel gave up (status %d)",
-                     out->status);
-  return CVF_OK;
+  return status_error(out->status);
 }
 
 int cvf_drain_series(cvf_handle* h, cvf_obs* host, int64_t cap, int64_t* n) {

@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kResBlock) k_resident2(LatticeArgs A, long lon
       uint32_t pk = 0;
       for (int i = threadIdx.x; i < R * Lh; i += kResThreads) {
         const int r = i / Lh, p = i - r * Lh;
+        if (!dcheck(r >= 0 && r < R && p >= 0 && p < Lh, &ctl->error, kSiteResident2)) continue;
         const int y = y0 + r;
         const int hi = (y & 1) ^ colour;  // the cell of this colour in word (y, p)
         const uint32_t own = lat[i];

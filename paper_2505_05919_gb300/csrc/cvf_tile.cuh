@@ -212,6 +212,7 @@ struct StepView {
   uint32_t q;
   uint32_t s_lo, s_hi;  // step index
   KEYS keys;
+  unsigned int* err;    // error word for the debug build's index checks (or null)
 };
 
 // Tile geometry shared by the pieces below.
@@ -239,7 +240,9 @@ __device__ __forceinline__ void stage_plain(const StepView<KEYS>& v, const TileG
     for (int jj = lane; jj < g.tw + 2; jj += 32) {
       int p = g.p0 + jj - 1;
       p = (p < 0) ? p + Lh : (p >= Lh ? p - Lh : p);
-      S.in[rr][jj + kInColOff] = CG ? __ldcg(row + p) : row[p];
+      if (dcheck(y >= 0 && y < L && p >= 0 && p < Lh && rr < TR + 4 && jj + kInColOff < TW + 8,
+                 v.err, kSiteStage))
+        S.in[rr][jj + kInColOff] = CG ? __ldcg(row + p) : row[p];
     }
   }
 }
@@ -272,6 +275,9 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
     // two cells per iteration give the scheduler two independent arm chains
 #pragma unroll 2
     for (int j = lcol; j < tw; j += kLanes) {
+      if (!dcheck(r + 1 >= 0 && r + 3 < TR + 4 && j + C + 1 < TW + 8 && j + 1 < TW + 2, v.err,
+                  kSiteTileRead))
+        continue;
       const int xg = 2 * (p0 + j) + hi;
       uint32_t pk_row = 0;
       const uint32_t out = update_in_word<RNG_WORDS, CMP64>(
@@ -298,6 +304,10 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
     uint32_t not_counted = 0;  // the ring cells belong to the neighbouring tiles
     // the unused side of the ring word is clamped into the staged columns
     const int jm = max(j, 0), jp = min(j + 2, tw + 1);
+    if (!dcheck(r + 1 >= 0 && r + 3 < TR + 4 && j + C >= 0 && j + C < TW + 8 &&
+                    jp + kInColOff < TW + 8 && j + 1 >= 0 && j + 1 < TW + 2,
+                v.err, kSiteTileRead))
+      continue;
     S.mid[r + 1][j + 1] = update_in_word<RNG_WORDS, CMP64>(
         S.in[r + 2][j + C], S.in[r + 2][jm + kInColOff], S.in[r + 2][jp + kInColOff],
         S.in[r + 1][j + C], S.in[r + 3][j + C], hi, (uint32_t)((long long)yg * L + xg), v.s_lo,
@@ -326,6 +336,9 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
     uint32_t* drow = v.dst + (size_t)y * Lh + p0;
 #pragma unroll 2
     for (int j = lcol; j < tw; j += kLanes) {
+      if (!dcheck(r + 2 < TR + 2 && j + 2 < TW + 2 && y >= 0 && y < L && p0 + j < Lh, v.err,
+                  kSiteTileWrite))
+        continue;
       const int xg = 2 * (p0 + j) + hi;
       drow[j] = update_in_word<RNG_WORDS, CMP64>(
           S.mid[r + 1][j + 1], S.mid[r + 1][j], S.mid[r + 1][j + 2], S.mid[r][j + 1],

@@ -1,0 +1,82 @@
+"""Parity cases run against the debug build of the library (libcvf_debug.so,
+compiled with CVF_DEBUG: every kernel checks its shared- and global-memory
+indices and the TMA alignment rule, records the first failing site in the
+lattice's status word and skips the access).  Run as a separate process by
+tests/test_gpu_debug_build.py, so that this process loads the debug library
+instead of the release one.  Every case must match the oracle bit for bit
+and every observables call must return CVF_OK (a failed check would make it
+raise CvfError with CVF_EBOUNDS and the site).
+"""
+import os
+import sys
+from dataclasses import asdict
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import paper_2505_05919_gb300.build as _build  # noqa: E402
+
+_build.LIB = _build.build(debug=True)
+
+import oracle  # noqa: E402
+from paper_2505_05919_gb300 import Batch, Lattice, Lattice3, params_from_dict  # noqa: E402
+
+
+def square(L, steps, tiles=-1, **kw):
+    op = oracle.physical_params(300.0, 0.1, L=L, seed=L + 7, **kw)
+    ref = oracle.Oracle(op)
+    ref.run(steps)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        if tiles >= 0:
+            lat.set_tiles(tiles)
+        lat.sweep(steps)
+        assert np.array_equal(lat.state(), ref.state()), ("square", L, tiles, kw)
+        o = lat.observables()                      # raises on a failed check
+    assert o["n_hb_raw"] == ref.observables()["n_hb_raw"]
+
+
+def cubic(L, steps, resident=-1):
+    op = oracle.physical_params3(300.0, 0.1, L=L, seed=L + 3, dv_max_frac=0.05)
+    ref = oracle.Oracle3(op)
+    ref.run(steps)
+    with Lattice3(params_from_dict(asdict(op))) as lat:
+        if resident >= 0:
+            lat.set_resident(resident)
+        lat.sweep(steps)
+        assert np.array_equal(lat.state(), ref.state()), ("cubic", L, resident)
+        lat.observables()
+
+
+def batch(sizes, steps):
+    ops = [oracle.physical_params(300.0, 0.1, L=L, seed=100 + L) for L in sizes]
+    with Batch([params_from_dict(asdict(op)) for op in ops]) as b:
+        b.sweep([steps] * len(ops))
+        for i, op in enumerate(ops):
+            ref = oracle.Oracle(op)
+            ref.run(steps)
+            assert np.array_equal(b.state(i), ref.state()), ("batch", sizes[i])
+            b.observables(i)
+
+
+def main():
+    from paper_2505_05919_gb300 import _capi
+    assert _capi.lib_path() == _build.DEBUG_LIB and _capi.cvf_debug_checks()
+    for L in (2, 16, 64):
+        square(L, 9)                               # resident cluster form where it applies
+    square(130, 6)                                 # odd number of words per row
+    for t in (0, 1, 2):
+        square(258, 5, tiles=t)                    # ragged tiles, periodic staging
+    square(1024, 4, tiles=0)                       # TMA staging
+    square(96, 7, rng_words=2)
+    square(64, 8, schedule=oracle.SCHED_LAYERED)
+    square(34, 8, schedule=oracle.SCHED_LAYERED)
+    for L, res in ((8, 0), (9, 0), (12, 0), (16, 1), (24, 1), (16, 0), (130, 0)):
+        cubic(L, 5, res)
+    batch([16, 34, 64, 130, 2], 12)
+    print("debug build: all cases match, no index check failed")
+
+
+if __name__ == "__main__":
+    main()

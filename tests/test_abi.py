@@ -139,3 +139,7 @@ def test_batch_tile_configs_and_cells_per_thread(lib):
     assert cfgs[0] == (64, 64)
     assert [cells_per_thread(c) for c in range(len(cfgs))] == [2 * r * w // 256 for r, w in cfgs]
     assert cells_per_thread(0) == 32 and min(cells_per_thread(c) for c in range(len(cfgs))) >= 1
+
+
+def test_release_build_has_no_debug_checks(lib):
+    assert not _capi.cvf_debug_checks()
