@@ -47,9 +47,11 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=1000, help="MC steps per benchmark step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-sweeps", type=int, default=10)
-    ap.add_argument("--mode", default="full", choices=["full", "kernel", "kernel3"],
-                    help="kernel / kernel3: one square / cubic lattice, warm-up then timed "
-                         "sweeps only (profiling cases)")
+    ap.add_argument("--mode", default="full", choices=["full", "kernel", "kernel3", "batch"],
+                    help="kernel / kernel3: one square / cubic lattice; batch: the 256 "
+                         "replicas of the batched configuration in one persistent launch "
+                         "per call (tile shape from the autotuner); warm-up then timed sweeps "
+                         "only (profiling cases)")
     ap.add_argument("--L3", type=int, default=260,
                     help="cube side of the 3D measurement (260: the paper's largest lattice)")
     ap.add_argument("--cubic-sweeps", type=int, default=320,
@@ -310,6 +312,40 @@ def run_kernel3_mode(args):
     print(json.dumps({"mode": "kernel3", "L": args.L3, "sweeps": args.steps, "ms": ms,
                       "updates_per_ns": 6.0 * args.L3 ** 3 * args.steps / (ms * 1e6),
                       "n_hb_raw": o["n_hb_raw"], "n_coop": o["n_coop"]}))
+    return 0
+
+
+def run_batch_mode(args):
+    """Profiling case of the batched sweep: the 256 replicas of the batched
+    configuration (L from {32..512}, T x P grid), tile configuration from the
+    autotuner, `warmup` MC steps each in one call, then one call of `steps`
+    MC steps each (one persistent launch) timed with CUDA events."""
+    import torch
+    from paper_2505_05919_gb300 import Batch, params, workloads, _capi, build as libbuild
+    from paper_2505_05919_gb300.autotune import autotune
+    libbuild.build()
+    _capi.load()
+    reps = workloads.c4(sweeps=args.steps)
+    ps = [params(r["T"], r["P"], L=r["L"], q=r["q"], seed=r["seed"]) for r in reps]
+    stream = torch.cuda.Stream()
+    best, _ = autotune(ps, probe_sweeps=20, stream=stream)
+    with Batch(ps, stream=stream) as b:
+        b.set_tiles(best)
+        b.sweep([args.warmup] * len(ps))
+        b.sync()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        b.sweep([args.steps] * len(ps))
+        ev1.record(stream)
+        ev1.synchronize()
+        b.sync()
+        ms = ev0.elapsed_time(ev1)
+    cells = sum(r["L"] * r["L"] for r in reps)
+    print(json.dumps({"mode": "batch", "replicas": len(ps), "sweeps": args.steps, "ms": ms,
+                      "tile_config": best,
+                      "replica_sweeps_per_s": len(ps) * args.steps / (ms / 1e3),
+                      "updates_per_ns": 4.0 * cells * args.steps / (ms * 1e6)}))
     return 0
 
 
@@ -583,6 +619,8 @@ def main():
         return run_kernel_mode(args)
     if args.mode == "kernel3":
         return run_kernel3_mode(args)
+    if args.mode == "batch":
+        return run_batch_mode(args)
     import numpy as np
     import torch
     from paper_2505_05919_gb300 import dist

@@ -38,7 +38,6 @@ struct ReplicaDesc {
   cvf_obs* ring;
   long long ring_cap;
   RoundKeys keys;
-  uint32_t seed_lo, seed_hi;
   int32_t L;
   uint32_t q;
 };
@@ -86,6 +85,7 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
   __shared__ long long s_rel;
   __shared__ uint32_t s_q;
   __shared__ uint32_t s_hist4[4];
+  __shared__ RoundKeys s_keys;  // the current replica's round keys (broadcast reads)
   if (threadIdx.x == 0) s_q = 0;
   if (threadIdx.x < 4) s_hist4[threadIdx.x] = 0;
   for (;;) {
@@ -138,6 +138,10 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     const long long step = vc->sweep;
     const int g = vc->next_g;
     fill_rows2(Tb, R.table24, g);
+    if (threadIdx.x < 10) {
+      s_keys.k0[threadIdx.x] = R.keys.k0[threadIdx.x];
+      s_keys.k1[threadIdx.x] = R.keys.k1[threadIdx.x];
+    }
     if (s_q != R.q) {  // block-uniform
       fill_prop2(Tb, R.q);
       __syncthreads();
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     __syncthreads();
     const int L = R.L, Lh = L >> 1;
     const long long N = (long long)L * L;
-    StepView<KeysSeed> v;
+    StepView<KeysRound> v;
     v.src = reinterpret_cast<const uint32_t*>(R.state + (size_t)(step & 1) * N);
     v.dst = reinterpret_cast<uint32_t*>(R.state + (size_t)((step + 1) & 1) * N);
     v.L = L;
@@ -154,15 +158,14 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     v.q = R.q;
     v.s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
     v.s_hi = (uint32_t)((unsigned long long)step >> 32);
-    v.keys.k0 = R.seed_lo;
-    v.keys.k1 = R.seed_hi;
+    v.keys.K = &s_keys;
     v.err = &W->error;
     const int tiles_x = (Lh + TW - 1) / TW;
     const int ntiles = tiles_x * ((L + TR - 1) / TR);
     const int t = s_tile;
     TileCounts cnt{0, 0, 0};
     const bool rec = step_recorded(vc->record_every, step);
-    sweep_tile<RNG_WORDS, CMP64, TR, TW, kThreads, KeysSeed, true>(
+    sweep_tile<RNG_WORDS, CMP64, TR, TW, kThreads, KeysRound, true>(
         v, (t / tiles_x) * TR, (t % tiles_x) * TW, S, Tb, cnt, rec ? s_hist4 : nullptr,
         ctl->acc_hist);
     uint32_t dhb = (uint32_t)cnt.dhb(), dc = (uint32_t)cnt.dc(), nacc = cnt.nacc;
@@ -313,8 +316,6 @@ int upload_descs(cvf_batch* b) {
     d.ring = r.ring;
     d.ring_cap = kReplicaRingCap;
     d.keys = make_round_keys(r.p.seed);
-    d.seed_lo = (uint32_t)(r.p.seed & 0xFFFFFFFFu);
-    d.seed_hi = (uint32_t)(r.p.seed >> 32);
     d.L = r.p.L;
     d.q = (uint32_t)r.p.q;
   }

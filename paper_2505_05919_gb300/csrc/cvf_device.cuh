@@ -68,27 +68,6 @@ __device__ __forceinline__ Words4 philox(uint32_t x0, uint32_t x1, uint32_t x2,
   return Words4{x0, x1, x2, x3};
 }
 
-// Same, with the round keys derived from the seed in registers (used where
-// every thread may serve a different replica).
-__device__ __forceinline__ Words4 philox_seed(uint32_t x0, uint32_t x1,
-                                              uint32_t x2, uint32_t x3,
-                                              uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint64_t m0 = (uint64_t)x0 * kPhiloxMul0;
-    const uint64_t m1 = (uint64_t)x2 * kPhiloxMul1;
-    const uint32_t y0 = (uint32_t)(m1 >> 32) ^ x1 ^ k0;
-    const uint32_t y2 = (uint32_t)(m0 >> 32) ^ x3 ^ k1;
-    x1 = (uint32_t)m1;
-    x3 = (uint32_t)m0;
-    x0 = y0;
-    x2 = y2;
-    k0 += kWeyl0;
-    k1 += kWeyl1;
-  }
-  return Words4{x0, x1, x2, x3};
-}
-
 // Cell word of the square lattice: sigma of arm a in bits [4a, 4a+3) (one
 // nibble per arm, bits 4a+3 zero).
 __device__ __forceinline__ uint32_t arm_of(uint32_t w, int a) {

@@ -13,11 +13,11 @@ constexpr int kThreads = 256;
 // tiles of the single-lattice sweep: 64 rows x 64 words (128 cells)
 constexpr int kTileRows = 64;
 constexpr int kTileWords = 64;
-// register budgets: five 256-thread blocks per SM for the single-lattice
-// sweep (the most its 38 KB of shared memory allows), four for the batched
-// kernel
+// register budgets: five 256-thread blocks per SM (48 registers a thread;
+// the most the 38 KB of shared memory of a block allows) for the
+// single-lattice sweep and for the batched kernel
 constexpr int kSweepBlocksPerSM = 5;
-constexpr int kBatchBlocksPerSM = 4;
+constexpr int kBatchBlocksPerSM = 5;
 
 struct LatticeArgs {
   uint16_t* state;                   // state pair: 2 * L*L packed cell words

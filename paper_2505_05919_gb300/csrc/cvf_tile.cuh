@@ -99,43 +99,18 @@ __device__ __forceinline__ uint32_t count_word4(uint32_t w) {
   return c;
 }
 
-// Philox key material of the lattice being swept: the precomputed round keys
-// (single lattice) or the seed words, advanced in registers (batch, where
-// consecutive tiles may belong to different replicas).
+// Philox key material of the lattice being swept: its precomputed round keys
+// (a kernel parameter for the single lattice, read from the constant bank; a
+// shared-memory copy of the current replica's keys in the batched kernel, read
+// by broadcast loads).
 struct KeysRound {
   const RoundKeys* K;
-};
-struct KeysSeed {
-  uint32_t k0, k1;
 };
 
 template <int RNG_WORDS>
 __device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi, const KeysRound& k,
                                       uint32_t q, uint32_t acc[4], uint32_t kk[4]) {
   cell_draws<RNG_WORDS>(c, s_lo, s_hi, *k.K, q, acc, kk);
-}
-
-template <int RNG_WORDS>
-__device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi, const KeysSeed& k,
-                                      uint32_t q, uint32_t acc[4], uint32_t kk[4]) {
-  const Words4 u = philox_seed(c, s_lo, s_hi, kTagAccept, k.k0, k.k1);
-  const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
-  if (RNG_WORDS == 1) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const uint64_t prod = (uint64_t)uw[a] * (uint64_t)(q - 1u);
-      kk[a] = (uint32_t)(prod >> 32);
-      acc[a] = (uint32_t)prod;
-    }
-  } else {
-    const Words4 p = philox_seed(c, s_lo, s_hi, kTagPropose, k.k0, k.k1);
-    const uint32_t pw[4] = {p.x, p.y, p.z, p.w};
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      acc[a] = uw[a];
-      kk[a] = __umulhi(pw[a], q - 1u);
-    }
-  }
 }
 
 // Update the cell in half `hi` of word `own` (its four arms in order, each
