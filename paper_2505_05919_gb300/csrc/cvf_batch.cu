@@ -73,6 +73,45 @@ __global__ void k_batch_reset(BatchWork* W, unsigned int* progress, int n_replic
   }
 }
 
+// Takes the next work item from the launch's counter and decodes it (thread
+// 0 only): returns false when the launch is out of items or has failed.
+__device__ __forceinline__ bool take_item(BatchWork* W, const int32_t* __restrict__ order,
+                                          const long long* __restrict__ tile_prefix, int* rep,
+                                          int* tile, long long* rel) {
+  const unsigned long long i = atomicAdd(&W->next, 1ull);
+  if ((long long)i >= W->total_items || *(volatile unsigned int*)&W->error) return false;
+  // segment, relative step, replica, tile
+  int k = 0;
+  while (k + 1 < W->nseg && (long long)i >= W->seg_base[k + 1]) ++k;
+  const int A = W->seg_active[k];
+  const long long T = tile_prefix[A];
+  const long long r = (long long)i - W->seg_base[k];
+  const long long s = W->seg_s0[k] + r / T;
+  const long long j = r % T;
+  int lo = 0, hi = A;  // largest ri with tile_prefix[ri] <= j
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tile_prefix[mid] <= j) lo = mid;
+    else hi = mid;
+  }
+  if (!dcheck(k < W->nseg && A <= W->n_active && lo >= 0 && lo < A && j >= 0 && j < T &&
+                  j < tile_prefix[lo + 1] && s >= 0,
+              &W->error, kSiteBatchItem))
+    return false;
+  *rep = order[lo];
+  *tile = (int)(j - tile_prefix[lo]);
+  *rel = s;
+  return true;
+}
+
+// The persistent batched sweep.  A block works through items (step s,
+// replica r, tile t) in counter order.  After an item's first colour, when
+// the S.in buffer is free, it takes its next item; if that item's replica
+// has already finished the steps before it, the next tile's rows are copied
+// in (16-byte cp.async through L2, lattices with L a multiple of 8) while the
+// second colour runs.  Otherwise the item waits (bounded) and stages its tile
+// when it comes up.  A block only waits for items taken before its own, so
+// the oldest unfinished item can always run.
 template <int RNG_WORDS, bool CMP64, int TR, int TW>
 __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(const ReplicaDesc* __restrict__ reps,
                                                              BatchWork* W,
@@ -81,58 +120,45 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
                                                              unsigned int* progress) {
   __shared__ TileSmem<TR, TW> S;
   __shared__ Tables2 Tb;
-  __shared__ int s_rep, s_tile, s_abort, s_last;
+  __shared__ int s_rep, s_tile, s_valid, s_staged, s_abort, s_last;
   __shared__ long long s_rel;
+  __shared__ int n_rep, n_tile, n_valid, n_ready;
+  __shared__ long long n_rel;
   __shared__ uint32_t s_q;
   __shared__ uint32_t s_hist4[4];
   __shared__ RoundKeys s_keys;  // the current replica's round keys (broadcast reads)
-  if (threadIdx.x == 0) s_q = 0;
+  if (threadIdx.x == 0) {
+    s_q = 0;
+    int r = 0, t = 0;
+    long long e = 0;
+    s_valid = take_item(W, order, tile_prefix, &r, &t, &e) ? 1 : 0;
+    s_rep = r;
+    s_tile = t;
+    s_rel = e;
+    s_staged = 0;
+  }
   if (threadIdx.x < 4) s_hist4[threadIdx.x] = 0;
   for (;;) {
     __syncthreads();
+    if (!s_valid) break;
     if (threadIdx.x == 0) {
       int abort = 0;
-      const unsigned long long i = atomicAdd(&W->next, 1ull);
-      if ((long long)i >= W->total_items || *(volatile unsigned int*)&W->error) {
-        abort = 1;
-      } else {
-        // decode the item: segment, relative step, replica, tile
-        int k = 0;
-        while (k + 1 < W->nseg && (long long)i >= W->seg_base[k + 1]) ++k;
-        const int A = W->seg_active[k];
-        const long long T = tile_prefix[A];
-        const long long rel = (long long)i - W->seg_base[k];
-        const long long s = W->seg_s0[k] + rel / T;
-        const long long j = rel % T;
-        int lo = 0, hi = A;  // largest ri with tile_prefix[ri] <= j
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (tile_prefix[mid] <= j) lo = mid;
-          else hi = mid;
-        }
-        const int rep = order[lo];
-        s_rep = rep;
-        s_tile = (int)(j - tile_prefix[lo]);
-        s_rel = s;
-        if (!dcheck(k < W->nseg && A <= W->n_active && lo >= 0 && lo < A && j >= 0 && j < T &&
-                        j < tile_prefix[lo + 1] && s >= 0,
-                    &W->error, kSiteBatchItem)) {
+      if (!s_staged) {
+        // wait until the replica has completed the item's earlier steps
+        const WaitResult wr = wait_flag_geq(&progress[s_rep], (unsigned int)s_rel, &W->error,
+                                            kWaitPollLimit);
+        if (wr != kWaitDone) {
+          if (wr == kWaitGaveUp) atomicExch(&W->error, 1u);
           abort = 1;
-        } else {
-          // wait until the replica has completed s steps of this launch
-          const WaitResult wr =
-              wait_flag_geq(&progress[rep], (unsigned int)s, &W->error, kWaitPollLimit);
-          if (wr != kWaitDone) {
-            if (wr == kWaitGaveUp) atomicExch(&W->error, 1u);
-            abort = 1;
-          }
         }
       }
       s_abort = abort;
     }
     __syncthreads();
     if (s_abort) break;
-    const ReplicaDesc& R = reps[s_rep];
+    const int rep = s_rep, t = s_tile, staged = s_staged;
+    const long long rel = s_rel;
+    const ReplicaDesc& R = reps[rep];
     Ctrl* ctl = R.ctrl;
     volatile Ctrl* vc = ctl;
     const long long step = vc->sweep;
@@ -147,7 +173,6 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
       __syncthreads();
       if (threadIdx.x == 0) s_q = R.q;
     }
-    __syncthreads();
     const int L = R.L, Lh = L >> 1;
     const long long N = (long long)L * L;
     StepView<KeysRound> v;
@@ -162,12 +187,46 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     v.err = &W->error;
     const int tiles_x = (Lh + TW - 1) / TW;
     const int ntiles = tiles_x * ((L + TR - 1) / TR);
-    const int t = s_tile;
+    const TileGeom gm = tile_geom<TR, TW>(L, Lh, (t / tiles_x) * TR, (t % tiles_x) * TW);
+    if (staged)
+      cp_async_wait_all();
+    else
+      stage_plain<TR, TW, kThreads, true>(v, gm, S);
+    __syncthreads();
     TileCounts cnt{0, 0, 0};
     const bool rec = step_recorded(vc->record_every, step);
-    sweep_tile<RNG_WORDS, CMP64, TR, TW, kThreads, KeysRound, true>(
-        v, (t / tiles_x) * TR, (t % tiles_x) * TW, S, Tb, cnt, rec ? s_hist4 : nullptr,
-        ctl->acc_hist);
+    colour0<RNG_WORDS, CMP64, TR, TW, kThreads>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
+    // S.in is free: take the next item and, when it can start, copy its tile
+    if (threadIdx.x == 0) {
+      int r = 0, tt = 0;
+      long long e = 0;
+      n_valid = take_item(W, order, tile_prefix, &r, &tt, &e) ? 1 : 0;
+      n_rep = r;
+      n_tile = tt;
+      n_rel = e;
+      n_ready = (n_valid && reps[r].L % 8 == 0 && ld_acquire(&progress[r]) >= (unsigned int)e)
+                    ? 1 : 0;
+    }
+    __syncthreads();
+    if (n_ready) {
+      const ReplicaDesc& Rn = reps[n_rep];
+      const int Ln = Rn.L, Lhn = Ln >> 1;
+      const long long Nn = (long long)Ln * Ln;
+      const long long step_n = ((volatile Ctrl*)Rn.ctrl)->sweep;
+      StepView<KeysRound> vn;
+      vn.src = reinterpret_cast<const uint32_t*>(Rn.state + (size_t)(step_n & 1) * Nn);
+      vn.L = Ln;
+      vn.Lh = Lhn;
+      vn.err = &W->error;
+      const int tx = (Lhn + TW - 1) / TW;
+      const TileGeom gn = tile_geom<TR, TW>(Ln, Lhn, (n_tile / tx) * TR, (n_tile % tx) * TW);
+      stage_async16<TR, TW, kThreads>(vn, gn, S);
+    }
+    colour1<RNG_WORDS, CMP64, TR, TW, kThreads>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
+    if (rec) {  // block-uniform: only on recorded steps
+      __syncthreads();
+      hist_flush(s_hist4, ctl->acc_hist);
+    }
     uint32_t dhb = (uint32_t)cnt.dhb(), dc = (uint32_t)cnt.dc(), nacc = cnt.nacc;
     block_sum3<kThreads>(dhb, dc, nacc);  // two's complement sums
     if (threadIdx.x == 0) {
@@ -181,10 +240,17 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
         __threadfence();
         finalize_step<true>(*R.vol, ctl, R.ring, R.ring_cap, R.keys);
         __threadfence();
-        st_release(&progress[s_rep], (unsigned int)(s_rel + 1));
+        st_release(&progress[rep], (unsigned int)(rel + 1));
       }
+      // the next item becomes the current one
+      s_valid = n_valid;
+      s_rep = n_rep;
+      s_tile = n_tile;
+      s_rel = n_rel;
+      s_staged = n_ready;
     }
   }
+  cp_async_wait_all();  // no copy may still be in flight when the block exits
 }
 
 }  // namespace cvf

@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "cvf_device.cuh"
+#include "cvf_tma.cuh"
 
 namespace cvf {
 
@@ -220,6 +221,30 @@ __device__ __forceinline__ void stage_plain(const StepView<KEYS>& v, const TileG
         S.in[rr][jj + kInColOff] = CG ? __ldcg(row + p) : row[p];
     }
   }
+}
+
+// Start the copy of the same rows y0-2 .. y0+th+1 in 16-byte chunks of
+// words p0-4 .. p0+tw+3 (columns 0 .. tw+7, so word p0-1 still lands in
+// column kInColOff), periodic in chunks, through L2 only.  Needs Lh and p0
+// multiples of 4 (every wrapped chunk then starts on a row's 16-byte
+// boundary); the caller waits (cp_async_wait_all) and synchronises.
+template <int TR, int TW, int NT, typename KEYS>
+__device__ __forceinline__ void stage_async16(const StepView<KEYS>& v, const TileGeom& g,
+                                              TileSmem<TR, TW>& S) {
+  const int L = v.L, Lh = v.Lh;
+  const int chunks = (g.tw + 8) >> 2, rows = g.th + 4;
+  for (int e = threadIdx.x; e < rows * chunks; e += NT) {
+    const int rr = e / chunks, k = e - rr * chunks;
+    int y = g.y0 + rr - 2;
+    y = (y < 0) ? y + L : (y >= L ? y - L : y);
+    int p = g.p0 - 4 + 4 * k;
+    p = (p < 0) ? p + Lh : (p >= Lh ? p - Lh : p);
+    if (dcheck(y >= 0 && y < L && p >= 0 && p + 4 <= Lh && (p & 3) == 0 && rr < TR + 4 &&
+                   4 * k + 4 <= TW + 8,
+               v.err, kSiteStage))
+      cp_async16_cg(&S.in[rr][4 * k], v.src + (size_t)y * Lh + p);
+  }
+  cp_async_commit();
 }
 
 // Colour 0: tile rows -1 .. th, words 0 .. tw-1 (the colour-0 cell of a word
