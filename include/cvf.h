@@ -277,9 +277,14 @@ int cvf_batch_observables(cvf_batch *b, int32_t replica, cvf_obs *out);
 int cvf_batch_get_state(cvf_batch *b, int32_t replica, uint16_t *host,
                         size_t n);
 
-/* Tile shape of the batched kernel: config c selects rows x words from a
- * fixed list (cvf_batch_tile_config); chosen by the autotuner. */
+/* Tile shape of the batched kernel: config c >= 0 selects rows x words from
+ * a fixed list (cvf_batch_tile_config; the autotuner times them all), -1
+ * (the default) chooses per call: the largest shape whose tiles over the
+ * replicas the call advances are at least as many as the kernel's
+ * co-resident blocks, else the smallest.  cvf_batch_get_tiles returns the
+ * setting and the shape the last call used (-1 before any call). */
 int cvf_batch_set_tiles(cvf_batch *b, int32_t config);
+int cvf_batch_get_tiles(cvf_batch *b, int32_t *config, int32_t *last_used);
 int cvf_batch_tile_config(int32_t config, int32_t *rows, int32_t *words);
 
 /* Waits for the stream and frees every replica and the batch. */

@@ -86,6 +86,7 @@ _SIGS = {
     "cvf_batch_observables": (ctypes.c_int, [_vp, ctypes.c_int32, _P(cvf_obs)]),
     "cvf_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int32, _P(ctypes.c_uint16), ctypes.c_size_t]),
     "cvf_batch_set_tiles": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "cvf_batch_get_tiles": (ctypes.c_int, [_vp, _P(ctypes.c_int32), _P(ctypes.c_int32)]),
     "cvf_batch_tile_config": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_int32)]),
     "cvf_batch_destroy": (ctypes.c_int, [_vp]),
     # cubic lattice (the paper's 3D model)
@@ -293,6 +294,13 @@ def cvf_batch_get_state(b: int, replica: int, host_ptr: int, n: int) -> None:
 
 def cvf_batch_set_tiles(b: int, config: int) -> None:
     _check(load().cvf_batch_set_tiles(b, config), "cvf_batch_set_tiles")
+
+
+def cvf_batch_get_tiles(b: int) -> tuple:
+    """(setting, shape the last call used): -1 = automatic / no call yet."""
+    c, u = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().cvf_batch_get_tiles(b, ctypes.byref(c), ctypes.byref(u)), "cvf_batch_get_tiles")
+    return c.value, u.value
 
 
 def cvf_batch_tile_config(config: int):

@@ -59,7 +59,14 @@ class Batch:
         _capi.cvf_batch_sync(self.b)
 
     def set_tiles(self, config: int) -> None:
+        """Tile configuration (index into tile_configs()), or -1 (the default)
+        to let each call choose the largest shape that still gives every
+        co-resident block a tile."""
         _capi.cvf_batch_set_tiles(self.b, config)
+
+    def tiles(self) -> tuple:
+        """(setting, configuration the last call used)."""
+        return _capi.cvf_batch_get_tiles(self.b)
 
     # results ---------------------------------------------------------------
     def observables(self, rid: int) -> dict:

@@ -291,7 +291,8 @@ struct cvf_batch {
   cudaStream_t cap_stream;
   std::vector<Replica> reps;
   int rng_words;       // shared by all replicas (-1 while empty)
-  int tile_cfg;
+  int tile_cfg;        // -1: chosen per call
+  int last_cfg;        // the shape the last call used
   ReplicaDesc* d_reps;
   int d_reps_cap;
   bool reps_dirty;
@@ -425,15 +426,44 @@ WorkLayout work_layout(int n_active, int n_reps) {
 
 // One launch over the work in b->d_work: reset + persistent kernel, captured
 // as a graph the first time for a given configuration and replica count.
-int launch(cvf_batch* b, int cfg, bool cmp64, int n_reps, int n_active) {
+// Co-resident blocks of the kernel for a tile shape (the launch's grid).
+int resident_grid(cvf_batch* b, int cfg, bool cmp64, int* grid) {
   const int c64 = cmp64 ? 1 : 0;
-  KernelFn fn = pick_kernel(b->rng_words, cmp64, cfg);
   if (b->grid[cfg][c64] == 0) {
     int per_sm = 0;
+    KernelFn fn = pick_kernel(b->rng_words, cmp64, cfg);
     CVF_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, kThreads, 0));
     if (per_sm < 1) return set_error(CVF_ECUDA, "batch kernel cannot be resident");
     b->grid[cfg][c64] = per_sm * sm_count();
   }
+  *grid = b->grid[cfg][c64];
+  return CVF_OK;
+}
+
+// The automatic tile shape of a call: the largest whose tiles over the
+// advanced replicas give every co-resident block a tile per step.
+int auto_tile_config(cvf_batch* b, const std::vector<int32_t>& act, bool cmp64, int* cfg) {
+  for (int c = 0; c < kNumTileConfigs; ++c) {
+    int grid = 0;
+    const int rc = resident_grid(b, c, cmp64, &grid);
+    if (rc) return rc;
+    long long tiles = 0;
+    for (int i : act) tiles += tiles_of(b->reps[i].p.L, c);
+    if (tiles >= grid) {
+      *cfg = c;
+      return CVF_OK;
+    }
+  }
+  *cfg = kNumTileConfigs - 1;
+  return CVF_OK;
+}
+
+int launch(cvf_batch* b, int cfg, bool cmp64, int n_reps, int n_active) {
+  const int c64 = cmp64 ? 1 : 0;
+  KernelFn fn = pick_kernel(b->rng_words, cmp64, cfg);
+  int grid_unused = 0;
+  int grc = resident_grid(b, cfg, cmp64, &grid_unused);
+  if (grc) return grc;
   (void)n_active;
   const WorkLayout wl = work_layout(n_reps, n_reps);
   char* base = reinterpret_cast<char*>(b->d_work);
@@ -525,7 +555,8 @@ int cvf_batch_create(const cvf_params* params, int32_t n, void* stream, cvf_batc
   if (!b) return set_error(CVF_ENOMEM, "host allocation failed");
   b->stream = reinterpret_cast<cudaStream_t>(stream);
   b->rng_words = -1;
-  b->tile_cfg = 1;
+  b->tile_cfg = -1;
+  b->last_cfg = -1;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_obs, sizeof(cvf_obs));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_hist, sizeof(unsigned long long) * 9);
@@ -650,9 +681,17 @@ int cvf_batch_size(cvf_batch* b, int32_t* n_slots, int32_t* n_live) {
 
 int cvf_batch_set_tiles(cvf_batch* b, int32_t config) {
   if (!b) return set_error(CVF_EINVAL, "batch is NULL");
-  if (config < 0 || config >= kNumTileConfigs)
-    return set_error(CVF_EINVAL, "tile config %d (0..%d)", config, kNumTileConfigs - 1);
+  if (config < -1 || config >= kNumTileConfigs)
+    return set_error(CVF_EINVAL, "tile config %d (-1 automatic, 0..%d)", config,
+                     kNumTileConfigs - 1);
   b->tile_cfg = config;
+  return CVF_OK;
+}
+
+int cvf_batch_get_tiles(cvf_batch* b, int32_t* config, int32_t* last_used) {
+  if (!b || !config || !last_used) return set_error(CVF_EINVAL, "NULL argument");
+  *config = b->tile_cfg;
+  *last_used = b->last_cfg;
   return CVF_OK;
 }
 
@@ -682,7 +721,12 @@ int cvf_batch_sweep(cvf_batch* b, const int64_t* sweeps, int32_t n) {
   int rc = upload_descs(b);
   if (rc) return rc;
   std::stable_sort(act.begin(), act.end(), [&](int a, int c) { return sweeps[a] > sweeps[c]; });
-  const int cfg = b->tile_cfg;
+  int cfg = b->tile_cfg;
+  if (cfg < 0) {
+    rc = auto_tile_config(b, act, any_cmp64(b), &cfg);
+    if (rc) return rc;
+  }
+  b->last_cfg = cfg;
   const int na = (int)act.size();
   // array capacities follow the slot count, so a captured graph stays valid
   // whatever subset of replicas a call advances

@@ -139,3 +139,32 @@ def test_autotuner_picks_a_config():
     best, timings = autotune.autotune(ps, probe_sweeps=5)
     assert best in timings and len(timings) == len(tile_configs())
     assert all(t > 0 for t in timings.values())
+
+
+def test_batch_automatic_tile_choice():
+    """The default tile setting picks, per call, the largest shape whose tiles
+    over the advanced replicas still give every co-resident block a tile;
+    results equal those of any fixed shape."""
+    # 512 + 512 + 128 + 512 tiles of 64 x 64 words: more than the blocks
+    big = [_params(L, 300.0, 0.1, seed=40 + i) for i, L in enumerate((2048, 2048, 1024, 2048))]
+    small = [_params(L, 300.0, 0.1, seed=60 + i) for i, L in enumerate((32, 64, 16))]
+    with Batch(big) as b:
+        assert b.tiles() == (-1, -1)
+        b.sweep([4] * len(big))
+        assert b.tiles()[1] == 0                  # 64 x 64 words: enough tiles
+        s_auto = [b.state(i) for i in range(len(big))]
+    with Batch(big) as b:
+        b.set_tiles(1)
+        b.sweep([4] * len(big))
+        assert b.tiles() == (1, 1)
+        assert all(np.array_equal(b.state(i), s_auto[i]) for i in range(len(big)))
+    with Batch(small) as b:
+        b.sweep([4] * len(small))
+        assert b.tiles()[1] == len(tile_configs()) - 1   # few cells: the smallest shape
+        for i, p in enumerate(small):
+            s, _ = _solo(p, [4])
+            assert np.array_equal(b.state(i), s)
+        with pytest.raises(_capi.CvfError):
+            b.set_tiles(len(tile_configs()))
+        b.set_tiles(-1)
+        assert b.tiles()[0] == -1
