@@ -598,7 +598,9 @@ def measure_serving(args, rank):
         finally:
             srv.close()
 
-    common = dict(epoch_steps=1000, epoch_cell_steps=4e9, max_resident_cells=64 << 20)
+    # epochs of at most 400 steps (about 4e9 cell-steps when many large
+    # lattices are resident): new jobs are admitted every few milliseconds
+    common = dict(epoch_steps=400, epoch_cell_steps=4e9, max_resident_cells=64 << 20)
     over = run(workloads.c5(), args.serve_seconds, **common)
     over["offered_jobs_per_s"] = 200.0
     over["workload"] = ("Poisson 200 jobs/s (seed 5), L uniform {64,...,2048}, steps log-uniform "

@@ -162,6 +162,39 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     Ctrl* ctl = R.ctrl;
     volatile Ctrl* vc = ctl;
     const long long step = vc->sweep;
+    const int tiles_x = (R.L / 2 + TW - 1) / TW;
+    const int ntiles = tiles_x * ((R.L + TR - 1) / TR);
+    if (t == ntiles) {
+      // The volume item: the move of the replica's next step, decided while
+      // the step's tiles run (it does not depend on the bonds unless the gate
+      // would flip; then the step's commit decides it with the new bonds).
+      if (threadIdx.x == 0) {
+        VolumeResult r;
+        if (volume_decide(*R.vol, step + 1, vc->next_V, vc->next_u, vc->next_g, -1, R.keys, &r)) {
+          vc->ahead_V = r.V;
+          vc->ahead_u = r.u;
+          vc->ahead_g = r.g;
+          vc->ahead_acc = r.accepted;
+          vc->ahead_state = 1;
+        }
+        __threadfence();
+        const unsigned int prev = atomicAdd(&ctl->done, 1u);
+        if (prev == (unsigned int)ntiles) {
+          __threadfence();
+          finalize_step<true>(*R.vol, ctl, R.ring, R.ring_cap, R.keys);
+          __threadfence();
+          st_release(&progress[rep], (unsigned int)(rel + 1));
+        }
+        int rr = 0, tt = 0;
+        long long e = 0;
+        s_valid = take_item(W, order, tile_prefix, &rr, &tt, &e) ? 1 : 0;
+        s_rep = rr;
+        s_tile = tt;
+        s_rel = e;
+        s_staged = 0;
+      }
+      continue;
+    }
     const int g = vc->next_g;
     fill_rows2(Tb, R.table24, g);
     if (threadIdx.x < 10) {
@@ -185,8 +218,6 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     v.s_hi = (uint32_t)((unsigned long long)step >> 32);
     v.keys.K = &s_keys;
     v.err = &W->error;
-    const int tiles_x = (Lh + TW - 1) / TW;
-    const int ntiles = tiles_x * ((L + TR - 1) / TR);
     const TileGeom gm = tile_geom<TR, TW>(L, Lh, (t / tiles_x) * TR, (t % tiles_x) * TW);
     if (staged)
       cp_async_wait_all();
@@ -204,8 +235,10 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
       n_rep = r;
       n_tile = tt;
       n_rel = e;
-      n_ready = (n_valid && reps[r].L % 8 == 0 && ld_acquire(&progress[r]) >= (unsigned int)e)
-                    ? 1 : 0;
+      const int nl = reps[r].L;
+      const int ntn = ((nl / 2 + TW - 1) / TW) * ((nl + TR - 1) / TR);
+      n_ready = (n_valid && tt < ntn && nl % 8 == 0 &&
+                 ld_acquire(&progress[r]) >= (unsigned int)e) ? 1 : 0;
     }
     __syncthreads();
     if (n_ready) {
@@ -235,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
       atomicAdd(&ctl->acc_moves, (unsigned long long)nacc);
       __threadfence();
       const unsigned int prev = atomicAdd(&ctl->done, 1u);
-      s_last = (prev == (unsigned int)ntiles - 1u) ? 1 : 0;
+      s_last = (prev == (unsigned int)ntiles) ? 1 : 0;  // ntiles tiles + the volume item
       if (s_last) {
         __threadfence();
         finalize_step<true>(*R.vol, ctl, R.ring, R.ring_cap, R.keys);
@@ -735,7 +768,9 @@ int cvf_batch_sweep(cvf_batch* b, const int64_t* sweeps, int32_t n) {
   if (rc) return rc;
   // segments of constant active prefix, in increasing relative step
   std::vector<long long> prefix(na + 1, 0);
-  for (int k = 0; k < na; ++k) prefix[k + 1] = prefix[k] + tiles_of(b->reps[act[k]].p.L, cfg);
+  // a replica-step's items: its tiles and one volume item (the next step's move)
+  for (int k = 0; k < na; ++k)
+    prefix[k + 1] = prefix[k] + tiles_of(b->reps[act[k]].p.L, cfg) + 1;
   std::vector<long long> bounds;  // distinct step counts, ascending
   for (int k = na - 1; k >= 0; --k)
     if (bounds.empty() || bounds.back() != sweeps[act[k]]) bounds.push_back(sweeps[act[k]]);
