@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -476,6 +477,39 @@ def cpu_small_configs():
     return out
 
 
+def measure_order_parameter(rank, L=32, steps=8000, skip=4000, max_lag=2000):
+    """The order parameter M and its correlation time (Sec. III.A) at the
+    paper's dynamics size N = 32^3 = 32768: a cube (300 K, 0.1 MPa, random
+    init) recorded every MC step on the GPU (N_q' counted in the sweep),
+    drained, and analysed: M = max N_q' / (6 N) at a few steps of the
+    relaxation, and C_M(dt) and tau (first 1/e) over the second half."""
+    import torch
+    from paper_2505_05919_gb300 import Lattice3, analysis, dist, params3
+    stream = torch.cuda.Stream()
+    with Lattice3(params3(300.0, 0.1, L=L, seed=11 + dist.seed_offset(rank)), stream=stream) as lat:
+        lat.sweep(8, 1)
+        lat.drain()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lat.sweep(steps, 1)
+        ev1.record(stream)
+        ev1.synchronize()
+        recs, overflow = lat.drain(steps + 16)
+    m = analysis.order_series(recs, L ** 3, arms=6)
+    c = analysis.autocorrelation(m[skip:], max_lag)
+    tau = analysis.correlation_time(c)  # None in the line when C_M stays above 1/e
+    return {"L": L, "cells": L ** 3, "steps": steps, "recorded_every": 1,
+            "ms_per_mc_step": ev0.elapsed_time(ev1) / steps, "records": len(recs),
+            "overflow": bool(overflow),
+            "M_at_step": {str(t + 1): float(m[t]) for t in (0, 9, 99, 999, 3999, steps - 1)},
+            "M_mean_after_skip": float(m[skip:].mean()), "max_lag": max_lag,
+            "tau_steps": tau if math.isfinite(tau) else None, "skip": skip,
+            "workload": "CVF 3D cube L=%d q=6, 300 K, 0.1 MPa, random init (seed 11), "
+                        "observables and N_q' recorded every MC step" % L}
+
+
 def measure_small_configs(rank):
     """Configurations 1 and 2 as single lattices through the public API:
     C1 = L 64, 1000 MC steps (latency of one small lattice); C2 = L 1024,
@@ -745,6 +779,7 @@ def main():
            "h2d_bytes_per_step": 2 * L * L, "d2h_bytes_per_step": 2 * L * L + 96}
 
     cubic = measure_cubic(args, rank, world) if args.cubic_sweeps > 0 else None
+    order = measure_order_parameter(rank) if args.cubic_sweeps > 0 else None
     small = measure_small_configs(rank)
     batched = measure_batched(args, rank) if args.batch_sweeps > 0 else None
     serving = measure_serving(args, rank) if args.serve_seconds > 0 else None
@@ -786,6 +821,7 @@ def main():
             "batched": batched,
             "serving": serving,
             "cubic": cubic,
+            "order_parameter_3d": order,
             "small_configs": small,
             "clocks": clocks,
             "wall_s": t_wall,
