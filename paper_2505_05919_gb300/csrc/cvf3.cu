@@ -249,12 +249,15 @@ __global__ void __launch_bounds__(kThreads3, 4) k_pass3(Args3 A, int launch) {
   const int n_arms = s_n;
   if (launch == 0 && blockIdx.x == 0) {
     __shared__ VolumeArgs sV;  // the parameters at shared-memory latency
+    __shared__ double s_xch;
     stage_volume_args(&sV, A.vol);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 64) {  // warps 0 and 1: the move on two FP64 pipes
       VolumeResult r;
-      if (volume_decide(sV, ctl->sweep + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1,
-                        A.keys, &r)) {
+      const bool ok = volume_decide_pair<3>((int)(threadIdx.x >> 5), sV, ctl->sweep + 1,
+                                            ctl->next_V, ctl->next_u, ctl->next_g, -1, A.keys,
+                                            &r, &s_xch);
+      if (threadIdx.x == 0 && ok) {
         ctl->ahead_V = r.V;
         ctl->ahead_u = r.u;
         ctl->ahead_g = r.g;
@@ -536,7 +539,7 @@ __global__ void __launch_bounds__(kThreads3) k_count3(const uint32_t* __restrict
 // ---------------------------------------------------------------------------
 constexpr int kRes3Ctas = 8;
 constexpr int kRes3Threads = 256;
-constexpr int kRes3Block = kRes3Threads + 32;
+constexpr int kRes3Block = kRes3Threads + 64;  // + two volume warps
 constexpr int kRes3MaxSide = 64;
 // the automatic choice takes the resident form up to this side (measured:
 // 7.6 / 9.3 us per step at 16^3 / 24^3 against 14.6 / 15.3 with four
@@ -567,6 +570,7 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
   __shared__ uint32_t red[3][kRes3Threads / 32];
   __shared__ int s_next_g, s_plan;
   __shared__ VolumeArgs sV;
+  __shared__ double s_xch;
   Ctrl* ctl = A.ctrl;
   const uint32_t L = A.L, L2 = A.L2, G = A.G, R = L / kRes3Ctas, z0 = rank * R;
   const uint32_t q = A.q, qm1 = q - 1u;
@@ -603,9 +607,12 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
     const bool rec = step_recorded(every, step);
     if (!sweeper) {
       cl_arrive();  // the end of segment 0
-      if (rank == 0 && threadIdx.x == kRes3Threads) {
+      if (rank == 0) {  // the two volume warps: the move on two FP64 pipes
         VolumeResult r;
-        if (volume_decide(sV, step + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1, A.keys, &r)) {
+        const bool ok = volume_decide_pair<3>((int)((threadIdx.x - kRes3Threads) >> 5), sV,
+                                              step + 1, ctl->next_V, ctl->next_u, ctl->next_g,
+                                              -1, A.keys, &r, &s_xch);
+        if (threadIdx.x == kRes3Threads && ok) {
           ctl->ahead_V = r.V;
           ctl->ahead_u = r.u;
           ctl->ahead_g = r.g;

@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
   __shared__ uint32_t s_q;
   __shared__ uint32_t s_hist4[4];
   __shared__ RoundKeys s_keys;  // the current replica's round keys (broadcast reads)
+  __shared__ double s_xch;      // the volume item's two warps' exchange
   if (threadIdx.x == 0) {
     s_q = 0;
     int r = 0, t = 0;
@@ -168,15 +169,20 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
       // The volume item: the move of the replica's next step, decided while
       // the step's tiles run (it does not depend on the bonds unless the gate
       // would flip; then the step's commit decides it with the new bonds).
-      if (threadIdx.x == 0) {
+      if (threadIdx.x < 64) {  // warps 0 and 1: the move on two FP64 pipes
         VolumeResult r;
-        if (volume_decide(*R.vol, step + 1, vc->next_V, vc->next_u, vc->next_g, -1, R.keys, &r)) {
+        const bool ok = volume_decide_pair<3>((int)(threadIdx.x >> 5), *R.vol, step + 1,
+                                              vc->next_V, vc->next_u, vc->next_g, -1, R.keys, &r,
+                                              &s_xch);
+        if (threadIdx.x == 0 && ok) {
           vc->ahead_V = r.V;
           vc->ahead_u = r.u;
           vc->ahead_g = r.g;
           vc->ahead_acc = r.accepted;
           vc->ahead_state = 1;
         }
+      }
+      if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int prev = atomicAdd(&ctl->done, 1u);
         if (prev == (unsigned int)ntiles) {

@@ -158,8 +158,31 @@ __device__ __forceinline__ int lj_shells_inside(const VolumeArgs& V, double v) {
   return lo;
 }
 
-__device__ __forceinline__ double lj_cell_energy(const VolumeArgs& V, double v) {
-  const int k = lj_shells_inside(V, v);
+// The same count with every lane of a warp testing its own shell: the test
+// holds for a prefix of the shells, so the number of lanes where it holds,
+// 32 shells at a time, is the bisection's result.  FP64 instructions occupy
+// the pipe for a whole warp whatever the number of active lanes, so 32 tests
+// cost what one does.  All 32 lanes call it.
+__device__ __forceinline__ int lj_shells_inside_warp(const VolumeArgs& V, double v) {
+  const int lane = (int)(threadIdx.x & 31u);
+  const bool cubic = V.dim == 3;
+  int n = 0;
+  for (int base = 0; base < V.nshell; base += 32) {
+    const int i = base + lane;
+    bool in = false;
+    if (i < V.nshell) {
+      const double key = cubic ? (V.shell_d2[i] * v) * v : V.shell_d2[i] * v;
+      in = key < V.cutoff2;
+    }
+    const unsigned int m = __ballot_sync(0xFFFFFFFFu, in);
+    n += __popc(m);
+    if (m != 0xFFFFFFFFu) break;
+  }
+  return n;
+}
+
+// u(v) from the number k of shells inside the cutoff.
+__device__ __forceinline__ double lj_energy_at(const VolumeArgs& V, double v, int k) {
   if (V.dim == 3) {
     const double x = 1.0 / v;
     const double x2 = x * x;
@@ -170,6 +193,10 @@ __device__ __forceinline__ double lj_cell_energy(const VolumeArgs& V, double v) 
   const double x3 = x * x * x;
   const double x6 = x3 * x3;
   return (2.0 * V.epsilon) * (x6 * V.S12[k] - x3 * V.S6[k]);
+}
+
+__device__ __forceinline__ double lj_cell_energy(const VolumeArgs& V, double v) {
+  return lj_energy_at(V, v, lj_shells_inside(V, v));
 }
 
 // Block-wide copy of the FP64 parameters and shell tables into shared
@@ -270,6 +297,70 @@ __device__ __forceinline__ bool volume_decide(const VolumeArgs& V, long long ste
   const double t3 = ((double)(g_new - g) * J_eff) * (double)(n_hb_raw < 0 ? 0 : n_hb_raw);
   const double dH = (t1 + t2) - t3;
   const double arg = -dH / V.kT + Nd * log(V_new / V_old);
+  if (u2 < exp(arg)) {
+    out->V = V_new;
+    out->u = u_new;
+    out->g = g_new;
+    out->accepted = 1;
+  }
+  return true;
+}
+
+// volume_decide on two warps of one block, for the kernels that have two
+// warps free while the lattice is swept.  FP64 instructions occupy the FP64
+// pipe of a warp's SM sub-partition for a whole warp (64 cycles on GB300)
+// whatever the number of active lanes, and warps w and w + 1 sit on
+// different sub-partitions, so (a) the two divisions of the proposal, v' =
+// V'/N and V'/V, run in lanes 0 and 1 of one pass, (b) the shells inside the
+// cutoff are counted 32 at a time (lj_shells_inside_warp), and (c) warp
+// role 1 takes log(V'/V) (the longest function here) while warp role 0
+// evaluates the energy change; role 0 waits for it on named barrier BAR
+// (64 threads) before the final exp.  The IEEE operations and their order
+// are those of volume_decide, so the decision is identical.  Called by all
+// 64 threads (role = 0 or 1 per warp) with the same arguments; xch is a
+// shared double; the result in *out is valid in role 0's lanes.  The early
+// returns depend only on values both warps compute alike, so either both
+// reach the barrier or neither does.
+template <int BAR>
+__device__ __forceinline__ bool volume_decide_pair(int role, const VolumeArgs& V, long long step,
+                                                   double V_old, double u_old, int g,
+                                                   long long n_hb_raw, const RoundKeys& K,
+                                                   VolumeResult* out, double* xch) {
+  out->V = V_old;
+  out->u = u_old;
+  out->g = g;
+  out->accepted = 0;
+  if (!V.volume_moves) return true;
+  const Words4 r = philox(kCellVolume, (uint32_t)((unsigned long long)step & 0xFFFFFFFFu),
+                          (uint32_t)((unsigned long long)step >> 32), kTagVolume, K);
+  const double u1 = u53(r.x, r.y);
+  const double u2 = u53(r.z, r.w);
+  const double Nd = (double)V.N;
+  const double dV = (2.0 * u1 - 1.0) * V.dV_max;
+  const double V_new = V_old + dV;
+  const unsigned int lane = threadIdx.x & 31u;
+  const double quot = V_new / ((lane == 1u) ? V_old : Nd);  // lane 0: v', lane 1: V'/V
+  const double v_new = __shfl_sync(0xFFFFFFFFu, quot, 0);
+  const double ratio = __shfl_sync(0xFFFFFFFFu, quot, 1);
+  if (v_new < 1.0) return true;
+  const int g_new = (v_new < 2.0) ? 1 : 0;
+  if (g_new != g && n_hb_raw < 0) return false;
+  if (role == 1) {
+    const double lr = Nd * log(ratio);
+    if (lane == 0u) *xch = lr;
+    asm volatile("bar.sync %0, 64;" ::"n"(BAR) : "memory");
+    return true;
+  }
+  const double J_eff = V.J - V.P * V.v_HB;
+  const double u_new = lj_energy_at(V, v_new, lj_shells_inside_warp(V, v_new));
+  const double du = u_new - u_old;
+  const double t1 = Nd * du;
+  const double t2 = V.P * dV;
+  const double t3 = ((double)(g_new - g) * J_eff) * (double)(n_hb_raw < 0 ? 0 : n_hb_raw);
+  const double dH = (t1 + t2) - t3;
+  const double q = -dH / V.kT;
+  asm volatile("bar.sync %0, 64;" ::"n"(BAR) : "memory");
+  const double arg = q + *xch;
   if (u2 < exp(arg)) {
     out->V = V_new;
     out->u = u_new;

@@ -209,12 +209,14 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     // not depend on this step's bonds, while the other blocks sweep (the
     // parameters staged into the unused tile buffers first)
     VolumeArgs* sV = &U.vol;
+    __shared__ double s_xch;
     stage_volume_args(sV, A.vol);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 64) {  // warps 0 and 1: the move on two FP64 pipes
       VolumeResult r;
-      if (volume_decide(*sV, step + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1, A.keys,
-                        &r)) {
+      const bool ok = volume_decide_pair<3>((int)(threadIdx.x >> 5), *sV, step + 1, ctl->next_V,
+                                            ctl->next_u, ctl->next_g, -1, A.keys, &r, &s_xch);
+      if (threadIdx.x == 0 && ok) {
         ctl->ahead_V = r.V;
         ctl->ahead_u = r.u;
         ctl->ahead_g = r.g;
@@ -448,12 +450,15 @@ __global__ void __launch_bounds__(kThreads) k_layer(LatticeArgs A, int launch) {
   if (launch == 0 && blockIdx.x == 0) {
     // the volume block: the next step's move, decided now unless it depends on the bonds
     __shared__ VolumeArgs sV;
+    __shared__ double s_xch;
     stage_volume_args(&sV, A.vol);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 64) {  // warps 0 and 1: the move on two FP64 pipes
       VolumeResult r;
-      if (volume_decide(sV, ctl->sweep + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1,
-                        A.keys, &r)) {
+      const bool ok = volume_decide_pair<3>((int)(threadIdx.x >> 5), sV, ctl->sweep + 1,
+                                            ctl->next_V, ctl->next_u, ctl->next_g, -1, A.keys,
+                                            &r, &s_xch);
+      if (threadIdx.x == 0 && ok) {
         ctl->ahead_V = r.V;
         ctl->ahead_u = r.u;
         ctl->ahead_g = r.g;

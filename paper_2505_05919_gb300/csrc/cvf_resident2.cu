@@ -10,8 +10,9 @@
 // CTA's slab are read from the neighbouring CTAs' shared memory.  Each cell
 // is updated exactly as in the tiled sweep (update_in_word: the same draws,
 // the same rule), so the lattice and every count are those of the tiled path.
-// An extra warp of CTA 0 decides the next step's volume move while the
-// colours run (it needs no bonds unless the gate would change).
+// Two extra warps of CTA 0 decide the next step's volume move while the
+// colours run (it needs no bonds unless the gate would change), each on its
+// own FP64 pipe (volume_decide_pair).
 //
 // Every CTA runs the same loop of steps with the same barriers; no CTA leaves
 // early, so the hardware barriers always complete.
@@ -31,7 +32,7 @@ namespace cvf {
 namespace {
 
 constexpr int kResThreads = 256;            // sweeping threads per CTA
-constexpr int kResBlock = kResThreads + 32;  // + the volume warp
+constexpr int kResBlock = kResThreads + 64;  // + two volume warps
 
 // Cluster barrier in two halves (PTX barrier.cluster: arrive releases, wait
 // acquires): a thread may work between its arrival and its wait.
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(kResBlock) k_resident2(LatticeArgs A, long lon
   __shared__ uint32_t s_hist4[4];
   __shared__ int s_next_g;                  // CTA 0: the gate of the next step
   __shared__ VolumeArgs sV;                 // FP64 parameters for the volume moves
+  __shared__ double s_xch;                  // the two volume warps' exchange
   Ctrl* ctl = A.ctrl;
   const int L = A.L, Lh = L >> 1, R = L / nctas, y0 = rank * R;
   const long long N = (long long)L * L;
@@ -125,9 +127,12 @@ __global__ void __launch_bounds__(kResBlock) k_resident2(LatticeArgs A, long lon
     const bool rec = step_recorded(every, step);
     if (!sweeper) {
       cluster_arrive();  // (1)
-      if (rank == 0 && threadIdx.x == kResThreads) {
+      if (rank == 0) {  // the two volume warps: the move on two FP64 pipes
         VolumeResult r;
-        if (volume_decide(sV, step + 1, ctl->next_V, ctl->next_u, ctl->next_g, -1, K, &r)) {
+        const bool ok = volume_decide_pair<3>((int)((threadIdx.x - kResThreads) >> 5), sV,
+                                              step + 1, ctl->next_V, ctl->next_u, ctl->next_g,
+                                              -1, K, &r, &s_xch);
+        if (threadIdx.x == kResThreads && ok) {
           ctl->ahead_V = r.V;
           ctl->ahead_u = r.u;
           ctl->ahead_g = r.g;
