@@ -73,13 +73,24 @@ __global__ void k_batch_reset(BatchWork* W, unsigned int* progress, int n_replic
   }
 }
 
-// Takes the next work item from the launch's counter and decodes it (thread
-// 0 only): returns false when the launch is out of items or has failed.
+// Takes the next work item from the launch's counter and decodes it.  Called
+// by all 32 lanes of warp 0; every lane returns the same value, the item is
+// valid in lane 0.  The replica of the item is found by a 32-way search of
+// the strictly increasing tile_prefix (two rounds of parallel loads for up to
+// 1024 replicas, where a binary search takes a dependent load per halving);
+// false when the launch is out of items or has failed.
 __device__ __forceinline__ bool take_item(BatchWork* W, const int32_t* __restrict__ order,
                                           const long long* __restrict__ tile_prefix, int* rep,
                                           int* tile, long long* rel) {
-  const unsigned long long i = atomicAdd(&W->next, 1ull);
-  if ((long long)i >= W->total_items || *(volatile unsigned int*)&W->error) return false;
+  const unsigned int lane = threadIdx.x & 31u;
+  unsigned long long i = 0;
+  int stop = 0;
+  if (lane == 0u) {
+    i = atomicAdd(&W->next, 1ull);
+    stop = ((long long)i >= W->total_items || *(volatile unsigned int*)&W->error) ? 1 : 0;
+  }
+  i = __shfl_sync(0xFFFFFFFFu, i, 0);
+  if (__shfl_sync(0xFFFFFFFFu, stop, 0)) return false;
   // segment, relative step, replica, tile
   int k = 0;
   while (k + 1 < W->nseg && (long long)i >= W->seg_base[k + 1]) ++k;
@@ -90,18 +101,23 @@ __device__ __forceinline__ bool take_item(BatchWork* W, const int32_t* __restric
   const long long j = r % T;
   int lo = 0, hi = A;  // largest ri with tile_prefix[ri] <= j
   while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (tile_prefix[mid] <= j) lo = mid;
-    else hi = mid;
+    const int span = (hi - lo + 31) / 32;
+    const int idx = lo + (int)lane * span;
+    const bool in = idx < hi && tile_prefix[idx] <= j;
+    const unsigned int m = __ballot_sync(0xFFFFFFFFu, in);  // bit 0 always set
+    lo += (31 - __clz((int)m)) * span;
+    hi = min(hi, lo + span);
   }
-  if (!dcheck(k < W->nseg && A <= W->n_active && lo >= 0 && lo < A && j >= 0 && j < T &&
-                  j < tile_prefix[lo + 1] && s >= 0,
-              &W->error, kSiteBatchItem))
-    return false;
-  *rep = order[lo];
-  *tile = (int)(j - tile_prefix[lo]);
-  *rel = s;
-  return true;
+  int ok = 1;
+  if (lane == 0u) {
+    ok = dcheck(k < W->nseg && A <= W->n_active && lo >= 0 && lo < A && j >= 0 && j < T &&
+                    j < tile_prefix[lo + 1] && s >= 0,
+                &W->error, kSiteBatchItem) ? 1 : 0;
+    *rep = order[lo];
+    *tile = (int)(j - tile_prefix[lo]);
+    *rel = s;
+  }
+  return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
 }
 
 // The persistent batched sweep.  A block works through items (step s,
@@ -128,15 +144,18 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
   __shared__ uint32_t s_hist4[4];
   __shared__ RoundKeys s_keys;  // the current replica's round keys (broadcast reads)
   __shared__ double s_xch;      // the volume item's two warps' exchange
-  if (threadIdx.x == 0) {
-    s_q = 0;
+  if (threadIdx.x < 32) {
     int r = 0, t = 0;
     long long e = 0;
-    s_valid = take_item(W, order, tile_prefix, &r, &t, &e) ? 1 : 0;
-    s_rep = r;
-    s_tile = t;
-    s_rel = e;
-    s_staged = 0;
+    const bool ok = take_item(W, order, tile_prefix, &r, &t, &e);
+    if (threadIdx.x == 0) {
+      s_q = 0;
+      s_valid = ok ? 1 : 0;
+      s_rep = r;
+      s_tile = t;
+      s_rel = e;
+      s_staged = 0;
+    }
   }
   if (threadIdx.x < 4) s_hist4[threadIdx.x] = 0;
   for (;;) {
@@ -191,13 +210,19 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
           __threadfence();
           st_release(&progress[rep], (unsigned int)(rel + 1));
         }
+      }
+      if (threadIdx.x < 32) {
+        __syncwarp();
         int rr = 0, tt = 0;
         long long e = 0;
-        s_valid = take_item(W, order, tile_prefix, &rr, &tt, &e) ? 1 : 0;
-        s_rep = rr;
-        s_tile = tt;
-        s_rel = e;
-        s_staged = 0;
+        const bool ok = take_item(W, order, tile_prefix, &rr, &tt, &e);
+        if (threadIdx.x == 0) {
+          s_valid = ok ? 1 : 0;
+          s_rep = rr;
+          s_tile = tt;
+          s_rel = e;
+          s_staged = 0;
+        }
       }
       continue;
     }
@@ -234,17 +259,20 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     const bool rec = step_recorded(vc->record_every, step);
     colour0<RNG_WORDS, CMP64, TR, TW, kThreads>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
     // S.in is free: take the next item and, when it can start, copy its tile
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       int r = 0, tt = 0;
       long long e = 0;
-      n_valid = take_item(W, order, tile_prefix, &r, &tt, &e) ? 1 : 0;
-      n_rep = r;
-      n_tile = tt;
-      n_rel = e;
-      const int nl = reps[r].L;
-      const int ntn = ((nl / 2 + TW - 1) / TW) * ((nl + TR - 1) / TR);
-      n_ready = (n_valid && tt < ntn && nl % 8 == 0 &&
-                 ld_acquire(&progress[r]) >= (unsigned int)e) ? 1 : 0;
+      const bool ok = take_item(W, order, tile_prefix, &r, &tt, &e);
+      if (threadIdx.x == 0) {
+        n_valid = ok ? 1 : 0;
+        n_rep = r;
+        n_tile = tt;
+        n_rel = e;
+        const int nl = reps[r].L;
+        const int ntn = ((nl / 2 + TW - 1) / TW) * ((nl + TR - 1) / TR);
+        n_ready = (n_valid && tt < ntn && nl % 8 == 0 &&
+                   ld_acquire(&progress[r]) >= (unsigned int)e) ? 1 : 0;
+      }
     }
     __syncthreads();
     if (n_ready) {
