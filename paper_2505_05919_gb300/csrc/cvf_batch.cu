@@ -42,6 +42,12 @@ struct ReplicaDesc {
   uint32_t q;
 };
 
+// colour loops: two cells per iteration in both colours, the half a runtime
+// value (over the 256 mixed-size replicas: 487 sigma-updates/ns, equal to one
+// loop per half with two cells per iteration in colour 1; 472 with one loop
+// per half and one cell per iteration)
+constexpr int kBatchShape = kUnroll0 | kUnroll1;
+
 // Launch description written by the host before every launch.
 constexpr int kBatchMaxSegments = 64;
 struct BatchWork {
@@ -257,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     __syncthreads();
     TileCounts cnt{0, 0, 0};
     const bool rec = step_recorded(vc->record_every, step);
-    colour0<RNG_WORDS, CMP64, TR, TW, kThreads>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
+    colour0<RNG_WORDS, CMP64, TR, TW, kThreads, kBatchShape>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
     // S.in is free: take the next item and, when it can start, copy its tile
     if (threadIdx.x < 32) {
       int r = 0, tt = 0;
@@ -289,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
       const TileGeom gn = tile_geom<TR, TW>(Ln, Lhn, (n_tile / tx) * TR, (n_tile % tx) * TW);
       stage_async16<TR, TW, kThreads>(vn, gn, S);
     }
-    colour1<RNG_WORDS, CMP64, TR, TW, kThreads>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
+    colour1<RNG_WORDS, CMP64, TR, TW, kThreads, kBatchShape>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
     if (rec) {  // block-uniform: only on recorded steps
       __syncthreads();
       hist_flush(s_hist4, ctl->acc_hist);

@@ -118,10 +118,12 @@ __device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi, 
 // seeing the earlier ones); xm / xp are the words to the left / right, ym /
 // yp the words of the rows y-1 / y+1.  Accepted moves add their packed count
 // changes to pk; with s_hist4 (recorded steps) the cell's N_q' is counted.
-template <int RNG_WORDS, bool CMP64, typename KEYS>
+// HI = 0 / 1 fixes the half at compile time (a warp whose lanes all update
+// the same half); HI = -1 takes it from hi_rt.
+template <int RNG_WORDS, bool CMP64, int HI = -1, typename KEYS>
 __device__ __forceinline__ uint32_t update_in_word(uint32_t own, uint32_t xm_word,
                                                    uint32_t xp_word, uint32_t ym_word,
-                                                   uint32_t yp_word, int hi, uint32_t c,
+                                                   uint32_t yp_word, int hi_rt, uint32_t c,
                                                    uint32_t s_lo, uint32_t s_hi,
                                                    const KEYS& keys, uint32_t q,
                                                    const Tables2& Tb, uint32_t& pk,
@@ -129,6 +131,7 @@ __device__ __forceinline__ uint32_t update_in_word(uint32_t own, uint32_t xm_wor
   // partners, moved to bits 16..18: arm 0 (+x) <-> arm 1 of the +x cell,
   // arm 1 (-x) <-> arm 0 of the -x cell, arm 2 (+y) <-> arm 3 of the +y cell,
   // arm 3 (-y) <-> arm 2 of the -y cell
+  const int hi = (HI >= 0) ? HI : hi_rt;
   uint32_t w, p0, p1, p2, p3;
   if (hi) {
     w = own >> 16;
@@ -253,13 +256,22 @@ __device__ __forceinline__ void stage_async16(const StepView<KEYS>& v, const Til
 // on odd rows; x0 + 2 tw, low half of word tw, on even rows).  Reads S.in,
 // writes S.mid.  s_hist4 != nullptr (recorded steps): N_q' of the tile's
 // cells is counted.
-template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS>
+// Code shape of the colour loops, fixed per kernel at compile time (each
+// kernel uses the combination that ran fastest for it):
+//   kHalfRows  a warp that covers one row compiles its row loop once per half
+//              of the word, so the half a cell occupies is a constant
+//   kUnroll0   two cells per loop iteration in colour 0 (two independent arm
+//              chains for the scheduler), kUnroll1 the same in colour 1
+enum TileShapeFlags : int { kHalfRows = 1, kUnroll0 = 2, kUnroll1 = 4 };
+
+template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, int SHAPE, typename KEYS>
 __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom& g,
                                         TileSmem<TR, TW>& S, const Tables2& Tb,
                                         TileCounts& cnt, uint32_t* s_hist4) {
   constexpr int kRows = (TW >= 32) ? 1 : 32 / TW;  // rows per warp pass
   constexpr int kLanes = (TW >= 32) ? 32 : TW;     // lanes per row
   constexpr int C = kInColOff + 1;                 // column of word 0
+  constexpr int kUnroll = (SHAPE & kUnroll0) ? 2 : 1;
   const int L = v.L;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lrow = lane / kLanes, lcol = lane % kLanes;
@@ -272,20 +284,29 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
     const int hi = y & 1;
     const int yg = (y < 0) ? y + L : (y >= L ? y - L : y);
     const bool inside = (r >= 0) && (r < th);
-    // two cells per iteration give the scheduler two independent arm chains
-#pragma unroll 2
-    for (int j = lcol; j < tw; j += kLanes) {
-      if (!dcheck(r + 1 >= 0 && r + 3 < TR + 4 && j + C + 1 < TW + 8 && j + 1 < TW + 2, v.err,
-                  kSiteTileRead))
-        continue;
-      const int xg = 2 * (p0 + j) + hi;
-      uint32_t pk_row = 0;
-      const uint32_t out = update_in_word<RNG_WORDS, CMP64>(
-          S.in[r + 2][j + C], S.in[r + 2][j + C - 1], S.in[r + 2][j + C + 1],
-          S.in[r + 1][j + C], S.in[r + 3][j + C], hi, (uint32_t)((long long)yg * L + xg),
-          v.s_lo, v.s_hi, v.keys, v.q, Tb, pk_row, inside ? s_hist4 : nullptr);
-      if (inside) pk += pk_row;  // the halo rows belong to other tiles
-      S.mid[r + 1][j + 1] = out;
+    auto row = [&](auto hi_c) {
+#pragma unroll(kUnroll)
+      for (int j = lcol; j < tw; j += kLanes) {
+        if (!dcheck(r + 1 >= 0 && r + 3 < TR + 4 && j + C + 1 < TW + 8 && j + 1 < TW + 2, v.err,
+                    kSiteTileRead))
+          continue;
+        const int xg = 2 * (p0 + j) + hi;
+        uint32_t pk_row = 0;
+        const uint32_t out = update_in_word<RNG_WORDS, CMP64, decltype(hi_c)::value>(
+            S.in[r + 2][j + C], S.in[r + 2][j + C - 1], S.in[r + 2][j + C + 1],
+            S.in[r + 1][j + C], S.in[r + 3][j + C], hi, (uint32_t)((long long)yg * L + xg),
+            v.s_lo, v.s_hi, v.keys, v.q, Tb, pk_row, inside ? s_hist4 : nullptr);
+        if (inside) pk += pk_row;  // the halo rows belong to other tiles
+        S.mid[r + 1][j + 1] = out;
+      }
+    };
+    if constexpr (kRows == 1 && (SHAPE & kHalfRows) != 0) {
+      if (hi)
+        row(std::integral_constant<int, 1>{});
+      else
+        row(std::integral_constant<int, 0>{});
+    } else {
+      row(std::integral_constant<int, -1>{});
     }
   }
   cnt.add(pk);
@@ -317,12 +338,13 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
 
 // Colour 1: tile rows 0 .. th-1 (low half on odd rows, high on even rows),
 // from S.mid to the destination buffer.
-template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS>
+template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, int SHAPE, typename KEYS>
 __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom& g,
                                         TileSmem<TR, TW>& S, const Tables2& Tb,
                                         TileCounts& cnt, uint32_t* s_hist4) {
   constexpr int kRows = (TW >= 32) ? 1 : 32 / TW;
   constexpr int kLanes = (TW >= 32) ? 32 : TW;
+  constexpr int kUnroll = (SHAPE & kUnroll1) ? 2 : 1;
   const int L = v.L, Lh = v.Lh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lrow = lane / kLanes, lcol = lane % kLanes;
@@ -334,44 +356,29 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
     const int y = y0 + r;
     const int hi = (y & 1) ^ 1;
     uint32_t* drow = v.dst + (size_t)y * Lh + p0;
-#pragma unroll 2
-    for (int j = lcol; j < tw; j += kLanes) {
-      if (!dcheck(r + 2 < TR + 2 && j + 2 < TW + 2 && y >= 0 && y < L && p0 + j < Lh, v.err,
-                  kSiteTileWrite))
-        continue;
-      const int xg = 2 * (p0 + j) + hi;
-      drow[j] = update_in_word<RNG_WORDS, CMP64>(
-          S.mid[r + 1][j + 1], S.mid[r + 1][j], S.mid[r + 1][j + 2], S.mid[r][j + 1],
-          S.mid[r + 2][j + 1], hi, (uint32_t)((long long)y * L + xg), v.s_lo, v.s_hi, v.keys,
-          v.q, Tb, pk, s_hist4);
+    auto row = [&](auto hi_c) {
+#pragma unroll(kUnroll)
+      for (int j = lcol; j < tw; j += kLanes) {
+        if (!dcheck(r + 2 < TR + 2 && j + 2 < TW + 2 && y >= 0 && y < L && p0 + j < Lh, v.err,
+                    kSiteTileWrite))
+          continue;
+        const int xg = 2 * (p0 + j) + hi;
+        drow[j] = update_in_word<RNG_WORDS, CMP64, decltype(hi_c)::value>(
+            S.mid[r + 1][j + 1], S.mid[r + 1][j], S.mid[r + 1][j + 2], S.mid[r][j + 1],
+            S.mid[r + 2][j + 1], hi, (uint32_t)((long long)y * L + xg), v.s_lo, v.s_hi, v.keys,
+            v.q, Tb, pk, s_hist4);
+      }
+    };
+    if constexpr (kRows == 1 && (SHAPE & kHalfRows) != 0) {
+      if (hi)
+        row(std::integral_constant<int, 1>{});
+      else
+        row(std::integral_constant<int, 0>{});
+    } else {
+      row(std::integral_constant<int, -1>{});
     }
   }
   cnt.add(pk);
-}
-
-// Sweep the tile at rows y0.., words p0.. of one lattice with synchronous
-// staging.  Called by all threads of the block; ends with the tile written
-// to dst (no trailing barrier: the caller synchronises before reusing the
-// shared buffers).  s_hist4 != nullptr (recorded steps): N_q' of the tile's
-// cells is added to hist_out[0..8) through the block's four zeroed shared
-// words.  The accepted moves and their dN_HB, dN_sigma are counted on every
-// step.  A warp covers max(1, 32/TW) rows per pass.
-template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, typename KEYS, bool CG = false>
-__device__ __forceinline__ void sweep_tile(const StepView<KEYS>& v, int y0, int p0,
-                                           TileSmem<TR, TW>& S, const Tables2& Tb,
-                                           TileCounts& cnt, uint32_t* s_hist4,
-                                           unsigned long long* hist_out) {
-  static_assert(TW >= 32 ? (TW % 32 == 0) : (32 % TW == 0), "tile width");
-  const TileGeom g = tile_geom<TR, TW>(v.L, v.Lh, y0, p0);
-  stage_plain<TR, TW, NT, CG>(v, g, S);
-  __syncthreads();
-  colour0<RNG_WORDS, CMP64, TR, TW, NT>(v, g, S, Tb, cnt, s_hist4);
-  __syncthreads();
-  colour1<RNG_WORDS, CMP64, TR, TW, NT>(v, g, S, Tb, cnt, s_hist4);
-  if (s_hist4) {  // block-uniform: only on recorded steps
-    __syncthreads();
-    hist_flush(s_hist4, hist_out);
-  }
 }
 
 }  // namespace cvf
