@@ -185,10 +185,10 @@ struct TileShape {
   static constexpr int W = (TILE == 0) ? 64 : 32;
 };
 constexpr int kNumSweepTiles = 3;
-// colour loops: one row loop per half, one cell per iteration (at 4096^2:
-// 515 sigma-updates/ns, against 500-503 for two cells per iteration with the
-// half a runtime value and 458 for one loop per half with two cells per
-// iteration in colour 0)
+// colour loops: one row loop per half (and per recorded / unrecorded step),
+// one cell per iteration (at 4096^2: 518 sigma-updates/ns, against 500-503
+// for two cells per iteration with the half a runtime value and 458 for one
+// loop per half with two cells per iteration in colour 0)
 constexpr int kSweepShape = kHalfRows;
 
 template <int RNG_WORDS, bool CMP64, int TILE>

@@ -259,7 +259,9 @@ __device__ __forceinline__ void stage_async16(const StepView<KEYS>& v, const Til
 // Code shape of the colour loops, fixed per kernel at compile time (each
 // kernel uses the combination that ran fastest for it):
 //   kHalfRows  a warp that covers one row compiles its row loop once per half
-//              of the word, so the half a cell occupies is a constant
+//              of the word, so the half a cell occupies is a constant, and
+//              once more for recorded steps (N_q' counted), so the other
+//              steps carry no per-cell test of the histogram pointer
 //   kUnroll0   two cells per loop iteration in colour 0 (two independent arm
 //              chains for the scheduler), kUnroll1 the same in colour 1
 enum TileShapeFlags : int { kHalfRows = 1, kUnroll0 = 2, kUnroll1 = 4 };
@@ -284,7 +286,8 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
     const int hi = y & 1;
     const int yg = (y < 0) ? y + L : (y >= L ? y - L : y);
     const bool inside = (r >= 0) && (r < th);
-    auto row = [&](auto hi_c) {
+    auto row = [&](auto hi_c, auto rec_c) {
+      uint32_t* const hist = decltype(rec_c)::value ? (inside ? s_hist4 : nullptr) : nullptr;
 #pragma unroll(kUnroll)
       for (int j = lcol; j < tw; j += kLanes) {
         if (!dcheck(r + 1 >= 0 && r + 3 < TR + 4 && j + C + 1 < TW + 8 && j + 1 < TW + 2, v.err,
@@ -295,18 +298,25 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
         const uint32_t out = update_in_word<RNG_WORDS, CMP64, decltype(hi_c)::value>(
             S.in[r + 2][j + C], S.in[r + 2][j + C - 1], S.in[r + 2][j + C + 1],
             S.in[r + 1][j + C], S.in[r + 3][j + C], hi, (uint32_t)((long long)yg * L + xg),
-            v.s_lo, v.s_hi, v.keys, v.q, Tb, pk_row, inside ? s_hist4 : nullptr);
+            v.s_lo, v.s_hi, v.keys, v.q, Tb, pk_row, hist);
         if (inside) pk += pk_row;  // the halo rows belong to other tiles
         S.mid[r + 1][j + 1] = out;
       }
     };
     if constexpr (kRows == 1 && (SHAPE & kHalfRows) != 0) {
-      if (hi)
-        row(std::integral_constant<int, 1>{});
-      else
-        row(std::integral_constant<int, 0>{});
+      if (s_hist4) {
+        if (hi)
+          row(std::integral_constant<int, 1>{}, std::true_type{});
+        else
+          row(std::integral_constant<int, 0>{}, std::true_type{});
+      } else {
+        if (hi)
+          row(std::integral_constant<int, 1>{}, std::false_type{});
+        else
+          row(std::integral_constant<int, 0>{}, std::false_type{});
+      }
     } else {
-      row(std::integral_constant<int, -1>{});
+      row(std::integral_constant<int, -1>{}, std::true_type{});
     }
   }
   cnt.add(pk);
@@ -356,7 +366,8 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
     const int y = y0 + r;
     const int hi = (y & 1) ^ 1;
     uint32_t* drow = v.dst + (size_t)y * Lh + p0;
-    auto row = [&](auto hi_c) {
+    auto row = [&](auto hi_c, auto rec_c) {
+      uint32_t* const hist = decltype(rec_c)::value ? s_hist4 : nullptr;
 #pragma unroll(kUnroll)
       for (int j = lcol; j < tw; j += kLanes) {
         if (!dcheck(r + 2 < TR + 2 && j + 2 < TW + 2 && y >= 0 && y < L && p0 + j < Lh, v.err,
@@ -366,16 +377,23 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
         drow[j] = update_in_word<RNG_WORDS, CMP64, decltype(hi_c)::value>(
             S.mid[r + 1][j + 1], S.mid[r + 1][j], S.mid[r + 1][j + 2], S.mid[r][j + 1],
             S.mid[r + 2][j + 1], hi, (uint32_t)((long long)y * L + xg), v.s_lo, v.s_hi, v.keys,
-            v.q, Tb, pk, s_hist4);
+            v.q, Tb, pk, hist);
       }
     };
     if constexpr (kRows == 1 && (SHAPE & kHalfRows) != 0) {
-      if (hi)
-        row(std::integral_constant<int, 1>{});
-      else
-        row(std::integral_constant<int, 0>{});
+      if (s_hist4) {
+        if (hi)
+          row(std::integral_constant<int, 1>{}, std::true_type{});
+        else
+          row(std::integral_constant<int, 0>{}, std::true_type{});
+      } else {
+        if (hi)
+          row(std::integral_constant<int, 1>{}, std::false_type{});
+        else
+          row(std::integral_constant<int, 0>{}, std::false_type{});
+      }
     } else {
-      row(std::integral_constant<int, -1>{});
+      row(std::integral_constant<int, -1>{}, std::true_type{});
     }
   }
   cnt.add(pk);
