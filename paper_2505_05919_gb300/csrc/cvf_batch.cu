@@ -42,11 +42,11 @@ struct ReplicaDesc {
   uint32_t q;
 };
 
-// colour loops: two cells per iteration in both colours, the half a runtime
-// value (over the 256 mixed-size replicas: 487 sigma-updates/ns, equal to one
-// loop per half with two cells per iteration in colour 1; 472 with one loop
-// per half and one cell per iteration)
-constexpr int kBatchShape = kUnroll0 | kUnroll1;
+// colour loops: the single-lattice sweep's shape (over the 256 mixed-size
+// replicas: 497 sigma-updates/ns; 487 with two cells per iteration in both
+// colours and the half a runtime value, 481 with that and the recorded-step
+// copy, 472 with one loop per half and one cell per iteration)
+constexpr int kBatchShape = kHalfRows | kUnroll1 | kSplitRec;
 
 // Launch description written by the host before every launch.
 constexpr int kBatchMaxSegments = 64;

@@ -185,11 +185,12 @@ struct TileShape {
   static constexpr int W = (TILE == 0) ? 64 : 32;
 };
 constexpr int kNumSweepTiles = 3;
-// colour loops: one row loop per half (and per recorded / unrecorded step),
-// one cell per iteration (at 4096^2: 518 sigma-updates/ns, against 500-503
-// for two cells per iteration with the half a runtime value and 458 for one
-// loop per half with two cells per iteration in colour 0)
-constexpr int kSweepShape = kHalfRows;
+// colour loops: one row loop per half and per recorded / unrecorded step,
+// two cells per iteration in colour 1 only (at 4096^2: 522 sigma-updates/ns;
+// 520 with one cell per iteration in both colours, 500-503 with two cells per
+// iteration and the half a runtime value, 458 with one loop per half and two
+// cells per iteration in colour 0)
+constexpr int kSweepShape = kHalfRows | kUnroll1 | kSplitRec;
 
 template <int RNG_WORDS, bool CMP64, int TILE>
 __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)

@@ -259,12 +259,37 @@ __device__ __forceinline__ void stage_async16(const StepView<KEYS>& v, const Til
 // Code shape of the colour loops, fixed per kernel at compile time (each
 // kernel uses the combination that ran fastest for it):
 //   kHalfRows  a warp that covers one row compiles its row loop once per half
-//              of the word, so the half a cell occupies is a constant, and
-//              once more for recorded steps (N_q' counted), so the other
-//              steps carry no per-cell test of the histogram pointer
+//              of the word, so the half a cell occupies is a constant
 //   kUnroll0   two cells per loop iteration in colour 0 (two independent arm
 //              chains for the scheduler), kUnroll1 the same in colour 1
-enum TileShapeFlags : int { kHalfRows = 1, kUnroll0 = 2, kUnroll1 = 4 };
+//   kSplitRec  recorded steps (N_q' counted) run a copy of the row loop of
+//              their own, so the other steps test no histogram pointer per
+//              cell
+enum TileShapeFlags : int { kHalfRows = 1, kUnroll0 = 2, kUnroll1 = 4, kSplitRec = 8 };
+
+// Runs row(half, recorded) with the half and the recorded flag as
+// compile-time constants where SHAPE asks for them (-1 / true otherwise).
+template <int SHAPE, int ROWS_PER_WARP, typename ROW>
+__device__ __forceinline__ void dispatch_row(const ROW& row, int hi, bool recorded) {
+  auto halves = [&](auto rec_c) {
+    if constexpr (ROWS_PER_WARP == 1 && (SHAPE & kHalfRows) != 0) {
+      if (hi)
+        row(std::integral_constant<int, 1>{}, rec_c);
+      else
+        row(std::integral_constant<int, 0>{}, rec_c);
+    } else {
+      row(std::integral_constant<int, -1>{}, rec_c);
+    }
+  };
+  if constexpr ((SHAPE & kSplitRec) != 0) {
+    if (recorded)
+      halves(std::true_type{});
+    else
+      halves(std::false_type{});
+  } else {
+    halves(std::true_type{});
+  }
+}
 
 template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, int SHAPE, typename KEYS>
 __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom& g,
@@ -303,21 +328,7 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
         S.mid[r + 1][j + 1] = out;
       }
     };
-    if constexpr (kRows == 1 && (SHAPE & kHalfRows) != 0) {
-      if (s_hist4) {
-        if (hi)
-          row(std::integral_constant<int, 1>{}, std::true_type{});
-        else
-          row(std::integral_constant<int, 0>{}, std::true_type{});
-      } else {
-        if (hi)
-          row(std::integral_constant<int, 1>{}, std::false_type{});
-        else
-          row(std::integral_constant<int, 0>{}, std::false_type{});
-      }
-    } else {
-      row(std::integral_constant<int, -1>{}, std::true_type{});
-    }
+    dispatch_row<SHAPE, kRows>(row, hi, s_hist4 != nullptr);
   }
   cnt.add(pk);
   // the ring goes to the warps after the first two, which take one row of
@@ -380,21 +391,7 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
             v.q, Tb, pk, hist);
       }
     };
-    if constexpr (kRows == 1 && (SHAPE & kHalfRows) != 0) {
-      if (s_hist4) {
-        if (hi)
-          row(std::integral_constant<int, 1>{}, std::true_type{});
-        else
-          row(std::integral_constant<int, 0>{}, std::true_type{});
-      } else {
-        if (hi)
-          row(std::integral_constant<int, 1>{}, std::false_type{});
-        else
-          row(std::integral_constant<int, 0>{}, std::false_type{});
-      }
-    } else {
-      row(std::integral_constant<int, -1>{}, std::true_type{});
-    }
+    dispatch_row<SHAPE, kRows>(row, hi, s_hist4 != nullptr);
   }
   cnt.add(pk);
 }
