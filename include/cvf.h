@@ -417,13 +417,16 @@ int cvf_debug_checks(void);
  *
  * Every device-side wait of the library is bounded: a tile of the persistent
  * batched sweep (cvf_batch_sweep) that waits for its replica's previous step
- * polls a progress word with acquire loads and gives up after about a second
- * of polls, after which the launch ends and the next call that reads results
- * returns CVF_ETIMEOUT with the context intact.
+ * polls a progress word with acquire loads, sleeping about 128 min(d, 8)^2 ns
+ * between polls when the word is d short of its target, and gives up after
+ * about half a second of such sleep, after which the launch ends and the next
+ * call that reads results returns CVF_ETIMEOUT with the context intact.
  *
  * cvf_wait_probe: run that same wait alone: one device thread polls the
- * 4-byte-aligned device word `flag` until it is >= `target`, at most `polls`
- * times (1 <= polls <= 2^22).  Synchronises `stream` (a cudaStream_t; NULL =
+ * 4-byte-aligned device word `flag` until it is >= `target`, with a budget of
+ * `polls` 128-ns sleep quanta (1 <= polls <= 2^22; a poll d short of the
+ * target uses min(d, 8)^2 of them, so one per poll when the flag is one
+ * short).  Synchronises `stream` (a cudaStream_t; NULL =
  * legacy default stream).  Returns CVF_OK when the value was seen,
  * CVF_ETIMEOUT when the wait gave up (a flag that nothing sets), CVF_EINVAL
  * for a NULL or misaligned flag or `polls` out of range, CVF_ECUDA if a CUDA

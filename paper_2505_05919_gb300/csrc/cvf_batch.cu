@@ -52,6 +52,8 @@ constexpr int kBatchShape = kHalfRows | kUnroll1 | kSplitRec;
 constexpr int kBatchMaxSegments = 64;
 struct BatchWork {
   unsigned long long next;   // item counter
+  unsigned long long pad_next[15];  // the counter alone in its 128-byte line: every
+                                    // claim is an atomic on it, every wait reads `error`
   unsigned int error;        // 1: a wait gave up; 0x100 + site: a debug index check failed
   unsigned int pad;
   long long total_items;
@@ -80,7 +82,7 @@ __global__ void k_batch_reset(BatchWork* W, unsigned int* progress, int n_replic
 }
 
 // Takes the next work item from the launch's counter and decodes it.  Called
-// by all 32 lanes of warp 0; every lane returns the same value, the item is
+// by all 32 lanes of one warp; every lane returns the same value, the item is
 // valid in lane 0.  The replica of the item is found by a 32-way search of
 // the strictly increasing tile_prefix (two rounds of parallel loads for up to
 // 1024 replicas, where a binary search takes a dependent load per halving);
@@ -150,6 +152,12 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
   __shared__ uint32_t s_hist4[4];
   __shared__ RoundKeys s_keys;  // the current replica's round keys (broadcast reads)
   __shared__ double s_xch;      // the volume item's two warps' exchange
+  __shared__ int s_tab_rep, s_tab_g, s_key_rep;  // whose rows / keys Tb and s_keys hold
+  if (threadIdx.x == 0) {
+    s_tab_rep = -1;
+    s_tab_g = -1;
+    s_key_rep = -1;
+  }
   if (threadIdx.x < 32) {
     int r = 0, t = 0;
     long long e = 0;
@@ -208,21 +216,19 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
         }
       }
       if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int prev = atomicAdd(&ctl->done, 1u);
-        if (prev == (unsigned int)ntiles) {
-          __threadfence();
+        // release: the decision is visible to the step's committer; acquire:
+        // the committer sees every item's counts
+        if (atom_add_acq_rel(&ctl->done, 1u) == (unsigned int)ntiles) {
           finalize_step<true>(*R.vol, ctl, R.ring, R.ring_cap, R.keys);
-          __threadfence();
           st_release(&progress[rep], (unsigned int)(rel + 1));
         }
       }
-      if (threadIdx.x < 32) {
-        __syncwarp();
+      // the last warp takes the next item while warps 0 and 1 decide
+      if ((int)(threadIdx.x >> 5) == kThreads / 32 - 1) {
         int rr = 0, tt = 0;
         long long e = 0;
         const bool ok = take_item(W, order, tile_prefix, &rr, &tt, &e);
-        if (threadIdx.x == 0) {
+        if ((threadIdx.x & 31) == 0) {
           s_valid = ok ? 1 : 0;
           s_rep = rr;
           s_tile = tt;
@@ -232,9 +238,12 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
       }
       continue;
     }
+    // the threshold rows and round keys stay from the block's previous item
+    // when it had the same replica (and gate); the gate of a step is fixed
+    // once its items can run, so every thread reads the same g
     const int g = vc->next_g;
-    fill_rows2(Tb, R.table24, g);
-    if (threadIdx.x < 10) {
+    if (rep != s_tab_rep || g != s_tab_g) fill_rows2(Tb, R.table24, g);
+    if (rep != s_key_rep && threadIdx.x < 10) {
       s_keys.k0[threadIdx.x] = R.keys.k0[threadIdx.x];
       s_keys.k1[threadIdx.x] = R.keys.k1[threadIdx.x];
     }
@@ -261,15 +270,22 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     else
       stage_plain<TR, TW, kThreads, true>(v, gm, S);
     __syncthreads();
+    if (threadIdx.x == 0) {  // read again only after the next item's first barrier
+      s_tab_rep = rep;
+      s_tab_g = g;
+      s_key_rep = rep;
+    }
     TileCounts cnt{0, 0, 0};
     const bool rec = step_recorded(vc->record_every, step);
     colour0<RNG_WORDS, CMP64, TR, TW, kThreads, kBatchShape>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
-    // S.in is free: take the next item and, when it can start, copy its tile
-    if (threadIdx.x < 32) {
+    // S.in is free: take the next item and, when it can start, copy its tile.
+    // The last warp takes it: it has the fewest rows (and no ring cells) in
+    // the first colour, so the take overlaps the other warps' remaining work.
+    if ((int)(threadIdx.x >> 5) == kThreads / 32 - 1) {
       int r = 0, tt = 0;
       long long e = 0;
       const bool ok = take_item(W, order, tile_prefix, &r, &tt, &e);
-      if (threadIdx.x == 0) {
+      if ((threadIdx.x & 31) == 0) {
         n_valid = ok ? 1 : 0;
         n_rep = r;
         n_tile = tt;
@@ -306,13 +322,11 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
       atomicAdd(&ctl->acc_hb, (unsigned long long)(long long)(int)dhb);
       atomicAdd(&ctl->acc_pairs, (unsigned long long)(long long)(int)dc);
       atomicAdd(&ctl->acc_moves, (unsigned long long)nacc);
-      __threadfence();
-      const unsigned int prev = atomicAdd(&ctl->done, 1u);
-      s_last = (prev == (unsigned int)ntiles) ? 1 : 0;  // ntiles tiles + the volume item
+      // after the block's barrier: releases the tile's words and counts to the
+      // step's committer (ntiles tiles + the volume item), which acquires them
+      s_last = (atom_add_acq_rel(&ctl->done, 1u) == (unsigned int)ntiles) ? 1 : 0;
       if (s_last) {
-        __threadfence();
         finalize_step<true>(*R.vol, ctl, R.ring, R.ring_cap, R.keys);
-        __threadfence();
         st_release(&progress[rep], (unsigned int)(rel + 1));
       }
       // the next item becomes the current one

@@ -467,17 +467,23 @@ __device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cv
   c->ahead_state = 0;
 }
 
+// Atomic add with acquire-release semantics at GPU scope: the caller's
+// earlier writes (and, after a block barrier, its block's) are visible to
+// whoever acquires a later value of the counter, and the caller sees every
+// write released before the values it adds to.
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
 // True in every thread of the block that arrives last (after all blocks
 // have published their atomics).
 __device__ __forceinline__ bool last_block(unsigned int* done) {
   __shared__ int is_last;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned int prev = atomicAdd(done, 1u);
-    is_last = (prev == gridDim.x - 1) ? 1 : 0;
-    if (is_last) __threadfence();
-  }
+  if (threadIdx.x == 0) is_last = (atom_add_acq_rel(done, 1u) == gridDim.x - 1) ? 1 : 0;
   __syncthreads();
   return is_last != 0;
 }
@@ -577,7 +583,7 @@ __device__ __forceinline__ constexpr bool dcheck(bool, unsigned int*, unsigned i
 // fixed number of polls, so that a wait that can never end returns an error
 // status instead of hanging the GPU.
 // ---------------------------------------------------------------------------
-constexpr unsigned int kWaitPollLimit = 1u << 22;  // about a second of polls
+constexpr unsigned int kWaitPollLimit = 1u << 22;  // about half a second of sleep
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
   unsigned int v;
@@ -588,17 +594,25 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
 enum WaitResult { kWaitDone = 0, kWaitGaveUp = 1, kWaitAborted = 2 };
 
 // Poll until *flag >= target; stop early when *abort_word becomes nonzero
-// (another block gave up), give up after `limit` polls.
+// (another block gave up).  A waiter d steps short of its target sleeps about
+// 128 min(d, 8)^2 ns between polls, so blocks that took work far ahead (a
+// small lattice's later steps) leave the memory system to the ones about to
+// run; one step short it polls every 128 ns.  Each poll is charged its sleep
+// in 128-ns quanta, and the wait gives up once `limit` quanta are used (one
+// per poll when d = 1).
 __device__ __forceinline__ WaitResult wait_flag_geq(const unsigned int* flag, unsigned int target,
                                                     const unsigned int* abort_word,
                                                     unsigned int limit) {
-  unsigned int polls = 0;
-  while (ld_acquire(flag) < target) {
+  unsigned int used = 0;
+  for (;;) {
+    const unsigned int v = ld_acquire(flag);
+    if (v >= target) return kWaitDone;
     if (abort_word && *(volatile const unsigned int*)abort_word) return kWaitAborted;
-    if (++polls > limit) return kWaitGaveUp;
-    __nanosleep(128);
+    const unsigned int d = min(target - v, 8u);
+    used += d * d;
+    if (used > limit) return kWaitGaveUp;
+    __nanosleep(128u * d * d);
   }
-  return kWaitDone;
 }
 
 }  // namespace cvf

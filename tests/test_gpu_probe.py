@@ -45,6 +45,10 @@ def test_wait_probe_gives_up_with_a_status_and_the_context_survives():
     with pytest.raises(_capi.CvfError) as e:
         _capi.cvf_wait_probe(flag.data_ptr(), 1, 1 << 14)
     assert e.value.code == 4  # CVF_ETIMEOUT
+    # far from the target the wait polls less often and still gives up
+    with pytest.raises(_capi.CvfError) as e:
+        _capi.cvf_wait_probe(flag.data_ptr(), 1000, 1 << 14)
+    assert e.value.code == 4
     op = oracle.physical_params(300.0, 0.1, L=16, seed=9)
     ref = oracle.Oracle(op)
     ref.run(12)
