@@ -153,10 +153,16 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
   __shared__ RoundKeys s_keys;  // the current replica's round keys (broadcast reads)
   __shared__ double s_xch;      // the volume item's two warps' exchange
   __shared__ int s_tab_rep, s_tab_g, s_key_rep;  // whose rows / keys Tb and s_keys hold
+  // a replica's step count when the launch began (s_step_rep's): only this
+  // launch advances it, so an item of relative step rel runs at step
+  // s_step0 + rel once the replica's progress reached rel
+  __shared__ int s_step_rep;
+  __shared__ long long s_step0;
   if (threadIdx.x == 0) {
     s_tab_rep = -1;
     s_tab_g = -1;
     s_key_rep = -1;
+    s_step_rep = -1;
   }
   if (threadIdx.x < 32) {
     int r = 0, t = 0;
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     const ReplicaDesc& R = reps[rep];
     Ctrl* ctl = R.ctrl;
     volatile Ctrl* vc = ctl;
-    const long long step = vc->sweep;
+    const long long step = (rep == s_step_rep) ? s_step0 + rel : vc->sweep;
     const int tiles_x = (R.L / 2 + TW - 1) / TW;
     const int ntiles = tiles_x * ((R.L + TR - 1) / TR);
     if (t == ntiles) {
@@ -270,10 +276,12 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     else
       stage_plain<TR, TW, kThreads, true>(v, gm, S);
     __syncthreads();
-    if (threadIdx.x == 0) {  // read again only after the next item's first barrier
+    if (threadIdx.x == 0) {  // read again only after a later barrier
       s_tab_rep = rep;
       s_tab_g = g;
       s_key_rep = rep;
+      s_step_rep = rep;
+      s_step0 = step - rel;
     }
     TileCounts cnt{0, 0, 0};
     const bool rec = step_recorded(vc->record_every, step);
@@ -301,7 +309,8 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
       const ReplicaDesc& Rn = reps[n_rep];
       const int Ln = Rn.L, Lhn = Ln >> 1;
       const long long Nn = (long long)Ln * Ln;
-      const long long step_n = ((volatile Ctrl*)Rn.ctrl)->sweep;
+      const long long step_n =
+          (n_rep == s_step_rep) ? s_step0 + n_rel : ((volatile Ctrl*)Rn.ctrl)->sweep;
       StepView<KeysRound> vn;
       vn.src = reinterpret_cast<const uint32_t*>(Rn.state + (size_t)(step_n & 1) * Nn);
       vn.L = Ln;

@@ -410,24 +410,39 @@ template <bool DELTA = false>
 __device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cvf_obs* ring,
                                               long long ring_cap, const RoundKeys& K) {
   volatile Ctrl* c = ctl;
-  Ctrl s;  // committed state after this step
+  // Every field the commit reads is loaded before the first store, so the
+  // loads are in flight together (one memory round trip on the step's
+  // critical path); the early decision's fields are used only when
+  // ahead_state says they hold one.
   const int every = c->record_every;
-  const bool recorded = (every > 0) && ((c->sweep + 1) % every == 0);
+  const long long sweep = c->sweep;
+  const long long n_hb_raw = c->n_hb_raw, n_coop = c->n_coop;
+  const long long acc_sigma = c->acc_sigma, acc_volume = c->acc_volume;
+  const unsigned long long acc_hb = c->acc_hb, acc_pairs = c->acc_pairs,
+                           acc_moves = c->acc_moves;
+  const double next_V = c->next_V, next_u = c->next_u;
+  const int next_g = c->next_g, next_acc = c->next_acc;
+  const int ahead = c->ahead_state;
+  const double ahead_V = c->ahead_V, ahead_u = c->ahead_u;
+  const int ahead_g = c->ahead_g, ahead_acc = c->ahead_acc;
+  const long long head = c->ring_head;
+  Ctrl s;  // committed state after this step
+  const bool recorded = (every > 0) && ((sweep + 1) % every == 0);
   if (DELTA) {
-    s.n_hb_raw = c->n_hb_raw + (long long)c->acc_hb;
-    s.n_coop = c->n_coop + (long long)c->acc_pairs;
+    s.n_hb_raw = n_hb_raw + (long long)acc_hb;
+    s.n_coop = n_coop + (long long)acc_pairs;
   } else {
-    s.n_hb_raw = (long long)c->acc_hb;
+    s.n_hb_raw = (long long)acc_hb;
     // N_sigma is counted by the sweep only on recorded steps; otherwise it is
     // unknown (-1) until a recount (cvf_observables counts it on demand)
-    s.n_coop = recorded ? (long long)c->acc_pairs : -1;
+    s.n_coop = recorded ? (long long)acc_pairs : -1;
   }
-  s.acc_sigma = c->acc_sigma + (long long)c->acc_moves;
-  s.V_iso = c->next_V;
-  s.u_cell = c->next_u;
-  s.g = c->next_g;
-  s.acc_volume = c->acc_volume + c->next_acc;
-  s.sweep = c->sweep + 1;
+  s.acc_sigma = acc_sigma + (long long)acc_moves;
+  s.V_iso = next_V;
+  s.u_cell = next_u;
+  s.g = next_g;
+  s.acc_volume = acc_volume + next_acc;
+  s.sweep = sweep + 1;
   c->n_hb_raw = s.n_hb_raw;
   c->n_coop = s.n_coop;
   c->acc_sigma = s.acc_sigma;
@@ -447,16 +462,15 @@ __device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cv
       c->hist[v] = s.hist[v];
       c->acc_hist[v] = 0;
     }
-    const long long head = c->ring_head;
     ring[head % ring_cap] = make_obs(V, &s);
     c->ring_head = head + 1;
   }
   VolumeResult r;
-  if (c->ahead_state == 1) {
-    r.V = c->ahead_V;
-    r.u = c->ahead_u;
-    r.g = c->ahead_g;
-    r.accepted = c->ahead_acc;
+  if (ahead == 1) {
+    r.V = ahead_V;
+    r.u = ahead_u;
+    r.g = ahead_g;
+    r.accepted = ahead_acc;
   } else {
     volume_decide(V, s.sweep, s.V_iso, s.u_cell, s.g, s.n_hb_raw, K, &r);
   }

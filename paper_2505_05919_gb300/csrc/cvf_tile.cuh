@@ -332,8 +332,10 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
   }
   cnt.add(pk);
   // the ring goes to the warps after the first two, which take one row of
-  // the th + 2 fewer than warps 0 and 1 when 8 warps share 66 rows
-  const int ring0 = (NT >= 128 && TW >= 32) ? 64 : 0;
+  // the th + 2 fewer than warps 0 and 1 when 8 warps share 66 rows; with two
+  // rows per warp pass (16-word tiles) warp 0 takes the two extra rows, and
+  // the ring starts at warp 1
+  const int ring0 = (NT >= 128) ? ((TW >= 32) ? 64 : 32) : 0;
   for (int i = (int)threadIdx.x - ring0; i < th + 2; i += NT) {
     if (i < 0) continue;
     const int r = i - 1;
