@@ -244,15 +244,9 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
       }
       continue;
     }
-    // the threshold rows and round keys stay from the block's previous item
-    // when it had the same replica (and gate); the gate of a step is fixed
-    // once its items can run, so every thread reads the same g
+    // the gate of a step is fixed once its items can run, so every thread
+    // reads the same g; its load is in flight while the tile is staged
     const int g = vc->next_g;
-    if (rep != s_tab_rep || g != s_tab_g) fill_rows2(Tb, R.table24, g);
-    if (rep != s_key_rep && threadIdx.x < 10) {
-      s_keys.k0[threadIdx.x] = R.keys.k0[threadIdx.x];
-      s_keys.k1[threadIdx.x] = R.keys.k1[threadIdx.x];
-    }
     if (s_q != R.q) {  // block-uniform
       fill_prop2(Tb, R.q);
       __syncthreads();
@@ -275,6 +269,13 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
       cp_async_wait_all();
     else
       stage_plain<TR, TW, kThreads, true>(v, gm, S);
+    // the threshold rows and round keys stay from the block's previous item
+    // when it had the same replica (and gate)
+    if (rep != s_tab_rep || g != s_tab_g) fill_rows2(Tb, R.table24, g);
+    if (rep != s_key_rep && threadIdx.x < 10) {
+      s_keys.k0[threadIdx.x] = R.keys.k0[threadIdx.x];
+      s_keys.k1[threadIdx.x] = R.keys.k1[threadIdx.x];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {  // read again only after a later barrier
       s_tab_rep = rep;

@@ -255,7 +255,9 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
   if (threadIdx.x < 4) s_hist4[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
-    s_tile = (int)atomicAdd(&ctl->tile_next, 1u);
+    // the first tile of tile block b is b - 1 (no round trip to the counter);
+    // the counter hands out the tiles after the first gridDim.x - 1
+    s_tile = (int)blockIdx.x - 1;
   }
   __syncthreads();
 
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
                                                          (t % tiles_x) * kTileWords);
     colour0<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, kSweepShape>(v, gm, S, Tb, cnt,
                                                                rec ? s_hist4 : nullptr);
-    if (threadIdx.x == 0) s_next = (int)atomicAdd(&ctl->tile_next, 1u);
+    if (threadIdx.x == 0) s_next = (int)(atomicAdd(&ctl->tile_next, 1u) + gridDim.x - 1u);
     __syncthreads();  // S.in is free: fetch the next tile while colour 1 runs
     const int t2 = s_next;
     const bool t2_tma = (t2 < ntiles) ? stage(t2) : false;
