@@ -302,12 +302,16 @@ __global__ void __launch_bounds__(kThreads3, 4) k_pass3(Args3 A, int launch) {
   const uint32_t stride = nblk * kThreads3;
   const uint32_t g_first = (blockIdx.x - first_block) * kThreads3 + threadIdx.x;
   if (ALIGNED) {
-    // The group loop is compiled once per number of passes in the launch.
+    // The group loop is compiled once per number of passes in the launch and
+    // once more for recorded steps (N_q' counted), so that the others carry
+    // no per-group test of the flag (at 260^3: 479 against 449
+    // sigma-updates/ns with the test inside the loop).
     // Pass p's neighbour word is at c0 + dlt - (coordinate == edge ? wrp : 0)
     // with the coordinate (x group, y or z), the edge value, the offset and
     // the periodic wrap fixed for the launch.
-    auto body = [&](auto na_c) {
+    auto body = [&](auto na_c, auto rec_c) {
       constexpr int NA = decltype(na_c)::value;
+      constexpr bool REC = decltype(rec_c)::value;
       int arm[NA];
       uint32_t ax[NA], edge[NA], dlt[NA], wrp[NA];
 #pragma unroll
@@ -374,15 +378,21 @@ __global__ void __launch_bounds__(kThreads3, 4) k_pass3(Args3 A, int launch) {
         }
         unpack_counts(pk, nacc, hb_b, dc_b);
         *reinterpret_cast<uint4*>(st + c0) = make_uint4(w0, w1, w2, w3);
-        if (rec) hist_group(w0, w1, w2, w3, s_hist);
+        if (REC) hist_group(w0, w1, w2, w3, s_hist);
       }
     };
-    if (n_arms == 1)
-      body(std::integral_constant<int, 1>{});
-    else if (n_arms == 2)
-      body(std::integral_constant<int, 2>{});
+    auto arms = [&](auto rec_c) {
+      if (n_arms == 1)
+        body(std::integral_constant<int, 1>{}, rec_c);
+      else if (n_arms == 2)
+        body(std::integral_constant<int, 2>{}, rec_c);
+      else
+        body(std::integral_constant<int, 3>{}, rec_c);
+    };
+    if (rec)
+      arms(std::true_type{});
     else
-      body(std::integral_constant<int, 3>{});
+      arms(std::false_type{});
   } else {
     for (uint32_t gi = g_first; gi < A.groups; gi += stride) {
       const uint32_t c0 = gi * 4u;
