@@ -273,8 +273,7 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocksPerSM) k_batch_sweep(con
     // when it had the same replica (and gate)
     if (rep != s_tab_rep || g != s_tab_g) fill_rows2(Tb, R.table24, g);
     if (rep != s_key_rep && threadIdx.x < 10) {
-      s_keys.k0[threadIdx.x] = R.keys.k0[threadIdx.x];
-      s_keys.k1[threadIdx.x] = R.keys.k1[threadIdx.x];
+      s_keys.k[threadIdx.x] = R.keys.k[threadIdx.x];
     }
     __syncthreads();
     if (threadIdx.x == 0) {  // read again only after a later barrier

@@ -28,17 +28,17 @@ constexpr uint32_t kTagLayers = 4u;   // layered-schedule arm order
 constexpr uint32_t kCellVolume = 0xFFFFFFFFu;
 constexpr uint32_t kCellLayers = 0xFFFFFFFEu;
 
+// Round r's two key words side by side (k[r].x for word 0, k[r].y for word
+// 1), so a copy in shared memory is read with one 8-byte load per round.
 struct RoundKeys {
-  uint32_t k0[10];
-  uint32_t k1[10];
+  uint2 k[10];
 };
 
 inline RoundKeys make_round_keys(uint64_t seed) {
   RoundKeys K;
   uint32_t a = (uint32_t)(seed & 0xFFFFFFFFu), b = (uint32_t)(seed >> 32);
   for (int r = 0; r < 10; ++r) {
-    K.k0[r] = a;
-    K.k1[r] = b;
+    K.k[r] = make_uint2(a, b);
     a += kWeyl0;
     b += kWeyl1;
   }
@@ -58,8 +58,9 @@ __device__ __forceinline__ Words4 philox(uint32_t x0, uint32_t x1, uint32_t x2,
   for (int r = 0; r < 10; ++r) {
     const uint64_t m0 = (uint64_t)x0 * kPhiloxMul0;
     const uint64_t m1 = (uint64_t)x2 * kPhiloxMul1;
-    const uint32_t y0 = (uint32_t)(m1 >> 32) ^ x1 ^ K.k0[r];
-    const uint32_t y2 = (uint32_t)(m0 >> 32) ^ x3 ^ K.k1[r];
+    const uint2 kr = K.k[r];
+    const uint32_t y0 = (uint32_t)(m1 >> 32) ^ x1 ^ kr.x;
+    const uint32_t y2 = (uint32_t)(m0 >> 32) ^ x3 ^ kr.y;
     x1 = (uint32_t)m1;
     x3 = (uint32_t)m0;
     x0 = y0;
