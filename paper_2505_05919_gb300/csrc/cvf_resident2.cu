@@ -91,12 +91,18 @@ __global__ void __launch_bounds__(kResBlock) k_resident2(LatticeArgs A, long lon
   __shared__ int s_next_g;                  // CTA 0: the gate of the next step
   __shared__ VolumeArgs sV;                 // FP64 parameters for the volume moves
   __shared__ double s_xch;                  // the two volume warps' exchange
-  Ctrl* ctl = A.ctrl;
+  // CTA 0 keeps the lattice's scalar state in shared memory for the whole
+  // call (no other launch touches it meanwhile) and writes it back at the
+  // end, so no step waits on a global-memory round trip
+  __shared__ Ctrl s_ctl;
+  Ctrl* const gctl = A.ctrl;
   const int L = A.L, Lh = L >> 1, R = L / nctas, y0 = rank * R;
   const long long N = (long long)L * L;
   const bool sweeper = threadIdx.x < kResThreads;
-  const long long step0 = ctl->sweep;
-  const int every = ctl->record_every;
+  const long long step0 = gctl->sweep;
+  const int every = gctl->record_every;
+  if (rank == 0 && threadIdx.x == 0) s_ctl = *gctl;
+  Ctrl* const ctl = &s_ctl;  // meaningful in CTA 0 only
   const RoundKeys& K = A.keys;
 
   // own rows from the source buffer of the first step
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(kResBlock) k_resident2(LatticeArgs A, long lon
       uint32_t pk = 0;
       for (int i = threadIdx.x; i < R * Lh; i += kResThreads) {
         const int r = i / Lh, p = i - r * Lh;
-        if (!dcheck(r >= 0 && r < R && p >= 0 && p < Lh, &ctl->error, kSiteResident2)) continue;
+        if (!dcheck(r >= 0 && r < R && p >= 0 && p < Lh, &gctl->error, kSiteResident2)) continue;
         const int y = y0 + r;
         const int hi = (y & 1) ^ colour;  // the cell of this colour in word (y, p)
         const uint32_t own = lat[i];
@@ -207,6 +213,12 @@ __global__ void __launch_bounds__(kResBlock) k_resident2(LatticeArgs A, long lon
     cluster_barrier();  // (3)
   }
 
+  // CTA 0's scalar state back to the handle (every CTA is past its last
+  // index check, so the device error word is final)
+  if (rank == 0 && threadIdx.x == 0) {
+    s_ctl.error = *(volatile unsigned int*)&gctl->error;
+    *gctl = s_ctl;
+  }
   // own rows to the buffer that holds the lattice after the last step
   __syncthreads();
   uint32_t* dst = reinterpret_cast<uint32_t*>(A.state + (size_t)((step0 + n_steps) & 1) * N);
