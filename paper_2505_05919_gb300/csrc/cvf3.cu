@@ -581,12 +581,17 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
   __shared__ int s_next_g, s_plan;
   __shared__ VolumeArgs sV;
   __shared__ double s_xch;
-  Ctrl* ctl = A.ctrl;
+  // CTA 0 keeps the lattice's scalar state in shared memory for the whole
+  // call and writes it back at the end (no global round trip per step)
+  __shared__ Ctrl s_ctl;
+  Ctrl* const gctl = A.ctrl;
   const uint32_t L = A.L, L2 = A.L2, G = A.G, R = L / kRes3Ctas, z0 = rank * R;
   const uint32_t q = A.q, qm1 = q - 1u;
   const bool sweeper = threadIdx.x < kRes3Threads;
-  const long long step0 = ctl->sweep;
-  const int every = ctl->record_every;
+  const long long step0 = gctl->sweep;
+  const int every = gctl->record_every;
+  if (rank == 0 && threadIdx.x == 0) s_ctl = *gctl;
+  Ctrl* const ctl = &s_ctl;  // meaningful in CTA 0 only
   uint32_t* const st = A.state;
 
   for (uint32_t i = threadIdx.x; i < R * L2; i += blockDim.x) cube[i] = st[z0 * L2 + i];
@@ -661,12 +666,12 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
       // index-checked in debug builds
       const uint32_t slab = R * L2;
       auto vec = [&](const uint32_t* base, uint32_t idx, uint32_t n) -> uint4 {
-        return dcheck((idx & 3u) == 0u && idx + 3u < n, &ctl->error, kSiteResident3)
+        return dcheck((idx & 3u) == 0u && idx + 3u < n, &gctl->error, kSiteResident3)
                    ? *reinterpret_cast<const uint4*>(base + idx)
                    : make_uint4(0u, 0u, 0u, 0u);
       };
       auto word = [&](uint32_t idx) -> uint32_t {
-        return dcheck(idx < slab, &ctl->error, kSiteResident3) ? cube[idx] : 0u;
+        return dcheck(idx < slab, &gctl->error, kSiteResident3) ? cube[idx] : 0u;
       };
       for (uint32_t i = threadIdx.x; i < R * L2 / 4u; i += kRes3Threads) {
         const uint32_t c0 = 4u * i;  // local cell of the group
@@ -699,7 +704,7 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
           w3 = update_arm3<CMP64>(w3, nb.w, r.w, sh, nsh, amask, qm1, sProp, sRows, sT64, pk);
         }
         unpack_counts(pk, nacc, hb_b, dc_b);
-        if (dcheck(c0 + 3u < slab, &ctl->error, kSiteResident3))
+        if (dcheck(c0 + 3u < slab, &gctl->error, kSiteResident3))
           *reinterpret_cast<uint4*>(cube + c0) = make_uint4(w0, w1, w2, w3);
         if (rec && j == nseg - 1) hist_group(w0, w1, w2, w3, s_h);
       }
@@ -744,6 +749,12 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
       s_next_g = ctl->next_g;
     }
     cl_barrier();  // the step committed
+  }
+  // CTA 0's scalar state back to the handle (every CTA is past its last
+  // index check, so the device error word is final)
+  if (rank == 0 && threadIdx.x == 0) {
+    s_ctl.error = *(volatile unsigned int*)&gctl->error;
+    *gctl = s_ctl;
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < R * L2; i += blockDim.x) st[z0 * L2 + i] = cube[i];
