@@ -482,6 +482,19 @@ __device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cv
   c->ahead_state = 0;
 }
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with
+// programmatic stream serialization may start while the previous kernel of
+// the stream still runs -- once every block of that kernel has called
+// pdl_trigger or exited -- and pdl_wait blocks until the previous kernel has
+// completed and its writes are visible.  A kernel that calls pdl_wait before
+// any global access computes exactly what it computes after a plain launch;
+// only the launch latency overlaps the previous kernel's tail.  Both are
+// no-ops for a plain launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Atomic add with acquire-release semantics at GPU scope: the caller's
 // earlier writes (and, after a block barrier, its block's) are visible to
 // whoever acquires a later value of the counter, and the caller sees every

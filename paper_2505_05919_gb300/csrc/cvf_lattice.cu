@@ -207,6 +207,8 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
   __shared__ int s_tile, s_next;
   __shared__ uint32_t s_hist4[4];
   __shared__ alignas(8) uint64_t s_bar;
+  pdl_wait();     // the previous step's launch has completed (programmatic launch)
+  pdl_trigger();  // the next step's launch may start while this one runs
   Ctrl* ctl = A.ctrl;
   const int g = ctl->next_g;
   const long long step = ctl->sweep;
@@ -678,7 +680,19 @@ void launch_sweep(const void* fn, int grid, cudaStream_t s, const LatticeArgs& A
                   const CUtensorMap& tm0, const CUtensorMap& tm1) {
   void* args[3] = {const_cast<LatticeArgs*>(&A), const_cast<CUtensorMap*>(&tm0),
                    const_cast<CUtensorMap*>(&tm1)};
-  cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, 0, s);
+  // programmatic stream serialization: the launch overlaps the previous
+  // step's tail; the kernel waits for that step before touching memory
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 // Enqueue one MC step on stream s.
