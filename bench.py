@@ -74,12 +74,12 @@ ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
 # ncu capture of the current kernel; scaled by L^2 for other sizes (the state
 # is read once per step, the writes stay in L2).  Reset to None whenever the
 # kernel changes until a new capture is taken.
-SWEEP_DRAM_BYTES_4096 = 34.15e6
+SWEEP_DRAM_BYTES_4096 = 34.0e6
 # Thread instructions executed per sigma update by k_sweep_tiled at L = 4096
 # (smsp__inst_executed.sum x 32 / (4 L^2) from the same capture): the issue
 # rate the kernel sustains is this times the measured update rate, against
 # the 128 thread-instructions per clock an SM can issue.  None when stale.
-SWEEP_INSTR_PER_UPDATE = 107.173771e6 * 32 / (4 * 4096 * 4096)
+SWEEP_INSTR_PER_UPDATE = 107.177384e6 * 32 / (4 * 4096 * 4096)
 
 
 def dist_env():
