@@ -250,12 +250,6 @@ __device__ __forceinline__ void stage_async16(const StepView<KEYS>& v, const Til
   cp_async_commit();
 }
 
-// Colour 0: tile rows -1 .. th, words 0 .. tw-1 (the colour-0 cell of a word
-// is its low half on even rows, its high half on odd rows), then the one
-// colour-0 cell per row just outside the tile (x0 - 1, high half of word -1,
-// on odd rows; x0 + 2 tw, low half of word tw, on even rows).  Reads S.in,
-// writes S.mid.  s_hist4 != nullptr (recorded steps): N_q' of the tile's
-// cells is counted.
 // Code shape of the colour loops, fixed per kernel at compile time (each
 // kernel uses the combination that ran fastest for it):
 //   kHalfRows  a warp that covers one row compiles its row loop once per half
@@ -291,6 +285,12 @@ __device__ __forceinline__ void dispatch_row(const ROW& row, int hi, bool record
   }
 }
 
+// Colour 0: tile rows -1 .. th, words 0 .. tw-1 (the colour-0 cell of a word
+// is its low half on even rows, its high half on odd rows), then the one
+// colour-0 cell per row just outside the tile (x0 - 1, high half of word -1,
+// on odd rows; x0 + 2 tw, low half of word tw, on even rows).  Reads S.in,
+// writes S.mid.  s_hist4 != nullptr (recorded steps): N_q' of the tile's
+// cells is counted.
 template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, int SHAPE, typename KEYS>
 __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom& g,
                                         TileSmem<TR, TW>& S, const Tables2& Tb,
