@@ -121,16 +121,14 @@ static uint32_t orc_arm(uint16_t word, int arm) {
 /* Lennard-Jones energy per cell (Sec. II.A, Table 1).  Reading: the 2D     */
 /* lattice is a monolayer of thickness r0, so v_iso = r^2 r0 and, in units   */
 /* of r0 and v0 = r0^3, the squared distance of a pair separated by lattice  */
-/* vector d is |d|^2 v_iso.  A pair contributes 4 eps [(1/dist)^12 -         */
-/* (1/dist)^6] when dist < cutoff (strict).  Every cell sees the same        */
+/* vector d is |d|^2 v_iso.  A pair contributes 4 eps [(r0/dist)^12 -        */
+/* (r0/dist)^6] when dist < cutoff (strict).  Every cell sees the same       */
 /* infinite-lattice neighbourhood, so U_LJ = N u(v_iso) with                 */
-/*   u(v) = 1/2 sum_{d != 0, |d|^2 v < cutoff^2} 4 eps [(x/|d|^2)^6 -        */
-/*          (x/|d|^2)^3],  x = v0/v_iso = 1/v,                               */
-/* evaluated as 2 eps [x^6 S12(n) - x^3 S6(n)], where the n shells with      */
-/* |d|^2 v < cutoff^2 are the first n in increasing |d|^2 and S12, S6 are    */
-/* the prefix sums of m/|d|^12 and m/|d|^6 over shells (m = number of        */
-/* lattice vectors in the shell), accumulated in increasing |d|^2.           */
-/* v >= 1 is the hard core.                                                  */
+/*   u(v) = 1/2 sum_{d != 0, |d|^2 v < cutoff^2} 4 eps [(1/(|d|^2 v))^6 -    */
+/*          (1/(|d|^2 v))^3],                                                */
+/* the half giving each cell its share of every pair.  The sum is taken     */
+/* pair by pair, shell by shell (the m lattice vectors of one |d|^2 give     */
+/* equal terms), in increasing |d|^2.  v >= 1 is the hard core.              */
 /* ------------------------------------------------------------------------ */
 #define ORC_MAX_SHELLS 4096
 static int orc_shells(double cutoff, int64_t d2s[], int64_t mult[]) {
@@ -154,29 +152,27 @@ static int orc_shells(double cutoff, int64_t d2s[], int64_t mult[]) {
 }
 
 double orc_lj_cell_energy(double v_iso, double epsilon, double cutoff) {
-  /* the shell list and its prefix sums depend on the cutoff only */
+  /* the shell list depends on the cutoff only */
   static int64_t d2s[ORC_MAX_SHELLS], mult[ORC_MAX_SHELLS];
-  static double S12[ORC_MAX_SHELLS + 1], S6[ORC_MAX_SHELLS + 1];
   static double last_cutoff = -1.0;
   static int n = 0;
   if (cutoff != last_cutoff) {
     n = orc_shells(cutoff, d2s, mult);
-    S12[0] = 0.0;
-    S6[0] = 0.0;
-    for (int s = 0; s < n; ++s) {
-      int64_t d6 = d2s[s] * d2s[s] * d2s[s];
-      S12[s + 1] = S12[s] + (double)mult[s] / ((double)d6 * (double)d6);
-      S6[s + 1] = S6[s] + (double)mult[s] / (double)d6;
-    }
+    if (n < 0) n = 0;
     last_cutoff = cutoff;
   }
   double rc2 = cutoff * cutoff;
-  int k = 0;
-  while (k < n && (double)d2s[k] * v_iso < rc2) ++k;
-  double x = 1.0 / v_iso;
-  double x3 = x * x * x;
-  double x6 = x3 * x3;
-  return (2.0 * epsilon) * (x6 * S12[k] - x3 * S6[k]);
+  double sum = 0.0;
+  for (int s = 0; s < n; ++s) {
+    double dist2 = (double)d2s[s] * v_iso; /* (r / r0)^2 of this shell's pairs */
+    if (!(dist2 < rc2)) break;            /* shells ascend: the rest lie outside */
+    double y = 1.0 / dist2;               /* (r0 / r)^2 */
+    double y3 = y * y * y;                /* (r0 / r)^6 */
+    double y6 = y3 * y3;                  /* (r0 / r)^12 */
+    double pair = (4.0 * epsilon) * (y6 - y3);
+    sum += (double)mult[s] * pair;
+  }
+  return 0.5 * sum;
 }
 
 int orc_shell_table(double cutoff, int64_t *d2s, int64_t *mult, int cap) {

@@ -33,10 +33,11 @@
  *     proposal offset k and the acceptance draw u; the random initial state
  *     is sigma_a(c) = floor(w q / 2^32), w word c mod 4 of
  *     Philox((floor(c / 4), 0, 16 + a));
- *   - Lennard-Jones: r = v_iso^(1/3) (Sec. II.A); a lattice vector d lies
- *     inside the 6 r0 cutoff iff |d|^6 v^2 < 6^6; per cell
- *     u(v) = 2 eps [v^-4 S12(n) - v^-2 S6(n)] with S12, S6 the sums of
- *     m / |d|^12 and m / |d|^6 over the first n shells;
+ *   - Lennard-Jones: r = v_iso^(1/3) (Sec. II.A), so a pair at lattice
+ *     vector d is at distance r |d| and (r0 / dist)^6 = 1 / (|d|^6 v^2); it
+ *     lies inside the 6 r0 cutoff iff |d|^6 v^2 < 6^6 (no cube roots); per
+ *     cell u(v) = 1/2 sum over those pairs of 4 eps [(r0/dist)^12 -
+ *     (r0/dist)^6], taken pair by pair, shell by shell in increasing |d|^2;
  *   - the gate is liquid iff v_iso < 2 (Sec. II.A, gas-like when
  *     v_iso >= 2 v0).
  * Compile: gcc -O2 -std=c11 -ffp-contract=off (with cvf_oracle.c).
@@ -111,28 +112,24 @@ int orc3_shell_table(double cutoff, int64_t *d2s, int64_t *mult, int cap) {
 #define O3_MAX_SHELLS 1024
 double orc3_lj_cell_energy(double v_iso, double epsilon, double cutoff) {
   static int64_t d2s[O3_MAX_SHELLS], mult[O3_MAX_SHELLS];
-  static double S12[O3_MAX_SHELLS + 1], S6[O3_MAX_SHELLS + 1];
   static double last_cutoff = -1.0;
   static int n = 0;
   if (cutoff != last_cutoff) {
     n = orc3_shell_table(cutoff, d2s, mult, O3_MAX_SHELLS);
     if (n < 0) n = 0;
-    S12[0] = 0.0;
-    S6[0] = 0.0;
-    for (int s = 0; s < n; ++s) {
-      int64_t d6 = d2s[s] * d2s[s] * d2s[s];
-      S12[s + 1] = S12[s] + (double)mult[s] / ((double)d6 * (double)d6);
-      S6[s + 1] = S6[s] + (double)mult[s] / (double)d6;
-    }
     last_cutoff = cutoff;
   }
   double rc6 = cutoff * cutoff * cutoff * cutoff * cutoff * cutoff;
-  int k = 0;
-  while (k < n && (double)(d2s[k] * d2s[k] * d2s[k]) * v_iso * v_iso < rc6) ++k;
-  double x = 1.0 / v_iso;
-  double x2 = x * x;
-  double x4 = x2 * x2;
-  return (2.0 * epsilon) * (x4 * S12[k] - x2 * S6[k]);
+  double sum = 0.0;
+  for (int s = 0; s < n; ++s) {
+    double d6v2 = (double)(d2s[s] * d2s[s] * d2s[s]) * v_iso * v_iso; /* (dist / r0)^6 */
+    if (!(d6v2 < rc6)) break; /* shells ascend: the rest lie outside */
+    double y6 = 1.0 / d6v2;   /* (r0 / dist)^6 */
+    double y12 = y6 * y6;     /* (r0 / dist)^12 */
+    double pair = (4.0 * epsilon) * (y12 - y6);
+    sum += (double)mult[s] * pair;
+  }
+  return 0.5 * sum;
 }
 
 /* ------------------------------------------------------------ thresholds -- */

@@ -405,3 +405,59 @@ def test_window_init_run_matches_whole_lattice(init):
     inner = (slice(y0 + m, y0 + H - m), slice(x0 + m, x0 + W - m))
     assert np.array_equal(w[inner], ref.state()[inner])
     assert not w[:y0].any() and not w[:, :x0].any()  # nothing written outside
+
+
+@pytest.mark.parametrize("init,dv,T", [(oracle.INIT_RANDOM, 0.01, 300.0),
+                                       (oracle.INIT_ORDERED, 0.05, 330.0),
+                                       (oracle.INIT_RANDOM, 0.4, 900.0)])
+def test_volume_chain_equals_full_run(init, dv, T):
+    """The V_iso chain run alone (orc_volume_chain, the V reference of the
+    sampled checks at large sizes) reproduces the V_iso and gate of every
+    step of the full MC run up to its first gate-changing proposal, and its
+    acceptance count equals the run's over the steps it covers; with large
+    moves from v = 1.9 the chain must stop early, exactly where the full run
+    meets the first proposal that would change the gate."""
+    L, K = 6, 400
+    op = oracle.physical_params(T, 0.1, L=L, seed=23, init=init, dv_max_frac=dv,
+                                v_iso_init=1.9 if dv > 0.1 else 2 ** (1 / 3))
+    ref = Oracle(op)
+    V0 = ref.observables()["V_iso"]
+    done, V, g, acc = oracle.volume_chain(op, V0, 0, K)
+    rec = ref.run(K, record_every=1)
+    assert len(rec) == K
+    Vr = np.array([r["V_iso"] for r in rec])
+    gr = np.array([r["g"] for r in rec])
+    accr = np.array([r["acc_volume"] for r in rec])
+    assert np.array_equal(V[:done], Vr[:done])
+    assert np.array_equal(g[:done], gr[:done])
+    if done == K:
+        assert acc == accr[-1]
+    else:
+        # step `done` proposes a gate change: recompute that proposal here
+        # from the Philox words (tag 3, cell word 2^32 - 1) and the rule
+        # dV = (2 u1 - 1) dV_max of the volume move
+        r = oracle.philox([0xFFFFFFFF, done & 0xFFFFFFFF, done >> 32, 3],
+                          [op.seed & 0xFFFFFFFF, op.seed >> 32])
+        u1 = ((int(r[0]) << 21) | (int(r[1]) >> 11)) / 2.0 ** 53
+        N = L * L
+        dV = (2.0 * u1 - 1.0) * (dv * N * op.v_iso_init)
+        v_before = (Vr[done - 1] if done > 0 else V0) / N
+        v_new = v_before + dV / N
+        assert v_new >= 1.0 and (v_new < 2.0) != (v_before < 2.0)
+    if dv > 0.1:
+        assert done < K  # this case must exercise the early stop
+
+
+def test_volume_chain3_equals_full_run():
+    """The 3D V_iso chain with the bond count held fixed equals the full
+    cubic run's V_iso at every step while the gate cannot change."""
+    L, K = 4, 300
+    op = oracle.physical_params3(300.0, 0.1, L=L, seed=29)
+    ref = oracle.Oracle3(op)
+    ob = ref.observables()
+    V, acc = oracle.volume_chain3(op, ob["V_iso"], ob["n_hb_raw"], 0, K)
+    rec = ref.run(K, record_every=1)
+    Vr = np.array([r["V_iso"] for r in rec])
+    assert all(r["g"] == 1 for r in rec)
+    assert np.array_equal(V, Vr)
+    assert acc == rec[-1]["acc_volume"]
