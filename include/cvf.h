@@ -223,11 +223,19 @@ int cvf_destroy(cvf_handle *h);
  *                it are copied to host_series[0..series_cap) (at most 256 per
  *                call, else CVF_EINVAL); *n_series receives their number.
  *   host_obs     receives the observables after the last step.
- * The call synchronises `stream`.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call on a device uses the same array and clears
- * what must start at zero, so calls whose GPU work overlaps (other threads,
- * other streams) race with each other: serialise them. */
+ * dev_state must hold valid cells for q (guard bits clear, every nibble < q);
+ * the call checks this on the device and returns CVF_EINVAL after the run
+ * when it does not hold (the lattice is then swept anyway and its contents
+ * are meaningless).  After the stream synchronises the call returns the
+ * lattice's status as cvf_observables does: CVF_ETIMEOUT when a bounded
+ * device wait gave up, CVF_EBOUNDS when an index check of a debug build
+ * failed; *n_series and host_obs are filled in either case.  A launch that
+ * fails ends the call with CVF_ECUDA.
+ * The call synchronises `stream`.  Every call looks up the array's device
+ * address on the current device (cudaGetSymbolAddress), so the address stays
+ * right across a device reset.  Every call on a device uses the same array
+ * and clears what must start at zero, so calls whose GPU work overlaps (other
+ * threads, other streams) race with each other: serialise them. */
 int cvf_sweep_noalloc(const cvf_params *p, void *dev_state, double V_iso,
                       int64_t sweep, int64_t n_sweeps, int32_t record_every,
                       cvf_obs *host_series, int64_t series_cap,
@@ -404,6 +412,21 @@ int cvf3_destroy(cvf3_handle *h);
  * misaligned argument, CVF_ECUDA if the launch fails.
  * ------------------------------------------------------------------------ */
 int cvf_copy_probe(void *dst, const void *src, size_t bytes, void *stream);
+
+/* cvf_philox_probe: enqueue the random-number work of one checkerboard step
+ * and nothing else: for every cell c < n_cells one Philox4x32-10 block with
+ * counter (c, step_lo, step_hi, 0) and key `seed` (the draws R7 assigns to
+ * cell c in MC step `step`; Salmon et al., SC'11), computed by the same
+ * device function as the sweep kernels.  The 4 n_cells words are XOR-folded
+ * into *dev_out (atomic XOR, so the caller zeroes it first; caller-owned
+ * device memory, 4-byte aligned), which keeps every draw live and lets a
+ * test check the words against another Philox implementation.  Timed with
+ * events, 4 n_cells / time is the most sigma updates per second a sweep
+ * that draws one block per cell can reach on this GPU: the measured ceiling
+ * beside which the sweep's rate is reported.  Asynchronous; CVF_EINVAL for
+ * a NULL or misaligned output or a negative step. */
+int cvf_philox_probe(uint64_t seed, uint32_t n_cells, int64_t step, uint32_t *dev_out,
+                     void *stream);
 
 /* 1 if this library was built with device-side index checks (CVF_DEBUG:
  * every kernel checks its shared- and global-memory indices and the TMA

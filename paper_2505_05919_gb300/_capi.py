@@ -74,6 +74,7 @@ _SIGS = {
     "cvf_destroy": (ctypes.c_int, [_vp]),
     "cvf_set_tiles": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "cvf_get_tiles": (ctypes.c_int, [_vp, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_int32)]),
+    "cvf_philox_probe": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, _vp, _vp]),
     "cvf_sweep_noalloc": (ctypes.c_int, [_P(cvf_params), _vp, ctypes.c_double, ctypes.c_int64,
                                          ctypes.c_int64, ctypes.c_int32, _P(cvf_obs), ctypes.c_int64,
                                          _P(ctypes.c_int64), _P(cvf_obs), _vp]),
@@ -392,6 +393,13 @@ def cvf3_get_resident(h: int) -> int:
 def cvf_copy_probe(dst_ptr: int, src_ptr: int, nbytes: int, stream_ptr: int = 0) -> None:
     """Enqueue one 16-byte-vector copy of nbytes between device buffers."""
     _check(load().cvf_copy_probe(dst_ptr, src_ptr, nbytes, stream_ptr or None), "cvf_copy_probe")
+
+
+def cvf_philox_probe(seed: int, n_cells: int, step: int, out_ptr: int, stream_ptr: int = 0) -> None:
+    """Enqueue the Philox draws of one checkerboard step over n_cells cells
+    (nothing else); their words are XOR-folded into the device word out_ptr."""
+    _check(load().cvf_philox_probe(seed, n_cells, step, out_ptr, stream_ptr or None),
+           "cvf_philox_probe")
 
 
 def cvf_wait_probe(flag_ptr: int, target: int, polls: int, stream_ptr: int = 0) -> None:

@@ -254,9 +254,15 @@ struct Ctrl {
   // observables go to the ring) and of the last recorded step
   unsigned long long acc_hist[8];
   long long hist[8];
-  unsigned int error;  // nonzero: a bounded device-side wait gave up
+  unsigned int error;  // nonzero: a bounded device-side wait gave up (bit 0), a
+                       // debug-build index check failed (0x100 + site), or a
+                       // lattice given to the sweep held an invalid cell
+                       // (kStatusBadCell)
   unsigned int pad1;
 };
+
+// Status bit of a lattice that holds a word which is not a valid cell for q.
+constexpr unsigned int kStatusBadCell = 0x200u;
 
 struct VolumeResult {
   double V, u;

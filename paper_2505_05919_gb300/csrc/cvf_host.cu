@@ -24,6 +24,9 @@ void clear_error() { g_last_error.clear(); }
 
 int status_error(int status) {
   if (status == 0) return CVF_OK;
+  if (status & (int)kStatusBadCell)
+    return set_error(CVF_EINVAL, "the lattice holds a word that is not a valid cell for q "
+                     "(a nibble >= q or a guard bit set); the result is meaningless");
   if (status >= 0x100)
     return set_error(CVF_EBOUNDS, "a device index check of a debug build failed (site %d)",
                      status - 0x100);

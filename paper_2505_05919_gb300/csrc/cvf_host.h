@@ -40,7 +40,8 @@ int sm_count();
 
 // The status word of a lattice's observables as a call result: 0 CVF_OK,
 // 1 CVF_ETIMEOUT (a bounded device wait gave up), 0x100 + site CVF_EBOUNDS
-// (a debug build's index check failed at `site`).
+// (a debug build's index check failed at `site`), bit 0x200 CVF_EINVAL (the
+// lattice held a word that is not a valid cell).
 int status_error(int status);
 
 // An NVTX range over one host entry point, named after it, so that a

@@ -8,7 +8,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <vector>
 
@@ -677,8 +676,8 @@ const void* sweep_kernel(int rng_words, bool cmp64, int tile) {
   return sweep_kernel_t<2>(rng_words, cmp64);
 }
 
-void launch_sweep(const void* fn, int grid, cudaStream_t s, const LatticeArgs& A,
-                  const CUtensorMap& tm0, const CUtensorMap& tm1, bool programmatic) {
+cudaError_t launch_sweep(const void* fn, int grid, cudaStream_t s, const LatticeArgs& A,
+                         const CUtensorMap& tm0, const CUtensorMap& tm1, bool programmatic) {
   void* args[3] = {const_cast<LatticeArgs*>(&A), const_cast<CUtensorMap*>(&tm0),
                    const_cast<CUtensorMap*>(&tm1)};
   // programmatic stream serialization: the launch overlaps the previous
@@ -696,15 +695,15 @@ void launch_sweep(const void* fn, int grid, cudaStream_t s, const LatticeArgs& A
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = programmatic ? 1 : 0;
-  cudaLaunchKernelExC(&cfg, fn, args);
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-// Enqueue one MC step on stream s.
-void enqueue_step(cvf_handle* h, cudaStream_t s) {
+// Enqueue one MC step on stream s; returns the launch error, if any.
+cudaError_t enqueue_step(cvf_handle* h, cudaStream_t s) {
   const bool one = h->p.rng_words == 1;
   if (h->p.schedule == CVF_SCHED_CHECKERBOARD) {
-    launch_sweep(sweep_kernel(h->p.rng_words, h->cmp64, h->tile), h->grid_tiles, s, h->args,
-                 h->tm[0], h->tm[1], h->programmatic);
+    return launch_sweep(sweep_kernel(h->p.rng_words, h->cmp64, h->tile), h->grid_tiles, s,
+                        h->args, h->tm[0], h->tm[1], h->programmatic);
   } else {
     for (int j = 0; j < kLayerLaunches; ++j) {
       const int grid = h->grid_layer + (j == 0 ? 1 : 0);  // + the volume block
@@ -717,6 +716,7 @@ void enqueue_step(cvf_handle* h, cudaStream_t s) {
       else
         k_layer<2, true><<<grid, kThreads, 0, s>>>(h->args, j);
     }
+    return cudaGetLastError();
   }
 }
 
@@ -865,8 +865,13 @@ int build_graph(cvf_handle* h) {
   if (h->graph) return CVF_OK;
   cudaGraph_t g = nullptr;
   CVF_CUDA_CHECK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < kGraphSteps; ++i) enqueue_step(h, h->cap_stream);
+  cudaError_t le = cudaSuccess;
+  for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i) le = enqueue_step(h, h->cap_stream);
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return set_error(CVF_ECUDA, "graph capture: launch failed: %s", cudaGetErrorString(le));
+  }
   if (e != cudaSuccess) return set_error(CVF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
   e = cudaGraphInstantiate(&h->graph, g, 0);
   cudaGraphDestroy(g);
@@ -997,7 +1002,7 @@ int cvf_sweep(cvf_handle* h, int64_t n_sweeps, int32_t record_every) {
       left -= h->graph_steps;
     }
   }
-  for (; left > 0; --left) enqueue_step(h, h->stream);
+  for (; left > 0; --left) CVF_CUDA_CHECK(enqueue_step(h, h->stream));
   CVF_CUDA_CHECK(cudaGetLastError());
   h->sweep_host += n_sweeps;
   return CVF_OK;
@@ -1182,15 +1187,27 @@ struct Table48 {
   unsigned long long t[48];
 };
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices];
-
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace cvf {
+
+// Flags (status bit kStatusBadCell in *err) a lattice holding a word that is
+// not a valid cell for q: a guard bit set or a nibble >= q.  The caller's
+// buffer is not checked on the host (that would need a copy).
+__global__ void __launch_bounds__(kThreads) k_check_cells(const uint16_t* __restrict__ state,
+                                                          long long N, uint32_t q,
+                                                          unsigned int* err) {
+  bool bad = false;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const uint32_t w = state[c];
+    bad |= (w & 0x8888u) != 0u || (w & 7u) >= q || ((w >> 4) & 7u) >= q ||
+           ((w >> 8) & 7u) >= q || ((w >> 12) & 7u) >= q;
+  }
+  if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31u) == 0u) atomicOr(err, kStatusBadCell);
+}
 
 // Copies the call's parameters (passed by value) into the scratch and clears
 // the control block.
@@ -1206,22 +1223,17 @@ __global__ void k_noalloc_setup(NoAllocScratch* s, VolumeArgs va, Table48 t) {
 
 namespace {
 
-// Device address of the scratch array on the current device, looked up once
-// per device (host code may not use the array's name as a device address).
+// Device address of the scratch array on the current device, looked up on
+// every call (host code may not use the array's name as a device address;
+// the lookup is cheap, and a context torn down and rebuilt -- a device
+// reset -- may place the array elsewhere, so no address is kept).
 int noalloc_scratch(NoAllocScratch** out) {
-  int dev = 0;
-  CVF_CUDA_CHECK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return set_error(CVF_EINVAL, "device %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr)
-      return set_error(CVF_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
-                       cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = ptr;
-  }
-  *out = reinterpret_cast<NoAllocScratch*>(g_noalloc_ptr[dev]);
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr)
+    return set_error(CVF_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
+                     cudaGetErrorString(e));
+  *out = reinterpret_cast<NoAllocScratch*>(ptr);
   return CVF_OK;
 }
 
@@ -1313,6 +1325,7 @@ extern "C" int cvf_sweep_noalloc(const cvf_params* p, void* dev_state, double V_
   uint16_t* cur = A.state + (size_t)(sweep & 1) * N;
   const int grid_cells = grid_for(N, 8);
   k_noalloc_setup<<<1, 256, 0, st>>>(s, va, t48);
+  k_check_cells<<<grid_cells, kThreads, 0, st>>>(cur, N, A.q, &s->ctrl.error);
   k_set_ctrl<<<1, 32, 0, st>>>(&s->vol, &s->ctrl, V_iso, sweep, N);
   k_recount<<<grid_cells, kThreads, 0, st>>>(cur, p->L, nullptr, &s->ctrl.acc_hb);
   k_commit_counts<<<1, 32, 0, st>>>(&s->ctrl);
@@ -1326,7 +1339,7 @@ extern "C" int cvf_sweep_noalloc(const cvf_params* p, void* dev_state, double V_
   const bool programmatic =
       tile_count(p->L, tile) >= resident_sweep_blocks(cmp64, p->rng_words, tile);
   for (int64_t i = 0; i < n_sweeps; ++i)
-    launch_sweep(fn, grid, st, A, no_map, no_map, programmatic);
+    CVF_CUDA_CHECK(launch_sweep(fn, grid, st, A, no_map, no_map, programmatic));
   CVF_CUDA_CHECK(cudaMemsetAsync(s->hist, 0, sizeof(s->hist), st));
   k_histogram<<<grid_cells, kThreads, 0, st>>>(A.state + (size_t)((sweep + n_sweeps) & 1) * N, N,
                                                s->hist);
@@ -1338,5 +1351,7 @@ extern "C" int cvf_sweep_noalloc(const cvf_params* p, void* dev_state, double V_
                                    cudaMemcpyDeviceToHost, st));
   CVF_CUDA_CHECK(cudaStreamSynchronize(st));
   *n_series = records;
-  return CVF_OK;
+  // a bounded wait that gave up, a failed index check of a debug build, or a
+  // caller lattice holding an invalid cell
+  return status_error(host_obs->status);
 }

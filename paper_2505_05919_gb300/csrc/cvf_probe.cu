@@ -2,9 +2,10 @@
 // the byte-roofline probe (a plain 16-byte vector copy whose event-timed
 // bandwidth on a given working set -- two buffers that fit in L2, or two much
 // larger than L2 -- is the denominator for the sweep's algorithmic bytes,
-// read 2 B + write 2 B per cell and step), and the bounded device wait of the
-// persistent batched sweep run alone on a flag, so that its give-up path is
-// exercised without a fault.
+// read 2 B + write 2 B per cell and step), the random-number ceiling (one
+// Philox4x32-10 block per cell and nothing else: the draws a sweep must
+// make), and the bounded device wait of the persistent batched sweep run
+// alone on a flag, so that its give-up path is exercised without a fault.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -32,6 +33,27 @@ __global__ void __launch_bounds__(kCopyThreads) k_copy16(const uint4* __restrict
     for (int u = 0; u < kCopyUnroll; ++u) dst[i + u * stride] = v[u];
   }
   for (; i < n; i += stride) dst[i] = src[i];
+}
+
+// The random-number ceiling of a sweep: every cell c < n draws the one
+// Philox4x32-10 block a checkerboard step must draw for it, counter (c,
+// step, tag 0), key = the seed, with the same device function the sweep
+// kernels call, and nothing else; the four words of every block are
+// XOR-folded so that no draw can be removed, and each warp adds its fold to
+// *out with one atomic XOR.  Its event-timed rate, four sigma updates per
+// cell, is the most a sweep that draws its numbers this way can reach.
+__global__ void __launch_bounds__(kCopyThreads) k_philox_probe(uint32_t n, uint32_t step_lo,
+                                                               uint32_t step_hi, RoundKeys K,
+                                                               unsigned int* out) {
+  uint32_t fold = 0;
+  const uint32_t stride = gridDim.x * kCopyThreads;
+  for (uint32_t c = blockIdx.x * kCopyThreads + threadIdx.x; c < n; c += stride) {
+    const Words4 r = philox(c, step_lo, step_hi, kTagAccept, K);
+    fold ^= (r.x ^ r.y) ^ (r.z ^ r.w);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fold ^= __shfl_xor_sync(0xFFFFFFFFu, fold, o);
+  if ((threadIdx.x & 31u) == 0u && fold) atomicXor(out, fold);
 }
 
 // One thread waits for *flag >= target exactly as a batched tile waits for
@@ -95,5 +117,27 @@ extern "C" int cvf_copy_probe(void* dst, const void* src, size_t bytes, void* st
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
     return set_error(CVF_ECUDA, "cvf_copy_probe: launch failed: %s", cudaGetErrorString(e));
+  return CVF_OK;
+}
+
+extern "C" int cvf_philox_probe(uint64_t seed, uint32_t n_cells, int64_t step, uint32_t* dev_out,
+                                void* stream) {
+  clear_error();
+  if (!dev_out) return set_error(CVF_EINVAL, "cvf_philox_probe: NULL output word");
+  if (reinterpret_cast<uintptr_t>(dev_out) & 3u)
+    return set_error(CVF_EINVAL, "cvf_philox_probe: output word must be 4-byte aligned");
+  if (step < 0) return set_error(CVF_EINVAL, "cvf_philox_probe: step must be >= 0");
+  if (n_cells == 0) return CVF_OK;
+  // as many 256-thread blocks as are resident at once (8 per SM), each
+  // thread taking cells a grid apart
+  const size_t want = ((size_t)n_cells + kCopyThreads - 1) / kCopyThreads;
+  const size_t cap = (size_t)sm_count() * 8u;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  k_philox_probe<<<grid, kCopyThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      n_cells, (uint32_t)((uint64_t)step & 0xFFFFFFFFu), (uint32_t)((uint64_t)step >> 32),
+      make_round_keys(seed), reinterpret_cast<unsigned int*>(dev_out));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return set_error(CVF_ECUDA, "cvf_philox_probe: launch failed: %s", cudaGetErrorString(e));
   return CVF_OK;
 }

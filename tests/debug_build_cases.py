@@ -60,6 +60,29 @@ def batch(sizes, steps):
             b.observables(i)
 
 
+def noalloc(L, steps):
+    """The allocation-free entry point on a caller-owned state pair (a torch
+    tensor), so its launches run the debug build's index checks too."""
+    import torch
+    from paper_2505_05919_gb300 import _capi
+    op = oracle.physical_params(300.0, 0.1, L=L, seed=L + 11)
+    ref = oracle.Oracle(op)
+    start = ref.state().copy()
+    V0 = ref.observables()["V_iso"]
+    ref.run(steps)
+    N = L * L
+    buf = torch.zeros(2 * N + 8, dtype=torch.int16, device="cuda")
+    base = buf.data_ptr() + (-buf.data_ptr()) % 16
+    off = (base - buf.data_ptr()) // 2
+    buf[off:off + N].copy_(torch.from_numpy(start.reshape(-1).view(np.int16)))
+    torch.cuda.synchronize()
+    _capi.cvf_sweep_noalloc(params_from_dict(asdict(op)), base, V0, 0, steps,
+                            stream=torch.cuda.current_stream().cuda_stream)  # raises on a check
+    h = (steps & 1) * N
+    got = buf[off + h:off + h + N].cpu().numpy().view(np.uint16).reshape(L, L)
+    assert np.array_equal(got, ref.state()), ("noalloc", L)
+
+
 def main():
     from paper_2505_05919_gb300 import _capi
     assert _capi.lib_path() == _build.DEBUG_LIB and _capi.cvf_debug_checks()
@@ -75,6 +98,8 @@ def main():
     for L, res in ((8, 0), (9, 0), (12, 0), (16, 1), (24, 1), (16, 0), (130, 0)):
         cubic(L, 5, res)
     batch([16, 34, 64, 130, 2], 12)
+    noalloc(64, 7)
+    noalloc(130, 6)
     print("debug build: all cases match, no index check failed")
 
 

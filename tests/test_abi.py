@@ -132,6 +132,13 @@ def test_wait_probe_rejects_bad_arguments_on_host(lib, flag, polls):
     assert e.value.code == 1  # CVF_EINVAL, before any device work
 
 
+@pytest.mark.parametrize("out,step", [(0, 0), (4098, 0), (4096, -1)])
+def test_philox_probe_rejects_bad_arguments_on_host(lib, out, step):
+    with pytest.raises(_capi.CvfError) as e:
+        _capi.cvf_philox_probe(1, 64, step, out, 0)
+    assert e.value.code == 1  # CVF_EINVAL, before any device work
+
+
 def test_batch_tile_configs_and_cells_per_thread(lib):
     from paper_2505_05919_gb300.autotune import cells_per_thread
     from paper_2505_05919_gb300.batch import tile_configs

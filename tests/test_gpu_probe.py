@@ -61,3 +61,26 @@ def test_wait_probe_returns_when_the_flag_is_set():
     flag = torch.full((1,), 7, dtype=torch.int32, device="cuda")
     _capi.cvf_wait_probe(flag.data_ptr(), 5, 1 << 14)   # already >= target
     _capi.cvf_wait_probe(flag.data_ptr(), 7, 1)
+
+
+@pytest.mark.parametrize("n,step,seed", [(1, 0, 3), (4097, 5, 3), (256 * 152 * 8 + 33, 1 << 33, 0xDEADBEEF12345)])
+def test_philox_probe_draws_the_sweep_words(n, step, seed):
+    """The random-number ceiling probe computes the very words a step draws:
+    the XOR fold of Philox((c, step, 0), seed) over every cell c < n equals
+    the fold of the oracle's own Philox4x32-10 (an independent
+    implementation, pinned by the published known-answer vectors); every
+    block enters the fold, so no draw is skipped."""
+    import numpy as np
+
+    import oracle
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    want = 0
+    for c in range(n):
+        r = oracle.philox([c, step & 0xFFFFFFFF, step >> 32, 0], key)
+        want ^= int(r[0]) ^ int(r[1]) ^ int(r[2]) ^ int(r[3])
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    _capi.cvf_philox_probe(seed, n, step, out.data_ptr(), s.cuda_stream)
+    s.synchronize()
+    assert int(out.cpu().numpy().view(np.uint32)[0]) == want

@@ -91,3 +91,26 @@ def test_noalloc_rejects_too_many_records():
     with pytest.raises(_capi.CvfError) as e:
         _capi.cvf_sweep_noalloc(p, base, 64 * 1.3, 0, 300, record_every=1, series_cap=300)
     assert e.value.code == _capi.CVF_EINVAL and "256" in str(e.value)
+
+
+def test_noalloc_reports_invalid_cells():
+    """A caller lattice holding a word that is not a valid cell for q is
+    reported as CVF_EINVAL once the call has run (the check runs on the
+    device: the library never copies the caller's buffer to the host)."""
+    import torch
+    L = 8
+    p = params_from_dict(asdict(oracle.physical_params(300.0, 0.1, L=L, seed=1, q=5)))
+    buf = torch.zeros(2 * L * L + 8, dtype=torch.int16, device="cuda")
+    base = buf.data_ptr() + (-buf.data_ptr()) % 16
+    off = (base - buf.data_ptr()) // 2
+    buf[off + 9] = 0x0500  # nibble 2 = 5 >= q
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(_capi.CvfError) as e:
+        _capi.cvf_sweep_noalloc(p, base, L * L * 1.3, 0, 3, stream=stream)
+    assert e.value.code == _capi.CVF_EINVAL
+    # the shared array is cleared by the next call: a valid lattice runs clean
+    buf.zero_()
+    torch.cuda.synchronize()
+    obs, _ = _capi.cvf_sweep_noalloc(p, base, L * L * 1.3, 0, 3, stream=stream)
+    assert obs.status == 0 and obs.sweep == 3
