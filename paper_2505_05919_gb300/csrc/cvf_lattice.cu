@@ -193,7 +193,7 @@ constexpr int kSweepShape = kHalfRows | kUnroll1 | kSplitRec;
 
 template <int RNG_WORDS, bool CMP64, int TILE>
 __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
-    k_sweep_tiled(LatticeArgs A, const __grid_constant__ CUtensorMap tm0,
+    k_sweep_tiled(const __grid_constant__ LatticeArgs A, const __grid_constant__ CUtensorMap tm0,
                   const __grid_constant__ CUtensorMap tm1) {
   constexpr int kTileRows = TileShape<TILE>::R, kTileWords = TileShape<TILE>::W;
   // the volume block uses the tile buffers for its copy of the parameters
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(kThreads) k_layer(LatticeArgs A, int launch) {
         // the draws of arm a, selected without indexing the arrays at run time
         const uint32_t ua = (a == 0) ? acc[0] : (a == 1) ? acc[1] : (a == 2) ? acc[2] : acc[3];
         const uint32_t ka = (a == 0) ? kk[0] : (a == 1) ? kk[1] : (a == 2) ? kk[2] : kk[3];
-        w = update_arm2<CMP64>(w, pa, ua, ka, 4u * (uint32_t)a, Tb, pk);
+        w = update_arm2<CMP64>(w, partner_operand(pa), ua, ka, (uint32_t)a, Tb, pk);
       }
       out = hi ? ((out & 0xFFFFu) | (w << 16)) : ((out & 0xFFFF0000u) | w);
     }

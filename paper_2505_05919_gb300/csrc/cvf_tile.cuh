@@ -19,8 +19,11 @@ namespace cvf {
 
 // Shared tables of one (lattice, step): the proposal for the current q and
 // the threshold rows of the current gate.
-//   prop[8 sigma + k] = ((sigma + 1 + k) mod q) * 0x11111111 (sigma' in every
-//                       nibble)
+//   prop[8 k + sigma] = ((sigma + 1 + k) mod q) * 0x11111111 for k < 7
+//                       (sigma' in every nibble; k <= q - 2 <= 6), and
+//   prop[56 + sigma]  = sigma * 0x11111111 (row k = 7, which no proposal
+//                       offset reaches), so that both words an update needs
+//                       sit at byte offsets 32 k + 4 sigma and 224 + 4 sigma
 //   rows[9 ps + pp]   = {T - 1, packed count change} for the nibble counts ps,
 //                       pp of update_arm2 (entries no move can reach are 0);
 //                       an accepted move adds the change (1 << 20) +
@@ -36,10 +39,18 @@ struct Tables2 {
 // Proposal part of the tables (depends on q only).
 __device__ __forceinline__ void fill_prop2(Tables2& Tb, uint32_t q) {
   for (int e = threadIdx.x; e < 64; e += blockDim.x) {
-    const uint32_t s = (uint32_t)e >> 3, k = (uint32_t)e & 7u;
-    uint32_t sp = s + 1u + k;
-    while (sp >= q) sp -= q;
-    Tb.prop[e] = (s < q && k + 1u < q) ? sp * 0x11111111u : 0u;
+    const uint32_t k = (uint32_t)e >> 3, s = (uint32_t)e & 7u;
+    uint32_t v = 0u;
+    if (s < q) {
+      if (k == 7u) {
+        v = s * 0x11111111u;
+      } else if (k + 1u < q) {
+        uint32_t sp = s + 1u + k;
+        while (sp >= q) sp -= q;
+        v = sp * 0x11111111u;
+      }
+    }
+    Tb.prop[e] = v;
   }
 }
 
@@ -65,28 +76,52 @@ __device__ __forceinline__ void fill_rows2(Tables2& Tb, const unsigned long long
   }
 }
 
-// Metropolis update of arm a (sh = 4a) of a cell word w (sigma_b in nibble
-// b, b = 0..3) against the partner value pa placed in nibble 4 (bits 16..18),
-// with draw u and proposal offset k (Sec. II.C, Eq. H).  The partner is
-// copied into nibbles 4..7 (wn = w | pa * 0x1111); f(v) = (((wn ^ v
-// 0x11111111) | 0x88888888) - 0x11111111) & 0x88888888 has bit 3 of nibble b
-// set iff nibble b differs from v (every nibble is >= 8 before the
-// subtraction, so no borrow crosses a nibble).  So popc f(sigma) = A_s +
-// 4 b_s and popc f(sigma') = A_p + 4 b_p, which index the rows directly.
-template <bool CMP64>
-__device__ __forceinline__ uint32_t update_arm2(uint32_t w, uint32_t pa, uint32_t u, uint32_t k,
-                                                uint32_t sh, const Tables2& Tb, uint32_t& pk) {
-  const uint32_t s = (w >> sh) & 7u;
-  const uint32_t sR = s * 0x11111111u;
-  const uint32_t spR = Tb.prop[s * 8u + k];
-  const uint32_t wn = w | (pa * 0x1111u);
-  const uint32_t fs = (((wn ^ sR) | 0x88888888u) - 0x11111111u) & 0x88888888u;
-  const uint32_t fp = (((wn ^ spR) | 0x88888888u) - 0x11111111u) & 0x88888888u;
+// The 32-bit word at byte offset `off` of a shared table (the offsets below
+// are computed already scaled, so no index arithmetic is added).
+__device__ __forceinline__ uint32_t table_word(const uint32_t* base, uint32_t off) {
+  return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(base) + off);
+}
+
+constexpr uint32_t kNib1 = 0x11111111u;   // 1 in every nibble
+constexpr uint32_t kGuard = 0x88888888u;  // bit 3 of every nibble
+
+// The partner operand of update_arm2 from a partner value pa placed at bits
+// 16..18: pa copied into nibbles 4..7 and bit 3 of every nibble set.
+__device__ __forceinline__ uint32_t partner_operand(uint32_t pa16) {
+  return pa16 * 0x1111u + kGuard;
+}
+
+// Metropolis update of arm a of a cell word w (sigma_b in nibble b, b =
+// 0..3, nibbles 4..7 zero) with draw u and proposal offset k (Sec. II.C,
+// Eq. H).  x is the partner operand: the partner value (arm a^1 of the
+// neighbour in direction a) in nibbles 4..7 and bit 3 of every nibble set.
+// For v = sigma or sigma' (v R = v in every nibble), t = w ^ v R ^ x holds
+// in each nibble 8 + (nibble ^ v), so f(v) = (t - R) & M has bit 3 of nibble
+// b set iff nibble b differs from v (no borrow crosses a nibble).  popc f
+// (sigma) = A_s + 4 b_s and popc f(sigma') = A_p + 4 b_p index the rows
+// directly.  ARM >= 0 fixes a at compile time; ARM = -1 takes it from a_rt.
+template <bool CMP64, int ARM = -1>
+__device__ __forceinline__ uint32_t update_arm2(uint32_t w, uint32_t x, uint32_t u, uint32_t k,
+                                                uint32_t a_rt, const Tables2& Tb, uint32_t& pk) {
+  const uint32_t a = (ARM >= 0) ? (uint32_t)ARM : a_rt;
+  // 4 sigma: the byte offset of sigma's column in the proposal table
+  uint32_t s4;
+  if (ARM == 0)
+    s4 = (w << 2) & 0x1Cu;
+  else if (ARM > 0)
+    s4 = (w >> (4 * ARM - 2)) & 0x1Cu;
+  else
+    s4 = ((w >> (4u * a)) & 7u) << 2;
+  const uint32_t spR = table_word(Tb.prop, (k << 5) + s4);  // sigma' in every nibble
+  const uint32_t sR = table_word(Tb.prop, 224u + s4);       // sigma in every nibble
+  const uint32_t fs = ((w ^ sR ^ x) - kNib1) & kGuard;
+  const uint32_t fp = ((w ^ spR ^ x) - kNib1) & kGuard;
   const uint32_t idx = (uint32_t)__popc(fs) * 9u + (uint32_t)__popc(fp);
   const uint2 row = Tb.rows[idx];
   const bool accept = CMP64 ? ((unsigned long long)u < Tb.T64[idx]) : (u <= row.x);
   if (accept) {
-    w ^= (sR ^ spR) & (0xFu << sh);
+    const uint32_t mask = 0xFu << (4u * a);
+    w = (w & ~mask) | (spR & mask);
     pk += row.y;
   }
   return w;
@@ -128,30 +163,32 @@ __device__ __forceinline__ uint32_t update_in_word(uint32_t own, uint32_t xm_wor
                                                    const KEYS& keys, uint32_t q,
                                                    const Tables2& Tb, uint32_t& pk,
                                                    uint32_t* s_hist4) {
-  // partners, moved to bits 16..18: arm 0 (+x) <-> arm 1 of the +x cell,
-  // arm 1 (-x) <-> arm 0 of the -x cell, arm 2 (+y) <-> arm 3 of the +y cell,
-  // arm 3 (-y) <-> arm 2 of the -y cell
+  // partner operands: arm 0 (+x) <-> arm 1 of the +x cell, arm 1 (-x) <->
+  // arm 0 of the -x cell, arm 2 (+y) <-> arm 3 of the +y cell, arm 3 (-y)
+  // <-> arm 2 of the -y cell; each partner value, masked where it lies,
+  // is copied into nibbles 4..7 by one multiply-add that also sets the
+  // guard bits (the multiplier moves it there from its own nibble)
   const int hi = (HI >= 0) ? HI : hi_rt;
-  uint32_t w, p0, p1, p2, p3;
+  uint32_t w, x0, x1, x2, x3;
   if (hi) {
     w = own >> 16;
-    p0 = (xp_word << 12) & 0x70000u;
-    p1 = (own << 16) & 0x70000u;
-    p2 = (yp_word >> 12) & 0x70000u;
-    p3 = (ym_word >> 8) & 0x70000u;
+    x0 = (xp_word & 0x70u) * 0x1111000u + kGuard;           // nibble 1 of the +x word
+    x1 = (own & 0x7u) * 0x11110000u + kGuard;               // nibble 0 of the own word
+    x2 = ((yp_word >> 12) & 0x70000u) * 0x1111u + kGuard;   // nibble 7 of the +y word
+    x3 = ((ym_word >> 8) & 0x70000u) * 0x1111u + kGuard;    // nibble 6 of the -y word
   } else {
     w = own & 0xFFFFu;
-    p0 = (own >> 4) & 0x70000u;
-    p1 = xm_word & 0x70000u;
-    p2 = (yp_word << 4) & 0x70000u;
-    p3 = (ym_word << 8) & 0x70000u;
+    x0 = ((own >> 4) & 0x70000u) * 0x1111u + kGuard;        // nibble 5 of the own word
+    x1 = (xm_word & 0x70000u) * 0x1111u + kGuard;           // nibble 4 of the -x word
+    x2 = (yp_word & 0x7000u) * 0x11110u + kGuard;           // nibble 3 of the +y word
+    x3 = (ym_word & 0x700u) * 0x111100u + kGuard;           // nibble 2 of the -y word
   }
   uint32_t acc[4], kk[4];
   draws<RNG_WORDS>(c, s_lo, s_hi, keys, q, acc, kk);
-  w = update_arm2<CMP64>(w, p0, acc[0], kk[0], 0u, Tb, pk);
-  w = update_arm2<CMP64>(w, p1, acc[1], kk[1], 4u, Tb, pk);
-  w = update_arm2<CMP64>(w, p2, acc[2], kk[2], 8u, Tb, pk);
-  w = update_arm2<CMP64>(w, p3, acc[3], kk[3], 12u, Tb, pk);
+  w = update_arm2<CMP64, 0>(w, x0, acc[0], kk[0], 0u, Tb, pk);
+  w = update_arm2<CMP64, 1>(w, x1, acc[1], kk[1], 1u, Tb, pk);
+  w = update_arm2<CMP64, 2>(w, x2, acc[2], kk[2], 2u, Tb, pk);
+  w = update_arm2<CMP64, 3>(w, x3, acc[3], kk[3], 3u, Tb, pk);
   if (s_hist4) hist_add_cell(s_hist4, count_word4(w));
   return hi ? ((own & 0xFFFFu) | (w << 16)) : ((own & 0xFFFF0000u) | w);
 }
