@@ -49,7 +49,8 @@ class Params(ctypes.Structure):
                 ("P", ctypes.c_double), ("v_iso_init", ctypes.c_double),
                 ("dv_max_frac", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("init", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("volume_moves", ctypes.c_int32), ("rng_words", ctypes.c_int32)]
+                ("volume_moves", ctypes.c_int32), ("rng_words", ctypes.c_int32),
+                ("eta_moves", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class Obs(ctypes.Structure):
@@ -84,7 +85,9 @@ class State3(ctypes.Structure):
                 ("sweep", ctypes.c_int64), ("n_hb_raw", ctypes.c_int64),
                 ("n_coop", ctypes.c_int64), ("acc_sigma", ctypes.c_int64),
                 ("acc_volume", ctypes.c_int64), ("g", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("table", ctypes.c_uint64 * 66)]
+                ("pad", ctypes.c_int32), ("table", ctypes.c_uint64 * 66),
+                ("eta", ctypes.POINTER(ctypes.c_uint8)), ("ncube", ctypes.c_int64),
+                ("acc_eta", ctypes.c_int64), ("eta_table", ctypes.c_uint64 * 18)]
 
 
 _lib = None
@@ -97,6 +100,7 @@ def lib():
         L = ctypes.CDLL(_LIB)
         P = ctypes.POINTER
         u16p, u32p, u64p = P(ctypes.c_uint16), P(ctypes.c_uint32), P(ctypes.c_uint64)
+        u8p = P(ctypes.c_uint8)
         i32p, i64p, dp = P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_double)
         sigs = {
             "orc_philox4x32_10": (None, [u32p, u32p, u32p]),
@@ -130,8 +134,19 @@ def lib():
             "orc3_threshold_table": (None, [P(Params), u64p]),
             "orc3_recount": (None, [P(Params), u32p, i64p, i64p]),
             "orc3_check_params": (ctypes.c_int, [P(Params)]),
-            "orc3_init": (ctypes.c_int, [P(State3), P(Params), u32p]),
-            "orc3_set": (ctypes.c_int, [P(State3), P(Params), u32p, ctypes.c_double, ctypes.c_int64]),
+            "orc3_init": (ctypes.c_int, [P(State3), P(Params), u32p, u8p]),
+            "orc3_set": (ctypes.c_int, [P(State3), P(Params), u32p, u8p, ctypes.c_double,
+                                        ctypes.c_int64]),
+            "orc3_matchings": (ctypes.c_int, [P(ctypes.c_uint16)]),
+            "orc3_cube_corner_cells": (None, [ctypes.c_int32, ctypes.c_int64, i64p]),
+            "orc3_edge_of": (None, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int, i64p,
+                                    P(ctypes.c_int)]),
+            "orc3_eta_of": (ctypes.c_int, [P(Params), u8p, ctypes.c_int64, ctypes.c_int]),
+            "orc3_eta_table": (None, [P(Params), u64p]),
+            "orc3_eta_moves": (None, [P(State3)]),
+            "orc3_eta_probe": (None, [P(Params), u32p, u8p, ctypes.c_int64, ctypes.c_uint32,
+                                      ctypes.c_int32, u32p, i32p, u64p]),
+            "orc3_recount_eta": (None, [P(Params), u32p, u8p, i64p, i64p]),
             "orc3_volume_move": (None, [P(State3)]),
             "orc3_permutation": (None, [ctypes.c_int, P(ctypes.c_int)]),
             "orc3_layer_order": (None, [P(Params), ctypes.c_int64, P(ctypes.c_int)]),
@@ -142,8 +157,8 @@ def lib():
                                       ctypes.c_int32, u32p, u64p]),
             "orc3_volume_chain": (ctypes.c_int64, [P(Params), ctypes.c_double, ctypes.c_int64,
                                                    ctypes.c_int64, ctypes.c_int64, dp]),
-            "orc3_init_window": (None, [P(Params), u32p] + [ctypes.c_int32] * 6),
-            "orc3_window_run": (None, [P(Params), u32p] + [ctypes.c_int32] * 6 +
+            "orc3_init_window": (None, [P(Params), u32p, u8p] + [ctypes.c_int32] * 6),
+            "orc3_window_run": (None, [P(Params), u32p, u8p] + [ctypes.c_int32] * 6 +
                                 [ctypes.c_int64, ctypes.c_int64, i32p]),
         }
         for name, (res, args) in sigs.items():
@@ -179,6 +194,7 @@ class OracleParams:
     schedule: int = SCHED_CHECKERBOARD
     volume_moves: int = 1
     rng_words: int = 1
+    eta_moves: int = 0      # 3D only: the eta update of App. A
 
     def c(self) -> Params:
         return Params(**asdict(self))
@@ -347,8 +363,10 @@ class Oracle:
 # --------------------------------------------------------------------------
 def params3(**kw) -> OracleParams:
     """3D defaults: v_iso0 = sqrt(2) (the pair minimum r = 2^(1/6) r0 with
-    v = r^3), the layered schedule and one random word per update."""
-    base = dict(L=16, v_iso_init=math.sqrt(2.0), schedule=SCHED_LAYERED, rng_words=1)
+    v = r^3), the layered schedule, one random word per update and the eta
+    moves of App. A (they need an even L; eta_moves=0 gives eta = 1)."""
+    base = dict(L=16, v_iso_init=math.sqrt(2.0), schedule=SCHED_LAYERED, rng_words=1,
+                eta_moves=1)
     base.update(kw)
     return OracleParams(**base)
 
@@ -410,6 +428,57 @@ def arm_probe3(p: OracleParams, w: np.ndarray, cell: int, arm: int, k: int, g: i
     return s_new.value, T.value
 
 
+def matchings3():
+    out = (ctypes.c_uint16 * 9)()
+    n = lib().orc3_matchings(out)
+    return n, list(out)
+
+
+def cube_corner_cells3(L: int, cube: int):
+    out = np.zeros(8, np.int64)
+    lib().orc3_cube_corner_cells(L, cube, _ptr(out, ctypes.c_int64))
+    return list(out)
+
+
+def edge_of3(L: int, cell: int, arm: int):
+    cube, e = ctypes.c_int64(), ctypes.c_int()
+    lib().orc3_edge_of(L, cell, arm, ctypes.byref(cube), ctypes.byref(e))
+    return cube.value, e.value
+
+
+def eta_of3(p: OracleParams, eta: np.ndarray, cell: int, arm: int) -> int:
+    a = np.ascontiguousarray(eta, dtype=np.uint8).reshape(-1)
+    cp = p.c()
+    return lib().orc3_eta_of(ctypes.byref(cp), _ptr(a, ctypes.c_uint8), cell, arm)
+
+
+def eta_table3(p: OracleParams) -> np.ndarray:
+    out = np.zeros(18, np.uint64)
+    cp = p.c()
+    lib().orc3_eta_table(ctypes.byref(cp), _ptr(out, ctypes.c_uint64))
+    return out.reshape(2, 9)
+
+
+def eta_probe3(p: OracleParams, w: np.ndarray, eta: np.ndarray, cube: int, k: int, g: int):
+    a = np.ascontiguousarray(w, dtype=np.uint32).reshape(-1)
+    e = np.ascontiguousarray(eta, dtype=np.uint8).reshape(-1)
+    nw, dhb, T = ctypes.c_uint32(), ctypes.c_int32(), ctypes.c_uint64()
+    cp = p.c()
+    lib().orc3_eta_probe(ctypes.byref(cp), _ptr(a, ctypes.c_uint32), _ptr(e, ctypes.c_uint8), cube,
+                         k, g, ctypes.byref(nw), ctypes.byref(dhb), ctypes.byref(T))
+    return nw.value, dhb.value, T.value
+
+
+def recount3_eta(p: OracleParams, w: np.ndarray, eta: np.ndarray):
+    a = np.ascontiguousarray(w, dtype=np.uint32).reshape(-1)
+    e = np.ascontiguousarray(eta, dtype=np.uint8).reshape(-1)
+    hb, co = ctypes.c_int64(), ctypes.c_int64()
+    cp = p.c()
+    lib().orc3_recount_eta(ctypes.byref(cp), _ptr(a, ctypes.c_uint32), _ptr(e, ctypes.c_uint8),
+                           ctypes.byref(hb), ctypes.byref(co))
+    return hb.value, co.value
+
+
 def volume_chain3(p: OracleParams, V_iso: float, n_hb_raw: int, step0: int, K: int):
     V = np.zeros(K, np.float64)
     cp = p.c()
@@ -419,19 +488,25 @@ def volume_chain3(p: OracleParams, V_iso: float, n_hb_raw: int, step0: int, K: i
 
 
 def window_init_run3(p: OracleParams, w_full: np.ndarray, x0: int, y0: int, z0: int, W: int,
-                     H: int, D: int, step0: int, gates) -> None:
-    """In place on the L^3 array w_full (possibly lazily zeroed): initialise
-    the box's cells by the init rule, then run len(gates) layered steps over
-    the box alone.  Cells more than 2 len(gates) inside the box are then
-    exact; the box must lie inside the cube."""
+                     H: int, D: int, step0: int, gates, eta_full: np.ndarray | None = None) -> None:
+    """In place on the L^3 array w_full (possibly lazily zeroed) and, with eta
+    moves, the L^3/4 cube configurations eta_full: initialise the box's cells
+    (and the cubes with a corner in it) by the init rule, then run len(gates)
+    layered steps over the box alone.  Cells more than 3 len(gates) (2
+    len(gates) without eta moves) inside the box are then exact; the box
+    must lie inside the cube."""
     L = p.L
     assert w_full.dtype == np.uint32 and w_full.flags.c_contiguous and w_full.size == L ** 3
     assert 0 <= x0 and x0 + W <= L and 0 <= y0 and y0 + H <= L and 0 <= z0 and z0 + D <= L
+    eptr = None
+    if p.eta_moves:
+        assert eta_full is not None and eta_full.dtype == np.uint8 and eta_full.size == L ** 3 // 4
+        eptr = eta_full.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
     g = np.ascontiguousarray(gates, dtype=np.int32)
     cp = p.c()
     ptr = w_full.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
-    lib().orc3_init_window(ctypes.byref(cp), ptr, x0, y0, z0, W, H, D)
-    lib().orc3_window_run(ctypes.byref(cp), ptr, x0, y0, z0, W, H, D, step0, len(g),
+    lib().orc3_init_window(ctypes.byref(cp), ptr, eptr, x0, y0, z0, W, H, D)
+    lib().orc3_window_run(ctypes.byref(cp), ptr, eptr, x0, y0, z0, W, H, D, step0, len(g),
                           _ptr(g, ctypes.c_int32))
 
 
@@ -439,21 +514,26 @@ class Oracle3:
     """One cubic lattice advanced by the 3D oracle, step by step."""
 
     def __init__(self, p: OracleParams, state: np.ndarray | None = None,
-                 V_iso: float | None = None, sweep: int = 0):
+                 V_iso: float | None = None, sweep: int = 0, eta: np.ndarray | None = None):
         self.p = p
         self._cp = p.c()
         self.N = p.L ** 3
         self.w = np.zeros(self.N, np.uint32)
+        # cube configurations (App. A), one byte per checkerboard cube
+        self.eta_cfg = np.zeros(max(self.N // 4, 1) if p.eta_moves else 1, np.uint8)
+        eptr = _ptr(self.eta_cfg, ctypes.c_uint8) if p.eta_moves else None
         self.st = State3()
         if state is None:
             rc = lib().orc3_init(ctypes.byref(self.st), ctypes.byref(self._cp),
-                                 _ptr(self.w, ctypes.c_uint32))
+                                 _ptr(self.w, ctypes.c_uint32), eptr)
         else:
             self.w[:] = np.asarray(state, dtype=np.uint32).reshape(-1)
+            if p.eta_moves and eta is not None:
+                self.eta_cfg[:] = np.asarray(eta, dtype=np.uint8).reshape(-1)
             if V_iso is None:
                 V_iso = self.N * p.v_iso_init
             rc = lib().orc3_set(ctypes.byref(self.st), ctypes.byref(self._cp),
-                                _ptr(self.w, ctypes.c_uint32), V_iso, sweep)
+                                _ptr(self.w, ctypes.c_uint32), eptr, V_iso, sweep)
         if rc != 0:
             raise ValueError("oracle rejected the parameters (code %d)" % rc)
 
@@ -478,5 +558,18 @@ class Oracle3:
         L = self.p.L
         return self.w.reshape(L, L, L).copy()
 
+    def eta(self) -> np.ndarray:
+        """The cube configurations 0..8 (empty without eta moves)."""
+        return self.eta_cfg.copy() if self.p.eta_moves else np.zeros(0, np.uint8)
+
+    def eta_moves(self) -> None:
+        lib().orc3_eta_moves(ctypes.byref(self.st))
+
+    @property
+    def acc_eta(self) -> int:
+        return self.st.acc_eta
+
     def recount(self):
+        if self.p.eta_moves:
+            return recount3_eta(self.p, self.w, self.eta_cfg)
         return recount3(self.p, self.w)

@@ -245,6 +245,8 @@ int orc_check_params(const orc_params *p) {
   if (p->schedule != ORC_SCHED_CHECKERBOARD && p->schedule != ORC_SCHED_LAYERED)
     return ORC_EINVAL;
   if (p->rng_words != 1 && p->rng_words != 2) return ORC_EINVAL;
+  /* a square-lattice cell has exactly four neighbours: every eta is 1 */
+  if (p->eta_moves != 0) return ORC_EINVAL;
   return ORC_OK;
 }
 

@@ -34,6 +34,8 @@ typedef struct {
   double v_iso_init, dv_max_frac;
   uint64_t seed;
   int32_t init, schedule, volume_moves, rng_words;
+  int32_t eta_moves; /* 3D only: 1 = the eta update of App. A, 0 = eta = 1 */
+  int32_t pad;
 } orc_params;
 
 typedef struct {
@@ -96,6 +98,12 @@ typedef struct {
   int64_t sweep, n_hb_raw, n_coop, acc_sigma, acc_volume;
   int32_t g, pad;
   uint64_t table[2][3][11];
+  /* eta (App. A): one configuration number 0..8 per checkerboard cube
+     (N / 4 cubes), the move thresholds [g][dN_HB + 4] and the number of
+     accepted cube moves; eta == NULL when eta_moves is 0 (eta = 1) */
+  uint8_t *eta;
+  int64_t ncube, acc_eta;
+  uint64_t eta_table[2][9];
 } orc3_state;
 
 int64_t orc3_neighbour(int32_t L, int64_t c, int arm);
@@ -105,9 +113,20 @@ void orc3_threshold_table(const orc_params *p, uint64_t out[2][3][11]);
 void orc3_recount(const orc_params *p, const uint32_t *w, int64_t *n_hb_raw,
                   int64_t *n_coop);
 int orc3_check_params(const orc_params *p);
-int orc3_init(orc3_state *st, const orc_params *p, uint32_t *w);
-int orc3_set(orc3_state *st, const orc_params *p, uint32_t *w, double V_iso,
-             int64_t sweep);
+int orc3_init(orc3_state *st, const orc_params *p, uint32_t *w, uint8_t *eta);
+int orc3_set(orc3_state *st, const orc_params *p, uint32_t *w, uint8_t *eta,
+             double V_iso, int64_t sweep);
+int orc3_matchings(uint16_t out[9]);
+void orc3_cube_corner_cells(int32_t L, int64_t cube, int64_t cells[8]);
+void orc3_edge_of(int32_t L, int64_t c, int a, int64_t *cube, int *e);
+int orc3_eta_of(const orc_params *p, const uint8_t *eta, int64_t c, int a);
+void orc3_eta_table(const orc_params *p, uint64_t out[2][9]);
+void orc3_eta_moves(orc3_state *st);
+void orc3_eta_probe(const orc_params *p, const uint32_t *w, const uint8_t *eta,
+                    int64_t cube, uint32_t k, int32_t g, uint32_t *cfg_new,
+                    int32_t *dhb, uint64_t *T);
+void orc3_recount_eta(const orc_params *p, const uint32_t *w, const uint8_t *eta,
+                      int64_t *n_hb_raw, int64_t *n_coop);
 void orc3_volume_move(orc3_state *st);
 void orc3_permutation(int idx, int order[6]);
 void orc3_layer_order(const orc_params *p, int64_t step, int order[6]);
@@ -117,10 +136,10 @@ int64_t orc3_run(orc3_state *st, int64_t n, int32_t record_every, orc_obs *ring,
                  int64_t cap);
 void orc3_arm_probe(const orc_params *p, const uint32_t *w, int64_t c, int a,
                     uint32_t k, int32_t g, uint32_t *s_new, uint64_t *T);
-void orc3_init_window(const orc_params *p, uint32_t *w, int32_t x0, int32_t y0, int32_t z0,
-                      int32_t W, int32_t H, int32_t D);
-void orc3_window_run(const orc_params *p, uint32_t *w, int32_t x0, int32_t y0, int32_t z0,
-                     int32_t W, int32_t H, int32_t D, int64_t step0, int64_t K,
+void orc3_init_window(const orc_params *p, uint32_t *w, uint8_t *eta, int32_t x0, int32_t y0,
+                      int32_t z0, int32_t W, int32_t H, int32_t D);
+void orc3_window_run(const orc_params *p, uint32_t *w, uint8_t *eta, int32_t x0, int32_t y0,
+                     int32_t z0, int32_t W, int32_t H, int32_t D, int64_t step0, int64_t K,
                      const int32_t *gates);
 int64_t orc3_volume_chain(const orc_params *p, double V_iso, int64_t n_hb_raw,
                           int64_t step0, int64_t K, double *V_out);

@@ -21,10 +21,24 @@
  *     of cell (1,0,1), so arm 4 points to +z; arm 2 points to +y by the same
  *     pattern (the paper prints no y example), and arm a ^ 1 is the
  *     opposite of arm a;
- *   - eta_ij = 1 for every pair: the checkerboard-cube eta update of App. A
- *     is not built (its allowed cube configurations are given only in a
- *     figure), so up to six bonds per molecule are possible here;
- *   - one MC step: volume move, then six passes, pass i updating arm
+ *   - eta (App. A, with eta_moves = 1): the checkerboard cubes are the unit
+ *     cells whose corner of smallest coordinates has all three coordinates
+ *     even (colour 0) or all odd (colour 1); every molecule is a corner of
+ *     one cube of each colour and every edge lies in exactly one cube, so
+ *     the L^3/4 cubes (L even) partition the 3N edges.  A cube's eta = 0
+ *     edges are one of the nine perfect matchings of the cube graph (each
+ *     corner loses exactly one of its three edges in the cube, so every
+ *     molecule keeps four allowed bonds whatever the other cubes do: the
+ *     nine configurations of App. A), numbered 0..8 in increasing order of
+ *     their 12-bit edge mask.  The eta step of an MC step moves every cube
+ *     by Metropolis: configuration (c + 1 + k) mod 9 with k = floor(r0 8 /
+ *     2^32), accepted iff r1 < T[g][dN_HB + 4], T from dH = -g J_eff dN_HB
+ *     (N_HB is the only term of Eq. H that involves eta), r = Philox((cube,
+ *     step, 5)); the cubes share no edge, so they move together.  Random
+ *     init: configuration floor(r0 9 / 2^32), r = Philox((cube, 0, 0, 6));
+ *     ordered init: configuration 0.  With eta_moves = 0, eta = 1 for every
+ *     pair (up to six bonds per molecule);
+ *   - one MC step: volume move, then eta, then six passes, pass i updating arm
  *     order[i] of every cell; order is permutation number
  *     floor(w 720 / 2^32) of the six arms in lexicographic order, w word 0
  *     of Philox((2^32-2, step, 4));
@@ -146,6 +160,216 @@ void orc3_threshold_table(const orc_params *p, uint64_t out[2][3][11]) {
       }
 }
 
+/* ------------------------------------------------------------------ eta -- */
+#define O3_TAG_ETA 5u
+#define O3_TAG_ETA_INIT 6u
+
+/* Edge e (0..11) of a cube runs along axis d = e / 4 from corner lo to corner
+   lo | (1 << d), lo the (e % 4)-th of the four corners with bit d clear in
+   increasing order; corner j sits at offset (j & 1, (j >> 1) & 1, (j >> 2) &
+   1) from the cube's corner of smallest coordinates. */
+static int o3_edge_lo(int e) {
+  int d = e / 4, k = e % 4, n = 0;
+  for (int j = 0; j < 8; ++j)
+    if (!((j >> d) & 1)) {
+      if (n == k) return j;
+      ++n;
+    }
+  return -1;
+}
+
+/* The nine configurations: the 12-bit masks of the perfect matchings of the
+   cube graph (four edges covering each of the eight corners once), in
+   increasing order.  Returns how many there are. */
+int orc3_matchings(uint16_t out[9]) {
+  int n = 0;
+  for (int m = 0; m < 4096; ++m) {
+    int cover[8] = {0, 0, 0, 0, 0, 0, 0, 0}, edges = 0;
+    for (int e = 0; e < 12; ++e)
+      if ((m >> e) & 1) {
+        int lo = o3_edge_lo(e);
+        cover[lo] += 1;
+        cover[lo | (1 << (e / 4))] += 1;
+        ++edges;
+      }
+    int ok = (edges == 4);
+    for (int j = 0; j < 8; ++j) ok = ok && (cover[j] == 1);
+    if (ok) {
+      if (n < 9) out[n] = (uint16_t)m;
+      ++n;
+    }
+  }
+  return n;
+}
+
+static uint16_t o3_mask(uint8_t cfg) {
+  static uint16_t masks[9];
+  static int ready = 0;
+  if (!ready) {
+    orc3_matchings(masks);
+    ready = 1;
+  }
+  return masks[cfg];
+}
+
+static int64_t o3_mod(int64_t a, int64_t L) { return ((a % L) + L) % L; }
+
+/* Cube index: colour (L/2)^3 + (Z (L/2) + Y) (L/2) + X for the cube whose
+   corner of smallest coordinates is (2X + colour, 2Y + colour, 2Z + colour). */
+static int64_t o3_cube_index(int32_t L, int64_t cx, int64_t cy, int64_t cz) {
+  int64_t H = L / 2, colour = cx & 1;
+  return ((colour * H + (cz >> 1)) * H + (cy >> 1)) * H + (cx >> 1);
+}
+
+void orc3_cube_corner_cells(int32_t L, int64_t cube, int64_t cells[8]) {
+  int64_t H = L / 2;
+  int64_t X = cube % H, Y = (cube / H) % H, Z = (cube / (H * H)) % H, colour = cube / (H * H * H);
+  int64_t cx = 2 * X + colour, cy = 2 * Y + colour, cz = 2 * Z + colour;
+  for (int j = 0; j < 8; ++j) {
+    int64_t x = (cx + (j & 1)) % L, y = (cy + ((j >> 1) & 1)) % L, z = (cz + ((j >> 2) & 1)) % L;
+    cells[j] = (z * L + y) * L + x;
+  }
+}
+
+/* The cube holding the edge of arm a of cell c, and the edge's number in it.
+   The edge joins v (its end of smaller coordinate along axis d = a / 2: c
+   itself for a +d arm, the neighbour for a -d arm) and v + e_d; the cube's
+   corner has v's coordinate along d and, along each other axis, v's
+   coordinate or the one below, whichever has the parity of v_d. */
+void orc3_edge_of(int32_t L, int64_t c, int a, int64_t *cube, int *e) {
+  int d = a >> 1;
+  int64_t v = (a & 1) ? orc3_neighbour(L, c, a) : c;
+  int64_t vc[3] = {v % L, (v / L) % L, v / ((int64_t)L * L)};
+  int64_t cc[3];
+  int j = 0;
+  for (int u = 0; u < 3; ++u) {
+    if (u == d) {
+      cc[u] = vc[u];
+    } else if (((vc[u] - vc[d]) & 1) == 0) {
+      cc[u] = vc[u];
+    } else {
+      cc[u] = o3_mod(vc[u] - 1, L);
+      j |= 1 << u;
+    }
+  }
+  *cube = o3_cube_index(L, cc[0], cc[1], cc[2]);
+  int k = 0;
+  for (int i = 0; i < 8; ++i)
+    if (!((i >> d) & 1)) {
+      if (i == j) break;
+      ++k;
+    }
+  *e = 4 * d + k;
+}
+
+/* eta of the edge of arm a of cell c: 0 if the edge is in its cube's
+   matching, else 1; always 1 without eta moves. */
+int orc3_eta_of(const orc_params *p, const uint8_t *eta, int64_t c, int a) {
+  if (!p->eta_moves || !eta) return 1;
+  int64_t cube;
+  int e;
+  orc3_edge_of(p->L, c, a, &cube, &e);
+  return ((o3_mask(eta[cube]) >> e) & 1) ? 0 : 1;
+}
+
+/* Thresholds of a cube move, [g][dN_HB + 4]: dH = -g J_eff dN_HB (the eta
+   enter Eq. H only through N_HB; the P v_HB N_HB of P V is in J_eff), T =
+   2^32 if dH <= 0, else floor(exp(-dH / kT) 2^32). */
+void orc3_eta_table(const orc_params *p, uint64_t out[2][9]) {
+  double J_eff = p->J - p->P * p->v_HB;
+  for (int g = 0; g < 2; ++g)
+    for (int i = 0; i < 9; ++i) {
+      int dhb = i - 4;
+      double dH = -((double)g * J_eff) * (double)dhb;
+      out[g][i] = (dH <= 0.0) ? ((uint64_t)1 << 32)
+                              : (uint64_t)(exp(-dH / p->kT) * 4294967296.0);
+    }
+}
+
+/* The 12-bit mask of the bonded edges of a cube: bit e set when the +d arm
+   of corner lo and the -d arm of corner lo | (1 << d) are equal. */
+static uint16_t o3_cube_bonds(int32_t L, const uint32_t *w, int64_t cube) {
+  int64_t cells[8];
+  orc3_cube_corner_cells(L, cube, cells);
+  uint16_t b = 0;
+  for (int e = 0; e < 12; ++e) {
+    int d = e / 4, lo = o3_edge_lo(e), hi = lo | (1 << d);
+    if (o3_arm(w[cells[lo]], 2 * d) == o3_arm(w[cells[hi]], 2 * d + 1)) b |= (uint16_t)(1u << e);
+  }
+  return b;
+}
+
+static int o3_popc12(uint16_t m) {
+  int n = 0;
+  for (int e = 0; e < 12; ++e) n += (m >> e) & 1;
+  return n;
+}
+
+/* Decision data of the move of cube `cube` with proposal offset k (0..7)
+   on an explicit configuration: the proposed configuration, the change of
+   N_HB_raw and the threshold. */
+void orc3_eta_probe(const orc_params *p, const uint32_t *w, const uint8_t *eta,
+                    int64_t cube, uint32_t k, int32_t g, uint32_t *cfg_new,
+                    int32_t *dhb, uint64_t *T) {
+  uint64_t table[2][9];
+  orc3_eta_table(p, table);
+  uint16_t b = o3_cube_bonds(p->L, w, cube);
+  uint8_t old = eta[cube];
+  uint8_t nw = (uint8_t)((old + 1u + k) % 9u);
+  /* the edges leaving the matching become allowed bonds, the edges entering
+     it stop counting */
+  int d = o3_popc12((uint16_t)(b & o3_mask(old))) - o3_popc12((uint16_t)(b & o3_mask(nw)));
+  *cfg_new = nw;
+  *dhb = d;
+  *T = table[g][d + 4];
+}
+
+/* Step 2 of the MC step (Sec. II.B, App. A): every cube makes one
+   Metropolis move of its configuration with the sigma fixed. */
+void orc3_eta_moves(orc3_state *st) {
+  const orc_params *p = &st->p;
+  for (int64_t cube = 0; cube < st->ncube; ++cube) {
+    uint32_t r[4];
+    o3_philox(p, (uint32_t)cube, st->sweep, O3_TAG_ETA, r);
+    uint32_t k = o3_scale(r[0], 8u), nw;
+    int32_t dhb;
+    uint64_t T;
+    orc3_eta_probe(p, st->w, st->eta, cube, k, st->g, &nw, &dhb, &T);
+    if ((uint64_t)r[1] < T) {
+      st->eta[cube] = (uint8_t)nw;
+      st->n_hb_raw += dhb;
+      st->acc_eta += 1;
+    }
+  }
+}
+
+/* N_HB_raw with the eta: bonds of the +axis arms whose edge is allowed. */
+void orc3_recount_eta(const orc_params *p, const uint32_t *w, const uint8_t *eta,
+                      int64_t *n_hb_raw, int64_t *n_coop) {
+  int64_t N = (int64_t)p->L * p->L * p->L, hb = 0, co = 0;
+  for (int64_t c = 0; c < N; ++c) {
+    uint32_t wc = w[c];
+    for (int a = 0; a < 6; a += 2)
+      if (o3_arm(wc, a) == o3_arm(w[orc3_neighbour(p->L, c, a)], a + 1) &&
+          orc3_eta_of(p, eta, c, a))
+        ++hb;
+    for (int a = 0; a < 6; ++a)
+      for (int b = a + 1; b < 6; ++b)
+        if (o3_arm(wc, a) == o3_arm(wc, b)) ++co;
+  }
+  *n_hb_raw = hb;
+  *n_coop = co;
+}
+
+/* The initial configuration of a cube: 0 (ordered init) or floor(r0 9 /
+   2^32) with r = Philox((cube, 0, 0, 6)) (random init). */
+static uint8_t o3_eta_init_cfg(const orc_params *p, int64_t cube) {
+  if (p->init != ORC_INIT_RANDOM) return 0;
+  uint32_t r[4];
+  o3_philox(p, (uint32_t)cube, 0, O3_TAG_ETA_INIT, r);
+  return (uint8_t)o3_scale(r[0], 9u);
+}
+
 /* ----------------------------------------------------------------- state -- */
 /* Full count: bonds between arm a of c and arm a^1 of its neighbour (each
    bond once, from its +axis end) and the equal pairs among a cell's six
@@ -172,21 +396,26 @@ int orc3_check_params(const orc_params *p) {
     return ORC_EINVAL;
   if (p->init != ORC_INIT_RANDOM && p->init != ORC_INIT_ORDERED) return ORC_EINVAL;
   if (p->schedule != ORC_SCHED_LAYERED || p->rng_words != 1) return ORC_EINVAL;
+  if (p->eta_moves != 0 && p->eta_moves != 1) return ORC_EINVAL;
+  if (p->eta_moves && (p->L & 1)) return ORC_EINVAL; /* the cube partition needs L even */
   return ORC_OK;
 }
 
-static void o3_start(orc3_state *st, const orc_params *p, uint32_t *w, double V_iso,
-                     int64_t sweep) {
+static void o3_start(orc3_state *st, const orc_params *p, uint32_t *w, uint8_t *eta,
+                     double V_iso, int64_t sweep) {
   memset(st, 0, sizeof(*st));
   st->p = *p;
   st->N = (int64_t)p->L * p->L * p->L;
   st->w = w;
+  st->eta = p->eta_moves ? eta : NULL;
+  st->ncube = p->eta_moves ? st->N / 4 : 0;
   st->V_iso = V_iso;
   st->g = (V_iso / (double)st->N < 2.0) ? 1 : 0;
   st->dV_max = p->dv_max_frac * ((double)st->N * p->v_iso_init);
   st->sweep = sweep;
   orc3_threshold_table(p, st->table);
-  orc3_recount(p, w, &st->n_hb_raw, &st->n_coop);
+  orc3_eta_table(p, st->eta_table);
+  orc3_recount_eta(p, w, st->eta, &st->n_hb_raw, &st->n_coop);
 }
 
 /* The initial word of cell c: every sigma 0 (ordered), or sigma_a =
@@ -199,19 +428,31 @@ static uint32_t o3_init_word(const orc_params *p, int64_t c) {
   return word;
 }
 
-int orc3_init(orc3_state *st, const orc_params *p, uint32_t *w) {
+int orc3_init(orc3_state *st, const orc_params *p, uint32_t *w, uint8_t *eta) {
   int rc = orc3_check_params(p);
   if (rc) return rc;
+  if (p->eta_moves && !eta) return ORC_EINVAL;
   int64_t N = (int64_t)p->L * p->L * p->L;
   for (int64_t c = 0; c < N; ++c) w[c] = o3_init_word(p, c);
-  o3_start(st, p, w, (double)N * p->v_iso_init, 0);
+  if (p->eta_moves)
+    for (int64_t cube = 0; cube < N / 4; ++cube) eta[cube] = o3_eta_init_cfg(p, cube);
+  o3_start(st, p, w, eta, (double)N * p->v_iso_init, 0);
   return ORC_OK;
 }
 
-int orc3_set(orc3_state *st, const orc_params *p, uint32_t *w, double V_iso, int64_t sweep) {
+/* Adopt an explicit configuration: sigma words w and, with eta moves, the
+   cube configurations eta (each 0..8). */
+int orc3_set(orc3_state *st, const orc_params *p, uint32_t *w, uint8_t *eta, double V_iso,
+             int64_t sweep) {
   int rc = orc3_check_params(p);
   if (rc) return rc;
-  o3_start(st, p, w, V_iso, sweep);
+  if (p->eta_moves) {
+    if (!eta) return ORC_EINVAL;
+    int64_t N = (int64_t)p->L * p->L * p->L;
+    for (int64_t cube = 0; cube < N / 4; ++cube)
+      if (eta[cube] > 8) return ORC_EINVAL;
+  }
+  o3_start(st, p, w, eta, V_iso, sweep);
   return ORC_OK;
 }
 
@@ -287,7 +528,8 @@ static void o3_update_arm(orc3_state *st, int64_t c, int a) {
   uint32_t s = o3_arm(wc, a);
   uint32_t sp = (s + 1u + k) % (uint32_t)p->q;
   uint32_t nb = o3_arm(st->w[orc3_neighbour(p->L, c, a)], a ^ 1);
-  int dhb = (sp == nb) - (s == nb);
+  /* an edge with eta = 0 is no bond whatever its two arms (Eq. H) */
+  int dhb = orc3_eta_of(p, st->eta, c, a) ? (sp == nb) - (s == nb) : 0;
   int dc = 0;
   for (int b = 0; b < 6; ++b) {
     if (b == a) continue;
@@ -302,10 +544,12 @@ static void o3_update_arm(orc3_state *st, int64_t c, int a) {
   }
 }
 
-/* One MC step (Sec. II.B): V_iso, then eta (fixed at 1 here), then sigma by
-   six passes over the arm domains in the drawn order. */
+/* One MC step (Sec. II.B): V_iso, then eta (the cube moves; eta = 1 without
+   eta moves), then sigma by six passes over the arm domains in the drawn
+   order. */
 void orc3_step(orc3_state *st) {
   if (st->p.volume_moves) orc3_volume_move(st);
+  if (st->p.eta_moves) orc3_eta_moves(st);
   int order[6];
   orc3_layer_order(&st->p, st->sweep, order);
   for (int pass = 0; pass < 6; ++pass)
@@ -314,36 +558,66 @@ void orc3_step(orc3_state *st) {
 }
 
 /* The initial words of the box x0 <= x < x0 + W, y0 <= y < y0 + H,
-   z0 <= z < z0 + D of the L^3 cube w (inside it; nothing else written). */
-void orc3_init_window(const orc_params *p, uint32_t *w, int32_t x0, int32_t y0, int32_t z0,
-                      int32_t W, int32_t H, int32_t D) {
+   z0 <= z < z0 + D of the L^3 cube w (inside it; nothing else written) and,
+   with eta moves, the initial configurations of every checkerboard cube
+   with a corner in the box. */
+void orc3_init_window(const orc_params *p, uint32_t *w, uint8_t *eta, int32_t x0, int32_t y0,
+                      int32_t z0, int32_t W, int32_t H, int32_t D) {
   const int64_t L = p->L;
   for (int64_t z = z0; z < (int64_t)z0 + D; ++z)
     for (int64_t y = y0; y < (int64_t)y0 + H; ++y)
       for (int64_t x = x0; x < (int64_t)x0 + W; ++x) {
         const int64_t c = (z * L + y) * L + x;
         w[c] = o3_init_word(p, c);
+        if (p->eta_moves && eta)
+          for (int a = 0; a < 6; ++a) {
+            int64_t cube;
+            int e;
+            orc3_edge_of(p->L, c, a, &cube, &e);
+            eta[cube] = o3_eta_init_cfg(p, cube);
+          }
       }
 }
 
 /* K steps over the box alone: step s takes the gate gates[s] (the gate its
-   passes use, after its volume move, which the caller's chain provides) and
-   runs the six passes in the step's drawn order over the box's cells.  A
-   pass moves information by at most one cell along its axis, so a step by at
-   most two along each axis: cells more than 2K inside the box are exact. */
-void orc3_window_run(const orc_params *p, uint32_t *w, int32_t x0, int32_t y0, int32_t z0,
-                     int32_t W, int32_t H, int32_t D, int64_t step0, int64_t K,
+   passes use, after its volume move, which the caller's chain provides),
+   moves the checkerboard cubes that lie wholly inside the box (with eta
+   moves), then runs the six passes in the step's drawn order over the box's
+   cells.  A pass moves information by at most one cell along its axis and a
+   cube move by one, so a step moves it by at most three along each axis:
+   cells more than 3K inside the box are exact (2K without eta moves). */
+void orc3_window_run(const orc_params *p, uint32_t *w, uint8_t *eta, int32_t x0, int32_t y0,
+                     int32_t z0, int32_t W, int32_t H, int32_t D, int64_t step0, int64_t K,
                      const int32_t *gates) {
   orc3_state st;
   memset(&st, 0, sizeof(st));
   st.p = *p;
   st.N = (int64_t)p->L * p->L * p->L;
   st.w = w;
+  st.eta = p->eta_moves ? eta : NULL;
   orc3_threshold_table(p, st.table);
+  orc3_eta_table(p, st.eta_table);
   const int64_t L = p->L;
   for (int64_t s = 0; s < K; ++s) {
     st.sweep = step0 + s;
     st.g = gates[s];
+    if (st.eta) {
+      /* cubes whose corner of smallest coordinates lies in the box with the
+         opposite corner inside too (no wrap) */
+      for (int64_t cz = z0; cz + 1 < (int64_t)z0 + D; ++cz)
+        for (int64_t cy = y0; cy + 1 < (int64_t)y0 + H; ++cy)
+          for (int64_t cx = x0; cx + 1 < (int64_t)x0 + W; ++cx) {
+            if ((cx & 1) != (cy & 1) || (cx & 1) != (cz & 1)) continue;
+            int64_t cube = o3_cube_index(p->L, cx, cy, cz);
+            uint32_t r[4];
+            o3_philox(p, (uint32_t)cube, st.sweep, O3_TAG_ETA, r);
+            uint32_t nw;
+            int32_t dhb;
+            uint64_t T;
+            orc3_eta_probe(p, w, eta, cube, o3_scale(r[0], 8u), st.g, &nw, &dhb, &T);
+            if ((uint64_t)r[1] < T) eta[cube] = (uint8_t)nw;
+          }
+    }
     int order[6];
     orc3_layer_order(p, st.sweep, order);
     for (int pass = 0; pass < 6; ++pass)
