@@ -78,6 +78,11 @@ typedef struct cvf_params {
   int32_t schedule;     /* CVF_SCHED_CHECKERBOARD (default) or CVF_SCHED_LAYERED */
   int32_t volume_moves; /* 1: isobaric volume move each step; 0: fixed V_iso */
   int32_t rng_words;    /* 1: one 32-bit word per update (default); 2: two */
+  int32_t eta_moves;    /* cubic lattice only: 1 = the eta update of App. A
+                           (default of cvf3_params_physical; needs L even),
+                           0 = eta identically 1.  Must be 0 on the square
+                           lattice, where eta is identically 1 */
+  int32_t pad;          /* zero */
 } cvf_params;
 
 /* Observables after a completed step (Eq. V and Eq. H). */
@@ -303,11 +308,30 @@ int cvf_batch_destroy(cvf_batch *b);
  * six bonding indices per cell (Sec. II.A: six nearest neighbours), updated
  * by the layered partition of Sec. II.C -- the six arm domains one after the
  * other, in an order drawn every MC step -- with up to C(6,2) = 15
- * cooperative pairs per cell in Eq. (H).  eta_ij is identically 1 (the
- * checkerboard-cube eta update of App. A is not built).
+ * cooperative pairs per cell in Eq. (H), and (eta_moves = 1) the eta update
+ * of App. A: every molecule keeps exactly four allowed bonds.
+ *   - eta: the checkerboard cubes are the unit cells whose corner of
+ *     smallest coordinates (cx, cy, cz) has all three coordinates even
+ *     (colour 0) or all odd (colour 1); each molecule is a corner of one cube
+ *     of each colour and each edge lies in exactly one cube, so the L^3/4
+ *     cubes (L even) partition the 3N edges.  A cube's configuration is the
+ *     set of its edges with eta = 0: one of the nine perfect matchings of
+ *     the cube graph, numbered 0..8 in increasing order of their 12-bit edge
+ *     mask (edge e runs along axis e / 4 from the (e % 4)-th corner, in
+ *     increasing corner number, whose offset along that axis is 0; corner j
+ *     sits at offset (j & 1, (j >> 1) & 1, (j >> 2) & 1)).  Cube index:
+ *     colour (L/2)^3 + (Z (L/2) + Y) (L/2) + X for the cube at (2X + colour,
+ *     2Y + colour, 2Z + colour).  Step 2 of every MC step moves each cube by
+ *     Metropolis: configuration (c + 1 + k) mod 9, k = floor(r0 8 / 2^32),
+ *     accepted iff r1 < T, T = 2^32 min(1, exp(g J_eff dN_HB / kT)) floored,
+ *     r = Philox((cube, step, 5)); random init takes configuration
+ *     floor(r0 9 / 2^32) of Philox((cube, 0, 0, 6)), ordered init 0.  A bond
+ *     counts in N_HB (and in the sigma moves) only on an edge with eta = 1.
  *   - Layout: cell c = x + L (y + L z), one uint32 word per cell holding
  *     sigma of arm a in bits [4a, 4a+3) -- one nibble per arm, bits 4a+3 and
- *     24..31 zero.  Arms 0..5 =
+ *     24..31 zero in every word the calls below exchange.  (Inside the
+ *     library bit 4a+3 holds the eta of arm a's edge: a caller reading the
+ *     device buffer directly masks it off with 0x777777.)  Arms 0..5 =
  *     left, right, front, back, top, bottom point to +x, -x, +y, -y, +z, -z
  *     (Sec. II.C's coalescing example and Table S1: arm 0 of cell c pairs
  *     with arm 1 of cell c+1, arm 4 of cell (1,0,0) with arm 5 of (1,0,1)).
@@ -323,16 +347,18 @@ int cvf_batch_destroy(cvf_batch *b);
  *     Philox((c / 4, 0, 16 + a)).
  *   - Parameters: cvf_params with L the cube side (2 <= L <= 1024), schedule
  *     CVF_SCHED_LAYERED and rng_words 1 (other values: CVF_EINVAL);
- *     v_iso_init defaults to 2^(1/2) (the pair minimum r = 2^(1/6) r0).
- *   - Observables: cvf_obs as above with N_HB <= 3N, N_sigma <= 15N and the
- *     order parameter M = max N_q' / (6N).
+ *     v_iso_init defaults to 2^(1/2) (the pair minimum r = 2^(1/6) r0);
+ *     eta_moves 1 needs an even L.
+ *   - Observables: cvf_obs as above with N_HB <= 2N with eta moves (3N
+ *     without), N_sigma <= 15N and the order parameter M = max N_q' / (6N).
+ *     n_hb_raw counts the equal arm pairs on edges with eta = 1.
  * Streams, ownership, errors and thread safety as for cvf_handle.
  * ------------------------------------------------------------------------ */
 typedef struct cvf3_handle cvf3_handle;
 
 /* Table 1 parameters at (T_kelvin, P_MPa) for the cubic lattice: as
  * cvf_params_physical with L = 16, v_iso_init = 2^(1/2), the layered
- * schedule and one RNG word per update. */
+ * schedule, one RNG word per update and the eta moves of App. A. */
 int cvf3_params_physical(double T_kelvin, double P_MPa, cvf_params *out);
 
 /* The 66 thresholds [g][dN_HB + 1][dN_sigma + 5] (dN_sigma in -5..5, the
@@ -375,10 +401,20 @@ int cvf3_get_window(cvf3_handle *h, int32_t x0, int32_t y0, int32_t z0, int32_t 
 int cvf3_set_state(cvf3_handle *h, const uint32_t *host, size_t n,
                    double V_iso, int64_t sweep);
 
-/* Recounts N_HB_raw and N_sigma with a separate reduction; synchronises. */
+/* The cube configurations (App. A), n = L^3 / 4 bytes, each 0..8, in the
+ * cube order above.  get copies them to the host; set replaces them (every
+ * value checked on the host, CVF_EINVAL otherwise, and without eta moves),
+ * recounts N_HB_raw and prepares the next volume move.  Checkpoint and
+ * resume: cvf3_set_state, then cvf3_set_eta.  Both synchronise. */
+int cvf3_get_eta(cvf3_handle *h, uint8_t *host, size_t n);
+int cvf3_set_eta(cvf3_handle *h, const uint8_t *host, size_t n);
+
+/* Recounts N_HB_raw (bonds on allowed edges) and N_sigma with a separate
+ * reduction; synchronises. */
 int cvf3_recount(cvf3_handle *h, int64_t *n_hb_raw, int64_t *n_sigma);
 
-/* Device address of the lattice (L^3 words). */
+/* Device address of the lattice (L^3 words; bit 4a+3 of a word holds the
+ * eta of arm a's edge, see the layout above). */
 int cvf3_state_device_ptr(cvf3_handle *h, void **dev_ptr);
 
 /* Form of the sweep: mode 1 keeps the cube in the shared memory of one
@@ -386,8 +422,9 @@ int cvf3_state_device_ptr(cvf3_handle *h, void **dev_ptr);
  * 16 <= L <= 64; the z-planes split among the CTAs), 0 runs the step as four
  * launches over the cube in global memory, -1 chooses.  The results do not depend on
  * the form; the call waits for the stream.  CVF_EINVAL for mode 1 where it
- * does not apply.  The automatic choice (-1, the default at creation) takes
- * the resident form up to L = 24. */
+ * does not apply (and with eta moves, which the resident form does not
+ * run).  The automatic choice (-1, the default at creation) takes the
+ * resident form up to L = 24 without eta moves. */
 int cvf3_set_resident(cvf3_handle *h, int32_t mode);
 int cvf3_get_resident(cvf3_handle *h, int32_t *resident);
 
@@ -415,8 +452,9 @@ int cvf_copy_probe(void *dst, const void *src, size_t bytes, void *stream);
 
 /* cvf_philox_probe: enqueue the random-number work of one checkerboard step
  * and nothing else: for every cell c < n_cells one Philox4x32-10 block with
- * counter (c, step_lo, step_hi, 0) and key `seed` (the draws R7 assigns to
- * cell c in MC step `step`; Salmon et al., SC'11), computed by the same
+ * counter (c, step_lo, step_hi, 0) and key `seed` (the draws of cell c in
+ * MC step `step` with one word per update; Salmon et al., SC'11), computed
+ * by the same
  * device function as the sweep kernels.  The 4 n_cells words are XOR-folded
  * into *dev_out (atomic XOR, so the caller zeroes it first; caller-owned
  * device memory, 4-byte aligned), which keeps every draw live and lets a

@@ -34,7 +34,8 @@ class cvf_params(ctypes.Structure):
                 ("P", ctypes.c_double), ("v_iso_init", ctypes.c_double),
                 ("dv_max_frac", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("init", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("volume_moves", ctypes.c_int32), ("rng_words", ctypes.c_int32)]
+                ("volume_moves", ctypes.c_int32), ("rng_words", ctypes.c_int32),
+                ("eta_moves", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -101,6 +102,8 @@ _SIGS = {
     "cvf3_set_state": (ctypes.c_int, [_vp, _P(ctypes.c_uint32), ctypes.c_size_t, ctypes.c_double,
                                       ctypes.c_int64]),
     "cvf3_recount": (ctypes.c_int, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
+    "cvf3_get_eta": (ctypes.c_int, [_vp, _P(ctypes.c_uint8), ctypes.c_size_t]),
+    "cvf3_set_eta": (ctypes.c_int, [_vp, _P(ctypes.c_uint8), ctypes.c_size_t]),
     "cvf3_state_device_ptr": (ctypes.c_int, [_vp, _P(_vp)]),
     "cvf3_destroy": (ctypes.c_int, [_vp]),
     "cvf3_set_resident": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -362,6 +365,14 @@ def cvf3_get_state(h: int, host_ptr: int, n: int) -> None:
 def cvf3_set_state(h: int, host_ptr: int, n: int, V_iso: float, sweep: int) -> None:
     _check(load().cvf3_set_state(h, ctypes.cast(host_ptr, _P(ctypes.c_uint32)), n, V_iso, sweep),
            "cvf3_set_state")
+
+
+def cvf3_get_eta(h: int, host_ptr: int, n: int) -> None:
+    _check(load().cvf3_get_eta(h, ctypes.cast(host_ptr, _P(ctypes.c_uint8)), n), "cvf3_get_eta")
+
+
+def cvf3_set_eta(h: int, host_ptr: int, n: int) -> None:
+    _check(load().cvf3_set_eta(h, ctypes.cast(host_ptr, _P(ctypes.c_uint8)), n), "cvf3_set_eta")
 
 
 def cvf3_recount(h: int):

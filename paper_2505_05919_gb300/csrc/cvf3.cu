@@ -5,6 +5,17 @@
 // counts of Eq. (H) kept incrementally, and the isobaric volume move of
 // Sec. II.B with the cubic-lattice Lennard-Jones energy.
 //
+// eta (App. A).  The checkerboard cubes are the unit cells whose corner of
+// smallest coordinates has all three coordinates even or all odd; they
+// partition the edges, and each cube's eta = 0 edges are one of the nine
+// perfect matchings of the cube graph (its configuration, one byte per cube
+// in `eta`).  The configurations are the state; every cell word also keeps
+// a copy of the eta of its six edges in the spare bit 3 of each arm's
+// nibble (1 = allowed), so that a pass reads it with the cell.  Step 2 of
+// the MC step (k_eta3, one thread per cube) moves every cube and flips the
+// copies at its corners by atomic XOR; the arm rule then drops the bond term
+// of an edge with eta = 0.  Without eta moves every copy is 1.
+//
 // Launch structure.  A pass over arm a reads, besides the cell's own word,
 // only arm a^1 of the neighbour in direction a.  That arm changes only in
 // the pass over a^1.  So consecutive passes whose arms contain no opposite
@@ -44,6 +55,9 @@ constexpr uint32_t kTagInit0 = 16u;     // random init of arm a: tag 16 + a
 constexpr uint32_t kR7 = 0x1111111u;    // 1 in nibbles 0..6
 constexpr uint32_t kM7 = 0x8888888u;    // bit 3 of nibbles 0..6
 constexpr uint32_t kArmBits = 0x777777u;  // the sigma bits of the six arm nibbles
+constexpr uint32_t kEtaBits = 0x888888u;  // bit 3 of the six arm nibbles: the edges' eta
+constexpr uint32_t kTagEta = 5u;          // cube moves: Philox tag 5
+constexpr uint32_t kTagEtaInit = 6u;      // random initial cube configurations: tag 6
 constexpr int kMaxSide3 = 1024;
 
 // Unsigned division by an invariant d (1 <= d < 2^31) for any 32-bit n,
@@ -83,6 +97,14 @@ struct Args3 {
   uint32_t G;                       // L / 4 (groups per row when L % 4 == 0)
   uint32_t q;
   FastDiv div_G, div_L, div_L2;
+  // eta (App. A): cube configurations (L^3/4 bytes; null without eta moves),
+  // the 12-bit edge masks of the nine configurations, the move thresholds
+  // [g][dN_HB + 4], L / 2 and the number of cubes
+  uint8_t* eta;
+  const unsigned long long* eta_table;
+  uint16_t masks[9];
+  uint32_t H, ncube;
+  FastDiv div_H;
 };
 
 // ---------------------------------------------------------------------------
@@ -150,6 +172,9 @@ struct Row3 {
   uint32_t delta;  // packed count change of an accepted move
 };
 
+// eta: bit 4a+3 of w (the copy of the edge's eta) moved to bit 27; when it
+// is 0 the mask drops the partner's flag from both nibble tests, so b_s =
+// b_p = 0, dN_HB = 0 and the row is the one of the arms alone.
 template <bool CMP64>
 __device__ __forceinline__ uint32_t update_arm3(uint32_t w, uint32_t nw, uint32_t r, uint32_t sh,
                                                 uint32_t nsh, uint32_t amask, uint32_t qm1,
@@ -161,8 +186,9 @@ __device__ __forceinline__ uint32_t update_arm3(uint32_t w, uint32_t nw, uint32_
   const uint32_t sR = s * kR7;
   const uint32_t spR = prop[s * 8u + k];
   const uint32_t wn = w | ((nw << nsh) & 0x7000000u);
-  const uint32_t fs = (((wn ^ sR) | kM7) - kR7) & kM7;
-  const uint32_t fp = (((wn ^ spR) | kM7) - kR7) & kM7;
+  const uint32_t meta = ((w << (24u - sh)) & 0x8000000u) | 0x0888888u;
+  const uint32_t fs = (((wn ^ sR) | kM7) - kR7) & meta;
+  const uint32_t fp = (((wn ^ spR) | kM7) - kR7) & meta;
   const int idx = (int)(__popc(fs) + 10u * (fs >> 27)) - (int)(__popc(fp) + 10u * (fp >> 27)) + 17;
   const Row3 row = rows[idx];
   const bool accept = CMP64 ? ((unsigned long long)u < T64[idx]) : (u <= row.t);
@@ -469,7 +495,8 @@ __global__ void __launch_bounds__(kThreads3, 4) k_pass3(Args3 A, int launch) {
 }
 
 // Random init: sigma_a(c) = floor(w q / 2^32), w word c mod 4 of
-// Philox((c / 4, 0, 0, 16 + a)); ordered init: every sigma 0.
+// Philox((c / 4, 0, 0, 16 + a)); ordered init: every sigma 0.  The eta
+// copies are written afterwards by k_eta_bits3.
 __global__ void __launch_bounds__(kThreads3) k_init3(uint32_t* __restrict__ state, uint32_t N,
                                                       uint32_t groups, uint32_t q, int random,
                                                       RoundKeys K) {
@@ -491,7 +518,8 @@ __global__ void __launch_bounds__(kThreads3) k_init3(uint32_t* __restrict__ stat
 }
 
 // Full count of a lattice: N_HB_raw (arms 0, 2, 4 against arms 1, 3, 5 of
-// the +x, +y, +z neighbours) and N_sigma (equal pairs among the six arms)
+// the +x, +y, +z neighbours, on edges with eta = 1) and N_sigma (equal pairs
+// among the six arms)
 // added to acc2[0], acc2[1]; N_q' added to hist[0..8).  Either may be NULL.
 __global__ void __launch_bounds__(kThreads3) k_count3(const uint32_t* __restrict__ state,
                                                        uint32_t L, uint32_t L2, uint32_t N,
@@ -512,9 +540,10 @@ __global__ void __launch_bounds__(kThreads3) k_count3(const uint32_t* __restrict
     const uint32_t wx = state[(x + 1u == L) ? c + 1u - L : c + 1u];
     const uint32_t wy = state[(y + 1u == L) ? c + L - L2 : c + L];
     const uint32_t wz = state[(z + 1u == L) ? c + L2 - N : c + L2];
-    hb += (uint32_t)(((w >> 0) & 7u) == ((wx >> 4) & 7u));
-    hb += (uint32_t)(((w >> 8) & 7u) == ((wy >> 12) & 7u));
-    hb += (uint32_t)(((w >> 16) & 7u) == ((wz >> 20) & 7u));
+    // a bond counts on an allowed edge only (the eta copy of the +axis arm)
+    hb += (uint32_t)(((w >> 0) & 7u) == ((wx >> 4) & 7u)) & ((w >> 3) & 1u);
+    hb += (uint32_t)(((w >> 8) & 7u) == ((wy >> 12) & 7u)) & ((w >> 11) & 1u);
+    hb += (uint32_t)(((w >> 16) & 7u) == ((wz >> 20) & 7u)) & ((w >> 19) & 1u);
     const uint32_t cnt = count_word(w);
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
@@ -533,6 +562,170 @@ __global__ void __launch_bounds__(kThreads3) k_count3(const uint32_t* __restrict
   }
   __syncthreads();
   if (hist && threadIdx.x < 8 && s_cnt[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// eta (App. A).  Cube (colour, X, Y, Z) has its corner of smallest
+// coordinates at (2X + colour, 2Y + colour, 2Z + colour); corner j sits at
+// offset (j & 1, (j >> 1) & 1, (j >> 2) & 1); edge e runs along axis d = e / 4
+// from corner lo(e) -- the (e % 4)-th corner with bit d clear -- to lo(e) |
+// (1 << d).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int edge_lo(int e) {
+  const int d = e >> 2, k = e & 3;
+  // corners with bit d clear, in increasing order: d = 0: 0 2 4 6; d = 1:
+  // 0 1 4 5; d = 2: 0 1 2 3
+  return (d == 0) ? 2 * k : (d == 1) ? ((k & 1) | ((k >> 1) << 2)) : k;
+}
+
+// The eight corner cells of a cube.
+__device__ __forceinline__ void cube_corners(const Args3& A, uint32_t cube, uint32_t cell[8]) {
+  const uint32_t H = A.H, H2 = H * H;
+  const uint32_t colour = (cube >= H2 * H) ? 1u : 0u;
+  const uint32_t rest = cube - colour * H2 * H;
+  const uint32_t Zc = fdiv(rest, A.div_H);  // Z H + Y
+  const uint32_t X = rest - Zc * H;
+  const uint32_t Z = fdiv(Zc, A.div_H);
+  const uint32_t Y = Zc - Z * H;
+  const uint32_t L = A.L;
+  const uint32_t x0 = 2u * X + colour, y0 = 2u * Y + colour, z0 = 2u * Z + colour;
+  const uint32_t x1 = (x0 + 1u == L) ? 0u : x0 + 1u, y1 = (y0 + 1u == L) ? 0u : y0 + 1u,
+                 z1 = (z0 + 1u == L) ? 0u : z0 + 1u;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    cell[j] = ((j & 4) ? z1 : z0) * A.L2 + ((j & 2) ? y1 : y0) * L + ((j & 1) ? x1 : x0);
+}
+
+// Step 2 of the MC step: one Metropolis move of every cube's configuration
+// with the sigma fixed -- proposal (c + 1 + k) mod 9, k = floor(r0 8 / 2^32),
+// accepted iff r1 < T[g][dN_HB + 4] with r = Philox((cube, step, 5)); the
+// edges leaving the matching become allowed, those entering it forbidden,
+// so dN_HB = |bonded & old| - |bonded & new|.  An accepted move rewrites the
+// cube's byte and flips the eta copies of the changed edges in its corner
+// words (atomic XOR: the other cube of each corner may flip other bits of
+// the same word at the same time); the changes of N_HB_raw go to the step's
+// accumulator.
+__global__ void __launch_bounds__(kThreads3) k_eta3(Args3 A) {
+  __shared__ unsigned long long sT[9];
+  __shared__ uint32_t sMask[9];
+  __shared__ int red[kThreads3 / 32];
+  Ctrl* ctl = A.ctrl;
+  const int g = ctl->next_g;
+  const long long step = ctl->sweep;
+  if (threadIdx.x < 9) {
+    sT[threadIdx.x] = A.eta_table[g * 9 + threadIdx.x];
+    sMask[threadIdx.x] = A.masks[threadIdx.x];
+  }
+  __syncthreads();
+  const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
+  const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
+  int dsum = 0;
+  for (uint32_t cube = blockIdx.x * kThreads3 + threadIdx.x; cube < A.ncube;
+       cube += gridDim.x * kThreads3) {
+    uint32_t cell[8], w[8];
+    cube_corners(A, cube, cell);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      w[j] = dcheck(cell[j] < A.N, &ctl->error, kSiteEta3) ? A.state[cell[j]] : 0u;
+    uint32_t bonds = 0;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) {
+      const int d = e >> 2, lo = edge_lo(e), hi = lo | (1 << d);
+      bonds |= (uint32_t)(((w[lo] >> (8 * d)) & 7u) == ((w[hi] >> (8 * d + 4)) & 7u)) << e;
+    }
+    const uint32_t old = A.eta[cube];
+    const Words4 r = philox(cube, s_lo, s_hi, kTagEta, A.keys);
+    uint32_t nw = old + 1u + __umulhi(r.x, 8u);
+    if (nw >= 9u) nw -= 9u;
+    if (!dcheck(old < 9u, &ctl->error, kSiteEta3)) continue;
+    const uint32_t zo = sMask[old], zn = sMask[nw];
+    const int dhb = __popc(bonds & zo) - __popc(bonds & zn);
+    if ((unsigned long long)r.y < sT[dhb + 4]) {
+      A.eta[cube] = (uint8_t)nw;
+      dsum += dhb;
+      const uint32_t flip = zo ^ zn;
+      uint32_t x[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int e = 0; e < 12; ++e) {
+        const int d = e >> 2, lo = edge_lo(e), hi = lo | (1 << d);
+        const uint32_t f = (flip >> e) & 1u;
+        x[lo] ^= f << (8 * d + 3);   // the +d arm of the low corner
+        x[hi] ^= f << (8 * d + 7);   // the -d arm of the high corner
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (x[j]) atomicXor(&A.state[cell[j]], x[j]);
+    }
+  }
+  // block sum of the changes of N_HB_raw, one atomic per block
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xFFFFFFFFu, dsum, o);
+  if ((threadIdx.x & 31u) == 0u) red[threadIdx.x >> 5] = dsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int i = 0; i < kThreads3 / 32; ++i) t += red[i];
+    if (t) atomicAdd(&ctl->acc_hb, (unsigned long long)(long long)t);
+  }
+}
+
+// Initial cube configurations: floor(r0 9 / 2^32) with r = Philox((cube, 0,
+// 0, 6)) (random init) or 0 (ordered init).
+__global__ void __launch_bounds__(kThreads3) k_eta_init3(uint8_t* eta, uint32_t ncube, int random,
+                                                          RoundKeys K) {
+  for (uint32_t cube = blockIdx.x * kThreads3 + threadIdx.x; cube < ncube;
+       cube += gridDim.x * kThreads3) {
+    uint32_t cfg = 0;
+    if (random) cfg = __umulhi(philox(cube, 0u, 0u, kTagEtaInit, K).x, 9u);
+    eta[cube] = (uint8_t)cfg;
+  }
+}
+
+// The eta copies of every cell word from the cube configurations (all 1
+// without eta moves).  The edge of arm a of cell (x, y, z) joins v and v +
+// e_d (d = a / 2; v is the cell for a +d arm, its -d neighbour otherwise);
+// its cube has v's coordinate along d and, along each other axis u, v_u or
+// v_u - 1, whichever has the parity of v_d; the edge's number follows from
+// v's corner in that cube.
+__global__ void __launch_bounds__(kThreads3) k_eta_bits3(Args3 A) {
+  for (uint32_t c = blockIdx.x * kThreads3 + threadIdx.x; c < A.N; c += gridDim.x * kThreads3) {
+    const uint32_t L = A.L;
+    const uint32_t z = fdiv(c, A.div_L2);
+    const uint32_t rem = c - z * A.L2;
+    const uint32_t y = fdiv(rem, A.div_L);
+    const uint32_t x = rem - y * L;
+    uint32_t bits = kEtaBits;
+    if (A.eta) {
+      bits = 0u;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const int d = a >> 1;
+        uint32_t v[3] = {x, y, z};
+        if (a & 1) v[d] = (v[d] == 0u) ? L - 1u : v[d] - 1u;
+        uint32_t cc[3];
+        int j = 0;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          if (u == d || ((v[u] ^ v[d]) & 1u) == 0u) {
+            cc[u] = v[u];
+          } else {
+            cc[u] = (v[u] == 0u) ? L - 1u : v[u] - 1u;
+            j |= 1 << u;
+          }
+        }
+        const uint32_t colour = v[d] & 1u;
+        const uint32_t cube = ((colour * A.H + (cc[2] >> 1)) * A.H + (cc[1] >> 1)) * A.H + (cc[0] >> 1);
+        // rank of corner j among the corners with bit d clear
+        const int k = (d == 0) ? (j >> 1) : (d == 1) ? ((j & 1) | ((j >> 2) << 1)) : j;
+        const int e = 4 * d + k;
+        uint32_t cfg = 0u;
+        if (dcheck(cube < A.ncube, &A.ctrl->error, kSiteEta3)) cfg = A.eta[cube];
+        const uint32_t forbidden = (cfg < 9u) ? ((uint32_t)A.masks[cfg] >> e) & 1u : 0u;
+        bits |= (forbidden ^ 1u) << (4 * a + 3);
+      }
+    }
+    A.state[c] = (A.state[c] & kArmBits) | bits;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -828,9 +1021,51 @@ int check_params3(const cvf_params* p) {
     return set_error(CVF_EINVAL, "the cubic lattice runs the layered schedule only");
   if (p->rng_words != 1)
     return set_error(CVF_EINVAL, "the cubic lattice draws one word per update (rng_words 1)");
+  if (p->eta_moves != 0 && p->eta_moves != 1)
+    return set_error(CVF_EINVAL, "eta_moves=%d must be 0 or 1", p->eta_moves);
+  if (p->eta_moves && (p->L & 1))
+    return set_error(CVF_EINVAL, "L=%d: the eta update of the checkerboard cubes needs an even L",
+                     p->L);
   cvf_params t = *p;
-  t.L = 2;  // the side rules of the square lattice do not apply here
+  t.L = 2;          // the side rules of the square lattice do not apply here
+  t.eta_moves = 0;  // nor its eta rule
   return check_params(&t);
+}
+
+// The nine configurations of a checkerboard cube: the 12-bit masks of the
+// perfect matchings of the cube graph (four edges covering each corner
+// once), in increasing order; edge e runs along axis e / 4 from the (e %
+// 4)-th corner with that axis's bit clear.
+void cube_matchings(uint16_t out[9]) {
+  int n = 0;
+  for (uint32_t m = 0; m < 4096u && n < 9; ++m) {
+    if (__builtin_popcount(m) != 4) continue;
+    int cover[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int e = 0; e < 12; ++e) {
+      if (!((m >> e) & 1u)) continue;
+      const int d = e / 4, k = e % 4;
+      int lo = -1, seen = 0;
+      for (int j = 0; j < 8 && lo < 0; ++j)
+        if (!((j >> d) & 1) && seen++ == k) lo = j;
+      cover[lo] += 1;
+      cover[lo | (1 << d)] += 1;
+    }
+    bool ok = true;
+    for (int j = 0; j < 8; ++j) ok = ok && cover[j] == 1;
+    if (ok) out[n++] = (uint16_t)m;
+  }
+}
+
+// Thresholds of a cube move [g][dN_HB + 4]: dH = -g J_eff dN_HB, T = 2^32
+// when dH <= 0, else floor(exp(-dH/kT) 2^32).
+void eta_table3(const cvf_params* p, unsigned long long out[18]) {
+  const double J_eff = p->J - p->P * p->v_HB;
+  for (int g = 0; g < 2; ++g)
+    for (int i = 0; i < 9; ++i) {
+      const double dH = -((double)g * J_eff) * (double)(i - 4);
+      out[g * 9 + i] = (dH <= 0.0) ? (1ull << 32)
+                                   : (unsigned long long)(std::exp(-dH / p->kT) * 4294967296.0);
+    }
 }
 
 void threshold_table3(const cvf_params* p, uint64_t out[66]) {
@@ -915,6 +1150,8 @@ struct cvf3_handle {
   unsigned long long* table_dev;
   VolumeArgs* vol_dev;
   unsigned long long* rc_dev;  // 10 counters: N_q'[8], N_HB_raw, N_sigma
+  uint8_t* eta;                // cube configurations (eta moves only)
+  unsigned long long* eta_table_dev;
   void* host_pinned;
   Args3 args;
   bool cmp64;
@@ -922,6 +1159,7 @@ struct cvf3_handle {
   bool resident;  // the cube stays in one cluster's shared memory during a call
   int grid;
   int grid_count;
+  int grid_eta;
   cudaGraphExec_t graph;
 };
 
@@ -937,6 +1175,8 @@ void release3(cvf3_handle* h) {
   if (h->table_dev) cudaFree(h->table_dev);
   if (h->vol_dev) cudaFree(h->vol_dev);
   if (h->rc_dev) cudaFree(h->rc_dev);
+  if (h->eta) cudaFree(h->eta);
+  if (h->eta_table_dev) cudaFree(h->eta_table_dev);
   if (h->host_pinned) cudaFreeHost(h->host_pinned);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
@@ -948,6 +1188,7 @@ const void* pass_kernel(bool aligned, bool cmp64) {
 }
 
 void enqueue_step3(cvf3_handle* h, cudaStream_t s) {
+  if (h->eta) k_eta3<<<h->grid_eta, kThreads3, 0, s>>>(h->args);  // step 2: eta
   for (int j = 0; j < kLaunches3; ++j) {
     const int grid = h->grid + (j == 0 ? 1 : 0);
     if (h->aligned) {
@@ -981,9 +1222,11 @@ int build_graph3(cvf3_handle* h) {
 }
 
 // Count the lattice into the control block (committed N_HB_raw, N_sigma) and
-// prepare the next volume move.
+// prepare the next volume move; the cell words' eta copies are rewritten
+// from the cube configurations first.
 int recount_into_ctrl3(cvf3_handle* h) {
   static_assert(offsetof(Ctrl, acc_pairs) == offsetof(Ctrl, acc_hb) + 8, "layout");
+  k_eta_bits3<<<h->grid_count, kThreads3, 0, h->stream>>>(h->args);
   k_count3<<<h->grid_count, kThreads3, 0, h->stream>>>(h->state, h->args.L, h->args.L2,
                                                         h->args.N, h->args.div_L, h->args.div_L2,
                                                         &h->ctrl->acc_hb, nullptr);
@@ -1004,6 +1247,7 @@ int cvf3_params_physical(double T_kelvin, double P_MPa, cvf_params* out) {
   out->v_iso_init = std::sqrt(2.0);
   out->schedule = CVF_SCHED_LAYERED;
   out->rng_words = 1;
+  out->eta_moves = 1;
   return CVF_OK;
 }
 
@@ -1061,6 +1305,10 @@ int cvf3_create(const cvf_params* p, void* stream, void* dev_state, cvf3_handle*
   CREATE_CHECK(cudaMalloc(&h->vol_dev, sizeof(VolumeArgs)));
   CREATE_CHECK(cudaMalloc(&h->rc_dev, sizeof(unsigned long long) * 10));
   CREATE_CHECK(cudaMallocHost(&h->host_pinned, 4096));
+  if (p->eta_moves) {
+    CREATE_CHECK(cudaMalloc(&h->eta, (size_t)(h->N / 4)));
+    CREATE_CHECK(cudaMalloc(&h->eta_table_dev, sizeof(unsigned long long) * 18));
+  }
 
   uint64_t table[66];
   threshold_table3(p, table);
@@ -1092,6 +1340,18 @@ int cvf3_create(const cvf_params* p, void* stream, void* dev_state, cvf3_handle*
   A.div_G = make_fastdiv(h->aligned ? A.G : 1u);
   A.div_L = make_fastdiv(L);
   A.div_L2 = make_fastdiv(L * L);
+  A.eta = h->eta;
+  A.eta_table = h->eta_table_dev;
+  cube_matchings(A.masks);
+  A.H = L / 2u;
+  A.ncube = p->eta_moves ? (uint32_t)(h->N / 4) : 0u;
+  A.div_H = make_fastdiv(A.H > 0u ? A.H : 1u);
+  if (p->eta_moves) {
+    unsigned long long et[18];
+    eta_table3(p, et);
+    CREATE_CHECK(cudaMemcpyAsync(h->eta_table_dev, et, sizeof(et), cudaMemcpyHostToDevice,
+                                 h->stream));
+  }
 
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel(h->aligned, h->cmp64),
@@ -1100,15 +1360,22 @@ int cvf3_create(const cvf_params* p, void* stream, void* dev_state, cvf3_handle*
     per_sm = 1;
   const long long blocks = ((long long)A.groups + kThreads3 - 1) / kThreads3;
   h->grid = (int)std::max<long long>(1, std::min<long long>(blocks, (long long)sm_count() * per_sm));
-  h->resident = (int)L <= kRes3AutoSide && resident3_fits(A, h->cmp64);
+  // the resident form does not run the eta step
+  h->resident = !p->eta_moves && (int)L <= kRes3AutoSide && resident3_fits(A, h->cmp64);
   h->grid_count = (int)std::max<long long>(
       1, std::min<long long>((h->N + kThreads3 - 1) / kThreads3, (long long)sm_count() * 8));
+  h->grid_eta = (int)std::max<long long>(
+      1, std::min<long long>((h->N / 4 + kThreads3 - 1) / kThreads3, (long long)sm_count() * 8));
 
   const int gi = (int)std::max<long long>(
       1, std::min<long long>(((long long)A.groups + kThreads3 - 1) / kThreads3,
                              (long long)sm_count() * 8));
   k_init3<<<gi, kThreads3, 0, h->stream>>>(h->state, A.N, A.groups, A.q,
                                             p->init == CVF_INIT_RANDOM ? 1 : 0, A.keys);
+  if (p->eta_moves)
+    k_eta_init3<<<h->grid_eta, kThreads3, 0, h->stream>>>(h->eta, A.ncube,
+                                                           p->init == CVF_INIT_RANDOM ? 1 : 0,
+                                                           A.keys);
   k_set_ctrl<<<1, 32, 0, h->stream>>>(h->vol_dev, h->ctrl, (double)h->N * p->v_iso_init, 0,
                                       h->N);
   rc = recount_into_ctrl3(h);
@@ -1204,6 +1471,7 @@ int cvf3_get_state(cvf3_handle* h, uint32_t* host, size_t n) {
   CVF_CUDA_CHECK(cudaMemcpyAsync(host, h->state, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost,
                                  h->stream));
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i < n; ++i) host[i] &= kArmBits;  // drop the eta copies
   return CVF_OK;
 }
 
@@ -1225,6 +1493,8 @@ int cvf3_get_window(cvf3_handle* h, int32_t x0, int32_t y0, int32_t z0, int32_t 
                                      cudaMemcpyDeviceToHost, h->stream));
   }
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  const size_t n = (size_t)W * H * D;
+  for (size_t i = 0; i < n; ++i) host[i] &= kArmBits;  // drop the eta copies
   return CVF_OK;
 }
 
@@ -1266,6 +1536,34 @@ int cvf3_set_state(cvf3_handle* h, const uint32_t* host, size_t n, double V_iso,
   return CVF_OK;
 }
 
+int cvf3_get_eta(cvf3_handle* h, uint8_t* host, size_t n) {
+  NvtxRange nvtx_range("cvf3_get_eta");
+  if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");
+  if (!h->eta) return set_error(CVF_EINVAL, "the lattice was created without eta moves");
+  if ((long long)n != h->N / 4)
+    return set_error(CVF_EINVAL, "n=%zu, the lattice has %lld cubes", n, h->N / 4);
+  CVF_CUDA_CHECK(cudaMemcpyAsync(host, h->eta, n, cudaMemcpyDeviceToHost, h->stream));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  return CVF_OK;
+}
+
+int cvf3_set_eta(cvf3_handle* h, const uint8_t* host, size_t n) {
+  NvtxRange nvtx_range("cvf3_set_eta");
+  if (!h || !host) return set_error(CVF_EINVAL, "NULL argument");
+  if (!h->eta) return set_error(CVF_EINVAL, "the lattice was created without eta moves");
+  if ((long long)n != h->N / 4)
+    return set_error(CVF_EINVAL, "n=%zu, the lattice has %lld cubes", n, h->N / 4);
+  for (size_t i = 0; i < n; ++i)
+    if (host[i] > 8u)
+      return set_error(CVF_EINVAL, "cube %zu: configuration %u, need 0..8", i, (unsigned)host[i]);
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  CVF_CUDA_CHECK(cudaMemcpyAsync(h->eta, host, n, cudaMemcpyHostToDevice, h->stream));
+  int rc = recount_into_ctrl3(h);
+  if (rc) return rc;
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  return CVF_OK;
+}
+
 int cvf3_recount(cvf3_handle* h, int64_t* n_hb_raw, int64_t* n_sigma) {
   NvtxRange nvtx_range("cvf3_recount");
   if (!h || !n_hb_raw || !n_sigma) return set_error(CVF_EINVAL, "NULL argument");
@@ -1287,10 +1585,10 @@ int cvf3_recount(cvf3_handle* h, int64_t* n_hb_raw, int64_t* n_sigma) {
 int cvf3_set_resident(cvf3_handle* h, int32_t mode) {
   if (!h) return set_error(CVF_EINVAL, "handle is NULL");
   if (mode < -1 || mode > 1) return set_error(CVF_EINVAL, "mode %d: need -1, 0 or 1", mode);
-  const bool fits = resident3_fits(h->args, h->cmp64);
+  const bool fits = !h->eta && resident3_fits(h->args, h->cmp64);
   if (mode == 1 && !fits)
-    return set_error(CVF_EINVAL, "the resident form needs L a multiple of %d, %d <= L <= %d",
-                     kRes3Ctas, 2 * kRes3Ctas, kRes3MaxSide);
+    return set_error(CVF_EINVAL, "the resident form needs L a multiple of %d, %d <= L <= %d, "
+                     "and no eta moves", kRes3Ctas, 2 * kRes3Ctas, kRes3MaxSide);
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
   h->resident = (mode == 1) || (mode == -1 && fits && h->p.L <= kRes3AutoSide);
   return CVF_OK;

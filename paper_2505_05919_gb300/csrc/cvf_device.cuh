@@ -597,6 +597,7 @@ enum DebugSite : unsigned int {
   kSiteResident3 = 7,   // cubic lattice resident in one cluster
   kSiteBatchItem = 8,   // batched sweep: decoded replica and tile of a work item
   kSiteLayer = 9,       // layered square-lattice passes
+  kSiteEta3 = 10,       // cubic lattice: cube moves and eta copies
 };
 
 #ifdef CVF_DEBUG

@@ -59,6 +59,10 @@ int check_params(const cvf_params* p) {
     return set_error(CVF_EINVAL, "volume_moves=%d must be 0 or 1", p->volume_moves);
   if (p->rng_words != 1 && p->rng_words != 2)
     return set_error(CVF_EINVAL, "rng_words=%d must be 1 or 2", p->rng_words);
+  if (p->eta_moves != 0)
+    return set_error(CVF_EINVAL, "eta_moves=%d: the square lattice has eta = 1 on every edge "
+                     "(four neighbours per cell); eta moves exist on the cubic lattice only",
+                     p->eta_moves);
   return CVF_OK;
 }
 

@@ -14,7 +14,7 @@ from ._capi import cvf_params
 
 def params3(T_kelvin: float = 300.0, P_MPa: float = 0.1, **overrides) -> cvf_params:
     """Table 1 parameters at (T, P) for the cubic lattice (L = 16,
-    v_iso0 = 2^(1/2), layered schedule), with field overrides."""
+    v_iso0 = 2^(1/2), layered schedule, eta moves), with field overrides."""
     p = _capi.cvf3_params_physical(T_kelvin, P_MPa)
     for k, v in overrides.items():
         if not hasattr(p, k):
@@ -67,6 +67,19 @@ class Lattice3:
     def set_state(self, words, V_iso: float, sweep: int = 0) -> None:
         a = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).reshape(-1))
         _capi.cvf3_set_state(self.h, a.ctypes.data, a.size, float(V_iso), int(sweep))
+
+    def eta(self) -> np.ndarray:
+        """The cube configurations 0..8 of the eta update (L^3 / 4 bytes;
+        empty without eta moves)."""
+        if not self.p.eta_moves:
+            return np.zeros(0, np.uint8)
+        out = np.empty(self.N // 4, np.uint8)
+        _capi.cvf3_get_eta(self.h, out.ctypes.data, out.size)
+        return out
+
+    def set_eta(self, cfg) -> None:
+        a = np.ascontiguousarray(np.asarray(cfg, dtype=np.uint8).reshape(-1))
+        _capi.cvf3_set_eta(self.h, a.ctypes.data, a.size)
 
     def recount(self):
         return _capi.cvf3_recount(self.h)

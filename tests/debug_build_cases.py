@@ -38,7 +38,9 @@ def square(L, steps, tiles=-1, **kw):
 
 
 def cubic(L, steps, resident=-1):
-    op = oracle.physical_params3(300.0, 0.1, L=L, seed=L + 3, dv_max_frac=0.05)
+    # eta moves where they apply (even side, launch form)
+    eta = 0 if (L % 2 or resident == 1) else 1
+    op = oracle.physical_params3(300.0, 0.1, L=L, seed=L + 3, dv_max_frac=0.05, eta_moves=eta)
     ref = oracle.Oracle3(op)
     ref.run(steps)
     with Lattice3(params_from_dict(asdict(op))) as lat:
@@ -46,6 +48,7 @@ def cubic(L, steps, resident=-1):
             lat.set_resident(resident)
         lat.sweep(steps)
         assert np.array_equal(lat.state(), ref.state()), ("cubic", L, resident)
+        assert np.array_equal(lat.eta(), ref.eta()), ("cubic eta", L, resident)
         lat.observables()
 
 

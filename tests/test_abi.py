@@ -150,3 +150,20 @@ def test_batch_tile_configs_and_cells_per_thread(lib):
 
 def test_release_build_has_no_debug_checks(lib):
     assert not _capi.cvf_debug_checks()
+
+
+def test_eta_moves_only_on_an_even_cubic_lattice(lib):
+    p = _capi.cvf_params_physical(300.0, 0.1)
+    assert p.eta_moves == 0
+    p.eta_moves = 1   # the square lattice has eta = 1 on every edge
+    with pytest.raises(_capi.CvfError) as e:
+        _capi.cvf_threshold_table(p)
+    assert e.value.code == _capi.CVF_EINVAL
+    p3 = _capi.cvf3_params_physical(300.0, 0.1)
+    assert p3.eta_moves == 1
+    _capi.cvf3_threshold_table(p3)
+    p3.L = 5
+    with pytest.raises(_capi.CvfError):
+        _capi.cvf3_threshold_table(p3)
+    p3.eta_moves = 0
+    _capi.cvf3_threshold_table(p3)

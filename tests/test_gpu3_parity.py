@@ -33,22 +33,29 @@ def _same(got, want, ctx=""):
 
 
 def _run_both(op, steps, record_every=0):
+    """The cube run on the GPU and by the oracle: (state, observables,
+    recount, series, eta configurations) of each."""
     ref = oracle.Oracle3(op)
     want_series = ref.run(steps, record_every)
     with Lattice3(params_from_dict(asdict(op))) as lat:
         lat.sweep(steps, record_every)
         got_series, overflow = lat.drain()
         assert not overflow
-        return (lat.state(), lat.observables(), lat.recount(), got_series), \
-               (ref.state(), ref.observables(), ref.recount(), want_series)
+        return (lat.state(), lat.observables(), lat.recount(), got_series, lat.eta()), \
+               (ref.state(), ref.observables(), ref.recount(), want_series, ref.eta())
 
 
-@pytest.mark.parametrize("L", [2, 3, 4, 5, 6, 8, 12, 16])
+# (L, eta moves): odd sides run with eta = 1 (the cube partition needs an even L)
+SIDES = [(2, 1), (3, 0), (4, 1), (4, 0), (5, 0), (6, 1), (8, 1), (12, 1), (16, 1), (16, 0)]
+
+
+@pytest.mark.parametrize("L,eta", SIDES)
 @pytest.mark.parametrize("init", [oracle.INIT_RANDOM, oracle.INIT_ORDERED])
-def test_lattice3_matches_oracle(L, init):
-    op = oracle.physical_params3(300.0, 0.1, L=L, init=init, seed=100 + L)
+def test_lattice3_matches_oracle(L, eta, init):
+    op = oracle.physical_params3(300.0, 0.1, L=L, init=init, seed=100 + L, eta_moves=eta)
     got, want = _run_both(op, 45)
     assert np.array_equal(got[0], want[0])
+    assert np.array_equal(got[4], want[4])   # the cube configurations (eta)
     _same(got[1], want[1], (L, init))
     assert got[2] == want[2] == (want[1]["n_hb_raw"], want[1]["n_coop"])
 
@@ -59,12 +66,14 @@ def test_lattice3_state_points(T, P, q):
     op = oracle.physical_params3(T, P, L=8, q=q, seed=int(T) + q, dv_max_frac=0.05)
     got, want = _run_both(op, 40)
     assert np.array_equal(got[0], want[0])
+    assert np.array_equal(got[4], want[4])
     _same(got[1], want[1], (T, P, q))
 
 
 @pytest.mark.parametrize("L,every", [(5, 3), (8, 1), (12, 7)])
 def test_lattice3_series_matches_oracle(L, every):
-    op = oracle.physical_params3(285.0, 10.0, L=L, seed=7 + L, dv_max_frac=0.05)
+    op = oracle.physical_params3(285.0, 10.0, L=L, seed=7 + L, dv_max_frac=0.05,
+                                 eta_moves=1 - L % 2)
     got, want = _run_both(op, 70, record_every=every)
     assert len(got[3]) == len(want[3]) == 70 // every
     for i, (g, w) in enumerate(zip(got[3], want[3])):
@@ -75,11 +84,13 @@ def test_lattice3_series_matches_oracle(L, every):
 def test_lattice3_gate_flips(L, P, kT):
     # small hot cubes near v = 2 whose volume moves cross the liquid/gas gate,
     # so the move of the next step is sometimes decided only after the bonds
-    op = oracle.params3(L=L, kT=kT, P=P, epsilon=0.0, v_iso_init=1.9, dv_max_frac=0.2, seed=31)
+    op = oracle.params3(L=L, kT=kT, P=P, epsilon=0.0, v_iso_init=1.9, dv_max_frac=0.2, seed=31,
+                        eta_moves=1 - L % 2)
     got, want = _run_both(op, 300, record_every=1)
     gates = [r["g"] for r in want[3]]
     assert sum(a != b for a, b in zip(gates, gates[1:])) >= 3
     assert np.array_equal(got[0], want[0])
+    assert np.array_equal(got[4], want[4])
     for i, (g, w) in enumerate(zip(got[3], want[3])):
         _same(g, w, ("record", i))
 
@@ -90,8 +101,10 @@ def test_lattice3_cmp64_ground_state():
     assert (oracle.threshold_table3(op) == 0).any()
     got, want = _run_both(op, 40)
     assert not got[0].any() and np.array_equal(got[0], want[0])
+    assert np.array_equal(got[4], want[4])
     _same(got[1], want[1])
-    assert got[1]["n_hb_raw"] == 3 * 512 and got[1]["n_coop"] == 15 * 512
+    # every allowed edge bonded: 2N of them with eta (3N without)
+    assert got[1]["n_hb_raw"] == 2 * 512 and got[1]["n_coop"] == 15 * 512
 
 
 def test_lattice3_checkpoint_resume():
@@ -102,12 +115,15 @@ def test_lattice3_checkpoint_resume():
     ref = oracle.Oracle3(op)
     ref.run(50)
     with Lattice3(params_from_dict(asdict(op))) as lat:
-        lat.sweep(3)                     # overwritten by set_state
+        lat.sweep(3)                     # overwritten by set_state and set_eta
         lat.set_state(mid.state(), ob["V_iso"], ob["sweep"])
+        lat.set_eta(mid.eta())
+        assert np.array_equal(lat.eta(), mid.eta())
         assert lat.observables()["n_hb_raw"] == ob["n_hb_raw"]
         lat.sweep(33)
-        s, o = lat.state(), lat.observables()
+        s, o, e = lat.state(), lat.observables(), lat.eta()
     assert np.array_equal(s, ref.state())
+    assert np.array_equal(e, ref.eta())
     want = ref.observables()
     for k in ("sweep", "n_hb_raw", "n_coop", "g", "n_state"):
         assert o[k] == want[k], k
@@ -124,6 +140,26 @@ def test_lattice3_calls_split_like_one_run():
             lat.sweep(n)
         assert np.array_equal(lat.state(), ref.state())
         _same(lat.observables(), ref.observables())
+
+
+def test_lattice3_rejects_bad_eta():
+    op = oracle.physical_params3(300.0, 0.1, L=4, q=6)
+    with Lattice3(params_from_dict(asdict(op))) as lat:
+        cfg = lat.eta()
+        assert cfg.size == 16 and cfg.max() <= 8
+        bad = cfg.copy()
+        bad[3] = 9
+        with pytest.raises(_capi.CvfError):
+            lat.set_eta(bad)
+        with pytest.raises(_capi.CvfError):
+            lat.set_eta(cfg[:-1])
+        assert np.array_equal(lat.eta(), cfg)
+    with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=4, eta_moves=0)))) as lat:
+        with pytest.raises(_capi.CvfError):
+            lat.set_eta(np.zeros(16, np.uint8))
+    with pytest.raises(_capi.CvfError):  # eta moves need an even side
+        Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=5, eta_moves=0))
+                                  | {"eta_moves": 1}))
 
 
 def test_lattice3_rejects_bad_state():
@@ -147,6 +183,7 @@ def test_lattice3_large_cubes(L, steps):
     op = oracle.physical_params3(300.0, 0.1, L=L, seed=3)
     got, want = _run_both(op, steps)
     assert np.array_equal(got[0], want[0])
+    assert np.array_equal(got[4], want[4])
     _same(got[1], want[1], L)
 
 
@@ -163,7 +200,7 @@ def test_lattice3_resident_cluster(L, steps, extra):
     """The cube resident in one thread-block cluster for each call gives the
     oracle's lattice, counts, N_q' and recorded series (and the same as the
     four-launch form)."""
-    extra = dict(extra)
+    extra = dict(extra, eta_moves=0)   # the resident form runs the eta = 1 model
     if "kT" in extra:
         op = oracle.params3(L=L, seed=500 + L, **extra)
     else:
@@ -190,10 +227,14 @@ def test_lattice3_resident_cluster(L, steps, extra):
 
 
 def test_lattice3_resident_choice():
-    with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=16)))) as lat:
-        assert lat.resident()              # small cubes run resident by default
+    with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=16, eta_moves=0)))) as lat:
+        assert lat.resident()              # small cubes without eta run resident by default
         lat.set_resident(0)
         assert not lat.resident()
+    with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=16)))) as lat:
+        assert not lat.resident()          # the eta step runs in the launch form
+        with pytest.raises(_capi.CvfError):
+            lat.set_resident(1)
     with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=12)))) as lat:
         assert not lat.resident()          # 12 is not a multiple of 8
         with pytest.raises(_capi.CvfError):
@@ -226,7 +267,7 @@ def test_lattice3_maximum_size_sampled_boxes(L):
     if free < 4 * L ** 3 + (4 << 30):
         pytest.skip("needs %.1f GB of free device memory" % (4 * L ** 3 / 1e9 + 4))
     K = 2
-    op = oracle.physical_params3(300.0, 0.1, L=L, seed=23)
+    op = oracle.physical_params3(300.0, 0.1, L=L, seed=23, eta_moves=1 - L % 2)
     N = L ** 3
     with Lattice3(params_from_dict(asdict(op))) as lat:
         ob0 = lat.observables()
@@ -237,19 +278,43 @@ def test_lattice3_maximum_size_sampled_boxes(L):
     gates = [int(v / N < 2.0) for v in V]
     assert all(gg == ob0["g"] for gg in gates)   # no gate change: the chain needs no bonds
     assert abs(o["V_iso"] - V[-1]) <= REL * V[-1] and o["acc_volume"] == acc
-    assert 0 < o["n_hb_raw"] <= 3 * N and 0 < o["n_coop"] <= 15 * N
-    margin, inner = 2 * K + 2, 16
+    assert 0 < o["n_hb_raw"] <= (2 if op.eta_moves else 3) * N and 0 < o["n_coop"] <= 15 * N
+    # a step carries information two cells along each axis, three with eta moves
+    margin, inner = (3 if op.eta_moves else 2) * K + 2, 16
     W = inner + 2 * margin
     rng = np.random.default_rng(L)
     spots = [(0, 0, 0), (L - W, L - W, L - W), (L - W, 0, L - W), (0, L - W, 0)]
     spots += [tuple(int(v) for v in rng.integers(0, L - W, 3)) for _ in range(4)]
     lazy = np.zeros(N, np.uint32)  # only the boxes' pages are ever touched
+    lazy_eta = np.zeros(N // 4 if op.eta_moves else 1, np.uint8)
     cube = lazy.reshape(L, L, L)
     with Lattice3(params_from_dict(asdict(op))) as lat:
         lat.sweep(K)
         for x0, y0, z0 in spots:
-            oracle.window_init_run3(op, lazy, x0, y0, z0, W, W, W, 0, gates)
+            oracle.window_init_run3(op, lazy, x0, y0, z0, W, W, W, 0, gates,
+                                    lazy_eta if op.eta_moves else None)
             want = cube[z0 + margin:z0 + margin + inner, y0 + margin:y0 + margin + inner,
                         x0 + margin:x0 + margin + inner]
             got = lat.window(x0 + margin, y0 + margin, z0 + margin, inner, inner, inner)
             assert np.array_equal(got, want), (x0, y0, z0)
+
+
+@pytest.mark.parametrize("T,P,init", [(270.0, 0.1, oracle.INIT_RANDOM), (330.0, 50.0, oracle.INIT_RANDOM),
+                                      (300.0, 0.1, oracle.INIT_ORDERED)])
+def test_lattice3_eta_every_step(T, P, init):
+    """The eta update of App. A on the GPU follows the oracle step by step:
+    the cube configurations, the recorded counts of every step (N_HB_raw
+    counts bonds on allowed edges only) and the final lattice."""
+    op = oracle.physical_params3(T, P, L=8, seed=71, init=init, dv_max_frac=0.05)
+    ref = oracle.Oracle3(op)
+    with Lattice3(params_from_dict(asdict(op))) as lat:
+        assert np.array_equal(lat.eta(), ref.eta())      # the initial configurations
+        for chunk in (1, 2, 5, 40):
+            want = ref.run(chunk, 1)
+            lat.sweep(chunk, 1)
+            got, _ = lat.drain()
+            for g, w in zip(got, want):
+                _same(g, w, (T, P, chunk))
+            assert np.array_equal(lat.eta(), ref.eta())
+        assert np.array_equal(lat.state(), ref.state())
+    assert ref.acc_eta > 0
