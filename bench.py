@@ -61,25 +61,91 @@ def parse():
                     help="steps per replica in the batched measurement (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=8.0,
                     help="time budget of the serving measurement (0: skip)")
+    ap.add_argument("--record-counters", default=None,
+                    help="write the sweep's counters file from this ncu CSV and exit")
     return ap.parse_args()
 
 
-# Algorithmic integer work of one sigma update with one Philox call per
-# cell: a quarter of a Philox4x32-10 call (10 rounds of two 32x32->64
-# multiplies and two 3-input XORs = 40 ops per cell) plus about 20 ops of the
-# update rule.  Peak: 152 SMs x 128 integer lanes x the 2070 MHz maximum clock.
-ALU_OPS_PER_UPDATE = 30.0
-ALU_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
-# DRAM bytes (read + write) of one k_sweep_tiled launch at L = 4096, from one
-# ncu capture of the current kernel; scaled by L^2 for other sizes (the state
-# is read once per step, the writes stay in L2).  Reset to None whenever the
-# kernel changes until a new capture is taken.
-SWEEP_DRAM_BYTES_4096 = 34.0e6
-# Thread instructions executed per sigma update by k_sweep_tiled at L = 4096
-# (smsp__inst_executed.sum x 32 / (4 L^2) from the same capture): the issue
-# rate the kernel sustains is this times the measured update rate, against
-# the 128 thread-instructions per clock an SM can issue.  None when stale.
-SWEEP_INSTR_PER_UPDATE = 107.177384e6 * 32 / (4 * 4096 * 4096)
+# Issue-rate peak: 152 SMs x 128 thread-instructions per clock x the 2070 MHz
+# maximum clock (four schedulers of one warp-instruction per clock per SM).
+ISSUE_PEAK_T = 152 * 128 * 2.070e9 / 1e12
+
+# Counters of one k_sweep_tiled launch at 4096^2 (ncu: DRAM read + write
+# bytes, executed warp instructions), recorded by `bench.py --record-counters`
+# from an ncu capture together with a hash of the sweep kernel's sources; the
+# bench uses them only while that hash matches the current sources (null
+# otherwise: the kernel changed since the capture).
+COUNTERS_FILE = os.path.join(ROOT, "profiles", "k_sweep_tiled_L4096_counters.json")
+SWEEP_SOURCES = ("paper_2505_05919_gb300/csrc/cvf_tile.cuh", "paper_2505_05919_gb300/csrc/cvf_lattice.cu",
+                 "paper_2505_05919_gb300/csrc/cvf_lattice.cuh", "paper_2505_05919_gb300/csrc/cvf_device.cuh",
+                 "paper_2505_05919_gb300/csrc/cvf_tma.cuh", "include/cvf.h")
+
+
+def sweep_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def sweep_counters():
+    """The recorded counters of the current sweep kernel, or None."""
+    try:
+        d = json.load(open(COUNTERS_FILE))
+    except Exception:
+        return None
+    return d if d.get("source_hash") == sweep_source_hash() else None
+
+
+def record_counters(csv_path: str) -> int:
+    """Write COUNTERS_FILE from an ncu CSV (--csv --log-file) of one
+    k_sweep_tiled launch at 4096^2 with the metrics dram__bytes_read.sum,
+    dram__bytes_write.sum and smsp__inst_executed.sum."""
+    import csv
+    rows = [r for r in csv.reader(open(csv_path)) if len(r) > 5]
+    hdr = rows[0]
+    im, iv, ik = hdr.index("Metric Name"), hdr.index("Metric Value"), hdr.index("Kernel Name")
+    vals = {}
+    for r in rows[1:]:
+        if "k_sweep_tiled" in r[ik]:
+            vals[r[im]] = float(r[iv].replace(",", ""))
+    cells = 4096 * 4096
+    out = {"kernel": "k_sweep_tiled<1, 0, 0> (one MC step of the 4096^2 lattice, q = 6, 300 K)",
+           "source_hash": sweep_source_hash(), "cells": cells,
+           "dram_bytes": vals["dram__bytes_read.sum"] + vals["dram__bytes_write.sum"],
+           "inst_executed_warp": vals["smsp__inst_executed.sum"],
+           "instructions_per_update": vals["smsp__inst_executed.sum"] * 32 / (4 * cells),
+           "capture": os.path.basename(csv_path)}
+    with open(COUNTERS_FILE, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out))
+    return 0
+
+
+def philox_ceiling(stream, n_cells, reps=50):
+    """Event-timed rate of the random-number work of one step alone
+    (cvf_philox_probe: one Philox4x32-10 block per cell, four sigma updates
+    per block), in sigma-updates/ns: the most a sweep that draws its numbers
+    this way can reach on this GPU."""
+    import torch
+    from paper_2505_05919_gb300 import _capi
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    sp = stream.cuda_stream
+    for i in range(3):
+        _capi.cvf_philox_probe(3, n_cells, i, out.data_ptr(), sp)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(reps):
+        _capi.cvf_philox_probe(3, n_cells, 100 + i, out.data_ptr(), sp)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return 4.0 * n_cells / (ms * 1e6), ms
 
 
 def dist_env():
@@ -284,12 +350,6 @@ PAPER_3D_MS_PER_STEP_260 = 280.0
 # caption), for context beside the per-size timings.
 PAPER_3D_FIT_A_MS = 4.11e-6
 PAPER_3D_FIT_B_MS = 1.2e-2
-# DRAM bytes (read + write) of one two-arm k_pass3 launch at L = 260 (the
-# commonest kind), from an ncu capture of the current kernel; reset to None
-# whenever the kernel changes until a new capture is taken.
-PASS3_DRAM_BYTES_260 = 83.6e6
-
-
 def run_kernel3_mode(args):
     """Profiling case of the cubic lattice: one cube (random init seed 3,
     300 K, 0.1 MPa), `warmup` MC steps, then `steps` timed with CUDA events."""
@@ -351,6 +411,9 @@ def run_batch_mode(args):
 
 
 def measure_cubic(args, rank, world):
+    if not hasattr(args, "philox_ceiling"):
+        import torch
+        args.philox_ceiling, _ = philox_ceiling(torch.cuda.Stream(), 4096 * 4096)
     """The paper's own 3D model at its largest size (260^3, q = 6, 300 K,
     0.1 MPa, random init seed 3): MC steps of the six-arm layered schedule
     timed with CUDA events on the lattice's stream (the 70 MB lattice stays
@@ -381,16 +444,18 @@ def measure_cubic(args, rank, world):
            "ms_per_mc_step": dev_s * 1e3, "sweeps_timed": S,
            "paper_ms_per_mc_step": PAPER_3D_MS_PER_STEP_260 if L == 260 else None,
            "paper_hardware": "RTX 3060 (sm_86), cuRAND and copies included",
-           "launches_per_mc_step": 4,
-           "roofline": {"bound": "alu", "achieved": ALU_OPS_PER_UPDATE * upd / (per_step * 1e-3) / 1e12,
-                        "peak": ALU_PEAK_TOPS, "unit": "Tintop/s",
-                        "frac": ALU_OPS_PER_UPDATE * upd / (per_step * 1e-3) / 1e12 / ALU_PEAK_TOPS,
-                        "traffic": PASS3_DRAM_BYTES_260 if L == 260 else None,
-                        "traffic_unit": "bytes per two-arm launch (ncu dram read + write)",
-                        "kernel": "k_pass3 (four launches per MC step)"},
+           "launches_per_mc_step": 5,
+           "roofline": {"bound": "alu", "achieved": upd / (per_step * 1e6),
+                        "peak": args.philox_ceiling, "unit": "sigma-updates/ns",
+                        "frac": upd / (per_step * 1e6) / args.philox_ceiling if args.philox_ceiling else None,
+                        "peak_kind": "measured: the Philox draws alone (cvf_philox_probe, four "
+                                     "updates per Philox block, as the passes draw them)",
+                        "traffic": None,
+                        "kernel": "k_eta3 + k_pass3 (five launches per MC step)"},
+           "eta_moves": 1,
            "acceptance": o["acc_sigma"] / max(1.0, upd * o["sweep"]),
-           "workload": "CVF 3D cubic lattice L=%d q=6, layered six-arm schedule, random init "
-                       "(seed 3), 300 K, 0.1 MPa" % L}
+           "workload": "CVF 3D cubic lattice L=%d q=6, layered six-arm schedule with the eta "
+                       "update of the checkerboard cubes, random init (seed 3), 300 K, 0.1 MPa" % L}
     # time per MC step against N over the sizes of the paper's Fig. 4, next
     # to its linear fit t = a N + b (RTX 3060, 32768 <= N <= 2097152)
     sizes = []
@@ -649,6 +714,8 @@ def measure_serving(args, rank):
 
 def main():
     args = parse()
+    if args.record_counters:
+        return record_counters(args.record_counters)
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "kernel":
@@ -723,27 +790,33 @@ def main():
     per_sweep_ms = statistics.median(sw_ms)
     peaks, peak_kind = measured_peaks()
     upd_per_s = 4.0 * L * L / (per_sweep_ms * 1e-3)
-    roofline = {"bound": "alu", "achieved": ALU_OPS_PER_UPDATE * upd_per_s / 1e12,
-                "peak": ALU_PEAK_TOPS, "unit": "Tintop/s",
-                "frac": ALU_OPS_PER_UPDATE * upd_per_s / 1e12 / ALU_PEAK_TOPS,
-                "traffic": (SWEEP_DRAM_BYTES_4096 * (L / 4096.0) ** 2
-                            if SWEEP_DRAM_BYTES_4096 else None),
-                "traffic_unit": "bytes per launch (ncu dram read + write)",
+    ceiling, philox_ms = philox_ceiling(stream, L * L)
+    args.philox_ceiling = ceiling
+    counters = sweep_counters()
+    achieved = upd_per_s / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ceiling, "unit": "sigma-updates/ns",
+                "frac": achieved / ceiling,
+                "traffic": (counters["dram_bytes"] * (L / 4096.0) ** 2 if counters else None),
+                "traffic_unit": "bytes per launch (ncu dram read + write of the current kernel)",
                 "kernel": "k_sweep_tiled (one launch per MC step)",
-                "ops_per_update": ALU_OPS_PER_UPDATE,
-                "peak_kind": "derived: 152 SM x 128 lanes x 2070 MHz"}
+                "peak_kind": "measured: the step's Philox4x32-10 draws alone (cvf_philox_probe "
+                             "over the same %d cells, %.1f us per step; four updates per block), "
+                             "the random numbers every sweep of this method must make" % (L * L, philox_ms * 1e3)}
     bytes_per_sweep = 4.0 * L * L  # read 2 B + write 2 B per cell (1 B per sigma update)
     achieved_gbs = bytes_per_sweep / (per_sweep_ms * 1e-3) / 1e9
     roofline_hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
                     "bytes_per_update": 1.0, "peak_kind": peak_kind}
     roofline_issue = None
-    if SWEEP_INSTR_PER_UPDATE:
-        issued = SWEEP_INSTR_PER_UPDATE * upd_per_s / 1e12
-        roofline_issue = {"bound": "issue", "achieved": issued, "peak": ALU_PEAK_TOPS,
-                          "unit": "T thread-instructions/s", "frac": issued / ALU_PEAK_TOPS,
-                          "instructions_per_update": SWEEP_INSTR_PER_UPDATE,
-                          "instructions_source": "ncu smsp__inst_executed.sum of one launch"}
+    if counters:
+        ipu = counters["instructions_per_update"]
+        issued = ipu * upd_per_s / 1e12
+        roofline_issue = {"bound": "issue", "achieved": issued, "peak": ISSUE_PEAK_T,
+                          "unit": "T thread-instructions/s", "frac": issued / ISSUE_PEAK_T,
+                          "instructions_per_update": ipu,
+                          "peak_kind": "derived: 152 SM x 128 thread-instructions per clock x 2070 MHz",
+                          "instructions_source": "ncu smsp__inst_executed.sum of one launch of the "
+                                                 "current kernel (profiles/k_sweep_tiled_L4096_counters.json)"}
     # the 32 MB state stays in L2 across steps: the byte roofline that
     # bounds it is the L2 copy bandwidth, measured here with the library's
     # own copy kernel on the same working-set size (and, for reference, on

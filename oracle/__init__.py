@@ -292,10 +292,11 @@ def window_init_run(p: OracleParams, w_full: np.ndarray, x0: int, y0: int, W: in
     array far larger than memory could hold written out): initialise the
     window's cells by the init rule, then run len(gates) checkerboard steps
     over the window alone.  Cells more than 2 len(gates) inside the window
-    are then exact; the window must lie inside the lattice."""
+    are then exact; the window may run across the periodic edges (cells
+    taken mod L, 0 <= x0, y0 < L, W, H <= L)."""
     assert w_full.dtype == np.uint16 and w_full.flags.c_contiguous
     assert w_full.size == p.L * p.L
-    assert 0 <= x0 and x0 + W <= p.L and 0 <= y0 and y0 + H <= p.L
+    assert 0 <= x0 < p.L and 0 < W <= p.L and 0 <= y0 < p.L and 0 < H <= p.L
     g = np.ascontiguousarray(gates, dtype=np.int32)
     cp = p.c()
     ptr = w_full.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16))

@@ -560,11 +560,12 @@ void orc_arm_probe_all(const orc_params *p, const uint16_t *cfgs, int64_t n,
 }
 
 /* Steps restricted to a rectangular window of a full L x L configuration:
-   only cells with x0 <= x < x0+W and y0 <= y < y0+H (no wrap) are updated,
-   the rest stay frozen, and the gate of each step is taken from gates[].
-   After K steps every window cell farther than 2K cells from the window
-   edge equals the full-lattice result, because a checkerboard step moves
-   information by at most two cells.  The volume chain is not run here. */
+   only cells (x mod L, y mod L) with x0 <= x < x0+W and y0 <= y < y0+H are
+   updated (a window may run across the periodic edges; W, H <= L), the rest
+   stay frozen, and the gate of each step is taken from gates[].  After K
+   steps every window cell farther than 2K cells from the window edge equals
+   the full-lattice result, because a checkerboard step moves information by
+   at most two cells.  The volume chain is not run here. */
 void orc_window_run(const orc_params *p, uint16_t *w, int32_t x0, int32_t y0,
                     int32_t W, int32_t H, int64_t step0, int64_t K,
                     const int32_t *gates) {
@@ -578,8 +579,9 @@ void orc_window_run(const orc_params *p, uint16_t *w, int32_t x0, int32_t y0,
     st.sweep = step0 + s;
     st.g = gates[s];
     for (int colour = 0; colour < 2; ++colour)
-      for (int64_t y = y0; y < (int64_t)y0 + H; ++y)
-        for (int64_t x = x0; x < (int64_t)x0 + W; ++x) {
+      for (int64_t yy = y0; yy < (int64_t)y0 + H; ++yy)
+        for (int64_t xx = x0; xx < (int64_t)x0 + W; ++xx) {
+          int64_t x = xx % p->L, y = yy % p->L;
           if (((x + y) & 1) != colour) continue;
           int64_t c = y * p->L + x;
           uint32_t acc[4], kk[4];
@@ -589,15 +591,17 @@ void orc_window_run(const orc_params *p, uint16_t *w, int32_t x0, int32_t y0,
   }
 }
 
-/* The initial words of the cells x0 <= x < x0 + W, y0 <= y < y0 + H of the
-   L x L lattice w (the rectangle must lie inside it; nothing else is
+/* The initial words of the cells (x mod L, y mod L), x0 <= x < x0 + W,
+   y0 <= y < y0 + H, of the L x L lattice w (W, H <= L; nothing else is
    written), so that a window of a lattice too large to initialise whole can
    be started and run by orc_window_run. */
 void orc_init_window(const orc_params *p, uint16_t *w, int32_t x0, int32_t y0,
                      int32_t W, int32_t H) {
-  for (int64_t y = y0; y < (int64_t)y0 + H; ++y)
-    for (int64_t x = x0; x < (int64_t)x0 + W; ++x)
-      w[y * p->L + x] = orc_init_word(p, y * p->L + x);
+  for (int64_t yy = y0; yy < (int64_t)y0 + H; ++yy)
+    for (int64_t xx = x0; xx < (int64_t)x0 + W; ++xx) {
+      int64_t c = (yy % p->L) * p->L + xx % p->L;
+      w[c] = orc_init_word(p, c);
+    }
 }
 
 /* The V_iso chain alone for K steps from (V_iso, step0), valid while no

@@ -306,17 +306,25 @@ def test_ring_overflow_keeps_newest():
         assert recs[0]["sweep"] == 101 and recs[-1]["sweep"] == 65636
 
 
-def test_full_size_sampled_windows():
-    """4096 x 4096, random init seed 3, ambient: the configuration the
-    benchmark times.  The oracle cannot run the whole lattice, so after K
-    steps it recomputes sampled windows: a checkerboard step moves information
-    by at most two cells, so a window run with its border frozen is exact
-    more than 2K cells inside.  V_iso follows from the oracle's own volume
-    chain (no gate flip is proposed at this state point)."""
-    L, K = 4096, 6
-    op = oracle.physical_params(300.0, 0.1, L=L, q=6, seed=3)
+@pytest.mark.parametrize("cfg", range(6))
+def test_full_size_sampled_windows(cfg):
+    """The six 4096 x 4096 lattices the benchmark times (random init seed 3
+    and ordered init, 270 / 300 / 330 K, 0.1 MPa), 50 steps through the
+    tiled sweep with programmatic launches.  The oracle cannot run the whole
+    lattice, so it recomputes eight sampled windows: a checkerboard step
+    moves information by at most two cells, so a window run with its border
+    frozen is exact more than 2K + 2 cells inside.  Four windows lie across
+    the periodic edges (the four corners of the lattice, wrapped) and four
+    at random places.  V_iso follows from the oracle's own volume chain (no
+    gate flip is proposed at these state points); the kept counts equal an
+    independent recount."""
+    from paper_2505_05919_gb300 import workloads
+    c = workloads.c3()[cfg]
+    L, K = 4096, 50
+    op = oracle.physical_params(c["T"], c["P"], L=L, q=c["q"], seed=c["seed"], init=c["init"])
     with Lattice(params_from_dict(asdict(op))) as lat:
         init_gpu = lat.state()
+        assert lat.tiles()[0] == 0
         lat.sweep(K)
         s_gpu = lat.state()
         o_gpu = lat.observables()
@@ -328,16 +336,17 @@ def test_full_size_sampled_windows():
     assert done == K
     assert V[-1] == pytest.approx(o_gpu["V_iso"], rel=FP_REL)
     assert o_gpu["acc_volume"] == acc
-    rng = np.random.default_rng(2024)
     margin, inner = 2 * K + 2, 48
+    W = inner + 2 * margin
+    rng = np.random.default_rng(2024 + cfg)
+    spots = [(L - W // 2, L - W // 2), (L - W // 2, 0), (0, L - W // 2), (L - 20, L - W + 7)]
+    spots += [(int(rng.integers(0, L)), int(rng.integers(0, L))) for _ in range(4)]
     full = ref0.state()
-    for _ in range(8):
-        x0 = int(rng.integers(0, L - inner - 2 * margin))
-        y0 = int(rng.integers(0, L - inner - 2 * margin))
-        W = inner + 2 * margin
+    for x0, y0 in spots:
         out = oracle.window_run(op, full, x0, y0, W, W, 0, g).reshape(L, L)
-        ys, xs = slice(y0 + margin, y0 + margin + inner), slice(x0 + margin, x0 + margin + inner)
-        assert np.array_equal(s_gpu[ys, xs], out[ys, xs])
+        ys = [(y0 + margin + i) % L for i in range(inner)]
+        xs = [(x0 + margin + i) % L for i in range(inner)]
+        assert np.array_equal(s_gpu[np.ix_(ys, xs)], out[np.ix_(ys, xs)]), (cfg, x0, y0)
     assert 0 < o_gpu["n_hb_raw"] <= 2 * L * L and 0 < o_gpu["n_coop"] <= 6 * L * L
 
 

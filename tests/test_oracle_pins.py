@@ -461,3 +461,26 @@ def test_volume_chain3_equals_full_run():
     assert all(r["g"] == 1 for r in rec)
     assert np.array_equal(V, Vr)
     assert acc == rec[-1]["acc_volume"]
+
+
+def test_window_across_the_periodic_edges_matches_whole_lattice():
+    """A window that runs across both periodic edges (cells taken mod L)
+    agrees with the whole lattice more than 2K + 2 cells inside, like one
+    that lies inside the lattice."""
+    L, K = 40, 3
+    op = oracle.physical_params(300.0, 0.1, L=L, seed=29)
+    ref = oracle.Oracle(op)
+    done, V, g, _ = oracle.volume_chain(op, ref.observables()["V_iso"], 0, K)
+    assert done == K
+    ref.run(K)
+    w = np.zeros((L, L), np.uint16)
+    x0, y0, W, H = 30, 33, 24, 22   # x 30..53 -> 30..39, 0..13; y 33..54 -> 33..39, 0..14
+    oracle.window_init_run(op, w, x0, y0, W, H, 0, g)
+    m = 2 * K + 2
+    ys = [(y0 + i) % L for i in range(m, H - m)]
+    xs = [(x0 + i) % L for i in range(m, W - m)]
+    assert np.array_equal(w[np.ix_(ys, xs)], ref.state()[np.ix_(ys, xs)])
+    # nothing outside the window was written
+    inside = np.zeros((L, L), bool)
+    inside[np.ix_([(y0 + i) % L for i in range(H)], [(x0 + i) % L for i in range(W)])] = True
+    assert not w[~inside].any()
