@@ -263,12 +263,17 @@ int cvf_sweep_noalloc(const cvf_params *p, void *dev_state, double V_iso,
 int cvf_batch_create(const cvf_params *params, int32_t n, void *stream,
                      cvf_batch **out);
 
-/* Adds one replica (allocates its state pair, control block, tables and a
- * 1024-record observable ring, initialises it; synchronises the stream) and
- * returns its id.  CVF_ENOMEM when the device has no room for it. */
+/* Adds one replica and returns its id: allocates its state pair, control
+ * block, tables and a 1024-record observable ring from the batch's
+ * stream-ordered memory pool and enqueues its initialisation on the stream,
+ * behind any launch in flight.  Does not wait for the GPU: the parameters
+ * travel as kernel arguments, so p may be reused on return.  CVF_ENOMEM
+ * when the device has no room for it (nothing leaked). */
 int cvf_batch_add(cvf_batch *b, const cvf_params *p, int32_t *replica);
 
-/* Frees a replica (waits for the stream first); its id becomes free. */
+/* Frees a replica, stream-ordered: its memory goes back to the batch's pool
+ * once the work already enqueued on the stream has run (no wait here).  Its
+ * id becomes free at once; the replica's results must be read before. */
 int cvf_batch_remove(cvf_batch *b, int32_t replica);
 
 /* Number of slots (live or free) and of live replicas. */
@@ -276,7 +281,9 @@ int cvf_batch_size(cvf_batch *b, int32_t *n_slots, int32_t *n_live);
 
 /* Advances replica i by sweeps[i] MC steps, i = 0..n-1 with n the slot count
  * (0 for free slots and for replicas to leave alone), in one persistent
- * launch; returns without waiting.  At most 64 distinct nonzero step counts
+ * launch; returns without waiting for it (the launch description goes
+ * through one of two pinned staging slots, so a call waits at most for the
+ * copy enqueued two calls before).  At most 64 distinct nonzero step counts
  * and 2^31-1 steps per replica per call.  A bounded device-side wait that
  * gives up is reported by the next call that reads results (CVF_ETIMEOUT). */
 int cvf_batch_sweep(cvf_batch *b, const int64_t *sweeps, int32_t n);
@@ -287,6 +294,26 @@ int cvf_batch_sync(cvf_batch *b);
 /* Observables / lattice (L*L words, layout above) of one replica; both
  * synchronise the stream. */
 int cvf_batch_observables(cvf_batch *b, int32_t replica, cvf_obs *out);
+
+/* Observables of n replicas (ids replicas[0..n), out[0..n)), each as
+ * cvf_batch_observables returns it, with one synchronisation of the stream.
+ * CVF_EINVAL for an id that is not a live replica (nothing read). */
+int cvf_batch_observables_many(cvf_batch *b, const int32_t *replicas,
+                               int32_t n, cvf_obs *out);
+
+/* The same read in two halves, so the host need not wait for work enqueued
+ * after it.  _enqueue computes the n replicas' observables at the current
+ * point of the stream (after the sweeps already enqueued, before any later
+ * call's work), copies them and the launch error word into pinned staging,
+ * and returns a ticket without waiting.  _collect waits for that point of
+ * the stream only (an event), then fills out[0..n) (n as enqueued) or
+ * returns the error of the sweeps before it (CVF_ETIMEOUT / CVF_EBOUNDS as
+ * cvf_batch_sync).  Four tickets stay valid at a time: the fifth enqueue
+ * reuses the first one's staging (CVF_EINVAL when it is then collected). */
+int cvf_batch_observables_enqueue(cvf_batch *b, const int32_t *replicas,
+                                  int32_t n, int64_t *ticket);
+int cvf_batch_observables_collect(cvf_batch *b, int64_t ticket, cvf_obs *out,
+                                  int32_t n);
 int cvf_batch_get_state(cvf_batch *b, int32_t replica, uint16_t *host,
                         size_t n);
 
@@ -300,7 +327,12 @@ int cvf_batch_set_tiles(cvf_batch *b, int32_t config);
 int cvf_batch_get_tiles(cvf_batch *b, int32_t *config, int32_t *last_used);
 int cvf_batch_tile_config(int32_t config, int32_t *rows, int32_t *words);
 
-/* Waits for the stream and frees every replica and the batch. */
+/* Device memory the batch's pool has mapped (reserved) and of that what
+ * live replicas and the descriptor array hold (used); reserved - used is
+ * free for later adds but not for other allocations. */
+int cvf_batch_memory(cvf_batch *b, uint64_t *reserved, uint64_t *used);
+
+/* Waits for the stream and frees every replica, the pool and the batch. */
 int cvf_batch_destroy(cvf_batch *b);
 
 /* ------------------------------------------------------------------------

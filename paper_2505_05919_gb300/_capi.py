@@ -86,6 +86,13 @@ _SIGS = {
     "cvf_batch_sweep": (ctypes.c_int, [_vp, _P(ctypes.c_int64), ctypes.c_int32]),
     "cvf_batch_sync": (ctypes.c_int, [_vp]),
     "cvf_batch_observables": (ctypes.c_int, [_vp, ctypes.c_int32, _P(cvf_obs)]),
+    "cvf_batch_memory": (ctypes.c_int, [_vp, _P(ctypes.c_uint64), _P(ctypes.c_uint64)]),
+    "cvf_batch_observables_many": (ctypes.c_int, [_vp, _P(ctypes.c_int32), ctypes.c_int32,
+                                                  _P(cvf_obs)]),
+    "cvf_batch_observables_enqueue": (ctypes.c_int, [_vp, _P(ctypes.c_int32), ctypes.c_int32,
+                                                     _P(ctypes.c_int64)]),
+    "cvf_batch_observables_collect": (ctypes.c_int, [_vp, ctypes.c_int64, _P(cvf_obs),
+                                                     ctypes.c_int32]),
     "cvf_batch_get_state": (ctypes.c_int, [_vp, ctypes.c_int32, _P(ctypes.c_uint16), ctypes.c_size_t]),
     "cvf_batch_set_tiles": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "cvf_batch_get_tiles": (ctypes.c_int, [_vp, _P(ctypes.c_int32), _P(ctypes.c_int32)]),
@@ -289,6 +296,36 @@ def cvf_batch_observables(b: int, replica: int) -> cvf_obs:
     o = cvf_obs()
     _check(load().cvf_batch_observables(b, replica, ctypes.byref(o)), "cvf_batch_observables")
     return o
+
+
+def cvf_batch_observables_many(b: int, replicas) -> list:
+    ids = [int(r) for r in replicas]
+    n = len(ids)
+    arr = (ctypes.c_int32 * max(n, 1))(*ids)
+    out = (cvf_obs * max(n, 1))()
+    _check(load().cvf_batch_observables_many(b, arr, n, out), "cvf_batch_observables_many")
+    return [out[i] for i in range(n)]
+
+
+def cvf_batch_observables_enqueue(b: int, replicas) -> int:
+    ids = [int(r) for r in replicas]
+    arr = (ctypes.c_int32 * max(len(ids), 1))(*ids)
+    t = ctypes.c_int64(-1)
+    _check(load().cvf_batch_observables_enqueue(b, arr, len(ids), ctypes.byref(t)),
+           "cvf_batch_observables_enqueue")
+    return t.value
+
+
+def cvf_batch_observables_collect(b: int, ticket: int, n: int) -> list:
+    out = (cvf_obs * max(n, 1))()
+    _check(load().cvf_batch_observables_collect(b, ticket, out, n), "cvf_batch_observables_collect")
+    return [out[i] for i in range(n)]
+
+
+def cvf_batch_memory(b: int) -> tuple:
+    r, u = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(load().cvf_batch_memory(b, ctypes.byref(r), ctypes.byref(u)), "cvf_batch_memory")
+    return r.value, u.value
 
 
 def cvf_batch_get_state(b: int, replica: int, host_ptr: int, n: int) -> None:

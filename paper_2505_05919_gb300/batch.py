@@ -1,7 +1,9 @@
 """Python face of a batch of replicas (one persistent launch per call).
 
-Device memory is allocated by the library per replica (one allocation each);
-the stream comes from PyTorch.  All method steps run in ``libcvf.so``.
+Device memory is allocated by the library per replica (one stream-ordered
+allocation each, from the batch's own pool); the stream comes from PyTorch.
+Adding, removing and sweeping enqueue work without waiting for the GPU.  All
+method steps run in ``libcvf.so``.
 """
 from __future__ import annotations
 
@@ -42,6 +44,10 @@ class Batch:
         _capi.cvf_batch_remove(self.b, rid)
         self.L.pop(rid, None)
 
+    def pool_bytes(self) -> tuple:
+        """(mapped, in use) bytes of the batch's memory pool."""
+        return _capi.cvf_batch_memory(self.b)
+
     def slots(self) -> int:
         return _capi.cvf_batch_size(self.b)[0]
 
@@ -71,6 +77,19 @@ class Batch:
     # results ---------------------------------------------------------------
     def observables(self, rid: int) -> dict:
         return _capi.cvf_batch_observables(self.b, rid).as_dict()
+
+    def observables_many(self, rids) -> list:
+        """Observables of several replicas with one synchronisation."""
+        return [o.as_dict() for o in _capi.cvf_batch_observables_many(self.b, rids)]
+
+    def observables_enqueue(self, rids) -> int:
+        """Ticket for the observables of rids at this point of the stream
+        (returns without waiting)."""
+        return _capi.cvf_batch_observables_enqueue(self.b, rids)
+
+    def observables_collect(self, ticket: int, n: int) -> list:
+        """Waits for a ticket's point of the stream and returns its n records."""
+        return [o.as_dict() for o in _capi.cvf_batch_observables_collect(self.b, ticket, n)]
 
     def state(self, rid: int) -> np.ndarray:
         L = self.L[rid]

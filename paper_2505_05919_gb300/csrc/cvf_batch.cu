@@ -72,6 +72,23 @@ __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// A replica's tables from the call's parameters (passed by value, so the
+// caller's host memory is free as soon as the launch is enqueued) and a
+// cleared control block.
+struct ReplicaTables {
+  unsigned long long t[48];
+};
+__global__ void k_replica_setup(Ctrl* ctl, unsigned long long* table, VolumeArgs* vol,
+                                ReplicaTables t, VolumeArgs va) {
+  if (blockIdx.x != 0) return;
+  for (int i = threadIdx.x; i < 48; i += blockDim.x) table[i] = t.t[i];
+  unsigned char* c = reinterpret_cast<unsigned char*>(ctl);
+  for (int i = threadIdx.x; i < (int)sizeof(Ctrl); i += blockDim.x) c[i] = 0;
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&va);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(vol);
+  for (int i = threadIdx.x; i < (int)(sizeof(VolumeArgs) / 8); i += blockDim.x) dst[i] = src[i];
+}
+
 __global__ void k_batch_reset(BatchWork* W, unsigned int* progress, int n_replicas) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_replicas; i += gridDim.x * blockDim.x)
     progress[i] = 0;
@@ -362,6 +379,7 @@ struct TileConfig {
 constexpr TileConfig kTileConfigs[] = {{64, 64}, {32, 32}, {32, 16}, {16, 16}};
 constexpr int kNumTileConfigs = 4;
 constexpr long long kReplicaRingCap = 1024;
+constexpr int kObsSlots = 4;  // observables tickets in flight per batch
 
 struct Replica {
   bool live;
@@ -385,6 +403,11 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct cvf_batch {
   cudaStream_t stream;
   cudaStream_t cap_stream;
+  // replica memory and the descriptor array come from the batch's own
+  // stream-ordered pool: a removed replica's memory is reused by a later
+  // add on the same stream without a device-wide wait, and the pool keeps
+  // what it has mapped until the batch is destroyed
+  cudaMemPool_t pool;
   std::vector<Replica> reps;
   int rng_words;       // shared by all replicas (-1 while empty)
   int tile_cfg;        // -1: chosen per call
@@ -394,11 +417,31 @@ struct cvf_batch {
   bool reps_dirty;
   void* d_work;
   size_t d_work_bytes;
-  void* h_work;  // pinned staging of the launch description
+  // pinned staging of the launch description and of the replica
+  // descriptors, two slots each: a slot is rewritten only after the copy
+  // that read it last has run (its event), so no call waits for a launch
+  void* h_work[2];
   size_t h_work_bytes;
-  cvf_obs* d_obs;
-  unsigned long long* d_hist;
-  void* h_pinned;
+  cudaEvent_t ev_work[2];
+  int work_slot;
+  ReplicaDesc* h_descs[2];
+  cudaEvent_t ev_descs[2];
+  int descs_slot;
+  // observables read-back: tickets rotate over kObsSlots slots, each with
+  // device staging (records + histograms), a pinned copy of the records and
+  // of the launch error word, and the event that marks the copy done
+  struct ObsSlot {
+    cvf_obs* d_obs;
+    unsigned long long* d_hist;
+    cvf_obs* h_obs;
+    unsigned int* h_err;
+    int cap;
+    int n;
+    long long ticket;
+    cudaEvent_t ev;
+  } obs[kObsSlots];
+  long long next_ticket;
+  void* h_pinned;     // 4096 bytes
   cudaGraphExec_t graph[kNumTileConfigs][2];  // [config][cmp64]
   int graph_n_reps[kNumTileConfigs][2];
   void* graph_work[kNumTileConfigs][2];
@@ -436,8 +479,10 @@ bool any_cmp64(const cvf_batch* b) {
   return false;
 }
 
-void free_replica(Replica& r) {
-  if (r.mem) cudaFree(r.mem);
+// Stream-ordered free: the memory returns to the pool once the work
+// enqueued before it on the batch's stream is done (no device-wide wait).
+void free_replica(Replica& r, cudaStream_t s) {
+  if (r.mem) cudaFreeAsync(r.mem, s);
   r = Replica();
 }
 
@@ -457,16 +502,25 @@ int upload_descs(cvf_batch* b) {
     int cap = std::max(16, b->d_reps_cap * 2);
     while (cap < n) cap *= 2;
     ReplicaDesc* d = nullptr;
-    CVF_CUDA_CHECK(cudaMalloc(&d, sizeof(ReplicaDesc) * cap));
-    if (b->d_reps) {
-      cudaStreamSynchronize(b->stream);
-      cudaFree(b->d_reps);
+    CVF_CUDA_CHECK(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&d), sizeof(ReplicaDesc) * cap,
+                                           b->pool, b->stream));
+    if (b->d_reps) CVF_CUDA_CHECK(cudaFreeAsync(b->d_reps, b->stream));
+    // the staging slots grow with the descriptor array (after their copies)
+    for (int k = 0; k < 2; ++k) {
+      CVF_CUDA_CHECK(cudaEventSynchronize(b->ev_descs[k]));
+      if (b->h_descs[k]) cudaFreeHost(b->h_descs[k]);
+      b->h_descs[k] = nullptr;
+      CVF_CUDA_CHECK(cudaMallocHost(reinterpret_cast<void**>(&b->h_descs[k]),
+                                    sizeof(ReplicaDesc) * cap));
     }
     drop_graphs(b);
     b->d_reps = d;
     b->d_reps_cap = cap;
   }
-  std::vector<ReplicaDesc> h(std::max(n, 1));
+  const int slot = b->descs_slot;
+  b->descs_slot ^= 1;
+  CVF_CUDA_CHECK(cudaEventSynchronize(b->ev_descs[slot]));  // the slot's last copy has run
+  ReplicaDesc* h = b->h_descs[slot];
   for (int i = 0; i < n; ++i) {
     const Replica& r = b->reps[i];
     ReplicaDesc& d = h[i];
@@ -483,10 +537,9 @@ int upload_descs(cvf_batch* b) {
     d.q = (uint32_t)r.p.q;
   }
   if (n > 0)
-    CVF_CUDA_CHECK(cudaMemcpyAsync(b->d_reps, h.data(), sizeof(ReplicaDesc) * n,
-                                   cudaMemcpyHostToDevice, b->stream));
-  // the copy reads a host vector: wait for it before the vector goes away
-  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
+    CVF_CUDA_CHECK(cudaMemcpyAsync(b->d_reps, h, sizeof(ReplicaDesc) * n, cudaMemcpyHostToDevice,
+                                   b->stream));
+  CVF_CUDA_CHECK(cudaEventRecord(b->ev_descs[slot], b->stream));
   b->reps_dirty = false;
   return CVF_OK;
 }
@@ -494,15 +547,17 @@ int upload_descs(cvf_batch* b) {
 int ensure_work_buffer(cvf_batch* b, size_t bytes) {
   if (bytes <= b->d_work_bytes) return CVF_OK;
   size_t cap = std::max<size_t>(bytes, 2 * b->d_work_bytes);
-  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));  // growth only: rare
   if (b->d_work) cudaFree(b->d_work);
-  if (b->h_work) cudaFreeHost(b->h_work);
+  for (int k = 0; k < 2; ++k) {
+    if (b->h_work[k]) cudaFreeHost(b->h_work[k]);
+    b->h_work[k] = nullptr;
+  }
   b->d_work = nullptr;
-  b->h_work = nullptr;
   b->d_work_bytes = b->h_work_bytes = 0;
   drop_graphs(b);
   CVF_CUDA_CHECK(cudaMalloc(&b->d_work, cap));
-  CVF_CUDA_CHECK(cudaMallocHost(&b->h_work, cap));
+  for (int k = 0; k < 2; ++k) CVF_CUDA_CHECK(cudaMallocHost(&b->h_work[k], cap));
   b->d_work_bytes = b->h_work_bytes = cap;
   return CVF_OK;
 }
@@ -621,6 +676,31 @@ int check_replica(cvf_batch* b, int32_t id) {
   return CVF_OK;
 }
 
+int launch_error(unsigned int err) {
+  if (err >= 0x100u)
+    return set_error(CVF_EBOUNDS, "a device index check of the batched sweep failed (site %u)",
+                     err - 0x100u);
+  if (err) return set_error(CVF_ETIMEOUT, "a replica wait in the batched sweep gave up");
+  return CVF_OK;
+}
+
+// (Re)allocates a ticket slot's staging for cap records; the slot's last
+// copy must be done.
+cudaError_t grow_obs_slot(cvf_batch::ObsSlot& o, int cap) {
+  if (o.d_obs) cudaFree(o.d_obs);
+  if (o.d_hist) cudaFree(o.d_hist);
+  if (o.h_obs) cudaFreeHost(o.h_obs);
+  o.d_obs = nullptr;
+  o.d_hist = nullptr;
+  o.h_obs = nullptr;
+  o.cap = 0;
+  cudaError_t e = cudaMalloc(&o.d_obs, sizeof(cvf_obs) * cap);
+  if (e == cudaSuccess) e = cudaMalloc(&o.d_hist, sizeof(unsigned long long) * 9 * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&o.h_obs), sizeof(cvf_obs) * cap);
+  if (e == cudaSuccess) o.cap = cap;
+  return e;
+}
+
 // Reads the error word of the last launch (synchronises the stream).
 int batch_status(cvf_batch* b) {
   CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
@@ -631,11 +711,7 @@ int batch_status(cvf_batch* b) {
   CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
   unsigned int err = 0;
   std::memcpy(&err, b->h_pinned, sizeof(err));
-  if (err >= 0x100u)
-    return set_error(CVF_EBOUNDS, "a device index check of the batched sweep failed (site %u)",
-                     err - 0x100u);
-  if (err) return set_error(CVF_ETIMEOUT, "a replica wait in the batched sweep gave up");
-  return CVF_OK;
+  return launch_error(err);
 }
 
 }  // namespace
@@ -654,9 +730,28 @@ int cvf_batch_create(const cvf_params* params, int32_t n, void* stream, cvf_batc
   b->tile_cfg = -1;
   b->last_cfg = -1;
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_obs, sizeof(cvf_obs));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_hist, sizeof(unsigned long long) * 9);
+  if (e == cudaSuccess) {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (e == cudaSuccess) e = cudaMemPoolCreate(&b->pool, &props);
+    uint64_t keep = ~0ull;
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(b->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_pinned, 4096);
+  for (int k = 0; k < kObsSlots && e == cudaSuccess; ++k) {
+    b->obs[k].ticket = -1;
+    e = cudaEventCreateWithFlags(&b->obs[k].ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b->obs[k].h_err), 64);
+    if (e == cudaSuccess) e = grow_obs_slot(b->obs[k], 16);
+  }
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&b->ev_work[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_descs[k], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     cvf_batch_destroy(b);
     return set_error(CVF_ECUDA, "batch setup: %s", cudaGetErrorString(e));
@@ -694,7 +789,7 @@ int cvf_batch_add(cvf_batch* b, const cvf_params* p, int32_t* replica) {
   const size_t o_vol = align256(o_table + sizeof(unsigned long long) * 48);
   const size_t o_ring = align256(o_vol + sizeof(VolumeArgs));
   const size_t total = align256(o_ring + sizeof(cvf_obs) * kReplicaRingCap);
-  cudaError_t e = cudaMalloc(&r.mem, total);
+  cudaError_t e = cudaMallocFromPoolAsync(&r.mem, total, b->pool, b->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(e == cudaErrorMemoryAllocation ? CVF_ENOMEM : CVF_ECUDA,
@@ -706,8 +801,8 @@ int cvf_batch_add(cvf_batch* b, const cvf_params* p, int32_t* replica) {
   r.table = reinterpret_cast<unsigned long long*>(m + o_table);
   r.vol = reinterpret_cast<VolumeArgs*>(m + o_vol);
   r.ring = reinterpret_cast<cvf_obs*>(m + o_ring);
-  unsigned long long t24[48];
-  r.cmp64 = fill_table24(p, t24);
+  ReplicaTables t24;
+  r.cmp64 = fill_table24(p, t24.t);
   VolumeArgs va;
   fill_volume_args(p, r.N, d2, mult, &va);
   const RoundKeys K = make_round_keys(p->seed);
@@ -716,13 +811,13 @@ int cvf_batch_add(cvf_batch* b, const cvf_params* p, int32_t* replica) {
   do {                                                                              \
     cudaError_t e_ = (expr);                                                        \
     if (e_ != cudaSuccess) {                                                        \
-      free_replica(r);                                                              \
+      free_replica(r, s);                                                           \
       return set_error(CVF_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_)); \
     }                                                                               \
   } while (0)
-  ADD_CHECK(cudaMemcpyAsync(r.table, t24, sizeof(t24), cudaMemcpyHostToDevice, s));
-  ADD_CHECK(cudaMemcpyAsync(r.vol, &va, sizeof(va), cudaMemcpyHostToDevice, s));
-  ADD_CHECK(cudaMemsetAsync(r.ctrl, 0, sizeof(Ctrl), s));
+  // everything is enqueued on the batch's stream (after any launch in
+  // flight) and the host data travel as kernel parameters: no wait here
+  k_replica_setup<<<1, 256, 0, s>>>(r.ctrl, r.table, r.vol, t24, va);
   const int grid = (int)std::max<long long>(1, std::min<long long>((r.N + 255) / 256, 4096));
   k_init<<<grid, 256, 0, s>>>(r.state, p->L, (uint32_t)p->q, p->init == CVF_INIT_RANDOM ? 1 : 0, K);
   k_set_ctrl<<<1, 32, 0, s>>>(r.vol, r.ctrl, (double)r.N * p->v_iso_init, 0, r.N);
@@ -730,8 +825,6 @@ int cvf_batch_add(cvf_batch* b, const cvf_params* p, int32_t* replica) {
   k_commit_counts<<<1, 32, 0, s>>>(r.ctrl);
   k_volume_prologue<<<1, 32, 0, s>>>(r.vol, r.ctrl, K);
   ADD_CHECK(cudaGetLastError());
-  // the host copies above read stack memory: complete them before returning
-  ADD_CHECK(cudaStreamSynchronize(s));
 #undef ADD_CHECK
   r.live = true;
   r.sweep_host = 0;
@@ -757,8 +850,10 @@ int cvf_batch_add(cvf_batch* b, const cvf_params* p, int32_t* replica) {
 int cvf_batch_remove(cvf_batch* b, int32_t replica) {
   int rc = check_replica(b, replica);
   if (rc) return rc;
-  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
-  free_replica(b->reps[replica]);
+  // stream-ordered: the memory is released after the launches already
+  // enqueued (which may still be reading it) have run
+  free_replica(b->reps[replica], b->stream);
+  CVF_CUDA_CHECK(cudaGetLastError());
   b->reps_dirty = true;
   bool any = false;
   for (const Replica& r : b->reps) any = any || r.live;
@@ -839,9 +934,12 @@ int cvf_batch_sweep(cvf_batch* b, const int64_t* sweeps, int32_t n) {
     if (bounds.empty() || bounds.back() != sweeps[act[k]]) bounds.push_back(sweeps[act[k]]);
   if ((int)bounds.size() > kBatchMaxSegments)
     return set_error(CVF_EINVAL, "at most %d distinct step counts per call", kBatchMaxSegments);
-  // wait for the previous launch before rewriting its description
-  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
-  char* h = reinterpret_cast<char*>(b->h_work);
+  // the description goes through one of two pinned slots; a slot is
+  // rewritten once the copy that read it two calls ago has run
+  const int slot = b->work_slot;
+  b->work_slot ^= 1;
+  CVF_CUDA_CHECK(cudaEventSynchronize(b->ev_work[slot]));
+  char* h = reinterpret_cast<char*>(b->h_work[slot]);
   std::memset(h, 0, sizeof(BatchWork));
   BatchWork* W = reinterpret_cast<BatchWork*>(h);
   W->n_active = na;
@@ -866,6 +964,7 @@ int cvf_batch_sweep(cvf_batch* b, const int64_t* sweeps, int32_t n) {
   std::memcpy(h + wl.order_off, act.data(), sizeof(int32_t) * na);
   std::memcpy(h + wl.prefix_off, prefix.data(), sizeof(long long) * (na + 1));
   CVF_CUDA_CHECK(cudaMemcpyAsync(b->d_work, h, wl.progress_off, cudaMemcpyHostToDevice, b->stream));
+  CVF_CUDA_CHECK(cudaEventRecord(b->ev_work[slot], b->stream));
   rc = launch(b, cfg, any_cmp64(b), n, na);
   if (rc) return rc;
   for (int i : act) b->reps[i].sweep_host += sweeps[i];
@@ -878,24 +977,77 @@ int cvf_batch_sync(cvf_batch* b) {
   return batch_status(b);
 }
 
+int cvf_batch_observables_enqueue(cvf_batch* b, const int32_t* replicas, int32_t n,
+                                  int64_t* ticket) {
+  NvtxRange nvtx_range("cvf_batch_observables_enqueue");
+  if (!b || !ticket || n < 0 || (n > 0 && !replicas)) return set_error(CVF_EINVAL, "bad argument");
+  for (int i = 0; i < n; ++i) {
+    const int rc = check_replica(b, replicas[i]);
+    if (rc) return rc;
+  }
+  const long long t = b->next_ticket;
+  cvf_batch::ObsSlot& o = b->obs[t % kObsSlots];
+  // the slot's previous ticket (kObsSlots enqueues ago) has been copied out
+  // by now or is given up
+  CVF_CUDA_CHECK(cudaEventSynchronize(o.ev));
+  if (n > o.cap) {
+    int cap = o.cap;
+    while (cap < n) cap *= 2;
+    CVF_CUDA_CHECK(grow_obs_slot(o, cap));
+  }
+  if (n > 0) {
+    CVF_CUDA_CHECK(cudaMemsetAsync(o.d_hist, 0, sizeof(unsigned long long) * 9 * n, b->stream));
+    for (int i = 0; i < n; ++i) {
+      const Replica& r = b->reps[replicas[i]];
+      const int grid = (int)std::max<long long>(1, std::min<long long>((r.N + kThreads - 1) / kThreads, 2048));
+      k_histogram<<<grid, kThreads, 0, b->stream>>>(r.state + (size_t)(r.sweep_host & 1) * r.N, r.N,
+                                                    o.d_hist + 9 * i);
+      k_observables<<<1, 32, 0, b->stream>>>(r.vol, r.ctrl, o.d_hist + 9 * i, o.d_obs + i);
+    }
+    CVF_CUDA_CHECK(cudaGetLastError());
+    CVF_CUDA_CHECK(cudaMemcpyAsync(o.h_obs, o.d_obs, sizeof(cvf_obs) * n, cudaMemcpyDeviceToHost,
+                                   b->stream));
+  }
+  o.h_err[0] = 0;
+  if (b->d_work)
+    CVF_CUDA_CHECK(cudaMemcpyAsync(o.h_err, reinterpret_cast<char*>(b->d_work) + offsetof(BatchWork, error),
+                                   sizeof(unsigned int), cudaMemcpyDeviceToHost, b->stream));
+  CVF_CUDA_CHECK(cudaEventRecord(o.ev, b->stream));
+  o.n = n;
+  o.ticket = t;
+  b->next_ticket = t + 1;
+  *ticket = t;
+  return CVF_OK;
+}
+
+int cvf_batch_observables_collect(cvf_batch* b, int64_t ticket, cvf_obs* out, int32_t n) {
+  NvtxRange nvtx_range("cvf_batch_observables_collect");
+  if (!b || n < 0 || (n > 0 && !out) || ticket < 0) return set_error(CVF_EINVAL, "bad argument");
+  cvf_batch::ObsSlot& o = b->obs[ticket % kObsSlots];
+  if (o.ticket != ticket)
+    return set_error(CVF_EINVAL, "ticket %lld was overwritten (at most %d in flight)",
+                     (long long)ticket, kObsSlots);
+  if (n != o.n) return set_error(CVF_EINVAL, "ticket %lld holds %d records, not %d",
+                                 (long long)ticket, o.n, n);
+  CVF_CUDA_CHECK(cudaEventSynchronize(o.ev));  // waits up to this point of the stream only
+  const int rc = launch_error(o.h_err[0]);
+  if (rc) return rc;
+  if (n > 0) std::memcpy(out, o.h_obs, sizeof(cvf_obs) * n);
+  return CVF_OK;
+}
+
+int cvf_batch_observables_many(cvf_batch* b, const int32_t* replicas, int32_t n, cvf_obs* out) {
+  NvtxRange nvtx_range("cvf_batch_observables_many");
+  int64_t t = -1;
+  int rc = cvf_batch_observables_enqueue(b, replicas, n, &t);
+  if (rc) return rc;
+  return cvf_batch_observables_collect(b, t, out, n);
+}
+
 int cvf_batch_observables(cvf_batch* b, int32_t replica, cvf_obs* out) {
   NvtxRange nvtx_range("cvf_batch_observables");
-  int rc = check_replica(b, replica);
-  if (rc) return rc;
   if (!out) return set_error(CVF_EINVAL, "out is NULL");
-  rc = batch_status(b);
-  if (rc) return rc;
-  const Replica& r = b->reps[replica];
-  CVF_CUDA_CHECK(cudaMemsetAsync(b->d_hist, 0, sizeof(unsigned long long) * 9, b->stream));
-  k_histogram<<<(int)std::max<long long>(1, std::min<long long>((r.N + kThreads - 1) / kThreads, 2048)),
-                kThreads, 0, b->stream>>>(r.state + (size_t)(r.sweep_host & 1) * r.N, r.N, b->d_hist);
-  k_observables<<<1, 32, 0, b->stream>>>(r.vol, r.ctrl, b->d_hist, b->d_obs);
-  CVF_CUDA_CHECK(cudaGetLastError());
-  CVF_CUDA_CHECK(cudaMemcpyAsync(b->h_pinned, b->d_obs, sizeof(cvf_obs), cudaMemcpyDeviceToHost,
-                                 b->stream));
-  CVF_CUDA_CHECK(cudaStreamSynchronize(b->stream));
-  std::memcpy(out, b->h_pinned, sizeof(cvf_obs));
-  return CVF_OK;
+  return cvf_batch_observables_many(b, &replica, 1, out);
 }
 
 int cvf_batch_get_state(cvf_batch* b, int32_t replica, uint16_t* host, size_t n) {
@@ -913,19 +1065,42 @@ int cvf_batch_get_state(cvf_batch* b, int32_t replica, uint16_t* host, size_t n)
   return CVF_OK;
 }
 
+int cvf_batch_memory(cvf_batch* b, uint64_t* reserved, uint64_t* used) {
+  if (!b || !reserved || !used) return set_error(CVF_EINVAL, "NULL argument");
+  unsigned long long r = 0, u = 0;  // 64-bit values, as the attributes are
+  CVF_CUDA_CHECK(cudaMemPoolGetAttribute(b->pool, cudaMemPoolAttrReservedMemCurrent, &r));
+  CVF_CUDA_CHECK(cudaMemPoolGetAttribute(b->pool, cudaMemPoolAttrUsedMemCurrent, &u));
+  *reserved = (uint64_t)r;
+  *used = (uint64_t)u;
+  return CVF_OK;
+}
+
 int cvf_batch_destroy(cvf_batch* b) {
   if (!b) return CVF_OK;
+  for (Replica& r : b->reps) free_replica(r, b->stream);
+  if (b->d_reps) cudaFreeAsync(b->d_reps, b->stream);
+  b->d_reps = nullptr;
   cudaStreamSynchronize(b->stream);
-  for (Replica& r : b->reps) free_replica(r);
   for (int c = 0; c < kNumTileConfigs; ++c)
     for (int k = 0; k < 2; ++k)
       if (b->graph[c][k]) cudaGraphExecDestroy(b->graph[c][k]);
-  if (b->d_reps) cudaFree(b->d_reps);
   if (b->d_work) cudaFree(b->d_work);
-  if (b->h_work) cudaFreeHost(b->h_work);
-  if (b->d_obs) cudaFree(b->d_obs);
-  if (b->d_hist) cudaFree(b->d_hist);
+  for (int k = 0; k < 2; ++k) {
+    if (b->h_work[k]) cudaFreeHost(b->h_work[k]);
+    if (b->h_descs[k]) cudaFreeHost(b->h_descs[k]);
+    if (b->ev_work[k]) cudaEventDestroy(b->ev_work[k]);
+    if (b->ev_descs[k]) cudaEventDestroy(b->ev_descs[k]);
+  }
+  for (int k = 0; k < kObsSlots; ++k) {
+    cvf_batch::ObsSlot& o = b->obs[k];
+    if (o.d_obs) cudaFree(o.d_obs);
+    if (o.d_hist) cudaFree(o.d_hist);
+    if (o.h_obs) cudaFreeHost(o.h_obs);
+    if (o.h_err) cudaFreeHost(o.h_err);
+    if (o.ev) cudaEventDestroy(o.ev);
+  }
   if (b->h_pinned) cudaFreeHost(b->h_pinned);
+  if (b->pool) cudaMemPoolDestroy(b->pool);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;
   return CVF_OK;

@@ -168,3 +168,43 @@ def test_batch_automatic_tile_choice():
             b.set_tiles(len(tile_configs()))
         b.set_tiles(-1)
         assert b.tiles()[0] == -1
+
+
+def test_batch_tickets_and_stream_ordered_churn():
+    """Observables read in two halves (enqueue now, collect later) describe
+    the replica at the point of the stream where they were enqueued, even
+    with sweeps, a removal and an add (all enqueued without waiting) behind
+    them; the freed slot's memory comes back from the batch's pool."""
+    ps = [_params(L, T, P, **kw) for (L, T, P, kw) in MIX[:3]]
+    extra = _params(56, 305.0, 3.0, seed=77)
+    with Batch(ps) as b:
+        b.sweep([5, 7, 3])
+        t1 = b.observables_enqueue([0, 1, 2])
+        b.sweep([4, 0, 6])
+        t2 = b.observables_enqueue([2])
+        b.remove(1)
+        assert b.add(extra) == 1
+        b.sweep([0, 9, 0])
+        t3 = b.observables_enqueue([1, 0])
+        mapped, used = b.pool_bytes()
+        assert mapped >= used > 0
+        o3 = b.observables_collect(t3, 2)
+        o1 = b.observables_collect(t1, 3)
+        o2 = b.observables_collect(t2, 1)
+        with pytest.raises(_capi.CvfError):
+            b.observables_collect(t1, 2)          # wrong record count
+        many = b.observables_many([0, 2, 1])
+        single = [b.observables(i) for i in (0, 2, 1)]
+        for a, c in zip(many, single):
+            _same(a, c)
+        for _ in range(4):                        # four newer tickets reuse t3's slot
+            b.observables_enqueue([0])
+        with pytest.raises(_capi.CvfError):
+            b.observables_collect(t3, 2)
+        assert b.observables_enqueue([]) >= 0
+    _same(o1[0], _solo(ps[0], [5])[1])
+    _same(o1[1], _solo(ps[1], [7])[1])
+    _same(o1[2], _solo(ps[2], [3])[1])
+    _same(o2[0], _solo(ps[2], [3, 6])[1])
+    _same(o3[0], _solo(extra, [9])[1])
+    _same(o3[1], _solo(ps[0], [5, 4])[1])

@@ -93,3 +93,80 @@ def test_trace_summary():
     assert stats["jobs_finished"] == 8 and stats["jobs_waiting"] == 0
     assert stats["latency_p50_s"] > 0 and stats["latency_p99_s"] >= stats["latency_p50_s"]
     assert stats["replica_sweeps_per_s"] > 0
+    assert stats["jobs_censored"] == 0 and not stats["latency_all_is_lower_bound"]
+    assert stats["latency_all_p50_s"] == stats["latency_p50_s"]
+    assert 0.0 < stats["gpu_busy_per_wall_s"] <= 1.05
+
+
+def _obs_same(job):
+    _, o = _alone(job)
+    for k in ("sweep", "n_hb_raw", "n_coop", "acc_sigma", "acc_volume", "g", "n_state"):
+        assert job.observables[k] == o[k], (job.id, k)
+    for k in ("V_iso", "V", "U_LJ", "H"):
+        assert abs(job.observables[k] - o[k]) <= 1e-12 * abs(o[k]), (job.id, k)
+
+
+@pytest.mark.parametrize("overlap", [True, False])
+def test_pipelined_epochs_match_solo_runs(overlap):
+    """With overlap on, epoch k+1 is enqueued before epoch k's results are
+    read; every job's observables (read back through tickets, no state
+    copies) still equal its solo run, zero-step jobs included."""
+    jobs = _jobs(12, seed=9)
+    for j in jobs:
+        j.keep_state = False
+    jobs[5].sweeps = 0
+    srv = Server(epoch_steps=29, overlap=overlap)
+    try:
+        for j in jobs[:5]:
+            srv.submit(j)
+        srv.step()
+        for j in jobs[5:9]:
+            srv.submit(j)
+        srv.step()
+        srv.step()
+        for j in jobs[9:]:
+            srv.submit(j)
+        while srv.busy():
+            srv.step()
+    finally:
+        srv.close()
+    assert len(srv.finished) == len(jobs) and not srv.inflight
+    assert srv.gpu_busy_s > 0
+    for j in jobs:
+        assert j.done == j.sweeps
+        _obs_same(j)
+
+
+def test_never_fitting_job_is_refused():
+    jobs = _jobs(3, seed=11)
+    big = Job(T=300.0, P=0.1, L=4096, sweeps=10, seed=1)
+    srv = Server(epoch_steps=50, mem_budget_bytes=max(j.device_bytes for j in jobs))
+    try:
+        srv.submit(big)
+        for j in jobs:
+            srv.submit(j)
+        assert big.error and big in srv.rejected and big not in srv.waiting
+        while srv.busy():
+            srv.step()
+    finally:
+        srv.close()
+    assert len(srv.finished) == 3 and big.finished is None
+
+
+def test_censored_latency_is_reported():
+    """Under a time limit that ends the run early, the all-arrived latency
+    percentiles count unfinished jobs with the time they waited (a lower
+    bound), and say so."""
+    jobs = [Job(T=300.0, P=0.1, L=1024, sweeps=50000, seed=100 + i, arrival=0.001 * i)
+            for i in range(6)]
+    jobs.append(Job(T=300.0, P=0.1, L=16, sweeps=10, seed=99, arrival=0.0))
+    srv = Server(epoch_steps=100)
+    try:
+        stats = srv.run_trace(jobs, time_limit=0.5)
+    finally:
+        srv.close()
+    assert stats["jobs_arrived"] == 7
+    assert stats["jobs_censored"] >= 1 and stats["latency_all_is_lower_bound"]
+    assert stats["jobs_finished"] + stats["jobs_censored"] == 7
+    assert stats["latency_all_p99_s"] >= 0.45
+    assert 0.0 < stats["gpu_busy_per_wall_s"] <= 1.05
