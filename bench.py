@@ -673,7 +673,8 @@ def measure_batched(args, rank):
                                       "form": "each replica alone in its fastest single-lattice "
                                               "form (small lattices resident in one cluster)"},
             "speedup_vs_one_lattice_at_a_time": batched_rate / alone_rate,
-            "tile_config": best, "tile": list(tile_configs()[best]),
+            "tile_config": best, "tile": list(tile_configs()[best][:2]),
+            "block_threads": tile_configs()[best][2],
             "cells_per_thread": cells_per_thread(best), "autotune_ms_per_step": timings,
             "workload": "256 replicas, L from {32,64,128,256,512} (seed 4), T_i = 270 + 4i K, "
                         "P_j = 0.1 + j 49.9/15 MPa, seeds 1000 + r"}

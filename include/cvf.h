@@ -317,15 +317,21 @@ int cvf_batch_observables_collect(cvf_batch *b, int64_t ticket, cvf_obs *out,
 int cvf_batch_get_state(cvf_batch *b, int32_t replica, uint16_t *host,
                         size_t n);
 
-/* Tile shape of the batched kernel: config c >= 0 selects rows x words from
- * a fixed list (cvf_batch_tile_config; the autotuner times them all), -1
- * (the default) chooses per call: the largest shape whose tiles over the
- * replicas the call advances are at least as many as the kernel's
+/* Kernel configuration of the batched sweep: config c >= 0 selects a tile
+ * of rows x 32-bit words and a block size from a fixed list of twelve
+ * (cvf_batch_tile_config, cvf_batch_config_threads): configs 0..3 are the
+ * tiles 64x64, 32x32, 32x16, 16x16 (rows x words) with 256-thread blocks,
+ * configs 4..7 the same tiles with 128-thread blocks and 8..11 with
+ * 512-thread blocks, so a thread updates 2 rows words / threads cells per
+ * MC step independently of the tile.  -1
+ * (the default) chooses among configs 0..3 per call: the largest tile whose
+ * count over the replicas the call advances is at least the kernel's
  * co-resident blocks, else the smallest.  cvf_batch_get_tiles returns the
- * setting and the shape the last call used (-1 before any call). */
+ * setting and the configuration the last call used (-1 before any call). */
 int cvf_batch_set_tiles(cvf_batch *b, int32_t config);
 int cvf_batch_get_tiles(cvf_batch *b, int32_t *config, int32_t *last_used);
 int cvf_batch_tile_config(int32_t config, int32_t *rows, int32_t *words);
+int cvf_batch_config_threads(int32_t config, int32_t *threads);
 
 /* Device memory the batch's pool has mapped (reserved) and of that what
  * live replicas and the descriptor array hold (used); reserved - used is

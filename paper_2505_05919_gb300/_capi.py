@@ -97,6 +97,7 @@ _SIGS = {
     "cvf_batch_set_tiles": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "cvf_batch_get_tiles": (ctypes.c_int, [_vp, _P(ctypes.c_int32), _P(ctypes.c_int32)]),
     "cvf_batch_tile_config": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_int32)]),
+    "cvf_batch_config_threads": (ctypes.c_int, [ctypes.c_int32, _P(ctypes.c_int32)]),
     "cvf_batch_destroy": (ctypes.c_int, [_vp]),
     # cubic lattice (the paper's 3D model)
     "cvf3_params_physical": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _P(cvf_params)]),
@@ -345,10 +346,12 @@ def cvf_batch_get_tiles(b: int) -> tuple:
 
 
 def cvf_batch_tile_config(config: int):
-    r, w = ctypes.c_int32(), ctypes.c_int32()
+    """(rows, words, block threads) of a batched-kernel configuration."""
+    r, w, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().cvf_batch_tile_config(config, ctypes.byref(r), ctypes.byref(w)),
            "cvf_batch_tile_config")
-    return r.value, w.value
+    _check(load().cvf_batch_config_threads(config, ctypes.byref(t)), "cvf_batch_config_threads")
+    return r.value, w.value, t.value
 
 
 def cvf_batch_destroy(b: int) -> None:

@@ -1,16 +1,21 @@
 """Autotuner of the batched kernel's tile shape and cells per thread.
 
-A tile configuration is a tile of rows x 32-bit words (two cells per word)
-swept by one block of 256 threads, so it fixes the cells each thread
-updates per colour phase: 64 x 64 words -> 32 cells per thread (16 per
-phase), 32 x 32 -> 8, 32 x 16 -> 4, 16 x 16 -> 2.  Large tiles amortise the
-recomputed one-cell ring and the staging; small ones give small lattices
-enough tiles to fill the GPU.
+A configuration is a tile of rows x 32-bit words (two cells per word) and the
+block of threads that sweeps it; together they fix the cells each thread
+updates per MC step, 2 rows words / threads.  The two dimensions are
+searched as a product: four tiles (64 x 64, 32 x 32, 32 x 16, 16 x 16) with
+256-thread blocks (32, 8, 4, 2 cells per thread), with 128-thread blocks
+(64, 16, 8, 4) and with 512-thread blocks (16, 4, 2, 1).  Large tiles
+amortise the recomputed one-cell ring and the staging; small ones give small
+lattices enough tiles to fill the GPU; more cells per thread give each
+thread more independent cells to interleave, fewer shorten the chain of one
+tile's work (a small lattice's step is a chain of such tiles).
 
 For a list of replica parameters the tuner builds a scratch batch with the
 same lattice sizes (other seeds, so the caller's replicas are untouched),
 times a short probe on every configuration with CUDA events, and returns
-the fastest.  Results are cached per size signature for the process.
+the fastest.  Results are cached for the process by the mix of (L, q,
+rng_words) and the probe length.
 """
 from __future__ import annotations
 
@@ -28,8 +33,8 @@ def signature(params_list) -> tuple:
 
 def cells_per_thread(config: int) -> int:
     """Cells one of the block's 256 threads updates per MC step."""
-    rows, words = tile_configs()[config]
-    return 2 * rows * words // 256
+    rows, words, threads = tile_configs()[config]
+    return 2 * rows * words // threads
 
 
 def autotune(params_list, probe_sweeps: int = 20, warmup: int = 3, stream=None):

@@ -14,7 +14,8 @@ from ._capi import cvf_params
 
 
 def tile_configs():
-    """The (rows, words) tile shapes the batched kernel can use."""
+    """The (rows, words, block threads) configurations the batched kernel can
+    use; the first four are the ones the automatic per-call choice takes."""
     out = []
     c = 0
     while True:
@@ -65,9 +66,9 @@ class Batch:
         _capi.cvf_batch_sync(self.b)
 
     def set_tiles(self, config: int) -> None:
-        """Tile configuration (index into tile_configs()), or -1 (the default)
-        to let each call choose the largest shape that still gives every
-        co-resident block a tile."""
+        """Kernel configuration (index into tile_configs()), or -1 (the
+        default) to let each call choose the largest 256-thread tile that
+        still gives every co-resident block a tile."""
         _capi.cvf_batch_set_tiles(self.b, config)
 
     def tiles(self) -> tuple:

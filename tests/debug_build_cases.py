@@ -52,9 +52,10 @@ def cubic(L, steps, resident=-1):
         lat.observables()
 
 
-def batch(sizes, steps):
+def batch(sizes, steps, config=-1):
     ops = [oracle.physical_params(300.0, 0.1, L=L, seed=100 + L) for L in sizes]
     with Batch([params_from_dict(asdict(op)) for op in ops]) as b:
+        b.set_tiles(config)
         b.sweep([steps] * len(ops))
         for i, op in enumerate(ops):
             ref = oracle.Oracle(op)
@@ -101,6 +102,8 @@ def main():
     for L, res in ((8, 0), (9, 0), (12, 0), (16, 1), (24, 1), (16, 0), (130, 0)):
         cubic(L, 5, res)
     batch([16, 34, 64, 130, 2], 12)
+    for config in (0, 4, 7, 8, 11):   # 256-, 128- and 512-thread blocks
+        batch([16, 34, 130, 2], 7, config)
     noalloc(64, 7)
     noalloc(130, 6)
     print("debug build: all cases match, no index check failed")

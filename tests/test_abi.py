@@ -143,9 +143,14 @@ def test_batch_tile_configs_and_cells_per_thread(lib):
     from paper_2505_05919_gb300.autotune import cells_per_thread
     from paper_2505_05919_gb300.batch import tile_configs
     cfgs = tile_configs()
-    assert cfgs[0] == (64, 64)
-    assert [cells_per_thread(c) for c in range(len(cfgs))] == [2 * r * w // 256 for r, w in cfgs]
-    assert cells_per_thread(0) == 32 and min(cells_per_thread(c) for c in range(len(cfgs))) >= 1
+    assert len(cfgs) == 12 and cfgs[0] == (64, 64, 256) and cfgs[4] == (64, 64, 128)
+    # the same four tiles with 256-, 128- and 512-thread blocks
+    assert [c[:2] for c in cfgs[:4]] == [c[:2] for c in cfgs[4:8]] == [c[:2] for c in cfgs[8:]]
+    assert [{c[2] for c in cfgs[k:k + 4]} for k in (0, 4, 8)] == [{256}, {128}, {512}]
+    assert [cells_per_thread(c) for c in range(len(cfgs))] == [2 * r * w // t for r, w, t in cfgs]
+    assert [cells_per_thread(c) for c in range(12)] == [32, 8, 4, 2, 64, 16, 8, 4, 16, 4, 2, 1]
+    with pytest.raises(_capi.CvfError):
+        _capi.cvf_batch_tile_config(12)
 
 
 def test_release_build_has_no_debug_checks(lib):

@@ -52,7 +52,7 @@ MIX = [  # L, T, P, extra
 ]
 
 
-@pytest.mark.parametrize("cfg", range(4))
+@pytest.mark.parametrize("cfg", range(12))
 def test_batch_equals_solo_every_tile_config(cfg):
     ps = [_params(L, T, P, **kw) for (L, T, P, kw) in MIX]
     steps = [23, 7, 15, 40, 3, 11, 60, 33]
@@ -160,7 +160,7 @@ def test_batch_automatic_tile_choice():
         assert all(np.array_equal(b.state(i), s_auto[i]) for i in range(len(big)))
     with Batch(small) as b:
         b.sweep([4] * len(small))
-        assert b.tiles()[1] == len(tile_configs()) - 1   # few cells: the smallest shape
+        assert b.tiles()[1] == 3   # few cells: the smallest automatic shape
         for i, p in enumerate(small):
             s, _ = _solo(p, [4])
             assert np.array_equal(b.state(i), s)
@@ -208,3 +208,21 @@ def test_batch_tickets_and_stream_ordered_churn():
     _same(o2[0], _solo(ps[2], [3, 6])[1])
     _same(o3[0], _solo(extra, [9])[1])
     _same(o3[1], _solo(ps[0], [5, 4])[1])
+
+
+@pytest.mark.parametrize("cfg", [0, 3, 4, 7, 8, 11])
+def test_batch_two_word_draws_every_block_size(cfg):
+    """Two Philox words per update (rng_words=2) through the 256-, 128- and
+    512-thread kernels."""
+    mix = [(48, 290.0, 5.0, dict(seed=21)), (130, 315.0, 30.0, dict(seed=22, q=5)),
+           (8, 300.0, 0.1, dict(seed=23, init=oracle.INIT_ORDERED))]
+    ps = [_params(L, T, P, rng_words=2, **kw) for (L, T, P, kw) in mix]
+    steps = [17, 9, 31]
+    with Batch(ps) as b:
+        b.set_tiles(cfg)
+        b.sweep(steps)
+        got = [(b.state(i), b.observables(i)) for i in range(len(ps))]
+    for i, p in enumerate(ps):
+        s, o = _solo(p, [steps[i]])
+        assert np.array_equal(got[i][0], s), (cfg, i)
+        _same(got[i][1], o)
