@@ -324,10 +324,12 @@ int cvf_batch_get_state(cvf_batch *b, int32_t replica, uint16_t *host,
  * configs 4..7 the same tiles with 128-thread blocks and 8..11 with
  * 512-thread blocks, so a thread updates 2 rows words / threads cells per
  * MC step independently of the tile.  -1
- * (the default) chooses among configs 0..3 per call: the largest tile whose
- * count over the replicas the call advances is at least the kernel's
- * co-resident blocks, else the smallest.  cvf_batch_get_tiles returns the
- * setting and the configuration the last call used (-1 before any call). */
+ * (the default) chooses per call: the largest 256-thread tile whose count
+ * over the replicas the call advances is at least the kernel's co-resident
+ * blocks; else the smallest tile, with 512-thread blocks (config 11) when
+ * its count is below a quarter of the blocks and 256-thread blocks (config
+ * 3) otherwise.  cvf_batch_get_tiles returns the setting and the
+ * configuration the last call used (-1 before any call). */
 int cvf_batch_set_tiles(cvf_batch *b, int32_t config);
 int cvf_batch_get_tiles(cvf_batch *b, int32_t *config, int32_t *last_used);
 int cvf_batch_tile_config(int32_t config, int32_t *rows, int32_t *words);

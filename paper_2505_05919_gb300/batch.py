@@ -68,7 +68,9 @@ class Batch:
     def set_tiles(self, config: int) -> None:
         """Kernel configuration (index into tile_configs()), or -1 (the
         default) to let each call choose the largest 256-thread tile that
-        still gives every co-resident block a tile."""
+        still gives every co-resident block a tile (the smallest tile, with
+        512-thread blocks when its tiles are under a quarter of the
+        blocks)."""
         _capi.cvf_batch_set_tiles(self.b, config)
 
     def tiles(self) -> tuple:

@@ -276,20 +276,24 @@ int resident_grid(cvf_batch* b, int cfg, bool cmp64, int* grid) {
 }
 
 // The automatic tile shape of a call: the largest whose tiles over the
-// advanced replicas give every co-resident block a tile per step.
+// advanced replicas give every co-resident block a tile per step.  When even
+// the smallest tile leaves three quarters of the blocks without one, a step
+// is a latency chain through few tiles, and the same tile with 512-thread
+// blocks (one cell per thread per colour) shortens each tile's part of it.
 int auto_tile_config(cvf_batch* b, const std::vector<int32_t>& act, bool cmp64, int* cfg) {
+  long long tiles = 0;
+  int grid = 0;
   for (int c = 0; c < kNumAutoConfigs; ++c) {
-    int grid = 0;
     const int rc = resident_grid(b, c, cmp64, &grid);
     if (rc) return rc;
-    long long tiles = 0;
+    tiles = 0;
     for (int i : act) tiles += tiles_of(b->reps[i].p.L, c);
     if (tiles >= grid) {
       *cfg = c;
       return CVF_OK;
     }
   }
-  *cfg = kNumAutoConfigs - 1;
+  *cfg = (4 * tiles < grid) ? kNumTileConfigs - 1 : kNumAutoConfigs - 1;
   return CVF_OK;
 }
 

@@ -160,7 +160,9 @@ def test_batch_automatic_tile_choice():
         assert all(np.array_equal(b.state(i), s_auto[i]) for i in range(len(big)))
     with Batch(small) as b:
         b.sweep([4] * len(small))
-        assert b.tiles()[1] == 3   # few cells: the smallest automatic shape
+        # 2 + 8 + 1 tiles of 16 x 16 words, under a quarter of the blocks:
+        # the smallest tile with 512-thread blocks
+        assert b.tiles()[1] == 11
         for i, p in enumerate(small):
             s, _ = _solo(p, [4])
             assert np.array_equal(b.state(i), s)

@@ -105,17 +105,25 @@ def test_checkerboard_every_tile_shape(config, L, K, extra):
                                        (128, 60, dict(T=270.0, init=oracle.INIT_ORDERED)),
                                        (256, 20, dict(q=8)), (24, 150, dict(kT=1e-3)),
                                        (32, 400, dict(kT=3.0, P=1.2, epsilon=0.0, v_iso_init=1.9,
-                                                      dv_max_frac=0.2))])
+                                                      dv_max_frac=0.2)),
+                                       (64, 700, dict(T=330.0, dv_max_frac=0.3)),
+                                       (16, 900, dict(kT=1.5, P=0.4, v_iso_init=1.98,
+                                                      dv_max_frac=0.01))])
 def test_resident_cluster_sweep(L, K, extra):
     """The resident form (the lattice in one cluster's shared memory for the
     whole call) gives the oracle's lattice, counts and recorded series --
-    both RNG modes, both inits, q = 8, the 64-bit compare, gate flips."""
+    both RNG modes, both inits, q = 8, the 64-bit compare, gate flips.  The
+    volume moves are decided ahead in passes over five steps' outcomes: the
+    V_iso series recorded every step equals the oracle's for long runs with
+    many rejected and accepted moves, and near the gate (v_iso close to 2,
+    small steps) where passes stop at gate-changing proposals."""
     extra = dict(extra)
     if "kT" in extra:
         op = oracle.OracleParams(L=L, seed=400 + L, **extra)
     else:
         T = extra.pop("T", 300.0)
-        op = oracle.physical_params(T, 0.1, L=L, seed=400 + L, dv_max_frac=0.02, **extra)
+        dv = extra.pop("dv_max_frac", 0.02)
+        op = oracle.physical_params(T, 0.1, L=L, seed=400 + L, dv_max_frac=dv, **extra)
     with Lattice(params_from_dict(asdict(op))) as lat:
         lat.set_tiles(3)
         assert lat.tiles() == (3, L // 8, L // 2)
