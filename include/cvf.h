@@ -196,12 +196,17 @@ int cvf_state_device_ptr(cvf_handle *h, void **dev_ptr);
 
 /* Tile shape of the checkerboard sweep: config 0 = 64 rows x 64 words (128
  * cells), 1 = 32 x 32, 2 = 16 x 32, 3 = the whole lattice resident in the
- * shared memory of one 8-CTA thread-block cluster for many steps per launch
- * (16 <= L <= 256, L a multiple of 8; rows = L/8 per CTA); -1 = automatic
- * (chosen at creation: the resident form for small lattices, else the
- * largest tile shape whose tiles fill every resident block).  The result
- * does not depend on the shape; set_tiles waits for the stream.  CVF_EINVAL
- * for other values, or config 3 where it does not apply. */
+ * shared memory of one thread-block cluster (8 CTAs hold rows, a ninth
+ * decides the volume moves ahead) for many steps per launch (16 <= L <=
+ * 256, L a multiple of 8; rows = L/8 per CTA); 4, 5, 6 = the tiles of 0, 1,
+ * 2 swept by one persistent cooperative launch per call in which a tile of
+ * step s + 1 waits only for the tiles around it to finish step s (a
+ * wavefront; the volume moves decided ahead by one block; L a multiple of 8
+ * and at least 3 x 3 tiles); -1 = automatic (chosen at creation: the
+ * resident form for small lattices, else the largest tile shape whose tiles
+ * fill every resident block, swept as a wavefront for 640 <= L <= 2560).  The result does not depend on the config;
+ * set_tiles waits for the stream.  CVF_EINVAL for other values, or a config
+ * that does not apply to the lattice. */
 int cvf_set_tiles(cvf_handle *h, int32_t config);
 int cvf_get_tiles(cvf_handle *h, int32_t *config, int32_t *rows,
                   int32_t *words);

@@ -464,6 +464,7 @@ __device__ __forceinline__ void finalize_step(const VolumeArgs& V, Ctrl* ctl, cv
   c->tile_next = 0;
   c->sweep = s.sweep;
   if (recorded) {
+    s.error = c->error;  // the record's status word
     for (int v = 0; v < 8; ++v) {
       s.hist[v] = (long long)c->acc_hist[v];
       c->hist[v] = s.hist[v];

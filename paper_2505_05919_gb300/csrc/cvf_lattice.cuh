@@ -57,6 +57,39 @@ bool resident_fits(const LatticeArgs& A, int rng_words, bool cmp64);
 cudaError_t launch_resident(const LatticeArgs& A, int rng_words, bool cmp64, long long n_steps,
                             cudaStream_t s);
 
+// The wavefront sweep (cvf_wave.cu): one persistent cooperative launch per
+// call, a tile of step s + 1 waiting only for the 3 x 3 tiles around it to
+// finish step s, the volume moves decided ahead by block 0.  Its scratch in
+// device memory: this header, then one progress word per tile.
+constexpr int kWaveRing = 16;  // MC steps in flight at most
+struct WaveMove {              // the volume move of a step, published by the engine
+  double V, u;
+  int g, acc;
+  unsigned int tag;            // relative step + 1 once published
+  unsigned int pad;
+};
+struct WaveAcc {               // a step's counts, added by its tiles
+  unsigned long long hb, pairs, moves;
+  unsigned long long hist[8];
+  unsigned int done;           // tiles of the step finished
+  unsigned int pad;
+};
+struct WaveHdr {
+  unsigned long long next;     // item counter
+  unsigned long long pad0[15]; // alone in its 128-byte line
+  unsigned int committed;      // steps of the call committed
+  unsigned int abort;          // nonzero: a wait gave up, every block stops
+  unsigned int pad1[30];
+  WaveMove vring[kWaveRing];
+  WaveAcc acc[kWaveRing];
+};
+// Co-resident blocks of the wavefront kernel for a tile shape (0 if none).
+int wave_blocks(int rng_words, bool cmp64, int shape);
+// Clears the scratch (scratch_bytes) and launches the call's steps.
+cudaError_t launch_wave(const LatticeArgs& A, WaveHdr* H, size_t scratch_bytes, int rng_words,
+                        bool cmp64, int shape, long long step0, long long n_steps,
+                        cudaStream_t s);
+
 // Host helpers shared by both paths.
 void fill_volume_args(const cvf_params* p, long long N, const std::vector<int64_t>& d2,
                       const std::vector<int64_t>& mult, VolumeArgs* va);

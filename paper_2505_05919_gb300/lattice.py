@@ -79,7 +79,9 @@ class Lattice:
 
     def set_tiles(self, config: int) -> None:
         """Tile shape of the sweep (0: 64x64, 1: 32x32, 2: 16x32 words; 3: the
-        whole lattice resident in one thread-block cluster; -1: automatic)."""
+        whole lattice resident in one thread-block cluster; 4, 5, 6: the
+        shapes of 0, 1, 2 in the wavefront sweep, one persistent launch per
+        call; -1: automatic)."""
         _capi.cvf_set_tiles(self.h, config)
 
     def tiles(self):

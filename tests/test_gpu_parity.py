@@ -140,14 +140,66 @@ def test_resident_cluster_sweep(L, K, extra):
         assert_obs_equal(a, b, ("record", i))
 
 
+@pytest.mark.parametrize("config,L,K,extra", [
+    (6, 136, 40, {}),                                     # 16 x 32 words: 3 x 9 tiles, ragged
+    (6, 200, 30, dict(rng_words=2)),
+    (5, 200, 25, dict(T=270.0, init=oracle.INIT_ORDERED)),  # 32 x 32: 4 x 7 tiles
+    (4, 392, 12, {}),                                     # 64 x 64: 4 x 7 tiles
+    (6, 136, 60, dict(kT=1e-3)),                          # the 64-bit threshold compare
+    # v_iso near 2 with a weak bond energy: the gate changes ~50 times in
+    # 300 steps, each decided after the step before is committed
+    (6, 136, 300, dict(kT=2.4, P=1.2, epsilon=0.0, J=1e-4, J_sigma=0.0, v_HB=0.0,
+                       v_iso_init=2.0, dv_max_frac=0.01)),
+    (5, 256, 200, dict(dv_max_frac=0.3)),
+])
+def test_wavefront_sweep(config, L, K, extra):
+    """The wavefront sweep (one persistent launch per call; a tile of step
+    s + 1 waits only for the tiles around it; the volume moves decided ahead
+    by one block, gate-changing ones after the step before is committed)
+    gives the oracle's lattice, counts and series recorded every step -- with
+    up to sixteen steps in flight on small tile grids, ragged tiles, both RNG
+    modes, both inits, the 64-bit compare and gate flips; and a second call
+    continues the first."""
+    extra = dict(extra)
+    if "kT" in extra:
+        op = oracle.OracleParams(L=L, seed=500 + L, **extra)
+    else:
+        T = extra.pop("T", 300.0)
+        dv = extra.pop("dv_max_frac", 0.02)
+        op = oracle.physical_params(T, 0.1, L=L, seed=500 + L, dv_max_frac=dv, **extra)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        lat.set_tiles(config)
+        assert lat.tiles()[0] == config
+        lat.sweep(K // 3, 1)
+        lat.sweep(K - K // 3, 1)
+        s_gpu, o_gpu = lat.state(), lat.observables()
+        r_gpu, _ = lat.drain()
+        assert lat.recount() == (o_gpu["n_hb_raw"], o_gpu["n_coop"])
+    s_ref, o_ref, r_ref = oracle_run(op, K, record_every=1)
+    assert np.array_equal(s_gpu, s_ref)
+    assert_obs_equal(o_gpu, o_ref)
+    assert len(r_gpu) == len(r_ref) == K
+    for i, (a, b) in enumerate(zip(r_gpu, r_ref)):
+        assert_obs_equal(a, b, ("record", i))
+    if "v_iso_init" in extra:
+        gs = [r["g"] for r in r_ref]
+        assert sum(1 for a, b in zip(gs, gs[1:]) if a != b) >= 3
+
+
 def test_tile_choice():
     with Lattice(params(300.0, 0.1, L=4096)) as lat:
         assert lat.tiles() == (0, 64, 64)  # the large tile at the benchmark size
+    with Lattice(params(300.0, 0.1, L=1024)) as lat:
+        assert lat.tiles() == (6, 16, 32)  # mid-size lattices: the wavefront sweep
+    with Lattice(params(300.0, 0.1, L=2048)) as lat:
+        assert lat.tiles() == (5, 32, 32)
     with Lattice(params(300.0, 0.1, L=256)) as lat:
         c, r, w = lat.tiles()
         assert c in (0, 1, 2, 3)
         with pytest.raises(_capi.CvfError):
-            lat.set_tiles(4)
+            lat.set_tiles(4)      # the wavefront needs 3 x 3 tiles: 2 x 4 of 64 x 64 words
+        with pytest.raises(_capi.CvfError):
+            lat.set_tiles(7)
     with Lattice(params(300.0, 0.1, L=64)) as lat:
         assert lat.tiles()[0] == 3  # small lattices run resident in one cluster
     with Lattice(params(300.0, 0.1, L=130)) as lat:
