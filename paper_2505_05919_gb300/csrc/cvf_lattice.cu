@@ -850,11 +850,11 @@ int wave_scratch(cvf_handle* h, int shape) {
 
 // The automatic configuration: the resident form for small lattices; the
 // wavefront sweep for mid-size ones (measured on GB300 with the tiled
-// sweep's shape rule: 640^2 9.9 against 10.3 us per step, 1024^2 13.5
-// against 15.8, 1536^2 24.0 against 26.9, 2560^2 59.4 against 60.5; at
-// 512^2 and from 3072^2 on the tiled sweep is ahead); else the tiled sweep
-// with the largest shape whose tiles fill every resident block.
-constexpr int kWaveAutoMin = 640, kWaveAutoMax = 2560;
+// sweep's shape rule: 512^2 8.4 against 9.0 us per step, 1024^2 12.6
+// against 15.8, 2048^2 38.9 against 41.1, 2560^2 59.4 against 60.5; from
+// 3072^2 on the tiled sweep is ahead); else the tiled sweep with the
+// largest shape whose tiles fill every resident block.
+constexpr int kWaveAutoMin = 512, kWaveAutoMax = 2560;
 int auto_config(const cvf_handle* h) {
   const cvf_params& p = h->p;
   if (p.schedule == CVF_SCHED_CHECKERBOARD && p.L <= kResAutoSide &&

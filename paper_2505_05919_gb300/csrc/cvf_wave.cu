@@ -47,6 +47,21 @@ __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) 
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_u32(unsigned int* p, unsigned int v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int atom_add_relaxed_u32(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.relaxed.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
 __device__ __forceinline__ void engine_sync() {
   asm volatile("bar.sync %0, 64;" ::"n"(kWaveEngineBar) : "memory");
 }
@@ -74,7 +89,7 @@ __device__ bool wave_wait_geq(const unsigned int* flag, unsigned int target, Wav
 // lane 10 the commit of step r - kWaveRing (its slots are free).  With
 // `block`, waits (bounded) until all hold; returns whether they hold (false
 // also on an abort).  The move's gate is returned in *g (lane 0).
-__device__ bool wave_deps(WaveHdr* H, const unsigned int* prog, long long r, int t, int tiles_x,
+__device__ bool wave_deps(WaveHdr* H, const unsigned int* prog, int r, int t, int tiles_x,
                           int tiles_y, bool block, unsigned int* err, int* g) {
   const int lane = (int)(threadIdx.x & 31u);
   const unsigned int* flag = nullptr;
@@ -182,8 +197,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
   } U;
   __shared__ Tables2 Tb;
   __shared__ uint32_t s_hist4[4];
-  __shared__ long long s_r, n_r;
-  __shared__ int s_t, s_ok, s_g, s_staged, n_t, n_ok, n_ready, n_g;
+  __shared__ int s_r, s_t, s_ok, s_g, s_staged, n_r, n_t, n_ok, n_ready, n_g;
   Ctrl* const ctl = A.ctrl;
   unsigned int* const err = &ctl->error;
 
@@ -267,8 +281,8 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     i = __shfl_sync(0xFFFFFFFFu, i, 0);
     const bool have = (long long)i < total;
     int g = 0;
-    const long long r = have ? (long long)i / T : 0;
-    const int t = have ? (int)((long long)i - r * T) : 0;
+    const int r = have ? (int)((long long)i / T) : 0;
+    const int t = have ? (int)((long long)i - (long long)r * T) : 0;
     const bool ok = have && wave_deps(H, prog, r, t, tiles_x, tiles_y, true, err, &g);
     if (threadIdx.x == 0) {
       s_ok = ok ? 1 : 0;
@@ -281,8 +295,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
   for (;;) {
     __syncthreads();
     if (!s_ok) break;
-    const long long r = s_r;
-    const int t = s_t, g = s_g, staged = s_staged;
+    const int r = s_r, t = s_t, g = s_g, staged = s_staged;
     const long long step = step0 + r;
     if (g != g_cur) {  // block-uniform
       fill_rows2(Tb, A.table24, g);
@@ -321,8 +334,8 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       i = __shfl_sync(0xFFFFFFFFu, i, 0);
       const bool have = (long long)i < total;
       int g2 = 0;
-      const long long r2 = have ? (long long)i / T : 0;
-      const int t2 = have ? (int)((long long)i - r2 * T) : 0;
+      const int r2 = have ? (int)((long long)i / T) : 0;
+      const int t2 = have ? (int)((long long)i - (long long)r2 * T) : 0;
       const bool ready = have && wave_deps(H, prog, r2, t2, tiles_x, tiles_y, false, err, &g2);
       if ((threadIdx.x & 31u) == 0) {
         n_ok = have ? 1 : 0;
@@ -352,14 +365,18 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     uint32_t dhb = (uint32_t)cnt.dhb(), dc = (uint32_t)cnt.dc(), nacc = cnt.nacc;
     block_sum3<kThreads>(dhb, dc, nacc);  // ends with a barrier: the tile's stores are done
     if (threadIdx.x == 0) {
-      // the tile's words to the tiles of the next step around it
-      __threadfence();
-      st_release_u32(&prog[t], (unsigned int)(r + 1));
+      // one fence releases the tile's words (ordered by the block's barrier)
+      // and its counts before both the progress word, which the tiles of the
+      // next step around it acquire, and the step's completion count
       atomicAdd(&slot->hb, (unsigned long long)(long long)(int)dhb);
       atomicAdd(&slot->pairs, (unsigned long long)(long long)(int)dc);
       atomicAdd(&slot->moves, (unsigned long long)nacc);
-      // the last tile of the step commits it, after the step before
-      if (atom_add_acq_rel(&slot->done, 1u) == (unsigned int)(T - 1)) {
+      fence_acq_rel_gpu();
+      st_relaxed_u32(&prog[t], (unsigned int)(r + 1));
+      // the last tile of the step commits it, after the step before (the
+      // fence acquires every other tile's counts, released the same way)
+      if (atom_add_relaxed_u32(&slot->done, 1u) == (unsigned int)(T - 1)) {
+        fence_acq_rel_gpu();
         if (r == 0 || wave_wait_geq(&H->committed, (unsigned int)r, H, err))
           wave_commit(A, H, step0, r);
       }
