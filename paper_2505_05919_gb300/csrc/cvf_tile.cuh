@@ -106,9 +106,9 @@ __device__ __forceinline__ uint32_t update_arm2(uint32_t w, uint32_t x, uint32_t
   const uint32_t a = (ARM >= 0) ? (uint32_t)ARM : a_rt;
   // 4 sigma: the byte offset of sigma's column in the proposal table
   uint32_t s4;
-  if (ARM == 0)
+  if constexpr (ARM == 0)
     s4 = (w << 2) & 0x1Cu;
-  else if (ARM > 0)
+  else if constexpr (ARM > 0)
     s4 = (w >> (4 * ARM - 2)) & 0x1Cu;
   else
     s4 = ((w >> (4u * a)) & 7u) << 2;
