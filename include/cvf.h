@@ -464,12 +464,12 @@ int cvf3_state_device_ptr(cvf3_handle *h, void **dev_ptr);
 
 /* Form of the sweep: mode 1 keeps the cube in the shared memory of one
  * 8-CTA thread-block cluster for all the steps of a call (L a multiple of 8,
- * 16 <= L <= 64; the z-planes split among the CTAs), 0 runs the step as four
- * launches over the cube in global memory, -1 chooses.  The results do not depend on
+ * 16 <= L <= 64; the z-planes split among the CTAs; with eta moves each CTA
+ * moves the cubes whose lower plane it holds), 0 runs the step as launches
+ * over the cube in global memory, -1 chooses.  The results do not depend on
  * the form; the call waits for the stream.  CVF_EINVAL for mode 1 where it
- * does not apply (and with eta moves, which the resident form does not
- * run).  The automatic choice (-1, the default at creation) takes the
- * resident form up to L = 24 without eta moves. */
+ * does not apply.  The automatic choice (-1, the default at creation) takes
+ * the resident form up to L = 24. */
 int cvf3_set_resident(cvf3_handle *h, int32_t mode);
 int cvf3_get_resident(cvf3_handle *h, int32_t *resident);
 

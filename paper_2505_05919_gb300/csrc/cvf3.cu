@@ -774,11 +774,14 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
   __shared__ int s_next_g, s_plan;
   __shared__ VolumeArgs sV;
   __shared__ double s_xch;
+  __shared__ unsigned long long sEtaT[18];  // eta move thresholds [g][dN_HB + 4]
+  __shared__ uint32_t sEtaMask[9];          // edge masks of the nine cube configurations
   // CTA 0 keeps the lattice's scalar state in shared memory for the whole
   // call and writes it back at the end (no global round trip per step)
   __shared__ Ctrl s_ctl;
   Ctrl* const gctl = A.ctrl;
   const uint32_t L = A.L, L2 = A.L2, G = A.G, R = L / kRes3Ctas, z0 = rank * R;
+  const bool eta_on = A.eta != nullptr;  // the eta step (App. A) opens every step
   const uint32_t q = A.q, qm1 = q - 1u;
   const bool sweeper = threadIdx.x < kRes3Threads;
   const long long step0 = gctl->sweep;
@@ -795,6 +798,8 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
     sProp[threadIdx.x - 64] = (sgm < q && k + 1u < q) ? sp * kR7 : 0u;
   }
   stage_volume_args(&sV, A.vol);
+  if (eta_on && threadIdx.x < 18) sEtaT[threadIdx.x] = A.eta_table[threadIdx.x];
+  if (eta_on && threadIdx.x < 9) sEtaMask[threadIdx.x] = A.masks[threadIdx.x];
   if (rank == 0 && threadIdx.x == 0) s_next_g = ctl->next_g;
   // the planes just below and above this slab, in the neighbours' shared memory
   const uint32_t* below = cluster.map_shared_rank(cube, (rank + kRes3Ctas - 1) % kRes3Ctas) + (R - 1) * L2;
@@ -814,7 +819,8 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
     const int nseg = plan_launches(plan);
     const bool rec = step_recorded(every, step);
     if (!sweeper) {
-      cl_arrive();  // the end of segment 0
+      // the end of the eta segment (with eta moves), else of segment 0
+      cl_arrive();
       if (rank == 0) {  // the two volume warps: the move on two FP64 pipes
         VolumeResult r;
         const bool ok = volume_decide_pair<3>((int)((threadIdx.x - kRes3Threads) >> 5), sV,
@@ -830,8 +836,8 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
       }
       __syncwarp();
       cl_wait();
-      for (int j = 1; j < nseg; ++j) cl_barrier();  // the later segments
-      cl_barrier();                                 // the step committed
+      for (int j = eta_on ? 0 : 1; j < nseg; ++j) cl_barrier();  // the later segments
+      cl_barrier();                                              // the step committed
       continue;
     }
     const int g = *next_g0;
@@ -852,6 +858,74 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
     const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
     const uint32_t s_hi = (uint32_t)((unsigned long long)step >> 32);
     uint32_t nacc = 0, hb_b = 0, dc_b = 0, pk = 0;
+    int eta_dhb = 0;  // this thread's changes of N_HB_raw by accepted cube moves
+    if (eta_on) {
+      // Step 2 of the MC step, as k_eta3: one Metropolis move of every
+      // checkerboard cube whose lower z-plane lies in this slab (its upper
+      // plane may be the next CTA's first: distributed shared memory); the
+      // eta copies of a changed edge are flipped by atomic XOR in the two
+      // corner words (other cubes flip other bits of the same words).
+      const uint32_t H = A.H;
+      uint32_t zmin[2], zcnt[2];
+#pragma unroll
+      for (uint32_t c = 0; c < 2u; ++c) {
+        const uint32_t lo = (z0 + 1u - c) >> 1;                // first Z with 2Z + c >= z0
+        const uint32_t hi = min((z0 + R + 1u - c) >> 1, H);    // first Z with 2Z + c >= z0 + R
+        zmin[c] = lo;
+        zcnt[c] = (hi > lo) ? hi - lo : 0u;
+      }
+      const uint32_t HH = H * H, n0 = zcnt[0] * HH, ncub = n0 + zcnt[1] * HH;
+      for (uint32_t i = threadIdx.x; i < ncub; i += kRes3Threads) {
+        const uint32_t c = (i >= n0) ? 1u : 0u;
+        const uint32_t k = i - c * n0;
+        const uint32_t zy = k / H, X = k - zy * H;
+        const uint32_t Zr = zy / H, Y = zy - Zr * H;
+        const uint32_t Z = zmin[c] + Zr;
+        const uint32_t cb = c * HH * H + (Z * H + Y) * H + X;  // global cube index
+        const uint32_t zl = 2u * Z + c - z0;                    // local plane of the lower corners
+        const uint32_t x0 = 2u * X + c, y0 = 2u * Y + c;
+        const uint32_t x1 = (x0 + 1u == L) ? 0u : x0 + 1u, y1 = (y0 + 1u == L) ? 0u : y0 + 1u;
+        uint32_t* const plo = cube + zl * L2;
+        uint32_t* const phi = (zl + 1u < R) ? cube + (zl + 1u) * L2 : const_cast<uint32_t*>(above);
+        uint32_t* wp[8];
+        uint32_t w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          wp[j] = ((j & 4) ? phi : plo) + ((j & 2) ? y1 : y0) * L + ((j & 1) ? x1 : x0);
+          w[j] = dcheck(zl < R && cb < A.ncube, &gctl->error, kSiteResident3) ? *wp[j] : 0u;
+        }
+        uint32_t bonds = 0;
+#pragma unroll
+        for (int e = 0; e < 12; ++e) {
+          const int d = e >> 2, lo = edge_lo(e), hi = lo | (1 << d);
+          bonds |= (uint32_t)(((w[lo] >> (8 * d)) & 7u) == ((w[hi] >> (8 * d + 4)) & 7u)) << e;
+        }
+        const uint32_t old = A.eta[cb];
+        if (!dcheck(old < 9u, &gctl->error, kSiteResident3)) continue;
+        const Words4 r = philox(cb, s_lo, s_hi, kTagEta, A.keys);
+        uint32_t nw = old + 1u + __umulhi(r.x, 8u);
+        if (nw >= 9u) nw -= 9u;
+        const uint32_t zo = sEtaMask[old], zn = sEtaMask[nw];
+        const int dhb = __popc(bonds & zo) - __popc(bonds & zn);
+        if ((unsigned long long)r.y < sEtaT[g * 9 + dhb + 4]) {
+          A.eta[cb] = (uint8_t)nw;
+          eta_dhb += dhb;
+          const uint32_t flip = zo ^ zn;
+          uint32_t x[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+          for (int e = 0; e < 12; ++e) {
+            const int d = e >> 2, lo = edge_lo(e), hi = lo | (1 << d);
+            const uint32_t f = (flip >> e) & 1u;
+            x[lo] ^= f << (8 * d + 3);
+            x[hi] ^= f << (8 * d + 7);
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (x[j]) atomicXor(wp[j], x[j]);
+        }
+      }
+      cl_barrier();  // every flip is in place before the sigma passes
+    }
     for (int j = 0; j < nseg; ++j) {
       int arms[3] = {0, 0, 0};
       const int n_arms = plan_arms(plan, j, arms);
@@ -903,7 +977,7 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
       }
       if (j == nseg - 1) {
         // the step's counts (and N_q') into CTA 0 before the last barrier
-        uint32_t a1 = hb_b - nacc, a2 = dc_b - 5u * nacc, a3 = nacc;
+        uint32_t a1 = hb_b - nacc + (uint32_t)eta_dhb, a2 = dc_b - 5u * nacc, a3 = nacc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           a1 += __shfl_xor_sync(0xFFFFFFFFu, a1, o);
@@ -1360,8 +1434,7 @@ int cvf3_create(const cvf_params* p, void* stream, void* dev_state, cvf3_handle*
     per_sm = 1;
   const long long blocks = ((long long)A.groups + kThreads3 - 1) / kThreads3;
   h->grid = (int)std::max<long long>(1, std::min<long long>(blocks, (long long)sm_count() * per_sm));
-  // the resident form does not run the eta step
-  h->resident = !p->eta_moves && (int)L <= kRes3AutoSide && resident3_fits(A, h->cmp64);
+  h->resident = (int)L <= kRes3AutoSide && resident3_fits(A, h->cmp64);
   h->grid_count = (int)std::max<long long>(
       1, std::min<long long>((h->N + kThreads3 - 1) / kThreads3, (long long)sm_count() * 8));
   h->grid_eta = (int)std::max<long long>(
@@ -1585,10 +1658,10 @@ int cvf3_recount(cvf3_handle* h, int64_t* n_hb_raw, int64_t* n_sigma) {
 int cvf3_set_resident(cvf3_handle* h, int32_t mode) {
   if (!h) return set_error(CVF_EINVAL, "handle is NULL");
   if (mode < -1 || mode > 1) return set_error(CVF_EINVAL, "mode %d: need -1, 0 or 1", mode);
-  const bool fits = !h->eta && resident3_fits(h->args, h->cmp64);
+  const bool fits = resident3_fits(h->args, h->cmp64);
   if (mode == 1 && !fits)
-    return set_error(CVF_EINVAL, "the resident form needs L a multiple of %d, %d <= L <= %d, "
-                     "and no eta moves", kRes3Ctas, 2 * kRes3Ctas, kRes3MaxSide);
+    return set_error(CVF_EINVAL, "the resident form needs L a multiple of %d, %d <= L <= %d",
+                     kRes3Ctas, 2 * kRes3Ctas, kRes3MaxSide);
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
   h->resident = (mode == 1) || (mode == -1 && fits && h->p.L <= kRes3AutoSide);
   return CVF_OK;

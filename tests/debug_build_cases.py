@@ -38,8 +38,8 @@ def square(L, steps, tiles=-1, **kw):
 
 
 def cubic(L, steps, resident=-1):
-    # eta moves where they apply (even side, launch form)
-    eta = 0 if (L % 2 or resident == 1) else 1
+    # eta moves where they apply (even side)
+    eta = 0 if L % 2 else 1
     op = oracle.physical_params3(300.0, 0.1, L=L, seed=L + 3, dv_max_frac=0.05, eta_moves=eta)
     ref = oracle.Oracle3(op)
     ref.run(steps)
@@ -96,6 +96,8 @@ def main():
     for t in (0, 1, 2):
         square(258, 5, tiles=t)                    # ragged tiles, periodic staging
     square(1024, 4, tiles=0)                       # TMA staging
+    for L, t in ((392, 4), (200, 5), (136, 6)):
+        square(L, 6, tiles=t)                      # the wavefront sweep, ragged tiles
     square(96, 7, rng_words=2)
     square(64, 8, schedule=oracle.SCHED_LAYERED)
     square(34, 8, schedule=oracle.SCHED_LAYERED)

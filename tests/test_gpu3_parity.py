@@ -196,11 +196,14 @@ def test_lattice3_large_cubes(L, steps):
     # gate flips: no bond or LJ bias, v fluctuating about the gate at v = 2
     (16, 200, dict(kT=1.0, P=0.5, J=0.0, v_HB=0.0, epsilon=0.0, v_iso_init=1.98, dv_max_frac=0.02)),
 ])
-def test_lattice3_resident_cluster(L, steps, extra):
+@pytest.mark.parametrize("eta_moves", [1, 0])
+def test_lattice3_resident_cluster(L, steps, extra, eta_moves):
     """The cube resident in one thread-block cluster for each call gives the
-    oracle's lattice, counts, N_q' and recorded series (and the same as the
-    four-launch form)."""
-    extra = dict(extra, eta_moves=0)   # the resident form runs the eta = 1 model
+    oracle's lattice, cube configurations, counts, N_q' and recorded series
+    -- with the eta step (the cubes whose lower plane lies in a CTA's slab
+    move there, their upper corners possibly in the next CTA's shared
+    memory) and without it (eta = 1)."""
+    extra = dict(extra, eta_moves=eta_moves)
     if "kT" in extra:
         op = oracle.params3(L=L, seed=500 + L, **extra)
     else:
@@ -217,10 +220,13 @@ def test_lattice3_resident_cluster(L, steps, extra):
         lat.sweep(steps // 3, 1)
         lat.sweep(steps - steps // 3, 1)   # two calls: the cube leaves and re-enters the cluster
         s, o = lat.state(), lat.observables()
+        eta = lat.eta() if eta_moves else None
         got, overflow = lat.drain()
         assert lat.recount() == (o["n_hb_raw"], o["n_coop"])
     assert not overflow and len(got) == len(want) == steps
     assert np.array_equal(s, ref.state())
+    if eta_moves:
+        assert np.array_equal(eta, ref.eta())
     _same(o, ref.observables(), L)
     for i, (g, w) in enumerate(zip(got, want)):
         _same(g, w, ("record", i))
@@ -228,13 +234,13 @@ def test_lattice3_resident_cluster(L, steps, extra):
 
 def test_lattice3_resident_choice():
     with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=16, eta_moves=0)))) as lat:
-        assert lat.resident()              # small cubes without eta run resident by default
+        assert lat.resident()              # small cubes run resident by default
         lat.set_resident(0)
         assert not lat.resident()
     with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=16)))) as lat:
-        assert not lat.resident()          # the eta step runs in the launch form
-        with pytest.raises(_capi.CvfError):
-            lat.set_resident(1)
+        assert lat.resident()              # with the eta step as well
+    with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=32)))) as lat:
+        assert not lat.resident()          # beyond 24^3 the launch form is faster
     with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=12)))) as lat:
         assert not lat.resident()          # 12 is not a multiple of 8
         with pytest.raises(_capi.CvfError):
