@@ -410,6 +410,62 @@ def test_full_size_sampled_windows(cfg):
     assert 0 < o_gpu["n_hb_raw"] <= 2 * L * L and 0 < o_gpu["n_coop"] <= 6 * L * L
 
 
+def test_configuration_2_through_the_wavefront():
+    """Configuration 2's lattice (1024 x 1024, random init seed 2, ambient,
+    recorded every 10 steps) takes the wavefront sweep by default: 1024 tiles
+    per step on every co-resident block, up to 16 steps in flight.  60 steps
+    in two calls give the oracle's whole lattice, counts and records."""
+    from paper_2505_05919_gb300 import workloads
+    c = workloads.c2()
+    K = 60
+    op = oracle.physical_params(c["T"], c["P"], L=c["L"], q=c["q"], seed=c["seed"])
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        assert lat.tiles()[0] == 6
+        lat.sweep(25, c["record_every"])
+        lat.sweep(K - 25, c["record_every"])
+        s_gpu, o_gpu = lat.state(), lat.observables()
+        r_gpu, overflow = lat.drain()
+    s_ref, o_ref, r_ref = oracle_run(op, K, record_every=c["record_every"])
+    assert not overflow and len(r_gpu) == len(r_ref) == K // c["record_every"]
+    assert np.array_equal(s_gpu, s_ref)
+    assert_obs_equal(o_gpu, o_ref)
+    for i, (a, b) in enumerate(zip(r_gpu, r_ref)):
+        assert_obs_equal(a, b, ("record", i))
+
+
+@pytest.mark.parametrize("L,config", [(2048, 5), (2560, 4)])
+def test_wavefront_sampled_windows(L, config):
+    """The largest lattices the wavefront sweep takes by default (2048^2 on
+    32 x 32-word tiles, 2560^2 on 64 x 64), 30 steps; windows recomputed by
+    the oracle with a frozen border 2K + 2 cells wide, four across the
+    periodic edges, as for the benchmark's lattices."""
+    K = 30
+    op = oracle.physical_params(300.0, 0.1, L=L, seed=77 + L)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        assert lat.tiles()[0] == config
+        lat.sweep(K)
+        s_gpu = lat.state()
+        o_gpu = lat.observables()
+        hb, co = lat.recount()
+    assert (hb, co) == (o_gpu["n_hb_raw"], o_gpu["n_coop"])
+    ref0 = oracle.Oracle(op)
+    done, V, g, acc = oracle.volume_chain(op, ref0.observables()["V_iso"], 0, K)
+    assert done == K
+    assert V[-1] == pytest.approx(o_gpu["V_iso"], rel=FP_REL)
+    assert o_gpu["acc_volume"] == acc
+    margin, inner = 2 * K + 2, 40
+    W = inner + 2 * margin
+    rng = np.random.default_rng(L)
+    spots = [(L - W // 2, L - W // 2), (L - W // 2, 0), (0, L - W // 2), (L - 20, L - W + 7)]
+    spots += [(int(rng.integers(0, L)), int(rng.integers(0, L))) for _ in range(4)]
+    full = ref0.state()
+    for x0, y0 in spots:
+        out = oracle.window_run(op, full, x0, y0, W, W, 0, g).reshape(L, L)
+        ys = [(y0 + margin + i) % L for i in range(inner)]
+        xs = [(x0 + margin + i) % L for i in range(inner)]
+        assert np.array_equal(s_gpu[np.ix_(ys, xs)], out[np.ix_(ys, xs)]), (L, x0, y0)
+
+
 def test_window_reads_match_the_whole_state():
     op = oracle.physical_params(300.0, 0.1, L=96, seed=12)
     with Lattice(params_from_dict(asdict(op))) as lat:
