@@ -32,6 +32,7 @@
 #include <cstring>
 
 #include "cvf_device.cuh"
+#include "cvf_fastdiv.cuh"
 #include "cvf_host.h"
 #include "cvf_lattice.cuh"
 #include "cvf_tile.cuh"
@@ -41,6 +42,27 @@ namespace cvf {
 namespace {
 
 constexpr int kWaveShape = kHalfRows | kUnroll1 | kSplitRec;  // the tiled sweep's loops
+
+// The tile grid of a launch, with the divisions it needs precomputed.
+struct WaveGeom {
+  int tiles_x, tiles_y, T;  // tiles per row, per column, per step
+  FastDiv div_T, div_x;     // item -> (step, tile); tile -> (row, column)
+  int small;                // the call's item count fits 32 bits
+};
+
+// Item i -> (relative step, tile).
+__device__ __forceinline__ void wave_item(const WaveGeom& G, unsigned long long i, int* r,
+                                          int* t) {
+  if (G.small) {
+    const uint32_t q = fdiv((uint32_t)i, G.div_T);
+    *r = (int)q;
+    *t = (int)((uint32_t)i - q * (uint32_t)G.T);
+  } else {
+    const long long q = (long long)(i / (unsigned long long)G.T);
+    *r = (int)q;
+    *t = (int)((long long)i - q * G.T);
+  }
+}
 constexpr int kWaveEngineBar = 5;                             // the engine's two warps
 
 __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
@@ -89,16 +111,17 @@ __device__ bool wave_wait_geq(const unsigned int* flag, unsigned int target, Wav
 // lane 10 the commit of step r - kWaveRing (its slots are free).  With
 // `block`, waits (bounded) until all hold; returns whether they hold (false
 // also on an abort).  The move's gate is returned in *g (lane 0).
-__device__ bool wave_deps(WaveHdr* H, const unsigned int* prog, int r, int t, int tiles_x,
-                          int tiles_y, bool block, unsigned int* err, int* g) {
+__device__ bool wave_deps(WaveHdr* H, const unsigned int* prog, int r, int t, const WaveGeom& G,
+                          bool block, unsigned int* err, int* g) {
   const int lane = (int)(threadIdx.x & 31u);
   const unsigned int* flag = nullptr;
   unsigned int target = 0;
   if (lane < 9) {
-    const int ty = t / tiles_x, tx = t - ty * tiles_x;
-    const int ny = (ty + lane / 3 - 1 + tiles_y) % tiles_y;
-    const int nx = (tx + lane % 3 - 1 + tiles_x) % tiles_x;
-    flag = &prog[ny * tiles_x + nx];
+    const int ty = (int)fdiv((uint32_t)t, G.div_x), tx = t - ty * G.tiles_x;
+    int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;  // periodic neighbours
+    ny = (ny < 0) ? ny + G.tiles_y : (ny >= G.tiles_y ? ny - G.tiles_y : ny);
+    nx = (nx < 0) ? nx + G.tiles_x : (nx >= G.tiles_x ? nx - G.tiles_x : nx);
+    flag = &prog[ny * G.tiles_x + nx];
     target = (unsigned int)r;
   } else if (lane == 9) {
     flag = &H->vring[r % kWaveRing].tag;
@@ -190,7 +213,7 @@ __device__ void wave_commit(const LatticeArgs& A, WaveHdr* H, long long step0, l
 template <int RNG_WORDS, bool CMP64, int TR, int TW>
 __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     k_sweep_wave(const __grid_constant__ LatticeArgs A, WaveHdr* H, long long step0,
-                 long long n_steps) {
+                 long long n_steps, const __grid_constant__ WaveGeom G) {
   __shared__ union {
     TileSmem<TR, TW> tile;
     VolumeArgs vol;  // the engine block's copy of the parameters
@@ -264,8 +287,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
   TileSmem<TR, TW>& S = U.tile;
   const int L = A.L, Lh = L >> 1;
   const long long N = (long long)L * L;
-  const int tiles_x = (Lh + TW - 1) / TW, tiles_y = (L + TR - 1) / TR;
-  const int T = tiles_x * tiles_y;
+  const int T = G.T;
   const long long total = n_steps * (long long)T;
   unsigned int* const prog = reinterpret_cast<unsigned int*>(H + 1);
   const int every = ctl->record_every;
@@ -273,6 +295,8 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
   fill_prop2(Tb, A.q);
   if (threadIdx.x < 4) s_hist4[threadIdx.x] = 0;
   int g_cur = -1;
+  TileCounts cnt{0, 0, 0};  // this thread's counts of the tiles not yet reported
+  int pend = 0;             // the block's tiles not yet reported (all of one step)
 
   // take an item and, blocking, wait for it (warp 0)
   if (threadIdx.x < 32) {
@@ -280,10 +304,9 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     if (threadIdx.x == 0) i = atomicAdd(&H->next, 1ull);
     i = __shfl_sync(0xFFFFFFFFu, i, 0);
     const bool have = (long long)i < total;
-    int g = 0;
-    const int r = have ? (int)((long long)i / T) : 0;
-    const int t = have ? (int)((long long)i - (long long)r * T) : 0;
-    const bool ok = have && wave_deps(H, prog, r, t, tiles_x, tiles_y, true, err, &g);
+    int g = 0, r = 0, t = 0;
+    if (have) wave_item(G, i, &r, &t);
+    const bool ok = have && wave_deps(H, prog, r, t, G, true, err, &g);
     if (threadIdx.x == 0) {
       s_ok = ok ? 1 : 0;
       s_r = r;
@@ -311,7 +334,8 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     v.s_hi = (uint32_t)((unsigned long long)step >> 32);
     v.keys.K = &A.keys;
     v.err = err;
-    const TileGeom gm = tile_geom<TR, TW>(L, Lh, (t / tiles_x) * TR, (t % tiles_x) * TW);
+    const int ty = (int)fdiv((uint32_t)t, G.div_x);
+    const TileGeom gm = tile_geom<TR, TW>(L, Lh, ty * TR, (t - ty * G.tiles_x) * TW);
     if (!staged) {
       // the words were written by other SMs during this launch: through L2
       if (async16)
@@ -322,7 +346,6 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     cp_async_wait_all();
     __syncthreads();
     const bool rec = step_recorded(every, step);
-    TileCounts cnt{0, 0, 0};
     colour0<RNG_WORDS, CMP64, TR, TW, kThreads, kWaveShape>(v, gm, S, Tb, cnt,
                                                              rec ? s_hist4 : nullptr);
     // S.in is free: the last warp (the least colour-0 work) takes the next
@@ -333,10 +356,9 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       if ((threadIdx.x & 31u) == 0) i = atomicAdd(&H->next, 1ull);
       i = __shfl_sync(0xFFFFFFFFu, i, 0);
       const bool have = (long long)i < total;
-      int g2 = 0;
-      const int r2 = have ? (int)((long long)i / T) : 0;
-      const int t2 = have ? (int)((long long)i - (long long)r2 * T) : 0;
-      const bool ready = have && wave_deps(H, prog, r2, t2, tiles_x, tiles_y, false, err, &g2);
+      int g2 = 0, r2 = 0, t2 = 0;
+      if (have) wave_item(G, i, &r2, &t2);
+      const bool ready = have && wave_deps(H, prog, r2, t2, G, false, err, &g2);
       if ((threadIdx.x & 31u) == 0) {
         n_ok = have ? 1 : 0;
         n_r = r2;
@@ -352,7 +374,8 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       vn.L = L;
       vn.Lh = Lh;
       vn.err = err;
-      const TileGeom gn = tile_geom<TR, TW>(L, Lh, (n_t / tiles_x) * TR, (n_t % tiles_x) * TW);
+      const int nty = (int)fdiv((uint32_t)n_t, G.div_x);
+      const TileGeom gn = tile_geom<TR, TW>(L, Lh, nty * TR, (n_t - nty * G.tiles_x) * TW);
       stage_async16<TR, TW, kThreads>(vn, gn, S);
     }
     colour1<RNG_WORDS, CMP64, TR, TW, kThreads, kWaveShape>(v, gm, S, Tb, cnt,
@@ -362,24 +385,38 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       __syncthreads();
       hist_flush(s_hist4, slot->hist);
     }
-    uint32_t dhb = (uint32_t)cnt.dhb(), dc = (uint32_t)cnt.dc(), nacc = cnt.nacc;
-    block_sum3<kThreads>(dhb, dc, nacc);  // ends with a barrier: the tile's stores are done
+    __syncthreads();  // the tile's stores (and N_q' adds) are done
     if (threadIdx.x == 0) {
-      // one fence releases the tile's words (ordered by the block's barrier)
-      // and its counts before both the progress word, which the tiles of the
-      // next step around it acquire, and the step's completion count
-      atomicAdd(&slot->hb, (unsigned long long)(long long)(int)dhb);
-      atomicAdd(&slot->pairs, (unsigned long long)(long long)(int)dc);
-      atomicAdd(&slot->moves, (unsigned long long)nacc);
+      // the tile's words to the tiles of the next step around it: a fence
+      // (releasing what the block's barrier ordered) and a relaxed store
       fence_acq_rel_gpu();
       st_relaxed_u32(&prog[t], (unsigned int)(r + 1));
-      // the last tile of the step commits it, after the step before (the
-      // fence acquires every other tile's counts, released the same way)
-      if (atom_add_relaxed_u32(&slot->done, 1u) == (unsigned int)(T - 1)) {
+    }
+    ++pend;
+    // The counts of consecutive tiles of one step stay in the threads'
+    // registers and are reported together when the block's next item is of
+    // another step, is not ready (the block is about to wait: nothing it
+    // holds may be what others wait for) or does not exist.
+    if (!n_ok || !n_ready || n_r != r) {  // block-uniform
+      uint32_t dhb = (uint32_t)cnt.dhb(), dc = (uint32_t)cnt.dc(), nacc = cnt.nacc;
+      block_sum3<kThreads>(dhb, dc, nacc);
+      if (threadIdx.x == 0) {
+        atomicAdd(&slot->hb, (unsigned long long)(long long)(int)dhb);
+        atomicAdd(&slot->pairs, (unsigned long long)(long long)(int)dc);
+        atomicAdd(&slot->moves, (unsigned long long)nacc);
+        // the counts before the completion count; the tile that completes
+        // the step commits it after the step before (its fence acquires
+        // every other tile's counts, released the same way)
         fence_acq_rel_gpu();
-        if (r == 0 || wave_wait_geq(&H->committed, (unsigned int)r, H, err))
-          wave_commit(A, H, step0, r);
+        if (atom_add_relaxed_u32(&slot->done, (unsigned int)pend) + (unsigned int)pend ==
+            (unsigned int)T) {
+          fence_acq_rel_gpu();
+          if (r == 0 || wave_wait_geq(&H->committed, (unsigned int)r, H, err))
+            wave_commit(A, H, step0, r);
+        }
       }
+      cnt = TileCounts{0, 0, 0};
+      pend = 0;
     }
     // the next item becomes the current one; if it could not be staged yet,
     // warp 0 waits for it
@@ -387,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       const bool have = n_ok != 0;
       bool ok = have;
       int g2 = n_g;
-      if (have && !n_ready) ok = wave_deps(H, prog, n_r, n_t, tiles_x, tiles_y, true, err, &g2);
+      if (have && !n_ready) ok = wave_deps(H, prog, n_r, n_t, G, true, err, &g2);
       if (threadIdx.x == 0) {
         s_ok = ok ? 1 : 0;
         s_r = n_r;
@@ -432,9 +469,17 @@ cudaError_t launch_wave(const LatticeArgs& A, WaveHdr* H, size_t scratch_bytes, 
                         cudaStream_t s) {
   const int grid = wave_blocks(rng_words, cmp64, shape);
   if (grid < 2) return cudaErrorCooperativeLaunchTooLarge;
+  const int tr = (shape == 0) ? 64 : (shape == 1) ? 32 : 16, tw = (shape == 0) ? 64 : 32;
+  WaveGeom G;
+  G.tiles_x = (A.L / 2 + tw - 1) / tw;
+  G.tiles_y = (A.L + tr - 1) / tr;
+  G.T = G.tiles_x * G.tiles_y;
+  G.div_T = make_fastdiv((uint32_t)G.T);
+  G.div_x = make_fastdiv((uint32_t)G.tiles_x);
+  G.small = (n_steps * (long long)G.T < (1ll << 31)) ? 1 : 0;
   cudaError_t e = cudaMemsetAsync(H, 0, scratch_bytes, s);
   if (e != cudaSuccess) return e;
-  void* args[4] = {const_cast<LatticeArgs*>(&A), &H, &step0, &n_steps};
+  void* args[5] = {const_cast<LatticeArgs*>(&A), &H, &step0, &n_steps, &G};
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3(grid);
