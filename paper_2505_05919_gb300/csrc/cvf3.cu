@@ -555,7 +555,8 @@ __device__ __forceinline__ int edge_lo(int e) {
   return (d == 0) ? 2 * k : (d == 1) ? ((k & 1) | ((k >> 1) << 2)) : k;
 }
 
-// The eight corner cells of a cube.
+// The eight corner cells of a cube: the corner of smallest coordinates and
+// the steps +x, +y, +z from it (periodic).
 __device__ __forceinline__ void cube_corners(const Args3& A, uint32_t cube, uint32_t cell[8]) {
   const uint32_t H = A.H, H2 = H * H;
   const uint32_t colour = (cube >= H2 * H) ? 1u : 0u;
@@ -564,13 +565,70 @@ __device__ __forceinline__ void cube_corners(const Args3& A, uint32_t cube, uint
   const uint32_t X = rest - Zc * H;
   const uint32_t Z = fdiv(Zc, A.div_H);
   const uint32_t Y = Zc - Z * H;
-  const uint32_t L = A.L;
+  const uint32_t L = A.L, L2 = A.L2;
   const uint32_t x0 = 2u * X + colour, y0 = 2u * Y + colour, z0 = 2u * Z + colour;
-  const uint32_t x1 = (x0 + 1u == L) ? 0u : x0 + 1u, y1 = (y0 + 1u == L) ? 0u : y0 + 1u,
-                 z1 = (z0 + 1u == L) ? 0u : z0 + 1u;
+  const uint32_t base = z0 * L2 + y0 * L + x0;
+  const uint32_t dx = (x0 + 1u == L) ? 1u - L : 1u;
+  const uint32_t dy = (y0 + 1u == L) ? L - L2 : L;
+  const uint32_t dz = (z0 + 1u == L) ? L2 - A.N : L2;  // unsigned wrap-around
+  cell[0] = base;
+  cell[1] = base + dx;
+  cell[2] = base + dy;
+  cell[3] = cell[1] + dy;
+  cell[4] = base + dz;
+  cell[5] = cell[1] + dz;
+  cell[6] = cell[2] + dz;
+  cell[7] = cell[3] + dz;
+}
+
+// The bonded edges of a cube (sigma only; eta is not read) in the packed
+// layout of the edge masks: edge e = 4 d + k (axis d, k-th lower corner)
+// at bit 8 k + 7 - d.  For axis d, byte d of a corner word holds its +d arm
+// (low nibble) and -d arm (high nibble); the bytes of the four lower and of
+// the four upper corners are gathered into one word each, and one nibble
+// comparison per byte tests the four edges at once.
+__device__ __forceinline__ uint32_t cube_bonds_packed(const uint32_t w[8]) {
+  uint32_t bonds = 0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j)
-    cell[j] = ((j & 4) ? z1 : z0) * A.L2 + ((j & 2) ? y1 : y0) * L + ((j & 1) ? x1 : x0);
+  for (int d = 0; d < 3; ++d) {
+    // corners with bit d clear, in increasing order, and their +d partners
+    const int l0 = (d == 0) ? 0 : 0, l1 = (d == 0) ? 2 : 1, l2 = (d == 0) ? 4 : (d == 1) ? 4 : 2,
+              l3 = (d == 0) ? 6 : (d == 1) ? 5 : 3;
+    const int u = 1 << d;
+    const uint32_t sel = (uint32_t)d | ((uint32_t)(4 + d) << 4);
+    const uint32_t lo = __byte_perm(__byte_perm(w[l0], w[l1], sel), __byte_perm(w[l2], w[l3], sel),
+                                    0x5410u);
+    const uint32_t hi = __byte_perm(__byte_perm(w[l0 | u], w[l1 | u], sel),
+                                    __byte_perm(w[l2 | u], w[l3 | u], sel), 0x5410u);
+    // byte k: the +d arm of lower corner k against the -d arm of its partner
+    const uint32_t m = (lo ^ (hi >> 4)) & 0x07070707u;
+    const uint32_t differ = (m | 0x80808080u) - 0x01010101u;  // bit 7 set where m != 0
+    bonds |= (~differ & 0x80808080u) >> d;
+  }
+  return bonds;
+}
+
+// An edge mask (bit e = edge e) in the packed layout of cube_bonds_packed.
+__device__ __forceinline__ uint32_t pack_edge_mask(uint32_t m12) {
+  uint32_t p = 0;
+#pragma unroll
+  for (int e = 0; e < 12; ++e) p |= ((m12 >> e) & 1u) << (8 * (e & 3) + 7 - (e >> 2));
+  return p;
+}
+
+// The eta-copy flips of the corner words for the edges set in a packed flip
+// mask: the +d arm (bit 8 d + 3) of the lower corner and the -d arm (bit
+// 8 d + 7) of the upper corner of each edge.
+__device__ __forceinline__ void cube_flip_bits(uint32_t flip, uint32_t x[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = 0u;
+#pragma unroll
+  for (int e = 0; e < 12; ++e) {
+    const int d = e >> 2, lo = edge_lo(e), hi = lo | (1 << d);
+    const uint32_t f = (flip >> (8 * (e & 3) + 7 - d)) & 1u;
+    x[lo] ^= f << (8 * d + 3);
+    x[hi] ^= f << (8 * d + 7);
+  }
 }
 
 // Step 2 of the MC step: one Metropolis move of every cube's configuration
@@ -591,7 +649,7 @@ __global__ void __launch_bounds__(kThreads3) k_eta3(Args3 A) {
   const long long step = ctl->sweep;
   if (threadIdx.x < 9) {
     sT[threadIdx.x] = A.eta_table[g * 9 + threadIdx.x];
-    sMask[threadIdx.x] = A.masks[threadIdx.x];
+    sMask[threadIdx.x] = pack_edge_mask(A.masks[threadIdx.x]);
   }
   __syncthreads();
   const uint32_t s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
@@ -604,12 +662,7 @@ __global__ void __launch_bounds__(kThreads3) k_eta3(Args3 A) {
 #pragma unroll
     for (int j = 0; j < 8; ++j)
       w[j] = dcheck(cell[j] < A.N, &ctl->error, kSiteEta3) ? A.state[cell[j]] : 0u;
-    uint32_t bonds = 0;
-#pragma unroll
-    for (int e = 0; e < 12; ++e) {
-      const int d = e >> 2, lo = edge_lo(e), hi = lo | (1 << d);
-      bonds |= (uint32_t)(((w[lo] >> (8 * d)) & 7u) == ((w[hi] >> (8 * d + 4)) & 7u)) << e;
-    }
+    const uint32_t bonds = cube_bonds_packed(w);
     const uint32_t old = A.eta[cube];
     const Words4 r = philox(cube, s_lo, s_hi, kTagEta, A.keys);
     uint32_t nw = old + 1u + __umulhi(r.x, 8u);
@@ -620,15 +673,8 @@ __global__ void __launch_bounds__(kThreads3) k_eta3(Args3 A) {
     if ((unsigned long long)r.y < sT[dhb + 4]) {
       A.eta[cube] = (uint8_t)nw;
       dsum += dhb;
-      const uint32_t flip = zo ^ zn;
-      uint32_t x[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-#pragma unroll
-      for (int e = 0; e < 12; ++e) {
-        const int d = e >> 2, lo = edge_lo(e), hi = lo | (1 << d);
-        const uint32_t f = (flip >> e) & 1u;
-        x[lo] ^= f << (8 * d + 3);   // the +d arm of the low corner
-        x[hi] ^= f << (8 * d + 7);   // the -d arm of the high corner
-      }
+      uint32_t x[8];
+      cube_flip_bits(zo ^ zn, x);
 #pragma unroll
       for (int j = 0; j < 8; ++j)
         if (x[j]) atomicXor(&A.state[cell[j]], x[j]);
@@ -776,7 +822,7 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
   }
   stage_volume_args(&sV, A.vol);
   if (eta_on && threadIdx.x < 18) sEtaT[threadIdx.x] = A.eta_table[threadIdx.x];
-  if (eta_on && threadIdx.x < 9) sEtaMask[threadIdx.x] = A.masks[threadIdx.x];
+  if (eta_on && threadIdx.x < 9) sEtaMask[threadIdx.x] = pack_edge_mask(A.masks[threadIdx.x]);
   if (rank == 0 && threadIdx.x == 0) s_next_g = ctl->next_g;
   // the planes just below and above this slab, in the neighbours' shared memory
   const uint32_t* below = cluster.map_shared_rank(cube, (rank + kRes3Ctas - 1) % kRes3Ctas) + (R - 1) * L2;
@@ -871,12 +917,7 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
           wp[j] = ((j & 4) ? phi : plo) + ((j & 2) ? y1 : y0) * L + ((j & 1) ? x1 : x0);
           w[j] = dcheck(zl < R && cb < A.ncube, &gctl->error, kSiteResident3) ? *wp[j] : 0u;
         }
-        uint32_t bonds = 0;
-#pragma unroll
-        for (int e = 0; e < 12; ++e) {
-          const int d = e >> 2, lo = edge_lo(e), hi = lo | (1 << d);
-          bonds |= (uint32_t)(((w[lo] >> (8 * d)) & 7u) == ((w[hi] >> (8 * d + 4)) & 7u)) << e;
-        }
+        const uint32_t bonds = cube_bonds_packed(w);
         const uint32_t old = A.eta[cb];
         if (!dcheck(old < 9u, &gctl->error, kSiteResident3)) continue;
         const Words4 r = philox(cb, s_lo, s_hi, kTagEta, A.keys);
@@ -887,15 +928,8 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
         if ((unsigned long long)r.y < sEtaT[g * 9 + dhb + 4]) {
           A.eta[cb] = (uint8_t)nw;
           eta_dhb += dhb;
-          const uint32_t flip = zo ^ zn;
-          uint32_t x[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-#pragma unroll
-          for (int e = 0; e < 12; ++e) {
-            const int d = e >> 2, lo = edge_lo(e), hi = lo | (1 << d);
-            const uint32_t f = (flip >> e) & 1u;
-            x[lo] ^= f << (8 * d + 3);
-            x[hi] ^= f << (8 * d + 7);
-          }
+          uint32_t x[8];
+          cube_flip_bits(zo ^ zn, x);
 #pragma unroll
           for (int j = 0; j < 8; ++j)
             if (x[j]) atomicXor(wp[j], x[j]);
