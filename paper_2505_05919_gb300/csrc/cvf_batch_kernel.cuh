@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "cvf.h"
 #include "cvf_device.cuh"
@@ -22,6 +23,20 @@
 #include "cvf_tile.cuh"
 
 namespace cvf {
+
+// The current replica's round keys held in registers for a whole item (the
+// 512-thread kernels have 64 registers a thread); the other kernels read
+// them from shared memory by broadcast loads (KeysRound).
+struct KeysInRegs {
+  RoundKeys K;
+};
+
+template <int RNG_WORDS>
+__device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi,
+                                      const KeysInRegs& k, uint32_t q, uint32_t acc[4],
+                                      uint32_t kk[4]) {
+  cell_draws<RNG_WORDS>(c, s_lo, s_hi, k.K, q, acc, kk);
+}
 
 struct ReplicaDesc {
   uint16_t* state;  // state pair, 2 * L * L words
@@ -241,7 +256,8 @@ __global__ void __launch_bounds__(NT, batch_min_blocks(NT))
     }
     const int L = R.L, Lh = L >> 1;
     const long long N = (long long)L * L;
-    StepView<KeysRound> v;
+    using Keys = std::conditional_t<(NT >= 512), KeysInRegs, KeysRound>;
+    StepView<Keys> v;
     v.src = reinterpret_cast<const uint32_t*>(R.state + (size_t)(step & 1) * N);
     v.dst = reinterpret_cast<uint32_t*>(R.state + (size_t)((step + 1) & 1) * N);
     v.L = L;
@@ -249,7 +265,7 @@ __global__ void __launch_bounds__(NT, batch_min_blocks(NT))
     v.q = R.q;
     v.s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
     v.s_hi = (uint32_t)((unsigned long long)step >> 32);
-    v.keys.K = &s_keys;
+    if constexpr (NT < 512) v.keys.K = &s_keys;
     v.err = &W->error;
     const TileGeom gm = tile_geom<TR, TW>(L, Lh, (t / tiles_x) * TR, (t % tiles_x) * TW);
     if (staged)
@@ -270,6 +286,7 @@ __global__ void __launch_bounds__(NT, batch_min_blocks(NT))
       s_step_rep = rep;
       s_step0 = step - rel;
     }
+    if constexpr (NT >= 512) v.keys.K = s_keys;  // after the barrier above
     TileCounts cnt{0, 0, 0};
     const bool rec = step_recorded(vc->record_every, step);
     colour0<RNG_WORDS, CMP64, TR, TW, NT, kBatchShape>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
