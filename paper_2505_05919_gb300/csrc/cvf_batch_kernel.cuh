@@ -24,20 +24,6 @@
 
 namespace cvf {
 
-// The current replica's round keys held in registers for a whole item (the
-// 512-thread kernels have 64 registers a thread); the other kernels read
-// them from shared memory by broadcast loads (KeysRound).
-struct KeysInRegs {
-  RoundKeys K;
-};
-
-template <int RNG_WORDS>
-__device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi,
-                                      const KeysInRegs& k, uint32_t q, uint32_t acc[4],
-                                      uint32_t kk[4]) {
-  cell_draws<RNG_WORDS>(c, s_lo, s_hi, k.K, q, acc, kk);
-}
-
 struct ReplicaDesc {
   uint16_t* state;  // state pair, 2 * L * L words
   Ctrl* ctrl;

@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kResBlock) k_resident2(LatticeArgs A, long lon
         const uint32_t yp = (r == R - 1) ? down[p] : lat[i + Lh];
         lat[i] = update_in_word<RNG_WORDS, CMP64>(own, xm, xp, ym, yp, hi,
                                                   (uint32_t)(y * L + 2 * p + hi), s_lo, s_hi,
-                                                  KeysRound{&K}, A.q, Tb, pk,
+                                                  KeysInRegs{A.keys}, A.q, Tb, pk,
                                                   rec ? s_hist4 : nullptr);
       }
       cnt.add(pk);

@@ -19,11 +19,10 @@ namespace cvf {
 
 // Shared tables of one (lattice, step): the proposal for the current q and
 // the threshold rows of the current gate.
-//   prop[8 k + sigma] = ((sigma + 1 + k) mod q) * 0x11111111 for k < 7
-//                       (sigma' in every nibble; k <= q - 2 <= 6), and
-//   prop[56 + sigma]  = sigma * 0x11111111 (row k = 7, which no proposal
-//                       offset reaches), so that both words an update needs
-//                       sit at byte offsets 32 k + 4 sigma and 224 + 4 sigma
+//   prop[8 k + sigma] = {sigma * 0x11111111, ((sigma + 1 + k) mod q) *
+//                       0x11111111} for k < 7 (sigma and sigma' in every
+//                       nibble; k <= q - 2 <= 6): both words an update needs
+//                       in one 8-byte load at byte offset 64 k + 8 sigma
 //   rows[9 ps + pp]   = {T - 1, packed count change} for the nibble counts ps,
 //                       pp of update_arm2 (entries no move can reach are 0);
 //                       an accepted move adds the change (1 << 20) +
@@ -32,7 +31,7 @@ namespace cvf {
 constexpr int kRows2 = 72;
 struct Tables2 {
   uint2 rows[kRows2];
-  uint32_t prop[64];
+  uint2 prop[64];
   unsigned long long T64[kRows2];
 };
 
@@ -41,16 +40,12 @@ __device__ __forceinline__ void fill_prop2(Tables2& Tb, uint32_t q) {
   for (int e = threadIdx.x; e < 64; e += blockDim.x) {
     const uint32_t k = (uint32_t)e >> 3, s = (uint32_t)e & 7u;
     uint32_t v = 0u;
-    if (s < q) {
-      if (k == 7u) {
-        v = s * 0x11111111u;
-      } else if (k + 1u < q) {
-        uint32_t sp = s + 1u + k;
-        while (sp >= q) sp -= q;
-        v = sp * 0x11111111u;
-      }
+    if (s < q && k + 1u < q) {
+      uint32_t sp = s + 1u + k;
+      while (sp >= q) sp -= q;
+      v = sp * 0x11111111u;
     }
-    Tb.prop[e] = v;
+    Tb.prop[e] = make_uint2(s * 0x11111111u, v);
   }
 }
 
@@ -76,12 +71,6 @@ __device__ __forceinline__ void fill_rows2(Tables2& Tb, const unsigned long long
   }
 }
 
-// The 32-bit word at byte offset `off` of a shared table (the offsets below
-// are computed already scaled, so no index arithmetic is added).
-__device__ __forceinline__ uint32_t table_word(const uint32_t* base, uint32_t off) {
-  return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(base) + off);
-}
-
 constexpr uint32_t kNib1 = 0x11111111u;   // 1 in every nibble
 constexpr uint32_t kGuard = 0x88888888u;  // bit 3 of every nibble
 
@@ -104,16 +93,18 @@ template <bool CMP64, int ARM = -1>
 __device__ __forceinline__ uint32_t update_arm2(uint32_t w, uint32_t x, uint32_t u, uint32_t k,
                                                 uint32_t a_rt, const Tables2& Tb, uint32_t& pk) {
   const uint32_t a = (ARM >= 0) ? (uint32_t)ARM : a_rt;
-  // 4 sigma: the byte offset of sigma's column in the proposal table
-  uint32_t s4;
+  // 8 sigma: the byte offset of sigma's entry in a proposal table row
+  uint32_t s8;
   if constexpr (ARM == 0)
-    s4 = (w << 2) & 0x1Cu;
+    s8 = (w << 3) & 0x38u;
   else if constexpr (ARM > 0)
-    s4 = (w >> (4 * ARM - 2)) & 0x1Cu;
+    s8 = (w >> (4 * ARM - 3)) & 0x38u;
   else
-    s4 = ((w >> (4u * a)) & 7u) << 2;
-  const uint32_t spR = table_word(Tb.prop, (k << 5) + s4);  // sigma' in every nibble
-  const uint32_t sR = table_word(Tb.prop, 224u + s4);       // sigma in every nibble
+    s8 = ((w >> (4u * a)) & 7u) << 3;
+  const uint2 pr = *reinterpret_cast<const uint2*>(reinterpret_cast<const char*>(Tb.prop) +
+                                                   (k << 6) + s8);
+  const uint32_t sR = pr.x;   // sigma in every nibble
+  const uint32_t spR = pr.y;  // sigma' in every nibble
   const uint32_t fs = ((w ^ sR ^ x) - kNib1) & kGuard;
   const uint32_t fp = ((w ^ spR ^ x) - kNib1) & kGuard;
   const uint32_t idx = (uint32_t)__popc(fs) * 9u + (uint32_t)__popc(fp);
@@ -147,6 +138,21 @@ template <int RNG_WORDS>
 __device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi, const KeysRound& k,
                                       uint32_t q, uint32_t acc[4], uint32_t kk[4]) {
   cell_draws<RNG_WORDS>(c, s_lo, s_hi, *k.K, q, acc, kk);
+}
+
+// The round keys held by value: a copy of a kernel parameter's keys (the
+// single-lattice sweep; the compiler takes them from the parameter bank as
+// instruction operands) or of the current replica's (the batched 512-thread
+// kernels, which keep them in registers for an item).
+struct KeysInRegs {
+  RoundKeys K;
+};
+
+template <int RNG_WORDS>
+__device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi,
+                                      const KeysInRegs& k, uint32_t q, uint32_t acc[4],
+                                      uint32_t kk[4]) {
+  cell_draws<RNG_WORDS>(c, s_lo, s_hi, k.K, q, acc, kk);
 }
 
 // Update the cell in half `hi` of word `own` (its four arms in order, each

@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       fill_rows2(Tb, A.table24, g);
       g_cur = g;
     }
-    StepView<KeysRound> v;
+    StepView<KeysInRegs> v;
     v.src = reinterpret_cast<const uint32_t*>(A.state + (size_t)(step & 1) * N);
     v.dst = reinterpret_cast<uint32_t*>(A.state + (size_t)((step + 1) & 1) * N);
     v.L = L;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     v.q = A.q;
     v.s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
     v.s_hi = (uint32_t)((unsigned long long)step >> 32);
-    v.keys.K = &A.keys;
+    v.keys.K = A.keys;
     v.err = err;
     const int ty = (int)fdiv((uint32_t)t, G.div_x);
     const TileGeom gm = tile_geom<TR, TW>(L, Lh, ty * TR, (t - ty * G.tiles_x) * TW);
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     }
     __syncthreads();
     if (n_ready) {
-      StepView<KeysRound> vn;
+      StepView<KeysInRegs> vn;
       vn.src = reinterpret_cast<const uint32_t*>(A.state + (size_t)((step0 + n_r) & 1) * N);
       vn.L = L;
       vn.Lh = Lh;
