@@ -287,6 +287,14 @@ def cpu_baseline_all_cores(cfg, L=1024, steps=20):
                       "init (seeds %d..%d), %g K" % (n, L, steps, cfg["seed"], cfg["seed"] + n - 1, cfg["T"])}
 
 
+def arm_config(L, S):
+    """The `config` of the benchmark line (both arms)."""
+    return {"workload": "CVF 2D L=%d q=6, %d MC steps/step, random(seed 3)+ordered init at "
+                        "270/300/330 K, 0.1 MPa" % (L, S),
+            "L": L, "sweeps_per_step": S, "l2": "flushed between timed steps (512 MB write)",
+            "rng_words": 1, "schedule": "checkerboard"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -305,13 +313,14 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     upd = 4.0 * args.L * args.L * per_step * args.steps
     value = upd / (dt * 1e9)
-    sample = ("each step: %d MC step(s) of the L=%d lattice (random init seed %d, %g K, %g MPa) "
-              "by the single-threaded oracle" % (per_step, args.L, cfg["seed"], cfg["T"], cfg["P"]))
+    sample = ("each step: %d MC step(s) of the L=%d lattice (random init seed %d, %g K, %g MPa; "
+              "one of the configuration's six, a bounded sample of its 1000-step step) by the "
+              "single-threaded oracle" % (per_step, args.L, cfg["seed"], cfg["T"], cfg["P"]))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u16+int64+f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "L=%d q=6 CVF 2D checkerboard Metropolis, oracle sample" % args.L},
+            "config": arm_config(args.L, args.sweeps),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -890,10 +899,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u16+int64+f64", "data": "synthetic",
-            "config": {"workload": "CVF 2D L=%d q=6, %d MC steps/step, random(seed 3)+ordered init at "
-                                   "270/300/330 K, 0.1 MPa" % (L, S),
-                       "L": L, "sweeps_per_step": S, "l2": "flushed between timed steps (512 MB write)",
-                       "rng_words": 1, "schedule": "checkerboard"},
+            "config": arm_config(L, S),
             "roofline": roofline,
             "roofline_hbm": roofline_hbm,
             "roofline_l2": roofline_l2,
