@@ -410,6 +410,57 @@ def test_full_size_sampled_windows(cfg):
     assert 0 < o_gpu["n_hb_raw"] <= 2 * L * L and 0 < o_gpu["n_coop"] <= 6 * L * L
 
 
+@pytest.mark.parametrize("L,K,every,extra", [
+    (136, 2000, 40, {}),
+    (200, 1200, 25, dict(rng_words=2, init=oracle.INIT_ORDERED)),
+    (136, 1500, 1, dict(kT=2.4, P=1.2, epsilon=0.0, J=1e-4, J_sigma=0.0, v_HB=0.0,
+                        v_iso_init=2.0, dv_max_frac=0.01)),
+])
+def test_wavefront_long_runs(L, K, every, extra):
+    """Long wavefront calls on small tile grids (16 x 32 words: every block
+    takes items up to sixteen steps ahead, and the steps' slots and volume
+    moves are reused about a hundred times), against the oracle's lattice
+    and records -- including a run whose gate changes hundreds of times."""
+    extra = dict(extra)
+    if "kT" in extra:
+        op = oracle.OracleParams(L=L, seed=900 + L, **extra)
+    else:
+        op = oracle.physical_params(300.0, 0.1, L=L, seed=900 + L, dv_max_frac=0.02, **extra)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        lat.set_tiles(6)
+        lat.sweep(K, every)
+        s_gpu, o_gpu = lat.state(), lat.observables()
+        r_gpu, overflow = lat.drain()
+    s_ref, o_ref, r_ref = oracle_run(op, K, record_every=every)
+    assert not overflow and len(r_gpu) == len(r_ref) == K // every
+    assert np.array_equal(s_gpu, s_ref)
+    assert_obs_equal(o_gpu, o_ref)
+    for i, (a, b) in enumerate(zip(r_gpu, r_ref)):
+        assert_obs_equal(a, b, ("record", i))
+
+
+def test_resident_volume_engine_long_run():
+    """The resident form's volume moves decided ahead in five-step passes,
+    over 3000 steps of a lattice whose gate changes hundreds of times (each
+    change stops a pass; the commit decides it and the engine restarts),
+    recorded every step against the oracle."""
+    op = oracle.OracleParams(L=16, seed=61, kT=2.4, P=1.2, epsilon=0.0, J=1e-4, J_sigma=0.0,
+                             v_HB=0.0, v_iso_init=2.0, dv_max_frac=0.05)
+    K = 3000
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        assert lat.tiles()[0] == 3
+        lat.sweep(K, 1)
+        s_gpu, o_gpu = lat.state(), lat.observables()
+        r_gpu, overflow = lat.drain()
+    s_ref, o_ref, r_ref = oracle_run(op, K, record_every=1)
+    assert not overflow and len(r_gpu) == K
+    gs = [r["g"] for r in r_ref]
+    assert sum(1 for a, b in zip(gs, gs[1:]) if a != b) >= 100
+    assert np.array_equal(s_gpu, s_ref)
+    for i, (a, b) in enumerate(zip(r_gpu, r_ref)):
+        assert_obs_equal(a, b, ("record", i))
+
+
 def test_configuration_2_through_the_wavefront():
     """Configuration 2's lattice (1024 x 1024, random init seed 2, ambient,
     recorded every 10 steps) takes the wavefront sweep by default: 1024 tiles
