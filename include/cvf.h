@@ -463,13 +463,15 @@ int cvf3_recount(cvf3_handle *h, int64_t *n_hb_raw, int64_t *n_sigma);
 int cvf3_state_device_ptr(cvf3_handle *h, void **dev_ptr);
 
 /* Form of the sweep: mode 1 keeps the cube in the shared memory of one
- * 8-CTA thread-block cluster for all the steps of a call (L a multiple of 8,
- * 16 <= L <= 64; the z-planes split among the CTAs; with eta moves each CTA
- * moves the cubes whose lower plane it holds), 0 runs the step as launches
- * over the cube in global memory, -1 chooses.  The results do not depend on
- * the form; the call waits for the stream.  CVF_EINVAL for mode 1 where it
- * does not apply.  The automatic choice (-1, the default at creation) takes
- * the resident form up to L = 24. */
+ * thread-block cluster for all the steps of a call (L a multiple of 8,
+ * 16 <= L <= 64; 16 CTAs where L is a multiple of 16 from 32 up and the GPU
+ * can place such a cluster, else 8; the z-planes split among the CTAs; with
+ * eta moves each CTA moves the cubes whose lower plane it holds), 0 runs the
+ * step as launches over the cube in global memory, -1 chooses.  The results
+ * do not depend on the form; the call waits for the stream.  CVF_EINVAL for
+ * mode 1 where it does not apply.  The automatic choice (-1, the default at
+ * creation) takes the resident form up to L = 24, and at L = 32 with a
+ * 16-CTA cluster. */
 int cvf3_set_resident(cvf3_handle *h, int32_t mode);
 int cvf3_get_resident(cvf3_handle *h, int32_t *resident);
 

@@ -752,9 +752,9 @@ __global__ void __launch_bounds__(kThreads3) k_eta_bits3(Args3 A) {
 }
 
 // ---------------------------------------------------------------------------
-// Small cubes resident in one thread-block cluster (L a multiple of
-// kRes3Ctas, 16 <= L <= 64): CTA r holds the z-planes [r R, (r+1) R),
-// R = L / kRes3Ctas, in shared memory for every step of a call.  The step's
+// Small cubes resident in one thread-block cluster of nct = 8 or 16 CTAs (L a
+// multiple of nct, 16 <= L <= 64): CTA r holds the z-planes [r R, (r+1) R),
+// R = L / nct, in shared memory for every step of a call.  The step's
 // launches of k_pass3 become segments separated by cluster barriers; the
 // z-partners across a slab boundary are read from the neighbouring CTA's
 // shared memory.  Every cell is updated with the same draws and rule as in
@@ -767,10 +767,12 @@ constexpr int kRes3Ctas = 8;
 constexpr int kRes3Threads = 256;
 constexpr int kRes3Block = kRes3Threads + 64;  // + two volume warps
 constexpr int kRes3MaxSide = 64;
-// the automatic choice takes the resident form up to this side (measured:
-// 7.6 / 9.3 us per step at 16^3 / 24^3 against 14.6 / 15.3 with four
-// launches; even at 32^3; slower beyond, where 8 SMs do all the work)
-constexpr int kRes3AutoSide = 24;
+// the automatic choice takes the resident form up to this side (measured
+// per MC step with the eta update, resident against four launches: 16^3 7.6
+// against 14.6 us, 24^3 9.3 against 15.3, 32^3 12.1 against 16.1 with a
+// 16-CTA cluster (19.7 with 8); beyond, 16 SMs do too much of the work:
+// 48^3 31.5 against 16.2, 64^3 66.7 against 17.7)
+constexpr int kRes3AutoSide = 32;
 
 __device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive;" ::: "memory"); }
 __device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait;" ::: "memory"); }
@@ -803,7 +805,8 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
   // call and writes it back at the end (no global round trip per step)
   __shared__ Ctrl s_ctl;
   Ctrl* const gctl = A.ctrl;
-  const uint32_t L = A.L, L2 = A.L2, G = A.G, R = L / kRes3Ctas, z0 = rank * R;
+  const int nct = (int)cluster.num_blocks();  // 8, or 16 for cubes with L a multiple of 16
+  const uint32_t L = A.L, L2 = A.L2, G = A.G, R = L / (uint32_t)nct, z0 = rank * R;
   const bool eta_on = A.eta != nullptr;  // the eta step (App. A) opens every step
   const uint32_t q = A.q, qm1 = q - 1u;
   const bool sweeper = threadIdx.x < kRes3Threads;
@@ -825,8 +828,8 @@ __global__ void __launch_bounds__(kRes3Block) k_resident3(Args3 A, long long n_s
   if (eta_on && threadIdx.x < 9) sEtaMask[threadIdx.x] = pack_edge_mask(A.masks[threadIdx.x]);
   if (rank == 0 && threadIdx.x == 0) s_next_g = ctl->next_g;
   // the planes just below and above this slab, in the neighbours' shared memory
-  const uint32_t* below = cluster.map_shared_rank(cube, (rank + kRes3Ctas - 1) % kRes3Ctas) + (R - 1) * L2;
-  const uint32_t* above = cluster.map_shared_rank(cube, (rank + 1) % kRes3Ctas);
+  const uint32_t* below = cluster.map_shared_rank(cube, (rank + nct - 1) % nct) + (R - 1) * L2;
+  const uint32_t* above = cluster.map_shared_rank(cube, (rank + 1) % nct);
   unsigned long long* acc0 = cluster.map_shared_rank(&s_acc[0], 0);
   unsigned long long* hist0 = cluster.map_shared_rank(&s_hist[0], 0);
   const int* next_g0 = cluster.map_shared_rank(&s_next_g, 0);
@@ -1056,21 +1059,23 @@ __global__ void k_observables3(const VolumeArgs* __restrict__ V, const Ctrl* ctl
 namespace {
 
 template <bool CMP64>
-cudaError_t launch_resident3_t(const Args3& A, long long n_steps, cudaStream_t s, bool query,
-                               int* clusters) {
+cudaError_t launch_resident3_t(const Args3& A, int nct, long long n_steps, cudaStream_t s,
+                               bool query, int* clusters) {
   const void* fn = (const void*)k_resident3<CMP64>;
-  const size_t smem = (size_t)(A.L / kRes3Ctas) * A.L2 * sizeof(uint32_t);
+  const size_t smem = (size_t)(A.L / nct) * A.L2 * sizeof(uint32_t);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
-  cfg.gridDim = dim3(kRes3Ctas);
+  cfg.gridDim = dim3(nct);
   cfg.blockDim = dim3(kRes3Block);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kRes3Ctas;
+  attr[0].val.clusterDim.x = nct;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -1079,22 +1084,44 @@ cudaError_t launch_resident3_t(const Args3& A, long long n_steps, cudaStream_t s
   return cudaLaunchKernelEx(&cfg, k_resident3<CMP64>, A, n_steps);
 }
 
-cudaError_t launch_resident3(const Args3& A, bool cmp64, long long n_steps, cudaStream_t s) {
-  return cmp64 ? launch_resident3_t<true>(A, n_steps, s, false, nullptr)
-               : launch_resident3_t<false>(A, n_steps, s, false, nullptr);
+int query_clusters3(const Args3& A, bool cmp64, int nct) {
+  int clusters = 0;
+  const cudaError_t e = cmp64 ? launch_resident3_t<true>(A, nct, 0, nullptr, true, &clusters)
+                              : launch_resident3_t<false>(A, nct, 0, nullptr, true, &clusters);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return clusters;
+}
+
+// CTAs of the resident cluster: 16 (a non-portable cluster size) where the
+// side splits into 16 slabs of at least two planes and the GPU can place
+// such a cluster, else 8.  At 32^3 the 16-CTA form takes 12.1 us per MC step
+// against 19.7 us with 8 CTAs (48^3: 31.5 / 57.9, 64^3: 66.7 / 127.4).
+int resident3_ctas(const Args3& A, bool cmp64) {
+  if (A.L % 16u == 0u && A.L >= 32u && query_clusters3(A, cmp64, 16) >= 1) return 16;
+  return kRes3Ctas;
+}
+
+cudaError_t launch_resident3(const Args3& A, bool cmp64, int nct, long long n_steps,
+                             cudaStream_t s) {
+  return cmp64 ? launch_resident3_t<true>(A, nct, n_steps, s, false, nullptr)
+               : launch_resident3_t<false>(A, nct, n_steps, s, false, nullptr);
 }
 
 // Whether the cube can run resident in one cluster on this GPU.
 bool resident3_fits(const Args3& A, bool cmp64) {
   if (A.L % kRes3Ctas != 0 || A.L < 2 * kRes3Ctas || (int)A.L > kRes3MaxSide) return false;
-  int clusters = 0;
-  const cudaError_t e = cmp64 ? launch_resident3_t<true>(A, 0, nullptr, true, &clusters)
-                              : launch_resident3_t<false>(A, 0, nullptr, true, &clusters);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return clusters >= 1;
+  return query_clusters3(A, cmp64, kRes3Ctas) >= 1;
+}
+
+// The automatic choice: resident up to 24^3 with any cluster, and at 32^3
+// only when the 16-CTA cluster fits (with 8 CTAs it is slower there than
+// the launch form).
+bool resident3_auto(const Args3& A, bool cmp64) {
+  if ((int)A.L > kRes3AutoSide || !resident3_fits(A, cmp64)) return false;
+  return (int)A.L <= 24 || resident3_ctas(A, cmp64) == 16;
 }
 
 int check_params3(const cvf_params* p) {
@@ -1242,6 +1269,7 @@ struct cvf3_handle {
   bool cmp64;
   bool aligned;
   bool resident;  // the cube stays in one cluster's shared memory during a call
+  int res_ctas;   // CTAs of that cluster (0 until it is first needed)
   int grid;
   int grid_count;
   int grid_eta;
@@ -1445,7 +1473,7 @@ int cvf3_create(const cvf_params* p, void* stream, void* dev_state, cvf3_handle*
     per_sm = 1;
   const long long blocks = ((long long)A.groups + kThreads3 - 1) / kThreads3;
   h->grid = (int)std::max<long long>(1, std::min<long long>(blocks, (long long)sm_count() * per_sm));
-  h->resident = (int)L <= kRes3AutoSide && resident3_fits(A, h->cmp64);
+  h->resident = resident3_auto(A, h->cmp64);
   h->grid_count = (int)std::max<long long>(
       1, std::min<long long>((h->N + kThreads3 - 1) / kThreads3, (long long)sm_count() * 8));
   h->grid_eta = (int)std::max<long long>(
@@ -1484,9 +1512,10 @@ int cvf3_sweep(cvf3_handle* h, int64_t n_sweeps, int32_t record_every) {
   k_set_record<<<1, 32, 0, h->stream>>>(h->ctrl, record_every);
   if (h->resident) {
     constexpr long long kChunk = 1 << 16;
+    if (!h->res_ctas) h->res_ctas = resident3_ctas(h->args, h->cmp64);
     for (long long done = 0; done < n_sweeps; done += kChunk)
-      CVF_CUDA_CHECK(launch_resident3(h->args, h->cmp64, std::min(kChunk, n_sweeps - done),
-                                      h->stream));
+      CVF_CUDA_CHECK(launch_resident3(h->args, h->cmp64, h->res_ctas,
+                                      std::min(kChunk, n_sweeps - done), h->stream));
     return CVF_OK;
   }
   long long left = n_sweeps;
@@ -1674,7 +1703,7 @@ int cvf3_set_resident(cvf3_handle* h, int32_t mode) {
     return set_error(CVF_EINVAL, "the resident form needs L a multiple of %d, %d <= L <= %d",
                      kRes3Ctas, 2 * kRes3Ctas, kRes3MaxSide);
   CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
-  h->resident = (mode == 1) || (mode == -1 && fits && h->p.L <= kRes3AutoSide);
+  h->resident = (mode == 1) || (mode == -1 && resident3_auto(h->args, h->cmp64));
   return CVF_OK;
 }
 

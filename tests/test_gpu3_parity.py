@@ -240,7 +240,9 @@ def test_lattice3_resident_choice():
     with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=16)))) as lat:
         assert lat.resident()              # with the eta step as well
     with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=32)))) as lat:
-        assert not lat.resident()          # beyond 24^3 the launch form is faster
+        assert lat.resident()              # 32^3 in a 16-CTA cluster
+    with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=40)))) as lat:
+        assert not lat.resident()          # beyond 32^3 the launch form is faster
     with Lattice3(params_from_dict(asdict(oracle.physical_params3(300.0, 0.1, L=12)))) as lat:
         assert not lat.resident()          # 12 is not a multiple of 8
         with pytest.raises(_capi.CvfError):
