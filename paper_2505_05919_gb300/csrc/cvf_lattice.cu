@@ -191,7 +191,12 @@ constexpr int kNumSweepTiles = 3;
 // cells per iteration in colour 0)
 constexpr int kSweepShape = kHalfRows | kUnroll1 | kSplitRec;
 
-template <int RNG_WORDS, bool CMP64, int TILE>
+// WALK: every tile of the lattice is full and the rows are 16-byte aligned
+// (L a multiple of the tile height and of 2 x the tile width, Lh of 4), so
+// the colour phases take the column-walking form (colour0_walk /
+// colour1_walk); a separate instantiation, since one kernel holding both forms
+// spills.
+template <int RNG_WORDS, bool CMP64, int TILE, bool WALK>
 __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     k_sweep_tiled(const __grid_constant__ LatticeArgs A, const __grid_constant__ CUtensorMap tm0,
                   const __grid_constant__ CUtensorMap tm1) {
@@ -326,14 +331,32 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     __syncthreads();
     const TileGeom gm = tile_geom<kTileRows, kTileWords>(v.L, v.Lh, (t / tiles_x) * kTileRows,
                                                          (t % tiles_x) * kTileWords);
-    colour0<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, kSweepShape>(v, gm, S, Tb, cnt,
-                                                               rec ? s_hist4 : nullptr);
+    if constexpr (WALK) {
+      if (rec)
+        colour0_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, true>(v, gm, S, Tb, cnt,
+                                                                               s_hist4);
+      else
+        colour0_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, false>(v, gm, S, Tb, cnt,
+                                                                                nullptr);
+    } else {
+      colour0<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, kSweepShape>(
+          v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
+    }
     if (threadIdx.x == 0) s_next = (int)(atomicAdd(&ctl->tile_next, 1u) + gridDim.x - 1u);
     __syncthreads();  // S.in is free: fetch the next tile while colour 1 runs
     const int t2 = s_next;
     const bool t2_tma = (t2 < ntiles) ? stage(t2) : false;
-    colour1<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, kSweepShape>(v, gm, S, Tb, cnt,
-                                                               rec ? s_hist4 : nullptr);
+    if constexpr (WALK) {
+      if (rec)
+        colour1_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, true>(v, gm, S, Tb, cnt,
+                                                                               s_hist4);
+      else
+        colour1_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, false>(v, gm, S, Tb, cnt,
+                                                                                nullptr);
+    } else {
+      colour1<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, kSweepShape>(
+          v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
+    }
     if (rec) {
       __syncthreads();
       hist_flush(s_hist4, ctl->acc_hist);
@@ -665,18 +688,33 @@ void release(cvf_handle* h) {
   delete h;
 }
 
-// The sweep kernel for (rng_words, cmp64, tile shape).
+// Whether every tile of shape `tile` on an L x L lattice is full with rows
+// 16-byte aligned (the column-walking form of the sweep).
 template <int TILE>
-const void* sweep_kernel_t(int rng_words, bool cmp64) {
-  if (rng_words == 1)
-    return cmp64 ? (const void*)k_sweep_tiled<1, true, TILE> : (const void*)k_sweep_tiled<1, false, TILE>;
-  return cmp64 ? (const void*)k_sweep_tiled<2, true, TILE> : (const void*)k_sweep_tiled<2, false, TILE>;
+bool walk_fits_t(int L) {
+  return L % TileShape<TILE>::R == 0 && (L / 2) % TileShape<TILE>::W == 0 && (L / 2) % 4 == 0;
 }
 
-const void* sweep_kernel(int rng_words, bool cmp64, int tile) {
-  if (tile == 0) return sweep_kernel_t<0>(rng_words, cmp64);
-  if (tile == 1) return sweep_kernel_t<1>(rng_words, cmp64);
-  return sweep_kernel_t<2>(rng_words, cmp64);
+// The sweep kernel for (rng_words, cmp64, tile shape, lattice side).
+template <int TILE, bool WALK>
+const void* sweep_kernel_tw(int rng_words, bool cmp64) {
+  if (rng_words == 1)
+    return cmp64 ? (const void*)k_sweep_tiled<1, true, TILE, WALK>
+                 : (const void*)k_sweep_tiled<1, false, TILE, WALK>;
+  return cmp64 ? (const void*)k_sweep_tiled<2, true, TILE, WALK>
+               : (const void*)k_sweep_tiled<2, false, TILE, WALK>;
+}
+
+template <int TILE>
+const void* sweep_kernel_t(int rng_words, bool cmp64, int L) {
+  return walk_fits_t<TILE>(L) ? sweep_kernel_tw<TILE, true>(rng_words, cmp64)
+                              : sweep_kernel_tw<TILE, false>(rng_words, cmp64);
+}
+
+const void* sweep_kernel(int rng_words, bool cmp64, int tile, int L) {
+  if (tile == 0) return sweep_kernel_t<0>(rng_words, cmp64, L);
+  if (tile == 1) return sweep_kernel_t<1>(rng_words, cmp64, L);
+  return sweep_kernel_t<2>(rng_words, cmp64, L);
 }
 
 cudaError_t launch_sweep(const void* fn, int grid, cudaStream_t s, const LatticeArgs& A,
@@ -705,7 +743,7 @@ cudaError_t launch_sweep(const void* fn, int grid, cudaStream_t s, const Lattice
 cudaError_t enqueue_step(cvf_handle* h, cudaStream_t s) {
   const bool one = h->p.rng_words == 1;
   if (h->p.schedule == CVF_SCHED_CHECKERBOARD) {
-    return launch_sweep(sweep_kernel(h->p.rng_words, h->cmp64, h->tile), h->grid_tiles, s,
+    return launch_sweep(sweep_kernel(h->p.rng_words, h->cmp64, h->tile, h->p.L), h->grid_tiles, s,
                         h->args, h->tm[0], h->tm[1], h->programmatic);
   } else {
     for (int j = 0; j < kLayerLaunches; ++j) {
@@ -793,7 +831,8 @@ long long tile_count(int L, int tile) {
 
 int resident_sweep_blocks(bool cmp64, int rng_words, int tile) {
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(rng_words, cmp64, tile),
+  // (both forms of the kernel have the same registers and shared memory)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(rng_words, cmp64, tile, 1),
                                                     kThreads, 0) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
@@ -1412,7 +1451,7 @@ extern "C" int cvf_sweep_noalloc(const cvf_params* p, void* dev_state, double V_
   k_set_record<<<1, 32, 0, st>>>(&s->ctrl, record_every);
   const int tile = choose_tile(p->L, cmp64, p->rng_words);
   const int grid = tiled_grid(p->L, cmp64, p->rng_words, tile);
-  const void* fn = sweep_kernel(p->rng_words, cmp64, tile);
+  const void* fn = sweep_kernel(p->rng_words, cmp64, tile, p->L);
   CUtensorMap no_map;  // this path stages every tile with cp.async
   std::memset(&no_map, 0, sizeof(no_map));
   const bool programmatic =

@@ -203,10 +203,13 @@ __device__ __forceinline__ uint32_t update_in_word(uint32_t own, uint32_t xm_wor
 // aligned box, so one TMA copy can fill it); word p0-1+jj sits in column
 // jj+3.  After colour 0: rows y0-1 .. y0+TR, words p0-1 .. p0+TW.
 constexpr int kInColOff = 3;
+// After colour 0: rows y0-1 .. y0+TR, words p0-1 .. p0+TW, word p0-1+jj in
+// column jj+3 as in `in` (rows 16-byte aligned from word p0 on).
+constexpr int kMidColOff = 3;
 template <int TR, int TW>
 struct TileSmem {
   alignas(128) uint32_t in[TR + 4][TW + 8];
-  uint32_t mid[TR + 2][TW + 2];
+  alignas(16) uint32_t mid[TR + 2][TW + 8];
 };
 
 // Per-thread totals of the accepted moves of the cells a thread finished
@@ -358,7 +361,7 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
       uint32_t* const hist = decltype(rec_c)::value ? (inside ? s_hist4 : nullptr) : nullptr;
 #pragma unroll(kUnroll)
       for (int j = lcol; j < tw; j += kLanes) {
-        if (!dcheck(r + 1 >= 0 && r + 3 < TR + 4 && j + C + 1 < TW + 8 && j + 1 < TW + 2, v.err,
+        if (!dcheck(r + 1 >= 0 && r + 3 < TR + 4 && j + C + 1 < TW + 8 && j + C < TW + 8, v.err,
                     kSiteTileRead))
           continue;
         const int xg = 2 * (p0 + j) + hi;
@@ -368,7 +371,7 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
             S.in[r + 1][j + C], S.in[r + 3][j + C], hi, (uint32_t)((long long)yg * L + xg),
             v.s_lo, v.s_hi, v.keys, v.q, Tb, pk_row, hist);
         if (inside) pk += pk_row;  // the halo rows belong to other tiles
-        S.mid[r + 1][j + 1] = out;
+        S.mid[r + 1][j + C] = out;
       }
     };
     dispatch_row<SHAPE, kRows>(row, hi, s_hist4 != nullptr);
@@ -392,10 +395,10 @@ __device__ __forceinline__ void colour0(const StepView<KEYS>& v, const TileGeom&
     // the unused side of the ring word is clamped into the staged columns
     const int jm = max(j, 0), jp = min(j + 2, tw + 1);
     if (!dcheck(r + 1 >= 0 && r + 3 < TR + 4 && j + C >= 0 && j + C < TW + 8 &&
-                    jp + kInColOff < TW + 8 && j + 1 >= 0 && j + 1 < TW + 2,
+                    jp + kInColOff < TW + 8,
                 v.err, kSiteTileRead))
       continue;
-    S.mid[r + 1][j + 1] = update_in_word<RNG_WORDS, CMP64>(
+    S.mid[r + 1][j + C] = update_in_word<RNG_WORDS, CMP64>(
         S.in[r + 2][j + C], S.in[r + 2][jm + kInColOff], S.in[r + 2][jp + kInColOff],
         S.in[r + 1][j + C], S.in[r + 3][j + C], hi, (uint32_t)((long long)yg * L + xg), v.s_lo,
         v.s_hi, v.keys, v.q, Tb, not_counted, nullptr);
@@ -411,6 +414,7 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
   constexpr int kRows = (TW >= 32) ? 1 : 32 / TW;
   constexpr int kLanes = (TW >= 32) ? 32 : TW;
   constexpr int kUnroll = (SHAPE & kUnroll1) ? 2 : 1;
+  constexpr int M = kMidColOff + 1;  // column of word 0 in S.mid
   const int L = v.L, Lh = v.Lh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lrow = lane / kLanes, lcol = lane % kLanes;
@@ -426,19 +430,137 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
       uint32_t* const hist = decltype(rec_c)::value ? s_hist4 : nullptr;
 #pragma unroll(kUnroll)
       for (int j = lcol; j < tw; j += kLanes) {
-        if (!dcheck(r + 2 < TR + 2 && j + 2 < TW + 2 && y >= 0 && y < L && p0 + j < Lh, v.err,
+        if (!dcheck(r + 2 < TR + 2 && j + M + 1 < TW + 8 && y >= 0 && y < L && p0 + j < Lh, v.err,
                     kSiteTileWrite))
           continue;
         const int xg = 2 * (p0 + j) + hi;
         drow[j] = update_in_word<RNG_WORDS, CMP64, decltype(hi_c)::value>(
-            S.mid[r + 1][j + 1], S.mid[r + 1][j], S.mid[r + 1][j + 2], S.mid[r][j + 1],
-            S.mid[r + 2][j + 1], hi, (uint32_t)((long long)y * L + xg), v.s_lo, v.s_hi, v.keys,
-            v.q, Tb, pk, hist);
+            S.mid[r + 1][j + M], S.mid[r + 1][j + M - 1], S.mid[r + 1][j + M + 1],
+            S.mid[r][j + M], S.mid[r + 2][j + M], hi, (uint32_t)((long long)y * L + xg), v.s_lo,
+            v.s_hi, v.keys, v.q, Tb, pk, hist);
       }
     };
     dispatch_row<SHAPE, kRows>(row, hi, s_hist4 != nullptr);
   }
   cnt.add(pk);
+}
+
+// ---------------------------------------------------------------------------
+// Full tiles (th = TR, tw = TW, y0 even, Lh a multiple of 4): each thread
+// walks down one word column through TR / (NT / TW) consecutive rows, two
+// rows per iteration (even row: the colour-0 cell in the low half, odd row:
+// in the high half, so both halves are compile-time constants), keeping the
+// rows above and below in registers (three shared loads per cell instead of
+// five).  Colour 0's halo rows -1 and TR and its ring of single cells follow
+// as one cell per thread.  Colour 1 writes each word back in place (a
+// colour-1 update reads only the colour-0 halves of its neighbours, which
+// colour 1 does not change), and the tile is copied out with 16-byte loads
+// and stores.
+// ---------------------------------------------------------------------------
+template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, bool REC, typename KEYS>
+__device__ __forceinline__ void colour0_walk(const StepView<KEYS>& v, const TileGeom& g,
+                                             TileSmem<TR, TW>& S, const Tables2& Tb,
+                                             TileCounts& cnt, uint32_t* s_hist4) {
+  constexpr int kGroups = NT / TW, kRows = TR / kGroups;
+  static_assert(NT % TW == 0 && TR % kGroups == 0 && kRows % 2 == 0, "walk shape");
+  constexpr int C = kInColOff + 1;  // column of word 0 (S.in and S.mid)
+  constexpr int P = TW + 8;         // row pitch (words) of S.in and S.mid
+  const uint32_t L = (uint32_t)v.L;
+  const int j = (int)threadIdx.x % TW, r0 = ((int)threadIdx.x / TW) * kRows;
+  uint32_t* const hist = REC ? s_hist4 : nullptr;
+  {
+    const uint32_t* p = &S.in[r0 + 2][j + C];  // own word of row r0
+    uint32_t* o = &S.mid[r0 + 1][j + C];
+    uint32_t cb = (uint32_t)(g.y0 + r0) * L + 2u * (uint32_t)(g.p0 + j);
+    uint32_t ym = p[-P], own = p[0];
+    uint32_t pk = 0;
+#pragma unroll 1
+    for (int k = 0; k < kRows; k += 2) {
+      const uint32_t yp = p[P];
+      o[0] = update_in_word<RNG_WORDS, CMP64, 0>(own, p[-1], p[1], ym, yp, 0, cb, v.s_lo,
+                                                 v.s_hi, v.keys, v.q, Tb, pk, hist);
+      const uint32_t yp2 = p[2 * P];
+      o[P] = update_in_word<RNG_WORDS, CMP64, 1>(yp, p[P - 1], p[P + 1], own, yp2, 1, cb + L + 1u,
+                                                 v.s_lo, v.s_hi, v.keys, v.q, Tb, pk, hist);
+      ym = yp;
+      own = yp2;
+      cb += 2u * L;
+      p += 2 * P;
+      o += 2 * P;
+    }
+    cnt.add(pk);
+  }
+  // rows -1 and TR (other tiles' cells: not counted), then the ring
+  const int th = g.th, tw = g.tw, y0 = g.y0, p0 = g.p0;
+  for (int i = (int)threadIdx.x; i < 2 * TW + TR + 2; i += NT) {
+    int r, jj;
+    if (i < 2 * TW) {
+      r = (i < TW) ? -1 : TR;
+      jj = i % TW;
+    } else {
+      r = i - 2 * TW - 1;
+      jj = ((y0 + r) & 1) ? -1 : tw;
+    }
+    const int y = y0 + r;
+    const int hi = y & 1;
+    const int yg = (y < 0) ? y + (int)L : (y >= (int)L ? y - (int)L : y);
+    int xg = 2 * (p0 + jj) + hi;
+    xg = (xg < 0) ? xg + (int)L : (xg >= (int)L ? xg - (int)L : xg);
+    const int jm = max(jj, 0), jp = min(jj + 2, tw + 1);
+    uint32_t not_counted = 0;
+    if (!dcheck(r + 1 >= 0 && r + 3 < TR + 4 && jj + C >= 0 && jj + C < TW + 8 &&
+                    jp + kInColOff < TW + 8 && th == TR,
+                v.err, kSiteTileRead))
+      continue;
+    S.mid[r + 1][jj + C] = update_in_word<RNG_WORDS, CMP64>(
+        S.in[r + 2][jj + C], S.in[r + 2][jm + kInColOff], S.in[r + 2][jp + kInColOff],
+        S.in[r + 1][jj + C], S.in[r + 3][jj + C], hi, (uint32_t)yg * L + (uint32_t)xg, v.s_lo,
+        v.s_hi, v.keys, v.q, Tb, not_counted, nullptr);
+  }
+}
+
+template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, bool REC, typename KEYS>
+__device__ __forceinline__ void colour1_walk(const StepView<KEYS>& v, const TileGeom& g,
+                                             TileSmem<TR, TW>& S, const Tables2& Tb,
+                                             TileCounts& cnt, uint32_t* s_hist4) {
+  constexpr int kGroups = NT / TW, kRows = TR / kGroups;
+  constexpr int C = kMidColOff + 1;
+  constexpr int P = TW + 8;
+  const uint32_t L = (uint32_t)v.L;
+  const int j = (int)threadIdx.x % TW, r0 = ((int)threadIdx.x / TW) * kRows;
+  uint32_t* const hist = REC ? s_hist4 : nullptr;
+  uint32_t* q = &S.mid[r0 + 1][j + C];  // own word of row r0
+  uint32_t cb = (uint32_t)(g.y0 + r0) * L + 2u * (uint32_t)(g.p0 + j);
+  uint32_t ym = q[-P], own = q[0];
+  uint32_t pk = 0;
+#pragma unroll 1
+  for (int k = 0; k < kRows; k += 2) {
+    // even row: the colour-1 cell in the high half; odd row: the low half
+    const uint32_t yp = q[P];
+    const uint32_t w0 = update_in_word<RNG_WORDS, CMP64, 1>(own, q[-1], q[1], ym, yp, 1, cb + 1u,
+                                                            v.s_lo, v.s_hi, v.keys, v.q, Tb, pk,
+                                                            hist);
+    const uint32_t yp2 = q[2 * P];
+    const uint32_t w1 = update_in_word<RNG_WORDS, CMP64, 0>(yp, q[P - 1], q[P + 1], own, yp2, 0,
+                                                            cb + L, v.s_lo, v.s_hi, v.keys, v.q,
+                                                            Tb, pk, hist);
+    reinterpret_cast<uint16_t*>(q)[1] = (uint16_t)(w0 >> 16);
+    reinterpret_cast<uint16_t*>(q + P)[0] = (uint16_t)w1;
+    ym = yp;
+    own = yp2;
+    cb += 2u * L;
+    q += 2 * P;
+  }
+  cnt.add(pk);
+  __syncthreads();
+  // the tile's TR x TW words to the destination, 16 bytes at a time
+  constexpr int kVec = TW / 4;
+  const size_t Lh = (size_t)v.Lh;
+  for (int e = (int)threadIdx.x; e < TR * kVec; e += NT) {
+    const int r = e / kVec, c4 = e % kVec;
+    const uint4 val = *reinterpret_cast<const uint4*>(&S.mid[r + 1][C + 4 * c4]);
+    *reinterpret_cast<uint4*>(v.dst + (size_t)(g.y0 + r) * Lh + (size_t)(g.p0 + 4 * c4)) = val;
+  }
 }
 
 }  // namespace cvf

@@ -210,7 +210,9 @@ __device__ void wave_commit(const LatticeArgs& A, WaveHdr* H, long long step0, l
   st_release_u32(&H->committed, (unsigned int)(r + 1));
 }
 
-template <int RNG_WORDS, bool CMP64, int TR, int TW>
+// WALK: every tile full and the rows 16-byte aligned (the column-walking
+// colour phases; a separate instantiation, as for k_sweep_tiled).
+template <int RNG_WORDS, bool CMP64, int TR, int TW, bool WALK>
 __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     k_sweep_wave(const __grid_constant__ LatticeArgs A, WaveHdr* H, long long step0,
                  long long n_steps, const __grid_constant__ WaveGeom G) {
@@ -346,8 +348,15 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     cp_async_wait_all();
     __syncthreads();
     const bool rec = step_recorded(every, step);
-    colour0<RNG_WORDS, CMP64, TR, TW, kThreads, kWaveShape>(v, gm, S, Tb, cnt,
-                                                             rec ? s_hist4 : nullptr);
+    if constexpr (WALK) {
+      if (rec)
+        colour0_walk<RNG_WORDS, CMP64, TR, TW, kThreads, true>(v, gm, S, Tb, cnt, s_hist4);
+      else
+        colour0_walk<RNG_WORDS, CMP64, TR, TW, kThreads, false>(v, gm, S, Tb, cnt, nullptr);
+    } else {
+      colour0<RNG_WORDS, CMP64, TR, TW, kThreads, kWaveShape>(v, gm, S, Tb, cnt,
+                                                               rec ? s_hist4 : nullptr);
+    }
     // S.in is free: the last warp (the least colour-0 work) takes the next
     // item and, when its dependencies already hold, it is staged while
     // colour 1 runs
@@ -378,8 +387,15 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       const TileGeom gn = tile_geom<TR, TW>(L, Lh, nty * TR, (n_t - nty * G.tiles_x) * TW);
       stage_async16<TR, TW, kThreads>(vn, gn, S);
     }
-    colour1<RNG_WORDS, CMP64, TR, TW, kThreads, kWaveShape>(v, gm, S, Tb, cnt,
-                                                             rec ? s_hist4 : nullptr);
+    if constexpr (WALK) {
+      if (rec)
+        colour1_walk<RNG_WORDS, CMP64, TR, TW, kThreads, true>(v, gm, S, Tb, cnt, s_hist4);
+      else
+        colour1_walk<RNG_WORDS, CMP64, TR, TW, kThreads, false>(v, gm, S, Tb, cnt, nullptr);
+    } else {
+      colour1<RNG_WORDS, CMP64, TR, TW, kThreads, kWaveShape>(v, gm, S, Tb, cnt,
+                                                               rec ? s_hist4 : nullptr);
+    }
     WaveAcc* slot = &H->acc[r % kWaveRing];
     if (rec) {  // block-uniform
       __syncthreads();
@@ -437,25 +453,35 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
   cp_async_wait_all();  // no copy may still be in flight when the block exits
 }
 
+template <int RW, bool C64, int TR, int TW>
+const void* wave_kernel_s(int L) {
+  const bool walk = L % TR == 0 && (L / 2) % TW == 0 && (L / 2) % 4 == 0;
+  return walk ? (const void*)k_sweep_wave<RW, C64, TR, TW, true>
+              : (const void*)k_sweep_wave<RW, C64, TR, TW, false>;
+}
+
 template <int RW, bool C64>
-const void* wave_kernel_t(int shape) {
+const void* wave_kernel_t(int shape, int L) {
   switch (shape) {
-    case 0: return (const void*)k_sweep_wave<RW, C64, 64, 64>;
-    case 1: return (const void*)k_sweep_wave<RW, C64, 32, 32>;
-    default: return (const void*)k_sweep_wave<RW, C64, 16, 32>;
+    case 0: return wave_kernel_s<RW, C64, 64, 64>(L);
+    case 1: return wave_kernel_s<RW, C64, 32, 32>(L);
+    default: return wave_kernel_s<RW, C64, 16, 32>(L);
   }
 }
 
-const void* wave_kernel(int rng_words, bool cmp64, int shape) {
-  if (rng_words == 1) return cmp64 ? wave_kernel_t<1, true>(shape) : wave_kernel_t<1, false>(shape);
-  return cmp64 ? wave_kernel_t<2, true>(shape) : wave_kernel_t<2, false>(shape);
+// The kernel for (rng_words, cmp64, tile shape, lattice side); L = 1 names
+// the general form (both forms have the same registers and shared memory).
+const void* wave_kernel(int rng_words, bool cmp64, int shape, int L) {
+  if (rng_words == 1)
+    return cmp64 ? wave_kernel_t<1, true>(shape, L) : wave_kernel_t<1, false>(shape, L);
+  return cmp64 ? wave_kernel_t<2, true>(shape, L) : wave_kernel_t<2, false>(shape, L);
 }
 
 }  // namespace
 
 int wave_blocks(int rng_words, bool cmp64, int shape) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_kernel(rng_words, cmp64, shape),
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_kernel(rng_words, cmp64, shape, 1),
                                                     kThreads, 0) != cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
@@ -490,7 +516,7 @@ cudaError_t launch_wave(const LatticeArgs& A, WaveHdr* H, size_t scratch_bytes, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, wave_kernel(rng_words, cmp64, shape), args);
+  return cudaLaunchKernelExC(&cfg, wave_kernel(rng_words, cmp64, shape, (int)A.L), args);
 }
 
 }  // namespace cvf

@@ -101,6 +101,41 @@ def test_checkerboard_every_tile_shape(config, L, K, extra):
         assert_obs_equal(a, b)
 
 
+@pytest.mark.parametrize("config", [0, 1, 2])
+@pytest.mark.parametrize("L,K,every,extra", [(128, 30, 1, {}), (256, 12, 3, dict(rng_words=2)),
+                                             (512, 6, 2, dict(T=270.0, init=oracle.INIT_ORDERED)),
+                                             (192, 10, 1, dict(q=5)), (128, 20, 4, dict(kT=1e-3)),
+                                             (256, 10, 1, dict(T=330.0, P=50.0, q=8))])
+def test_checkerboard_walking_form(config, L, K, every, extra):
+    """Lattices whose tiles are all full (L a multiple of the tile height and
+    of twice the tile width) sweep in the column-walking form: colour 1
+    updated in place and the tile copied out in 16-byte rows, the halo rows
+    and the ring swept one cell per thread.  Same lattice, counts and
+    recorded series as the oracle (L = 192 with 64-word tiles falls back to
+    the general form)."""
+    extra = dict(extra)
+    if "kT" in extra:  # the 64-bit threshold compare
+        op = oracle.OracleParams(L=L, seed=700 + L + config, init=oracle.INIT_RANDOM, **extra)
+    else:
+        T = extra.pop("T", 300.0)
+        P = extra.pop("P", 0.1)
+        op = oracle.physical_params(T, P, L=L, seed=700 + L + config, dv_max_frac=0.02, **extra)
+    with Lattice(params_from_dict(asdict(op))) as lat:
+        lat.set_tiles(config)
+        assert lat.tiles()[0] == config
+        lat.sweep(K // 2, every)
+        lat.sweep(K - K // 2, every)
+        s_gpu, o_gpu = lat.state(), lat.observables()
+        r_gpu, overflow = lat.drain()
+        assert lat.recount() == (o_gpu["n_hb_raw"], o_gpu["n_coop"])
+    s_ref, o_ref, r_ref = oracle_run(op, K, record_every=every)
+    assert not overflow and len(r_gpu) == len(r_ref)
+    assert np.array_equal(s_gpu, s_ref)
+    assert_obs_equal(o_gpu, o_ref)
+    for a, b in zip(r_gpu, r_ref):
+        assert_obs_equal(a, b)
+
+
 @pytest.mark.parametrize("L,K,extra", [(16, 300, {}), (64, 200, dict(rng_words=2)),
                                        (128, 60, dict(T=270.0, init=oracle.INIT_ORDERED)),
                                        (256, 20, dict(q=8)), (24, 150, dict(kT=1e-3)),
