@@ -63,6 +63,11 @@ def parse():
                     help="time budget of the serving measurement (0: skip)")
     ap.add_argument("--record-counters", default=None,
                     help="write the sweep's counters file from this ncu CSV and exit")
+    ap.add_argument("--tiles", type=int, default=-1,
+                    help="kernel mode: the sweep configuration (cvf_set_tiles; -1: automatic)")
+    ap.add_argument("--counter-steps", type=int, default=1,
+                    help="MC steps in the launch the counters CSV captured (the wavefront "
+                         "sweep runs a whole call in one launch)")
     return ap.parse_args()
 
 
@@ -70,17 +75,20 @@ def parse():
 # maximum clock (four schedulers of one warp-instruction per clock per SM).
 ISSUE_PEAK_T = 152 * 128 * 2.070e9 / 1e12
 
-# Counters of one k_sweep_tiled launch at 4096^2 (ncu: DRAM read + write
-# bytes, executed warp instructions), recorded by `bench.py --record-counters`
-# from an ncu capture together with a hash of the sweep kernel's sources; the
-# bench uses them only while that hash matches the current sources (null
-# otherwise: the kernel changed since the capture).
-COUNTERS_FILE = os.path.join(ROOT, "profiles", "k_sweep_tiled_L4096_counters.json")
-# the device code of the sweep (the public header's declarations and comments
-# do not enter it and are left out)
+# Counters of the 4096^2 sweep per MC step (ncu: DRAM read + write bytes,
+# executed warp instructions of one launch of the sweep kernel the automatic
+# configuration runs there -- k_sweep_wave, one launch per call -- divided
+# by the launch's steps), recorded by `bench.py --record-counters` from an ncu
+# capture together with a hash of the sweep kernels' sources; the bench uses
+# them only while that hash matches the current sources (null otherwise: the
+# kernel changed since the capture).
+COUNTERS_FILE = os.path.join(ROOT, "profiles", "k_sweep_wave_L4096_counters.json")
+# the device code of the sweeps (the public header's declarations and
+# comments do not enter it and are left out)
 SWEEP_SOURCES = ("paper_2505_05919_gb300/csrc/cvf_tile.cuh", "paper_2505_05919_gb300/csrc/cvf_lattice.cu",
                  "paper_2505_05919_gb300/csrc/cvf_lattice.cuh", "paper_2505_05919_gb300/csrc/cvf_device.cuh",
-                 "paper_2505_05919_gb300/csrc/cvf_tma.cuh")
+                 "paper_2505_05919_gb300/csrc/cvf_tma.cuh", "paper_2505_05919_gb300/csrc/cvf_wave.cu",
+                 "paper_2505_05919_gb300/csrc/cvf_fastdiv.cuh")
 
 
 def sweep_source_hash() -> str:
@@ -101,24 +109,28 @@ def sweep_counters():
     return d if d.get("source_hash") == sweep_source_hash() else None
 
 
-def record_counters(csv_path: str) -> int:
-    """Write COUNTERS_FILE from an ncu CSV (--csv --log-file) of one
-    k_sweep_tiled launch at 4096^2 with the metrics dram__bytes_read.sum,
+def record_counters(csv_path: str, steps: int) -> int:
+    """Write COUNTERS_FILE from an ncu CSV (--csv --log-file) of one launch
+    of the 4096^2 sweep kernel (k_sweep_wave or k_sweep_tiled) covering
+    `steps` MC steps, with the metrics dram__bytes_read.sum,
     dram__bytes_write.sum and smsp__inst_executed.sum."""
     import csv
     rows = [r for r in csv.reader(open(csv_path)) if len(r) > 5]
     hdr = rows[0]
     im, iv, ik = hdr.index("Metric Name"), hdr.index("Metric Value"), hdr.index("Kernel Name")
-    vals = {}
+    vals, kernel = {}, None
     for r in rows[1:]:
-        if "k_sweep_tiled" in r[ik]:
+        if "k_sweep_wave" in r[ik] or "k_sweep_tiled" in r[ik]:
             vals[r[im]] = float(r[iv].replace(",", ""))
+            kernel = r[ik]
     cells = 4096 * 4096
-    out = {"kernel": "k_sweep_tiled<1, 0, 0> (one MC step of the 4096^2 lattice, q = 6, 300 K)",
-           "source_hash": sweep_source_hash(), "cells": cells,
-           "dram_bytes": vals["dram__bytes_read.sum"] + vals["dram__bytes_write.sum"],
-           "inst_executed_warp": vals["smsp__inst_executed.sum"],
-           "instructions_per_update": vals["smsp__inst_executed.sum"] * 32 / (4 * cells),
+    out = {"kernel": "%s (%d MC steps of the 4096^2 lattice in the launch, q = 6, 300 K)"
+                     % (kernel, steps),
+           "source_hash": sweep_source_hash(), "cells": cells, "steps_in_launch": steps,
+           "dram_bytes": (vals["dram__bytes_read.sum"] + vals["dram__bytes_write.sum"]) / steps,
+           "inst_executed_warp": vals["smsp__inst_executed.sum"] / steps,
+           "instructions_per_update": vals["smsp__inst_executed.sum"] * 32 / (4 * cells * steps),
+           "per": "MC step",
            "capture": os.path.basename(csv_path)}
     with open(COUNTERS_FILE, "w") as f:
         json.dump(out, f, indent=1)
@@ -337,6 +349,9 @@ def run_kernel_mode(args):
     cfg = workload_configs(args.L)[1]
     stream = torch.cuda.Stream()
     lat = Lattice(lib_params(cfg), stream=stream)
+    if args.tiles >= 0:
+        lat.set_tiles(args.tiles)
+    tiles = lat.tiles()[0]
     lat.sweep(args.warmup)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -348,7 +363,7 @@ def run_kernel_mode(args):
     ms = ev0.elapsed_time(ev1)
     o = lat.observables()
     lat.close()
-    print(json.dumps({"mode": "kernel", "L": args.L, "sweeps": args.steps, "ms": ms,
+    print(json.dumps({"mode": "kernel", "L": args.L, "tiles": tiles, "sweeps": args.steps, "ms": ms,
                       "updates_per_ns": 4.0 * args.L * args.L * args.steps / (ms * 1e6),
                       "n_hb_raw": o["n_hb_raw"], "n_coop": o["n_coop"]}))
     return 0
@@ -735,7 +750,7 @@ def measure_serving(args, rank):
 def main():
     args = parse()
     if args.record_counters:
-        return record_counters(args.record_counters)
+        return record_counters(args.record_counters, args.counter_steps)
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "kernel":
@@ -795,10 +810,15 @@ def main():
     value = updates / (dev_s * 1e9)
     obs = [l.observables() for l in lats]
 
-    # dominant kernel: k_sweep_tiled, one launch per MC step; its average
-    # duration from CUDA events around 200 steps on the lattice's stream
+    # dominant kernel: the sweep of the automatic configuration (at 4096^2
+    # the wavefront, k_sweep_wave: one launch per call; the tiled sweep:
+    # one launch per MC step); its time per MC step from CUDA events around
+    # a 200-step call on the lattice's stream
     sw_ms = []
     lat = lats[1]
+    wave = lat.tiles()[0] >= 4
+    sweep_kernel = ("k_sweep_wave (one launch per call, the MC steps of the call in a wavefront)"
+                    if wave else "k_sweep_tiled (one launch per MC step)")
     for _ in range(5):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -817,8 +837,8 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": ceiling, "unit": "sigma-updates/ns",
                 "frac": achieved / ceiling,
                 "traffic": (counters["dram_bytes"] * (L / 4096.0) ** 2 if counters else None),
-                "traffic_unit": "bytes per launch (ncu dram read + write of the current kernel)",
-                "kernel": "k_sweep_tiled (one launch per MC step)",
+                "traffic_unit": "bytes per MC step (ncu dram read + write of the current kernel)",
+                "kernel": sweep_kernel,
                 "peak_kind": "measured: the step's Philox4x32-10 draws alone (cvf_philox_probe "
                              "over the same %d cells, %.1f us per step; four updates per block), "
                              "the random numbers every sweep of this method must make" % (L * L, philox_ms * 1e3)}
@@ -836,7 +856,8 @@ def main():
                           "instructions_per_update": ipu,
                           "peak_kind": "derived: 152 SM x 128 thread-instructions per clock x 2070 MHz",
                           "instructions_source": "ncu smsp__inst_executed.sum of one launch of the "
-                                                 "current kernel (profiles/k_sweep_tiled_L4096_counters.json)"}
+                                                 "current kernel per MC step "
+                                                 "(profiles/k_sweep_wave_L4096_counters.json)"}
     # the 32 MB state stays in L2 across steps: the byte roofline that
     # bounds it is the L2 copy bandwidth, measured here with the library's
     # own copy kernel on the same working-set size (and, for reference, on
@@ -894,7 +915,9 @@ def main():
                     small[k]["oracle"] = v
             except Exception as e:
                 small["oracle_error"] = str(e)
-        launches_per_sweep = 1  # k_sweep_tiled (the volume move runs inside it)
+        # k_set_record per call, then one k_sweep_wave launch per call or one
+        # k_sweep_tiled launch per MC step (the volume move runs inside it)
+        launches_per_call = 2 if wave else S + 1
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,
@@ -907,7 +930,7 @@ def main():
             "cpu_baseline": cpu,
             "cpu_baseline_all_cores": cpu_all,
             "e2e": e2e,
-            "gpu_launches": args.steps * (S * launches_per_sweep + 1),
+            "gpu_launches": args.steps * launches_per_call,
             "batched": batched,
             "serving": serving,
             "cubic": cubic,

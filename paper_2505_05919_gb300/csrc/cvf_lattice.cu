@@ -888,12 +888,16 @@ int wave_scratch(cvf_handle* h, int shape) {
 }
 
 // The automatic configuration: the resident form for small lattices; the
-// wavefront sweep for mid-size ones (measured on GB300 with the tiled
-// sweep's shape rule: 512^2 8.4 against 9.0 us per step, 1024^2 12.6
-// against 15.8, 2048^2 38.9 against 41.1, 2560^2 59.4 against 60.5; from
-// 3072^2 on the tiled sweep is ahead); else the tiled sweep with the
-// largest shape whose tiles fill every resident block.
-constexpr int kWaveAutoMin = 512, kWaveAutoMax = 2560;
+// wavefront sweep from 512^2 to 6144^2, with the tiled sweep's shape rule
+// (the largest shape with at least as many tiles as the tiled sweep has
+// resident blocks, which is also the fastest wavefront shape at every size
+// measured); else the tiled sweep with that shape.  Measured on GB300, us per
+// MC step, wavefront against the best tiled shape: 512^2 7.4 / 8.3, 1024^2
+// 11.2 / 14.3, 1536^2 19.6 / 24.0, 2048^2 32.8 / 36.8, 2560^2 47.9 / 54.9,
+// 3072^2 64.2 / 71.2, 4096^2 108.6 / 115.0, 5120^2 168.3 / 176.8, 6144^2
+// 241.9 / 248.9; 8192^2 429.1 / 427.3 (the tiled sweep's partly filled last
+// round of tiles costs less the more tiles a step has).
+constexpr int kWaveAutoMin = 512, kWaveAutoMax = 6144;
 int auto_config(const cvf_handle* h) {
   const cvf_params& p = h->p;
   if (p.schedule == CVF_SCHED_CHECKERBOARD && p.L <= kResAutoSide &&
@@ -911,9 +915,13 @@ void set_tile(cvf_handle* h, int tile) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
   }
-  if (tile == kResident || is_wave(tile)) return;
+  if (tile == kResident) return;
   int r, w;
   tile_shape(tile, h->p.L, &r, &w);
+  if (is_wave(tile)) {  // the wavefront stages interior tiles with these boxes too
+    h->args.use_tma = encode_state_maps(h->state, h->p.L, r, w, h->tm) ? 1 : 0;
+    return;
+  }
   h->grid_tiles = tiled_grid(h->p.L, h->cmp64, h->p.rng_words, tile);
   h->programmatic =
       tile_count(h->p.L, tile) >= resident_sweep_blocks(h->cmp64, h->p.rng_words, tile);
@@ -1093,7 +1101,7 @@ int cvf_sweep(cvf_handle* h, int64_t n_sweeps, int32_t record_every) {
     for (long long done = 0; done < n_sweeps; done += kChunk)
       CVF_CUDA_CHECK(launch_wave(h->args, h->wave, h->wave_bytes, h->p.rng_words, h->cmp64,
                                  h->tile - kWave, h->sweep_host + done,
-                                 std::min(kChunk, n_sweeps - done), h->stream));
+                                 std::min(kChunk, n_sweeps - done), h->tm, h->stream));
     h->sweep_host += n_sweeps;
     return CVF_OK;
   }

@@ -1,5 +1,6 @@
 // cvf_lattice.cuh -- launch arguments of the single-lattice kernels.
 #pragma once
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -14,10 +15,19 @@ constexpr int kThreads = 256;
 constexpr int kTileRows = 64;
 constexpr int kTileWords = 64;
 // register budgets: five 256-thread blocks per SM (48 registers a thread;
-// the most the 38 KB of shared memory of a block allows) for the
-// single-lattice sweep and for the batched kernel
+// the most the 40 KB of shared memory of a 64 x 64-word tile allows) for the
+// single-lattice tiled sweep; four (64 registers) for the batched kernel,
+// which keeps its item's replica state across the colour phases (the 256
+// replicas of the batched workload: 140.8 against 148.3 us per step on the
+// 64 x 64-word tiles the autotuner picks)
 constexpr int kSweepBlocksPerSM = 5;
-constexpr int kBatchBlocksPerSM = 5;
+constexpr int kBatchBlocksPerSM = 4;
+// the wavefront sweep keeps more state across its items (the item, its
+// dependencies, the counts not yet reported): four blocks per SM at 64
+// registers (at five blocks, 48 registers, its column-walking form spills
+// about 220 bytes and runs 6 % slower at 4096^2: 115.9 against 108.6 us per
+// step)
+constexpr int kWaveBlocksPerSM = 4;
 
 struct LatticeArgs {
   uint16_t* state;                   // state pair: 2 * L*L packed cell words
@@ -88,7 +98,7 @@ int wave_blocks(int rng_words, bool cmp64, int shape);
 // Clears the scratch (scratch_bytes) and launches the call's steps.
 cudaError_t launch_wave(const LatticeArgs& A, WaveHdr* H, size_t scratch_bytes, int rng_words,
                         bool cmp64, int shape, long long step0, long long n_steps,
-                        cudaStream_t s);
+                        const CUtensorMap* tm, cudaStream_t s);
 
 // Host helpers shared by both paths.
 void fill_volume_args(const cvf_params* p, long long N, const std::vector<int64_t>& d2,

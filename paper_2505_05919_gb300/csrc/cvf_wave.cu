@@ -64,6 +64,9 @@ __device__ __forceinline__ void wave_item(const WaveGeom& G, unsigned long long 
   }
 }
 constexpr int kWaveEngineBar = 5;                             // the engine's two warps
+// Bounded wait for a TMA stage (the copies complete in microseconds; the
+// limit only guards against a copy that never lands).
+constexpr uint32_t kWaveTmaWaitLimit = 1u << 26;
 
 __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -213,16 +216,19 @@ __device__ void wave_commit(const LatticeArgs& A, WaveHdr* H, long long step0, l
 // WALK: every tile full and the rows 16-byte aligned (the column-walking
 // colour phases; a separate instantiation, as for k_sweep_tiled).
 template <int RNG_WORDS, bool CMP64, int TR, int TW, bool WALK>
-__global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
+__global__ void __launch_bounds__(kThreads, kWaveBlocksPerSM)
     k_sweep_wave(const __grid_constant__ LatticeArgs A, WaveHdr* H, long long step0,
-                 long long n_steps, const __grid_constant__ WaveGeom G) {
+                 long long n_steps, const __grid_constant__ WaveGeom G,
+                 const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1) {
   __shared__ union {
     TileSmem<TR, TW> tile;
     VolumeArgs vol;  // the engine block's copy of the parameters
   } U;
   __shared__ Tables2 Tb;
   __shared__ uint32_t s_hist4[4];
+  // s_staged: 0 the item is not staged, 1 staged by cp.async, 2 by TMA
   __shared__ int s_r, s_t, s_ok, s_g, s_staged, n_r, n_t, n_ok, n_ready, n_g;
+  __shared__ alignas(8) uint64_t s_bar;
   Ctrl* const ctl = A.ctrl;
   unsigned int* const err = &ctl->error;
 
@@ -296,6 +302,8 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
   const bool async16 = (L % 8) == 0;  // rows and tile origins on 16-byte boundaries
   fill_prop2(Tb, A.q);
   if (threadIdx.x < 4) s_hist4[threadIdx.x] = 0;
+  if (threadIdx.x == 0) mbar_init(&s_bar, 1);  // before the loop's first barrier
+  uint32_t parity = 0;
   int g_cur = -1;
   TileCounts cnt{0, 0, 0};  // this thread's counts of the tiles not yet reported
   int pend = 0;             // the block's tiles not yet reported (all of one step)
@@ -326,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       fill_rows2(Tb, A.table24, g);
       g_cur = g;
     }
-    StepView<KeysInRegs> v;
+    StepView<KeysStep> v;
     v.src = reinterpret_cast<const uint32_t*>(A.state + (size_t)(step & 1) * N);
     v.dst = reinterpret_cast<uint32_t*>(A.state + (size_t)((step + 1) & 1) * N);
     v.L = L;
@@ -334,7 +342,8 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     v.q = A.q;
     v.s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
     v.s_hi = (uint32_t)((unsigned long long)step >> 32);
-    v.keys.K = A.keys;
+    v.keys.K = &A.keys;
+    v.keys.sd = step_draw(v.s_lo, v.s_hi, A.keys);
     v.err = err;
     const int ty = (int)fdiv((uint32_t)t, G.div_x);
     const TileGeom gm = tile_geom<TR, TW>(L, Lh, ty * TR, (t - ty * G.tiles_x) * TW);
@@ -345,7 +354,19 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       else
         stage_plain<TR, TW, kThreads, true>(v, gm, S);
     }
-    cp_async_wait_all();
+    if (staged == 2) {  // block-uniform: the TMA copy started during the last item
+      uint32_t spins = 0;
+      while (!mbar_try_wait(&s_bar, parity)) {
+        if (++spins > kWaveTmaWaitLimit) {  // a copy that never lands: stop the launch
+          atomicOr(err, 1u);
+          atomicExch(&H->abort, 1u);
+          break;
+        }
+      }
+      parity ^= 1u;
+    } else {
+      cp_async_wait_all();
+    }
     __syncthreads();
     const bool rec = step_recorded(every, step);
     if constexpr (WALK) {
@@ -377,6 +398,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       }
     }
     __syncthreads();
+    bool next_tma = false;
     if (n_ready) {
       StepView<KeysInRegs> vn;
       vn.src = reinterpret_cast<const uint32_t*>(A.state + (size_t)((step0 + n_r) & 1) * N);
@@ -385,7 +407,34 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
       vn.err = err;
       const int nty = (int)fdiv((uint32_t)n_t, G.div_x);
       const TileGeom gn = tile_geom<TR, TW>(L, Lh, nty * TR, (n_t - nty * G.tiles_x) * TW);
-      stage_async16<TR, TW, kThreads>(vn, gn, S);
+      // 64 x 64-word tiles: one TMA box (issued by thread 0) when the tile
+      // and its halo lie inside the lattice (the box's x, p0 - 4, is a
+      // multiple of 4 words); at 4096^2 106.7 against 108.6 us per step with
+      // cp.async.  The smaller tiles keep the 16-byte cp.async copies, which
+      // ran 1-2 % faster there (1024^2 with 16 x 32 words: 11.2 against
+      // 11.4 us; 2048^2 with 32 x 32: 32.8 against 33.3).
+      next_tma = TR >= 64 && A.use_tma && gn.th == TR && gn.tw == TW && gn.p0 >= 4 &&
+                 gn.p0 + TW + 4 <= Lh && gn.y0 >= 2 && gn.y0 + TR + 2 <= L;
+      if (next_tma) {
+        if (threadIdx.x == 0) {
+          // S.in's colour-0 reads are done (the barrier above); the words
+          // of the tiles around were acquired by the dependency test (warp
+          // NT/32 - 1, before the barrier) and are read by the async proxy
+          fence_proxy_async_shared();
+          fence_proxy_async_global();
+          if (dcheck(((gn.p0 - 4) & 3) == 0 && gn.y0 - 2 >= 0 && gn.p0 + TW + 4 <= Lh &&
+                         gn.y0 + TR + 2 <= L,
+                     err, kSiteTma)) {
+            mbar_arrive_expect_tx(&s_bar, (uint32_t)sizeof(S.in));
+            tma_load_2d(&S.in[0][0], ((step0 + n_r) & 1) ? &tm1 : &tm0, gn.p0 - 4, gn.y0 - 2,
+                        &s_bar);
+          } else {
+            mbar_arrive_expect_tx(&s_bar, 0u);
+          }
+        }
+      } else {
+        stage_async16<TR, TW, kThreads>(vn, gn, S);
+      }
     }
     if constexpr (WALK) {
       if (rec)
@@ -446,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
         s_r = n_r;
         s_t = n_t;
         s_g = g2;
-        s_staged = n_ready;
+        s_staged = n_ready ? (next_tma ? 2 : 1) : 0;
       }
     }
   }
@@ -492,7 +541,7 @@ int wave_blocks(int rng_words, bool cmp64, int shape) {
 
 cudaError_t launch_wave(const LatticeArgs& A, WaveHdr* H, size_t scratch_bytes, int rng_words,
                         bool cmp64, int shape, long long step0, long long n_steps,
-                        cudaStream_t s) {
+                        const CUtensorMap* tm, cudaStream_t s) {
   const int grid = wave_blocks(rng_words, cmp64, shape);
   if (grid < 2) return cudaErrorCooperativeLaunchTooLarge;
   const int tr = (shape == 0) ? 64 : (shape == 1) ? 32 : 16, tw = (shape == 0) ? 64 : 32;
@@ -505,7 +554,8 @@ cudaError_t launch_wave(const LatticeArgs& A, WaveHdr* H, size_t scratch_bytes, 
   G.small = (n_steps * (long long)G.T < (1ll << 31)) ? 1 : 0;
   cudaError_t e = cudaMemsetAsync(H, 0, scratch_bytes, s);
   if (e != cudaSuccess) return e;
-  void* args[5] = {const_cast<LatticeArgs*>(&A), &H, &step0, &n_steps, &G};
+  void* args[7] = {const_cast<LatticeArgs*>(&A), &H, &step0, &n_steps, &G,
+                   const_cast<CUtensorMap*>(&tm[0]), const_cast<CUtensorMap*>(&tm[1])};
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3(grid);

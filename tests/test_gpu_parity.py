@@ -223,7 +223,9 @@ def test_wavefront_sweep(config, L, K, extra):
 
 def test_tile_choice():
     with Lattice(params(300.0, 0.1, L=4096)) as lat:
-        assert lat.tiles() == (0, 64, 64)  # the large tile at the benchmark size
+        assert lat.tiles() == (4, 64, 64)  # the benchmark size: the wavefront, large tiles
+    with Lattice(params(300.0, 0.1, L=8192)) as lat:
+        assert lat.tiles() == (0, 64, 64)  # beyond 6144: the tiled sweep
     with Lattice(params(300.0, 0.1, L=1024)) as lat:
         assert lat.tiles() == (6, 16, 32)  # mid-size lattices: the wavefront sweep
     with Lattice(params(300.0, 0.1, L=2048)) as lat:
@@ -405,7 +407,9 @@ def test_ring_overflow_keeps_newest():
 def test_full_size_sampled_windows(cfg):
     """The six 4096 x 4096 lattices the benchmark times (random init seed 3
     and ordered init, 270 / 300 / 330 K, 0.1 MPa), 50 steps through the
-    tiled sweep with programmatic launches.  The oracle cannot run the whole
+    automatic form the benchmark runs (the wavefront sweep on 64 x 64-word
+    tiles, one launch for the call), and for two of them through the tiled
+    sweep with programmatic launches as well.  The oracle cannot run the whole
     lattice, so it recomputes eight sampled windows: a checkerboard step
     moves information by at most two cells, so a window run with its border
     frozen is exact more than 2K + 2 cells inside.  Four windows lie across
@@ -419,12 +423,18 @@ def test_full_size_sampled_windows(cfg):
     op = oracle.physical_params(c["T"], c["P"], L=L, q=c["q"], seed=c["seed"], init=c["init"])
     with Lattice(params_from_dict(asdict(op))) as lat:
         init_gpu = lat.state()
-        assert lat.tiles()[0] == 0
+        assert lat.tiles()[0] == 4
         lat.sweep(K)
         s_gpu = lat.state()
         o_gpu = lat.observables()
         hb, co = lat.recount()
     assert (hb, co) == (o_gpu["n_hb_raw"], o_gpu["n_coop"])
+    if cfg in (0, 4):
+        with Lattice(params_from_dict(asdict(op))) as lat:
+            lat.set_tiles(0)
+            lat.sweep(K)
+            assert np.array_equal(lat.state(), s_gpu)
+            assert_obs_equal(lat.observables(), o_gpu)
     ref0 = oracle.Oracle(op)
     assert np.array_equal(init_gpu, ref0.state())
     done, V, g, acc = oracle.volume_chain(op, ref0.observables()["V_iso"], 0, K)
