@@ -333,10 +333,10 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
                                                          (t % tiles_x) * kTileWords);
     if constexpr (WALK) {
       if (rec)
-        colour0_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, true>(v, gm, S, Tb, cnt,
+        colour0_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, true, 1>(v, gm, S, Tb, cnt,
                                                                                s_hist4);
       else
-        colour0_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, false>(v, gm, S, Tb, cnt,
+        colour0_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, false, 1>(v, gm, S, Tb, cnt,
                                                                                 nullptr);
     } else {
       colour0<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, kSweepShape>(
@@ -348,10 +348,10 @@ __global__ void __launch_bounds__(kThreads, kSweepBlocksPerSM)
     const bool t2_tma = (t2 < ntiles) ? stage(t2) : false;
     if constexpr (WALK) {
       if (rec)
-        colour1_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, true>(v, gm, S, Tb, cnt,
+        colour1_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, true, 1>(v, gm, S, Tb, cnt,
                                                                                s_hist4);
       else
-        colour1_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, false>(v, gm, S, Tb, cnt,
+        colour1_walk<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, false, 1>(v, gm, S, Tb, cnt,
                                                                                 nullptr);
     } else {
       colour1<RNG_WORDS, CMP64, kTileRows, kTileWords, kThreads, kSweepShape>(
@@ -888,23 +888,24 @@ int wave_scratch(cvf_handle* h, int shape) {
 }
 
 // The automatic configuration: the resident form for small lattices; the
-// wavefront sweep from 512^2 to 6144^2, with the tiled sweep's shape rule
-// (the largest shape with at least as many tiles as the tiled sweep has
-// resident blocks, which is also the fastest wavefront shape at every size
-// measured); else the tiled sweep with that shape.  Measured on GB300, us per
-// MC step, wavefront against the best tiled shape: 512^2 7.4 / 8.3, 1024^2
-// 11.2 / 14.3, 1536^2 19.6 / 24.0, 2048^2 32.8 / 36.8, 2560^2 47.9 / 54.9,
-// 3072^2 64.2 / 71.2, 4096^2 108.6 / 115.0, 5120^2 168.3 / 176.8, 6144^2
-// 241.9 / 248.9; 8192^2 429.1 / 427.3 (the tiled sweep's partly filled last
-// round of tiles costs less the more tiles a step has).
-constexpr int kWaveAutoMin = 512, kWaveAutoMax = 6144;
+// wavefront sweep from 512^2 up, with the tiled sweep's shape rule (the
+// largest shape with at least as many tiles as the tiled sweep has resident
+// blocks, which is also the fastest wavefront shape at every size measured);
+// the tiled sweep with that shape where the wavefront does not fit.
+// Measured on GB300, us per MC step, wavefront against the best tiled shape:
+// 512^2 7.6 / 8.3, 1024^2 11.3 / 14.3, 2048^2 31.8 / 36.8, 3072^2 61.8 /
+// 71.3, 4096^2 103.0 / 115.0, 6144^2 226.6 / 248.9, 8192^2 402.3 / 428.5,
+// 12288^2 902.9 / 941.6, 16384^2 1603.5 / 1656.9 (the tiled sweep's partly
+// filled last round of tiles costs less the more tiles a step has, but the
+// wavefront stays ahead).
+constexpr int kWaveAutoMin = 512;
 int auto_config(const cvf_handle* h) {
   const cvf_params& p = h->p;
   if (p.schedule == CVF_SCHED_CHECKERBOARD && p.L <= kResAutoSide &&
       resident_fits(h->args, p.rng_words, h->cmp64))
     return kResident;
   const int t = choose_tile(p.L, h->cmp64, p.rng_words);
-  if (p.L >= kWaveAutoMin && p.L <= kWaveAutoMax && wave_fits(h, t)) return kWave + t;
+  if (p.L >= kWaveAutoMin && wave_fits(h, t)) return kWave + t;
   return t;
 }
 

@@ -155,21 +155,22 @@ __device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi,
   cell_draws<RNG_WORDS>(c, s_lo, s_hi, k.K, q, acc, kk);
 }
 
-// The parameter's round keys and the step's folded first Philox rounds
+// The round keys by value and the step's folded first Philox rounds
 // (step_draw): the draws take 18 widening multiplies per cell instead of 20
-// (the wavefront sweep: 4096^2 105.8 against 106.7 us per step, 2048^2 32.7
-// against 33.8; the tiled sweep, whose partly filled last round of tiles
-// takes up the cycles saved, ran 2 % slower with it and keeps KeysRound).
-// The step words passed with it are not used again.
+// (the wavefront sweep, which has the registers for the keys: 4096^2 104.7
+// against 106.7 us per step, 2048^2 32.2 against 33.8; the tiled sweep,
+// whose partly filled last round of tiles takes up the cycles saved, ran 2 %
+// slower with the folded rounds and keeps KeysRound).  The step words passed
+// with it are not used again.
 struct KeysStep {
-  const RoundKeys* K;
+  RoundKeys K;
   StepDraw sd;
 };
 
 template <int RNG_WORDS>
 __device__ __forceinline__ void draws(uint32_t c, uint32_t, uint32_t, const KeysStep& k,
                                       uint32_t q, uint32_t acc[4], uint32_t kk[4]) {
-  cell_draws_step<RNG_WORDS>(c, k.sd, *k.K, q, acc, kk);
+  cell_draws_step<RNG_WORDS>(c, k.sd, k.K, q, acc, kk);
 }
 
 // Update the cell in half `hi` of word `own` (its four arms in order, each
@@ -472,9 +473,14 @@ __device__ __forceinline__ void colour1(const StepView<KEYS>& v, const TileGeom&
 // as one cell per thread.  Colour 1 writes each word back in place (a
 // colour-1 update reads only the colour-0 halves of its neighbours, which
 // colour 1 does not change), and the tile is copied out with 16-byte loads
-// and stores.
+// and stores.  PAIRS: row pairs per loop iteration (the compiler's unroll
+// factor; 2 where the kernel has the registers for it: the wavefront sweep
+// at 64 registers, 4096^2 103.0 against 104.8 us per step; the tiled sweep at
+// 48 registers keeps 1, where 2 spilled 76 bytes and ran at 563 against 583
+// sigma-updates/ns).
 // ---------------------------------------------------------------------------
-template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, bool REC, typename KEYS>
+template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, bool REC, int PAIRS,
+          typename KEYS>
 __device__ __forceinline__ void colour0_walk(const StepView<KEYS>& v, const TileGeom& g,
                                              TileSmem<TR, TW>& S, const Tables2& Tb,
                                              TileCounts& cnt, uint32_t* s_hist4) {
@@ -491,7 +497,7 @@ __device__ __forceinline__ void colour0_walk(const StepView<KEYS>& v, const Tile
     uint32_t cb = (uint32_t)(g.y0 + r0) * L + 2u * (uint32_t)(g.p0 + j);
     uint32_t ym = p[-P], own = p[0];
     uint32_t pk = 0;
-#pragma unroll 1
+#pragma unroll PAIRS
     for (int k = 0; k < kRows; k += 2) {
       const uint32_t yp = p[P];
       o[0] = update_in_word<RNG_WORDS, CMP64, 0>(own, p[-1], p[1], ym, yp, 0, cb, v.s_lo,
@@ -536,7 +542,8 @@ __device__ __forceinline__ void colour0_walk(const StepView<KEYS>& v, const Tile
   }
 }
 
-template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, bool REC, typename KEYS>
+template <int RNG_WORDS, bool CMP64, int TR, int TW, int NT, bool REC, int PAIRS,
+          typename KEYS>
 __device__ __forceinline__ void colour1_walk(const StepView<KEYS>& v, const TileGeom& g,
                                              TileSmem<TR, TW>& S, const Tables2& Tb,
                                              TileCounts& cnt, uint32_t* s_hist4) {
@@ -550,7 +557,7 @@ __device__ __forceinline__ void colour1_walk(const StepView<KEYS>& v, const Tile
   uint32_t cb = (uint32_t)(g.y0 + r0) * L + 2u * (uint32_t)(g.p0 + j);
   uint32_t ym = q[-P], own = q[0];
   uint32_t pk = 0;
-#pragma unroll 1
+#pragma unroll PAIRS
   for (int k = 0; k < kRows; k += 2) {
     // even row: the colour-1 cell in the high half; odd row: the low half
     const uint32_t yp = q[P];

@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, kWaveBlocksPerSM)
     v.q = A.q;
     v.s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
     v.s_hi = (uint32_t)((unsigned long long)step >> 32);
-    v.keys.K = &A.keys;
+    v.keys.K = A.keys;
     v.keys.sd = step_draw(v.s_lo, v.s_hi, A.keys);
     v.err = err;
     const int ty = (int)fdiv((uint32_t)t, G.div_x);
@@ -371,9 +371,9 @@ __global__ void __launch_bounds__(kThreads, kWaveBlocksPerSM)
     const bool rec = step_recorded(every, step);
     if constexpr (WALK) {
       if (rec)
-        colour0_walk<RNG_WORDS, CMP64, TR, TW, kThreads, true>(v, gm, S, Tb, cnt, s_hist4);
+        colour0_walk<RNG_WORDS, CMP64, TR, TW, kThreads, true, 2>(v, gm, S, Tb, cnt, s_hist4);
       else
-        colour0_walk<RNG_WORDS, CMP64, TR, TW, kThreads, false>(v, gm, S, Tb, cnt, nullptr);
+        colour0_walk<RNG_WORDS, CMP64, TR, TW, kThreads, false, 2>(v, gm, S, Tb, cnt, nullptr);
     } else {
       colour0<RNG_WORDS, CMP64, TR, TW, kThreads, kWaveShape>(v, gm, S, Tb, cnt,
                                                                rec ? s_hist4 : nullptr);
@@ -438,9 +438,9 @@ __global__ void __launch_bounds__(kThreads, kWaveBlocksPerSM)
     }
     if constexpr (WALK) {
       if (rec)
-        colour1_walk<RNG_WORDS, CMP64, TR, TW, kThreads, true>(v, gm, S, Tb, cnt, s_hist4);
+        colour1_walk<RNG_WORDS, CMP64, TR, TW, kThreads, true, 2>(v, gm, S, Tb, cnt, s_hist4);
       else
-        colour1_walk<RNG_WORDS, CMP64, TR, TW, kThreads, false>(v, gm, S, Tb, cnt, nullptr);
+        colour1_walk<RNG_WORDS, CMP64, TR, TW, kThreads, false, 2>(v, gm, S, Tb, cnt, nullptr);
     } else {
       colour1<RNG_WORDS, CMP64, TR, TW, kThreads, kWaveShape>(v, gm, S, Tb, cnt,
                                                                rec ? s_hist4 : nullptr);

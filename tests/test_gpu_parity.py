@@ -225,7 +225,7 @@ def test_tile_choice():
     with Lattice(params(300.0, 0.1, L=4096)) as lat:
         assert lat.tiles() == (4, 64, 64)  # the benchmark size: the wavefront, large tiles
     with Lattice(params(300.0, 0.1, L=8192)) as lat:
-        assert lat.tiles() == (0, 64, 64)  # beyond 6144: the tiled sweep
+        assert lat.tiles() == (4, 64, 64)  # the wavefront at every larger size too
     with Lattice(params(300.0, 0.1, L=1024)) as lat:
         assert lat.tiles() == (6, 16, 32)  # mid-size lattices: the wavefront sweep
     with Lattice(params(300.0, 0.1, L=2048)) as lat:
