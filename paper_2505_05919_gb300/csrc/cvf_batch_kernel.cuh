@@ -275,7 +275,23 @@ __global__ void __launch_bounds__(NT, batch_min_blocks(NT))
     if constexpr (NT >= 512) v.keys.K = s_keys;  // after the barrier above
     TileCounts cnt{0, 0, 0};
     const bool rec = step_recorded(vc->record_every, step);
-    colour0<RNG_WORDS, CMP64, TR, TW, NT, kBatchShape>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
+    // replicas whose tiles are all full (and rows 16-byte aligned) take the
+    // column-walking colour phases where the block shape allows them (each
+    // thread group an even number of rows): the 256 replicas of the batched
+    // workload on 64 x 64-word tiles, 140.8 -> 126.4 us per step
+    constexpr bool kWalkShape =
+        NT % TW == 0 && TR % (NT / TW) == 0 && (TR / (NT / TW)) % 2 == 0;
+    const bool walk = kWalkShape && L % TR == 0 && Lh % TW == 0 && (Lh & 3) == 0;
+    if constexpr (kWalkShape) {
+      if (walk) {
+        if (rec)
+          colour0_walk<RNG_WORDS, CMP64, TR, TW, NT, true, 1>(v, gm, S, Tb, cnt, s_hist4);
+        else
+          colour0_walk<RNG_WORDS, CMP64, TR, TW, NT, false, 1>(v, gm, S, Tb, cnt, nullptr);
+      }
+    }
+    if (!walk)
+      colour0<RNG_WORDS, CMP64, TR, TW, NT, kBatchShape>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
     // S.in is free: take the next item and, when it can start, copy its tile.
     // The last warp takes it: it has the fewest rows (and no ring cells) in
     // the first colour, so the take overlaps the other warps' remaining work.
@@ -310,7 +326,16 @@ __global__ void __launch_bounds__(NT, batch_min_blocks(NT))
       const TileGeom gn = tile_geom<TR, TW>(Ln, Lhn, (n_tile / tx) * TR, (n_tile % tx) * TW);
       stage_async16<TR, TW, NT>(vn, gn, S);
     }
-    colour1<RNG_WORDS, CMP64, TR, TW, NT, kBatchShape>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
+    if constexpr (kWalkShape) {
+      if (walk) {
+        if (rec)
+          colour1_walk<RNG_WORDS, CMP64, TR, TW, NT, true, 1>(v, gm, S, Tb, cnt, s_hist4);
+        else
+          colour1_walk<RNG_WORDS, CMP64, TR, TW, NT, false, 1>(v, gm, S, Tb, cnt, nullptr);
+      }
+    }
+    if (!walk)
+      colour1<RNG_WORDS, CMP64, TR, TW, NT, kBatchShape>(v, gm, S, Tb, cnt, rec ? s_hist4 : nullptr);
     if (rec) {  // block-uniform: only on recorded steps
       __syncthreads();
       hist_flush(s_hist4, ctl->acc_hist);
