@@ -134,6 +134,21 @@ __global__ void k_observables(const VolumeArgs* __restrict__ V, const Ctrl* ctl,
   }
 }
 
+// The first word of w[0, n) that is not a valid cell for q (a spare bit set or
+// an arm >= q), as an atomic minimum into *first (left at its initial value,
+// the caller's all-ones, when every word is valid).
+__global__ void __launch_bounds__(kThreads) k_first_invalid(const uint16_t* __restrict__ w,
+                                                            long long n, uint32_t q,
+                                                            unsigned long long* first) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint32_t x = w[i];
+    if ((x & 0x8888u) || (x & 7u) >= q || ((x >> 4) & 7u) >= q || ((x >> 8) & 7u) >= q ||
+        ((x >> 12) & 7u) >= q)
+      atomicMin(first, (unsigned long long)i);
+  }
+}
+
 // N_q' of a lattice (the number of sigma variables in each state) added to
 // out[0..8), and its equal in-cell pairs (N_sigma) added to out[8].
 __global__ void __launch_bounds__(kThreads) k_histogram(const uint16_t* __restrict__ state,
@@ -948,24 +963,6 @@ int recount_into_ctrl(cvf_handle* h) {
 // nibble's bit 3 set), n if none.  Four cells per 64-bit load: with the
 // guard bits clear every nibble v is <= 7, and v + 8 - q sets the nibble's
 // bit 3 exactly when v >= q (no carry leaves a nibble: v + 8 - q <= 13).
-size_t first_invalid_cell(const uint16_t* host, size_t n, uint32_t q) {
-  const uint64_t G = 0x8888888888888888ull;
-  const uint64_t add = (uint64_t)(8u - q) * 0x1111111111111111ull;
-  size_t i = 0;
-  for (; i + 4 <= n; i += 4) {
-    uint64_t x;
-    std::memcpy(&x, host + i, sizeof(x));
-    if ((x & G) | ((x + add) & G)) break;
-  }
-  for (; i < n; ++i) {
-    const uint32_t w = host[i];
-    if ((w & 0x8888u) || ((w & 7u) >= q) || (((w >> 4) & 7u) >= q) || (((w >> 8) & 7u) >= q) ||
-        (((w >> 12) & 7u) >= q))
-      return i;
-  }
-  return n;
-}
-
 int build_graph(cvf_handle* h) {
   if (h->graph) return CVF_OK;
   cudaGraph_t g = nullptr;
@@ -1207,13 +1204,28 @@ int cvf_set_state(cvf_handle* h, const uint16_t* host, size_t n, double V_iso, i
   if (!(V_iso >= (double)h->N) || !std::isfinite(V_iso))
     return set_error(CVF_EINVAL, "V_iso=%g below the hard core N v0 = %lld", V_iso, h->N);
   if (sweep < 0) return set_error(CVF_EINVAL, "sweep must be >= 0");
-  const size_t bad = first_invalid_cell(host, n, (uint32_t)h->p.q);
-  if (bad < n)
-    return set_error(CVF_EINVAL, "word %zu = 0x%04x is not a valid cell for q = %d", bad,
+  // The words go to the state pair's other buffer (free between calls) and
+  // are checked there on the device; only a valid lattice replaces the
+  // current one (a device copy where the new step parity needs the other
+  // buffer), so an invalid upload leaves the handle as it was.
+  const size_t bytes = sizeof(uint16_t) * n;
+  uint16_t* up = h->state + (size_t)((h->sweep_host + 1) & 1) * h->N;
+  CVF_CUDA_CHECK(cudaMemcpyAsync(up, host, bytes, cudaMemcpyHostToDevice, h->stream));
+  CVF_CUDA_CHECK(cudaMemsetAsync(h->rc_dev, 0xFF, sizeof(unsigned long long), h->stream));
+  k_first_invalid<<<h->grid_cells, kThreads, 0, h->stream>>>(up, h->N, (uint32_t)h->p.q,
+                                                              h->rc_dev);
+  CVF_CUDA_CHECK(cudaGetLastError());
+  CVF_CUDA_CHECK(cudaMemcpyAsync(h->host_pinned, h->rc_dev, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, h->stream));
+  CVF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  const unsigned long long bad = *reinterpret_cast<const unsigned long long*>(h->host_pinned);
+  if (bad < (unsigned long long)n)
+    return set_error(CVF_EINVAL, "word %llu = 0x%04x is not a valid cell for q = %d", bad,
                      (unsigned)host[bad], h->p.q);
+  uint16_t* dst = h->state + (size_t)(sweep & 1) * h->N;
+  if (dst != up)
+    CVF_CUDA_CHECK(cudaMemcpyAsync(dst, up, bytes, cudaMemcpyDeviceToDevice, h->stream));
   h->sweep_host = sweep;
-  CVF_CUDA_CHECK(cudaMemcpyAsync(current(h), host, sizeof(uint16_t) * n, cudaMemcpyHostToDevice,
-                                 h->stream));
   k_set_ctrl<<<1, 32, 0, h->stream>>>(h->vol_dev, h->ctrl, V_iso, sweep, h->N);
   int rc = recount_into_ctrl(h);
   if (rc) return rc;
