@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(NT, batch_min_blocks(NT))
   __shared__ long long n_rel;
   __shared__ uint32_t s_q;
   __shared__ uint32_t s_hist4[4];
-  __shared__ RoundKeys s_keys;  // the current replica's round keys (broadcast reads)
+  __shared__ RoundKeys s_keys;  // the current replica's round keys (copied into registers per item)
   __shared__ double s_xch;      // the volume item's two warps' exchange
   __shared__ int s_tab_rep, s_tab_g, s_key_rep;  // whose rows / keys Tb and s_keys hold
   // a replica's step count when the launch began (s_step_rep's): only this
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(NT, batch_min_blocks(NT))
     }
     const int L = R.L, Lh = L >> 1;
     const long long N = (long long)L * L;
-    using Keys = std::conditional_t<(NT >= 512), KeysInRegs, KeysRound>;
+    using Keys = KeysStep;
     StepView<Keys> v;
     v.src = reinterpret_cast<const uint32_t*>(R.state + (size_t)(step & 1) * N);
     v.dst = reinterpret_cast<uint32_t*>(R.state + (size_t)((step + 1) & 1) * N);
@@ -251,7 +251,6 @@ __global__ void __launch_bounds__(NT, batch_min_blocks(NT))
     v.q = R.q;
     v.s_lo = (uint32_t)((unsigned long long)step & 0xFFFFFFFFu);
     v.s_hi = (uint32_t)((unsigned long long)step >> 32);
-    if constexpr (NT < 512) v.keys.K = &s_keys;
     v.err = &W->error;
     const TileGeom gm = tile_geom<TR, TW>(L, Lh, (t / tiles_x) * TR, (t % tiles_x) * TW);
     if (staged)
@@ -272,7 +271,12 @@ __global__ void __launch_bounds__(NT, batch_min_blocks(NT))
       s_step_rep = rep;
       s_step0 = step - rel;
     }
-    if constexpr (NT >= 512) v.keys.K = s_keys;  // after the barrier above
+    // the replica's keys by value and the step's folded first Philox rounds
+    // (KeysStep; the batched workload on 64 x 64-word tiles: 126.6 -> 125.7
+    // us per step, on 32 x 32: 137.8 -> 134.4, against the keys read from
+    // shared memory in every round), after the barrier above
+    v.keys.K = s_keys;
+    v.keys.sd = step_draw(v.s_lo, v.s_hi, s_keys);
     TileCounts cnt{0, 0, 0};
     const bool rec = step_recorded(vc->record_every, step);
     // replicas whose tiles are all full (and rows 16-byte aligned) take the

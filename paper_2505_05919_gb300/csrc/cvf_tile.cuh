@@ -126,10 +126,9 @@ __device__ __forceinline__ uint32_t count_word4(uint32_t w) {
   return c;
 }
 
-// Philox key material of the lattice being swept: its precomputed round keys
-// (a kernel parameter for the single lattice, read from the constant bank; a
-// shared-memory copy of the current replica's keys in the batched kernel, read
-// by broadcast loads).
+// Philox key material of the lattice being swept: a pointer to its
+// precomputed round keys (the tiled sweep's kernel parameter, read from the
+// constant bank).
 struct KeysRound {
   const RoundKeys* K;
 };
@@ -141,9 +140,8 @@ __device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi, 
 }
 
 // The round keys held by value: a copy of a kernel parameter's keys (the
-// single-lattice sweep; the compiler takes them from the parameter bank as
-// instruction operands) or of the current replica's (the batched 512-thread
-// kernels, which keep them in registers for an item).
+// small lattice resident in one cluster; the compiler takes them from the
+// parameter bank as instruction operands).
 struct KeysInRegs {
   RoundKeys K;
 };
@@ -157,11 +155,11 @@ __device__ __forceinline__ void draws(uint32_t c, uint32_t s_lo, uint32_t s_hi,
 
 // The round keys by value and the step's folded first Philox rounds
 // (step_draw): the draws take 18 widening multiplies per cell instead of 20
-// (the wavefront sweep, which has the registers for the keys: 4096^2 104.7
-// against 106.7 us per step, 2048^2 32.2 against 33.8; the tiled sweep,
-// whose partly filled last round of tiles takes up the cycles saved, ran 2 %
-// slower with the folded rounds and keeps KeysRound).  The step words passed
-// with it are not used again.
+// (the wavefront sweep and the batched kernel, which have the registers for
+// the keys: 4096^2 104.7 against 106.7 us per step, 2048^2 32.2 against
+// 33.8; the tiled sweep, whose partly filled last round of tiles takes up
+// the cycles saved, ran 2 % slower with the folded rounds and keeps
+// KeysRound).  The step words passed with it are not used again.
 struct KeysStep {
   RoundKeys K;
   StepDraw sd;
