@@ -178,9 +178,10 @@ int cvf_get_window(cvf_handle *h, int32_t x0, int32_t y0, int32_t W, int32_t H,
 
 /* Replaces the lattice by host[0..n) (n = L*L), sets V_iso and the step
  * counter, recounts N_HB_raw and N_sigma, and clears the acceptance
- * counters and the ring.  Every word is validated on the host first
- * (arms < q, bits 3, 7, 11, 15 zero): CVF_EINVAL otherwise, with nothing
- * changed.
+ * counters and the ring.  The words are uploaded into the state pair's free
+ * buffer and validated there on the device before they replace the lattice
+ * (arms < q, bits 3, 7, 11, 15 zero): CVF_EINVAL otherwise, naming the
+ * first invalid word, with nothing changed.
  * V_iso must be >= N (the hard core).  Synchronises. */
 int cvf_set_state(cvf_handle *h, const uint16_t *host, size_t n, double V_iso,
                   int64_t sweep);
