@@ -205,7 +205,7 @@ int cvf_state_device_ptr(cvf_handle *h, void **dev_ptr);
  * wavefront; the volume moves decided ahead by one block; L a multiple of 8
  * and at least 3 x 3 tiles); -1 = automatic (chosen at creation: the
  * resident form for small lattices, else the largest tile shape whose tiles
- * fill every resident block, swept as a wavefront from L = 512 up).  The result does not depend on the config;
+ * fill every resident block, swept as a wavefront from L = 256 up).  The result does not depend on the config;
  * set_tiles waits for the stream.  CVF_EINVAL for other values, or a config
  * that does not apply to the lattice. */
 int cvf_set_tiles(cvf_handle *h, int32_t config);

@@ -903,17 +903,18 @@ int wave_scratch(cvf_handle* h, int shape) {
 }
 
 // The automatic configuration: the resident form for small lattices; the
-// wavefront sweep from 512^2 up, with the tiled sweep's shape rule (the
+// wavefront sweep from 256^2 up, with the tiled sweep's shape rule (the
 // largest shape with at least as many tiles as the tiled sweep has resident
 // blocks, which is also the fastest wavefront shape at every size measured);
 // the tiled sweep with that shape where the wavefront does not fit.
 // Measured on GB300, us per MC step, wavefront against the best tiled shape:
+// 256^2 6.6 / 7.5, 320^2 6.4 / 7.5, 384^2 7.0 / 7.4, 448^2 7.3 / 8.1,
 // 512^2 7.6 / 8.3, 1024^2 11.3 / 14.3, 2048^2 31.8 / 36.8, 3072^2 61.8 /
 // 71.3, 4096^2 103.0 / 115.0, 6144^2 226.6 / 248.9, 8192^2 402.3 / 428.5,
 // 12288^2 902.9 / 941.6, 16384^2 1603.5 / 1656.9 (the tiled sweep's partly
 // filled last round of tiles costs less the more tiles a step has, but the
 // wavefront stays ahead).
-constexpr int kWaveAutoMin = 512;
+constexpr int kWaveAutoMin = 256;
 int auto_config(const cvf_handle* h) {
   const cvf_params& p = h->p;
   if (p.schedule == CVF_SCHED_CHECKERBOARD && p.L <= kResAutoSide &&
