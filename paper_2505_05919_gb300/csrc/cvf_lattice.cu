@@ -905,8 +905,10 @@ int wave_scratch(cvf_handle* h, int shape) {
 // The automatic configuration: the resident form for small lattices; the
 // wavefront sweep from 256^2 up, with the tiled sweep's shape rule (the
 // largest shape with at least as many tiles as the tiled sweep has resident
-// blocks, which is also the fastest wavefront shape at every size measured);
-// the tiled sweep with that shape where the wavefront does not fit.
+// blocks: the fastest wavefront shape at 768^2, 1536^2, 2048^2 and from
+// 2560^2 up, within 1.2 % of it at 1024^2, where 32 x 32 words ran at 11.2
+// against 11.3 us per step); the tiled sweep with that shape where the
+// wavefront does not fit.
 // Measured on GB300, us per MC step, wavefront against the best tiled shape:
 // 256^2 6.6 / 7.5, 320^2 6.4 / 7.5, 384^2 7.0 / 7.4, 448^2 7.3 / 8.1,
 // 512^2 7.6 / 8.3, 1024^2 11.3 / 14.3, 2048^2 31.8 / 36.8, 3072^2 61.8 /
